@@ -1,0 +1,152 @@
+"""FP64 CPU oracle of Holographic Radiance Cascades (test infrastructure).
+
+This package is TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the
+benchmark's CPU-baseline leg use it to check and time the CUDA path.  The
+product package never imports it, and it shares no code with the product.
+
+``hrc_oracle.c`` follows Algorithm 1 and Eqs. 7-20 step by step in double
+precision; ``recursive.py`` is a second, independent formulation of
+Eqs. 14-20 (memoised recursion, pure Python, tiny grids only).
+
+Images are numpy arrays: emission ``e[C][H][W]`` and extinction ``s[H][W]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hrc_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP on)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.orc_trace.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D]
+        L.orc_trace.restype = None
+        L.orc_arc.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.orc_arc.restype = ctypes.c_double
+        L.orc_levels.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.orc_levels.restype = ctypes.c_int
+        L.orc_fluence.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.orc_fluence.restype = None
+        L.orc_frame_level.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.orc_frame_level.restype = ctypes.c_long
+        L.orc_fluence_adjoint.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _D, _D]
+        L.orc_fluence_adjoint.restype = None
+        L.orc_bruteforce.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.orc_bruteforce.restype = None
+        L.orc_num_threads.argtypes = []
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        L.orc_set_num_threads.restype = None
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _img(e, s):
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    if e.ndim == 2:
+        e = e[None]
+    C, H, W = e.shape
+    assert s.shape == (H, W)
+    return e, s, C, H, W
+
+
+def trace(e, s, p, q):
+    """Trace(p, q) of Eq. 9 in image coordinates: returns (L[C], T)."""
+    e, s, C, H, W = _img(e, s)
+    L = np.zeros(C)
+    T = np.zeros(1)
+    lib().orc_trace(_p(e), _p(s), C, W, H, float(p[0]), float(p[1]), float(q[0]), float(q[1]), _p(L), _p(T))
+    return L, float(T[0])
+
+
+def arc(n: int, ip: int) -> float:
+    """A_n(i) of Eq. 13 for the cone i = ip + 1/2."""
+    return lib().orc_arc(n, ip)
+
+
+def levels(U: int, cascades: int = 0) -> int:
+    return lib().orc_levels(U, cascades)
+
+
+def fluence(e, s, cascades: int = 0) -> np.ndarray:
+    """Algorithm 1 (Lighting): F[C][H][W] in float64."""
+    e, s, C, H, W = _img(e, s)
+    F = np.zeros((C, H, W))
+    lib().orc_fluence(_p(e), _p(s), C, W, H, cascades, _p(F))
+    return F
+
+
+def frame_dims(q: int, W: int, H: int):
+    return (W, H) if q < 2 else (H, W)
+
+
+def frame_level(e, s, q: int, which: str, n: int, cascades: int = 0) -> np.ndarray:
+    """T_n (which='T', shape [U_n][2^n+1][V][C+1]) or R_n (which='R', shape
+    [U_n][2^n][V][C]) of quadrant frame q."""
+    e, s, C, H, W = _img(e, s)
+    U, V = frame_dims(q, W, H)
+    Un = -(-U // (1 << n))
+    w = 0 if which == "T" else 1
+    cnt = lib().orc_frame_level(_p(e), _p(s), C, W, H, q, cascades, w, n, None)
+    if cnt < 0:
+        raise ValueError(f"level {which}_{n} does not exist")
+    out = np.zeros(cnt)
+    lib().orc_frame_level(_p(e), _p(s), C, W, H, q, cascades, w, n, _p(out))
+    if w == 0:
+        return out.reshape(Un, (1 << n) + 1, V, C + 1)
+    return out.reshape(Un, 1 << n, V, C)
+
+
+def fluence_adjoint(e, s, gF, cascades: int = 0):
+    """Gradient of sum(gF * F) w.r.t. (e, s), float64."""
+    e, s, C, H, W = _img(e, s)
+    gF = np.ascontiguousarray(gF, dtype=np.float64).reshape(C, H, W)
+    ge = np.zeros((C, H, W))
+    gs = np.zeros((H, W))
+    lib().orc_fluence_adjoint(_p(e), _p(s), _p(gF), C, W, H, cascades, _p(ge), _p(gs))
+    return ge, gs
+
+
+def bruteforce(e, s, M: int = 4096) -> np.ndarray:
+    """Eq. 1 by brute force with M uniformly spaced directions per pixel."""
+    e, s, C, H, W = _img(e, s)
+    F = np.zeros((C, H, W))
+    lib().orc_bruteforce(_p(e), _p(s), C, W, H, M, _p(F))
+    return F
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    lib().orc_set_num_threads(n)
