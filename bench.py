@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Benchmark of the HRC hot path on GB300.
+
+A step is one HRC frame (Algorithm 1: trace T_0..T_2, merge up T_3..T_N,
+merge down R_{N-1}..R_0, four-quadrant fluence sum) over the 1024 x 1024,
+three-channel volumetric workload, fp32, with the inputs resident in HBM.
+The L2 is flushed (a 256 MB write) before every timed step, outside the
+timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (the method has no other reference
+implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "volumetric1024": "1024x1024, C=3, sigma_t = 5 fBm (4 octaves) + 30 emitter disks + 100 walls "
+                      "(sigma_t 200, 1-3 px), seed 2",
+    "fog512": "512x512, C=3, fog 0.02 + 20 emitter disks + 40 rotated rectangles (sigma_t 50), seed 1",
+    "fog2048": "2048x2048, C=3, as fog512 scaled, seed 5",
+    "disks64": "64x64, C=1, vacuum, 3 emitter disks, 2 opaque boxes, seed 0",
+}
+PAPER_MS = {"volumetric1024": 7.67, "fog512": 1.85, "fog2048": 33.9}   # Table 1, RTX 3080 Laptop
+METRIC = "HRC ms/frame & HBM GB/s (% peak) at 1024²; fwd+bwd ms; batched scenes/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2505_02041_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind, workload):
+    """Per-launch DRAM bytes of `kind` from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = source_hash()
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 4 and parts[0] == kind and parts[1] == workload and parts[3] == src:
+                return float(parts[2])
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    """FP64 CPU oracle, as it stands, on the host cores (rank 0 only)."""
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_2505_02041_gb300 import scenes
+    e, s = scenes.scene_by_name(args.workload)
+    for _ in range(args.warmup):
+        oracle.fluence(e, s)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fluence(e, s)
+        times.append((time.perf_counter() - t0) * 1e3)
+    ms = statistics.mean(times)
+    C, H, W = e.shape
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms/frame", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "precision": "fp64 CPU oracle"},
+        "cpu_baseline": {"value": ms, "unit": "ms/frame", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} full {W}x{H} C={C} frames (OpenMP over rows)"},
+        "e2e": {"value": ms, "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(workload, budget_s=20.0):
+    import oracle
+    from paper_2505_02041_gb300 import scenes
+    e, s = scenes.scene_by_name(workload)
+    C, H, W = e.shape
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle.fluence(e, s)
+        times.append((time.perf_counter() - t0) * 1e3)
+        if time.perf_counter() - t_start > budget_s * 0.5 or len(times) >= 5:
+            break
+    return {"value": statistics.mean(times), "unit": "ms/frame", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(times)} full {W}x{H} C={C} frames of the same workload (FP64, OpenMP over rows)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2505_02041_gb300 import HRC, _lib, scenes
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    e_np, s_np = scenes.scene_by_name(args.workload)
+    C, H, W = e_np.shape
+    e = torch.from_numpy(e_np).to(dev)
+    s = torch.from_numpy(s_np).to(dev)
+    F = torch.empty((C, H, W), dtype=torch.float32, device=dev)
+    h = HRC(W, H, C, 0, args.precision)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        h.forward(e, s, F)
+    launches_per_step = h.launch_count()
+    _lib.hrc_set_timing(h.ctx, True)
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    per_kind = {}
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.forward(e, s, F)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        for kind, level, ms, by in _lib.hrc_get_timing(h.ctx):
+            d = per_kind.setdefault(kind, [0.0, 0.0, 0])
+            d[0] += ms
+            d[1] += by
+            d[2] += 1
+    barrier()
+    clk = clocks.stop()
+    _lib.hrc_set_timing(h.ctx, False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_frame = total_ms / (args.steps * world)
+
+    # end to end: host buffers through the C ABI, copies included
+    e_h = torch.from_numpy(e_np).pin_memory()
+    s_h = torch.from_numpy(s_np).pin_memory()
+    F_h = torch.empty((C, H, W), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        h.forward_host(e_h, s_h, F_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h.forward_host(e_h, s_h, F_h)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    hbm_peak, peak_kind = peaks()
+    dom = max(per_kind.items(), key=lambda kv: kv[1][0])
+    kind, (kms, kbytes, kcount) = dom
+    achieved = (kbytes / kcount) / ((kms / kcount) * 1e-3) / 1e9
+    phases = {k: {"ms_per_frame": v[0] / args.steps, "launches_per_frame": v[2] / args.steps,
+                  "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None}
+              for k, v in sorted(per_kind.items())}
+    frame_bytes = sum(v[1] for v in per_kind.values()) / args.steps
+    line = {
+        "metric": METRIC, "value": ms_per_frame, "unit": "ms/frame", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": (ms_per_frame / PAPER_MS[args.workload]) if args.workload in PAPER_MS else None,
+        "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "precision": args.precision,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "flushed (256 MB write) before every timed step, outside the timed events",
+                   "baseline_context": "paper Table 1 on an RTX 3080 Laptop with fp16 storage"},
+        "roofline": {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(kind, args.workload)},
+        "frame": {"algorithmic_bytes": frame_bytes, "GBps": frame_bytes / (ms_per_frame * 1e-3) / 1e9,
+                  "frac_of_peak": frame_bytes / (ms_per_frame * 1e-3) / 1e9 / hbm_peak},
+        "phases": phases,
+        "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": (C + 1) * H * W * 4,
+                "d2h_bytes_per_step": C * H * W * 4},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="volumetric1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * hrc.h -- C ABI of the GB300 Holographic Radiance Cascades (HRC) library.
+ *
+ * The library computes the 2D fluence F(p) of Eq. 1 (Sec. 3) by the HRC
+ * method of Sec. 4: directly traced intervals T_0..T_2 (Sec. 4.2, Eq. 9),
+ * the acceleration structure T_3..T_N built by interval extension (Sec. 4.1,
+ * Eqs. 18-20), the merge down the cascades R_{N-1}..R_0 (Eqs. 13-17) and the
+ * sum over four quadrants (Algorithm 1, procedure Lighting), plus the exact
+ * adjoint of all of it.  No cross blur (Eq. 21) is applied.
+ *
+ * Data conventions (shared by every entry point):
+ *   - Images are row-major: emission e[C][H][W] (the per-unit-length source
+ *     term integrated in Eq. 4), extinction sigma_t[H][W] (Eq. 2, per pixel
+ *     length, one channel shared by all C colours), fluence F[C][H][W].
+ *     Pixel (x, y) is the unit square [x, x+1] x [y, y+1]; its probe sits at
+ *     the centre.  Cells outside the grid are vacuum with no emission.
+ *   - Unless stated otherwise, tensor pointers are DEVICE pointers to
+ *     contiguous fp32 data, 16-byte aligned.  The library never frees or
+ *     keeps ownership of caller memory.
+ *   - A context owns every scratch buffer (all T and R levels, gradients).
+ *     It allocates them in hrc_create / hrc_create_batched (and, for the FP64
+ *     test precision, in hrc_set_precision); compute calls allocate nothing.
+ *   - Compute calls are asynchronous on the context's stream: HRC_OK means
+ *     "enqueued".  Argument errors are reported synchronously; an
+ *     asynchronous CUDA error surfaces as HRC_ECUDA on a later call.
+ *   - NaN / Inf inputs are accepted and propagate; negative sigma_t is not
+ *     rejected (the formulas are analytic in sigma_t).
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - hrc_last_error returns a static description of the last failure.
+ */
+#ifndef HRC_H
+#define HRC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hrc_ctx hrc_ctx;
+
+typedef enum {
+    HRC_OK = 0,
+    HRC_EINVAL = 1,    /* bad argument (size, null pointer, misalignment)      */
+    HRC_ENOMEM = 2,    /* device allocation failed                              */
+    HRC_ECUDA = 3,     /* CUDA launch or runtime error                          */
+    HRC_ESTATE = 4,    /* call out of order (e.g. backward before forward)      */
+    HRC_ETIMEOUT = 5,  /* a bounded device-side wait gave up (batched path)     */
+    HRC_EBOUNDS = 6    /* a device-side bounds check fired (debug builds)       */
+} hrc_status;
+
+typedef enum {
+    HRC_FP32 = 0,       /* intervals and fluence stored and computed in fp32          */
+    HRC_FP16_LOGT = 1,  /* radiance/fluence stored fp16, transmittance as fp32
+                           tau = -ln T; arithmetic in fp32 (Sec. 5 stores fp16)   */
+    HRC_BF16_LOGT = 2,  /* as above with bf16 radiance/fluence storage              */
+    HRC_FP64_TEST = 3   /* fp64 everywhere; only for finite-difference checks via
+                           hrc_fluence_f64 / hrc_fluence_backward_f64              */
+} hrc_precision;
+
+/* Create a context for one W x H scene with `channels` colours
+ * (1 <= channels <= 4, W, H >= 1).  `cascades` <= 0 selects
+ * N = ceil(log2 U) per quadrant frame (U = W for +-x, U = H for +-y; Sec. 4.2);
+ * a positive value caps N (R_cascades is then taken as 0, as R_N is).
+ * Allocates every buffer of the forward and backward passes on the current
+ * device.  Returns HRC_EINVAL / HRC_ENOMEM / HRC_ECUDA on failure (*out = 0). */
+hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out);
+
+/* Release the context and its device buffers (synchronises its stream). */
+hrc_status hrc_destroy(hrc_ctx *ctx);
+
+/* Stream for all later calls (a cudaStream_t; NULL = legacy default stream). */
+hrc_status hrc_set_stream(hrc_ctx *ctx, void *cuda_stream);
+
+/* Storage precision of the interval and fluence buffers (see hrc_precision).
+ * Switching to HRC_FP64_TEST allocates its fp64 buffers once. */
+hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec);
+
+/* Forward pass, Algorithm 1 (Lighting) without the Eq. 21 blur:
+ * out[c][y][x] = sum over the four quadrant frames of R_0([u+1, v], 1/2).
+ * emission [C][H][W], sigma_t [H][W], out [C][H][W]: device fp32.
+ * The context remembers (borrows) emission and sigma_t for the backward
+ * pass; the caller keeps them alive and unchanged until then. */
+hrc_status hrc_fluence(hrc_ctx *ctx, const float *emission, const float *sigma_t, float *out);
+
+/* Same computation from HOST buffers: copies emission and sigma_t to
+ * context-owned device buffers, runs hrc_fluence, copies the fluence back to
+ * `out` (host) and waits for the stream.  Host buffers may be pageable or
+ * pinned (pinned is faster).  A later hrc_fluence_backward borrows the
+ * context's own device copies. */
+hrc_status hrc_fluence_host(hrc_ctx *ctx, const float *emission, const float *sigma_t, float *out);
+
+/* Adjoint of the last hrc_fluence on this context: given dLoss/dF (grad_F,
+ * [C][H][W]), writes dLoss/d emission ([C][H][W]) and dLoss/d sigma_t
+ * ([H][W]).  Outputs are overwritten, not accumulated.  The intervals are
+ * recomputed from the borrowed inputs (no forward-time storage is assumed).
+ * HRC_ESTATE if no forward ran on this context. */
+hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_emission,
+                                float *grad_sigma_t);
+
+/* FP64 instance of hrc_fluence / hrc_fluence_backward (device fp64 buffers,
+ * same layouts); requires hrc_set_precision(ctx, HRC_FP64_TEST). */
+hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *sigma_t, double *out);
+hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *grad_emission,
+                                    double *grad_sigma_t);
+
+/* Batched context: n scenes of sizes W[i] x H[i], one channel count.  The
+ * scenes' tensors are packed back to back; hrc_scene_offsets gives the
+ * element offsets (n + 1 entries each: emission/out offsets in floats of the
+ * [C][H][W] blocks, sigma offsets in floats of the [H][W] blocks). */
+hrc_status hrc_create_batched(int n, const int *W, const int *H, int channels, int cascades,
+                              hrc_ctx **out);
+hrc_status hrc_scene_offsets(const hrc_ctx *ctx, long long *emis_off, long long *sigma_off);
+
+/* Forward / backward of every scene of a batched context in one persistent,
+ * CUDA-graph-launched kernel; same semantics as the single-scene calls.
+ * HRC_ETIMEOUT if a bounded device-side dependency wait gave up. */
+hrc_status hrc_fluence_batched(hrc_ctx *ctx, const float *emission, const float *sigma_t, float *out);
+hrc_status hrc_fluence_backward_batched(hrc_ctx *ctx, const float *grad_F, float *grad_emission,
+                                        float *grad_sigma_t);
+
+/* Introspection for tests: copies level n of quadrant frame q (0..3) from
+ * the last forward into `dst` (device fp32).  which = 0: T_n as
+ * [U_n][2^n+1][V][C+1] (C radiances then the transmittance T, linear even in
+ * the log-T precisions); which = 1: R_n as [U_n][2^n][V][C].  *count
+ * receives the element count; dst may be NULL to query it.  HRC_EINVAL if
+ * the level does not exist. */
+hrc_status hrc_copy_level(hrc_ctx *ctx, int q, int which, int n, float *dst, long long *count);
+
+/* Number of kernel launches the last compute call enqueued. */
+int hrc_last_launch_count(const hrc_ctx *ctx);
+
+/* Per-launch timing.  With timing enabled, every kernel a compute call
+ * enqueues is bracketed by CUDA events on the context's stream.
+ * hrc_get_timing synchronises the stream and fills up to `cap` records of
+ * the last compute call; it returns the number of records (or -1 on error).
+ * `kind`: 0 trace T_0..T_2, 1 merge up, 2 merge down, 3 fluence sum,
+ * 4 adjoint sum, 5 adjoint merge down, 6 adjoint merge up, 7 adjoint trace,
+ * 8 batched persistent kernel, 9 other.  `bytes` is the launch's
+ * algorithmic traffic (each array it consumes read once, each array it
+ * produces written once). */
+typedef struct { int kind; int level; float ms; double bytes; } hrc_kernel_time;
+hrc_status hrc_set_timing(hrc_ctx *ctx, int enable);
+int hrc_get_timing(hrc_ctx *ctx, hrc_kernel_time *out, int cap);
+
+/* Static description of the last error on ctx (or of the last failed
+ * creation when ctx is NULL). */
+const char *hrc_last_error(const hrc_ctx *ctx);
+
+/* Library version string. */
+const char *hrc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HRC_H */

@@ -1,0 +1,187 @@
+"""ctypes binding of the C ABI in include/hrc.h (argument marshalling only).
+
+The functions keep the C names (``hrc_create``, ``hrc_fluence`` ...).  Every
+step of the computation runs in the CUDA kernels of ``libhrc.so``; there is
+no Python or CPU fallback: if the library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhrc.so")
+
+HRC_OK, HRC_EINVAL, HRC_ENOMEM, HRC_ECUDA, HRC_ESTATE, HRC_ETIMEOUT, HRC_EBOUNDS = range(7)
+HRC_FP32, HRC_FP16_LOGT, HRC_BF16_LOGT, HRC_FP64_TEST = range(4)
+STATUS_NAMES = ["HRC_OK", "HRC_EINVAL", "HRC_ENOMEM", "HRC_ECUDA", "HRC_ESTATE", "HRC_ETIMEOUT", "HRC_EBOUNDS"]
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_ll = ctypes.c_longlong
+
+# (name, restype, argtypes) for every function declared in include/hrc.h
+SIGNATURES = [
+    ("hrc_create", _i, [_i, _i, _i, _i, ctypes.POINTER(_vp)]),
+    ("hrc_destroy", _i, [_vp]),
+    ("hrc_set_stream", _i, [_vp, _vp]),
+    ("hrc_set_precision", _i, [_vp, _i]),
+    ("hrc_fluence", _i, [_vp, _vp, _vp, _vp]),
+    ("hrc_fluence_host", _i, [_vp, _vp, _vp, _vp]),
+    ("hrc_fluence_backward", _i, [_vp, _vp, _vp, _vp]),
+    ("hrc_fluence_f64", _i, [_vp, _vp, _vp, _vp]),
+    ("hrc_fluence_backward_f64", _i, [_vp, _vp, _vp, _vp]),
+    ("hrc_create_batched", _i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _i, ctypes.POINTER(_vp)]),
+    ("hrc_scene_offsets", _i, [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
+    ("hrc_fluence_batched", _i, [_vp, _vp, _vp, _vp]),
+    ("hrc_fluence_backward_batched", _i, [_vp, _vp, _vp, _vp]),
+    ("hrc_copy_level", _i, [_vp, _i, _i, _i, _vp, ctypes.POINTER(_ll)]),
+    ("hrc_last_launch_count", _i, [_vp]),
+    ("hrc_set_timing", _i, [_vp, _i]),
+    ("hrc_get_timing", _i, [_vp, _vp, _i]),
+    ("hrc_last_error", ctypes.c_char_p, [_vp]),
+    ("hrc_version", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+class HRCError(RuntimeError):
+    def __init__(self, status, msg):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libhrc.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libhrc.so not built at {path}: run __graft_entry__.build() "
+                               "(the CUDA path has no fallback)")
+        L = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int, ctx=None) -> None:
+    if status != HRC_OK:
+        msg = load().hrc_last_error(ctx).decode(errors="replace")
+        raise HRCError(status, msg)
+
+
+def ptr(t) -> int:
+    """Device or host address of a tensor / ndarray (None -> NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+# Thin wrappers with the C names -------------------------------------------------
+
+def hrc_create(W: int, H: int, channels: int, cascades: int = 0):
+    out = _vp()
+    check(load().hrc_create(W, H, channels, cascades, ctypes.byref(out)))
+    return out
+
+
+def hrc_destroy(ctx):
+    check(load().hrc_destroy(ctx), ctx)
+
+
+def hrc_set_stream(ctx, stream_handle: int):
+    check(load().hrc_set_stream(ctx, stream_handle), ctx)
+
+
+def hrc_set_precision(ctx, prec: int):
+    check(load().hrc_set_precision(ctx, prec), ctx)
+
+
+def hrc_fluence(ctx, emission, sigma_t, out):
+    check(load().hrc_fluence(ctx, ptr(emission), ptr(sigma_t), ptr(out)), ctx)
+
+
+def hrc_fluence_host(ctx, emission, sigma_t, out):
+    check(load().hrc_fluence_host(ctx, ptr(emission), ptr(sigma_t), ptr(out)), ctx)
+
+
+def hrc_fluence_backward(ctx, grad_F, grad_emission, grad_sigma_t):
+    check(load().hrc_fluence_backward(ctx, ptr(grad_F), ptr(grad_emission), ptr(grad_sigma_t)), ctx)
+
+
+def hrc_fluence_f64(ctx, emission, sigma_t, out):
+    check(load().hrc_fluence_f64(ctx, ptr(emission), ptr(sigma_t), ptr(out)), ctx)
+
+
+def hrc_fluence_backward_f64(ctx, grad_F, grad_emission, grad_sigma_t):
+    check(load().hrc_fluence_backward_f64(ctx, ptr(grad_F), ptr(grad_emission), ptr(grad_sigma_t)), ctx)
+
+
+def hrc_create_batched(Ws, Hs, channels: int, cascades: int = 0):
+    n = len(Ws)
+    out = _vp()
+    Wa = (_i * n)(*Ws)
+    Ha = (_i * n)(*Hs)
+    check(load().hrc_create_batched(n, Wa, Ha, channels, cascades, ctypes.byref(out)))
+    return out
+
+
+def hrc_scene_offsets(ctx, n: int):
+    eo = (_ll * (n + 1))()
+    so = (_ll * (n + 1))()
+    check(load().hrc_scene_offsets(ctx, eo, so), ctx)
+    return list(eo), list(so)
+
+
+def hrc_fluence_batched(ctx, emission, sigma_t, out):
+    check(load().hrc_fluence_batched(ctx, ptr(emission), ptr(sigma_t), ptr(out)), ctx)
+
+
+def hrc_fluence_backward_batched(ctx, grad_F, grad_emission, grad_sigma_t):
+    check(load().hrc_fluence_backward_batched(ctx, ptr(grad_F), ptr(grad_emission), ptr(grad_sigma_t)), ctx)
+
+
+def hrc_copy_level(ctx, q: int, which: int, n: int, dst=None) -> int:
+    cnt = _ll()
+    check(load().hrc_copy_level(ctx, q, which, n, ptr(dst), ctypes.byref(cnt)), ctx)
+    return cnt.value
+
+
+def hrc_last_launch_count(ctx) -> int:
+    return load().hrc_last_launch_count(ctx)
+
+
+class hrc_kernel_time(ctypes.Structure):
+    _fields_ = [("kind", _i), ("level", _i), ("ms", ctypes.c_float), ("bytes", ctypes.c_double)]
+
+
+KERNEL_KINDS = ["trace012", "merge_up", "merge_down", "fluence_sum", "adj_sum", "adj_merge_down",
+                "adj_merge_up", "adj_trace", "batched", "other"]
+
+
+def hrc_set_timing(ctx, enable: bool):
+    check(load().hrc_set_timing(ctx, 1 if enable else 0), ctx)
+
+
+def hrc_get_timing(ctx, cap: int = 512):
+    """List of (kind name, level, ms, algorithmic bytes) of the last call."""
+    arr = (hrc_kernel_time * cap)()
+    n = load().hrc_get_timing(ctx, ctypes.cast(arr, _vp), cap)
+    if n < 0:
+        raise HRCError(HRC_ECUDA, "hrc_get_timing failed")
+    return [(KERNEL_KINDS[arr[i].kind], arr[i].level, arr[i].ms, arr[i].bytes) for i in range(n)]
+
+
+def hrc_last_error(ctx=None) -> str:
+    return load().hrc_last_error(ctx).decode(errors="replace")
+
+
+def hrc_version() -> str:
+    return load().hrc_version().decode()

@@ -1,0 +1,159 @@
+"""PyTorch-facing API: device memory, streams and autograd around libhrc.so.
+
+PyTorch is plumbing here: it allocates device tensors and provides the
+current CUDA stream.  Every step of the method runs in the library's CUDA
+kernels through the C ABI (``_lib``).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+_PREC = {
+    "fp32": _lib.HRC_FP32,
+    "fp16": _lib.HRC_FP16_LOGT,
+    "bf16": _lib.HRC_BF16_LOGT,
+    "fp64": _lib.HRC_FP64_TEST,
+}
+
+
+def _dev_tensor(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        t = t.contiguous()
+    if t.data_ptr() % 16:
+        t = t.clone()
+    return t
+
+
+class HRC:
+    """One HRC context: a W x H grid with C channels on the current device.
+
+    ``precision`` is one of 'fp32', 'fp16', 'bf16' (reduced-precision
+    interval storage with log-domain transmittance) or 'fp64' (test only).
+    """
+
+    def __init__(self, W: int, H: int, channels: int = 1, cascades: int = 0, precision: str = "fp32"):
+        self.W, self.H, self.C, self.cascades = W, H, channels, cascades
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.ctx = _lib.hrc_create(W, H, channels, cascades)
+        self.precision = "fp32"
+        self._borrowed = (None, None)
+        self.set_precision(precision)
+
+    # -- configuration -----------------------------------------------------
+    def set_precision(self, precision: str) -> None:
+        _lib.hrc_set_precision(self.ctx, _PREC[precision])
+        self.precision = precision
+        self._borrowed = (None, None)
+
+    @property
+    def dtype(self):
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def _stream(self):
+        _lib.hrc_set_stream(self.ctx, torch.cuda.current_stream(self.device).cuda_stream)
+
+    # -- compute -----------------------------------------------------------
+    def forward(self, emission, sigma_t, out=None):
+        C, H, W = self.C, self.H, self.W
+        emission = _dev_tensor(emission, self.dtype, (C, H, W), "emission")
+        sigma_t = _dev_tensor(sigma_t, self.dtype, (H, W), "sigma_t")
+        if out is None:
+            out = torch.empty((C, H, W), dtype=self.dtype, device=emission.device)
+        self._stream()
+        if self.precision == "fp64":
+            _lib.hrc_fluence_f64(self.ctx, emission, sigma_t, out)
+        else:
+            _lib.hrc_fluence(self.ctx, emission, sigma_t, out)
+        self._borrowed = (emission, sigma_t)
+        return out
+
+    __call__ = forward
+
+    def forward_host(self, emission, sigma_t, out=None):
+        """Host (CPU) float32 tensors in and out, copies included."""
+        C, H, W = self.C, self.H, self.W
+        emission = emission.contiguous()
+        sigma_t = sigma_t.contiguous()
+        assert emission.dtype == torch.float32 and tuple(emission.shape) == (C, H, W)
+        assert sigma_t.dtype == torch.float32 and tuple(sigma_t.shape) == (H, W)
+        if out is None:
+            out = torch.empty((C, H, W), dtype=torch.float32, pin_memory=emission.is_pinned())
+        self._stream()
+        _lib.hrc_fluence_host(self.ctx, emission, sigma_t, out)
+        self._borrowed = (None, None)
+        return out
+
+    def backward(self, grad_F, emission=None, sigma_t=None):
+        """dLoss/d(emission, sigma_t) of the last forward (or of the given
+        inputs, which are re-borrowed first when they differ)."""
+        C, H, W = self.C, self.H, self.W
+        if emission is not None and (self._borrowed[0] is None or
+                                     self._borrowed[0].data_ptr() != emission.data_ptr() or
+                                     self._borrowed[1].data_ptr() != sigma_t.data_ptr()):
+            self.forward(emission, sigma_t)
+        grad_F = _dev_tensor(grad_F, self.dtype, (C, H, W), "grad_F")
+        ge = torch.empty((C, H, W), dtype=self.dtype, device=grad_F.device)
+        gs = torch.empty((H, W), dtype=self.dtype, device=grad_F.device)
+        self._stream()
+        if self.precision == "fp64":
+            _lib.hrc_fluence_backward_f64(self.ctx, grad_F, ge, gs)
+        else:
+            _lib.hrc_fluence_backward(self.ctx, grad_F, ge, gs)
+        return ge, gs
+
+    def level(self, q: int, which: str, n: int) -> torch.Tensor:
+        """T_n (which='T': [U_n][2^n+1][V][C+1]) or R_n (which='R':
+        [U_n][2^n][V][C]) of quadrant frame q from the last forward."""
+        w = 0 if which == "T" else 1
+        cnt = _lib.hrc_copy_level(self.ctx, q, w, n, None)
+        U, V = (self.W, self.H) if q < 2 else (self.H, self.W)
+        Un = -(-U // (1 << n))
+        dst = torch.empty(cnt, dtype=torch.float32, device=self.device)
+        self._stream()
+        _lib.hrc_copy_level(self.ctx, q, w, n, dst)
+        if w == 0:
+            return dst.view(Un, (1 << n) + 1, V, self.C + 1)
+        return dst.view(Un, 1 << n, V, self.C)
+
+    def launch_count(self) -> int:
+        return _lib.hrc_last_launch_count(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            _lib.hrc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _FluenceFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, hrc: HRC, emission, sigma_t):
+        out = hrc.forward(emission.detach(), sigma_t.detach())
+        ctx.hrc = hrc
+        ctx.save_for_backward(emission, sigma_t)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_F):
+        emission, sigma_t = ctx.saved_tensors
+        ge, gs = ctx.hrc.backward(grad_F.contiguous(), emission.detach(), sigma_t.detach())
+        return None, ge, gs
+
+
+def fluence(hrc: HRC, emission, sigma_t):
+    """Differentiable fluence F(emission, sigma_t) (torch.autograd.Function):
+    forward -> hrc_fluence, backward -> hrc_fluence_backward."""
+    return _FluenceFn.apply(hrc, emission, sigma_t)

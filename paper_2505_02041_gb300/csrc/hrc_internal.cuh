@@ -1,0 +1,205 @@
+// hrc_internal.cuh -- device-side building blocks shared by the HRC kernels.
+//
+// Frame geometry (Algorithm 1, procedure Lighting).  Instead of rotating the
+// world four times, each quadrant q is computed in its own frame (u, v), the
+// gathering direction being +u; the per-quadrant recursion is symmetric under
+// v -> V-1-v (Eqs. 13-20), so reflections give the same result as rotations:
+//   q0: (u,v) = (x, y)     q1: (u,v) = (W-1-x, y)
+//   q2: (u,v) = (y, x)     q3: (u,v) = (H-1-y, x)
+//
+// Probe layout (Sec. 4): level n has probes p = (x 2^n, v) for x < U_n =
+// ceil(U / 2^n); direction k in [0, 2^n] has offset v_n(k) = (2^n, 2k - 2^n);
+// cone i = i' + 1/2 spans directions i' .. i'+1.
+//
+// HBM layout (per quadrant, per level; v is contiguous, rows padded to Vs):
+//   T_n: row group (x, k) holds C radiance rows of SL then one transmittance
+//        row of ST (T, or tau = -ln T in the log-T precisions):
+//        byte offset of component c of (x, k, v) =
+//            Toff + (x*K_n + k) * G_n + c * Vs * sizeof(SL) + v * sizeof(elem),
+//        G_n = Vs * (C * sizeof(SL) + sizeof(ST)), K_n = 2^n + 1.
+//   R_n: planar per channel: element (x, i, c, v) at ((x*2^n + i)*C + c)*Vs + v.
+// Every Eq. 18/19 and Eq. 14/15 access is then a contiguous run along v,
+// shifted by an even offset for n >= 1: coalesced, sector-aligned loads.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define HRC_MAXL 15
+#define HRC_MAXRAY 10      // ray shapes of levels 0..2: 2 + 3 + 5
+#define HRC_MAXPIECE 48    // their pixel pieces: 4 + 9 + 29 = 42
+
+namespace hrc {
+
+struct QuadGeom {
+    int U, V, Vs, N;                 // frame extent, padded row stride, cascade count
+    int Un[HRC_MAXL + 1];            // probe columns per level
+    long long Toff[HRC_MAXL + 1];    // byte offset of T_n in the arena
+    long long Roff[HRC_MAXL + 1];    // byte offset of R_n (n < N)
+};
+
+struct Plan {
+    int W, H, C, prec;
+    long long arcs_off;              // byte offset: float A[2^n + j] for level n (n >= 1)
+    long long arcs_off_d;            // same table in double
+    char *arena;
+    QuadGeom q[4];
+};
+
+// Pieces of the directly traced rays (levels 0..2) from a pixel centre:
+// pixel offset (du, dv) and length.  Ray r of level n, direction k:
+// r = 0,1 (n=0), 2..4 (n=1), 5..9 (n=2).
+struct RayPiece { int8_t du, dv; int8_t pad0, pad1; float len; };
+struct RayTable {
+    int start[HRC_MAXRAY + 1];
+    RayPiece p[HRC_MAXPIECE];
+    double lenD[HRC_MAXPIECE];
+};
+
+__host__ __device__ inline int ray_id(int n, int k) { return n == 0 ? k : (n == 1 ? 2 + k : 5 + k); }
+
+// frame (u, v) of quadrant q -> image pixel (x, y)
+__host__ __device__ inline void frame_to_image(int q, int W, int H, int u, int v, int &x, int &y) {
+    x = q == 0 ? u : (q == 1 ? W - 1 - u : v);
+    y = q < 2 ? v : (q == 2 ? u : H - 1 - u);
+}
+// image pixel (x, y) -> frame (u, v) of quadrant q
+__host__ __device__ inline void image_to_frame(int q, int W, int H, int x, int y, int &u, int &v) {
+    u = q == 0 ? x : (q == 1 ? W - 1 - x : (q == 2 ? y : H - 1 - y));
+    v = q < 2 ? y : x;
+}
+
+// ---------------------------------------------------------------------------
+// Precision traits.  SL: radiance / fluence storage, ST: transmittance
+// storage, A: arithmetic type, LOG: ST holds tau = -ln T.
+// ---------------------------------------------------------------------------
+enum { P_FP32 = 0, P_FP16 = 1, P_BF16 = 2, P_FP64 = 3 };
+
+template <int P> struct Prec;
+template <> struct Prec<P_FP32> { using SL = float;          using ST = float;  using A = float;  static constexpr bool LOG = false; };
+template <> struct Prec<P_FP16> { using SL = __half;         using ST = float;  using A = float;  static constexpr bool LOG = true;  };
+template <> struct Prec<P_BF16> { using SL = __nv_bfloat16;  using ST = float;  using A = float;  static constexpr bool LOG = true;  };
+template <> struct Prec<P_FP64> { using SL = double;         using ST = double; using A = double; static constexpr bool LOG = false; };
+
+__device__ __forceinline__ float to_acc(float x) { return x; }
+__device__ __forceinline__ double to_acc(double x) { return x; }
+__device__ __forceinline__ float to_acc(__half x) { return __half2float(x); }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <class S> __device__ __forceinline__ S from_acc(float x);
+template <> __device__ __forceinline__ float from_acc<float>(float x) { return x; }
+template <> __device__ __forceinline__ __half from_acc<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <class S> __device__ __forceinline__ S from_acc(double x);
+template <> __device__ __forceinline__ double from_acc<double>(double x) { return x; }
+
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ double fexp(double x) { return exp(x); }
+__device__ __forceinline__ float fexpm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double fexpm1(double x) { return expm1(x); }
+__device__ __forceinline__ float flog1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double flog1p(double x) { return log1p(x); }
+
+// ---------------------------------------------------------------------------
+// An interval <L, T> in registers (Eq. 9).  For LOG precisions `t` holds
+// tau = -ln T so that Merge adds and long opaque paths never underflow.
+// ---------------------------------------------------------------------------
+template <int P, int C> struct Iv {
+    using A = typename Prec<P>::A;
+    A L[C];
+    A t;
+    __device__ __forceinline__ static Iv vacuum() {
+        Iv r;
+#pragma unroll
+        for (int c = 0; c < C; ++c) r.L[c] = A(0);
+        r.t = Prec<P>::LOG ? A(0) : A(1);
+        return r;
+    }
+    __device__ __forceinline__ A trans() const { return Prec<P>::LOG ? fexp(-t) : t; }
+};
+
+// Merge (Eq. 7): <r_n + t_n r_f, t_n t_f>
+template <int P, int C>
+__device__ __forceinline__ Iv<P, C> merge(const Iv<P, C> &n, const Iv<P, C> &f) {
+    Iv<P, C> r;
+    typename Prec<P>::A tn = n.trans();
+#pragma unroll
+    for (int c = 0; c < C; ++c) r.L[c] = fma(tn, f.L[c], n.L[c]);
+    r.t = Prec<P>::LOG ? n.t + f.t : n.t * f.t;
+    return r;
+}
+
+// Eq. 20: the average of two intervals (radiance and transmittance).
+template <int P, int C>
+__device__ __forceinline__ Iv<P, C> blend(const Iv<P, C> &a, const Iv<P, C> &b) {
+    using A = typename Prec<P>::A;
+    Iv<P, C> r;
+#pragma unroll
+    for (int c = 0; c < C; ++c) r.L[c] = A(0.5) * (a.L[c] + b.L[c]);
+    if (Prec<P>::LOG) {
+        // -ln((e^-a + e^-b)/2) = min + ln 2 - ln(1 + e^-|a-b|)
+        A lo = fmin(a.t, b.t), d = fabs(a.t - b.t);
+        r.t = lo + A(0.69314718055994530942) - flog1p(fexp(-d));
+    } else {
+        r.t = A(0.5) * (a.t + b.t);
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Level addressing
+// ---------------------------------------------------------------------------
+template <int P, int C> struct TLevel {
+    using SL = typename Prec<P>::SL;
+    using ST = typename Prec<P>::ST;
+    char *base;
+    int K, Vs;
+    long long G;   // bytes per (x, k) row group
+    __device__ __forceinline__ TLevel(const Plan &pl, int q, int n) {
+        base = pl.arena + pl.q[q].Toff[n];
+        K = (1 << n) + 1;
+        Vs = pl.q[q].Vs;
+        G = (long long)Vs * (C * (long long)sizeof(SL) + (long long)sizeof(ST));
+    }
+    __device__ __forceinline__ char *row(int x, int k) const { return base + ((long long)x * K + k) * G; }
+    __device__ __forceinline__ Iv<P, C> load(int x, int k, int v) const {
+        const char *g = row(x, k);
+        Iv<P, C> r;
+#pragma unroll
+        for (int c = 0; c < C; ++c) r.L[c] = to_acc(reinterpret_cast<const SL *>(g)[(long long)c * Vs + v]);
+        r.t = to_acc(reinterpret_cast<const ST *>(g + (long long)C * Vs * sizeof(SL))[v]);
+        return r;
+    }
+    __device__ __forceinline__ void store(int x, int k, int v, const Iv<P, C> &r) const {
+        char *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) reinterpret_cast<SL *>(g)[(long long)c * Vs + v] = from_acc<SL>(r.L[c]);
+        reinterpret_cast<ST *>(g + (long long)C * Vs * sizeof(SL))[v] = from_acc<ST>(r.t);
+    }
+};
+
+template <int P, int C> struct RLevel {
+    using SL = typename Prec<P>::SL;
+    using A = typename Prec<P>::A;
+    SL *base;
+    int I, Vs;
+    __device__ __forceinline__ RLevel(const Plan &pl, int q, int n) {
+        base = reinterpret_cast<SL *>(pl.arena + pl.q[q].Roff[n]);
+        I = 1 << n;
+        Vs = pl.q[q].Vs;
+    }
+    __device__ __forceinline__ long long idx(int x, int i, int c, int v) const {
+        return (((long long)x * I + i) * C + c) * Vs + v;
+    }
+    __device__ __forceinline__ A load(int x, int i, int c, int v) const { return to_acc(base[idx(x, i, c, v)]); }
+    __device__ __forceinline__ void store(int x, int i, int c, int v, A val) const { base[idx(x, i, c, v)] = from_acc<SL>(val); }
+};
+
+template <int P> __device__ __forceinline__ typename Prec<P>::A arc(const Plan &pl, int n, int j) {
+    if (P == P_FP64) return reinterpret_cast<const double *>(pl.arena + pl.arcs_off_d)[(1 << n) + j];
+    return reinterpret_cast<const float *>(pl.arena + pl.arcs_off)[(1 << n) + j];
+}
+
+}  // namespace hrc

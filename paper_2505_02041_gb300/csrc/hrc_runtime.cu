@@ -1,0 +1,371 @@
+// hrc_runtime.cu -- host runtime behind the C ABI of include/hrc.h:
+// contexts, buffer plans, ray-shape tables, arc tables and launch sequencing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hrc.h"
+#include "hrc_internal.cuh"
+#include "launch.h"
+
+using namespace hrc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int levels_for(int U, int cascades) {
+    int N = 0;
+    while ((1 << N) < U) ++N;
+    if (cascades > 0 && cascades < N) N = cascades;
+    return N;
+}
+
+size_t sl_bytes(int prec) { return prec == P_FP32 ? 4 : (prec == P_FP64 ? 8 : 2); }
+size_t st_bytes(int prec) { return prec == P_FP64 ? 8 : 4; }
+
+// Ray shapes of the directly traced levels 0..2 (Sec. 4.2): from a pixel
+// centre (1/2, 1/2) along v_n(k) = (2^n, 2k - 2^n).  The segment is clipped
+// against the integer grid lines in exact integer arithmetic: with
+// a = 2^n and b = 2k - 2^n, the crossings of u = g are at t = (2g-1)/(2a)
+// and those of v at t = (2m-1)/(2|b|); over the common denominator 2a|b|
+// all crossing parameters are integers.  Zero-length pieces (the ray
+// passing exactly through a grid corner) are dropped.
+RayTable make_ray_table() {
+    RayTable rt;
+    std::memset(&rt, 0, sizeof(rt));
+    int np = 0;
+    for (int n = 0; n <= 2; ++n) {
+        const int a = 1 << n;
+        for (int k = 0; k <= a; ++k) {
+            const int r = ray_id(n, k);
+            rt.start[r] = np;
+            const int b = 2 * k - a, ab = b < 0 ? -b : b;
+            const long long D = 2LL * a * (ab > 0 ? ab : 1);
+            std::vector<long long> ts = {0, D};
+            for (int g = 1; g <= a; ++g) ts.push_back((2LL * g - 1) * (D / (2LL * a)));
+            for (int m = 1; m <= ab; ++m) ts.push_back((2LL * m - 1) * (D / (2LL * ab)));
+            std::sort(ts.begin(), ts.end());
+            ts.erase(std::unique(ts.begin(), ts.end()), ts.end());
+            const double len = std::sqrt(double(a) * a + double(b) * b);
+            for (size_t i = 0; i + 1 < ts.size(); ++i) {
+                const double tm = 0.5 * double(ts[i] + ts[i + 1]) / double(D);
+                const int du = (int)std::floor(0.5 + a * tm);
+                const int dv = (int)std::floor(0.5 + b * tm);
+                const double l = double(ts[i + 1] - ts[i]) / double(D) * len;
+                rt.p[np].du = (int8_t)du;
+                rt.p[np].dv = (int8_t)dv;
+                rt.p[np].len = (float)l;
+                rt.lenD[np] = l;
+                ++np;
+            }
+        }
+    }
+    rt.start[HRC_MAXRAY] = np;
+    return rt;
+}
+
+// Lays out T_0..T_N and R_0..R_{N-1} of all four frames from byte `off`;
+// returns the end offset.
+size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan &pl) {
+    std::memset(&pl, 0, sizeof(pl));
+    pl.W = W; pl.H = H; pl.C = C; pl.prec = prec;
+    const size_t SLb = sl_bytes(prec), STb = st_bytes(prec);
+    int Nmax = 0;
+    for (int q = 0; q < 4; ++q) {
+        QuadGeom &g = pl.q[q];
+        g.U = q < 2 ? W : H;
+        g.V = q < 2 ? H : W;
+        g.Vs = (int)align_up((size_t)g.V, 32);
+        g.N = levels_for(g.U, cascades);
+        Nmax = std::max(Nmax, g.N);
+        for (int n = 0; n <= g.N; ++n) {
+            g.Un[n] = (g.U + (1 << n) - 1) >> n;
+            const size_t G = (size_t)g.Vs * (C * SLb + STb);
+            g.Toff[n] = (long long)off;
+            off = align_up(off + (size_t)g.Un[n] * ((1u << n) + 1) * G, 256);
+        }
+        for (int n = 0; n < g.N; ++n) {
+            g.Roff[n] = (long long)off;
+            off = align_up(off + (size_t)g.Un[n] * (1u << n) * C * g.Vs * SLb, 256);
+        }
+    }
+    pl.arcs_off = (long long)off;
+    off = align_up(off + sizeof(float) * (size_t(2) << Nmax), 256);
+    pl.arcs_off_d = (long long)off;
+    off = align_up(off + sizeof(double) * (size_t(2) << Nmax), 256);
+    return off;
+}
+
+int plan_nmax(const Plan &pl) {
+    int N = 0;
+    for (int q = 0; q < 4; ++q) N = std::max(N, pl.q[q].N);
+    return N;
+}
+
+// Eq. 13: A_n(j + 1/2) = angle(v_n(j + 1)) - angle(v_n(j)), angle = atan(y/x).
+void fill_arcs(int Nmax, std::vector<float> &af, std::vector<double> &ad) {
+    af.assign(size_t(2) << Nmax, 0.f);
+    ad.assign(size_t(2) << Nmax, 0.0);
+    for (int n = 0; n <= Nmax; ++n) {
+        const double s = double(1 << n);
+        for (int j = 0; j < (1 << n); ++j) {
+            const double a = std::atan2(2.0 * (j + 1) - s, s) - std::atan2(2.0 * j - s, s);
+            ad[(size_t(1) << n) + j] = a;
+            af[(size_t(1) << n) + j] = (float)a;
+        }
+    }
+}
+
+}  // namespace
+
+struct hrc_ctx {
+    int W = 0, H = 0, C = 0, cascades = 0;
+    int prec = P_FP32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    RayTable rt;
+    Plan plan;                   // layout of the current (non-fp64) precision
+    Plan plan64;                 // fp64 layout (arena64)
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    char *arena64 = nullptr;
+    size_t arena64_bytes = 0;
+    float *dev_e = nullptr, *dev_s = nullptr, *dev_F = nullptr;   // hrc_fluence_host staging
+    const void *last_e = nullptr, *last_s = nullptr;
+    bool have_fwd = false;
+    int launches = 0;
+    Recorder rec;
+    std::string err;
+};
+
+namespace {
+
+hrc_status fail(hrc_ctx *ctx, hrc_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+hrc_status cuda_fail(hrc_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, HRC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Upload the arc tables of a plan into its arena.
+cudaError_t upload_arcs(const Plan &pl, char *arena) {
+    std::vector<float> af;
+    std::vector<double> ad;
+    fill_arcs(plan_nmax(pl), af, ad);
+    cudaError_t e = cudaMemcpy(arena + pl.arcs_off, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(arena + pl.arcs_off_d, ad.data(), ad.size() * sizeof(double), cudaMemcpyHostToDevice);
+}
+
+hrc_status check_ctx(hrc_ctx *ctx) {
+    if (!ctx) return HRC_EINVAL;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pending CUDA error");
+    return HRC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hrc_version(void) { return "hrc-gb300 0.1 (sm_103a)"; }
+
+const char *hrc_last_error(const hrc_ctx *ctx) {
+    static thread_local std::string copy;
+    copy = ctx ? ctx->err : g_create_error;
+    return copy.c_str();
+}
+
+int hrc_last_launch_count(const hrc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+hrc_status hrc_set_timing(hrc_ctx *ctx, int enable) {
+    if (!ctx) return HRC_EINVAL;
+    ctx->rec.on = enable != 0;
+    return HRC_OK;
+}
+
+int hrc_get_timing(hrc_ctx *ctx, hrc_kernel_time *out, int cap) {
+    if (!ctx) return -1;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return -1;
+    int n = 0;
+    for (const auto &r : ctx->rec.recs) {
+        if (n >= cap) break;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return -1;
+        if (out) out[n] = hrc_kernel_time{r.kind, r.level, ms, r.bytes};
+        ++n;
+    }
+    return n;
+}
+
+hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out) {
+    if (!out) return fail(nullptr, HRC_EINVAL, "hrc_create: out is NULL");
+    *out = nullptr;
+    if (W < 1 || H < 1 || W > 16384 || H > 16384)
+        return fail(nullptr, HRC_EINVAL, "hrc_create: W and H must be in [1, 16384]");
+    if (channels < 1 || channels > 4) return fail(nullptr, HRC_EINVAL, "hrc_create: channels must be in [1, 4]");
+    hrc_ctx *ctx = new (std::nothrow) hrc_ctx();
+    if (!ctx) return fail(nullptr, HRC_ENOMEM, "hrc_create: host allocation failed");
+    ctx->W = W; ctx->H = H; ctx->C = channels; ctx->cascades = cascades;
+    ctx->rt = make_ray_table();
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) { delete ctx; return fail(nullptr, HRC_ECUDA, std::string("hrc_create: ") + cudaGetErrorString(e)); }
+    // The fp32 layout is the largest of the fp32 / fp16 / bf16 layouts.
+    Plan p32;
+    size_t bytes = build_plan(W, H, channels, cascades, P_FP32, 0, p32);
+    ctx->arena_bytes = bytes;
+    e = cudaMalloc(&ctx->arena, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return fail(nullptr, HRC_ENOMEM, "hrc_create: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    const size_t img = (size_t)W * H;
+    e = cudaMalloc(&ctx->dev_e, img * channels * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_s, img * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dev_F, img * channels * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hrc_destroy(ctx);
+        return fail(nullptr, HRC_ENOMEM, "hrc_create: staging allocation failed");
+    }
+    ctx->plan = p32;
+    ctx->plan.arena = ctx->arena;
+    e = upload_arcs(ctx->plan, ctx->arena);
+    if (e != cudaSuccess) { hrc_destroy(ctx); return fail(nullptr, HRC_ECUDA, "hrc_create: arc upload failed"); }
+    *out = ctx;
+    return HRC_OK;
+}
+
+hrc_status hrc_destroy(hrc_ctx *ctx) {
+    if (!ctx) return HRC_EINVAL;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(ctx->arena);
+    cudaFree(ctx->arena64);
+    cudaFree(ctx->dev_e);
+    cudaFree(ctx->dev_s);
+    cudaFree(ctx->dev_F);
+    delete ctx;
+    return HRC_OK;
+}
+
+hrc_status hrc_set_stream(hrc_ctx *ctx, void *stream) {
+    if (!ctx) return HRC_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return HRC_OK;
+}
+
+hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
+    if (!ctx) return HRC_EINVAL;
+    if (prec < HRC_FP32 || prec > HRC_FP64_TEST) return fail(ctx, HRC_EINVAL, "hrc_set_precision: unknown precision");
+    if (prec == HRC_FP64_TEST) {
+        if (!ctx->arena64) {
+            Plan p64;
+            size_t bytes = build_plan(ctx->W, ctx->H, ctx->C, ctx->cascades, P_FP64, 0, p64);
+            cudaError_t e = cudaMalloc(&ctx->arena64, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                ctx->arena64 = nullptr;
+                return fail(ctx, HRC_ENOMEM, "hrc_set_precision: fp64 buffers do not fit");
+            }
+            ctx->arena64_bytes = bytes;
+            p64.arena = ctx->arena64;
+            ctx->plan64 = p64;
+            e = upload_arcs(ctx->plan64, ctx->arena64);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
+        }
+    } else {
+        Plan p;
+        build_plan(ctx->W, ctx->H, ctx->C, ctx->cascades, (int)prec, 0, p);
+        p.arena = ctx->arena;
+        ctx->plan = p;
+        cudaError_t e = upload_arcs(ctx->plan, ctx->arena);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
+    }
+    ctx->prec = (int)prec;
+    ctx->have_fwd = false;
+    return HRC_OK;
+}
+
+hrc_status hrc_fluence(hrc_ctx *ctx, const float *emission, const float *sigma_t, float *out) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (ctx->prec == P_FP64) return fail(ctx, HRC_ESTATE, "hrc_fluence: context is in HRC_FP64_TEST; use hrc_fluence_f64");
+    if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence: NULL pointer");
+    if (!aligned16(emission) || !aligned16(sigma_t) || !aligned16(out))
+        return fail(ctx, HRC_EINVAL, "hrc_fluence: pointers must be 16-byte aligned");
+    ctx->launches = 0;
+    ctx->rec.reset(ctx->stream);
+    cudaError_t e = launch_forward(ctx->plan, ctx->rt, emission, sigma_t, out, ctx->stream, &ctx->launches, &ctx->rec);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence");
+    ctx->last_e = emission;
+    ctx->last_s = sigma_t;
+    ctx->have_fwd = true;
+    return HRC_OK;
+}
+
+hrc_status hrc_fluence_host(hrc_ctx *ctx, const float *emission, const float *sigma_t, float *out) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence_host: NULL pointer");
+    const size_t img = (size_t)ctx->W * ctx->H;
+    cudaError_t e = cudaMemcpyAsync(ctx->dev_e, emission, img * ctx->C * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->dev_s, sigma_t, img * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence_host: upload");
+    st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
+    if (st != HRC_OK) return st;
+    e = cudaMemcpyAsync(out, ctx->dev_F, img * ctx->C * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence_host: download");
+    return HRC_OK;
+}
+
+hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *sigma_t, double *out) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (ctx->prec != P_FP64) return fail(ctx, HRC_ESTATE, "hrc_fluence_f64: set HRC_FP64_TEST first");
+    if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence_f64: NULL pointer");
+    if (!aligned16(emission) || !aligned16(sigma_t) || !aligned16(out))
+        return fail(ctx, HRC_EINVAL, "hrc_fluence_f64: pointers must be 16-byte aligned");
+    ctx->launches = 0;
+    ctx->rec.reset(ctx->stream);
+    cudaError_t e = launch_forward(ctx->plan64, ctx->rt, emission, sigma_t, out, ctx->stream, &ctx->launches, &ctx->rec);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence_f64");
+    ctx->last_e = emission;
+    ctx->last_s = sigma_t;
+    ctx->have_fwd = true;
+    return HRC_OK;
+}
+
+hrc_status hrc_copy_level(hrc_ctx *ctx, int q, int which, int n, float *dst, long long *count) {
+    if (!ctx) return HRC_EINVAL;
+    const Plan &pl = ctx->prec == P_FP64 ? ctx->plan64 : ctx->plan;
+    if (q < 0 || q > 3 || (which != 0 && which != 1)) return fail(ctx, HRC_EINVAL, "hrc_copy_level: bad q / which");
+    const QuadGeom &g = pl.q[q];
+    if (n < 0 || (which == 0 && n > g.N) || (which == 1 && n >= g.N))
+        return fail(ctx, HRC_EINVAL, "hrc_copy_level: level does not exist");
+    const long long cnt = which == 0 ? (long long)g.Un[n] * ((1 << n) + 1) * g.V * (ctx->C + 1)
+                                     : (long long)g.Un[n] * (1 << n) * g.V * ctx->C;
+    if (count) *count = cnt;
+    if (!dst) return HRC_OK;
+    cudaError_t e = launch_copy_level(pl, q, which, n, dst, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_copy_level");
+    return HRC_OK;
+}
+
+}  // extern "C"

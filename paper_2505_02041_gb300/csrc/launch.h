@@ -1,0 +1,65 @@
+// launch.h -- host-side entry points of the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "hrc_internal.cuh"
+
+namespace hrc {
+
+// Kernel kinds, for per-launch timing records.
+enum KernelKind {
+    K_TRACE012 = 0, K_MERGE_UP = 1, K_MERGE_DOWN = 2, K_FLUENCE_SUM = 3,
+    K_ADJ_SUM = 4, K_ADJ_MERGE_DOWN = 5, K_ADJ_MERGE_UP = 6, K_ADJ_TRACE = 7,
+    K_BATCHED = 8, K_OTHER = 9
+};
+
+// Optional per-launch CUDA-event timing (off by default).  Events come from
+// a pool created when timing is enabled; recording is stream-ordered.
+struct Recorder {
+    struct Rec { int kind, level; double bytes; cudaEvent_t a, b; };
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> recs;
+    size_t used = 0;
+    void reset(cudaStream_t s) { st = s; recs.clear(); used = 0; }
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void begin(int kind, int level, double bytes) {
+        if (!on) return;
+        Rec r{kind, level, bytes, next(), next()};
+        cudaEventRecord(r.a, st);
+        recs.push_back(r);
+    }
+    void end() {
+        if (!on || recs.empty()) return;
+        cudaEventRecord(recs.back().b, st);
+    }
+    ~Recorder() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+// Forward pass of Algorithm 1 (all four quadrant frames), enqueued on `st`.
+// e, s, F are fp32 device pointers (fp64 for P_FP64).
+cudaError_t launch_forward(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
+                           cudaStream_t st, int *launches, Recorder *rec);
+
+// Dense fp32 copy of level n of frame q (which = 0: T_n, 1: R_n).
+cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *dst, cudaStream_t st);
+
+// Algorithmic bytes of one launch (each array read once per consuming
+// phase, each written once): T entries of C radiances + 1 transmittance,
+// R entries of C values.
+double bytes_T(const Plan &pl, int q, int n);
+double bytes_R(const Plan &pl, int q, int n);
+
+}  // namespace hrc

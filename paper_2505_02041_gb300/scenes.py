@@ -43,46 +43,55 @@ def empty(W: int, H: int, C: int):
     return np.zeros((C, H, W), np.float32), np.zeros((H, W), np.float32)
 
 
-def _centres(W: int, H: int):
-    y, x = np.mgrid[0:H, 0:W]
-    return x + 0.5, y + 0.5
+def _window(W, H, x0, x1, y0, y1):
+    """Pixel-centre grids of the pixels whose centres may lie in the box
+    [x0, x1] x [y0, y1] (clipped to the image), and their slices."""
+    xa, xb = max(int(np.floor(x0)) - 1, 0), min(int(np.ceil(x1)) + 1, W)
+    ya, yb = max(int(np.floor(y0)) - 1, 0), min(int(np.ceil(y1)) + 1, H)
+    xa, ya = min(xa, W), min(ya, H)
+    y, x = np.mgrid[ya:max(yb, ya), xa:max(xb, xa)]
+    return x + 0.5, y + 0.5, (slice(ya, max(yb, ya)), slice(xa, max(xb, xa)))
 
 
 def paint_disk(e, s, cx, cy, r, rgb):
     """Emitter disk: sets e inside, keeps the extinction beneath."""
     C, H, W = e.shape
-    X, Y = _centres(W, H)
+    X, Y, win = _window(W, H, cx - r, cx + r, cy - r, cy + r)
     m = (X - cx) ** 2 + (Y - cy) ** 2 <= r * r
     for c in range(C):
-        e[c][m] = rgb[c]
+        e[c][win][m] = rgb[c]
     return m
 
 
 def paint_rect(e, s, cx, cy, w, h, angle, sigma):
     """Occluder rectangle (rotated by ``angle`` about its centre)."""
     C, H, W = e.shape
-    X, Y = _centres(W, H)
+    rad = 0.5 * np.hypot(w, h)
+    X, Y, win = _window(W, H, cx - rad, cx + rad, cy - rad, cy + rad)
     ca, sa = np.cos(angle), np.sin(angle)
     dx, dy = X - cx, Y - cy
     a = ca * dx + sa * dy
     b = -sa * dx + ca * dy
     m = (np.abs(a) <= 0.5 * w) & (np.abs(b) <= 0.5 * h)
-    s[m] = sigma
-    e[:, m] = 0.0
+    s[win][m] = sigma
+    for c in range(C):
+        e[c][win][m] = 0.0
     return m
 
 
 def paint_capsule(e, s, x0, y0, x1, y1, width, sigma):
     """Occluder wall: all pixel centres within width/2 of the segment."""
     C, H, W = e.shape
-    X, Y = _centres(W, H)
+    hw = 0.5 * width
+    X, Y, win = _window(W, H, min(x0, x1) - hw, max(x0, x1) + hw, min(y0, y1) - hw, max(y0, y1) + hw)
     dx, dy = x1 - x0, y1 - y0
     L2 = dx * dx + dy * dy
     t = np.clip(((X - x0) * dx + (Y - y0) * dy) / max(L2, 1e-12), 0.0, 1.0)
     px, py = x0 + t * dx, y0 + t * dy
-    m = (X - px) ** 2 + (Y - py) ** 2 <= (0.5 * width) ** 2
-    s[m] = sigma
-    e[:, m] = 0.0
+    m = (X - px) ** 2 + (Y - py) ** 2 <= hw * hw
+    s[win][m] = sigma
+    for c in range(C):
+        e[c][win][m] = 0.0
     return m
 
 

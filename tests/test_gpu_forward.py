@@ -1,0 +1,92 @@
+"""Forward parity: CUDA path (through the C ABI) vs the FP64 oracle.
+
+Tolerance: err_max = max|F_gpu - F_ref| / max|F_ref| <= 1e-4 in fp32
+(the target bound for the fp32 forward); fp32 rounding over ~2N merges
+gives ~1e-6 in practice.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_02041_gb300 import scenes
+from gpu_util import require_gpu, err_max, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def _gpu_F(e, s, cascades=0, precision="fp32"):
+    from paper_2505_02041_gb300 import HRC
+    C, H, W = e.shape
+    h = HRC(W, H, C, cascades, precision)
+    F = h.forward(to_dev(e, torch.float32), to_dev(s, torch.float32))
+    torch.cuda.synchronize()
+    return h, F.cpu().numpy()
+
+
+@pytest.mark.parametrize("W,H,C,casc,seed", [
+    (64, 64, 1, 0, 0), (37, 23, 2, 0, 1), (5, 7, 1, 0, 2), (1, 6, 1, 0, 3), (1, 1, 1, 0, 4),
+    (2, 2, 3, 0, 5), (128, 96, 3, 0, 6), (100, 100, 4, 0, 7), (64, 64, 1, 3, 8), (33, 65, 1, 0, 9),
+    (257, 130, 1, 0, 10),
+])
+def test_forward_random_scenes(W, H, C, casc, seed):
+    require_gpu()
+    e, s = scenes.random_scene(W, H, C, seed)
+    _, F = _gpu_F(e, s, casc)
+    Fr = oracle.fluence(e, s, casc)
+    assert err_max(F, Fr) <= TOL
+
+
+def test_forward_disks64_scene():
+    require_gpu()
+    e, s = scenes.scene_by_name("disks64")
+    _, F = _gpu_F(e, s)
+    assert err_max(F, oracle.fluence(e, s)) <= TOL
+
+
+def test_forward_vacuum_is_zero():
+    require_gpu()
+    e = np.zeros((1, 40, 40), np.float32)
+    s = np.zeros((40, 40), np.float32)
+    s[10:20, 10:20] = 1e3
+    _, F = _gpu_F(e, s)
+    assert np.all(F == 0.0)
+
+
+@pytest.mark.parametrize("q", range(4))
+def test_levels_match_oracle(q):
+    """Every T_n and R_n level of every quadrant frame, element by element."""
+    require_gpu()
+    e, s = scenes.random_scene(48, 40, 2, 12)
+    h, _ = _gpu_F(e, s)
+    U = 48 if q < 2 else 40
+    N = int(np.ceil(np.log2(U)))
+    for n in range(N + 1):
+        Tg = h.level(q, "T", n).cpu().numpy()
+        Tr = oracle.frame_level(e, s, q, "T", n)
+        assert Tg.shape == Tr.shape
+        assert np.max(np.abs(Tg - Tr)) <= 2e-5 * max(1.0, np.max(np.abs(Tr))), (q, n)
+    for n in range(N):
+        Rg = h.level(q, "R", n).cpu().numpy()
+        Rr = oracle.frame_level(e, s, q, "R", n)
+        assert np.max(np.abs(Rg - Rr)) <= 2e-5 * max(1.0, np.max(np.abs(Rr))), (q, n)
+
+
+@pytest.mark.parametrize("name", ["fog512", "volumetric1024"])
+def test_forward_full_size_workloads(name):
+    """The 512^2 and 1024^2 three-channel workloads at full size."""
+    require_gpu()
+    e, s = scenes.scene_by_name(name)
+    _, F = _gpu_F(e, s)
+    assert err_max(F, oracle.fluence(e, s)) <= TOL
+
+
+def test_forward_host_entry_matches_device_entry():
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC
+    e, s = scenes.random_scene(70, 50, 3, 13)
+    h = HRC(70, 50, 3)
+    Fd = h.forward(to_dev(e), to_dev(s)).cpu()
+    Fh = h.forward_host(torch.from_numpy(e).pin_memory(), torch.from_numpy(s).pin_memory())
+    assert torch.equal(Fd, Fh)
