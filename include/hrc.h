@@ -117,6 +117,37 @@ hrc_status hrc_fluence_batched(hrc_ctx *ctx, const float *emission, const float 
 hrc_status hrc_fluence_backward_batched(hrc_ctx *ctx, const float *grad_F, float *grad_emission,
                                         float *grad_sigma_t);
 
+/* Allocation-free forward pass.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- a frame callback
+ * running under an engine-owned memory budget, code whose host framework
+ * must own every device allocation, or a plugin in a process that forbids
+ * new device allocations after start-up (cudaMalloc also synchronises the
+ * device, which a real-time frame loop cannot afford).
+ *
+ * Computes exactly what hrc_fluence computes (fp32, cascades chosen
+ * automatically) for one W x H grid with `channels` colours, on
+ * `cuda_stream` (NULL = legacy default stream), without a context.  The
+ * caller passes the device buffers emission [C][H][W], sigma_t [H][W] and
+ * out [C][H][W] (fp32, 16-byte aligned).  Every intermediate level lives in
+ * one fixed file-scope device array of HRC_NOALLOC_SCRATCH_BYTES bytes,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * Limits: 1 <= W, H <= HRC_NOALLOC_MAX_SIDE and 1 <= channels <= 4; larger
+ * requests return HRC_EINVAL with a message from hrc_last_error(NULL).
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ * Set-up: the first call on each device (made with that device current)
+ * resolves the array's device address and writes a constant arc table into
+ * it with a synchronous copy; make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (every level is fully rewritten before it is read, so nothing
+ * needs clearing); calls that overlap on the GPU -- on different streams
+ * or different host threads -- race on it and must be serialised by the
+ * caller. */
+#define HRC_NOALLOC_MAX_SIDE 128
+#define HRC_NOALLOC_SCRATCH_BYTES 20443136ULL
+hrc_status hrc_fluence_noalloc(int W, int H, int channels, const float *emission, const float *sigma_t,
+                               float *out, void *cuda_stream);
+
 /* Introspection for tests: copies level n of quadrant frame q (0..3) from
  * the last forward into `dst` (device fp32).  which = 0: T_n as
  * [U_n][2^n+1][V][C+1] (C radiances then the transmittance T, linear even in

@@ -35,6 +35,7 @@ SIGNATURES = [
     ("hrc_scene_offsets", _i, [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
     ("hrc_fluence_batched", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_fluence_backward_batched", _i, [_vp, _vp, _vp, _vp]),
+    ("hrc_fluence_noalloc", _i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
     ("hrc_copy_level", _i, [_vp, _i, _i, _i, _vp, ctypes.POINTER(_ll)]),
     ("hrc_last_launch_count", _i, [_vp]),
     ("hrc_set_timing", _i, [_vp, _i]),
@@ -146,6 +147,11 @@ def hrc_fluence_batched(ctx, emission, sigma_t, out):
 
 def hrc_fluence_backward_batched(ctx, grad_F, grad_emission, grad_sigma_t):
     check(load().hrc_fluence_backward_batched(ctx, ptr(grad_F), ptr(grad_emission), ptr(grad_sigma_t)), ctx)
+
+
+def hrc_fluence_noalloc(W: int, H: int, channels: int, emission, sigma_t, out, stream_handle=None):
+    """Allocation-free forward (no context); see include/hrc.h."""
+    check(load().hrc_fluence_noalloc(W, H, channels, ptr(emission), ptr(sigma_t), ptr(out), stream_handle))
 
 
 def hrc_copy_level(ctx, q: int, which: int, n: int, dst=None) -> int:

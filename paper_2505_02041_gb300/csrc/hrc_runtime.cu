@@ -20,6 +20,12 @@ namespace {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+namespace hrc {
+
+void set_global_error(const char *msg) { g_create_error = msg; }
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int levels_for(int U, int cascades) {
@@ -125,7 +131,7 @@ void fill_arcs(int Nmax, std::vector<float> &af, std::vector<double> &ad) {
     }
 }
 
-}  // namespace
+}  // namespace hrc
 
 struct hrc_ctx {
     int W = 0, H = 0, C = 0, cascades = 0;

@@ -53,6 +53,15 @@ struct Recorder {
 cudaError_t launch_forward(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
                            cudaStream_t st, int *launches, Recorder *rec);
 
+// Host-side plan and table builders (hrc_runtime.cu).
+size_t align_up(size_t x, size_t a);
+int levels_for(int U, int cascades);
+RayTable make_ray_table();
+size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan &pl);
+int plan_nmax(const Plan &pl);
+// Message returned by hrc_last_error(NULL) on this thread.
+void set_global_error(const char *msg);
+
 // Dense fp32 copy of level n of frame q (which = 0: T_n, 1: R_n).
 cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *dst, cudaStream_t st);
 
