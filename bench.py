@@ -229,6 +229,30 @@ def run_ours(args):
             d[0] += ms
             d[1] += by
             d[2] += 1
+    # forward + backward (adjoint with recompute), same workload and timing rules
+    gF = torch.ones((C, H, W), dtype=torch.float32, device=dev)
+    gE = torch.empty_like(e)
+    gS = torch.empty_like(s)
+    bwd_kind = {}
+    fb_ms = []
+    bwd_launches = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.forward(e, s, F)
+        nf = h.launch_count()
+        _lib.hrc_fluence_backward(h.ctx, gF, gE, gS)
+        b.record(stream)
+        b.synchronize()
+        fb_ms.append(a.elapsed_time(b))
+        bwd_launches = nf + h.launch_count()
+        for kind, level, ms, by in _lib.hrc_get_timing(h.ctx):
+            d = bwd_kind.setdefault(kind, [0.0, 0.0, 0])
+            d[0] += ms
+            d[1] += by
+            d[2] += 1
     barrier()
     clk = clocks.stop()
     _lib.hrc_set_timing(h.ctx, False)
@@ -264,6 +288,8 @@ def run_ours(args):
                   "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None}
               for k, v in sorted(per_kind.items())}
     frame_bytes = sum(v[1] for v in per_kind.values()) / args.steps
+    fb_mean = statistics.mean(fb_ms)
+    fb_bytes = frame_bytes + sum(v[1] for v in bwd_kind.values()) / args.steps
     line = {
         "metric": METRIC, "value": ms_per_frame, "unit": "ms/frame", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
@@ -283,7 +309,13 @@ def run_ours(args):
         "phases": phases,
         "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": (C + 1) * H * W * 4,
                 "d2h_bytes_per_step": C * H * W * 4},
-        "gpu_launches": launches_per_step * args.steps,
+        "fwd_bwd": {"ms": fb_mean, "algorithmic_bytes": fb_bytes,
+                    "GBps": fb_bytes / (fb_mean * 1e-3) / 1e9,
+                    "frac_of_peak": fb_bytes / (fb_mean * 1e-3) / 1e9 / hbm_peak,
+                    "backward_phases": {k: {"ms_per_frame": v[0] / args.steps,
+                                            "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None}
+                                        for k, v in sorted(bwd_kind.items())}},
+        "gpu_launches": launches_per_step * args.steps + bwd_launches * args.steps,
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -38,6 +38,8 @@ struct QuadGeom {
     int Un[HRC_MAXL + 1];            // probe columns per level
     long long Toff[HRC_MAXL + 1];    // byte offset of T_n in the arena
     long long Roff[HRC_MAXL + 1];    // byte offset of R_n (n < N)
+    long long gToff[HRC_MAXL + 1];   // adjoint buffers: dLoss/dT_n (C radiances + linear T) ...
+    long long gRoff[HRC_MAXL + 1];   // ... and dLoss/dR_n, in the arithmetic type
 };
 
 struct Plan {
@@ -195,6 +197,51 @@ template <int P, int C> struct RLevel {
     }
     __device__ __forceinline__ A load(int x, int i, int c, int v) const { return to_acc(base[idx(x, i, c, v)]); }
     __device__ __forceinline__ void store(int x, int i, int c, int v, A val) const { base[idx(x, i, c, v)] = from_acc<SL>(val); }
+};
+
+// Adjoint levels: dLoss/dT_n entries (C radiance components, then the
+// derivative with respect to the LINEAR transmittance, in every precision)
+// and dLoss/dR_n, both stored in the arithmetic type with the T/R layouts.
+template <int P, int C> struct GTLevel {
+    using A = typename Prec<P>::A;
+    char *base;
+    int K, Vs;
+    long long G;
+    __device__ __forceinline__ GTLevel(const Plan &pl, int q, int n) {
+        base = pl.arena + pl.q[q].gToff[n];
+        K = (1 << n) + 1;
+        Vs = pl.q[q].Vs;
+        G = (long long)Vs * (C + 1) * (long long)sizeof(A);
+    }
+    __device__ __forceinline__ A *row(int x, int k) const { return reinterpret_cast<A *>(base + ((long long)x * K + k) * G); }
+    __device__ __forceinline__ void load(int x, int k, int v, A (&L)[C], A &T) const {
+        const A *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) L[c] = g[(long long)c * Vs + v];
+        T = g[(long long)C * Vs + v];
+    }
+    __device__ __forceinline__ void store(int x, int k, int v, const A (&L)[C], A T) const {
+        A *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) g[(long long)c * Vs + v] = L[c];
+        g[(long long)C * Vs + v] = T;
+    }
+};
+
+template <int P, int C> struct GRLevel {
+    using A = typename Prec<P>::A;
+    A *base;
+    int I, Vs;
+    __device__ __forceinline__ GRLevel(const Plan &pl, int q, int n) {
+        base = reinterpret_cast<A *>(pl.arena + pl.q[q].gRoff[n]);
+        I = 1 << n;
+        Vs = pl.q[q].Vs;
+    }
+    __device__ __forceinline__ long long idx(int x, int i, int c, int v) const {
+        return (((long long)x * I + i) * C + c) * Vs + v;
+    }
+    __device__ __forceinline__ A load(int x, int i, int c, int v) const { return base[idx(x, i, c, v)]; }
+    __device__ __forceinline__ void store(int x, int i, int c, int v, A val) const { base[idx(x, i, c, v)] = val; }
 };
 
 template <int P> __device__ __forceinline__ typename Prec<P>::A arc(const Plan &pl, int n, int j) {

@@ -137,7 +137,7 @@ extern "C" hrc_status hrc_fluence_noalloc(int W, int H, int channels, const floa
     hrc_status st = setup_device(dev, &base);
     if (st != HRC_OK) return st;
     Plan pl;
-    const size_t end = build_plan(W, H, channels, 0, P_FP32, kLevelsOff, pl);
+    const size_t end = build_plan(W, H, channels, 0, P_FP32, kLevelsOff, pl, /*adjoint=*/false);
     if (end > kScratchBytes) return fail(HRC_EINVAL, "grid does not fit the fixed scratch");
     pl.arena = base;
     pl.arcs_off = (long long)kArcFloatOff;

@@ -79,9 +79,10 @@ RayTable make_ray_table() {
     return rt;
 }
 
-// Lays out T_0..T_N and R_0..R_{N-1} of all four frames from byte `off`;
-// returns the end offset.
-size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan &pl) {
+// Lays out T_0..T_N and R_0..R_{N-1} of all four frames from byte `off`
+// (and, with `adjoint`, the dL/dT_n and dL/dR_n buffers of the backward
+// pass); returns the end offset.
+size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan &pl, bool adjoint) {
     std::memset(&pl, 0, sizeof(pl));
     pl.W = W; pl.H = H; pl.C = C; pl.prec = prec;
     const size_t SLb = sl_bytes(prec), STb = st_bytes(prec);
@@ -102,6 +103,19 @@ size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan 
         for (int n = 0; n < g.N; ++n) {
             g.Roff[n] = (long long)off;
             off = align_up(off + (size_t)g.Un[n] * (1u << n) * C * g.Vs * SLb, 256);
+        }
+    }
+    // adjoint buffers (arithmetic type: fp64 for the fp64 precision, else fp32)
+    const size_t Ab = prec == P_FP64 ? 8 : 4;
+    for (int q = 0; q < 4 && adjoint; ++q) {
+        QuadGeom &g = pl.q[q];
+        for (int n = 0; n <= g.N; ++n) {
+            g.gToff[n] = (long long)off;
+            off = align_up(off + (size_t)g.Un[n] * ((1u << n) + 1) * g.Vs * (C + 1) * Ab, 256);
+        }
+        for (int n = 0; n < g.N; ++n) {
+            g.gRoff[n] = (long long)off;
+            off = align_up(off + (size_t)g.Un[n] * (1u << n) * C * g.Vs * Ab, 256);
         }
     }
     pl.arcs_off = (long long)off;
@@ -232,7 +246,7 @@ hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out) {
     if (e != cudaSuccess) { delete ctx; return fail(nullptr, HRC_ECUDA, std::string("hrc_create: ") + cudaGetErrorString(e)); }
     // The fp32 layout is the largest of the fp32 / fp16 / bf16 layouts.
     Plan p32;
-    size_t bytes = build_plan(W, H, channels, cascades, P_FP32, 0, p32);
+    size_t bytes = build_plan(W, H, channels, cascades, P_FP32, 0, p32, true);
     ctx->arena_bytes = bytes;
     e = cudaMalloc(&ctx->arena, bytes);
     if (e != cudaSuccess) {
@@ -282,7 +296,7 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
     if (prec == HRC_FP64_TEST) {
         if (!ctx->arena64) {
             Plan p64;
-            size_t bytes = build_plan(ctx->W, ctx->H, ctx->C, ctx->cascades, P_FP64, 0, p64);
+            size_t bytes = build_plan(ctx->W, ctx->H, ctx->C, ctx->cascades, P_FP64, 0, p64, true);
             cudaError_t e = cudaMalloc(&ctx->arena64, bytes);
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -297,7 +311,7 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
         }
     } else {
         Plan p;
-        build_plan(ctx->W, ctx->H, ctx->C, ctx->cascades, (int)prec, 0, p);
+        build_plan(ctx->W, ctx->H, ctx->C, ctx->cascades, (int)prec, 0, p, true);
         p.arena = ctx->arena;
         ctx->plan = p;
         cudaError_t e = upload_arcs(ctx->plan, ctx->arena);
@@ -355,6 +369,38 @@ hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *s
     ctx->last_e = emission;
     ctx->last_s = sigma_t;
     ctx->have_fwd = true;
+    return HRC_OK;
+}
+
+hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_emission, float *grad_sigma_t) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (ctx->prec == P_FP64) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward: context is in HRC_FP64_TEST");
+    if (!ctx->have_fwd) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward: no forward pass on this context");
+    if (!grad_F || !grad_emission || !grad_sigma_t) return fail(ctx, HRC_EINVAL, "hrc_fluence_backward: NULL pointer");
+    if (!aligned16(grad_F) || !aligned16(grad_emission) || !aligned16(grad_sigma_t))
+        return fail(ctx, HRC_EINVAL, "hrc_fluence_backward: pointers must be 16-byte aligned");
+    ctx->launches = 0;
+    ctx->rec.reset(ctx->stream);
+    cudaError_t e = launch_backward(ctx->plan, ctx->rt, ctx->last_e, ctx->last_s, grad_F, grad_emission, grad_sigma_t,
+                                    ctx->stream, &ctx->launches, &ctx->rec);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence_backward");
+    return HRC_OK;
+}
+
+hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *grad_emission, double *grad_sigma_t) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (ctx->prec != P_FP64) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward_f64: set HRC_FP64_TEST first");
+    if (!ctx->have_fwd) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward_f64: no forward pass on this context");
+    if (!grad_F || !grad_emission || !grad_sigma_t) return fail(ctx, HRC_EINVAL, "hrc_fluence_backward_f64: NULL pointer");
+    if (!aligned16(grad_F) || !aligned16(grad_emission) || !aligned16(grad_sigma_t))
+        return fail(ctx, HRC_EINVAL, "hrc_fluence_backward_f64: pointers must be 16-byte aligned");
+    ctx->launches = 0;
+    ctx->rec.reset(ctx->stream);
+    cudaError_t e = launch_backward(ctx->plan64, ctx->rt, ctx->last_e, ctx->last_s, grad_F, grad_emission,
+                                    grad_sigma_t, ctx->stream, &ctx->launches, &ctx->rec);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence_backward_f64");
     return HRC_OK;
 }
 

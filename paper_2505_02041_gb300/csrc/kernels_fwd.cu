@@ -22,74 +22,104 @@ struct RowSplit {
     long long start[5];   // first global row of each quadrant; start[4] = total
 };
 
-__device__ __forceinline__ int find_quadrant(const RowSplit &rs, long long r) {
+__device__ __forceinline__ int find_quadrant(const RowSplit &rs, long long r, int &local) {
     int q = 0;
+    long long base = 0;
 #pragma unroll
-    for (int j = 1; j < 4; ++j) q += (r >= rs.start[j]) ? 1 : 0;
+    for (int j = 1; j < 4; ++j)
+        if (r >= rs.start[j]) { q = j; base = rs.start[j]; }
+    local = (int)(r - base);
     return q;
 }
 
-// ---------------------------------------------------------------------------
-// Trace (Eq. 9) of one precomputed ray shape from probe pixel (u, v) of
-// frame q.  Each piece covers one pixel over a known length; a uniform
-// piece contributes <e l phi(sigma l), exp(-sigma l)>, phi(t) = (1-e^-t)/t.
-// ---------------------------------------------------------------------------
-template <int P, int C>
-__device__ __forceinline__ Iv<P, C> trace_ray(const Plan &pl, const RayTable &rt, int r, int q, int u, int v,
-                                              const float *__restrict__ e, const float *__restrict__ s,
-                                              const double *__restrict__ ed, const double *__restrict__ sd) {
-    using A = typename Prec<P>::A;
-    const QuadGeom &g = pl.q[q];
-    Iv<P, C> acc;
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc.L[c] = A(0);
-    A Tacc = A(1), tau_acc = A(0);
-    const long long HW = (long long)pl.W * pl.H;
-    for (int j = rt.start[r]; j < rt.start[r + 1]; ++j) {
-        const int uu = u + rt.p[j].du, vv = v + rt.p[j].dv;
-        if (uu >= g.U || vv < 0 || vv >= g.V) continue;   // vacuum outside the grid
-        int x, y;
-        frame_to_image(q, pl.W, pl.H, uu, vv, x, y);
-        const long long pix = (long long)y * pl.W + x;
-        const A len = (P == P_FP64) ? A(rt.lenD[j]) : A(rt.p[j].len);
-        const A sg = (P == P_FP64) ? A(sd[pix]) : A(s[pix]);
-        const A tau = sg * len;
-        const A m = fexpm1(-tau);                       // T_piece - 1
-        const A w = (sg != A(0)) ? -m / sg : len;       // len * phi(sigma len)
-        const A wt = Tacc * w;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const A ec = (P == P_FP64) ? A(ed[c * HW + pix]) : A(e[c * HW + pix]);
-            acc.L[c] = fma(wt, ec, acc.L[c]);
-        }
-        Tacc = Tacc + Tacc * m;
-        tau_acc += tau;
-    }
-    acc.t = Prec<P>::LOG ? tau_acc : Tacc;
-    return acc;
+// Piece weights of a uniform pixel crossed over length len (Eq. 4 over one
+// piece): returns w = len * phi(sigma len) and sets tp = exp(-sigma len).
+__device__ __forceinline__ float piece(float sg, float len, float &tp) {
+    const float tau = sg * len;
+    tp = __expf(-tau);
+    // len * phi(tau): (1 - e^-tau) / sigma away from 0, a short Taylor series near 0
+    const float series = len * (1.f - tau * (0.5f - tau * (1.f / 6.f - tau * (1.f / 24.f))));
+    return fabsf(tau) < 0.03f ? series : (1.f - tp) / sg;
+}
+__device__ __forceinline__ double piece(double sg, double len, double &tp) {
+    const double tau = sg * len;
+    const double m = expm1(-tau);
+    tp = 1.0 + m;
+    return sg != 0.0 ? -m / sg : len;
 }
 
-// One thread per (quadrant, probe pixel u, v): rays of level 0 always, of
-// level 1 when 2 | u, of level 2 when 4 | u (levels <= N only).  Warps run
-// along v, so every branch is warp-uniform.
+// T_0..T_min(2,N) of all four quadrant frames for one 32 x 32 image tile.
+// The tile's extinction and emission plus a 4-pixel halo (the longest
+// directly traced ray, v_2(k), reaches 4 pixels along and across) are
+// staged once in shared memory, zero outside the image (= vacuum, exact).
+// Work rows are (column c of the tile along the frame's u axis, ray r):
+// each warp traces one row for 32 consecutive v, so its T stores are
+// 128-byte coalesced row segments in every frame.
+constexpr int TR_TILE = 32, TR_HALO = 4, TR_REG = TR_TILE + 2 * TR_HALO, TR_PITCH = TR_REG + 1;
+
 template <int P, int C>
-__global__ void __launch_bounds__(256) k_trace012(Plan pl, RayTable rt, RowSplit rs, const float *__restrict__ e,
+__global__ void __launch_bounds__(256) k_trace012(Plan pl, RayTable rt, const float *__restrict__ e,
                                                   const float *__restrict__ s, const double *__restrict__ ed,
                                                   const double *__restrict__ sd) {
-    const long long row = blockIdx.x;             // (q, u)
-    const int q = find_quadrant(rs, row);
-    const int u = (int)(row - rs.start[q]);
-    const QuadGeom &g = pl.q[q];
-    const int v = blockIdx.y * blockDim.x + threadIdx.x;
-    if (v >= g.V) return;
-    const int nmax = g.N < 2 ? g.N : 2;
-    for (int n = 0; n <= nmax; ++n) {
-        if (u & ((1 << n) - 1)) break;
-        TLevel<P, C> T(pl, q, n);
-        const int x = u >> n;
-        for (int k = 0; k <= (1 << n); ++k) {
-            Iv<P, C> iv = trace_ray<P, C>(pl, rt, ray_id(n, k), q, u, v, e, s, ed, sd);
-            T.store(x, k, v, iv);
+    using A = typename Prec<P>::A;
+    extern __shared__ __align__(16) unsigned char tr_smem[];
+    A *sm_s = reinterpret_cast<A *>(tr_smem);                 // [TR_REG][TR_PITCH]
+    A *sm_e = sm_s + TR_REG * TR_PITCH;                        // [C][TR_REG][TR_PITCH]
+    const int W = pl.W, H = pl.H;
+    const int x0 = blockIdx.x * TR_TILE, y0 = blockIdx.y * TR_TILE;
+    const long long HW = (long long)W * H;
+    for (int i = threadIdx.x; i < TR_REG * TR_REG; i += blockDim.x) {
+        const int ry = i / TR_REG, rx = i - ry * TR_REG;
+        const int x = x0 - TR_HALO + rx, y = y0 - TR_HALO + ry;
+        const bool in = x >= 0 && x < W && y >= 0 && y < H;
+        const long long pix = (long long)y * W + x;
+        sm_s[ry * TR_PITCH + rx] = in ? ((P == P_FP64) ? A(sd[pix]) : A(s[pix])) : A(0);
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+            sm_e[(c * TR_REG + ry) * TR_PITCH + rx] = in ? ((P == P_FP64) ? A(ed[c * HW + pix]) : A(e[c * HW + pix])) : A(0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int q = 0; q < 4; ++q) {
+        const QuadGeom &g = pl.q[q];
+        const int nmax = g.N < 2 ? g.N : 2;
+        const bool xu = q < 2;                              // frame u runs along image x
+        const int tu = xu ? x0 : y0, tv = xu ? y0 : x0;     // tile origin along u / v axes
+        const int ext_u = xu ? W : H;
+        const int v = tv + lane;
+        for (int row = warp; row < TR_TILE * HRC_MAXRAY; row += nwarp) {
+            const int c = row / HRC_MAXRAY, r = row - c * HRC_MAXRAY;
+            const int n = r < 2 ? 0 : (r < 5 ? 1 : 2);
+            const int k = r - (n == 0 ? 0 : (n == 1 ? 2 : 5));
+            if (n > nmax || tu + c >= ext_u) continue;
+            const int u = (q == 0 || q == 2) ? tu + c : ext_u - 1 - (tu + c);
+            if (u & ((1 << n) - 1)) continue;
+            if (v >= g.V) continue;
+            A L[C];
+#pragma unroll
+            for (int cc = 0; cc < C; ++cc) L[cc] = A(0);
+            A Tacc = A(1), tau = A(0);
+            const int sgn = (q == 0 || q == 2) ? 1 : -1;     // image step along u
+            for (int j = rt.start[r]; j < rt.start[r + 1]; ++j) {
+                const int du = rt.p[j].du, dv = rt.p[j].dv;
+                const int a = TR_HALO + c + sgn * du, b = TR_HALO + lane + dv;   // tile coords (u axis, v axis)
+                const int sx = xu ? a : b, sy = xu ? b : a;
+                const int o = sy * TR_PITCH + sx;
+                const A len = (P == P_FP64) ? A(rt.lenD[j]) : A(rt.p[j].len);
+                const A sg = sm_s[o];
+                A tp;
+                const A w = piece(sg, len, tp);
+                const A wt = Tacc * w;
+#pragma unroll
+                for (int cc = 0; cc < C; ++cc) L[cc] = fma(wt, sm_e[cc * TR_REG * TR_PITCH + o], L[cc]);
+                Tacc *= tp;
+                tau += sg * len;
+            }
+            Iv<P, C> iv;
+#pragma unroll
+            for (int cc = 0; cc < C; ++cc) iv.L[cc] = L[cc];
+            iv.t = Prec<P>::LOG ? tau : Tacc;
+            TLevel<P, C>(pl, q, n).store(u >> n, k, v, iv);
         }
     }
 }
@@ -98,13 +128,12 @@ __global__ void __launch_bounds__(256) k_trace012(Plan pl, RayTable rt, RowSplit
 // operand at column 2x + 1 shifted by 2k' - 2^{n-1} along v.
 template <int P, int C>
 __global__ void __launch_bounds__(256) k_merge_up(Plan pl, RowSplit rs, int n) {
-    const long long row = blockIdx.x;             // (q, x, k)
-    const int q = find_quadrant(rs, row);
+    int local;
+    const int q = find_quadrant(rs, blockIdx.x, local);   // row = (q, x, k)
     const QuadGeom &g = pl.q[q];
     const int v = blockIdx.y * blockDim.x + threadIdx.x;
     if (v >= g.V) return;
     const int K = (1 << n) + 1;
-    const int local = (int)(row - rs.start[q]);
     const int x = local / K, k = local - x * K;
     const int m = n - 1, sm = 1 << m;
     TLevel<P, C> Tm(pl, q, m), Tn(pl, q, n);
@@ -130,13 +159,12 @@ __global__ void __launch_bounds__(256) k_merge_up(Plan pl, RowSplit rs, int n) {
 template <int P, int C>
 __global__ void __launch_bounds__(256) k_merge_down(Plan pl, RowSplit rs, int n) {
     using A = typename Prec<P>::A;
-    const long long row = blockIdx.x;             // (q, x, ip)
-    const int q = find_quadrant(rs, row);
+    int local;
+    const int q = find_quadrant(rs, blockIdx.x, local);   // row = (q, x, ip)
     const QuadGeom &g = pl.q[q];
     const int v = blockIdx.y * blockDim.x + threadIdx.x;
     if (v >= g.V) return;
     const int I = 1 << n;
-    const int local = (int)(row - rs.start[q]);
     const int x = local >> n, ip = local & (I - 1);
     const bool top = (n + 1 >= g.N);               // R_N = 0
     const int s = 1 << n;
@@ -270,7 +298,7 @@ double bytes_R(const Plan &pl, int q, int n) {
 
 template <int P, int C>
 static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
-                            cudaStream_t st, int *launches, Recorder *rec) {
+                            cudaStream_t st, int *launches, Recorder *rec, bool with_sum) {
     const int bs = 256;
     const int vb = vblocks(pl, bs);
     int Nmax = 0;
@@ -280,13 +308,18 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
     const double esz = P == P_FP64 ? 8.0 : 4.0;
     const double img = double(pl.W) * pl.H;
     {
-        RowSplit rs = make_split(pl, 0, 0);
         double by = img * (pl.C + 1) * esz;
         for (int q = 0; q < 4; ++q)
             for (int n = 0; n <= 2; ++n) by += bytes_T(pl, q, n);
-        dim3 grid((unsigned)rs.start[4], vb);
+        const size_t smem = sizeof(typename Prec<P>::A) * (C + 1) * TR_REG * TR_PITCH;
+        static bool attr_set = false;   // per template instance
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_trace012<P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr_set = true;
+        }
+        dim3 grid((pl.W + TR_TILE - 1) / TR_TILE, (pl.H + TR_TILE - 1) / TR_TILE);
         rec->begin(K_TRACE012, 0, by);
-        k_trace012<P, C><<<grid, bs, 0, st>>>(pl, rt, rs, ef, sf, ed, sd);
+        k_trace012<P, C><<<grid, 256, smem, st>>>(pl, rt, ef, sf, ed, sd);
         rec->end();
         ++*launches;
     }
@@ -309,9 +342,9 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         for (int q = 0; q < 4; ++q) {
             const QuadGeom &g = pl.q[q];
             if (n >= g.N) continue;
-            // odd columns of T_n, odd directions of T_{n+1}, R_{n+1} once, R_n written
+            // odd columns of T_n, even directions of T_{n+1}, R_{n+1} once, R_n written
             by += bytes_T(pl, q, n) * (double(g.Un[n] / 2) / g.Un[n]);
-            by += bytes_T(pl, q, n + 1) * (double(1 << n) / ((1 << (n + 1)) + 1));
+            by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
             by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
         }
         dim3 grid((unsigned)rs.start[4], vb);
@@ -320,7 +353,7 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         rec->end();
         ++*launches;
     }
-    {
+    if (with_sum) {
         double by = img * pl.C * esz;
         for (int q = 0; q < 4; ++q) by += bytes_R(pl, q, 0);
         dim3 grid((pl.W + bs - 1) / bs, pl.H);
@@ -337,11 +370,16 @@ template <int P>
 static cudaError_t fwd_prec(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
                             cudaStream_t st, int *launches, Recorder *rec) {
     switch (pl.C) {
-    case 1: return fwd_impl<P, 1>(pl, rt, e, s, F, st, launches, rec);
-    case 2: return fwd_impl<P, 2>(pl, rt, e, s, F, st, launches, rec);
-    case 3: return fwd_impl<P, 3>(pl, rt, e, s, F, st, launches, rec);
-    default: return fwd_impl<P, 4>(pl, rt, e, s, F, st, launches, rec);
+    case 1: return fwd_impl<P, 1>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
+    case 2: return fwd_impl<P, 2>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
+    case 3: return fwd_impl<P, 3>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
+    default: return fwd_impl<P, 4>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
     }
+}
+
+cudaError_t launch_forward_levels(const Plan &pl, const RayTable &rt, const void *e, const void *s,
+                                  cudaStream_t st, int *launches, Recorder *rec) {
+    return launch_forward(pl, rt, e, s, nullptr, st, launches, rec);
 }
 
 cudaError_t launch_forward(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,

@@ -57,10 +57,19 @@ cudaError_t launch_forward(const Plan &pl, const RayTable &rt, const void *e, co
 size_t align_up(size_t x, size_t a);
 int levels_for(int U, int cascades);
 RayTable make_ray_table();
-size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan &pl);
+size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan &pl, bool adjoint);
 int plan_nmax(const Plan &pl);
 // Message returned by hrc_last_error(NULL) on this thread.
 void set_global_error(const char *msg);
+
+// Forward without the fluence sum: every T and R level (for the backward).
+cudaError_t launch_forward_levels(const Plan &pl, const RayTable &rt, const void *e, const void *s,
+                                  cudaStream_t st, int *launches, Recorder *rec);
+
+// Backward pass: recompute every level from (e, s), then the adjoint of
+// every step; writes dL/de (ge) and dL/dsigma (gs) from dL/dF (gF).
+cudaError_t launch_backward(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,
+                            void *ge, void *gs, cudaStream_t st, int *launches, Recorder *rec);
 
 // Dense fp32 copy of level n of frame q (which = 0: T_n, 1: R_n).
 cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *dst, cudaStream_t st);
