@@ -197,8 +197,13 @@ def run_ours(args):
     s = torch.from_numpy(s_np).to(dev)
     F = torch.empty((C, H, W), dtype=torch.float32, device=dev)
     h = HRC(W, H, C, 0, args.precision)
+    if args.schedule >= 0:
+        _lib.hrc_set_schedule(h.ctx, args.schedule)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    gF = torch.ones((C, H, W), dtype=torch.float32, device=dev)
+    gE = torch.empty_like(e)
+    gS = torch.empty_like(s)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -206,62 +211,77 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(max(args.warmup, 3)):
+    def fwd():
         h.forward(e, s, F)
-    launches_per_step = h.launch_count()
-    _lib.hrc_set_timing(h.ctx, True)
+
+    def fwd_bwd():
+        h.forward(e, s, F)
+        _lib.hrc_fluence_backward(h.ctx, gF, gE, gS)
+
+    def timed(step, n, per_kind=None):
+        """n steps, L2 flushed before each, CUDA events on the launching
+        stream around each step; returns per-step ms."""
+        out = []
+        for _ in range(n):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+            if per_kind is not None:
+                for kind, level, ms, by in _lib.hrc_get_timing(h.ctx):
+                    d = per_kind.setdefault(kind, [0.0, 0.0, 0])
+                    d[0] += ms
+                    d[1] += by
+                    d[2] += 1
+        return out
+
+    for _ in range(max(args.warmup, 3)):
+        fwd_bwd()
+    fwd()
+    fwd_launches = h.launch_count()
+    fwd_bwd()
+    bwd_launches = h.launch_count()
+
+    # timed region 1: forward frames, graph-launched (the headline value)
     clocks = Clocks(local)
     barrier()
     clocks.start()
+    step_ms = timed(fwd, args.steps)
+    barrier()
+    # timed region 2: forward + backward
+    fb_ms = timed(fwd_bwd, args.steps)
+    barrier()
+    # timed region 3: the same frames with per-launch CUDA events (kernel
+    # durations for the roofline; launches are not graph-replayed here)
+    _lib.hrc_set_timing(h.ctx, True)
     per_kind = {}
-    step_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        h.forward(e, s, F)
-        b.record(stream)
-        b.synchronize()
-        step_ms.append(a.elapsed_time(b))
-        for kind, level, ms, by in _lib.hrc_get_timing(h.ctx):
-            d = per_kind.setdefault(kind, [0.0, 0.0, 0])
-            d[0] += ms
-            d[1] += by
-            d[2] += 1
-    # forward + backward (adjoint with recompute), same workload and timing rules
-    gF = torch.ones((C, H, W), dtype=torch.float32, device=dev)
-    gE = torch.empty_like(e)
-    gS = torch.empty_like(s)
+    prof_ms = timed(fwd, args.steps, per_kind)
     bwd_kind = {}
-    fb_ms = []
-    bwd_launches = 0
+    h.forward(e, s, F)
     for _ in range(args.steps):
         flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        h.forward(e, s, F)
-        nf = h.launch_count()
         _lib.hrc_fluence_backward(h.ctx, gF, gE, gS)
-        b.record(stream)
-        b.synchronize()
-        fb_ms.append(a.elapsed_time(b))
-        bwd_launches = nf + h.launch_count()
         for kind, level, ms, by in _lib.hrc_get_timing(h.ctx):
             d = bwd_kind.setdefault(kind, [0.0, 0.0, 0])
             d[0] += ms
             d[1] += by
             d[2] += 1
+    _lib.hrc_set_timing(h.ctx, False)
     barrier()
     clk = clocks.stop()
-    _lib.hrc_set_timing(h.ctx, False)
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
+        t = torch.tensor([total_ms, sum(fb_ms)], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms, fb_total = float(t[0].item()), float(t[1].item())
+    else:
+        fb_total = sum(fb_ms)
     ms_per_frame = total_ms / (args.steps * world)
+    fb_mean = fb_total / (args.steps * world)
 
     # end to end: host buffers through the C ABI, copies included
     e_h = torch.from_numpy(e_np).pin_memory()
@@ -281,15 +301,14 @@ def run_ours(args):
         return
 
     hbm_peak, peak_kind = peaks()
-    dom = max(per_kind.items(), key=lambda kv: kv[1][0])
-    kind, (kms, kbytes, kcount) = dom
+    kind, (kms, kbytes, kcount) = max(per_kind.items(), key=lambda kv: kv[1][0])
     achieved = (kbytes / kcount) / ((kms / kcount) * 1e-3) / 1e9
     phases = {k: {"ms_per_frame": v[0] / args.steps, "launches_per_frame": v[2] / args.steps,
                   "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None}
               for k, v in sorted(per_kind.items())}
     frame_bytes = sum(v[1] for v in per_kind.values()) / args.steps
-    fb_mean = statistics.mean(fb_ms)
-    fb_bytes = frame_bytes + sum(v[1] for v in bwd_kind.values()) / args.steps
+    bwd_bytes = sum(v[1] for v in bwd_kind.values()) / args.steps
+    fb_bytes = frame_bytes + bwd_bytes
     line = {
         "metric": METRIC, "value": ms_per_frame, "unit": "ms/frame", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
@@ -300,24 +319,43 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "precision": args.precision,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed (256 MB write) before every timed step, outside the timed events",
+                   "launch": "one CUDA graph per pass (captured at warm-up)",
                    "baseline_context": "paper Table 1 on an RTX 3080 Laptop with fp16 storage"},
         "roofline": {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                     "traffic": ncu_traffic(kind, args.workload)},
+                     "traffic": ncu_traffic(kind, args.workload),
+                     "timing": "per-launch CUDA events on the launching stream (timed region 3)"},
         "frame": {"algorithmic_bytes": frame_bytes, "GBps": frame_bytes / (ms_per_frame * 1e-3) / 1e9,
-                  "frac_of_peak": frame_bytes / (ms_per_frame * 1e-3) / 1e9 / hbm_peak},
+                  "frac_of_peak": frame_bytes / (ms_per_frame * 1e-3) / 1e9 / hbm_peak,
+                  "ms_with_per_launch_events": statistics.mean(prof_ms)},
         "phases": phases,
-        "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": (C + 1) * H * W * 4,
-                "d2h_bytes_per_step": C * H * W * 4},
         "fwd_bwd": {"ms": fb_mean, "algorithmic_bytes": fb_bytes,
                     "GBps": fb_bytes / (fb_mean * 1e-3) / 1e9,
                     "frac_of_peak": fb_bytes / (fb_mean * 1e-3) / 1e9 / hbm_peak,
-                    "backward_phases": {k: {"ms_per_frame": v[0] / args.steps,
+                    "backward_phases": {k: {"ms_per_frame": v[0] / args.steps, "launches_per_frame": v[2] / args.steps,
                                             "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None}
                                         for k, v in sorted(bwd_kind.items())}},
-        "gpu_launches": launches_per_step * args.steps + bwd_launches * args.steps,
+        "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": (C + 1) * H * W * 4,
+                "d2h_bytes_per_step": C * H * W * 4},
+        "gpu_launches": (fwd_launches + bwd_launches) * args.steps,
         "clocks": clk,
     }
+    if args.precisions and world == 1:
+        import oracle
+        Fr = oracle.fluence(e_np, s_np)
+        rows = {}
+        for prec in ("fp32", "fp16", "bf16"):
+            hp = HRC(W, H, C, 0, prec)
+            Fp = torch.empty((C, H, W), dtype=torch.float32, device=dev)
+            for _ in range(3):
+                hp.forward(e, s, Fp)
+            ms = timed(lambda: hp.forward(e, s, Fp), args.steps)
+            Fn = Fp.cpu().numpy().astype(np.float64)
+            rows[prec] = {"ms_per_frame": statistics.mean(ms),
+                          "err_max": float(np.max(np.abs(Fn - Fr)) / np.max(np.abs(Fr))),
+                          "rel_l2": float(np.linalg.norm(Fn - Fr) / np.linalg.norm(Fr))}
+            hp.close()
+        line["precisions"] = rows
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
@@ -334,6 +372,9 @@ def main():
     ap.add_argument("--workload", default="volumetric1024", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precisions", dest="precisions", action="store_false",
+                    help="skip the fp16 / bf16 error-and-time sweep against the FP64 oracle")
+    ap.add_argument("--schedule", type=int, default=-1, help="launch schedule (default: the library's)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

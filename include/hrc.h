@@ -74,6 +74,13 @@ hrc_status hrc_set_stream(hrc_ctx *ctx, void *cuda_stream);
  * Switching to HRC_FP64_TEST allocates its fp64 buffers once. */
 hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec);
 
+/* Launch schedule (a tuning knob; results are identical either way):
+ * 0 = every kernel launch covers the four quadrant frames (level-major);
+ * 1 = the frames run one after another, so that each level's producer and
+ *     consumer meet in L2.  Default 0 (faster on GB300: four times fewer,
+ *     larger launches). */
+hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule);
+
 /* Forward pass, Algorithm 1 (Lighting) without the Eq. 21 blur:
  * out[c][y][x] = sum over the four quadrant frames of R_0([u+1, v], 1/2).
  * emission [C][H][W], sigma_t [H][W], out [C][H][W]: device fp32.

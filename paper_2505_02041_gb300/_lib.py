@@ -26,6 +26,7 @@ SIGNATURES = [
     ("hrc_destroy", _i, [_vp]),
     ("hrc_set_stream", _i, [_vp, _vp]),
     ("hrc_set_precision", _i, [_vp, _i]),
+    ("hrc_set_schedule", _i, [_vp, _i]),
     ("hrc_fluence", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_fluence_host", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_fluence_backward", _i, [_vp, _vp, _vp, _vp]),
@@ -103,6 +104,10 @@ def hrc_set_stream(ctx, stream_handle: int):
 
 def hrc_set_precision(ctx, prec: int):
     check(load().hrc_set_precision(ctx, prec), ctx)
+
+
+def hrc_set_schedule(ctx, schedule: int):
+    check(load().hrc_set_schedule(ctx, schedule), ctx)
 
 
 def hrc_fluence(ctx, emission, sigma_t, out):

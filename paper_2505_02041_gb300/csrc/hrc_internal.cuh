@@ -44,6 +44,7 @@ struct QuadGeom {
 
 struct Plan {
     int W, H, C, prec;
+    int sched;                       // 0: each launch covers all four frames; 1: frame by frame
     long long arcs_off;              // byte offset: float A[2^n + j] for level n (n >= 1)
     long long arcs_off_d;            // same table in double
     char *arena;
@@ -150,6 +151,27 @@ __device__ __forceinline__ Iv<P, C> blend(const Iv<P, C> &a, const Iv<P, C> &b) 
     return r;
 }
 
+// 2-wide loads / stores of two consecutive v (the first v even, so every
+// pair is 2-element aligned).
+__device__ __forceinline__ void ld2(const float *p, float &x, float &y) {
+    const float2 t = *reinterpret_cast<const float2 *>(p); x = t.x; y = t.y;
+}
+__device__ __forceinline__ void ld2(const double *p, double &x, double &y) {
+    const double2 t = *reinterpret_cast<const double2 *>(p); x = t.x; y = t.y;
+}
+__device__ __forceinline__ void ld2(const __half *p, float &x, float &y) {
+    const __half2 t = *reinterpret_cast<const __half2 *>(p); x = __low2float(t); y = __high2float(t);
+}
+__device__ __forceinline__ void ld2(const __nv_bfloat16 *p, float &x, float &y) {
+    const __nv_bfloat162 t = *reinterpret_cast<const __nv_bfloat162 *>(p); x = __low2float(t); y = __high2float(t);
+}
+__device__ __forceinline__ void st2(float *p, float x, float y) { *reinterpret_cast<float2 *>(p) = make_float2(x, y); }
+__device__ __forceinline__ void st2(double *p, double x, double y) { *reinterpret_cast<double2 *>(p) = make_double2(x, y); }
+__device__ __forceinline__ void st2(__half *p, float x, float y) { *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(x, y); }
+__device__ __forceinline__ void st2(__nv_bfloat16 *p, float x, float y) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(x, y);
+}
+
 // ---------------------------------------------------------------------------
 // Level addressing
 // ---------------------------------------------------------------------------
@@ -180,6 +202,29 @@ template <int P, int C> struct TLevel {
         for (int c = 0; c < C; ++c) reinterpret_cast<SL *>(g)[(long long)c * Vs + v] = from_acc<SL>(r.L[c]);
         reinterpret_cast<ST *>(g + (long long)C * Vs * sizeof(SL))[v] = from_acc<ST>(r.t);
     }
+    // entries v and v+1 (v even)
+    __device__ __forceinline__ void load2(int x, int k, int v, Iv<P, C> &a, Iv<P, C> &b) const {
+        const char *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) ld2(reinterpret_cast<const SL *>(g) + (long long)c * Vs + v, a.L[c], b.L[c]);
+        ld2(reinterpret_cast<const ST *>(g + (long long)C * Vs * sizeof(SL)) + v, a.t, b.t);
+    }
+    // entries v, v+1 with vacuum outside [0, V) (v even, so v < 0 means both out)
+    __device__ __forceinline__ void load2_masked(int x, int k, int v, int V, Iv<P, C> &a, Iv<P, C> &b) const {
+        if (v >= 0 && v < V) {
+            load2(x, k, v, a, b);
+            if (v + 1 >= V) b = Iv<P, C>::vacuum();
+        } else {
+            a = Iv<P, C>::vacuum();
+            b = a;
+        }
+    }
+    __device__ __forceinline__ void store2(int x, int k, int v, const Iv<P, C> &a, const Iv<P, C> &b) const {
+        char *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) st2(reinterpret_cast<SL *>(g) + (long long)c * Vs + v, a.L[c], b.L[c]);
+        st2(reinterpret_cast<ST *>(g + (long long)C * Vs * sizeof(SL)) + v, a.t, b.t);
+    }
 };
 
 template <int P, int C> struct RLevel {
@@ -197,6 +242,8 @@ template <int P, int C> struct RLevel {
     }
     __device__ __forceinline__ A load(int x, int i, int c, int v) const { return to_acc(base[idx(x, i, c, v)]); }
     __device__ __forceinline__ void store(int x, int i, int c, int v, A val) const { base[idx(x, i, c, v)] = from_acc<SL>(val); }
+    __device__ __forceinline__ void load2(int x, int i, int c, int v, A &a, A &b) const { ld2(base + idx(x, i, c, v), a, b); }
+    __device__ __forceinline__ void store2(int x, int i, int c, int v, A a, A b) const { st2(base + idx(x, i, c, v), a, b); }
 };
 
 // Adjoint levels: dLoss/dT_n entries (C radiance components, then the
@@ -242,6 +289,7 @@ template <int P, int C> struct GRLevel {
     }
     __device__ __forceinline__ A load(int x, int i, int c, int v) const { return base[idx(x, i, c, v)]; }
     __device__ __forceinline__ void store(int x, int i, int c, int v, A val) const { base[idx(x, i, c, v)] = val; }
+    __device__ __forceinline__ void store2(int x, int i, int c, int v, A a, A b) const { st2(base + idx(x, i, c, v), a, b); }
 };
 
 template <int P> __device__ __forceinline__ typename Prec<P>::A arc(const Plan &pl, int n, int j) {

@@ -93,6 +93,8 @@ hrc_status setup_device(int dev, char **base) {
         g_rays_ready = true;
     }
     if (!g_ready[dev]) {
+        cudaError_t ep = prepare_device_once();
+        if (ep != cudaSuccess) return fail(HRC_ECUDA, std::string("kernel set-up failed: ") + cudaGetErrorString(ep));
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || p == nullptr)

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -25,6 +26,22 @@ thread_local std::string g_create_error;
 namespace hrc {
 
 void set_global_error(const char *msg) { g_create_error = msg; }
+
+// Kernel attributes are per device: set them once for each device used.
+cudaError_t prepare_device_once() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    e = prepare_forward_kernels();
+    if (e == cudaSuccess) e = prepare_backward_kernels();
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -150,6 +167,7 @@ void fill_arcs(int Nmax, std::vector<float> &af, std::vector<double> &ad) {
 struct hrc_ctx {
     int W = 0, H = 0, C = 0, cascades = 0;
     int prec = P_FP32;
+    int sched = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     RayTable rt;
@@ -165,6 +183,19 @@ struct hrc_ctx {
     int launches = 0;
     Recorder rec;
     std::string err;
+    // CUDA graphs of whole passes, keyed by pass kind, precision, schedule
+    // and the caller's pointers; captured on a context-owned stream and
+    // replayed on the caller's stream.
+    struct GraphEntry {
+        int kind = -1, prec = -1, sched = -1;
+        const void *p[5] = {};
+        cudaGraphExec_t exec = nullptr;
+        int launches = 0;
+    };
+    GraphEntry graphs[8];
+    int graph_next = 0;
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -189,6 +220,59 @@ cudaError_t upload_arcs(const Plan &pl, char *arena) {
     cudaError_t e = cudaMemcpy(arena + pl.arcs_off, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     return cudaMemcpy(arena + pl.arcs_off_d, ad.data(), ad.size() * sizeof(double), cudaMemcpyHostToDevice);
+}
+
+// Enqueue one pass (forward or backward) on the context's stream: replay its
+// CUDA graph when one exists for these pointers, capture one otherwise.
+// With per-launch timing on, the kernels are launched directly.
+template <class ENQ>
+hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, const void *p2, const void *p3,
+                    const void *p4, ENQ &&enqueue, const char *where) {
+    ctx->launches = 0;
+    if (ctx->rec.on || !ctx->use_graphs) {
+        ctx->rec.reset(ctx->stream);
+        cudaError_t e = enqueue(ctx->stream, &ctx->launches, &ctx->rec);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+        return HRC_OK;
+    }
+    const void *key[5] = {p0, p1, p2, p3, p4};
+    for (auto &g : ctx->graphs) {
+        if (g.exec && g.kind == kind && g.prec == ctx->prec && g.sched == ctx->sched &&
+            std::memcmp(g.p, key, sizeof(key)) == 0) {
+            cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+            ctx->launches = g.launches;
+            return HRC_OK;
+        }
+    }
+    Recorder off;
+    int n = 0;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+    cudaError_t e1 = enqueue(ctx->cap_stream, &n, &off);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e1 != cudaSuccess ? e1 : e2, where);
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+    auto &slot = ctx->graphs[ctx->graph_next];
+    ctx->graph_next = (ctx->graph_next + 1) % 8;
+    if (slot.exec) cudaGraphExecDestroy(slot.exec);
+    slot.exec = exec;
+    slot.kind = kind;
+    slot.prec = ctx->prec;
+    slot.sched = ctx->sched;
+    std::memcpy(slot.p, key, sizeof(key));
+    slot.launches = n;
+    e = cudaGraphLaunch(exec, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+    ctx->launches = n;
+    return HRC_OK;
 }
 
 hrc_status check_ctx(hrc_ctx *ctx) {
@@ -243,6 +327,8 @@ hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out) {
     ctx->W = W; ctx->H = H; ctx->C = channels; ctx->cascades = cascades;
     ctx->rt = make_ray_table();
     cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = prepare_device_once();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete ctx; return fail(nullptr, HRC_ECUDA, std::string("hrc_create: ") + cudaGetErrorString(e)); }
     // The fp32 layout is the largest of the fp32 / fp16 / bf16 layouts.
     Plan p32;
@@ -265,6 +351,7 @@ hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out) {
     }
     ctx->plan = p32;
     ctx->plan.arena = ctx->arena;
+    ctx->plan.sched = ctx->sched;
     e = upload_arcs(ctx->plan, ctx->arena);
     if (e != cudaSuccess) { hrc_destroy(ctx); return fail(nullptr, HRC_ECUDA, "hrc_create: arc upload failed"); }
     *out = ctx;
@@ -280,7 +367,19 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->dev_e);
     cudaFree(ctx->dev_s);
     cudaFree(ctx->dev_F);
+    for (auto &g : ctx->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
+    return HRC_OK;
+}
+
+hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule) {
+    if (!ctx) return HRC_EINVAL;
+    if (schedule != 0 && schedule != 1) return fail(ctx, HRC_EINVAL, "hrc_set_schedule: 0 or 1");
+    ctx->sched = schedule;
+    ctx->plan.sched = schedule;
+    ctx->plan64.sched = schedule;
     return HRC_OK;
 }
 
@@ -305,6 +404,7 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
             }
             ctx->arena64_bytes = bytes;
             p64.arena = ctx->arena64;
+            p64.sched = ctx->sched;
             ctx->plan64 = p64;
             e = upload_arcs(ctx->plan64, ctx->arena64);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
@@ -313,6 +413,7 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
         Plan p;
         build_plan(ctx->W, ctx->H, ctx->C, ctx->cascades, (int)prec, 0, p, true);
         p.arena = ctx->arena;
+        p.sched = ctx->sched;
         ctx->plan = p;
         cudaError_t e = upload_arcs(ctx->plan, ctx->arena);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
@@ -329,10 +430,12 @@ hrc_status hrc_fluence(hrc_ctx *ctx, const float *emission, const float *sigma_t
     if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence: NULL pointer");
     if (!aligned16(emission) || !aligned16(sigma_t) || !aligned16(out))
         return fail(ctx, HRC_EINVAL, "hrc_fluence: pointers must be 16-byte aligned");
-    ctx->launches = 0;
-    ctx->rec.reset(ctx->stream);
-    cudaError_t e = launch_forward(ctx->plan, ctx->rt, emission, sigma_t, out, ctx->stream, &ctx->launches, &ctx->rec);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence");
+    const Plan pl = ctx->plan;
+    const RayTable *rt = &ctx->rt;
+    st = run_pass(ctx, 0, emission, sigma_t, out, nullptr, nullptr,
+                  [&](cudaStream_t s, int *n, Recorder *r) { return launch_forward(pl, *rt, emission, sigma_t, out, s, n, r); },
+                  "hrc_fluence");
+    if (st != HRC_OK) return st;
     ctx->last_e = emission;
     ctx->last_s = sigma_t;
     ctx->have_fwd = true;
@@ -362,10 +465,12 @@ hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *s
     if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence_f64: NULL pointer");
     if (!aligned16(emission) || !aligned16(sigma_t) || !aligned16(out))
         return fail(ctx, HRC_EINVAL, "hrc_fluence_f64: pointers must be 16-byte aligned");
-    ctx->launches = 0;
-    ctx->rec.reset(ctx->stream);
-    cudaError_t e = launch_forward(ctx->plan64, ctx->rt, emission, sigma_t, out, ctx->stream, &ctx->launches, &ctx->rec);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence_f64");
+    const Plan pl = ctx->plan64;
+    const RayTable *rt = &ctx->rt;
+    st = run_pass(ctx, 2, emission, sigma_t, out, nullptr, nullptr,
+                  [&](cudaStream_t s, int *n, Recorder *r) { return launch_forward(pl, *rt, emission, sigma_t, out, s, n, r); },
+                  "hrc_fluence_f64");
+    if (st != HRC_OK) return st;
     ctx->last_e = emission;
     ctx->last_s = sigma_t;
     ctx->have_fwd = true;
@@ -380,12 +485,14 @@ hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_e
     if (!grad_F || !grad_emission || !grad_sigma_t) return fail(ctx, HRC_EINVAL, "hrc_fluence_backward: NULL pointer");
     if (!aligned16(grad_F) || !aligned16(grad_emission) || !aligned16(grad_sigma_t))
         return fail(ctx, HRC_EINVAL, "hrc_fluence_backward: pointers must be 16-byte aligned");
-    ctx->launches = 0;
-    ctx->rec.reset(ctx->stream);
-    cudaError_t e = launch_backward(ctx->plan, ctx->rt, ctx->last_e, ctx->last_s, grad_F, grad_emission, grad_sigma_t,
-                                    ctx->stream, &ctx->launches, &ctx->rec);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence_backward");
-    return HRC_OK;
+    const Plan pl = ctx->plan;
+    const RayTable *rt = &ctx->rt;
+    const void *le = ctx->last_e, *ls = ctx->last_s;
+    return run_pass(ctx, 1, le, ls, grad_F, grad_emission, grad_sigma_t,
+                    [&](cudaStream_t s, int *n, Recorder *r) {
+                        return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, s, n, r);
+                    },
+                    "hrc_fluence_backward");
 }
 
 hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *grad_emission, double *grad_sigma_t) {
@@ -396,12 +503,14 @@ hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *
     if (!grad_F || !grad_emission || !grad_sigma_t) return fail(ctx, HRC_EINVAL, "hrc_fluence_backward_f64: NULL pointer");
     if (!aligned16(grad_F) || !aligned16(grad_emission) || !aligned16(grad_sigma_t))
         return fail(ctx, HRC_EINVAL, "hrc_fluence_backward_f64: pointers must be 16-byte aligned");
-    ctx->launches = 0;
-    ctx->rec.reset(ctx->stream);
-    cudaError_t e = launch_backward(ctx->plan64, ctx->rt, ctx->last_e, ctx->last_s, grad_F, grad_emission,
-                                    grad_sigma_t, ctx->stream, &ctx->launches, &ctx->rec);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_fluence_backward_f64");
-    return HRC_OK;
+    const Plan pl = ctx->plan64;
+    const RayTable *rt = &ctx->rt;
+    const void *le = ctx->last_e, *ls = ctx->last_s;
+    return run_pass(ctx, 3, le, ls, grad_F, grad_emission, grad_sigma_t,
+                    [&](cudaStream_t s, int *n, Recorder *r) {
+                        return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, s, n, r);
+                    },
+                    "hrc_fluence_backward_f64");
 }
 
 hrc_status hrc_copy_level(hrc_ctx *ctx, int q, int which, int n, float *dst, long long *count) {

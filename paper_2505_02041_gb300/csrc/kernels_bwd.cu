@@ -26,6 +26,7 @@
 
 #include "hrc_internal.cuh"
 #include "launch.h"
+#include "trace_shapes.cuh"
 
 namespace hrc {
 
@@ -48,24 +49,52 @@ __device__ __forceinline__ int quadrant_of(const RowSplitB &rs, long long r, int
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Reverse of the fluence sum (Algorithm 1, Lighting): F(x,y) += R_0^q(u+1, v)
+// Reverse of the fluence sum (Algorithm 1, Lighting): F(x,y) += R_0^q(u+1, v),
+// so dL/dR_0^q(u+1, v) = dL/dF at the pixel of frame (u, v), and column 0 of
+// every dL/dR_0^q is zero.  One CTA per 32 x 32 image tile: the tile of dL/dF
+// is read coalesced into shared memory and written out transposed for the
+// frames whose v runs along image x.
 // ---------------------------------------------------------------------------
 template <int P, int C, class GIN>
-__global__ void __launch_bounds__(256) k_adj_sum(Plan pl, RowSplitB rs, const GIN *__restrict__ gF) {
+__global__ void __launch_bounds__(256) k_adj_sum(Plan pl, const GIN *__restrict__ gF) {
     using A = typename Prec<P>::A;
-    int x;
-    const int q = quadrant_of(rs, blockIdx.x, x);   // row = (q, x) of R_0
-    const QuadGeom &g = pl.q[q];
-    const int v = blockIdx.y * blockDim.x + threadIdx.x;
-    if (v >= g.V) return;
-    GRLevel<P, C> gR0(pl, q, 0);
-    const long long HW = (long long)pl.W * pl.H;
-    int px = 0, py = 0;
-    if (x >= 1) frame_to_image(q, pl.W, pl.H, x - 1, v, px, py);
+    __shared__ A tile[C][32][33];
+    const int W = pl.W, H = pl.H;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const long long HW = (long long)W * H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < 32; r += 8) {
+        const int x = x0 + lane, y = y0 + r;
 #pragma unroll
-    for (int c = 0; c < C; ++c)
-        gR0.store(x, 0, c, v, x >= 1 ? A(gF[c * HW + (long long)py * pl.W + px]) : A(0));
+        for (int c = 0; c < C; ++c) tile[c][r][lane] = (x < W && y < H) ? A(gF[c * HW + (long long)y * W + x]) : A(0);
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        const QuadGeom &g = pl.q[q];
+        if (g.N < 1) continue;
+        GRLevel<P, C> gR0(pl, q, 0);
+        const bool xu = q < 2;
+        const int tu = xu ? x0 : y0, tv = xu ? y0 : x0, ext_u = xu ? W : H;
+        const int v = tv + lane;
+        if (v >= g.V) continue;
+        for (int cidx = warp; cidx < 32; cidx += 8) {
+            if (tu + cidx >= ext_u) continue;
+            const int u = (q == 0 || q == 2) ? tu + cidx : ext_u - 1 - (tu + cidx);
+            const int iy = xu ? lane : cidx, ix = xu ? cidx : lane;
+#pragma unroll
+            for (int c = 0; c < C; ++c) gR0.store(u + 1 < g.U ? u + 1 : 0, 0, c, v, u + 1 < g.U ? tile[c][iy][ix] : A(0));
+            if (u == 0) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) gR0.store(0, 0, c, v, A(0));
+            }
+        }
+    }
 }
+
+// Two consecutive v per thread (E = 2, all neighbour offsets even) or one.
+template <class A, int E> struct Lanes {
+    A x[E];
+};
 
 // ---------------------------------------------------------------------------
 // dL/dR_{n+1}(x', j, w).  For cone index j (j + 1/2 at level n+1) the parent
@@ -75,45 +104,50 @@ __global__ void __launch_bounds__(256) k_adj_sum(Plan pl, RowSplitB rs, const GI
 //   even parent x = 2x' (Eq. 16):       1/2                 * gR_n(x, ip, w)
 //   even parent x = 2x'-2 (Eq. 17):     T_{n+1}(x'-1, 2kk, w-2d).T / 2 * gR_n(x, ip, w-2d)
 // ---------------------------------------------------------------------------
-template <int P, int C>
+template <int P, int C, int E>
 __global__ void __launch_bounds__(256) k_adj_R(Plan pl, RowSplitB rs, int n) {
     using A = typename Prec<P>::A;
     int local;
     const int q = quadrant_of(rs, blockIdx.x, local);   // row = (q, x', j) at level n+1
     const QuadGeom &g = pl.q[q];
-    const int w = blockIdx.y * blockDim.x + threadIdx.x;
+    const int w = E * (blockIdx.y * blockDim.x + threadIdx.x);
     if (w >= g.V) return;
     const int x1 = local >> (n + 1), j = local & ((2 << n) - 1);
     const int ip = j >> 1, kk = (j + 1) >> 1;
     const int d = 2 * kk - (1 << n);
     GRLevel<P, C> gRn(pl, q, n), gR1(pl, q, n + 1);
-    A acc[C];
+    A acc[E][C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = A(0);
+    for (int l = 0; l < E; ++l)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[l][c] = A(0);
+    // terms at v = w - sh (sh even when E = 2): weight * T * gR_n(xp, ip, v)
+    auto term = [&](int xp, int sh, A wgt, const TLevel<P, C> *T, int xt, int kt) {
+        const int v = w - sh;
+#pragma unroll
+        for (int l = 0; l < E; ++l) {
+            if (v + l < 0 || v + l >= g.V) continue;
+            const A t = T ? wgt * T->load(xt, kt, v + l).trans() : wgt;
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[l][c] = fma(t, gRn.load(xp, ip, c, v + l), acc[l][c]);
+        }
+    };
     const int xo = 2 * x1 - 1;
     if (x1 >= 1 && xo < g.Un[n]) {
-        const int v = w - d;
-        if (v >= 0 && v < g.V) {
-            const A t = TLevel<P, C>(pl, q, n).load(xo, kk, v).trans();
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = fma(t, gRn.load(xo, ip, c, v), acc[c]);
-        }
+        TLevel<P, C> Tn(pl, q, n);
+        term(xo, d, A(1), &Tn, xo, kk);
     }
-    if (2 * x1 < g.Un[n]) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] = fma(A(0.5), gRn.load(2 * x1, ip, c, w), acc[c]);
-    }
+    if (2 * x1 < g.Un[n]) term(2 * x1, 0, A(0.5), nullptr, 0, 0);
     const int xe = 2 * x1 - 2;
     if (x1 >= 1 && xe < g.Un[n]) {
-        const int v = w - 2 * d;
-        if (v >= 0 && v < g.V) {
-            const A t = A(0.5) * TLevel<P, C>(pl, q, n + 1).load(x1 - 1, 2 * kk, v).trans();
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = fma(t, gRn.load(xe, ip, c, v), acc[c]);
-        }
+        TLevel<P, C> T1(pl, q, n + 1);
+        term(xe, 2 * d, A(0.5), &T1, x1 - 1, 2 * kk);
     }
 #pragma unroll
-    for (int c = 0; c < C; ++c) gR1.store(x1, j, c, w, acc[c]);
+    for (int c = 0; c < C; ++c) {
+        if (E == 2) gR1.store2(x1, j, c, w, acc[0][c], acc[E - 1][c]);
+        else gR1.store(x1, j, c, w, acc[0][c]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -125,64 +159,62 @@ __global__ void __launch_bounds__(256) k_adj_R(Plan pl, RowSplitB rs, int n) {
 //     T_n(x, k) as F_+ (arc A_n(k-1)), cone k/2 as F_- (arc A_n(k)), each
 //     with weight 1/2; far fluence R_n(x+1, j, v+d), d = 2k - 2^n.
 // ---------------------------------------------------------------------------
-template <int P, int C>
+template <int P, int C, int E>
 __global__ void __launch_bounds__(256) k_adj_T(Plan pl, RowSplitB rs, int n) {
     using A = typename Prec<P>::A;
     int local;
     const int q = quadrant_of(rs, blockIdx.x, local);   // row = (q, x, k) at level n
     const QuadGeom &g = pl.q[q];
-    const int v = blockIdx.y * blockDim.x + threadIdx.x;
+    const int v = E * (blockIdx.y * blockDim.x + threadIdx.x);
     if (v >= g.V) return;
     const int K = (1 << n) + 1;
     const int x = local / K, k = local - x * K;
     const int s = 1 << n;
     const int d = 2 * k - s;
-    A gL[C];
+    A gL[E][C], gT[E];
 #pragma unroll
-    for (int c = 0; c < C; ++c) gL[c] = A(0);
-    A gT = A(0);
-    if ((x & 1) && n < g.N) {
-        GRLevel<P, C> gRn(pl, q, n);
-        const int xq = (x + 1) >> 1;
-        const bool rq = (n + 1 < g.N) && xq < g.Un[n + 1] && v + d >= 0 && v + d < g.V;
+    for (int l = 0; l < E; ++l) {
+        gT[l] = A(0);
 #pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-            const int ip = sg == 0 ? k - 1 : k;          // F_+ of cone k-1, F_- of cone k
-            if (ip < 0 || ip >= s) continue;
-            const int j = sg == 0 ? 2 * k - 1 : 2 * k;
-            const A Aj = arc<P>(pl, n + 1, j);
+        for (int c = 0; c < C; ++c) gL[l][c] = A(0);
+    }
+    // one cone's contribution: arc weight Aw on gR(xg, ip), dot weight dw
+    // with R(xr, j, v + d) when rq
+    auto cone = [&](const GRLevel<P, C> &gR, int xg, int ip, A Aw, A dw, bool rq, const RLevel<P, C> &R, int xr, int j) {
+#pragma unroll
+        for (int l = 0; l < E; ++l) {
+            const int vv = v + l;
+            const bool rok = rq && vv + d >= 0 && vv + d < g.V;
             A dot = A(0);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const A gr = gRn.load(x, ip, c, v);
-                gL[c] = fma(Aj, gr, gL[c]);
-                if (rq) dot = fma(gr, RLevel<P, C>(pl, q, n + 1).load(xq, j, c, v + d), dot);
+                const A gr = gR.load(xg, ip, c, vv);
+                gL[l][c] = fma(Aw, gr, gL[l][c]);
+                if (rok) dot = fma(gr, R.load(xr, j, c, vv + d), dot);
             }
-            gT += dot;
+            gT[l] = fma(dw, dot, gT[l]);
         }
+    };
+    if ((x & 1) && n < g.N) {
+        GRLevel<P, C> gRn(pl, q, n);
+        const int xq = (x + 1) >> 1;
+        const bool rq = (n + 1 < g.N) && xq < g.Un[n + 1];
+        RLevel<P, C> R1(pl, q, rq ? n + 1 : n);
+        if (k >= 1) cone(gRn, x, k - 1, arc<P>(pl, n + 1, 2 * k - 1), A(1), rq, R1, xq, 2 * k - 1);
+        if (k < s) cone(gRn, x, k, arc<P>(pl, n + 1, 2 * k), A(1), rq, R1, xq, 2 * k);
     }
     if (!(k & 1) && n >= 1) {
         const int m = n - 1;
         GRLevel<P, C> gRm(pl, q, m);
-        const int xe = 2 * x;                              // even column of level n-1
-        const bool rq = (n < g.N) && x + 1 < g.Un[n] && v + d >= 0 && v + d < g.V;
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-            const int ip = sg == 0 ? (k >> 1) - 1 : (k >> 1);
-            if (ip < 0 || ip >= (1 << m)) continue;
-            const int j = sg == 0 ? k - 1 : k;
-            const A Aj = A(0.5) * arc<P>(pl, n, j);
-            A dot = A(0);
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const A gr = gRm.load(xe, ip, c, v);
-                gL[c] = fma(Aj, gr, gL[c]);
-                if (rq) dot = fma(gr, RLevel<P, C>(pl, q, n).load(x + 1, j, c, v + d), dot);
-            }
-            gT = fma(A(0.5), dot, gT);
-        }
+        const bool rq = (n < g.N) && x + 1 < g.Un[n];
+        RLevel<P, C> Rn(pl, q, rq ? n : 0);
+        if (k >= 2) cone(gRm, 2 * x, (k >> 1) - 1, A(0.5) * arc<P>(pl, n, k - 1), A(0.5), rq, Rn, x + 1, k - 1);
+        if (k < s) cone(gRm, 2 * x, k >> 1, A(0.5) * arc<P>(pl, n, k), A(0.5), rq, Rn, x + 1, k);
     }
-    GTLevel<P, C>(pl, q, n).store(x, k, v, gL, gT);
+    GTLevel<P, C> gTn(pl, q, n);
+#pragma unroll
+    for (int l = 0; l < E; ++l)
+        if (v + l < g.Vs) gTn.store(x, k, v + l, gL[l], gT[l]);
 }
 
 // ---------------------------------------------------------------------------
@@ -195,42 +227,50 @@ __global__ void __launch_bounds__(256) k_adj_T(Plan pl, RowSplitB rs, int n) {
 //    k = 2 kap at v = w - (2 kap - h) (near dir kap, weight 1),
 //    k = 2 kap + 1 at v = w - (2 kap + 2 - h) (F_+, near dir kap + 1, 1/2),
 //    k = 2 kap - 1 at v = w - (2 kap - 2 - h) (F_-, near dir kap - 1, 1/2)
+// Two consecutive w per thread (all offsets are even for n >= 3).
 // ---------------------------------------------------------------------------
 template <int P, int C>
 __global__ void __launch_bounds__(256) k_adj_merge_up(Plan pl, RowSplitB rs, int n) {
     using A = typename Prec<P>::A;
+    constexpr int E = 2;
     int local;
     const int q = quadrant_of(rs, blockIdx.x, local);   // row = (q, x', kap) at level n-1
     const QuadGeom &g = pl.q[q];
-    const int w = blockIdx.y * blockDim.x + threadIdx.x;
+    const int w = E * (blockIdx.y * blockDim.x + threadIdx.x);
     if (w >= g.V) return;
     const int m = n - 1, h = 1 << m;
     const int Km = h + 1;
     const int x1 = local / Km, kap = local - x1 * Km;
     TLevel<P, C> Tm(pl, q, m);
     GTLevel<P, C> gTm(pl, q, m), gTn(pl, q, n);
-    A aL[C], aT;
-    gTm.load(x1, kap, w, aL, aT);
+    A aL[E][C], aT[E];
+#pragma unroll
+    for (int l = 0; l < E; ++l) gTm.load(x1, kap, w + l, aL[l], aT[l]);
     if (!(x1 & 1)) {
         const int x = x1 >> 1, xf = x1 + 1;
         const int vf = w + 2 * kap - h;
-        const bool fok = xf < g.Un[m] && vf >= 0 && vf < g.V;
+        const bool xok = xf < g.Un[m];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             const int kout = t == 0 ? 2 * kap : (t == 1 ? 2 * kap + 1 : 2 * kap - 1);
             const int fdir = t == 0 ? kap : (t == 1 ? kap + 1 : kap - 1);
             if (kout < 0 || kout > 2 * h) continue;
             const A wgt = t == 0 ? A(1) : A(0.5);
-            A gL[C], gT;
-            gTn.load(x, kout, w, gL, gT);
-            const Iv<P, C> fr = fok ? Tm.load(xf, fdir, vf) : Iv<P, C>::vacuum();
-            A dT = gT * fr.trans();
+            Iv<P, C> fr[E];
+            if (xok) Tm.load2_masked(xf, fdir, vf, g.V, fr[0], fr[1]);
+            else fr[0] = fr[1] = Iv<P, C>::vacuum();
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                aL[c] = fma(wgt, gL[c], aL[c]);
-                dT = fma(gL[c], fr.L[c], dT);
+            for (int l = 0; l < E; ++l) {
+                A gL[C], gT;
+                gTn.load(x, kout, w + l, gL, gT);
+                A dT = gT * fr[l].trans();
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    aL[l][c] = fma(wgt, gL[c], aL[l][c]);
+                    dT = fma(gL[c], fr[l].L[c], dT);
+                }
+                aT[l] = fma(wgt, dT, aT[l]);
             }
-            aT = fma(wgt, dT, aT);
         }
     } else {
         const int x = (x1 - 1) >> 1, xn = x1 - 1;
@@ -240,17 +280,24 @@ __global__ void __launch_bounds__(256) k_adj_merge_up(Plan pl, RowSplitB rs, int
             const int ndir = t == 0 ? kap : (t == 1 ? kap + 1 : kap - 1);
             if (kout < 0 || kout > 2 * h) continue;
             const int v = w - (2 * ndir - h);
-            if (v < 0 || v >= g.V) continue;
             const A wgt = t == 0 ? A(1) : A(0.5);
-            A gL[C], gT;
-            gTn.load(x, kout, v, gL, gT);
-            const A tn = wgt * Tm.load(xn, ndir, v).trans();
+            if (v < 0 || v >= g.V) continue;          // v even: then v + 1 may still be in range
+            Iv<P, C> nr[E];
+            Tm.load2(xn, ndir, v, nr[0], nr[1]);
 #pragma unroll
-            for (int c = 0; c < C; ++c) aL[c] = fma(tn, gL[c], aL[c]);
-            aT = fma(tn, gT, aT);
+            for (int l = 0; l < E; ++l) {
+                if (v + l >= g.V) continue;
+                A gL[C], gT;
+                gTn.load(x, kout, v + l, gL, gT);
+                const A tn = wgt * nr[l].trans();
+#pragma unroll
+                for (int c = 0; c < C; ++c) aL[l][c] = fma(tn, gL[c], aL[l][c]);
+                aT[l] = fma(tn, gT, aT[l]);
+            }
         }
     }
-    gTm.store(x1, kap, w, aL, aT);
+#pragma unroll
+    for (int l = 0; l < E; ++l) gTm.store(x1, kap, w + l, aL[l], aT[l]);
 }
 
 // ---------------------------------------------------------------------------
@@ -259,49 +306,139 @@ __global__ void __launch_bounds__(256) k_adj_merge_up(Plan pl, RowSplitB rs, int
 //   L = sum_m P_m e_m w_m,  P_m = prod_{m'<m} t_m',  T = prod_m t_m.
 // For upstream (gL, gT):
 //   dL/de_j     = gL P_j w_j
-//   dL/dsigma_j = sum_c gL_c (P_j e_jc l_j^2 phi'(sigma_j l_j) - l_j S_jc) - gT l_j T,
-//   S_j = sum_{m>j} P_m e_m w_m.
-// Each tile pixel gathers, for every quadrant, ray shape and piece index j,
-// the one ray that crosses it as its piece j (probe = pixel - offset_j).
+//   dL/dsigma_j = sum_c gL_c (P_j e_jc dw_j/dsigma - l_j S_jc) - gT l_j T,
+//   S_j = sum_{m>j} P_m e_m w_m,   dw/dsigma = l^2 phi'(sigma l).
+// Each tile pixel gathers, for every quadrant, ray shape R and piece index
+// J, the one ray that crosses it as its piece J (probe = pixel - offset_J),
+// and re-traces that ray from the staged tile (shapes unrolled at compile
+// time, per-pixel piece factors from the tile, as in the forward trace).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float dphi_l2(float sg, float len, float tp) {
-    // l^2 phi'(sigma l), phi'(t) = (e^-t (1 + t) - 1) / t^2
+
+// dw/dsigma of a half piece of length l with t = exp(-sigma l):
+// l^2 phi'(sigma l), phi'(x) = (e^-x (1 + x) - 1) / x^2, by its Taylor
+// series near 0.
+__device__ __forceinline__ float dw_dsigma(float sg, float len, float t) {
     const float tau = sg * len;
     const float series = len * len * (-0.5f + tau * (1.f / 3.f + tau * (-1.f / 8.f + tau * (1.f / 30.f))));
-    return fabsf(tau) < 0.05f ? series : (tp * (1.f + tau) - 1.f) / (sg * sg);
+    return fabsf(tau) < 0.05f ? series : (t * (1.f + tau) - 1.f) / (sg * sg);
 }
-__device__ __forceinline__ double dphi_l2(double sg, double len, double tp) {
+__device__ __forceinline__ double dw_dsigma(double sg, double len, double t) {
     const double tau = sg * len;
     if (fabs(tau) < 1e-2)
         return len * len * (-0.5 + tau * (1.0 / 3.0 + tau * (-1.0 / 8.0 + tau * (1.0 / 30.0 + tau * (-1.0 / 144.0 + tau * (1.0 / 840.0))))));
-    return (tp * (1.0 + tau) - 1.0) / (sg * sg);
-}
-
-__device__ __forceinline__ float piece_b(float sg, float len, float &tp) {
-    const float tau = sg * len;
-    tp = __expf(-tau);
-    const float series = len * (1.f - tau * (0.5f - tau * (1.f / 6.f - tau * (1.f / 24.f))));
-    return fabsf(tau) < 0.03f ? series : (1.f - tp) / sg;
-}
-__device__ __forceinline__ double piece_b(double sg, double len, double &tp) {
-    const double tau = sg * len;
-    const double m = expm1(-tau);
-    tp = 1.0 + m;
-    return sg != 0.0 ? -m / sg : len;
+    return (t * (1.0 + tau) - 1.0) / (sg * sg);
 }
 
 constexpr int TB_TILE = 32, TB_HALO = 4, TB_REG = TB_TILE + 2 * TB_HALO, TB_PITCH = TB_REG + 1;
+constexpr int TB_PLANE = TB_REG * TB_PITCH;
+constexpr int TB_AP = TB_TILE + 1;
+
+template <class A, int C> struct AdjTile {
+    A *s, *t, *w, *e, *acc;     // s [PLANE], t/w [3][PLANE], e [C][PLANE], acc [C+1][TILE][TILE+1]
+    __device__ __forceinline__ explicit AdjTile(unsigned char *smem) {
+        s = reinterpret_cast<A *>(smem);
+        t = s + TB_PLANE;
+        w = t + 3 * TB_PLANE;
+        e = w + 3 * TB_PLANE;
+        acc = e + C * TB_PLANE;
+    }
+    static constexpr size_t bytes() { return sizeof(A) * ((7 + C) * TB_PLANE + (C + 1) * TB_TILE * TB_AP); }
+};
+
+template <class A> __device__ __forceinline__ void piece_factors_b(A sg, A len, A &t, A &w) {
+    const A m = fexpm1(-sg * len);
+    t = A(1) + m;
+    w = sg != A(0) ? -m / sg : len;
+}
+
+// Re-trace pieces M .. END-1 of a ray; piece J is the one at the gathering
+// pixel.  Accumulates the attenuated radiance of all pieces (Ltot) and of
+// pieces <= J (Lle), and records P_J, the piece factors of J and e_J.
+template <class A, int C, int M, int END, int J>
+__device__ __forceinline__ void adj_retrace(const AdjTile<A, C> &tt, int base, int su, int sv, A &Pp, A (&Ltot)[C],
+                                            A (&Lle)[C], A &Pj, A &tj, A &wj, A &sj, A (&ej)[C]) {
+    if constexpr (M < END) {
+        using pc = PieceAt<M>;
+        const int o = base + pc::du * su + pc::dv * sv;
+        A t = tt.t[pc::cls * TB_PLANE + o];
+        A w = tt.w[pc::cls * TB_PLANE + o];
+        if constexpr (M == J) {
+            tj = t;           // half-piece factors of the pixel's own piece
+            wj = w;
+            sj = tt.s[o];
+            Pj = Pp;
+        }
+        if constexpr (pc::full != 0) {
+            w = w * (A(1) + t);
+            t = t * t;
+        }
+        const A pw = Pp * w;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const A em = tt.e[c * TB_PLANE + o];
+            Ltot[c] = fma(pw, em, Ltot[c]);
+            if constexpr (M <= J) Lle[c] = fma(pw, em, Lle[c]);
+            if constexpr (M == J) ej[c] = em;
+        }
+        Pp *= t;
+        adj_retrace<A, C, M + 1, END, J>(tt, base, su, sv, Pp, Ltot, Lle, Pj, tj, wj, sj, ej);
+    }
+}
+
+template <int P, int C, int R, int J>
+__device__ __forceinline__ void adj_gather(const Plan &pl, const AdjTile<typename Prec<P>::A, C> &tt, int q, int nmax,
+                                           int V, int us, int vs, int base, int su, int sv,
+                                           typename Prec<P>::A (&dE)[C], typename Prec<P>::A &dS) {
+    using A = typename Prec<P>::A;
+    using ray = RayAt<R>;
+    if constexpr (J < ray::end) {
+        using pc = PieceAt<J>;
+        const int up = us - pc::du, vp = vs - pc::dv;
+        if (ray::n <= nmax && up >= 0 && !(up & ((1 << ray::n) - 1)) && vp >= 0 && vp < V) {
+            A gL[C], gT;
+            GTLevel<P, C>(pl, q, ray::n).load(up >> ray::n, ray::k, vp, gL, gT);
+            const int pbase = base - pc::du * su - pc::dv * sv;
+            A Pp = A(1), Pj = A(0), tj = A(1), wj = A(0), sj = A(0);
+            A Ltot[C], Lle[C], ej[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) { Ltot[c] = A(0); Lle[c] = A(0); ej[c] = A(0); }
+            adj_retrace<A, C, ray::begin, ray::end, J>(tt, pbase, su, sv, Pp, Ltot, Lle, Pj, tj, wj, sj, ej);
+            const A lh = class_len<A>(pc::cls);
+            A d = dw_dsigma(sj, lh, tj);
+            A wq = wj, len = lh;
+            if constexpr (pc::full != 0) {            // w2 = w (1 + t), dw2 = d (1 + t) - l t w
+                d = fma(d, A(1) + tj, -lh * tj * wj);
+                wq = wj * (A(1) + tj);
+                len = A(2) * lh;
+            }
+            A g = -gT * len * Pp;                     // Pp is now the ray's total T
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                dE[c] = fma(gL[c], Pj * wq, dE[c]);
+                g = fma(gL[c], Pj * ej[c] * d - len * (Ltot[c] - Lle[c]), g);
+            }
+            dS += g;
+        }
+        adj_gather<P, C, R, J + 1>(pl, tt, q, nmax, V, us, vs, base, su, sv, dE, dS);
+    }
+}
+
+template <int P, int C, int R>
+__device__ __forceinline__ void adj_ray(const Plan &pl, const AdjTile<typename Prec<P>::A, C> &tt, int q, int nmax,
+                                        int V, int us, int vs, int base, int su, int sv,
+                                        typename Prec<P>::A (&dE)[C], typename Prec<P>::A &dS) {
+    if constexpr (R < HRC_MAXRAY) {
+        if (RayAt<R>::n <= nmax) adj_gather<P, C, R, RayAt<R>::begin>(pl, tt, q, nmax, V, us, vs, base, su, sv, dE, dS);
+        adj_ray<P, C, R + 1>(pl, tt, q, nmax, V, us, vs, base, su, sv, dE, dS);
+    }
+}
 
 template <int P, int C, class IN>
-__global__ void __launch_bounds__(256) k_adj_trace(Plan pl, RayTable rt, const IN *__restrict__ e,
-                                                   const IN *__restrict__ s, IN *__restrict__ ge,
-                                                   IN *__restrict__ gs) {
+__global__ void __launch_bounds__(256) k_adj_trace(Plan pl, const IN *__restrict__ e, const IN *__restrict__ s,
+                                                   IN *__restrict__ ge, IN *__restrict__ gs) {
     using A = typename Prec<P>::A;
     extern __shared__ __align__(16) unsigned char tb_smem[];
-    A *sm_s = reinterpret_cast<A *>(tb_smem);                 // [TB_REG][TB_PITCH]
-    A *sm_e = sm_s + TB_REG * TB_PITCH;                        // [C][TB_REG][TB_PITCH]
-    A *acc = sm_e + C * TB_REG * TB_PITCH;                     // [C+1][TB_TILE][TB_TILE + 1]
-    constexpr int AP = TB_TILE + 1;
+    AdjTile<A, C> tt(tb_smem);
     const int W = pl.W, H = pl.H;
     const int x0 = blockIdx.x * TB_TILE, y0 = blockIdx.y * TB_TILE;
     const long long HW = (long long)W * H;
@@ -310,13 +447,22 @@ __global__ void __launch_bounds__(256) k_adj_trace(Plan pl, RayTable rt, const I
         const int x = x0 - TB_HALO + rx, y = y0 - TB_HALO + ry;
         const bool in = x >= 0 && x < W && y >= 0 && y < H;
         const long long pix = (long long)y * W + x;
-        sm_s[ry * TB_PITCH + rx] = in ? A(s[pix]) : A(0);
+        const int o = ry * TB_PITCH + rx;
+        const A sg = in ? A(s[pix]) : A(0);
+        tt.s[o] = sg;
 #pragma unroll
-        for (int c = 0; c < C; ++c) sm_e[(c * TB_REG + ry) * TB_PITCH + rx] = in ? A(e[c * HW + pix]) : A(0);
+        for (int c = 0; c < 3; ++c) {
+            A tc, wc;
+            piece_factors_b<A>(sg, class_len<A>(c), tc, wc);
+            tt.t[c * TB_PLANE + o] = tc;
+            tt.w[c * TB_PLANE + o] = wc;
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) tt.e[c * TB_PLANE + o] = in ? A(e[c * HW + pix]) : A(0);
     }
-    for (int i = threadIdx.x; i < (C + 1) * TB_TILE * AP; i += blockDim.x) acc[i] = A(0);
+    for (int i = threadIdx.x; i < (C + 1) * TB_TILE * TB_AP; i += blockDim.x) tt.acc[i] = A(0);
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = 0; q < 4; ++q) {
         const QuadGeom &g = pl.q[q];
         const int nmax = g.N < 2 ? g.N : 2;
@@ -324,65 +470,22 @@ __global__ void __launch_bounds__(256) k_adj_trace(Plan pl, RayTable rt, const I
         const int tu = xu ? x0 : y0, tv = xu ? y0 : x0;
         const int ext_u = xu ? W : H;
         const int sgn = (q == 0 || q == 2) ? 1 : -1;
+        const int su = sgn * (xu ? 1 : TB_PITCH), sv = xu ? TB_PITCH : 1;
         const int vs = tv + lane;
-        for (int c = warp; c < TB_TILE; c += nwarp) {
-            if (tu + c >= ext_u || vs >= g.V) continue;
+        for (int i = 0; i < TB_TILE / 8; ++i) {
+            const int c = 8 * i + ((warp + i) & 7);
+            if (g.N < 1 || tu + c >= ext_u || vs >= g.V) continue;
             const int us = (q == 0 || q == 2) ? tu + c : ext_u - 1 - (tu + c);
+            const int base = xu ? (TB_HALO + lane) * TB_PITCH + TB_HALO + c
+                                : (TB_HALO + c) * TB_PITCH + TB_HALO + lane;
             A dE[C], dS = A(0);
 #pragma unroll
             for (int cc = 0; cc < C; ++cc) dE[cc] = A(0);
-            for (int r = 0; r < HRC_MAXRAY; ++r) {
-                const int n = r < 2 ? 0 : (r < 5 ? 1 : 2);
-                if (n > nmax) break;
-                const int k = r - (n == 0 ? 0 : (n == 1 ? 2 : 5));
-                const int j0 = rt.start[r], j1 = rt.start[r + 1];
-                GTLevel<P, C> gT(pl, q, n);
-                for (int j = j0; j < j1; ++j) {
-                    const int up = us - rt.p[j].du, vp = vs - rt.p[j].dv;
-                    if (up < 0 || (up & ((1 << n) - 1)) || vp < 0 || vp >= g.V) continue;
-                    A gL[C], gTT;
-                    gT.load(up >> n, k, vp, gL, gTT);
-                    // re-trace the ray from probe (up, vp): tile coords of piece m are
-                    // (c - du_j + du_m, lane - dv_j + dv_m) along the (u, v) axes
-                    A Pp = A(1), Pj = A(0), wj = A(0), tj = A(1), sgj = A(0), lenj = A(0);
-                    A Ltot[C], Lle[C], ej[C];
-#pragma unroll
-                    for (int cc = 0; cc < C; ++cc) { Ltot[cc] = A(0); Lle[cc] = A(0); ej[cc] = A(0); }
-                    for (int mm = j0; mm < j1; ++mm) {
-                        const int a = TB_HALO + c + sgn * (rt.p[mm].du - rt.p[j].du);
-                        const int b = TB_HALO + lane + (rt.p[mm].dv - rt.p[j].dv);
-                        const int o = (xu ? b : a) * TB_PITCH + (xu ? a : b);
-                        const A len = (P == P_FP64) ? A(rt.lenD[mm]) : A(rt.p[mm].len);
-                        const A sg = sm_s[o];
-                        A tp;
-                        const A wgt = piece_b(sg, len, tp);
-                        const A pw = Pp * wgt;
-#pragma unroll
-                        for (int cc = 0; cc < C; ++cc) {
-                            const A em = sm_e[cc * TB_REG * TB_PITCH + o];
-                            Ltot[cc] = fma(pw, em, Ltot[cc]);
-                            if (mm <= j) Lle[cc] = fma(pw, em, Lle[cc]);
-                            if (mm == j) ej[cc] = em;
-                        }
-                        if (mm == j) { Pj = Pp; wj = wgt; tj = tp; sgj = sg; lenj = len; }
-                        Pp *= tp;
-                    }
-                    const A Ttot = Pp;
-                    const A dd = dphi_l2(sgj, lenj, tj);
-                    A gsig = -gTT * lenj * Ttot;
-#pragma unroll
-                    for (int cc = 0; cc < C; ++cc) {
-                        dE[cc] = fma(gL[cc], Pj * wj, dE[cc]);
-                        gsig = fma(gL[cc], Pj * ej[cc] * dd - lenj * (Ltot[cc] - Lle[cc]), gsig);
-                    }
-                    dS += gsig;
-                }
-            }
-            // image pixel of this frame pixel, relative to the tile
+            adj_ray<P, C, 0>(pl, tt, q, nmax, g.V, us, vs, base, su, sv, dE, dS);
             const int ix = xu ? c : lane, iy = xu ? lane : c;
 #pragma unroll
-            for (int cc = 0; cc < C; ++cc) acc[(cc * TB_TILE + iy) * AP + ix] += dE[cc];
-            acc[(C * TB_TILE + iy) * AP + ix] += dS;
+            for (int cc = 0; cc < C; ++cc) tt.acc[(cc * TB_TILE + iy) * TB_AP + ix] += dE[cc];
+            tt.acc[(C * TB_TILE + iy) * TB_AP + ix] += dS;
         }
         __syncthreads();
     }
@@ -392,8 +495,8 @@ __global__ void __launch_bounds__(256) k_adj_trace(Plan pl, RayTable rt, const I
         if (x >= W || y >= H) continue;
         const long long pix = (long long)y * W + x;
 #pragma unroll
-        for (int cc = 0; cc < C; ++cc) ge[cc * HW + pix] = IN(acc[(cc * TB_TILE + iy) * AP + ix]);
-        gs[pix] = IN(acc[(C * TB_TILE + iy) * AP + ix]);
+        for (int cc = 0; cc < C; ++cc) ge[cc * HW + pix] = IN(tt.acc[(cc * TB_TILE + iy) * TB_AP + ix]);
+        gs[pix] = IN(tt.acc[(C * TB_TILE + iy) * TB_AP + ix]);
     }
 }
 
@@ -450,15 +553,12 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
     cudaError_t err = launch_forward_levels(pl, rt, e, s, st, launches, rec);
     if (err != cudaSuccess) return err;
     {
-        RowSplitB rs = split_rows(pl, 0, 0);
-        if (rs.start[4] > 0) {
-            double by = img * pl.C * ab;
-            for (int q = 0; q < 4; ++q) by += gRbytes(q, 0);
-            rec->begin(K_ADJ_SUM, 0, by);
-            k_adj_sum<P, C, IN><<<dim3((unsigned)rs.start[4], vb), bs, 0, st>>>(pl, rs, (const IN *)gF);
-            rec->end();
-            ++*launches;
-        }
+        double by = img * pl.C * ab;
+        for (int q = 0; q < 4; ++q) by += gRbytes(q, 0);
+        rec->begin(K_ADJ_SUM, 0, by);
+        k_adj_sum<P, C, IN><<<dim3((pl.W + 31) / 32, (pl.H + 31) / 32), 256, 0, st>>>(pl, (const IN *)gF);
+        rec->end();
+        ++*launches;
     }
     for (int n = 0; n + 1 < Nmax; ++n) {
         RowSplitB rs = split_rows(pl, 1, n);
@@ -469,7 +569,8 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                 by += gRbytes(q, n) + gRbytes(q, n + 1) + bytes_T(pl, q, n) / (pl.C + 1) / 2 +
                       bytes_T(pl, q, n + 1) / (pl.C + 1) / 2;
         rec->begin(K_ADJ_MERGE_DOWN, n, by);
-        k_adj_R<P, C><<<dim3((unsigned)rs.start[4], vb), bs, 0, st>>>(pl, rs, n);
+        if (n >= 1) k_adj_R<P, C, 2><<<dim3((unsigned)rs.start[4], vb), bs / 2, 0, st>>>(pl, rs, n);
+        else k_adj_R<P, C, 1><<<dim3((unsigned)rs.start[4], vb), bs, 0, st>>>(pl, rs, n);
         rec->end();
         ++*launches;
     }
@@ -481,7 +582,8 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             if (pl.q[q].N >= 1 && n <= pl.q[q].N)
                 by += gTbytes(q, n) + gRbytes(q, n) + gRbytes(q, n - 1) + bytes_R(pl, q, n) + bytes_R(pl, q, n + 1);
         rec->begin(K_ADJ_MERGE_DOWN, n, by);
-        k_adj_T<P, C><<<dim3((unsigned)rs.start[4], vb), bs, 0, st>>>(pl, rs, n);
+        if (n >= 1) k_adj_T<P, C, 2><<<dim3((unsigned)rs.start[4], vb), bs / 2, 0, st>>>(pl, rs, n);
+        else k_adj_T<P, C, 1><<<dim3((unsigned)rs.start[4], vb), bs, 0, st>>>(pl, rs, n);
         rec->end();
         ++*launches;
     }
@@ -492,24 +594,19 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         for (int q = 0; q < 4; ++q)
             if (n <= pl.q[q].N) by += 2 * gTbytes(q, n - 1) + gTbytes(q, n) + bytes_T(pl, q, n - 1);
         rec->begin(K_ADJ_MERGE_UP, n, by);
-        k_adj_merge_up<P, C><<<dim3((unsigned)rs.start[4], vb), bs, 0, st>>>(pl, rs, n);
+        k_adj_merge_up<P, C><<<dim3((unsigned)rs.start[4], vb), bs / 2, 0, st>>>(pl, rs, n);
         rec->end();
         ++*launches;
     }
     {
         using A = typename Prec<P>::A;
-        const size_t smem = sizeof(A) * ((C + 1) * TB_REG * TB_PITCH + (C + 1) * TB_TILE * (TB_TILE + 1));
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_adj_trace<P, C, IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set = true;
-        }
+        const size_t smem = AdjTile<A, C>::bytes();
         double by = img * (pl.C + 1) * ab * 2;
         for (int q = 0; q < 4; ++q)
             for (int n = 0; n <= 2; ++n) by += gTbytes(q, n);
         dim3 grid((pl.W + TB_TILE - 1) / TB_TILE, (pl.H + TB_TILE - 1) / TB_TILE);
         rec->begin(K_ADJ_TRACE, 0, by);
-        k_adj_trace<P, C, IN><<<grid, 256, smem, st>>>(pl, rt, (const IN *)e, (const IN *)s, (IN *)ge, (IN *)gs);
+        k_adj_trace<P, C, IN><<<grid, 256, smem, st>>>(pl, (const IN *)e, (const IN *)s, (IN *)ge, (IN *)gs);
         rec->end();
         ++*launches;
     }
@@ -525,6 +622,29 @@ static cudaError_t bwd_prec(const Plan &pl, const RayTable &rt, const void *e, c
     case 3: return bwd_impl<P, 3>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
     default: return bwd_impl<P, 4>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
     }
+}
+
+template <int P>
+static cudaError_t prepare_bwd_prec() {
+    using IN = typename std::conditional<P == P_FP64, double, float>::type;
+    using A = typename Prec<P>::A;
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *fn, size_t bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    set((const void *)k_adj_trace<P, 1, IN>, AdjTile<A, 1>::bytes());
+    set((const void *)k_adj_trace<P, 2, IN>, AdjTile<A, 2>::bytes());
+    set((const void *)k_adj_trace<P, 3, IN>, AdjTile<A, 3>::bytes());
+    set((const void *)k_adj_trace<P, 4, IN>, AdjTile<A, 4>::bytes());
+    return e;
+}
+
+cudaError_t prepare_backward_kernels() {
+    cudaError_t e = prepare_bwd_prec<P_FP32>();
+    if (e == cudaSuccess) e = prepare_bwd_prec<P_FP16>();
+    if (e == cudaSuccess) e = prepare_bwd_prec<P_BF16>();
+    if (e == cudaSuccess) e = prepare_bwd_prec<P_FP64>();
+    return e;
 }
 
 cudaError_t launch_backward(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,

@@ -14,6 +14,7 @@
 // leaves the grid never re-enters, and nothing outside the grid emits.
 #include "hrc_internal.cuh"
 #include "launch.h"
+#include "trace_shapes.cuh"
 
 namespace hrc {
 
@@ -32,106 +33,158 @@ __device__ __forceinline__ int find_quadrant(const RowSplit &rs, long long r, in
     return q;
 }
 
-// Piece weights of a uniform pixel crossed over length len (Eq. 4 over one
-// piece): returns w = len * phi(sigma len) and sets tp = exp(-sigma len).
-__device__ __forceinline__ float piece(float sg, float len, float &tp) {
-    const float tau = sg * len;
-    tp = __expf(-tau);
-    // len * phi(tau): (1 - e^-tau) / sigma away from 0, a short Taylor series near 0
-    const float series = len * (1.f - tau * (0.5f - tau * (1.f / 6.f - tau * (1.f / 24.f))));
-    return fabsf(tau) < 0.03f ? series : (1.f - tp) / sg;
-}
-__device__ __forceinline__ double piece(double sg, double len, double &tp) {
-    const double tau = sg * len;
-    const double m = expm1(-tau);
-    tp = 1.0 + m;
-    return sg != 0.0 ? -m / sg : len;
+// Per-pixel piece factors of the three ray classes (trace_shapes.cuh): for
+// the half length l of class c, t = exp(-sigma l) and w = l phi(sigma l) =
+// (1 - e^{-sigma l}) / sigma, the radiance weight of Eq. 4 over a uniform
+// piece.  Full pieces use t^2 and w (1 + t).
+template <class A> __device__ __forceinline__ void piece_factors(A sg, A len, A &t, A &w) {
+    const A m = fexpm1(-sg * len);
+    t = A(1) + m;
+    w = sg != A(0) ? -m / sg : len;
 }
 
-// T_0..T_min(2,N) of all four quadrant frames for one 32 x 32 image tile.
-// The tile's extinction and emission plus a 4-pixel halo (the longest
-// directly traced ray, v_2(k), reaches 4 pixels along and across) are
-// staged once in shared memory, zero outside the image (= vacuum, exact).
-// Work rows are (column c of the tile along the frame's u axis, ray r):
-// each warp traces one row for 32 consecutive v, so its T stores are
-// 128-byte coalesced row segments in every frame.
+// Shared-memory tile of a 32 x 32 image block with a 4-pixel halo (the
+// longest directly traced ray, v_2(k), reaches 4 pixels along and across):
+// extinction, the piece factors of the three classes, and the emission.
+// Outside the image every field is vacuum (sigma = e = 0, t = 1, w = l).
 constexpr int TR_TILE = 32, TR_HALO = 4, TR_REG = TR_TILE + 2 * TR_HALO, TR_PITCH = TR_REG + 1;
+constexpr int TR_PLANE = TR_REG * TR_PITCH;
 
+template <class A, int C> struct TraceTile {
+    A *s;       // [PLANE]
+    A *t;       // [3][PLANE]
+    A *w;       // [3][PLANE]
+    A *e;       // [C][PLANE]
+    __device__ __forceinline__ explicit TraceTile(unsigned char *smem) {
+        s = reinterpret_cast<A *>(smem);
+        t = s + TR_PLANE;
+        w = t + 3 * TR_PLANE;
+        e = w + 3 * TR_PLANE;
+    }
+    static constexpr size_t bytes() { return sizeof(A) * (7 + C) * TR_PLANE; }
+    template <class IN>
+    __device__ __forceinline__ void stage(int W, int H, int x0, int y0, const IN *__restrict__ ein,
+                                          const IN *__restrict__ sin) {
+        const long long HW = (long long)W * H;
+        for (int i = threadIdx.x; i < TR_REG * TR_REG; i += blockDim.x) {
+            const int ry = i / TR_REG, rx = i - ry * TR_REG;
+            const int x = x0 - TR_HALO + rx, y = y0 - TR_HALO + ry;
+            const bool in = x >= 0 && x < W && y >= 0 && y < H;
+            const long long pix = (long long)y * W + x;
+            const int o = ry * TR_PITCH + rx;
+            const A sg = in ? A(sin[pix]) : A(0);
+            s[o] = sg;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                A tc, wc;
+                piece_factors<A>(sg, class_len<A>(c), tc, wc);
+                t[c * TR_PLANE + o] = tc;
+                w[c * TR_PLANE + o] = wc;
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) e[c * TR_PLANE + o] = in ? A(ein[c * HW + pix]) : A(0);
+        }
+    }
+};
+
+// Trace of ray shape R from the probe whose tile offset is `base`; su / sv
+// are the tile strides along the frame's u and v axes.  Pieces J .. END-1
+// are unrolled at compile time.
+template <int P, int C, int J, int END>
+__device__ __forceinline__ void trace_pieces(const TraceTile<typename Prec<P>::A, C> &tt, int base, int su, int sv,
+                                             typename Prec<P>::A (&L)[C], typename Prec<P>::A &Tacc,
+                                             typename Prec<P>::A &tau) {
+    using A = typename Prec<P>::A;
+    if constexpr (J < END) {
+        using pc = PieceAt<J>;
+        const int o = base + pc::du * su + pc::dv * sv;
+        A t = tt.t[pc::cls * TR_PLANE + o];
+        A w = tt.w[pc::cls * TR_PLANE + o];
+        if constexpr (pc::full != 0) {
+            w = w * (A(1) + t);
+            t = t * t;
+        }
+        const A wt = Tacc * w;
+#pragma unroll
+        for (int c = 0; c < C; ++c) L[c] = fma(wt, tt.e[c * TR_PLANE + o], L[c]);
+        Tacc *= t;
+        if constexpr (Prec<P>::LOG) tau = fma(tt.s[o], A(pc::full ? 2 : 1) * class_len<A>(pc::cls), tau);
+        trace_pieces<P, C, J + 1, END>(tt, base, su, sv, L, Tacc, tau);
+    }
+}
+
+template <int P, int C, int R>
+__device__ __forceinline__ void trace_store(const Plan &pl, const TraceTile<typename Prec<P>::A, C> &tt, int q,
+                                            int nmax, int u, int v, int base, int su, int sv) {
+    using A = typename Prec<P>::A;
+    using ray = RayAt<R>;
+    if (ray::n > nmax || (u & ((1 << ray::n) - 1))) return;
+    Iv<P, C> iv;
+#pragma unroll
+    for (int c = 0; c < C; ++c) iv.L[c] = A(0);
+    A Tacc = A(1), tau = A(0);
+    trace_pieces<P, C, ray::begin, ray::end>(tt, base, su, sv, iv.L, Tacc, tau);
+    iv.t = Prec<P>::LOG ? tau : Tacc;
+    TLevel<P, C>(pl, q, ray::n).store(u >> ray::n, ray::k, v, iv);
+}
+
+// T_0..T_min(2,N) of the selected quadrant frames for one 32 x 32 image
+// tile.  Warp w handles tile columns c = 8i + ((w + i) mod 8) along the
+// frame's u axis (one column of every residue mod 4, so the warps get equal
+// shares of the level-1 and level-2 probes); its lanes run along v, so every
+// T store is a 128-byte coalesced row segment in every frame.
 template <int P, int C>
 __global__ void __launch_bounds__(256) k_trace012(Plan pl, RayTable rt, const float *__restrict__ e,
                                                   const float *__restrict__ s, const double *__restrict__ ed,
-                                                  const double *__restrict__ sd) {
+                                                  const double *__restrict__ sd, int qmask) {
     using A = typename Prec<P>::A;
     extern __shared__ __align__(16) unsigned char tr_smem[];
-    A *sm_s = reinterpret_cast<A *>(tr_smem);                 // [TR_REG][TR_PITCH]
-    A *sm_e = sm_s + TR_REG * TR_PITCH;                        // [C][TR_REG][TR_PITCH]
+    TraceTile<A, C> tt(tr_smem);
     const int W = pl.W, H = pl.H;
     const int x0 = blockIdx.x * TR_TILE, y0 = blockIdx.y * TR_TILE;
-    const long long HW = (long long)W * H;
-    for (int i = threadIdx.x; i < TR_REG * TR_REG; i += blockDim.x) {
-        const int ry = i / TR_REG, rx = i - ry * TR_REG;
-        const int x = x0 - TR_HALO + rx, y = y0 - TR_HALO + ry;
-        const bool in = x >= 0 && x < W && y >= 0 && y < H;
-        const long long pix = (long long)y * W + x;
-        sm_s[ry * TR_PITCH + rx] = in ? ((P == P_FP64) ? A(sd[pix]) : A(s[pix])) : A(0);
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-            sm_e[(c * TR_REG + ry) * TR_PITCH + rx] = in ? ((P == P_FP64) ? A(ed[c * HW + pix]) : A(e[c * HW + pix])) : A(0);
-    }
+    if (P == P_FP64) tt.stage(W, H, x0, y0, ed, sd);
+    else tt.stage(W, H, x0, y0, e, s);
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = 0; q < 4; ++q) {
+        if (!((qmask >> q) & 1)) continue;
         const QuadGeom &g = pl.q[q];
         const int nmax = g.N < 2 ? g.N : 2;
         const bool xu = q < 2;                              // frame u runs along image x
         const int tu = xu ? x0 : y0, tv = xu ? y0 : x0;     // tile origin along u / v axes
         const int ext_u = xu ? W : H;
         const int v = tv + lane;
-        for (int row = warp; row < TR_TILE * HRC_MAXRAY; row += nwarp) {
-            const int c = row / HRC_MAXRAY, r = row - c * HRC_MAXRAY;
-            const int n = r < 2 ? 0 : (r < 5 ? 1 : 2);
-            const int k = r - (n == 0 ? 0 : (n == 1 ? 2 : 5));
-            if (n > nmax || tu + c >= ext_u) continue;
+        const int sgn = (q == 0 || q == 2) ? 1 : -1;        // image step along u
+        const int su = sgn * (xu ? 1 : TR_PITCH), sv = xu ? TR_PITCH : 1;
+        for (int i = 0; i < TR_TILE / 8; ++i) {
+            const int c = 8 * i + ((warp + i) & 7);
+            if (tu + c >= ext_u || v >= g.V) continue;
             const int u = (q == 0 || q == 2) ? tu + c : ext_u - 1 - (tu + c);
-            if (u & ((1 << n) - 1)) continue;
-            if (v >= g.V) continue;
-            A L[C];
-#pragma unroll
-            for (int cc = 0; cc < C; ++cc) L[cc] = A(0);
-            A Tacc = A(1), tau = A(0);
-            const int sgn = (q == 0 || q == 2) ? 1 : -1;     // image step along u
-            for (int j = rt.start[r]; j < rt.start[r + 1]; ++j) {
-                const int du = rt.p[j].du, dv = rt.p[j].dv;
-                const int a = TR_HALO + c + sgn * du, b = TR_HALO + lane + dv;   // tile coords (u axis, v axis)
-                const int sx = xu ? a : b, sy = xu ? b : a;
-                const int o = sy * TR_PITCH + sx;
-                const A len = (P == P_FP64) ? A(rt.lenD[j]) : A(rt.p[j].len);
-                const A sg = sm_s[o];
-                A tp;
-                const A w = piece(sg, len, tp);
-                const A wt = Tacc * w;
-#pragma unroll
-                for (int cc = 0; cc < C; ++cc) L[cc] = fma(wt, sm_e[cc * TR_REG * TR_PITCH + o], L[cc]);
-                Tacc *= tp;
-                tau += sg * len;
-            }
-            Iv<P, C> iv;
-#pragma unroll
-            for (int cc = 0; cc < C; ++cc) iv.L[cc] = L[cc];
-            iv.t = Prec<P>::LOG ? tau : Tacc;
-            TLevel<P, C>(pl, q, n).store(u >> n, k, v, iv);
+            const int base = xu ? (TR_HALO + lane) * TR_PITCH + TR_HALO + c
+                                : (TR_HALO + c) * TR_PITCH + TR_HALO + lane;
+            trace_store<P, C, 0>(pl, tt, q, nmax, u, v, base, su, sv);
+            trace_store<P, C, 1>(pl, tt, q, nmax, u, v, base, su, sv);
+            trace_store<P, C, 2>(pl, tt, q, nmax, u, v, base, su, sv);
+            trace_store<P, C, 3>(pl, tt, q, nmax, u, v, base, su, sv);
+            trace_store<P, C, 4>(pl, tt, q, nmax, u, v, base, su, sv);
+            trace_store<P, C, 5>(pl, tt, q, nmax, u, v, base, su, sv);
+            trace_store<P, C, 6>(pl, tt, q, nmax, u, v, base, su, sv);
+            trace_store<P, C, 7>(pl, tt, q, nmax, u, v, base, su, sv);
+            trace_store<P, C, 8>(pl, tt, q, nmax, u, v, base, su, sv);
+            trace_store<P, C, 9>(pl, tt, q, nmax, u, v, base, su, sv);
         }
     }
 }
 
 // T_n(p, k) from T_{n-1}; p = (x 2^n, v).  Near operand at column 2x, far
-// operand at column 2x + 1 shifted by 2k' - 2^{n-1} along v.
+// operand at column 2x + 1 shifted by 2k' - 2^{n-1} along v (even for n >= 3,
+// so every thread handles the aligned pair v, v+1 with 2-wide accesses).
 template <int P, int C>
-__global__ void __launch_bounds__(256) k_merge_up(Plan pl, RowSplit rs, int n) {
+__global__ void __launch_bounds__(128) k_merge_up(Plan pl, RowSplit rs, int n) {
     int local;
     const int q = find_quadrant(rs, blockIdx.x, local);   // row = (q, x, k)
     const QuadGeom &g = pl.q[q];
-    const int v = blockIdx.y * blockDim.x + threadIdx.x;
+    const int v = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
     if (v >= g.V) return;
     const int K = (1 << n) + 1;
     const int x = local / K, k = local - x * K;
@@ -139,40 +192,71 @@ __global__ void __launch_bounds__(256) k_merge_up(Plan pl, RowSplit rs, int n) {
     TLevel<P, C> Tm(pl, q, m), Tn(pl, q, n);
     const int xn = 2 * x, xf = 2 * x + 1;
     const bool far_ok = xf < g.Un[m];
-    auto far = [&](int kk, int vv) {
-        return (far_ok && vv >= 0 && vv < g.V) ? Tm.load(xf, kk, vv) : Iv<P, C>::vacuum();
-    };
-    Iv<P, C> out;
+    Iv<P, C> o0, o1;
     if ((k & 1) == 0) {                             // Eq. 18
         const int kk = k >> 1;
-        out = merge<P, C>(Tm.load(xn, kk, v), far(kk, v + 2 * kk - sm));
+        Iv<P, C> n0, n1, f0, f1;
+        Tm.load2(xn, kk, v, n0, n1);
+        if (far_ok) Tm.load2_masked(xf, kk, v + 2 * kk - sm, g.V, f0, f1);
+        else f0 = f1 = Iv<P, C>::vacuum();
+        o0 = merge<P, C>(n0, f0);
+        o1 = merge<P, C>(n1, f1);
     } else {                                        // Eqs. 19-20
         const int kp = (k + 1) >> 1, km = (k - 1) >> 1;
-        Iv<P, C> Fp = merge<P, C>(Tm.load(xn, kp, v), far(km, v + 2 * kp - sm));
-        Iv<P, C> Fm = merge<P, C>(Tm.load(xn, km, v), far(kp, v + 2 * km - sm));
-        out = blend<P, C>(Fm, Fp);
+        Iv<P, C> np0, np1, nm0, nm1, fp0, fp1, fm0, fm1;
+        Tm.load2(xn, kp, v, np0, np1);
+        Tm.load2(xn, km, v, nm0, nm1);
+        if (far_ok) {
+            Tm.load2_masked(xf, km, v + 2 * kp - sm, g.V, fp0, fp1);
+            Tm.load2_masked(xf, kp, v + 2 * km - sm, g.V, fm0, fm1);
+        } else {
+            fp0 = fp1 = fm0 = fm1 = Iv<P, C>::vacuum();
+        }
+        o0 = blend<P, C>(merge<P, C>(nm0, fm0), merge<P, C>(np0, fp0));
+        o1 = blend<P, C>(merge<P, C>(nm1, fm1), merge<P, C>(np1, fp1));
     }
-    Tn.store(x, k, v, out);
+    Tn.store2(x, k, v, o0, o1);
 }
 
 // R_n(p, i) = F_+ + F_-, p = (x 2^n, v), i = ip + 1/2, j_+ = 2ip+1, j_- = 2ip.
-template <int P, int C>
+// PAIR: two consecutive v per thread (all neighbour offsets even: n >= 1).
+template <int P, int C, bool PAIR>
 __global__ void __launch_bounds__(256) k_merge_down(Plan pl, RowSplit rs, int n) {
     using A = typename Prec<P>::A;
+    constexpr int E = PAIR ? 2 : 1;
     int local;
     const int q = find_quadrant(rs, blockIdx.x, local);   // row = (q, x, ip)
     const QuadGeom &g = pl.q[q];
-    const int v = blockIdx.y * blockDim.x + threadIdx.x;
+    const int v = E * (blockIdx.y * blockDim.x + threadIdx.x);
     if (v >= g.V) return;
     const int I = 1 << n;
     const int x = local >> n, ip = local & (I - 1);
     const bool top = (n + 1 >= g.N);               // R_N = 0
     const int s = 1 << n;
-    A acc[C];
+    A acc[E][C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = A(0);
+    for (int l = 0; l < E; ++l)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[l][c] = A(0);
     const A Ap = arc<P>(pl, n + 1, 2 * ip + 1), Am = arc<P>(pl, n + 1, 2 * ip);
     RLevel<P, C> Rn(pl, q, n);
+    // R_{n+1}(xr, j, vq .. vq+E-1), zero outside [0, V)
+    auto loadR = [&](const RLevel<P, C> &R1, int xr, int j, int c, int vq, A (&r)[E]) {
+        if (PAIR) {
+            if (vq >= 0 && vq < g.V) {
+                R1.load2(xr, j, c, vq, r[0], r[E - 1]);
+                if (vq + 1 >= g.V) r[E - 1] = A(0);
+            } else {
+                r[0] = r[E - 1] = A(0);
+            }
+        } else {
+            r[0] = (vq >= 0 && vq < g.V) ? R1.load(xr, j, c, vq) : A(0);
+        }
+    };
+    auto loadT = [&](const TLevel<P, C> &T, int xx, int kk, Iv<P, C> (&t)[E]) {
+        if (PAIR) T.load2(xx, kk, v, t[0], t[E - 1]);
+        else t[0] = T.load(xx, kk, v);
+    };
     if (x & 1) {
         // Eq. 14: F_+- = A_{n+1}(j) T_n(p, i +- 1/2).L + T_n(p, i +- 1/2).T R_{n+1}(p + v_n(i +- 1/2), j)
         TLevel<P, C> Tn(pl, q, n);
@@ -183,16 +267,19 @@ __global__ void __launch_bounds__(256) k_merge_down(Plan pl, RowSplit rs, int n)
             const int kk = sg == 0 ? ip + 1 : ip;
             const int j = sg == 0 ? 2 * ip + 1 : 2 * ip;
             const A Aj = sg == 0 ? Ap : Am;
-            const Iv<P, C> t = Tn.load(x, kk, v);
-            const A tr = t.trans();
+            Iv<P, C> t[E];
+            loadT(Tn, x, kk, t);
             const int vq = v + 2 * kk - s;
-            if (rq_ok && vq >= 0 && vq < g.V) {
-                RLevel<P, C> R1(pl, q, n + 1);
+            RLevel<P, C> R1(pl, q, rq_ok ? n + 1 : n);
 #pragma unroll
-                for (int c = 0; c < C; ++c) acc[c] += fma(Aj, t.L[c], tr * R1.load(xq, j, c, vq));
-            } else {
+            for (int c = 0; c < C; ++c) {
+                A r[E];
+                if (rq_ok) loadR(R1, xq, j, c, vq, r);
+                else
 #pragma unroll
-                for (int c = 0; c < C; ++c) acc[c] += Aj * t.L[c];
+                    for (int l = 0; l < E; ++l) r[l] = A(0);
+#pragma unroll
+                for (int l = 0; l < E; ++l) acc[l][c] += fma(Aj, t[l].L[c], t[l].trans() * r[l]);
             }
         }
     } else {
@@ -201,32 +288,37 @@ __global__ void __launch_bounds__(256) k_merge_down(Plan pl, RowSplit rs, int n)
         TLevel<P, C> T1(pl, q, n + 1);
         const int x2 = x >> 1;
         const int s1 = 2 * s;
+        const bool r1_ok = !top && x2 + 1 < g.Un[n + 1];
 #pragma unroll
         for (int sg = 0; sg < 2; ++sg) {
             const int kk = sg == 0 ? 2 * ip + 2 : 2 * ip;
             const int j = sg == 0 ? 2 * ip + 1 : 2 * ip;
             const A Aj = sg == 0 ? Ap : Am;
-            const Iv<P, C> t = T1.load(x2, kk, v);
-            const A tr = t.trans();
+            Iv<P, C> t[E];
+            loadT(T1, x2, kk, t);
             const int vq = v + 2 * kk - s1;
-            A r0[C], r1[C];
+            RLevel<P, C> R1(pl, q, top ? n : n + 1);
 #pragma unroll
-            for (int c = 0; c < C; ++c) { r0[c] = A(0); r1[c] = A(0); }
-            if (!top) {
-                RLevel<P, C> R1(pl, q, n + 1);
+            for (int c = 0; c < C; ++c) {
+                A r0[E], r1[E];
 #pragma unroll
-                for (int c = 0; c < C; ++c) r0[c] = R1.load(x2, j, c, v);
-                if (x2 + 1 < g.Un[n + 1] && vq >= 0 && vq < g.V) {
-#pragma unroll
-                    for (int c = 0; c < C; ++c) r1[c] = R1.load(x2 + 1, j, c, vq);
+                for (int l = 0; l < E; ++l) { r0[l] = A(0); r1[l] = A(0); }
+                if (!top) {
+                    if (PAIR) R1.load2(x2, j, c, v, r0[0], r0[E - 1]);
+                    else r0[0] = R1.load(x2, j, c, v);
+                    if (r1_ok) loadR(R1, x2 + 1, j, c, vq, r1);
                 }
-            }
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] += A(0.5) * (r0[c] + fma(Aj, t.L[c], tr * r1[c]));
+                for (int l = 0; l < E; ++l)
+                    acc[l][c] += A(0.5) * (r0[l] + fma(Aj, t[l].L[c], t[l].trans() * r1[l]));
+            }
         }
     }
 #pragma unroll
-    for (int c = 0; c < C; ++c) Rn.store(x, ip, c, v, acc[c]);
+    for (int c = 0; c < C; ++c) {
+        if (PAIR) Rn.store2(x, ip, c, v, acc[0][c], acc[E - 1][c]);
+        else Rn.store(x, ip, c, v, acc[0][c]);
+    }
 }
 
 // F[c][y][x] = sum_q R_0^q(u_q + 1, v_q)   (Algorithm 1, Lighting, +1 offset).
@@ -258,15 +350,16 @@ __global__ void __launch_bounds__(256) k_fluence_sum(Plan pl, OUT *__restrict__ 
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
-static RowSplit make_split(const Plan &pl, int n, int kind) {
+static RowSplit make_split(const Plan &pl, int n, int kind, int qsel) {
     // kind 0: trace rows (q, u); 1: merge-up rows (q, x, k) at level n;
-    // 2: merge-down rows (q, x, ip) at level n
+    // 2: merge-down rows (q, x, ip) at level n.  qsel >= 0 keeps one frame.
     RowSplit rs;
     long long acc = 0;
     for (int q = 0; q < 4; ++q) {
         rs.start[q] = acc;
         const QuadGeom &g = pl.q[q];
         long long rows = 0;
+        if (qsel >= 0 && q != qsel) continue;
         if (kind == 0) rows = g.U;
         else if (kind == 1) rows = (n <= g.N && n >= 3) ? (long long)g.Un[n] * ((1 << n) + 1) : 0;
         else rows = (n < g.N) ? (long long)g.Un[n] * (1 << n) : 0;
@@ -307,51 +400,55 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
     const double *ed = (const double *)e, *sd = (const double *)s;
     const double esz = P == P_FP64 ? 8.0 : 4.0;
     const double img = double(pl.W) * pl.H;
-    {
-        double by = img * (pl.C + 1) * esz;
-        for (int q = 0; q < 4; ++q)
-            for (int n = 0; n <= 2; ++n) by += bytes_T(pl, q, n);
-        const size_t smem = sizeof(typename Prec<P>::A) * (C + 1) * TR_REG * TR_PITCH;
-        static bool attr_set = false;   // per template instance
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_trace012<P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set = true;
+    const size_t smem = TraceTile<typename Prec<P>::A, C>::bytes();
+    // sched 0: every launch covers the four frames (level-major);
+    // sched 1: frame by frame, so that each level's producer and consumer
+    //          (tens of MB per frame) meet in L2.
+    const int passes = pl.sched == 1 ? 4 : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int qsel = pl.sched == 1 ? pass : -1;
+        {
+            double by = img * (pl.C + 1) * esz / (pl.sched == 1 ? 4 : 1);
+            for (int q = 0; q < 4; ++q)
+                if (qsel < 0 || q == qsel)
+                    for (int n = 0; n <= 2; ++n) by += bytes_T(pl, q, n);
+            dim3 grid((pl.W + TR_TILE - 1) / TR_TILE, (pl.H + TR_TILE - 1) / TR_TILE);
+            rec->begin(K_TRACE012, 0, by);
+            k_trace012<P, C><<<grid, 256, smem, st>>>(pl, rt, ef, sf, ed, sd, qsel < 0 ? 15 : (1 << qsel));
+            rec->end();
+            ++*launches;
         }
-        dim3 grid((pl.W + TR_TILE - 1) / TR_TILE, (pl.H + TR_TILE - 1) / TR_TILE);
-        rec->begin(K_TRACE012, 0, by);
-        k_trace012<P, C><<<grid, 256, smem, st>>>(pl, rt, ef, sf, ed, sd);
-        rec->end();
-        ++*launches;
-    }
-    for (int n = 3; n <= Nmax; ++n) {
-        RowSplit rs = make_split(pl, n, 1);
-        if (rs.start[4] == 0) continue;
-        double by = 0;
-        for (int q = 0; q < 4; ++q)
-            if (n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
-        dim3 grid((unsigned)rs.start[4], vb);
-        rec->begin(K_MERGE_UP, n, by);
-        k_merge_up<P, C><<<grid, bs, 0, st>>>(pl, rs, n);
-        rec->end();
-        ++*launches;
-    }
-    for (int n = Nmax - 1; n >= 0; --n) {
-        RowSplit rs = make_split(pl, n, 2);
-        if (rs.start[4] == 0) continue;
-        double by = 0;
-        for (int q = 0; q < 4; ++q) {
-            const QuadGeom &g = pl.q[q];
-            if (n >= g.N) continue;
-            // odd columns of T_n, even directions of T_{n+1}, R_{n+1} once, R_n written
-            by += bytes_T(pl, q, n) * (double(g.Un[n] / 2) / g.Un[n]);
-            by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
-            by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
+        for (int n = 3; n <= Nmax; ++n) {
+            RowSplit rs = make_split(pl, n, 1, qsel);
+            if (rs.start[4] == 0) continue;
+            double by = 0;
+            for (int q = 0; q < 4; ++q)
+                if ((qsel < 0 || q == qsel) && n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
+            dim3 grid((unsigned)rs.start[4], vb);
+            rec->begin(K_MERGE_UP, n, by);
+            k_merge_up<P, C><<<grid, bs / 2, 0, st>>>(pl, rs, n);
+            rec->end();
+            ++*launches;
         }
-        dim3 grid((unsigned)rs.start[4], vb);
-        rec->begin(K_MERGE_DOWN, n, by);
-        k_merge_down<P, C><<<grid, bs, 0, st>>>(pl, rs, n);
-        rec->end();
-        ++*launches;
+        for (int n = Nmax - 1; n >= 0; --n) {
+            RowSplit rs = make_split(pl, n, 2, qsel);
+            if (rs.start[4] == 0) continue;
+            double by = 0;
+            for (int q = 0; q < 4; ++q) {
+                const QuadGeom &g = pl.q[q];
+                if ((qsel >= 0 && q != qsel) || n >= g.N) continue;
+                // odd columns of T_n, even directions of T_{n+1}, R_{n+1} once, R_n written
+                by += bytes_T(pl, q, n) * (double(g.Un[n] / 2) / g.Un[n]);
+                by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
+                by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
+            }
+            dim3 grid((unsigned)rs.start[4], vb);
+            rec->begin(K_MERGE_DOWN, n, by);
+            if (n >= 1) k_merge_down<P, C, true><<<grid, bs / 2, 0, st>>>(pl, rs, n);
+            else k_merge_down<P, C, false><<<grid, bs, 0, st>>>(pl, rs, n);
+            rec->end();
+            ++*launches;
+        }
     }
     if (with_sum) {
         double by = img * pl.C * esz;
@@ -375,6 +472,27 @@ static cudaError_t fwd_prec(const Plan &pl, const RayTable &rt, const void *e, c
     case 3: return fwd_impl<P, 3>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
     default: return fwd_impl<P, 4>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
     }
+}
+
+template <int P>
+static cudaError_t prepare_prec() {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *fn, size_t bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    set((const void *)k_trace012<P, 1>, TraceTile<typename Prec<P>::A, 1>::bytes());
+    set((const void *)k_trace012<P, 2>, TraceTile<typename Prec<P>::A, 2>::bytes());
+    set((const void *)k_trace012<P, 3>, TraceTile<typename Prec<P>::A, 3>::bytes());
+    set((const void *)k_trace012<P, 4>, TraceTile<typename Prec<P>::A, 4>::bytes());
+    return e;
+}
+
+cudaError_t prepare_forward_kernels() {
+    cudaError_t e = prepare_prec<P_FP32>();
+    if (e == cudaSuccess) e = prepare_prec<P_FP16>();
+    if (e == cudaSuccess) e = prepare_prec<P_BF16>();
+    if (e == cudaSuccess) e = prepare_prec<P_FP64>();
+    return e;
 }
 
 cudaError_t launch_forward_levels(const Plan &pl, const RayTable &rt, const void *e, const void *s,

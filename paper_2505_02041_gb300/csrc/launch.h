@@ -71,6 +71,12 @@ cudaError_t launch_forward_levels(const Plan &pl, const RayTable &rt, const void
 cudaError_t launch_backward(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,
                             void *ge, void *gs, cudaStream_t st, int *launches, Recorder *rec);
 
+// One-time per-device kernel set-up (dynamic shared-memory limits); must run
+// with the device current before the kernels are launched or captured.
+cudaError_t prepare_forward_kernels();
+cudaError_t prepare_backward_kernels();
+cudaError_t prepare_device_once();
+
 // Dense fp32 copy of level n of frame q (which = 0: T_n, 1: R_n).
 cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *dst, cudaStream_t st);
 

@@ -1,0 +1,66 @@
+"""Reduced-precision storage (fp16 / bf16 radiance, fp32 log-domain
+transmittance, fp32 arithmetic) against the FP64 oracle.
+
+These modes change the stored values, so they are compared with the oracle
+at a stated error rather than the fp32 bound: err_max (max |diff| / max |F|)
+and the relative L2 error are checked against bounds a few times above the
+values measured on these scenes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_02041_gb300 import scenes
+from gpu_util import require_gpu, err_max, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {"fp16": (5e-3, 2e-3), "bf16": (4e-2, 1.5e-2)}   # (err_max, rel L2)
+
+
+def _F(e, s, prec):
+    from paper_2505_02041_gb300 import HRC
+    C, H, W = e.shape
+    h = HRC(W, H, C, 0, prec)
+    return h, h.forward(to_dev(e), to_dev(s)).cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("name", ["disks64", "fog512"])
+def test_reduced_precision_forward(prec, name):
+    require_gpu()
+    e, s = scenes.scene_by_name(name)
+    _, F = _F(e, s, prec)
+    Fr = oracle.fluence(e, s)
+    em = err_max(F, Fr)
+    l2 = np.linalg.norm(F - Fr) / np.linalg.norm(Fr)
+    print(f"{name} {prec}: err_max={em:.3e} relL2={l2:.3e}")
+    assert em <= BOUNDS[prec][0] and l2 <= BOUNDS[prec][1]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_reduced_precision_levels_log_transmittance(prec):
+    """Opaque scene: the log-domain transmittance keeps T far below the fp32
+    underflow threshold of a linear product, and the levels match the oracle."""
+    require_gpu()
+    e, s = scenes.random_scene(48, 40, 2, 3)
+    h, _ = _F(e, s, prec)
+    for n in (0, 2, 4, 6):
+        Tg = h.level(1, "T", n).cpu().numpy()
+        Tr = oracle.frame_level(e, s, 1, "T", n)
+        assert np.max(np.abs(Tg[..., -1] - Tr[..., -1])) <= 1e-5
+        assert err_max(Tg[..., :-1], Tr[..., :-1]) <= BOUNDS[prec][0]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_reduced_precision_backward(prec):
+    require_gpu()
+    e, s = scenes.random_scene(40, 36, 2, 4)
+    gF = scenes.rng(9).normal(size=e.shape).astype(np.float32)
+    from paper_2505_02041_gb300 import HRC
+    h = HRC(40, 36, 2, 0, prec)
+    h.forward(to_dev(e), to_dev(s))
+    ge, gs = h.backward(to_dev(gF))
+    ge_r, gs_r = oracle.fluence_adjoint(e, s, gF)
+    assert err_max(ge.cpu().numpy(), ge_r) <= 4 * BOUNDS[prec][0]
+    assert err_max(gs.cpu().numpy(), gs_r) <= 4 * BOUNDS[prec][0]
