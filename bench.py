@@ -356,11 +356,70 @@ def run_ours(args):
                           "rel_l2": float(np.linalg.norm(Fn - Fr) / np.linalg.norm(Fr))}
             hp.close()
         line["precisions"] = rows
+    if args.batched and world == 1:
+        del h, e, s, F, gF, gE, gS, flush
+        torch.cuda.empty_cache()
+        line["batched"] = bench_batched(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_batched(args, dev):
+    """64 scenes of sizes drawn from {128, 256, 512, 1024, 2048}^2 (seed 4),
+    C = 3, fog / disks / rectangles as the 512^2 workload (seeds 400+i),
+    bf16 interval storage: forward and forward+backward of the whole batch,
+    each pass one persistent launch (graph-replayed)."""
+    import torch
+    from paper_2505_02041_gb300 import BatchedHRC, scenes
+    sizes = scenes.batched_sizes(64, 4)
+    es, ss = [], []
+    for i, X in enumerate(sizes):
+        e, s = scenes.scene_disks_rects_fog(X, X, 3, 400 + i)
+        es.append(torch.from_numpy(e))
+        ss.append(torch.from_numpy(s))
+    try:
+        b = BatchedHRC([(X, X) for X in sizes], 3, 0, "bf16")
+    except Exception as ex:   # the batch needs about 200 GB of device memory
+        return {"unavailable": f"batched context: {ex}"}
+    e, s = b.pack(es, ss)
+    del es, ss
+    F = torch.empty_like(e)
+    gF = torch.ones_like(e)
+    ge = torch.empty_like(e)
+    gs = torch.empty_like(s)
+    tune = b.autotune(e, s, reps=2)
+    b.forward(e, s, F)
+    b.backward(gF, ge, gs)
+    b.sync()
+    n = max(3, min(args.steps, 5))
+    stream = torch.cuda.current_stream(dev)
+
+    def run(step):
+        ts = []
+        for _ in range(n):
+            a = torch.cuda.Event(enable_timing=True)
+            z = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            z.record(stream)
+            z.synchronize()
+            ts.append(a.elapsed_time(z))
+        return statistics.mean(ts)
+
+    fwd_ms = run(lambda: b.forward(e, s, F))
+    fb_ms = run(lambda: (b.forward(e, s, F), b.backward(gF, ge, gs)))
+    b.sync()
+    from collections import Counter
+    out = {"scenes": len(sizes), "sizes": dict(Counter(sizes)), "channels": 3, "precision": "bf16",
+           "forward_ms": fwd_ms, "forward_scenes_per_s": len(sizes) / (fwd_ms * 1e-3),
+           "fwd_bwd_ms": fb_ms, "fwd_bwd_scenes_per_s": len(sizes) / (fb_ms * 1e-3),
+           "launches_per_pass": 1, "autotune_ms": {f"bpsm{k[0]}_order{k[1]}": v for k, v in tune.items()},
+           "timed_batches": n}
+    b.close()
+    return out
 
 
 def main():
@@ -375,6 +434,8 @@ def main():
     ap.add_argument("--no-precisions", dest="precisions", action="store_false",
                     help="skip the fp16 / bf16 error-and-time sweep against the FP64 oracle")
     ap.add_argument("--schedule", type=int, default=-1, help="launch schedule (default: the library's)")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 64-scene batched persistent-launch measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -117,6 +117,13 @@ hrc_status hrc_create_batched(int n, const int *W, const int *H, int channels, i
                               hrc_ctx **out);
 hrc_status hrc_scene_offsets(const hrc_ctx *ctx, long long *emis_off, long long *sigma_off);
 
+/* As hrc_create_batched, with the interval storage precision chosen at
+ * creation (HRC_FP32, HRC_FP16_LOGT or HRC_BF16_LOGT), so the buffers are
+ * sized for that precision's layout.  A later hrc_set_precision to a larger
+ * layout reallocates them. */
+hrc_status hrc_create_batched_prec(int n, const int *W, const int *H, int channels, int cascades,
+                                   hrc_precision prec, hrc_ctx **out);
+
 /* Forward / backward of every scene of a batched context in one persistent,
  * CUDA-graph-launched kernel; same semantics as the single-scene calls.
  * HRC_ETIMEOUT if a bounded device-side dependency wait gave up. */
@@ -154,6 +161,22 @@ hrc_status hrc_fluence_backward_batched(hrc_ctx *ctx, const float *grad_F, float
 #define HRC_NOALLOC_SCRATCH_BYTES 20443136ULL
 hrc_status hrc_fluence_noalloc(int W, int H, int channels, const float *emission, const float *sigma_t,
                                float *out, void *cuda_stream);
+
+/* Waits for the batched context's stream and reports the status of its
+ * last persistent launch: HRC_ETIMEOUT if a bounded dependency wait gave
+ * up (the launch then ended early and its outputs are incomplete). */
+hrc_status hrc_batched_sync(hrc_ctx *ctx);
+
+/* Tuning of the persistent launch: resident blocks per SM (0 = as many as
+ * fit) and the ticket order within each stage (0 = input order, 1 = largest
+ * scene first).  Results are identical for every setting. */
+hrc_status hrc_batched_tune(hrc_ctx *ctx, int blocks_per_sm, int order);
+
+/* Test hook for the bounded waits: `withhold_counter` >= 0 makes that stage
+ * counter never publish, so the stages after it time out after
+ * `spin_limit` polls (about 128 ns each; <= 0 restores the default, about
+ * 2 s) and the launch ends with HRC_ETIMEOUT instead of hanging. */
+hrc_status hrc_batched_debug(hrc_ctx *ctx, int withhold_counter, long long spin_limit);
 
 /* Introspection for tests: copies level n of quadrant frame q (0..3) from
  * the last forward into `dst` (device fp32).  which = 0: T_n as

@@ -33,9 +33,13 @@ SIGNATURES = [
     ("hrc_fluence_f64", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_fluence_backward_f64", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_create_batched", _i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _i, ctypes.POINTER(_vp)]),
+    ("hrc_create_batched_prec", _i, [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _i, _i, ctypes.POINTER(_vp)]),
     ("hrc_scene_offsets", _i, [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
     ("hrc_fluence_batched", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_fluence_backward_batched", _i, [_vp, _vp, _vp, _vp]),
+    ("hrc_batched_sync", _i, [_vp]),
+    ("hrc_batched_tune", _i, [_vp, _i, _i]),
+    ("hrc_batched_debug", _i, [_vp, _i, _ll]),
     ("hrc_fluence_noalloc", _i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
     ("hrc_copy_level", _i, [_vp, _i, _i, _i, _vp, ctypes.POINTER(_ll)]),
     ("hrc_last_launch_count", _i, [_vp]),
@@ -139,6 +143,15 @@ def hrc_create_batched(Ws, Hs, channels: int, cascades: int = 0):
     return out
 
 
+def hrc_create_batched_prec(Ws, Hs, channels: int, cascades: int, prec: int):
+    n = len(Ws)
+    out = _vp()
+    Wa = (_i * n)(*Ws)
+    Ha = (_i * n)(*Hs)
+    check(load().hrc_create_batched_prec(n, Wa, Ha, channels, cascades, prec, ctypes.byref(out)))
+    return out
+
+
 def hrc_scene_offsets(ctx, n: int):
     eo = (_ll * (n + 1))()
     so = (_ll * (n + 1))()
@@ -152,6 +165,18 @@ def hrc_fluence_batched(ctx, emission, sigma_t, out):
 
 def hrc_fluence_backward_batched(ctx, grad_F, grad_emission, grad_sigma_t):
     check(load().hrc_fluence_backward_batched(ctx, ptr(grad_F), ptr(grad_emission), ptr(grad_sigma_t)), ctx)
+
+
+def hrc_batched_sync(ctx):
+    check(load().hrc_batched_sync(ctx), ctx)
+
+
+def hrc_batched_tune(ctx, blocks_per_sm: int, order: int):
+    check(load().hrc_batched_tune(ctx, blocks_per_sm, order), ctx)
+
+
+def hrc_batched_debug(ctx, withhold_counter: int, spin_limit: int):
+    check(load().hrc_batched_debug(ctx, withhold_counter, spin_limit), ctx)
 
 
 def hrc_fluence_noalloc(W: int, H: int, channels: int, emission, sigma_t, out, stream_handle=None):

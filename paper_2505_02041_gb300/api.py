@@ -138,6 +138,104 @@ class HRC:
             pass
 
 
+class BatchedHRC:
+    """Many scenes of uneven size, each pass in one persistent launch.
+
+    Scenes are packed back to back: emission / fluence as the concatenation
+    of the flattened [C][H_i][W_i] blocks, extinction as that of the [H_i][W_i]
+    blocks (``offsets()`` gives the element offsets).
+    """
+
+    def __init__(self, sizes, channels: int = 1, cascades: int = 0, precision: str = "fp32"):
+        self.sizes = [(int(w), int(h)) for (w, h) in sizes]
+        self.C = channels
+        Ws = [w for w, _ in self.sizes]
+        Hs = [h for _, h in self.sizes]
+        self.ctx = _lib.hrc_create_batched_prec(Ws, Hs, channels, cascades, _PREC[precision])
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.eoff, self.soff = _lib.hrc_scene_offsets(self.ctx, len(self.sizes))
+        self._borrowed = None
+
+    def offsets(self):
+        return self.eoff, self.soff
+
+    def pack(self, emissions, sigmas):
+        """Lists of per-scene tensors -> packed device tensors."""
+        e = torch.cat([t.reshape(-1) for t in emissions]).to(self.device, torch.float32).contiguous()
+        s = torch.cat([t.reshape(-1) for t in sigmas]).to(self.device, torch.float32).contiguous()
+        return e, s
+
+    def unpack(self, packed, which="e"):
+        off = self.eoff if which == "e" else self.soff
+        out = []
+        for i, (w, h) in enumerate(self.sizes):
+            t = packed[off[i]:off[i + 1]]
+            out.append(t.view(self.C, h, w) if which == "e" else t.view(h, w))
+        return out
+
+    def _stream(self):
+        _lib.hrc_set_stream(self.ctx, torch.cuda.current_stream(self.device).cuda_stream)
+
+    def forward(self, e_packed, s_packed, out=None):
+        assert e_packed.numel() == self.eoff[-1] and s_packed.numel() == self.soff[-1]
+        if out is None:
+            out = torch.empty_like(e_packed)
+        self._stream()
+        _lib.hrc_fluence_batched(self.ctx, e_packed, s_packed, out)
+        self._borrowed = (e_packed, s_packed)
+        return out
+
+    def backward(self, gF_packed, ge=None, gs=None):
+        if ge is None:
+            ge = torch.empty(self.eoff[-1], dtype=torch.float32, device=self.device)
+        if gs is None:
+            gs = torch.empty(self.soff[-1], dtype=torch.float32, device=self.device)
+        self._stream()
+        _lib.hrc_fluence_backward_batched(self.ctx, gF_packed.contiguous(), ge, gs)
+        return ge, gs
+
+    def sync(self):
+        """Wait and raise HRCError(HRC_ETIMEOUT) if a dependency wait gave up."""
+        _lib.hrc_batched_sync(self.ctx)
+
+    def tune(self, blocks_per_sm: int = 0, order: int = 0):
+        _lib.hrc_batched_tune(self.ctx, blocks_per_sm, order)
+
+    def autotune(self, e_packed, s_packed, reps: int = 3):
+        """Time each (blocks per SM, ticket order) candidate on these inputs
+        and keep the fastest; returns {candidate: ms}."""
+        res = {}
+        out = torch.empty_like(e_packed)
+        for bpsm in (0, 1, 2):
+            for order in (0, 1):
+                self.tune(bpsm, order)
+                self.forward(e_packed, s_packed, out)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(reps):
+                    self.forward(e_packed, s_packed, out)
+                b.record()
+                b.synchronize()
+                res[(bpsm, order)] = a.elapsed_time(b) / reps
+        best = min(res, key=res.get)
+        self.tune(*best)
+        return res
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            _lib.hrc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class _FluenceFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, hrc: HRC, emission, sigma_t):

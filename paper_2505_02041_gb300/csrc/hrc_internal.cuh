@@ -61,6 +61,12 @@ struct RayTable {
     double lenD[HRC_MAXPIECE];
 };
 
+// Row-to-quadrant lookup for flattened (q, row) grids: the first global row
+// of each quadrant frame; start[4] = total rows.
+struct RowSplit {
+    long long start[5];
+};
+
 __host__ __device__ inline int ray_id(int n, int k) { return n == 0 ? k : (n == 1 ? 2 + k : 5 + k); }
 
 // frame (u, v) of quadrant q -> image pixel (x, y)

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -196,6 +197,26 @@ struct hrc_ctx {
     int graph_next = 0;
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
+    // batched contexts
+    bool batched = false;
+    int nscenes = 0;
+    std::vector<int> Ws, Hs;
+    std::vector<Plan> bplans;
+    std::vector<long long> eoff, soff;
+    Plan *d_plans = nullptr;
+    long long *d_eoff = nullptr, *d_soff = nullptr;
+    StageBlock *d_blocks[2] = {nullptr, nullptr};
+    int nblocks[2] = {0, 0};
+    long long total[2] = {0, 0};
+    double bbytes[2] = {0, 0};
+    int *d_counters = nullptr;
+    int ncounters[2] = {0, 0};
+    unsigned long long *d_ticket = nullptr;
+    int *d_status = nullptr;
+    int withhold = -1;
+    long long spin_limit = 1LL << 24;   // ~2 s of 128 ns polls
+    int blocks_per_sm = 0;              // 0: as many as fit
+    int order = 0;                      // 0: scenes in input order per stage, 1: largest first
 };
 
 namespace {
@@ -275,6 +296,13 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
     return HRC_OK;
 }
 
+void clear_graphs(hrc_ctx *ctx) {
+    for (auto &g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = hrc_ctx::GraphEntry();
+    }
+}
+
 hrc_status check_ctx(hrc_ctx *ctx) {
     if (!ctx) return HRC_EINVAL;
     cudaError_t e = cudaGetLastError();
@@ -283,6 +311,10 @@ hrc_status check_ctx(hrc_ctx *ctx) {
 }
 
 }  // namespace
+
+namespace {
+hrc_status build_batched_plans(hrc_ctx *ctx, int prec);
+}
 
 extern "C" {
 
@@ -369,6 +401,14 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->dev_F);
     for (auto &g : ctx->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    cudaFree(ctx->d_plans);
+    cudaFree(ctx->d_eoff);
+    cudaFree(ctx->d_soff);
+    cudaFree(ctx->d_blocks[0]);
+    cudaFree(ctx->d_blocks[1]);
+    cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_ticket);
+    cudaFree(ctx->d_status);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return HRC_OK;
@@ -392,6 +432,31 @@ hrc_status hrc_set_stream(hrc_ctx *ctx, void *stream) {
 hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
     if (!ctx) return HRC_EINVAL;
     if (prec < HRC_FP32 || prec > HRC_FP64_TEST) return fail(ctx, HRC_EINVAL, "hrc_set_precision: unknown precision");
+    clear_graphs(ctx);
+    if (ctx->batched) {
+        if (prec == HRC_FP64_TEST) return fail(ctx, HRC_EINVAL, "hrc_set_precision: fp64 is not available on batched contexts");
+        size_t bytes = 0;
+        for (int i = 0; i < ctx->nscenes; ++i) {
+            Plan p;
+            bytes = build_plan(ctx->Ws[i], ctx->Hs[i], ctx->C, ctx->cascades, (int)prec, bytes, p, true);
+        }
+        if (bytes > ctx->arena_bytes) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->arena);
+            ctx->arena = nullptr;
+            ctx->arena_bytes = 0;
+            cudaError_t e = cudaMalloc(&ctx->arena, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                ctx->arena = nullptr;
+                return fail(ctx, HRC_ENOMEM, "hrc_set_precision: batched buffers do not fit");
+            }
+            ctx->arena_bytes = bytes;
+        }
+        ctx->prec = (int)prec;
+        ctx->have_fwd = false;
+        return build_batched_plans(ctx, (int)prec);
+    }
     if (prec == HRC_FP64_TEST) {
         if (!ctx->arena64) {
             Plan p64;
@@ -427,6 +492,7 @@ hrc_status hrc_fluence(hrc_ctx *ctx, const float *emission, const float *sigma_t
     hrc_status st = check_ctx(ctx);
     if (st != HRC_OK) return st;
     if (ctx->prec == P_FP64) return fail(ctx, HRC_ESTATE, "hrc_fluence: context is in HRC_FP64_TEST; use hrc_fluence_f64");
+    if (ctx->batched) return fail(ctx, HRC_ESTATE, "hrc_fluence: batched context; use hrc_fluence_batched");
     if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence: NULL pointer");
     if (!aligned16(emission) || !aligned16(sigma_t) || !aligned16(out))
         return fail(ctx, HRC_EINVAL, "hrc_fluence: pointers must be 16-byte aligned");
@@ -511,6 +577,268 @@ hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *
                         return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, s, n, r);
                     },
                     "hrc_fluence_backward_f64");
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched contexts
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+// Build and upload the ticket tables of both modes (forward, backward).
+hrc_status build_batched_tables(hrc_ctx *ctx) {
+    std::vector<int> order(ctx->nscenes);
+    for (int i = 0; i < ctx->nscenes; ++i) order[i] = i;
+    if (ctx->order == 1)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (long long)ctx->Ws[a] * ctx->Hs[a] > (long long)ctx->Ws[b] * ctx->Hs[b];
+        });
+    for (int mode = 0; mode < 2; ++mode) {
+        std::vector<std::vector<StageDesc>> st(ctx->nscenes);
+        size_t maxs = 0;
+        for (int i = 0; i < ctx->nscenes; ++i) {
+            batched_stages(ctx->bplans[i], mode, st[i]);
+            maxs = std::max(maxs, st[i].size());
+        }
+        std::vector<int> cbase(ctx->nscenes);
+        int nc = 0;
+        for (int i = 0; i < ctx->nscenes; ++i) { cbase[i] = nc; nc += (int)st[i].size(); }
+        std::vector<StageBlock> blocks;
+        long long tick = 0;
+        double bytes = 0;
+        for (size_t k = 0; k < maxs; ++k)
+            for (int i : order) {
+                if (k >= st[i].size()) continue;
+                const StageDesc &d = st[i][k];
+                StageBlock b;
+                b.first = tick;
+                b.count = d.count;
+                b.scene = i;
+                b.kind = d.kind;
+                b.level = d.level;
+                b.nvb = d.nvb;
+                b.rpi = d.rpi;
+                b.rows = d.rows;
+                b.dep = k == 0 ? -1 : cbase[i] + (int)k - 1;
+                b.dep_target = k == 0 ? 0 : st[i][k - 1].count;
+                b.own = cbase[i] + (int)k;
+                b.rs = d.rs;
+                blocks.push_back(b);
+                tick += d.count;
+                bytes += d.bytes;
+            }
+        if (ctx->d_blocks[mode]) cudaFree(ctx->d_blocks[mode]);
+        ctx->d_blocks[mode] = nullptr;
+        cudaError_t e = cudaMalloc(&ctx->d_blocks[mode], sizeof(StageBlock) * blocks.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ctx->d_blocks[mode], blocks.data(), sizeof(StageBlock) * blocks.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batched tables");
+        ctx->nblocks[mode] = (int)blocks.size();
+        ctx->total[mode] = tick;
+        ctx->ncounters[mode] = nc;
+        ctx->bbytes[mode] = bytes;
+    }
+    return HRC_OK;
+}
+
+// Lay out every scene's levels (fp32 layout = the largest) in the arena and
+// upload plans, offsets and arc tables for the current precision.
+hrc_status build_batched_plans(hrc_ctx *ctx, int prec) {
+    size_t off = 0;
+    ctx->bplans.assign(ctx->nscenes, Plan());
+    for (int i = 0; i < ctx->nscenes; ++i) {
+        off = build_plan(ctx->Ws[i], ctx->Hs[i], ctx->C, ctx->cascades, prec, off, ctx->bplans[i], true);
+        ctx->bplans[i].arena = ctx->arena;
+        ctx->bplans[i].sched = 0;
+    }
+    if (off > ctx->arena_bytes) return fail(ctx, HRC_ENOMEM, "batched layout exceeds the arena");
+    for (int i = 0; i < ctx->nscenes; ++i) {
+        cudaError_t e = upload_arcs(ctx->bplans[i], ctx->arena);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batched arcs");
+    }
+    cudaError_t e = cudaMemcpy(ctx->d_plans, ctx->bplans.data(), sizeof(Plan) * ctx->nscenes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batched plans");
+    return build_batched_tables(ctx);
+}
+
+hrc_status run_batched(hrc_ctx *ctx, int mode, const void *e, const void *s, void *F, const void *gF, void *ge,
+                       void *gs, const char *where) {
+    BatchArgs a;
+    a.plans = ctx->d_plans;
+    a.eoff = ctx->d_eoff;
+    a.soff = ctx->d_soff;
+    a.blocks = ctx->d_blocks[mode];
+    a.nblocks = ctx->nblocks[mode];
+    a.total = ctx->total[mode];
+    a.ticket = ctx->d_ticket;
+    a.counters = ctx->d_counters;
+    a.status = ctx->d_status;
+    a.withhold = ctx->withhold;
+    a.spin_limit = ctx->spin_limit;
+    a.e = e;
+    a.s = s;
+    a.F = F;
+    a.gF = gF;
+    a.ge = ge;
+    a.gs = gs;
+    const int prec = ctx->prec, C = ctx->C, bpsm = ctx->blocks_per_sm, nc = ctx->ncounters[mode];
+    const double bytes = ctx->bbytes[mode];
+    auto enqueue = [&](cudaStream_t st, int *n, Recorder *r) {
+        cudaError_t err = cudaMemsetAsync(a.counters, 0, sizeof(int) * nc, st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned long long), st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(a.status, 0, sizeof(int), st);
+        if (err != cudaSuccess) return err;
+        r->begin(K_BATCHED, mode, bytes);
+        err = launch_batched(a, prec, C, bpsm, mode, st);
+        r->end();
+        ++*n;
+        return err;
+    };
+    // the graph key includes the tuning state (blocks per SM, order, test hooks)
+    const void *k3 = (const void *)(intptr_t)((ctx->blocks_per_sm << 8) | (ctx->order << 4) | (ctx->withhold >= 0 ? 1 : 0));
+    const void *k4 = (const void *)(intptr_t)ctx->spin_limit;
+    return run_pass(ctx, 8 + mode, mode == 0 ? e : gF, mode == 0 ? s : ge, mode == 0 ? F : gs, k3, k4, enqueue, where);
+}
+
+}  // namespace
+
+extern "C" {
+
+hrc_status hrc_create_batched(int n, const int *W, const int *H, int channels, int cascades, hrc_ctx **out) {
+    return hrc_create_batched_prec(n, W, H, channels, cascades, HRC_FP32, out);
+}
+
+hrc_status hrc_create_batched_prec(int n, const int *W, const int *H, int channels, int cascades, hrc_precision prec,
+                                   hrc_ctx **out) {
+    if (!out) return fail(nullptr, HRC_EINVAL, "hrc_create_batched: out is NULL");
+    if (prec < HRC_FP32 || prec > HRC_BF16_LOGT)
+        return fail(nullptr, HRC_EINVAL, "hrc_create_batched: precision must be fp32, fp16 or bf16");
+    *out = nullptr;
+    if (n < 1 || !W || !H) return fail(nullptr, HRC_EINVAL, "hrc_create_batched: need n >= 1 scenes");
+    if (channels < 1 || channels > 4) return fail(nullptr, HRC_EINVAL, "hrc_create_batched: channels must be in [1, 4]");
+    for (int i = 0; i < n; ++i)
+        if (W[i] < 1 || H[i] < 1 || W[i] > 16384 || H[i] > 16384)
+            return fail(nullptr, HRC_EINVAL, "hrc_create_batched: W and H must be in [1, 16384]");
+    hrc_ctx *ctx = new (std::nothrow) hrc_ctx();
+    if (!ctx) return fail(nullptr, HRC_ENOMEM, "hrc_create_batched: host allocation failed");
+    ctx->batched = true;
+    ctx->nscenes = n;
+    ctx->Ws.assign(W, W + n);
+    ctx->Hs.assign(H, H + n);
+    ctx->C = channels;
+    ctx->cascades = cascades;
+    ctx->rt = make_ray_table();
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = prepare_device_once();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete ctx; return fail(nullptr, HRC_ECUDA, std::string("hrc_create_batched: ") + cudaGetErrorString(e)); }
+    size_t bytes = 0;
+    ctx->eoff.assign(n + 1, 0);
+    ctx->soff.assign(n + 1, 0);
+    ctx->prec = (int)prec;
+    for (int i = 0; i < n; ++i) {
+        Plan p;
+        bytes = build_plan(W[i], H[i], channels, cascades, (int)prec, bytes, p, true);
+        ctx->eoff[i + 1] = ctx->eoff[i] + (long long)channels * W[i] * H[i];
+        ctx->soff[i + 1] = ctx->soff[i] + (long long)W[i] * H[i];
+    }
+    ctx->arena_bytes = bytes;
+    int maxstages = 0;
+    for (int i = 0; i < n; ++i) maxstages += 4 * (levels_for(std::max(W[i], H[i]), cascades) + 3) + 8;
+    e = cudaMalloc(&ctx->arena, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_plans, sizeof(Plan) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_eoff, sizeof(long long) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_soff, sizeof(long long) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, sizeof(int) * maxstages);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_ticket, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hrc_destroy(ctx);
+        return fail(nullptr, HRC_ENOMEM, "hrc_create_batched: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    e = cudaMemcpy(ctx->d_eoff, ctx->eoff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_soff, ctx->soff.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) { hrc_destroy(ctx); return fail(nullptr, HRC_ECUDA, "hrc_create_batched: upload failed"); }
+    hrc_status st = build_batched_plans(ctx, (int)prec);
+    if (st != HRC_OK) {
+        std::string msg = ctx->err;
+        hrc_destroy(ctx);
+        return fail(nullptr, st, msg);
+    }
+    for (int mode = 0; mode < 2; ++mode)
+        if (ctx->ncounters[mode] > maxstages) {
+            hrc_destroy(ctx);
+            return fail(nullptr, HRC_EINVAL, "hrc_create_batched: stage count exceeds the counter buffer");
+        }
+    *out = ctx;
+    return HRC_OK;
+}
+
+hrc_status hrc_scene_offsets(const hrc_ctx *ctx, long long *emis_off, long long *sigma_off) {
+    if (!ctx || !ctx->batched) return HRC_EINVAL;
+    for (int i = 0; i <= ctx->nscenes; ++i) {
+        if (emis_off) emis_off[i] = ctx->eoff[i];
+        if (sigma_off) sigma_off[i] = ctx->soff[i];
+    }
+    return HRC_OK;
+}
+
+hrc_status hrc_fluence_batched(hrc_ctx *ctx, const float *emission, const float *sigma_t, float *out) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (!ctx->batched) return fail(ctx, HRC_ESTATE, "hrc_fluence_batched: not a batched context");
+    if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence_batched: NULL pointer");
+    if (!aligned16(emission) || !aligned16(sigma_t) || !aligned16(out))
+        return fail(ctx, HRC_EINVAL, "hrc_fluence_batched: pointers must be 16-byte aligned");
+    st = run_batched(ctx, 0, emission, sigma_t, out, nullptr, nullptr, nullptr, "hrc_fluence_batched");
+    if (st != HRC_OK) return st;
+    ctx->last_e = emission;
+    ctx->last_s = sigma_t;
+    ctx->have_fwd = true;
+    return HRC_OK;
+}
+
+hrc_status hrc_fluence_backward_batched(hrc_ctx *ctx, const float *grad_F, float *grad_emission, float *grad_sigma_t) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (!ctx->batched) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward_batched: not a batched context");
+    if (!ctx->have_fwd) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward_batched: no forward pass on this context");
+    if (!grad_F || !grad_emission || !grad_sigma_t) return fail(ctx, HRC_EINVAL, "hrc_fluence_backward_batched: NULL pointer");
+    if (!aligned16(grad_F) || !aligned16(grad_emission) || !aligned16(grad_sigma_t))
+        return fail(ctx, HRC_EINVAL, "hrc_fluence_backward_batched: pointers must be 16-byte aligned");
+    return run_batched(ctx, 1, ctx->last_e, ctx->last_s, nullptr, grad_F, grad_emission, grad_sigma_t,
+                       "hrc_fluence_backward_batched");
+}
+
+hrc_status hrc_batched_sync(hrc_ctx *ctx) {
+    if (!ctx || !ctx->batched) return HRC_EINVAL;
+    int status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_batched_sync");
+    if (status == HRC_ETIMEOUT) return fail(ctx, HRC_ETIMEOUT, "batched launch: a dependency wait gave up");
+    return status == 0 ? HRC_OK : (hrc_status)status;
+}
+
+hrc_status hrc_batched_debug(hrc_ctx *ctx, int withhold_counter, long long spin_limit) {
+    if (!ctx || !ctx->batched) return HRC_EINVAL;
+    ctx->withhold = withhold_counter;
+    ctx->spin_limit = spin_limit > 0 ? spin_limit : (1LL << 24);
+    return HRC_OK;
+}
+
+hrc_status hrc_batched_tune(hrc_ctx *ctx, int blocks_per_sm, int order) {
+    if (!ctx || !ctx->batched || blocks_per_sm < 0 || order < 0 || order > 1) return HRC_EINVAL;
+    ctx->blocks_per_sm = blocks_per_sm;
+    if (order != ctx->order) {
+        ctx->order = order;
+        return build_batched_tables(ctx);
+    }
+    return HRC_OK;
 }
 
 hrc_status hrc_copy_level(hrc_ctx *ctx, int q, int which, int n, float *dst, long long *count) {

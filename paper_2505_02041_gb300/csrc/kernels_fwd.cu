@@ -1,350 +1,31 @@
-// kernels_fwd.cu -- forward HRC kernels for sm_103a.
-//
-//   k_trace012    : T_0..T_min(2,N) by direct tracing (Sec. 4.2, Eq. 9)
-//   k_merge_up    : T_n from T_{n-1} (Eq. 18 even k, Eqs. 19-20 odd k)
-//   k_merge_down  : R_n from R_{n+1}, T_n, T_{n+1} (Eq. 14 odd x, Eqs. 15-17 even x)
-//   k_fluence_sum : F = sum over quadrants of R_0([u+1, v], 1/2) (Algorithm 1, Lighting)
-//
-// All four quadrant frames run in one launch.  The work is memory-bound
-// (about one FMA per byte), so the kernels are organised around coalesced,
-// v-contiguous rows: one CTA handles one (x, k) or (x, i) row segment of
-// BLOCK consecutive v, every neighbour access being a shifted run of the
-// same length.  Out-of-range lookups read as vacuum (T = <0, 1>, R = 0),
-// which is exact for this method: paths are monotone in v, so a path that
-// leaves the grid never re-enters, and nothing outside the grid emits.
-#include "hrc_internal.cuh"
+// kernels_fwd.cu -- forward HRC kernels for sm_103a (standalone launches of
+// the bodies in fwd_bodies.cuh) and the forward launch sequence.
+#include "fwd_bodies.cuh"
 #include "launch.h"
-#include "trace_shapes.cuh"
 
 namespace hrc {
 
-// Row-to-quadrant lookup for flattened (q, row) grids.
-struct RowSplit {
-    long long start[5];   // first global row of each quadrant; start[4] = total
-};
-
-__device__ __forceinline__ int find_quadrant(const RowSplit &rs, long long r, int &local) {
-    int q = 0;
-    long long base = 0;
-#pragma unroll
-    for (int j = 1; j < 4; ++j)
-        if (r >= rs.start[j]) { q = j; base = rs.start[j]; }
-    local = (int)(r - base);
-    return q;
-}
-
-// Per-pixel piece factors of the three ray classes (trace_shapes.cuh): for
-// the half length l of class c, t = exp(-sigma l) and w = l phi(sigma l) =
-// (1 - e^{-sigma l}) / sigma, the radiance weight of Eq. 4 over a uniform
-// piece.  Full pieces use t^2 and w (1 + t).
-template <class A> __device__ __forceinline__ void piece_factors(A sg, A len, A &t, A &w) {
-    const A m = fexpm1(-sg * len);
-    t = A(1) + m;
-    w = sg != A(0) ? -m / sg : len;
-}
-
-// Shared-memory tile of a 32 x 32 image block with a 4-pixel halo (the
-// longest directly traced ray, v_2(k), reaches 4 pixels along and across):
-// extinction, the piece factors of the three classes, and the emission.
-// Outside the image every field is vacuum (sigma = e = 0, t = 1, w = l).
-constexpr int TR_TILE = 32, TR_HALO = 4, TR_REG = TR_TILE + 2 * TR_HALO, TR_PITCH = TR_REG + 1;
-constexpr int TR_PLANE = TR_REG * TR_PITCH;
-
-template <class A, int C> struct TraceTile {
-    A *s;       // [PLANE]
-    A *t;       // [3][PLANE]
-    A *w;       // [3][PLANE]
-    A *e;       // [C][PLANE]
-    __device__ __forceinline__ explicit TraceTile(unsigned char *smem) {
-        s = reinterpret_cast<A *>(smem);
-        t = s + TR_PLANE;
-        w = t + 3 * TR_PLANE;
-        e = w + 3 * TR_PLANE;
-    }
-    static constexpr size_t bytes() { return sizeof(A) * (7 + C) * TR_PLANE; }
-    template <class IN>
-    __device__ __forceinline__ void stage(int W, int H, int x0, int y0, const IN *__restrict__ ein,
-                                          const IN *__restrict__ sin) {
-        const long long HW = (long long)W * H;
-        for (int i = threadIdx.x; i < TR_REG * TR_REG; i += blockDim.x) {
-            const int ry = i / TR_REG, rx = i - ry * TR_REG;
-            const int x = x0 - TR_HALO + rx, y = y0 - TR_HALO + ry;
-            const bool in = x >= 0 && x < W && y >= 0 && y < H;
-            const long long pix = (long long)y * W + x;
-            const int o = ry * TR_PITCH + rx;
-            const A sg = in ? A(sin[pix]) : A(0);
-            s[o] = sg;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                A tc, wc;
-                piece_factors<A>(sg, class_len<A>(c), tc, wc);
-                t[c * TR_PLANE + o] = tc;
-                w[c * TR_PLANE + o] = wc;
-            }
-#pragma unroll
-            for (int c = 0; c < C; ++c) e[c * TR_PLANE + o] = in ? A(ein[c * HW + pix]) : A(0);
-        }
-    }
-};
-
-// Trace of ray shape R from the probe whose tile offset is `base`; su / sv
-// are the tile strides along the frame's u and v axes.  Pieces J .. END-1
-// are unrolled at compile time.
-template <int P, int C, int J, int END>
-__device__ __forceinline__ void trace_pieces(const TraceTile<typename Prec<P>::A, C> &tt, int base, int su, int sv,
-                                             typename Prec<P>::A (&L)[C], typename Prec<P>::A &Tacc,
-                                             typename Prec<P>::A &tau) {
-    using A = typename Prec<P>::A;
-    if constexpr (J < END) {
-        using pc = PieceAt<J>;
-        const int o = base + pc::du * su + pc::dv * sv;
-        A t = tt.t[pc::cls * TR_PLANE + o];
-        A w = tt.w[pc::cls * TR_PLANE + o];
-        if constexpr (pc::full != 0) {
-            w = w * (A(1) + t);
-            t = t * t;
-        }
-        const A wt = Tacc * w;
-#pragma unroll
-        for (int c = 0; c < C; ++c) L[c] = fma(wt, tt.e[c * TR_PLANE + o], L[c]);
-        Tacc *= t;
-        if constexpr (Prec<P>::LOG) tau = fma(tt.s[o], A(pc::full ? 2 : 1) * class_len<A>(pc::cls), tau);
-        trace_pieces<P, C, J + 1, END>(tt, base, su, sv, L, Tacc, tau);
-    }
-}
-
-template <int P, int C, int R>
-__device__ __forceinline__ void trace_store(const Plan &pl, const TraceTile<typename Prec<P>::A, C> &tt, int q,
-                                            int nmax, int u, int v, int base, int su, int sv) {
-    using A = typename Prec<P>::A;
-    using ray = RayAt<R>;
-    if (ray::n > nmax || (u & ((1 << ray::n) - 1))) return;
-    Iv<P, C> iv;
-#pragma unroll
-    for (int c = 0; c < C; ++c) iv.L[c] = A(0);
-    A Tacc = A(1), tau = A(0);
-    trace_pieces<P, C, ray::begin, ray::end>(tt, base, su, sv, iv.L, Tacc, tau);
-    iv.t = Prec<P>::LOG ? tau : Tacc;
-    TLevel<P, C>(pl, q, ray::n).store(u >> ray::n, ray::k, v, iv);
-}
-
-// T_0..T_min(2,N) of the selected quadrant frames for one 32 x 32 image
-// tile.  Warp w handles tile columns c = 8i + ((w + i) mod 8) along the
-// frame's u axis (one column of every residue mod 4, so the warps get equal
-// shares of the level-1 and level-2 probes); its lanes run along v, so every
-// T store is a 128-byte coalesced row segment in every frame.
 template <int P, int C>
-__global__ void __launch_bounds__(256) k_trace012(Plan pl, RayTable rt, const float *__restrict__ e,
-                                                  const float *__restrict__ s, const double *__restrict__ ed,
-                                                  const double *__restrict__ sd, int qmask) {
-    using A = typename Prec<P>::A;
+__global__ void __launch_bounds__(256) k_trace012(Plan pl, const float *__restrict__ e, const float *__restrict__ s,
+                                                  const double *__restrict__ ed, const double *__restrict__ sd,
+                                                  int qmask) {
     extern __shared__ __align__(16) unsigned char tr_smem[];
-    TraceTile<A, C> tt(tr_smem);
-    const int W = pl.W, H = pl.H;
-    const int x0 = blockIdx.x * TR_TILE, y0 = blockIdx.y * TR_TILE;
-    if (P == P_FP64) tt.stage(W, H, x0, y0, ed, sd);
-    else tt.stage(W, H, x0, y0, e, s);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = 0; q < 4; ++q) {
-        if (!((qmask >> q) & 1)) continue;
-        const QuadGeom &g = pl.q[q];
-        const int nmax = g.N < 2 ? g.N : 2;
-        const bool xu = q < 2;                              // frame u runs along image x
-        const int tu = xu ? x0 : y0, tv = xu ? y0 : x0;     // tile origin along u / v axes
-        const int ext_u = xu ? W : H;
-        const int v = tv + lane;
-        const int sgn = (q == 0 || q == 2) ? 1 : -1;        // image step along u
-        const int su = sgn * (xu ? 1 : TR_PITCH), sv = xu ? TR_PITCH : 1;
-        for (int i = 0; i < TR_TILE / 8; ++i) {
-            const int c = 8 * i + ((warp + i) & 7);
-            if (tu + c >= ext_u || v >= g.V) continue;
-            const int u = (q == 0 || q == 2) ? tu + c : ext_u - 1 - (tu + c);
-            const int base = xu ? (TR_HALO + lane) * TR_PITCH + TR_HALO + c
-                                : (TR_HALO + c) * TR_PITCH + TR_HALO + lane;
-            trace_store<P, C, 0>(pl, tt, q, nmax, u, v, base, su, sv);
-            trace_store<P, C, 1>(pl, tt, q, nmax, u, v, base, su, sv);
-            trace_store<P, C, 2>(pl, tt, q, nmax, u, v, base, su, sv);
-            trace_store<P, C, 3>(pl, tt, q, nmax, u, v, base, su, sv);
-            trace_store<P, C, 4>(pl, tt, q, nmax, u, v, base, su, sv);
-            trace_store<P, C, 5>(pl, tt, q, nmax, u, v, base, su, sv);
-            trace_store<P, C, 6>(pl, tt, q, nmax, u, v, base, su, sv);
-            trace_store<P, C, 7>(pl, tt, q, nmax, u, v, base, su, sv);
-            trace_store<P, C, 8>(pl, tt, q, nmax, u, v, base, su, sv);
-            trace_store<P, C, 9>(pl, tt, q, nmax, u, v, base, su, sv);
-        }
-    }
+    body_trace012<P, C>(pl, e, s, ed, sd, qmask, blockIdx.x, blockIdx.y, tr_smem);
 }
 
-// T_n(p, k) from T_{n-1}; p = (x 2^n, v).  Near operand at column 2x, far
-// operand at column 2x + 1 shifted by 2k' - 2^{n-1} along v (even for n >= 3,
-// so every thread handles the aligned pair v, v+1 with 2-wide accesses).
 template <int P, int C>
 __global__ void __launch_bounds__(128) k_merge_up(Plan pl, RowSplit rs, int n) {
-    int local;
-    const int q = find_quadrant(rs, blockIdx.x, local);   // row = (q, x, k)
-    const QuadGeom &g = pl.q[q];
-    const int v = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
-    if (v >= g.V) return;
-    const int K = (1 << n) + 1;
-    const int x = local / K, k = local - x * K;
-    const int m = n - 1, sm = 1 << m;
-    TLevel<P, C> Tm(pl, q, m), Tn(pl, q, n);
-    const int xn = 2 * x, xf = 2 * x + 1;
-    const bool far_ok = xf < g.Un[m];
-    Iv<P, C> o0, o1;
-    if ((k & 1) == 0) {                             // Eq. 18
-        const int kk = k >> 1;
-        Iv<P, C> n0, n1, f0, f1;
-        Tm.load2(xn, kk, v, n0, n1);
-        if (far_ok) Tm.load2_masked(xf, kk, v + 2 * kk - sm, g.V, f0, f1);
-        else f0 = f1 = Iv<P, C>::vacuum();
-        o0 = merge<P, C>(n0, f0);
-        o1 = merge<P, C>(n1, f1);
-    } else {                                        // Eqs. 19-20
-        const int kp = (k + 1) >> 1, km = (k - 1) >> 1;
-        Iv<P, C> np0, np1, nm0, nm1, fp0, fp1, fm0, fm1;
-        Tm.load2(xn, kp, v, np0, np1);
-        Tm.load2(xn, km, v, nm0, nm1);
-        if (far_ok) {
-            Tm.load2_masked(xf, km, v + 2 * kp - sm, g.V, fp0, fp1);
-            Tm.load2_masked(xf, kp, v + 2 * km - sm, g.V, fm0, fm1);
-        } else {
-            fp0 = fp1 = fm0 = fm1 = Iv<P, C>::vacuum();
-        }
-        o0 = blend<P, C>(merge<P, C>(nm0, fm0), merge<P, C>(np0, fp0));
-        o1 = blend<P, C>(merge<P, C>(nm1, fm1), merge<P, C>(np1, fp1));
-    }
-    Tn.store2(x, k, v, o0, o1);
+    body_merge_up<P, C>(pl, rs, n, blockIdx.x, blockIdx.y);
 }
 
-// R_n(p, i) = F_+ + F_-, p = (x 2^n, v), i = ip + 1/2, j_+ = 2ip+1, j_- = 2ip.
-// PAIR: two consecutive v per thread (all neighbour offsets even: n >= 1).
 template <int P, int C, bool PAIR>
 __global__ void __launch_bounds__(256) k_merge_down(Plan pl, RowSplit rs, int n) {
-    using A = typename Prec<P>::A;
-    constexpr int E = PAIR ? 2 : 1;
-    int local;
-    const int q = find_quadrant(rs, blockIdx.x, local);   // row = (q, x, ip)
-    const QuadGeom &g = pl.q[q];
-    const int v = E * (blockIdx.y * blockDim.x + threadIdx.x);
-    if (v >= g.V) return;
-    const int I = 1 << n;
-    const int x = local >> n, ip = local & (I - 1);
-    const bool top = (n + 1 >= g.N);               // R_N = 0
-    const int s = 1 << n;
-    A acc[E][C];
-#pragma unroll
-    for (int l = 0; l < E; ++l)
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[l][c] = A(0);
-    const A Ap = arc<P>(pl, n + 1, 2 * ip + 1), Am = arc<P>(pl, n + 1, 2 * ip);
-    RLevel<P, C> Rn(pl, q, n);
-    // R_{n+1}(xr, j, vq .. vq+E-1), zero outside [0, V)
-    auto loadR = [&](const RLevel<P, C> &R1, int xr, int j, int c, int vq, A (&r)[E]) {
-        if (PAIR) {
-            if (vq >= 0 && vq < g.V) {
-                R1.load2(xr, j, c, vq, r[0], r[E - 1]);
-                if (vq + 1 >= g.V) r[E - 1] = A(0);
-            } else {
-                r[0] = r[E - 1] = A(0);
-            }
-        } else {
-            r[0] = (vq >= 0 && vq < g.V) ? R1.load(xr, j, c, vq) : A(0);
-        }
-    };
-    auto loadT = [&](const TLevel<P, C> &T, int xx, int kk, Iv<P, C> (&t)[E]) {
-        if (PAIR) T.load2(xx, kk, v, t[0], t[E - 1]);
-        else t[0] = T.load(xx, kk, v);
-    };
-    if (x & 1) {
-        // Eq. 14: F_+- = A_{n+1}(j) T_n(p, i +- 1/2).L + T_n(p, i +- 1/2).T R_{n+1}(p + v_n(i +- 1/2), j)
-        TLevel<P, C> Tn(pl, q, n);
-        const int xq = (x + 1) >> 1;
-        const bool rq_ok = !top && xq < g.Un[n + 1];
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-            const int kk = sg == 0 ? ip + 1 : ip;
-            const int j = sg == 0 ? 2 * ip + 1 : 2 * ip;
-            const A Aj = sg == 0 ? Ap : Am;
-            Iv<P, C> t[E];
-            loadT(Tn, x, kk, t);
-            const int vq = v + 2 * kk - s;
-            RLevel<P, C> R1(pl, q, rq_ok ? n + 1 : n);
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                A r[E];
-                if (rq_ok) loadR(R1, xq, j, c, vq, r);
-                else
-#pragma unroll
-                    for (int l = 0; l < E; ++l) r[l] = A(0);
-#pragma unroll
-                for (int l = 0; l < E; ++l) acc[l][c] += fma(Aj, t[l].L[c], t[l].trans() * r[l]);
-            }
-        }
-    } else {
-        // Eqs. 15-17 with Sec. 4.1: F_+- = (R_{n+1}(p, j) + A T_{n+1}(p, 2i +- 1).L
-        //                                    + T_{n+1}(p, 2i +- 1).T R_{n+1}(p + v_{n+1}(2i +- 1), j)) / 2
-        TLevel<P, C> T1(pl, q, n + 1);
-        const int x2 = x >> 1;
-        const int s1 = 2 * s;
-        const bool r1_ok = !top && x2 + 1 < g.Un[n + 1];
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-            const int kk = sg == 0 ? 2 * ip + 2 : 2 * ip;
-            const int j = sg == 0 ? 2 * ip + 1 : 2 * ip;
-            const A Aj = sg == 0 ? Ap : Am;
-            Iv<P, C> t[E];
-            loadT(T1, x2, kk, t);
-            const int vq = v + 2 * kk - s1;
-            RLevel<P, C> R1(pl, q, top ? n : n + 1);
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                A r0[E], r1[E];
-#pragma unroll
-                for (int l = 0; l < E; ++l) { r0[l] = A(0); r1[l] = A(0); }
-                if (!top) {
-                    if (PAIR) R1.load2(x2, j, c, v, r0[0], r0[E - 1]);
-                    else r0[0] = R1.load(x2, j, c, v);
-                    if (r1_ok) loadR(R1, x2 + 1, j, c, vq, r1);
-                }
-#pragma unroll
-                for (int l = 0; l < E; ++l)
-                    acc[l][c] += A(0.5) * (r0[l] + fma(Aj, t[l].L[c], t[l].trans() * r1[l]));
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        if (PAIR) Rn.store2(x, ip, c, v, acc[0][c], acc[E - 1][c]);
-        else Rn.store(x, ip, c, v, acc[0][c]);
-    }
+    body_merge_down<P, C, PAIR>(pl, rs, n, blockIdx.x, blockIdx.y);
 }
 
-// F[c][y][x] = sum_q R_0^q(u_q + 1, v_q)   (Algorithm 1, Lighting, +1 offset).
 template <int P, int C, class OUT>
 __global__ void __launch_bounds__(256) k_fluence_sum(Plan pl, OUT *__restrict__ F) {
-    using A = typename Prec<P>::A;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= pl.W) return;
-    A acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = A(0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const QuadGeom &g = pl.q[q];
-        int u, v;
-        image_to_frame(q, pl.W, pl.H, x, y, u, v);
-        if (g.N >= 1 && u + 1 < g.U) {
-            RLevel<P, C> R0(pl, q, 0);
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] += R0.load(u + 1, 0, c, v);
-        }
-    }
-    const long long HW = (long long)pl.W * pl.H;
-#pragma unroll
-    for (int c = 0; c < C; ++c) F[c * HW + (long long)y * pl.W + x] = (OUT)acc[c];
+    body_fluence_sum<P, C, OUT>(pl, F, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -414,7 +95,7 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                     for (int n = 0; n <= 2; ++n) by += bytes_T(pl, q, n);
             dim3 grid((pl.W + TR_TILE - 1) / TR_TILE, (pl.H + TR_TILE - 1) / TR_TILE);
             rec->begin(K_TRACE012, 0, by);
-            k_trace012<P, C><<<grid, 256, smem, st>>>(pl, rt, ef, sf, ed, sd, qsel < 0 ? 15 : (1 << qsel));
+            k_trace012<P, C><<<grid, 256, smem, st>>>(pl, ef, sf, ed, sd, qsel < 0 ? 15 : (1 << qsel));
             rec->end();
             ++*launches;
         }

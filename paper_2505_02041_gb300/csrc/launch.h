@@ -53,6 +53,55 @@ struct Recorder {
 cudaError_t launch_forward(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
                            cudaStream_t st, int *launches, Recorder *rec);
 
+// ---------------------------------------------------------------------------
+// Batched persistent launch (kernels_batched.cu)
+// ---------------------------------------------------------------------------
+enum BatchKind {
+    BK_TRACE = 0, BK_MERGE_UP, BK_MERGE_DOWN2, BK_MERGE_DOWN1, BK_SUM, BK_ADJ_SUM, BK_ADJ_R2, BK_ADJ_R1,
+    BK_ADJ_T2, BK_ADJ_T1, BK_ADJ_MU, BK_ADJ_TRACE
+};
+
+// One stage of one scene: tickets first .. first+count-1.  Row kinds decode
+// an item j as (row j / nvb, v-block j % nvb); tile kinds as (x-block
+// j % nvb, y-block j / nvb).
+struct StageBlock {
+    long long first;
+    int count, scene, kind, level, nvb;
+    int rpi;               // rows per item (row kinds); item j covers rows (j / nvb) * rpi ..
+    long long rows;        // rows of the stage (row kinds)
+    int dep, dep_target;   // counter waited on (-1: none) and its final value
+    int own;               // counter published to
+    RowSplit rs;
+};
+
+struct BatchArgs {
+    const Plan *plans;
+    const long long *eoff, *soff;     // per-scene element offsets of [C][H][W] / [H][W] blocks
+    const StageBlock *blocks;
+    int nblocks;
+    long long total;                  // tickets
+    unsigned long long *ticket;
+    int *counters;
+    int *status;
+    int withhold;                     // test hook: a counter never published (-1: none)
+    long long spin_limit;             // polls before a wait gives up
+    const void *e, *s;
+    void *F;
+    const void *gF;
+    void *ge, *gs;
+};
+
+// Stage list of one scene: mode 0 = forward (with the fluence sum),
+// mode 1 = backward (forward levels recomputed, then every adjoint step).
+struct StageDesc {
+    int kind, level, count, nvb, rpi;
+    long long rows;
+    RowSplit rs;
+    double bytes;
+};
+void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out);
+cudaError_t launch_batched(const BatchArgs &a, int prec, int C, int blocks_per_sm, int mode, cudaStream_t st);
+
 // Host-side plan and table builders (hrc_runtime.cu).
 size_t align_up(size_t x, size_t a);
 int levels_for(int U, int cascades);

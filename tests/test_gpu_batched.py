@@ -1,0 +1,108 @@
+"""Batched persistent launch: many scenes of uneven size in one launch.
+
+Each scene's fluence and gradients must equal the single-scene path's
+(the same bodies run in both, so they agree to rounding), and the single-
+scene path is itself checked against the oracle; small scenes are also
+compared with the oracle directly.  The bounded dependency wait is tested
+by withholding one stage's publication: the launch must end with
+HRC_ETIMEOUT, and the context must stay usable.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_02041_gb300 import scenes
+from gpu_util import require_gpu, err_max, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(64, 64), (37, 23), (128, 96), (5, 7), (256, 256), (1, 9), (100, 130)]
+
+
+def _scenes(C, seed0=0):
+    es, ss = [], []
+    for i, (w, h) in enumerate(SIZES):
+        e, s = scenes.random_scene(w, h, C, seed0 + i)
+        es.append(torch.from_numpy(e))
+        ss.append(torch.from_numpy(s))
+    return es, ss
+
+
+@pytest.mark.parametrize("C,prec", [(1, "fp32"), (3, "fp32"), (2, "bf16")])
+def test_batched_forward_matches_single_and_oracle(C, prec):
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC, BatchedHRC
+    es, ss = _scenes(C)
+    b = BatchedHRC(SIZES, C, 0, prec)
+    e, s = b.pack(es, ss)
+    F = b.forward(e, s)
+    b.sync()
+    Fs = b.unpack(F)
+    for i, (w, h) in enumerate(SIZES):
+        h1 = HRC(w, h, C, 0, prec)
+        Fr = h1.forward(es[i].cuda(), ss[i].cuda())
+        assert err_max(Fs[i].cpu().numpy(), Fr.cpu().numpy()) <= 1e-6, i
+        if prec == "fp32" and w * h <= 128 * 96:
+            assert err_max(Fs[i].cpu().numpy(), oracle.fluence(es[i].numpy(), ss[i].numpy())) <= 1e-4, i
+
+
+def test_batched_backward_matches_single():
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC, BatchedHRC
+    C = 2
+    es, ss = _scenes(C, 10)
+    b = BatchedHRC(SIZES, C)
+    e, s = b.pack(es, ss)
+    b.forward(e, s)
+    gF = torch.randn(e.numel(), device="cuda")
+    ge, gs = b.backward(gF)
+    b.sync()
+    ges, gss = b.unpack(ge), b.unpack(gs, "s")
+    gFs = b.unpack(gF)
+    for i, (w, h) in enumerate(SIZES):
+        h1 = HRC(w, h, C)
+        h1.forward(es[i].cuda(), ss[i].cuda())
+        ge1, gs1 = h1.backward(gFs[i].contiguous())
+        assert err_max(ges[i].cpu().numpy(), ge1.cpu().numpy()) <= 1e-6, i
+        assert err_max(gss[i].cpu().numpy(), gs1.cpu().numpy()) <= 1e-6, i
+    # and one scene against the oracle's adjoint
+    ge_r, gs_r = oracle.fluence_adjoint(es[0].numpy(), ss[0].numpy(), gFs[0].cpu().numpy())
+    assert err_max(ges[0].cpu().numpy(), ge_r) <= 1e-4
+    assert err_max(gss[0].cpu().numpy(), gs_r) <= 1e-4
+
+
+def test_batched_tuning_does_not_change_results():
+    require_gpu()
+    from paper_2505_02041_gb300 import BatchedHRC
+    es, ss = _scenes(1, 20)
+    b = BatchedHRC(SIZES, 1)
+    e, s = b.pack(es, ss)
+    ref = b.forward(e, s).clone()
+    for bpsm in (1, 2):
+        for order in (0, 1):
+            b.tune(bpsm, order)
+            F = b.forward(e, s)
+            b.sync()
+            assert torch.equal(F, ref)
+
+
+def test_batched_withheld_dependency_times_out_and_recovers():
+    """A stage that never publishes: every wait on it gives up after the
+    short spin limit, the launch ends with HRC_ETIMEOUT, and the next
+    launch (hook removed) is correct."""
+    require_gpu()
+    from paper_2505_02041_gb300 import BatchedHRC, _lib
+    es, ss = _scenes(1, 30)
+    b = BatchedHRC(SIZES, 1)
+    e, s = b.pack(es, ss)
+    ref = b.forward(e, s).clone()
+    b.sync()
+    _lib.hrc_batched_debug(b.ctx, 1, 20000)      # stage 1 of scene 0 never publishes; ~3 ms limit
+    b.forward(e, s)
+    with pytest.raises(_lib.HRCError) as ex:
+        b.sync()
+    assert ex.value.status == _lib.HRC_ETIMEOUT
+    _lib.hrc_batched_debug(b.ctx, -1, 0)
+    F = b.forward(e, s)
+    b.sync()
+    assert torch.equal(F, ref)
