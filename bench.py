@@ -126,6 +126,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate_max(values, world, device=None):
+    """Element-wise max over ranks of per-rank totals (identity on one rank):
+    the job's time is its slowest rank's."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def per_frame(total_ms, steps, world):
+    """Whole-job ms per frame: every rank runs `steps` frames of its own
+    (independent replicas, weak scaling), all ranks in the max time."""
+    return total_ms / (steps * world)
+
+
 def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -273,15 +291,9 @@ def run_ours(args):
     _lib.hrc_set_timing(h.ctx, False)
     barrier()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms, sum(fb_ms)], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, fb_total = float(t[0].item()), float(t[1].item())
-    else:
-        fb_total = sum(fb_ms)
-    ms_per_frame = total_ms / (args.steps * world)
-    fb_mean = fb_total / (args.steps * world)
+    total_ms, fb_total = aggregate_max([sum(step_ms), sum(fb_ms)], world, dev)
+    ms_per_frame = per_frame(total_ms, args.steps, world)
+    fb_mean = per_frame(fb_total, args.steps, world)
 
     # end to end: host buffers through the C ABI, copies included
     e_h = torch.from_numpy(e_np).pin_memory()

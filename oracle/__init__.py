@@ -26,43 +26,75 @@ _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, out: str = _LIB, defines=()) -> str:
     """Compile the C oracle with gcc (OpenMP on)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", *[f"-D{d}" for d in defines],
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
+def _declare(L):
+    L.orc_trace.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D]
+    L.orc_trace.restype = None
+    L.orc_arc.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.orc_arc.restype = ctypes.c_double
+    L.orc_levels.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.orc_levels.restype = ctypes.c_int
+    L.orc_fluence.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+    L.orc_fluence.restype = None
+    L.orc_frame_level.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+    L.orc_frame_level.restype = ctypes.c_long
+    L.orc_fluence_adjoint.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, _D, _D]
+    L.orc_fluence_adjoint.restype = None
+    L.orc_bruteforce.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+    L.orc_bruteforce.restype = None
+    L.orc_num_threads.argtypes = []
+    L.orc_num_threads.restype = ctypes.c_int
+    L.orc_set_num_threads.argtypes = [ctypes.c_int]
+    L.orc_set_num_threads.restype = None
+    return L
 
 
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB)
-        L.orc_trace.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D]
-        L.orc_trace.restype = None
-        L.orc_arc.argtypes = [ctypes.c_int, ctypes.c_int]
-        L.orc_arc.restype = ctypes.c_double
-        L.orc_levels.argtypes = [ctypes.c_int, ctypes.c_int]
-        L.orc_levels.restype = ctypes.c_int
-        L.orc_fluence.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
-        L.orc_fluence.restype = None
-        L.orc_frame_level.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
-        L.orc_frame_level.restype = ctypes.c_long
-        L.orc_fluence_adjoint.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                          ctypes.c_int, _D, _D]
-        L.orc_fluence_adjoint.restype = None
-        L.orc_bruteforce.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
-        L.orc_bruteforce.restype = None
-        L.orc_num_threads.argtypes = []
-        L.orc_num_threads.restype = ctypes.c_int
-        L.orc_set_num_threads.argtypes = [ctypes.c_int]
-        L.orc_set_num_threads.restype = None
-        _lib = L
+        _lib = _declare(ctypes.CDLL(_LIB))
     return _lib
+
+
+class _Bound:
+    """The oracle API bound to one compiled variant of hrc_oracle.c."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def __getattr__(self, name):
+        fn = globals()[name]
+
+        def call(*a, **k):
+            global _lib
+            saved = _lib
+            _lib = self._h
+            try:
+                return fn(*a, **k)
+            finally:
+                _lib = saved
+        return call
+
+
+def load_variant(path: str, defines=()):
+    """Build (if needed) and load a variant of the oracle compiled with the
+    given preprocessor definitions; returns an object with this module's
+    functions (trace, fluence, fluence_adjoint, ...)."""
+    build(out=path, defines=defines)
+    return _Bound(_declare(ctypes.CDLL(path)))
 
 
 def _p(a: np.ndarray):

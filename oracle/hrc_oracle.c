@@ -36,6 +36,13 @@
 
 #define ORC_MAXL 16
 
+/* ORC_MUTANT selects a deliberately planted mistake (0 = none).  Only the
+ * mutation test builds the non-zero variants, to show that the pins catch
+ * a wrong sign, index, weight or operand anywhere in the method. */
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0
+#endif
+
 /* ---------------------------------------------------------------------------
  * Frame fields (Algorithm 1, Lighting: one orientation per quadrant).
  * ------------------------------------------------------------------------ */
@@ -52,7 +59,7 @@ static void frame_to_image(int q, int W, int H, long u, long v, long *x, long *y
     case 0: *x = u;         *y = v;         break;
     case 1: *x = W - 1 - u; *y = v;         break;
     case 2: *x = v;         *y = u;         break;
-    default: *x = v;        *y = H - 1 - u; break;
+    default: *x = v;        *y = ORC_MUTANT == 10 ? u : H - 1 - u; break;
     }
 }
 
@@ -176,7 +183,7 @@ static void trace(const Frame *f, double pu, double pv, double qu, double qv, do
         double sg = frame_sigma(f, pc[m].u, pc[m].v);
         double l = pc[m].len;
         double tau = sg * l;
-        double w = l * phi(tau);
+        double w = ORC_MUTANT == 7 ? l : l * phi(tau);
         for (int c = 0; c < f->C; ++c) L[c] += Tacc * frame_emis(f, c, pc[m].u, pc[m].v) * w;
         Tacc *= exp(-tau);
     }
@@ -222,7 +229,7 @@ static void trace_adjoint(const Frame *f, double pu, double pv, double qu, doubl
         for (int c = 0; c < C; ++c) {
             double em = f->e[((size_t)c * f->U + u) * f->V + v];
             ge[((size_t)c * f->U + u) * f->V + v] += gL[c] * P[m] * l * phi(sg * l);
-            g += gL[c] * (P[m] * em * l * l * dphi(sg * l) - l * S[m * C + c]);
+            g += gL[c] * (P[m] * em * l * l * dphi(sg * l) - (ORC_MUTANT == 13 ? -l : l) * S[m * C + c]);
         }
         g -= gT * l * Ttot;
         gs[u * f->V + v] += g;
@@ -300,7 +307,7 @@ static void merge(int C, const double *a, const double *b, double *out)
     double Ta = a ? a[C] : 1.0, Tb = b ? b[C] : 1.0;
     for (int c = 0; c < C; ++c) {
         double La = a ? a[c] : 0.0, Lb = b ? b[c] : 0.0;
-        out[c] = La + Ta * Lb;
+        out[c] = La + (ORC_MUTANT == 8 ? Tb : Ta) * Lb;
     }
     out[C] = Ta * Tb;
 }
@@ -350,16 +357,16 @@ static void hrc_frame(const Frame *f, int cascades, Cascades *cs)
                     if ((k & 1) == 0) {
                         long kk = k / 2;   /* T_n(p, 2kk) = Merge(T_m(p,kk), T_m(p+v_m(kk),kk)) */
                         merge(C, T_get(cs, m, pu, pv, kk),
-                              T_get(cs, m, pu + sm, pv + 2 * kk - sm, kk), o);
+                              T_get(cs, m, pu + sm, ORC_MUTANT == 1 ? pv - 2 * kk + sm : pv + 2 * kk - sm, kk), o);
                     } else {
                         long kp = (k + 1) / 2, km = (k - 1) / 2;   /* kappa +- 1/2 */
                         /* F_+ = Merge(T_m(p, kappa+1/2), T_m(p + v_m(kappa+1/2), kappa-1/2)) */
                         merge(C, T_get(cs, m, pu, pv, kp),
-                              T_get(cs, m, pu + sm, pv + 2 * kp - sm, km), Fp);
+                              T_get(cs, m, pu + sm, pv + 2 * kp - sm, ORC_MUTANT == 2 ? kp : km), Fp);
                         /* F_- = Merge(T_m(p, kappa-1/2), T_m(p + v_m(kappa-1/2), kappa+1/2)) */
                         merge(C, T_get(cs, m, pu, pv, km),
                               T_get(cs, m, pu + sm, pv + 2 * km - sm, kp), Fm);
-                        for (int c = 0; c <= C; ++c) o[c] = 0.5 * (Fm[c] + Fp[c]);   /* Eq. 20 */
+                        for (int c = 0; c <= C; ++c) o[c] = ORC_MUTANT == 3 ? Fp[c] : 0.5 * (Fm[c] + Fp[c]);   /* Eq. 20 */
                     }
                 }
         }
@@ -376,9 +383,11 @@ static void hrc_frame(const Frame *f, int cascades, Cascades *cs)
                     double *o = cs->R[n] + R_index(cs, n, x, ip, y);
                     /* j_+ = 2i + 1/2 -> index 2ip+1; j_- = 2i - 1/2 -> 2ip */
                     long jp = 2 * ip + 1, jm = 2 * ip;
-                    double Ap = orc_arc(n + 1, (int)jp), Am = orc_arc(n + 1, (int)jm);
+                    double Ap = orc_arc(ORC_MUTANT == 14 ? n : n + 1, (int)(ORC_MUTANT == 14 ? ip : jp));
+                    double Am = orc_arc(ORC_MUTANT == 14 ? n : n + 1, (int)(ORC_MUTANT == 14 ? ip : jm));
+                    if (ORC_MUTANT == 4) Ap = Am;
                     for (int c = 0; c < C; ++c) o[c] = 0.0;
-                    if (x & 1) {
+                    if (ORC_MUTANT == 11 ? !(x & 1) && x > 0 : (x & 1)) {
                         /* Eq. 14: F_+- = Merge_r(A x T_n(p, i +- 1/2), R_{n+1}(q_+-, j_+-)),
                          * q_+- = p + v_n(i +- 1/2); i + 1/2 = ip + 1, i - 1/2 = ip. */
                         for (int sgn = 0; sgn < 2; ++sgn) {
@@ -401,10 +410,10 @@ static void hrc_frame(const Frame *f, int cascades, Cascades *cs)
                             double A = sgn == 0 ? Ap : Am;
                             const double *r0 = R_get(cs, n + 1, pu, pv, j);
                             const double *t = T_get(cs, n + 1, pu, pv, kk);
-                            const double *r1 = R_get(cs, n + 1, pu + s1, pv + 2 * kk - s1, j);
+                            const double *r1 = R_get(cs, n + 1, pu + s1, ORC_MUTANT == 9 ? pv + kk - s : pv + 2 * kk - s1, j);
                             double Tt = t ? t[C] : 1.0;
                             for (int c = 0; c < C; ++c)
-                                o[c] += 0.5 * ((r0 ? r0[c] : 0.0) + A * (t ? t[c] : 0.0) +
+                                o[c] += 0.5 * ((ORC_MUTANT == 5 ? 2.0 : 1.0) * (r0 ? r0[c] : 0.0) + A * (t ? t[c] : 0.0) +
                                                Tt * (r1 ? r1[c] : 0.0));
                         }
                     }
@@ -443,7 +452,7 @@ void orc_fluence(const double *e, const double *s, int C, int W, int H, int casc
                 for (long v = 0; v < f.V; ++v) {
                     long x, y;
                     frame_to_image(q, W, H, u, v, &x, &y);
-                    const double *r = R_get(&cs, 0, u + 1, v, 0);
+                    const double *r = R_get(&cs, 0, ORC_MUTANT == 6 ? u : u + 1, v, 0);
                     if (!r) continue;
                     for (int c = 0; c < C; ++c) F[((size_t)c * H + y) * W + x] += r[c];
                 }
@@ -544,7 +553,7 @@ void orc_fluence_adjoint(const double *e, const double *s, const double *gF, int
                                 double Tt = t ? t[C] : 1.0;
                                 if (r0) {
                                     double *gr = gR[n + 1] + R_index(&cs, n + 1, pu >> (n + 1), j, pv);
-                                    for (int c = 0; c < C; ++c) gr[c] += 0.5 * g[c];
+                                    for (int c = 0; c < C; ++c) gr[c] += (ORC_MUTANT == 12 ? 1.0 : 0.5) * g[c];
                                 }
                                 if (t) {
                                     double *gt = gT[n + 1] + T_index(&cs, n + 1, pu >> (n + 1), kk, pv);

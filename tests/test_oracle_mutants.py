@@ -1,0 +1,99 @@
+"""Mutation check of the oracle's pins.
+
+Each variant of hrc_oracle.c compiled with -DORC_MUTANT=k carries one
+planted mistake (a flipped sign, a swapped index, a dropped weight, a wrong
+operand, a wrong quadrant map, a broken adjoint term).  The pins used
+against the real oracle -- Fig. 2, the uniform slab, the independent
+recursive formulation, the uniform emissive medium and central
+differences -- must reject every variant.  The mistakes are planted in the
+oracle, on the CPU; the real oracle passes the same checks.
+"""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import recursive
+from paper_2505_02041_gb300 import scenes
+from conftest import read_golden
+
+MUTANTS = {
+    1: "Eq. 18 far-operand offset sign",
+    2: "Eq. 19 far-operand direction",
+    3: "Eq. 20 average dropped",
+    4: "Eq. 14 arc of the wrong half-cone",
+    5: "Eq. 15 weight of R_{n+1}(p, j)",
+    6: "fluence sum without the +1 offset",
+    7: "Trace piece weight without phi",
+    8: "Merge with the far transmittance",
+    9: "Eq. 17 offset on the wrong level",
+    10: "quadrant frame map of -y",
+    11: "odd / even x swapped",
+    12: "adjoint weight of R_{n+1}(p, j)",
+    13: "adjoint sign of the suffix-radiance term",
+    14: "Eq. 14 arcs of level n",
+}
+
+
+def failed_pins(O):
+    """Names of the pins that variant O fails."""
+    bad = []
+    g = {r[0]: float(r[1]) for r in read_golden("fig2_worked_example.txt")}
+    s = np.zeros((1, 3))
+    e = np.zeros((1, 1, 3))
+    s[0, :2] = math.log(2.0)
+    e[0, 0, :2] = 4.0 * math.log(2.0)
+    L, T = O.trace(e, s, (0.0, 0.5), (2.0, 0.5))
+    if abs(L[0] - g["L_a_d"]) > 1e-12 or abs(T - g["T_a_d"]) > 1e-12:
+        bad.append("fig2")
+    sg, em = 0.7, 1.3
+    ss = np.full((16, 16), sg)
+    ee = np.full((1, 16, 16), em)
+    L, T = O.trace(ee, ss, (3.2, 4.1), (9.7, 11.3))
+    d = math.hypot(6.5, 7.2)
+    if abs(L[0] - em / sg * -math.expm1(-sg * d)) > 1e-12:
+        bad.append("slab")
+    e1, s1 = scenes.random_scene(12, 10, 1, 77)
+    if np.max(np.abs(O.fluence(e1, s1) - recursive.fluence(e1, s1))) > 1e-10:
+        bad.append("recursive")
+    for n in (3, 4):
+        if np.max(np.abs(O.frame_level(e1, s1, 0, "T", n) - recursive.frame_T(e1, s1, 0, n))) > 1e-10:
+            bad.append(f"T{n}")
+    X = 64
+    c = 1.7
+    Fu = O.fluence(np.full((1, X, X), c), np.ones((X, X)))
+    if np.max(np.abs(Fu[0, 28:36, 28:36] - 2 * math.pi * c)) > 1e-9:
+        bad.append("uniform")
+    e2, s2 = scenes.random_scene(10, 8, 1, 78)
+    e2 = e2.astype(np.float64)
+    s2 = s2.astype(np.float64)
+    gF = np.random.default_rng(5).normal(size=e2.shape)
+    ge, gs = O.fluence_adjoint(e2, s2, gF)
+    h = 1e-4
+    for (y, x) in [(3, 4), (6, 2)]:
+        sp, sm = s2.copy(), s2.copy()
+        sp[y, x] += h
+        sm[y, x] -= h
+        fd = (np.sum(gF * O.fluence(e2, sp)) - np.sum(gF * O.fluence(e2, sm))) / (2 * h)
+        if abs(fd - gs[y, x]) > 1e-6 * max(1.0, abs(fd)):
+            bad.append("fd")
+            break
+    return bad
+
+
+def test_real_oracle_passes_every_pin():
+    assert failed_pins(oracle) == []
+
+
+@pytest.mark.parametrize("k", sorted(MUTANTS))
+def test_every_planted_mistake_is_caught(k):
+    path = os.path.join(tempfile.gettempdir(), f"liboracle_mutant{k}_{os.getpid()}.so")
+    try:
+        O = oracle.load_variant(path, defines=[f"ORC_MUTANT={k}"])
+        assert failed_pins(O), f"mutant {k} ({MUTANTS[k]}) passed every pin"
+    finally:
+        if os.path.exists(path):
+            os.remove(path)
