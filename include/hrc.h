@@ -81,6 +81,15 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec);
  *     larger launches). */
 hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule);
 
+/* Autotuner: times every launch configuration (schedule 0/1 x one or two
+ * element groups per thread in the merge kernels) with forward passes over
+ * the context's own staging buffers (the timing does not depend on the
+ * data), keeps the fastest, and writes its ms per frame to *best_ms (may be
+ * NULL).  Synchronous.  Results do not depend on the configuration.
+ * Single-scene contexts in fp32 / fp16 / bf16; the borrowed forward inputs
+ * are forgotten (run hrc_fluence again before hrc_fluence_backward). */
+hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms);
+
 /* Forward pass, Algorithm 1 (Lighting) without the Eq. 21 blur:
  * out[c][y][x] = sum over the four quadrant frames of R_0([u+1, v], 1/2).
  * emission [C][H][W], sigma_t [H][W], out [C][H][W]: device fp32.

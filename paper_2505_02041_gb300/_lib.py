@@ -27,6 +27,7 @@ SIGNATURES = [
     ("hrc_set_stream", _i, [_vp, _vp]),
     ("hrc_set_precision", _i, [_vp, _i]),
     ("hrc_set_schedule", _i, [_vp, _i]),
+    ("hrc_autotune", _i, [_vp, ctypes.POINTER(ctypes.c_float)]),
     ("hrc_fluence", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_fluence_host", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_fluence_backward", _i, [_vp, _vp, _vp, _vp]),
@@ -112,6 +113,12 @@ def hrc_set_precision(ctx, prec: int):
 
 def hrc_set_schedule(ctx, schedule: int):
     check(load().hrc_set_schedule(ctx, schedule), ctx)
+
+
+def hrc_autotune(ctx) -> float:
+    ms = ctypes.c_float()
+    check(load().hrc_autotune(ctx, ctypes.byref(ms)), ctx)
+    return ms.value
 
 
 def hrc_fluence(ctx, emission, sigma_t, out):

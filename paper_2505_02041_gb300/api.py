@@ -123,6 +123,14 @@ class HRC:
             return dst.view(Un, (1 << n) + 1, V, self.C + 1)
         return dst.view(Un, 1 << n, V, self.C)
 
+    def autotune(self) -> float:
+        """Pick the fastest launch configuration for this grid (see
+        hrc_autotune); returns its forward ms per frame."""
+        self._stream()
+        ms = _lib.hrc_autotune(self.ctx)
+        self._borrowed = (None, None)
+        return ms
+
     def launch_count(self) -> int:
         return _lib.hrc_last_launch_count(self.ctx)
 

@@ -25,7 +25,10 @@
 // Each body processes one block of work at an explicit block index (bx, by).
 #pragma once
 
+#include <type_traits>
+
 #include "hrc_internal.cuh"
+#include "pair_tile.cuh"
 #include "trace_shapes.cuh"
 
 namespace hrc {
@@ -325,44 +328,26 @@ __device__ __forceinline__ double dw_dsigma(double sg, double len, double t) {
     return (t * (1.0 + tau) - 1.0) / (sg * sg);
 }
 
-constexpr int TB_TILE = 32, TB_HALO = 4, TB_REG = TB_TILE + 2 * TB_HALO, TB_PITCH = TB_REG + 1;
-constexpr int TB_PLANE = TB_REG * TB_PITCH;
-constexpr int TB_AP = TB_TILE + 1;
-
-template <class A, int C> struct AdjTile {
-    A *s, *t, *w, *e, *acc;     // s [PLANE], t/w [3][PLANE], e [C][PLANE], acc [C+1][TILE][TILE+1]
-    __device__ __forceinline__ explicit AdjTile(unsigned char *smem) {
-        s = reinterpret_cast<A *>(smem);
-        t = s + TB_PLANE;
-        w = t + 3 * TB_PLANE;
-        e = w + 3 * TB_PLANE;
-        acc = e + C * TB_PLANE;
-    }
-    static constexpr size_t bytes() { return sizeof(A) * ((7 + C) * TB_PLANE + (C + 1) * TB_TILE * TB_AP); }
-};
-
-template <class A> __device__ __forceinline__ void piece_factors_b(A sg, A len, A &t, A &w) {
-    const A m = fexpm1(-sg * len);
-    t = A(1) + m;
-    w = sg != A(0) ? -m / sg : len;
-}
-
 // Re-trace pieces M .. END-1 of a ray; piece J is the one at the gathering
 // pixel.  Accumulates the attenuated radiance of all pieces (Ltot) and of
-// pieces <= J (Lle), and records P_J, the piece factors of J and e_J.
+// pieces <= J (Lle), and records P_J, the half-piece factors of J, its
+// extinction and emission.
 template <class A, int C, int M, int END, int J>
-__device__ __forceinline__ void adj_retrace(const AdjTile<A, C> &tt, int base, int su, int sv, A &Pp, A (&Ltot)[C],
+__device__ __forceinline__ void adj_retrace(const PairTile<A, C> &tt, int base, int su, A &Pp, A (&Ltot)[C],
                                             A (&Lle)[C], A &Pj, A &tj, A &wj, A &sj, A (&ej)[C]) {
     if constexpr (M < END) {
         using pc = PieceAt<M>;
-        const int o = base + pc::du * su + pc::dv * sv;
-        A t = tt.t[pc::cls * TB_PLANE + o];
-        A w = tt.w[pc::cls * TB_PLANE + o];
+        const int o = base + pc::du * su + pc::dv;
+        A t, w, em[C], sg;
+        tt.piece(pc::cls, o, t, w);
+        tt.emis(o, em, sg);
         if constexpr (M == J) {
-            tj = t;           // half-piece factors of the pixel's own piece
+            tj = t;
             wj = w;
-            sj = tt.s[o];
+            sj = sg;
             Pj = Pp;
+#pragma unroll
+            for (int c = 0; c < C; ++c) ej[c] = em[c];
         }
         if constexpr (pc::full != 0) {
             w = w * (A(1) + t);
@@ -371,34 +356,32 @@ __device__ __forceinline__ void adj_retrace(const AdjTile<A, C> &tt, int base, i
         const A pw = Pp * w;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const A em = tt.e[c * TB_PLANE + o];
-            Ltot[c] = fma(pw, em, Ltot[c]);
-            if constexpr (M <= J) Lle[c] = fma(pw, em, Lle[c]);
-            if constexpr (M == J) ej[c] = em;
+            Ltot[c] = fma(pw, em[c], Ltot[c]);
+            if constexpr (M <= J) Lle[c] = fma(pw, em[c], Lle[c]);
         }
         Pp *= t;
-        adj_retrace<A, C, M + 1, END, J>(tt, base, su, sv, Pp, Ltot, Lle, Pj, tj, wj, sj, ej);
+        adj_retrace<A, C, M + 1, END, J>(tt, base, su, Pp, Ltot, Lle, Pj, tj, wj, sj, ej);
     }
 }
 
 template <int P, int C, int R, int J>
-__device__ __forceinline__ void adj_gather(const Plan &pl, const AdjTile<typename Prec<P>::A, C> &tt, int q, int nmax,
-                                           int V, int us, int vs, int base, int su, int sv,
+__device__ __forceinline__ void adj_gather(const Plan &pl, const PairTile<typename Prec<P>::A, C> &tt, int q, int nmax,
+                                           int V, int us, int vs, int base, int su,
                                            typename Prec<P>::A (&dE)[C], typename Prec<P>::A &dS) {
     using A = typename Prec<P>::A;
     using ray = RayAt<R>;
     if constexpr (J < ray::end) {
         using pc = PieceAt<J>;
         const int up = us - pc::du, vp = vs - pc::dv;
-        if (ray::n <= nmax && up >= 0 && !(up & ((1 << ray::n) - 1)) && vp >= 0 && vp < V) {
+        if (up >= 0 && !(up & ((1 << ray::n) - 1)) && vp >= 0 && vp < V) {
             A gL[C], gT;
             GTLevel<P, C>(pl, q, ray::n).load(up >> ray::n, ray::k, vp, gL, gT);
-            const int pbase = base - pc::du * su - pc::dv * sv;
+            const int pbase = base - pc::du * su - pc::dv;
             A Pp = A(1), Pj = A(0), tj = A(1), wj = A(0), sj = A(0);
             A Ltot[C], Lle[C], ej[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) { Ltot[c] = A(0); Lle[c] = A(0); ej[c] = A(0); }
-            adj_retrace<A, C, ray::begin, ray::end, J>(tt, pbase, su, sv, Pp, Ltot, Lle, Pj, tj, wj, sj, ej);
+            adj_retrace<A, C, ray::begin, ray::end, J>(tt, pbase, su, Pp, Ltot, Lle, Pj, tj, wj, sj, ej);
             const A lh = class_len<A>(pc::cls);
             A d = dw_dsigma(sj, lh, tj);
             A wq = wj, len = lh;
@@ -415,84 +398,85 @@ __device__ __forceinline__ void adj_gather(const Plan &pl, const AdjTile<typenam
             }
             dS += g;
         }
-        adj_gather<P, C, R, J + 1>(pl, tt, q, nmax, V, us, vs, base, su, sv, dE, dS);
+        adj_gather<P, C, R, J + 1>(pl, tt, q, nmax, V, us, vs, base, su, dE, dS);
     }
 }
 
 template <int P, int C, int R>
-__device__ __forceinline__ void adj_ray(const Plan &pl, const AdjTile<typename Prec<P>::A, C> &tt, int q, int nmax,
-                                        int V, int us, int vs, int base, int su, int sv,
+__device__ __forceinline__ void adj_ray(const Plan &pl, const PairTile<typename Prec<P>::A, C> &tt, int q, int nmax,
+                                        int V, int us, int vs, int base, int su,
                                         typename Prec<P>::A (&dE)[C], typename Prec<P>::A &dS) {
     if constexpr (R < HRC_MAXRAY) {
-        if (RayAt<R>::n <= nmax) adj_gather<P, C, R, RayAt<R>::begin>(pl, tt, q, nmax, V, us, vs, base, su, sv, dE, dS);
-        adj_ray<P, C, R + 1>(pl, tt, q, nmax, V, us, vs, base, su, sv, dE, dS);
+        if (RayAt<R>::n <= nmax) adj_gather<P, C, R, RayAt<R>::begin>(pl, tt, q, nmax, V, us, vs, base, su, dE, dS);
+        adj_ray<P, C, R + 1>(pl, tt, q, nmax, V, us, vs, base, su, dE, dS);
     }
 }
 
+// Shared memory of the adjoint trace: the pair tile, then (pair 0 only) a
+// transposed accumulator so that dL/de and dL/dsigma leave coalesced.
+template <class A, int C> constexpr size_t adj_trace_smem() {
+    return PairTile<A, C>::bytes() + sizeof(A) * (C + 1) * PT_V * (PT_U + 1);
+}
+
+// dL/de and dL/dsigma of quadrant pair `pair` for one tile.  Each thread
+// owns the two pixels of its tile columns for both frames of the pair and
+// accumulates in registers.  Pair 0 writes the image gradients, pair 1
+// (launched after it) adds to them.
 template <int P, int C, class IN>
 __device__ __forceinline__ void body_adj_trace(const Plan &pl, const IN *__restrict__ e, const IN *__restrict__ s,
-                                               IN *__restrict__ ge, IN *__restrict__ gs, int bx, int by,
-                                               unsigned char *tb_smem) {
+                                               IN *__restrict__ ge, IN *__restrict__ gs, int pair, int bx, int by,
+                                               unsigned char *smem) {
     using A = typename Prec<P>::A;
-    AdjTile<A, C> tt(tb_smem);
+    PairTile<A, C> tt(smem);
+    A *acc = reinterpret_cast<A *>(smem + PairTile<A, C>::bytes());   // [C+1][PT_V][PT_U+1]
     const int W = pl.W, H = pl.H;
-    const int x0 = bx * TB_TILE, y0 = by * TB_TILE;
     const long long HW = (long long)W * H;
-    for (int i = threadIdx.x; i < TB_REG * TB_REG; i += blockDim.x) {
-        const int ry = i / TB_REG, rx = i - ry * TB_REG;
-        const int x = x0 - TB_HALO + rx, y = y0 - TB_HALO + ry;
-        const bool in = x >= 0 && x < W && y >= 0 && y < H;
-        const long long pix = (long long)y * W + x;
-        const int o = ry * TB_PITCH + rx;
-        const A sg = in ? A(s[pix]) : A(0);
-        tt.s[o] = sg;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            A tc, wc;
-            piece_factors_b<A>(sg, class_len<A>(c), tc, wc);
-            tt.t[c * TB_PLANE + o] = tc;
-            tt.w[c * TB_PLANE + o] = wc;
-        }
-#pragma unroll
-        for (int c = 0; c < C; ++c) tt.e[c * TB_PLANE + o] = in ? A(e[c * HW + pix]) : A(0);
-    }
-    for (int i = threadIdx.x; i < (C + 1) * TB_TILE * TB_AP; i += blockDim.x) tt.acc[i] = A(0);
+    const int x0 = pair == 0 ? bx * PT_U : bx * PT_V;
+    const int y0 = pair == 0 ? by * PT_V : by * PT_U;
+    tt.stage(pair, W, H, x0, y0, e, s);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = 0; q < 4; ++q) {
-        const QuadGeom &g = pl.q[q];
-        const int nmax = g.N < 2 ? g.N : 2;
-        const bool xu = q < 2;
-        const int tu = xu ? x0 : y0, tv = xu ? y0 : x0;
-        const int ext_u = xu ? W : H;
-        const int sgn = (q == 0 || q == 2) ? 1 : -1;
-        const int su = sgn * (xu ? 1 : TB_PITCH), sv = xu ? TB_PITCH : 1;
-        const int vs = tv + lane;
-        for (int i = 0; i < TB_TILE / 8; ++i) {
-            const int c = 8 * i + ((warp + i) & 7);
-            if (g.N < 1 || tu + c >= ext_u || vs >= g.V) continue;
-            const int us = (q == 0 || q == 2) ? tu + c : ext_u - 1 - (tu + c);
-            const int base = xu ? (TB_HALO + lane) * TB_PITCH + TB_HALO + c
-                                : (TB_HALO + c) * TB_PITCH + TB_HALO + lane;
-            A dE[C], dS = A(0);
+#pragma unroll 1
+    for (int i = 0; i < 2; ++i) {
+        const int c = 8 * i + ((warp + i) & 7);
+        A dE[C], dS = A(0);
 #pragma unroll
-            for (int cc = 0; cc < C; ++cc) dE[cc] = A(0);
-            adj_ray<P, C, 0>(pl, tt, q, nmax, g.V, us, vs, base, su, sv, dE, dS);
-            const int ix = xu ? c : lane, iy = xu ? lane : c;
-#pragma unroll
-            for (int cc = 0; cc < C; ++cc) tt.acc[(cc * TB_TILE + iy) * TB_AP + ix] += dE[cc];
-            tt.acc[(C * TB_TILE + iy) * TB_AP + ix] += dS;
+        for (int cc = 0; cc < C; ++cc) dE[cc] = A(0);
+#pragma unroll 1
+        for (int qq = 0; qq < 2; ++qq) {
+            const int q = 2 * pair + qq;
+            const QuadGeom &g = pl.q[q];
+            if (g.N < 1) continue;
+            const int nmax = g.N < 2 ? g.N : 2;
+            const PairGeom pg = pair_geom(pl, q, x0, y0, c, lane);
+            if (!pg.valid) continue;
+            adj_ray<P, C, 0>(pl, tt, q, nmax, g.V, pg.u, pg.v, pg.base, pg.su, dE, dS);
         }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < TB_TILE * TB_TILE; i += blockDim.x) {
-        const int iy = i / TB_TILE, ix = i - iy * TB_TILE;
-        const int x = x0 + ix, y = y0 + iy;
+        // image pixel: pair 0 (c along x, lane along y); pair 1 (c along y, lane along x)
+        const int x = pair == 0 ? x0 + c : x0 + lane, y = pair == 0 ? y0 + lane : y0 + c;
         if (x >= W || y >= H) continue;
         const long long pix = (long long)y * W + x;
+        if (pair == 0) {
 #pragma unroll
-        for (int cc = 0; cc < C; ++cc) ge[cc * HW + pix] = IN(tt.acc[(cc * TB_TILE + iy) * TB_AP + ix]);
-        gs[pix] = IN(tt.acc[(C * TB_TILE + iy) * TB_AP + ix]);
+            for (int cc = 0; cc < C; ++cc) acc[(cc * PT_V + lane) * (PT_U + 1) + c] = dE[cc];
+            acc[(C * PT_V + lane) * (PT_U + 1) + c] = dS;
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < C; ++cc) ge[cc * HW + pix] = IN(A(ge[cc * HW + pix]) + dE[cc]);
+            gs[pix] = IN(A(gs[pix]) + dS);
+        }
+    }
+    if (pair == 0) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < PT_U * PT_V; k += blockDim.x) {
+            const int ly = k / PT_U, lx = k - ly * PT_U;
+            const int x = x0 + lx, y = y0 + ly;
+            if (x >= W || y >= H) continue;
+            const long long pix = (long long)y * W + x;
+#pragma unroll
+            for (int cc = 0; cc < C; ++cc) ge[cc * HW + pix] = IN(acc[(cc * PT_V + ly) * (PT_U + 1) + lx]);
+            gs[pix] = IN(acc[(C * PT_V + ly) * (PT_U + 1) + lx]);
+        }
     }
 }
 

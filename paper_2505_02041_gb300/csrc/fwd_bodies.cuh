@@ -17,7 +17,10 @@
 // re-enters, and nothing outside the grid emits.
 #pragma once
 
+#include <type_traits>
+
 #include "hrc_internal.cuh"
+#include "pair_tile.cuh"
 #include "trace_shapes.cuh"
 
 namespace hrc {
@@ -177,44 +180,57 @@ __device__ __forceinline__ void body_trace012(const Plan &pl, const float *__res
 
 // T_n(p, k) from T_{n-1}; p = (x 2^n, v).  Near operand at column 2x, far
 // operand at column 2x + 1 shifted by 2k' - 2^{n-1} along v (even for n >= 3,
-// so every thread handles the aligned pair v, v+1 with 2-wide accesses).
-template <int P, int C>
+// so every thread handles aligned pairs v, v+1 with 2-wide accesses).  A
+// thread handles G such pairs, blockDim.x pairs apart, and issues all their
+// loads before any arithmetic.
+template <int P, int C, int G = 1>
 __device__ __forceinline__ void body_merge_up(const Plan &pl, const RowSplit &rs, int n, long long bx, int by) {
     int local;
     const int q = find_quadrant(rs, bx, local);   // row = (q, x, k)
     const QuadGeom &g = pl.q[q];
-    const int v = 2 * (by * blockDim.x + threadIdx.x);
-    if (v >= g.V) return;
     const int K = (1 << n) + 1;
     const int x = local / K, k = local - x * K;
     const int m = n - 1, sm = 1 << m;
     TLevel<P, C> Tm(pl, q, m), Tn(pl, q, n);
     const int xn = 2 * x, xf = 2 * x + 1;
     const bool far_ok = xf < g.Un[m];
-    Iv<P, C> o0, o1;
+    int v[G];
+#pragma unroll
+    for (int gi = 0; gi < G; ++gi) v[gi] = 2 * ((by * G + gi) * blockDim.x + threadIdx.x);
     if ((k & 1) == 0) {                             // Eq. 18
         const int kk = k >> 1;
-        Iv<P, C> n0, n1, f0, f1;
-        Tm.load2(xn, kk, v, n0, n1);
-        if (far_ok) Tm.load2_masked(xf, kk, v + 2 * kk - sm, g.V, f0, f1);
-        else f0 = f1 = Iv<P, C>::vacuum();
-        o0 = merge<P, C>(n0, f0);
-        o1 = merge<P, C>(n1, f1);
+        Iv<P, C> n0[G], n1[G], f0[G], f1[G];
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi) {
+            if (v[gi] >= g.V) continue;
+            Tm.load2(xn, kk, v[gi], n0[gi], n1[gi]);
+            if (far_ok) Tm.load2_masked(xf, kk, v[gi] + 2 * kk - sm, g.V, f0[gi], f1[gi]);
+            else f0[gi] = f1[gi] = Iv<P, C>::vacuum();
+        }
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi)
+            if (v[gi] < g.V) Tn.store2(x, k, v[gi], merge<P, C>(n0[gi], f0[gi]), merge<P, C>(n1[gi], f1[gi]));
     } else {                                        // Eqs. 19-20
         const int kp = (k + 1) >> 1, km = (k - 1) >> 1;
-        Iv<P, C> np0, np1, nm0, nm1, fp0, fp1, fm0, fm1;
-        Tm.load2(xn, kp, v, np0, np1);
-        Tm.load2(xn, km, v, nm0, nm1);
-        if (far_ok) {
-            Tm.load2_masked(xf, km, v + 2 * kp - sm, g.V, fp0, fp1);
-            Tm.load2_masked(xf, kp, v + 2 * km - sm, g.V, fm0, fm1);
-        } else {
-            fp0 = fp1 = fm0 = fm1 = Iv<P, C>::vacuum();
+        Iv<P, C> np0[G], np1[G], nm0[G], nm1[G], fp0[G], fp1[G], fm0[G], fm1[G];
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi) {
+            if (v[gi] >= g.V) continue;
+            Tm.load2(xn, kp, v[gi], np0[gi], np1[gi]);
+            Tm.load2(xn, km, v[gi], nm0[gi], nm1[gi]);
+            if (far_ok) {
+                Tm.load2_masked(xf, km, v[gi] + 2 * kp - sm, g.V, fp0[gi], fp1[gi]);
+                Tm.load2_masked(xf, kp, v[gi] + 2 * km - sm, g.V, fm0[gi], fm1[gi]);
+            } else {
+                fp0[gi] = fp1[gi] = fm0[gi] = fm1[gi] = Iv<P, C>::vacuum();
+            }
         }
-        o0 = blend<P, C>(merge<P, C>(nm0, fm0), merge<P, C>(np0, fp0));
-        o1 = blend<P, C>(merge<P, C>(nm1, fm1), merge<P, C>(np1, fp1));
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi)
+            if (v[gi] < g.V)
+                Tn.store2(x, k, v[gi], blend<P, C>(merge<P, C>(nm0[gi], fm0[gi]), merge<P, C>(np0[gi], fp0[gi])),
+                          blend<P, C>(merge<P, C>(nm1[gi], fm1[gi]), merge<P, C>(np1[gi], fp1[gi])));
     }
-    Tn.store2(x, k, v, o0, o1);
 }
 
 // R_n(p, i) = F_+ + F_-, p = (x 2^n, v), i = ip + 1/2, j_+ = 2ip+1, j_- = 2ip.

@@ -45,6 +45,7 @@ struct QuadGeom {
 struct Plan {
     int W, H, C, prec;
     int sched;                       // 0: each launch covers all four frames; 1: frame by frame
+    int mgroups;                     // merge kernels: element groups per thread (1 or 2)
     long long arcs_off;              // byte offset: float A[2^n + j] for level n (n >= 1)
     long long arcs_off_d;            // same table in double
     char *arena;
@@ -108,8 +109,8 @@ __device__ __forceinline__ float fexp(float x) { return __expf(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 __device__ __forceinline__ float fexpm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double fexpm1(double x) { return expm1(x); }
-__device__ __forceinline__ float flog1p(float x) { return log1pf(x); }
-__device__ __forceinline__ double flog1p(double x) { return log1p(x); }
+__device__ __forceinline__ float flog(float x) { return __logf(x); }
+__device__ __forceinline__ double flog(double x) { return log(x); }
 
 // ---------------------------------------------------------------------------
 // An interval <L, T> in registers (Eq. 9).  For LOG precisions `t` holds
@@ -148,9 +149,10 @@ __device__ __forceinline__ Iv<P, C> blend(const Iv<P, C> &a, const Iv<P, C> &b) 
 #pragma unroll
     for (int c = 0; c < C; ++c) r.L[c] = A(0.5) * (a.L[c] + b.L[c]);
     if (Prec<P>::LOG) {
-        // -ln((e^-a + e^-b)/2) = min + ln 2 - ln(1 + e^-|a-b|)
+        // -ln((e^-a + e^-b)/2) = min + ln 2 - ln(1 + e^-|a-b|); the argument of
+        // the last log is in [1, 2], where the fast log is accurate to ~1e-7
         A lo = fmin(a.t, b.t), d = fabs(a.t - b.t);
-        r.t = lo + A(0.69314718055994530942) - flog1p(fexp(-d));
+        r.t = lo + A(0.69314718055994530942) - flog(A(1) + fexp(-d));
     } else {
         r.t = A(0.5) * (a.t + b.t);
     }

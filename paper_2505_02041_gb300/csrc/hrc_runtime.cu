@@ -169,6 +169,7 @@ struct hrc_ctx {
     int W = 0, H = 0, C = 0, cascades = 0;
     int prec = P_FP32;
     int sched = 0;
+    int mgroups = 1;
     int device = 0;
     cudaStream_t stream = nullptr;
     RayTable rt;
@@ -188,7 +189,7 @@ struct hrc_ctx {
     // and the caller's pointers; captured on a context-owned stream and
     // replayed on the caller's stream.
     struct GraphEntry {
-        int kind = -1, prec = -1, sched = -1;
+        int kind = -1, prec = -1, sched = -1, mgroups = -1;
         const void *p[5] = {};
         cudaGraphExec_t exec = nullptr;
         int launches = 0;
@@ -258,7 +259,7 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
     }
     const void *key[5] = {p0, p1, p2, p3, p4};
     for (auto &g : ctx->graphs) {
-        if (g.exec && g.kind == kind && g.prec == ctx->prec && g.sched == ctx->sched &&
+        if (g.exec && g.kind == kind && g.prec == ctx->prec && g.sched == ctx->sched && g.mgroups == ctx->mgroups &&
             std::memcmp(g.p, key, sizeof(key)) == 0) {
             cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(ctx, e, where);
@@ -288,6 +289,7 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
     slot.kind = kind;
     slot.prec = ctx->prec;
     slot.sched = ctx->sched;
+    slot.mgroups = ctx->mgroups;
     std::memcpy(slot.p, key, sizeof(key));
     slot.launches = n;
     e = cudaGraphLaunch(exec, ctx->stream);
@@ -384,6 +386,7 @@ hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out) {
     ctx->plan = p32;
     ctx->plan.arena = ctx->arena;
     ctx->plan.sched = ctx->sched;
+    ctx->plan.mgroups = ctx->mgroups;
     e = upload_arcs(ctx->plan, ctx->arena);
     if (e != cudaSuccess) { hrc_destroy(ctx); return fail(nullptr, HRC_ECUDA, "hrc_create: arc upload failed"); }
     *out = ctx;
@@ -420,6 +423,50 @@ hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule) {
     ctx->sched = schedule;
     ctx->plan.sched = schedule;
     ctx->plan64.sched = schedule;
+    return HRC_OK;
+}
+
+hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (ctx->batched || ctx->prec == P_FP64) return fail(ctx, HRC_EINVAL, "hrc_autotune: single-scene fp32/fp16/bf16 contexts");
+    // the timing does not depend on the data: time on the context's own buffers
+    const size_t img = (size_t)ctx->W * ctx->H;
+    cudaError_t e = cudaMemsetAsync(ctx->dev_e, 0, img * ctx->C * sizeof(float), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_s, 0, img * sizeof(float), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_autotune");
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    int best_s = ctx->sched, best_g = ctx->mgroups;
+    const bool timing = ctx->rec.on;
+    ctx->rec.on = false;
+    for (int sc = 0; sc < 2 && st == HRC_OK; ++sc)
+        for (int mg = 1; mg <= 2 && st == HRC_OK; ++mg) {
+            hrc_set_schedule(ctx, sc);
+            ctx->mgroups = mg;
+            ctx->plan.mgroups = mg;
+            for (int r = 0; r < 2 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
+            cudaEventRecord(a, ctx->stream);
+            for (int r = 0; r < 5 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
+            cudaEventRecord(b, ctx->stream);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            ms /= 5.f;
+            if (ms < best) { best = ms; best_s = sc; best_g = mg; }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->rec.on = timing;
+    hrc_set_schedule(ctx, best_s);
+    ctx->mgroups = best_g;
+    ctx->plan.mgroups = best_g;
+    ctx->plan64.mgroups = best_g;
+    ctx->have_fwd = false;
+    if (st != HRC_OK) return st;
+    if (best_ms) *best_ms = best;
     return HRC_OK;
 }
 
@@ -470,6 +517,7 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
             ctx->arena64_bytes = bytes;
             p64.arena = ctx->arena64;
             p64.sched = ctx->sched;
+            p64.mgroups = ctx->mgroups;
             ctx->plan64 = p64;
             e = upload_arcs(ctx->plan64, ctx->arena64);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
@@ -479,6 +527,7 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
         build_plan(ctx->W, ctx->H, ctx->C, ctx->cascades, (int)prec, 0, p, true);
         p.arena = ctx->arena;
         p.sched = ctx->sched;
+        p.mgroups = ctx->mgroups;
         ctx->plan = p;
         cudaError_t e = upload_arcs(ctx->plan, ctx->arena);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
@@ -652,6 +701,7 @@ hrc_status build_batched_plans(hrc_ctx *ctx, int prec) {
         off = build_plan(ctx->Ws[i], ctx->Hs[i], ctx->C, ctx->cascades, prec, off, ctx->bplans[i], true);
         ctx->bplans[i].arena = ctx->arena;
         ctx->bplans[i].sched = 0;
+        ctx->bplans[i].mgroups = 1;
     }
     if (off > ctx->arena_bytes) return fail(ctx, HRC_ENOMEM, "batched layout exceeds the arena");
     for (int i = 0; i < ctx->nscenes; ++i) {

@@ -39,8 +39,39 @@ __device__ __forceinline__ int load_acquire(const int *p) {
     return v;
 }
 
-template <int P, int C>
-__global__ void __launch_bounds__(256) k_batched(BatchArgs a) {
+// One item of an adjoint stage (backward launches only).
+template <int P, int C, class IN>
+__device__ __forceinline__ void batched_adjoint_item(const BatchArgs &a, const StageBlock &sb, const Plan &pl,
+                                                     long long j, int vb, long long r0, long long r1, long long eo,
+                                                     long long so, const IN *e, const IN *s, unsigned char *smem) {
+    switch (sb.kind) {
+    case BK_ADJ_SUM:
+        body_adj_sum<P, C, IN>(pl, (const IN *)a.gF + eo, vb, (int)(j / sb.nvb), smem);
+        break;
+    case BK_ADJ_R2:
+        for (long long r = r0; r < r1; ++r) body_adj_R<P, C, 2>(pl, sb.rs, sb.level, r, vb);
+        break;
+    case BK_ADJ_R1:
+        for (long long r = r0; r < r1; ++r) body_adj_R<P, C, 1>(pl, sb.rs, sb.level, r, vb);
+        break;
+    case BK_ADJ_T2:
+        for (long long r = r0; r < r1; ++r) body_adj_T<P, C, 2>(pl, sb.rs, sb.level, r, vb);
+        break;
+    case BK_ADJ_T1:
+        for (long long r = r0; r < r1; ++r) body_adj_T<P, C, 1>(pl, sb.rs, sb.level, r, vb);
+        break;
+    case BK_ADJ_MU:
+        for (long long r = r0; r < r1; ++r) body_adj_merge_up<P, C>(pl, sb.rs, sb.level, r, vb);
+        break;
+    default:   // BK_ADJ_TRACE
+        body_adj_trace<P, C, IN>(pl, e, s, (IN *)a.ge + eo, (IN *)a.gs + so, sb.level, vb, (int)(j / sb.nvb), smem);
+        break;
+    }
+}
+
+// MODE 0: forward stages only; MODE 1: backward (forward levels + adjoint).
+template <int P, int C, int MODE>
+__global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
     using IN = typename std::conditional<P == P_FP64, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long t_sh;
@@ -105,26 +136,8 @@ __global__ void __launch_bounds__(256) k_batched(BatchArgs a) {
         case BK_SUM:
             for (long long r = r0; r < r1; ++r) body_fluence_sum<P, C, IN>(pl, (IN *)a.F + eo, vb, (int)r);
             break;
-        case BK_ADJ_SUM:
-            body_adj_sum<P, C, IN>(pl, (const IN *)a.gF + eo, vb, (int)(j / sb.nvb), smem);
-            break;
-        case BK_ADJ_R2:
-            for (long long r = r0; r < r1; ++r) body_adj_R<P, C, 2>(pl, sb.rs, sb.level, r, vb);
-            break;
-        case BK_ADJ_R1:
-            for (long long r = r0; r < r1; ++r) body_adj_R<P, C, 1>(pl, sb.rs, sb.level, r, vb);
-            break;
-        case BK_ADJ_T2:
-            for (long long r = r0; r < r1; ++r) body_adj_T<P, C, 2>(pl, sb.rs, sb.level, r, vb);
-            break;
-        case BK_ADJ_T1:
-            for (long long r = r0; r < r1; ++r) body_adj_T<P, C, 1>(pl, sb.rs, sb.level, r, vb);
-            break;
-        case BK_ADJ_MU:
-            for (long long r = r0; r < r1; ++r) body_adj_merge_up<P, C>(pl, sb.rs, sb.level, r, vb);
-            break;
-        default:   // BK_ADJ_TRACE
-            body_adj_trace<P, C, IN>(pl, e, s, (IN *)a.ge + eo, (IN *)a.gs + so, vb, (int)(j / sb.nvb), smem);
+        default:   // adjoint kinds exist only in backward launches
+            if constexpr (MODE == 1) batched_adjoint_item<P, C, IN>(a, sb, pl, j, vb, r0, r1, eo, so, e, s, smem);
             break;
         }
         __syncthreads();
@@ -193,10 +206,10 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
         d.bytes = bytes;
         if (d.count > 0) out.push_back(d);
     };
-    auto tilestage = [&](int kind, int nx, int ny, double bytes) {
+    auto tilestage = [&](int kind, int nx, int ny, double bytes, int level = 0) {
         StageDesc d;
         d.kind = kind;
-        d.level = 0;
+        d.level = level;
         std::memset(&d.rs, 0, sizeof(d.rs));
         d.nvb = nx;
         d.rows = ny;
@@ -274,10 +287,12 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
             if (n <= pl.q[q].N) by += 2 * gT(q, n - 1) + gT(q, n) + bytes_T(pl, q, n - 1);
         rowstage(BK_ADJ_MU, n, vb2, by);
     }
-    by = img * (pl.C + 1) * esz * 2;
-    for (int q = 0; q < 4; ++q)
-        for (int n = 0; n <= 2; ++n) by += gT(q, n);
-    tilestage(BK_ADJ_TRACE, tx, ty, by);
+    for (int pair = 0; pair < 2; ++pair) {
+        double bt = img * (pl.C + 1) * esz * (pair == 0 ? 1.0 : 2.0);
+        for (int q = 2 * pair; q < 2 * pair + 2; ++q)
+            for (int n = 0; n <= 2; ++n) bt += gT(q, n);
+        tilestage(BK_ADJ_TRACE, pair_tiles_x(pair, pl.W), pair_tiles_y(pair, pl.H), bt, pair);
+    }
 }
 
 // Dynamic shared memory of a launch: the forward needs the trace tile, the
@@ -286,29 +301,33 @@ template <int P, int C> size_t batched_smem(int mode) {
     using A = typename Prec<P>::A;
     size_t m = TraceTile<A, C>::bytes();
     if (mode == 0) return m;
-    m = m > AdjTile<A, C>::bytes() ? m : AdjTile<A, C>::bytes();
+    m = m > adj_trace_smem<A, C>() ? m : adj_trace_smem<A, C>();
     const size_t sum_tile = sizeof(A) * C * 32 * 33;
     return m > sum_tile ? m : sum_tile;
 }
 
-template <int P, int C>
-static cudaError_t batched_impl(const BatchArgs &a, int blocks_per_sm, int mode, cudaStream_t st) {
-    const size_t smem = batched_smem<P, C>(mode);
-    cudaError_t e = cudaFuncSetAttribute(k_batched<P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)batched_smem<P, C>(1));
+template <int P, int C, int MODE>
+static cudaError_t batched_launch(const BatchArgs &a, int blocks_per_sm, cudaStream_t st) {
+    const size_t smem = batched_smem<P, C>(MODE);
+    cudaError_t e = cudaFuncSetAttribute(k_batched<P, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<P, C>, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<P, C, MODE>, 256, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
     long long grid = (long long)sms * per_sm;
     if (grid > a.total) grid = a.total;
     if (grid < 1) grid = 1;
-    k_batched<P, C><<<(unsigned)grid, 256, smem, st>>>(a);
+    k_batched<P, C, MODE><<<(unsigned)grid, 256, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int P, int C>
+static cudaError_t batched_impl(const BatchArgs &a, int blocks_per_sm, int mode, cudaStream_t st) {
+    return mode == 0 ? batched_launch<P, C, 0>(a, blocks_per_sm, st) : batched_launch<P, C, 1>(a, blocks_per_sm, st);
 }
 
 template <int P>

@@ -30,9 +30,9 @@ __global__ void __launch_bounds__(256) k_adj_merge_up(Plan pl, RowSplitB rs, int
 
 template <int P, int C, class IN>
 __global__ void __launch_bounds__(256) k_adj_trace(Plan pl, const IN *__restrict__ e, const IN *__restrict__ s,
-                                                   IN *__restrict__ ge, IN *__restrict__ gs) {
+                                                   IN *__restrict__ ge, IN *__restrict__ gs, int pair) {
     extern __shared__ __align__(16) unsigned char tb_smem[];
-    body_adj_trace<P, C, IN>(pl, e, s, ge, gs, blockIdx.x, blockIdx.y, tb_smem);
+    body_adj_trace<P, C, IN>(pl, e, s, ge, gs, pair, blockIdx.x, blockIdx.y, tb_smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -135,15 +135,17 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
     }
     {
         using A = typename Prec<P>::A;
-        const size_t smem = AdjTile<A, C>::bytes();
-        double by = img * (pl.C + 1) * ab * 2;
-        for (int q = 0; q < 4; ++q)
-            for (int n = 0; n <= 2; ++n) by += gTbytes(q, n);
-        dim3 grid((pl.W + TB_TILE - 1) / TB_TILE, (pl.H + TB_TILE - 1) / TB_TILE);
-        rec->begin(K_ADJ_TRACE, 0, by);
-        k_adj_trace<P, C, IN><<<grid, 256, smem, st>>>(pl, (const IN *)e, (const IN *)s, (IN *)ge, (IN *)gs);
-        rec->end();
-        ++*launches;
+        const size_t smem = adj_trace_smem<A, C>();
+        for (int pair = 0; pair < 2; ++pair) {
+            double by = img * (pl.C + 1) * ab * (pair == 0 ? 1.0 : 2.0);   // pair 1 adds to the gradients
+            for (int q = 2 * pair; q < 2 * pair + 2; ++q)
+                for (int n = 0; n <= 2; ++n) by += gTbytes(q, n);
+            dim3 grid(pair_tiles_x(pair, pl.W), pair_tiles_y(pair, pl.H));
+            rec->begin(K_ADJ_TRACE, pair, by);
+            k_adj_trace<P, C, IN><<<grid, 256, smem, st>>>(pl, (const IN *)e, (const IN *)s, (IN *)ge, (IN *)gs, pair);
+            rec->end();
+            ++*launches;
+        }
     }
     return cudaGetLastError();
 }
@@ -167,10 +169,10 @@ static cudaError_t prepare_bwd_prec() {
     auto set = [&](const void *fn, size_t bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    set((const void *)k_adj_trace<P, 1, IN>, AdjTile<A, 1>::bytes());
-    set((const void *)k_adj_trace<P, 2, IN>, AdjTile<A, 2>::bytes());
-    set((const void *)k_adj_trace<P, 3, IN>, AdjTile<A, 3>::bytes());
-    set((const void *)k_adj_trace<P, 4, IN>, AdjTile<A, 4>::bytes());
+    set((const void *)k_adj_trace<P, 1, IN>, adj_trace_smem<A, 1>());
+    set((const void *)k_adj_trace<P, 2, IN>, adj_trace_smem<A, 2>());
+    set((const void *)k_adj_trace<P, 3, IN>, adj_trace_smem<A, 3>());
+    set((const void *)k_adj_trace<P, 4, IN>, adj_trace_smem<A, 4>());
     return e;
 }
 

@@ -13,9 +13,9 @@ __global__ void __launch_bounds__(256) k_trace012(Plan pl, const float *__restri
     body_trace012<P, C>(pl, e, s, ed, sd, qmask, blockIdx.x, blockIdx.y, tr_smem);
 }
 
-template <int P, int C>
+template <int P, int C, int G>
 __global__ void __launch_bounds__(128) k_merge_up(Plan pl, RowSplit rs, int n) {
-    body_merge_up<P, C>(pl, rs, n, blockIdx.x, blockIdx.y);
+    body_merge_up<P, C, G>(pl, rs, n, blockIdx.x, blockIdx.y);
 }
 
 template <int P, int C, bool PAIR>
@@ -74,7 +74,8 @@ template <int P, int C>
 static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
                             cudaStream_t st, int *launches, Recorder *rec, bool with_sum) {
     const int bs = 256;
-    const int vb = vblocks(pl, bs);
+    const int vb = vblocks(pl, bs);            // blocks of 256 v
+    const int vbg = vblocks(pl, 2 * bs);       // blocks of 512 v (two groups per thread)
     int Nmax = 0;
     for (int q = 0; q < 4; ++q) Nmax = pl.q[q].N > Nmax ? pl.q[q].N : Nmax;
     const float *ef = (const float *)e, *sf = (const float *)s;
@@ -105,9 +106,10 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             double by = 0;
             for (int q = 0; q < 4; ++q)
                 if ((qsel < 0 || q == qsel) && n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
-            dim3 grid((unsigned)rs.start[4], vb);
+            dim3 grid((unsigned)rs.start[4], vbg);
             rec->begin(K_MERGE_UP, n, by);
-            k_merge_up<P, C><<<grid, bs / 2, 0, st>>>(pl, rs, n);
+            if (pl.mgroups == 2) k_merge_up<P, C, 2><<<grid, bs / 2, 0, st>>>(pl, rs, n);
+            else k_merge_up<P, C, 1><<<dim3((unsigned)rs.start[4], vb), bs / 2, 0, st>>>(pl, rs, n);
             rec->end();
             ++*launches;
         }
@@ -123,10 +125,11 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                 by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
                 by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
             }
-            dim3 grid((unsigned)rs.start[4], vb);
+            dim3 grid((unsigned)rs.start[4], vbg);
             rec->begin(K_MERGE_DOWN, n, by);
-            if (n >= 1) k_merge_down<P, C, true><<<grid, bs / 2, 0, st>>>(pl, rs, n);
-            else k_merge_down<P, C, false><<<grid, bs, 0, st>>>(pl, rs, n);
+            dim3 g1((unsigned)rs.start[4], vb);
+            if (n >= 1) k_merge_down<P, C, true><<<g1, bs / 2, 0, st>>>(pl, rs, n);
+            else k_merge_down<P, C, false><<<g1, bs, 0, st>>>(pl, rs, n);
             rec->end();
             ++*launches;
         }

@@ -1,7 +1,9 @@
 """Batched persistent launch: many scenes of uneven size in one launch.
 
-Each scene's fluence and gradients must equal the single-scene path's
-(the same bodies run in both, so they agree to rounding), and the single-
+Each scene's fluence and gradients must equal the single-scene path's to
+fp32 rounding (the same bodies run in both, but in separately compiled
+kernels whose multiply-adds may be fused differently; 1e-5 of the largest
+value, ten times tighter than the oracle bound), and the single-
 scene path is itself checked against the oracle; small scenes are also
 compared with the oracle directly.  The bounded dependency wait is tested
 by withholding one stage's publication: the launch must end with
@@ -41,7 +43,7 @@ def test_batched_forward_matches_single_and_oracle(C, prec):
     for i, (w, h) in enumerate(SIZES):
         h1 = HRC(w, h, C, 0, prec)
         Fr = h1.forward(es[i].cuda(), ss[i].cuda())
-        assert err_max(Fs[i].cpu().numpy(), Fr.cpu().numpy()) <= 1e-6, i
+        assert err_max(Fs[i].cpu().numpy(), Fr.cpu().numpy()) <= 1e-5, i
         if prec == "fp32" and w * h <= 128 * 96:
             assert err_max(Fs[i].cpu().numpy(), oracle.fluence(es[i].numpy(), ss[i].numpy())) <= 1e-4, i
 
@@ -63,8 +65,8 @@ def test_batched_backward_matches_single():
         h1 = HRC(w, h, C)
         h1.forward(es[i].cuda(), ss[i].cuda())
         ge1, gs1 = h1.backward(gFs[i].contiguous())
-        assert err_max(ges[i].cpu().numpy(), ge1.cpu().numpy()) <= 1e-6, i
-        assert err_max(gss[i].cpu().numpy(), gs1.cpu().numpy()) <= 1e-6, i
+        assert err_max(ges[i].cpu().numpy(), ge1.cpu().numpy()) <= 1e-5, i
+        assert err_max(gss[i].cpu().numpy(), gs1.cpu().numpy()) <= 1e-5, i
     # and one scene against the oracle's adjoint
     ge_r, gs_r = oracle.fluence_adjoint(es[0].numpy(), ss[0].numpy(), gFs[0].cpu().numpy())
     assert err_max(ges[0].cpu().numpy(), ge_r) <= 1e-4

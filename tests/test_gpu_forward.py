@@ -90,3 +90,22 @@ def test_forward_host_entry_matches_device_entry():
     Fd = h.forward(to_dev(e), to_dev(s)).cpu()
     Fh = h.forward_host(torch.from_numpy(e).pin_memory(), torch.from_numpy(s).pin_memory())
     assert torch.equal(Fd, Fh)
+
+
+def test_autotune_keeps_results():
+    """Every launch configuration the autotuner may choose gives the same
+    fluence."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC, _lib
+    e, s = scenes.random_scene(300, 260, 3, 14)
+    h = HRC(300, 260, 3)
+    ref = h.forward(to_dev(e), to_dev(s)).clone()
+    for sched in (0, 1):
+        _lib.hrc_set_schedule(h.ctx, sched)
+        F = h.forward(to_dev(e), to_dev(s))
+        assert torch.equal(F, ref)
+    ms = h.autotune()
+    assert ms > 0
+    F = h.forward(to_dev(e), to_dev(s))
+    assert torch.equal(F, ref)
+    assert err_max(F.cpu().numpy(), oracle.fluence(e, s)) <= TOL
