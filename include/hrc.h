@@ -190,9 +190,11 @@ hrc_status hrc_batched_debug(hrc_ctx *ctx, int withhold_counter, long long spin_
 /* Introspection for tests: copies level n of quadrant frame q (0..3) from
  * the last forward into `dst` (device fp32).  which = 0: T_n as
  * [U_n][2^n+1][V][C+1] (C radiances then the transmittance T, linear even in
- * the log-T precisions); which = 1: R_n as [U_n][2^n][V][C].  *count
- * receives the element count; dst may be NULL to query it.  HRC_EINVAL if
- * the level does not exist. */
+ * the log-T precisions); which = 1: R_n as [U_n][2^n][V][C].  Column x = 0
+ * of every level is NaN: no fluence depends on it (the sum of Algorithm 1
+ * reads R_0 at u + 1, and column 0 feeds only column 0 of the levels next to
+ * it), so the library never computes it.  *count receives the element count;
+ * dst may be NULL to query it.  HRC_EINVAL if the level does not exist. */
 hrc_status hrc_copy_level(hrc_ctx *ctx, int q, int which, int n, float *dst, long long *count);
 
 /* Number of kernel launches the last compute call enqueued. */

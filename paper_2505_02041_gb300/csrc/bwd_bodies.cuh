@@ -107,10 +107,11 @@ template <int P, int C, int E>
 __device__ __forceinline__ void body_adj_R(const Plan &pl, const RowSplitB &rs, int n, long long bx, int by) {
     using A = typename Prec<P>::A;
     int local;
-    const int q = quadrant_of(rs, bx, local);   // row = (q, x', j) at level n+1
+    const int q = quadrant_of(rs, bx, local);   // row = (q, x', j) at level n+1, x' >= 1
     const QuadGeom &g = pl.q[q];
     const int w = E * (by * blockDim.x + threadIdx.x);
     if (w >= g.V) return;
+    local += 2 << n;                              // column 0 is dead: its gradient is never read
     const int x1 = local >> (n + 1), j = local & ((2 << n) - 1);
     const int ip = j >> 1, kk = (j + 1) >> 1;
     const int d = 2 * kk - (1 << n);
@@ -132,13 +133,13 @@ __device__ __forceinline__ void body_adj_R(const Plan &pl, const RowSplitB &rs, 
         }
     };
     const int xo = 2 * x1 - 1;
-    if (x1 >= 1 && xo < g.Un[n]) {
+    if (xo < g.Un[n]) {
         TLevel<P, C> Tn(pl, q, n);
         term(xo, d, A(1), &Tn, xo, kk);
     }
     if (2 * x1 < g.Un[n]) term(2 * x1, 0, A(0.5), nullptr, 0, 0);
     const int xe = 2 * x1 - 2;
-    if (x1 >= 1 && xe < g.Un[n]) {
+    if (x1 >= 2 && xe < g.Un[n]) {                // xe = 0 is dead (its gradient is zero)
         TLevel<P, C> T1(pl, q, n + 1);
         term(xe, 2 * d, A(0.5), &T1, x1 - 1, 2 * kk);
     }
@@ -162,11 +163,12 @@ template <int P, int C, int E>
 __device__ __forceinline__ void body_adj_T(const Plan &pl, const RowSplitB &rs, int n, long long bx, int by) {
     using A = typename Prec<P>::A;
     int local;
-    const int q = quadrant_of(rs, bx, local);   // row = (q, x, k) at level n
+    const int q = quadrant_of(rs, bx, local);   // row = (q, x, k) at level n, x >= 1
     const QuadGeom &g = pl.q[q];
     const int v = E * (by * blockDim.x + threadIdx.x);
     if (v >= g.V) return;
     const int K = (1 << n) + 1;
+    local += K;
     const int x = local / K, k = local - x * K;
     const int s = 1 << n;
     const int d = 2 * k - s;
@@ -239,6 +241,7 @@ __device__ __forceinline__ void body_adj_merge_up(const Plan &pl, const RowSplit
     if (w >= g.V) return;
     const int m = n - 1, h = 1 << m;
     const int Km = h + 1;
+    local += Km;                                  // x' >= 1: column 0 is dead
     const int x1 = local / Km, kap = local - x1 * Km;
     TLevel<P, C> Tm(pl, q, m);
     GTLevel<P, C> gTm(pl, q, m), gTn(pl, q, n);
@@ -271,7 +274,7 @@ __device__ __forceinline__ void body_adj_merge_up(const Plan &pl, const RowSplit
                 aT[l] = fma(wgt, dT, aT[l]);
             }
         }
-    } else {
+    } else if (x1 >= 3) {                         // x' = 1 is the far operand of the dead column 0
         const int x = (x1 - 1) >> 1, xn = x1 - 1;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
@@ -373,7 +376,7 @@ __device__ __forceinline__ void adj_gather(const Plan &pl, const PairTile<typena
     if constexpr (J < ray::end) {
         using pc = PieceAt<J>;
         const int up = us - pc::du, vp = vs - pc::dv;
-        if (up >= 0 && !(up & ((1 << ray::n) - 1)) && vp >= 0 && vp < V) {
+        if (up >= 1 && !(up & ((1 << ray::n) - 1)) && vp >= 0 && vp < V) {   // probes at u = 0 are dead
             A gL[C], gT;
             GTLevel<P, C>(pl, q, ray::n).load(up >> ray::n, ray::k, vp, gL, gT);
             const int pbase = base - pc::du * su - pc::dv;

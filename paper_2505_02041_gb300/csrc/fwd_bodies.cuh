@@ -15,6 +15,11 @@
 // lookups read as vacuum (T = <0, 1>, R = 0), which is exact for this
 // method: paths are monotone in v, so a path that leaves the grid never
 // re-enters, and nothing outside the grid emits.
+//
+// Column x = 0 of every level is dead: the fluence sum reads R_0 at u + 1,
+// R_n(0) feeds only R_{n-1}(0), and T_n(0) only T_{n+1}(0) and R_n(0).  No
+// body computes or reads it (T_N, a single column when U <= 2^N, is then
+// skipped entirely).
 #pragma once
 
 #include <type_traits>
@@ -121,7 +126,7 @@ __device__ __forceinline__ void trace_store(const Plan &pl, const TraceTile<type
                                             int nmax, int u, int v, int base, int su, int sv) {
     using A = typename Prec<P>::A;
     using ray = RayAt<R>;
-    if (ray::n > nmax || (u & ((1 << ray::n) - 1))) return;
+    if (u == 0 || ray::n > nmax || (u & ((1 << ray::n) - 1))) return;   // probes at u = 0 are dead
     Iv<P, C> iv;
 #pragma unroll
     for (int c = 0; c < C; ++c) iv.L[c] = A(0);
@@ -186,9 +191,10 @@ __device__ __forceinline__ void body_trace012(const Plan &pl, const float *__res
 template <int P, int C, int G = 1>
 __device__ __forceinline__ void body_merge_up(const Plan &pl, const RowSplit &rs, int n, long long bx, int by) {
     int local;
-    const int q = find_quadrant(rs, bx, local);   // row = (q, x, k)
+    const int q = find_quadrant(rs, bx, local);   // row = (q, x, k), x >= 1 (column 0 is dead)
     const QuadGeom &g = pl.q[q];
     const int K = (1 << n) + 1;
+    local += K;
     const int x = local / K, k = local - x * K;
     const int m = n - 1, sm = 1 << m;
     TLevel<P, C> Tm(pl, q, m), Tn(pl, q, n);
@@ -240,11 +246,12 @@ __device__ __forceinline__ void body_merge_down(const Plan &pl, const RowSplit &
     using A = typename Prec<P>::A;
     constexpr int E = PAIR ? 2 : 1;
     int local;
-    const int q = find_quadrant(rs, bx, local);   // row = (q, x, ip)
+    const int q = find_quadrant(rs, bx, local);   // row = (q, x, ip), x >= 1 (column 0 is dead)
     const QuadGeom &g = pl.q[q];
     const int v = E * (by * blockDim.x + threadIdx.x);
     if (v >= g.V) return;
     const int I = 1 << n;
+    local += I;
     const int x = local >> n, ip = local & (I - 1);
     const bool top = (n + 1 >= g.N);               // R_N = 0
     const int s = 1 << n;

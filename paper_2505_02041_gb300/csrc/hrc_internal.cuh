@@ -46,6 +46,8 @@ struct Plan {
     int W, H, C, prec;
     int sched;                       // 0: each launch covers all four frames; 1: frame by frame
     int mgroups;                     // merge kernels: element groups per thread (1 or 2)
+    int mthreads;                    // merge kernels: threads per block for paired-v bodies
+    int vmajor;                      // merge kernels: 1 = v-blocks of a row are adjacent in launch order
     long long arcs_off;              // byte offset: float A[2^n + j] for level n (n >= 1)
     long long arcs_off_d;            // same table in double
     char *arena;

@@ -103,6 +103,10 @@ RayTable make_ray_table() {
 size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan &pl, bool adjoint) {
     std::memset(&pl, 0, sizeof(pl));
     pl.W = W; pl.H = H; pl.C = C; pl.prec = prec;
+    pl.sched = 0;
+    pl.mgroups = 1;
+    pl.mthreads = 128;
+    pl.vmajor = 0;
     const size_t SLb = sl_bytes(prec), STb = st_bytes(prec);
     int Nmax = 0;
     for (int q = 0; q < 4; ++q) {
@@ -170,6 +174,8 @@ struct hrc_ctx {
     int prec = P_FP32;
     int sched = 0;
     int mgroups = 1;
+    int mthreads = 128;
+    int vmajor = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     RayTable rt;
@@ -189,7 +195,7 @@ struct hrc_ctx {
     // and the caller's pointers; captured on a context-owned stream and
     // replayed on the caller's stream.
     struct GraphEntry {
-        int kind = -1, prec = -1, sched = -1, mgroups = -1;
+        int kind = -1, prec = -1, sched = -1, mgroups = -1, tune = -1;
         const void *p[5] = {};
         cudaGraphExec_t exec = nullptr;
         int launches = 0;
@@ -260,6 +266,7 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
     const void *key[5] = {p0, p1, p2, p3, p4};
     for (auto &g : ctx->graphs) {
         if (g.exec && g.kind == kind && g.prec == ctx->prec && g.sched == ctx->sched && g.mgroups == ctx->mgroups &&
+            g.tune == ctx->mthreads * 2 + ctx->vmajor &&
             std::memcmp(g.p, key, sizeof(key)) == 0) {
             cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(ctx, e, where);
@@ -290,6 +297,7 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
     slot.prec = ctx->prec;
     slot.sched = ctx->sched;
     slot.mgroups = ctx->mgroups;
+    slot.tune = ctx->mthreads * 2 + ctx->vmajor;
     std::memcpy(slot.p, key, sizeof(key));
     slot.launches = n;
     e = cudaGraphLaunch(exec, ctx->stream);
@@ -387,6 +395,8 @@ hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out) {
     ctx->plan.arena = ctx->arena;
     ctx->plan.sched = ctx->sched;
     ctx->plan.mgroups = ctx->mgroups;
+    ctx->plan.mthreads = ctx->mthreads;
+    ctx->plan.vmajor = ctx->vmajor;
     e = upload_arcs(ctx->plan, ctx->arena);
     if (e != cudaSuccess) { hrc_destroy(ctx); return fail(nullptr, HRC_ECUDA, "hrc_create: arc upload failed"); }
     *out = ctx;
@@ -439,14 +449,22 @@ hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     float best = 1e30f;
-    int best_s = ctx->sched, best_g = ctx->mgroups;
+    int best_s = ctx->sched, best_g = ctx->mgroups, best_t = ctx->mthreads, best_v = ctx->vmajor;
     const bool timing = ctx->rec.on;
     ctx->rec.on = false;
-    for (int sc = 0; sc < 2 && st == HRC_OK; ++sc)
-        for (int mg = 1; mg <= 2 && st == HRC_OK; ++mg) {
+    static const int kThreads[3] = {128, 256, 512};
+    for (int cand = 0; cand < 2 * 2 * 3 * 2 && st == HRC_OK; ++cand) {
+            const int sc = cand & 1, mg = 1 + ((cand >> 1) & 1), mt = kThreads[(cand >> 2) % 3], vm = (cand / 12) & 1;
+            // v-block-major grids put rows in gridDim.y (at most 65535; the
+            // adjoint's level 0 has 4 (W + H) rows)
+            if (vm && 4LL * (ctx->W + ctx->H) > 65535) continue;
             hrc_set_schedule(ctx, sc);
             ctx->mgroups = mg;
             ctx->plan.mgroups = mg;
+            ctx->mthreads = mt;
+            ctx->plan.mthreads = mt;
+            ctx->vmajor = vm;
+            ctx->plan.vmajor = vm;
             for (int r = 0; r < 2 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
             cudaEventRecord(a, ctx->stream);
             for (int r = 0; r < 5 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
@@ -455,8 +473,8 @@ hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, a, b);
             ms /= 5.f;
-            if (ms < best) { best = ms; best_s = sc; best_g = mg; }
-        }
+            if (ms < best) { best = ms; best_s = sc; best_g = mg; best_t = mt; best_v = vm; }
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     ctx->rec.on = timing;
@@ -464,6 +482,12 @@ hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
     ctx->mgroups = best_g;
     ctx->plan.mgroups = best_g;
     ctx->plan64.mgroups = best_g;
+    ctx->mthreads = best_t;
+    ctx->plan.mthreads = best_t;
+    ctx->plan64.mthreads = best_t;
+    ctx->vmajor = best_v;
+    ctx->plan.vmajor = best_v;
+    ctx->plan64.vmajor = best_v;
     ctx->have_fwd = false;
     if (st != HRC_OK) return st;
     if (best_ms) *best_ms = best;
@@ -518,6 +542,8 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
             p64.arena = ctx->arena64;
             p64.sched = ctx->sched;
             p64.mgroups = ctx->mgroups;
+            p64.mthreads = ctx->mthreads;
+            p64.vmajor = ctx->vmajor;
             ctx->plan64 = p64;
             e = upload_arcs(ctx->plan64, ctx->arena64);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
@@ -528,6 +554,8 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
         p.arena = ctx->arena;
         p.sched = ctx->sched;
         p.mgroups = ctx->mgroups;
+        p.mthreads = ctx->mthreads;
+        p.vmajor = ctx->vmajor;
         ctx->plan = p;
         cudaError_t e = upload_arcs(ctx->plan, ctx->arena);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
@@ -702,6 +730,8 @@ hrc_status build_batched_plans(hrc_ctx *ctx, int prec) {
         ctx->bplans[i].arena = ctx->arena;
         ctx->bplans[i].sched = 0;
         ctx->bplans[i].mgroups = 1;
+        ctx->bplans[i].mthreads = 128;
+        ctx->bplans[i].vmajor = 0;
     }
     if (off > ctx->arena_bytes) return fail(ctx, HRC_ENOMEM, "batched layout exceeds the arena");
     for (int i = 0; i < ctx->nscenes; ++i) {

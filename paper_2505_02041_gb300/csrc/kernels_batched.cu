@@ -163,14 +163,14 @@ RowSplit rows_for(const Plan &pl, int kind, int n) {
         const QuadGeom &g = pl.q[q];
         long long rows = 0;
         switch (kind) {
-        case BK_MERGE_UP: rows = (n >= 3 && n <= g.N) ? (long long)g.Un[n] * ((1 << n) + 1) : 0; break;
+        case BK_MERGE_UP: rows = (n >= 3 && n <= g.N) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0; break;
         case BK_MERGE_DOWN2:
-        case BK_MERGE_DOWN1: rows = n < g.N ? (long long)g.Un[n] * (1 << n) : 0; break;
+        case BK_MERGE_DOWN1: rows = n < g.N ? (long long)(g.Un[n] - 1) * (1 << n) : 0; break;
         case BK_ADJ_R2:
-        case BK_ADJ_R1: rows = (n + 1 < g.N) ? (long long)g.Un[n + 1] * (2 << n) : 0; break;
+        case BK_ADJ_R1: rows = (n + 1 < g.N) ? (long long)(g.Un[n + 1] - 1) * (2 << n) : 0; break;
         case BK_ADJ_T2:
-        case BK_ADJ_T1: rows = (g.N >= 1 && n <= g.N) ? (long long)g.Un[n] * ((1 << n) + 1) : 0; break;
-        case BK_ADJ_MU: rows = (n >= 3 && n <= g.N) ? (long long)g.Un[n - 1] * ((1 << (n - 1)) + 1) : 0; break;
+        case BK_ADJ_T1: rows = (g.N >= 1 && n <= g.N) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0; break;
+        case BK_ADJ_MU: rows = (n >= 3 && n <= g.N) ? (long long)(g.Un[n - 1] - 1) * ((1 << (n - 1)) + 1) : 0; break;
         default: break;
         }
         acc += rows;
@@ -233,7 +233,7 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
         for (int q = 0; q < 4; ++q) {
             const QuadGeom &g = pl.q[q];
             if (n >= g.N) continue;
-            by += bytes_T(pl, q, n) * (double(g.Un[n] / 2) / g.Un[n]);
+            by += bytes_T_odd(pl, q, n);
             by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
             by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
         }
@@ -259,11 +259,11 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
     const double ab = 4.0;   // adjoint buffers are fp32 in the batched precisions
     auto gT = [&](int q, int n) {
         const QuadGeom &g = pl.q[q];
-        return (n < 0 || n > g.N) ? 0.0 : double(g.Un[n]) * ((1 << n) + 1) * g.V * (pl.C + 1) * ab;
+        return (n < 0 || n > g.N) ? 0.0 : double(g.Un[n] - 1) * ((1 << n) + 1) * g.V * (pl.C + 1) * ab;
     };
     auto gR = [&](int q, int n) {
         const QuadGeom &g = pl.q[q];
-        return (n < 0 || n >= g.N) ? 0.0 : double(g.Un[n]) * (1 << n) * g.V * pl.C * ab;
+        return (n < 0 || n >= g.N) ? 0.0 : double(g.Un[n] - 1) * (1 << n) * g.V * pl.C * ab;
     };
     by = img * pl.C * esz;
     for (int q = 0; q < 4; ++q) by += gR(q, 0);

@@ -13,19 +13,34 @@ __global__ void __launch_bounds__(256) k_adj_sum(Plan pl, const GIN *__restrict_
     body_adj_sum<P, C, GIN>(pl, gF, blockIdx.x, blockIdx.y, smem);
 }
 
-template <int P, int C, int E>
-__global__ void __launch_bounds__(256) k_adj_R(Plan pl, RowSplitB rs, int n) {
-    body_adj_R<P, C, E>(pl, rs, n, blockIdx.x, blockIdx.y);
+// Row and v-block of this block (see the forward merge kernels).
+__device__ __forceinline__ void row_block_b(const Plan &pl, long long &row, int &vb) {
+    if (pl.vmajor) { row = blockIdx.y; vb = blockIdx.x; }
+    else { row = blockIdx.x; vb = blockIdx.y; }
 }
 
 template <int P, int C, int E>
-__global__ void __launch_bounds__(256) k_adj_T(Plan pl, RowSplitB rs, int n) {
-    body_adj_T<P, C, E>(pl, rs, n, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(512) k_adj_R(Plan pl, RowSplitB rs, int n) {
+    long long row;
+    int vb;
+    row_block_b(pl, row, vb);
+    body_adj_R<P, C, E>(pl, rs, n, row, vb);
+}
+
+template <int P, int C, int E>
+__global__ void __launch_bounds__(512) k_adj_T(Plan pl, RowSplitB rs, int n) {
+    long long row;
+    int vb;
+    row_block_b(pl, row, vb);
+    body_adj_T<P, C, E>(pl, rs, n, row, vb);
 }
 
 template <int P, int C>
-__global__ void __launch_bounds__(256) k_adj_merge_up(Plan pl, RowSplitB rs, int n) {
-    body_adj_merge_up<P, C>(pl, rs, n, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(512) k_adj_merge_up(Plan pl, RowSplitB rs, int n) {
+    long long row;
+    int vb;
+    row_block_b(pl, row, vb);
+    body_adj_merge_up<P, C>(pl, rs, n, row, vb);
 }
 
 template <int P, int C, class IN>
@@ -50,13 +65,20 @@ RowSplitB split_rows(const Plan &pl, int kind, int n) {
         const QuadGeom &g = pl.q[q];
         long long rows = 0;
         if (kind == 0) rows = g.N >= 1 ? g.Un[0] : 0;
-        else if (kind == 1) rows = (n + 1 < g.N) ? (long long)g.Un[n + 1] * (2 << n) : 0;
-        else if (kind == 2) rows = (g.N >= 1 && n <= g.N) ? (long long)g.Un[n] * ((1 << n) + 1) : 0;
-        else rows = (n >= 3 && n <= g.N) ? (long long)g.Un[n - 1] * ((1 << (n - 1)) + 1) : 0;
+        else if (kind == 1) rows = (n + 1 < g.N) ? (long long)(g.Un[n + 1] - 1) * (2 << n) : 0;
+        else if (kind == 2) rows = (g.N >= 1 && n <= g.N) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0;
+        else rows = (n >= 3 && n <= g.N) ? (long long)(g.Un[n - 1] - 1) * ((1 << (n - 1)) + 1) : 0;
         acc += rows;
     }
     rs.start[4] = acc;
     return rs;
+}
+
+dim3 row_grid_b(const Plan &pl, long long rows, int per_block) {
+    int Vmax = 0;
+    for (int q = 0; q < 4; ++q) Vmax = pl.q[q].V > Vmax ? pl.q[q].V : Vmax;
+    const unsigned vb = (unsigned)((Vmax + per_block - 1) / per_block);
+    return pl.vmajor ? dim3(vb, (unsigned)rows) : dim3((unsigned)rows, vb);
 }
 
 int vblocks_b(const Plan &pl, int bs) {
@@ -71,18 +93,19 @@ template <int P, int C>
 static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,
                             void *ge, void *gs, cudaStream_t st, int *launches, Recorder *rec) {
     using IN = typename std::conditional<P == P_FP64, double, float>::type;
-    const int bs = 256, vb = vblocks_b(pl, bs);
+    const int mt = pl.mthreads, ts = 2 * mt > 512 ? 512 : 2 * mt;   // paired-v / single-v block sizes
     int Nmax = 0;
     for (int q = 0; q < 4; ++q) Nmax = pl.q[q].N > Nmax ? pl.q[q].N : Nmax;
     const double ab = P == P_FP64 ? 8.0 : 4.0;
     const double img = double(pl.W) * pl.H;
+    // live columns x >= 1 only (column 0 is dead)
     auto gTbytes = [&](int q, int n) {
         const QuadGeom &g = pl.q[q];
-        return (n < 0 || n > g.N) ? 0.0 : double(g.Un[n]) * ((1 << n) + 1) * g.V * (pl.C + 1) * ab;
+        return (n < 0 || n > g.N) ? 0.0 : double(g.Un[n] - 1) * ((1 << n) + 1) * g.V * (pl.C + 1) * ab;
     };
     auto gRbytes = [&](int q, int n) {
         const QuadGeom &g = pl.q[q];
-        return (n < 0 || n >= g.N) ? 0.0 : double(g.Un[n]) * (1 << n) * g.V * pl.C * ab;
+        return (n < 0 || n >= g.N) ? 0.0 : double(g.Un[n] - 1) * (1 << n) * g.V * pl.C * ab;
     };
     // forward recompute of every T and R level (no fluence sum)
     cudaError_t err = launch_forward_levels(pl, rt, e, s, st, launches, rec);
@@ -104,8 +127,8 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                 by += gRbytes(q, n) + gRbytes(q, n + 1) + bytes_T(pl, q, n) / (pl.C + 1) / 2 +
                       bytes_T(pl, q, n + 1) / (pl.C + 1) / 2;
         rec->begin(K_ADJ_MERGE_DOWN, n, by);
-        if (n >= 1) k_adj_R<P, C, 2><<<dim3((unsigned)rs.start[4], vb), bs / 2, 0, st>>>(pl, rs, n);
-        else k_adj_R<P, C, 1><<<dim3((unsigned)rs.start[4], vb), bs, 0, st>>>(pl, rs, n);
+        if (n >= 1) k_adj_R<P, C, 2><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
+        else k_adj_R<P, C, 1><<<row_grid_b(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
         rec->end();
         ++*launches;
     }
@@ -117,8 +140,8 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             if (pl.q[q].N >= 1 && n <= pl.q[q].N)
                 by += gTbytes(q, n) + gRbytes(q, n) + gRbytes(q, n - 1) + bytes_R(pl, q, n) + bytes_R(pl, q, n + 1);
         rec->begin(K_ADJ_MERGE_DOWN, n, by);
-        if (n >= 1) k_adj_T<P, C, 2><<<dim3((unsigned)rs.start[4], vb), bs / 2, 0, st>>>(pl, rs, n);
-        else k_adj_T<P, C, 1><<<dim3((unsigned)rs.start[4], vb), bs, 0, st>>>(pl, rs, n);
+        if (n >= 1) k_adj_T<P, C, 2><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
+        else k_adj_T<P, C, 1><<<row_grid_b(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
         rec->end();
         ++*launches;
     }
@@ -129,7 +152,7 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         for (int q = 0; q < 4; ++q)
             if (n <= pl.q[q].N) by += 2 * gTbytes(q, n - 1) + gTbytes(q, n) + bytes_T(pl, q, n - 1);
         rec->begin(K_ADJ_MERGE_UP, n, by);
-        k_adj_merge_up<P, C><<<dim3((unsigned)rs.start[4], vb), bs / 2, 0, st>>>(pl, rs, n);
+        k_adj_merge_up<P, C><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
         rec->end();
         ++*launches;
     }

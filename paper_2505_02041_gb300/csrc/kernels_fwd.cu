@@ -13,14 +13,27 @@ __global__ void __launch_bounds__(256) k_trace012(Plan pl, const float *__restri
     body_trace012<P, C>(pl, e, s, ed, sd, qmask, blockIdx.x, blockIdx.y, tr_smem);
 }
 
+// Row and v-block of this block: the launch grid is (rows, v-blocks), or
+// (v-blocks, rows) when the plan puts the v-blocks of a row side by side.
+__device__ __forceinline__ void row_block(const Plan &pl, long long &row, int &vb) {
+    if (pl.vmajor) { row = blockIdx.y; vb = blockIdx.x; }
+    else { row = blockIdx.x; vb = blockIdx.y; }
+}
+
 template <int P, int C, int G>
-__global__ void __launch_bounds__(128) k_merge_up(Plan pl, RowSplit rs, int n) {
-    body_merge_up<P, C, G>(pl, rs, n, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(512) k_merge_up(Plan pl, RowSplit rs, int n) {
+    long long row;
+    int vb;
+    row_block(pl, row, vb);
+    body_merge_up<P, C, G>(pl, rs, n, row, vb);
 }
 
 template <int P, int C, bool PAIR>
-__global__ void __launch_bounds__(256) k_merge_down(Plan pl, RowSplit rs, int n) {
-    body_merge_down<P, C, PAIR>(pl, rs, n, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(512) k_merge_down(Plan pl, RowSplit rs, int n) {
+    long long row;
+    int vb;
+    row_block(pl, row, vb);
+    body_merge_down<P, C, PAIR>(pl, rs, n, row, vb);
 }
 
 template <int P, int C, class OUT>
@@ -42,12 +55,20 @@ static RowSplit make_split(const Plan &pl, int n, int kind, int qsel) {
         long long rows = 0;
         if (qsel >= 0 && q != qsel) continue;
         if (kind == 0) rows = g.U;
-        else if (kind == 1) rows = (n <= g.N && n >= 3) ? (long long)g.Un[n] * ((1 << n) + 1) : 0;
-        else rows = (n < g.N) ? (long long)g.Un[n] * (1 << n) : 0;
+        else if (kind == 1) rows = (n <= g.N && n >= 3) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0;
+        else rows = (n < g.N) ? (long long)(g.Un[n] - 1) * (1 << n) : 0;
         acc += rows;
     }
     rs.start[4] = acc;
     return rs;
+}
+
+// Grid of a row kernel: `rows` rows of blocks covering `per_block` v each.
+static dim3 row_grid(const Plan &pl, long long rows, int per_block) {
+    int Vmax = 0;
+    for (int q = 0; q < 4; ++q) Vmax = pl.q[q].V > Vmax ? pl.q[q].V : Vmax;
+    const unsigned vb = (unsigned)((Vmax + per_block - 1) / per_block);
+    return pl.vmajor ? dim3(vb, (unsigned)rows) : dim3((unsigned)rows, vb);
 }
 
 static int vblocks(const Plan &pl, int bs) {
@@ -56,26 +77,36 @@ static int vblocks(const Plan &pl, int bs) {
     return (Vmax + bs - 1) / bs;
 }
 
+// Algorithmic bytes of T_n / R_n of frame q: the live columns x >= 1 only
+// (column 0 is dead and never touched).
+static double t_entry_bytes(const Plan &pl) {
+    return pl.C * (pl.prec == P_FP32 ? 4.0 : (pl.prec == P_FP64 ? 8.0 : 2.0)) + (pl.prec == P_FP64 ? 8.0 : 4.0);
+}
+
 double bytes_T(const Plan &pl, int q, int n) {
     const QuadGeom &g = pl.q[q];
     if (n < 0 || n > g.N) return 0.0;
-    const double vt = pl.C * (pl.prec == P_FP32 ? 4.0 : (pl.prec == P_FP64 ? 8.0 : 2.0)) + (pl.prec == P_FP64 ? 8.0 : 4.0);
-    return double(g.Un[n]) * ((1 << n) + 1) * g.V * vt;
+    return double(g.Un[n] - 1) * ((1 << n) + 1) * g.V * t_entry_bytes(pl);
+}
+
+// The odd live columns of T_n (read by the level-n merge down, Eq. 14).
+double bytes_T_odd(const Plan &pl, int q, int n) {
+    const QuadGeom &g = pl.q[q];
+    if (n < 0 || n > g.N) return 0.0;
+    return double(g.Un[n] / 2) * ((1 << n) + 1) * g.V * t_entry_bytes(pl);
 }
 
 double bytes_R(const Plan &pl, int q, int n) {
     const QuadGeom &g = pl.q[q];
     if (n < 0 || n >= g.N) return 0.0;
     const double vr = pl.C * (pl.prec == P_FP32 ? 4.0 : (pl.prec == P_FP64 ? 8.0 : 2.0));
-    return double(g.Un[n]) * (1 << n) * g.V * vr;
+    return double(g.Un[n] - 1) * (1 << n) * g.V * vr;
 }
 
 template <int P, int C>
 static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
                             cudaStream_t st, int *launches, Recorder *rec, bool with_sum) {
     const int bs = 256;
-    const int vb = vblocks(pl, bs);            // blocks of 256 v
-    const int vbg = vblocks(pl, 2 * bs);       // blocks of 512 v (two groups per thread)
     int Nmax = 0;
     for (int q = 0; q < 4; ++q) Nmax = pl.q[q].N > Nmax ? pl.q[q].N : Nmax;
     const float *ef = (const float *)e, *sf = (const float *)s;
@@ -106,10 +137,10 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             double by = 0;
             for (int q = 0; q < 4; ++q)
                 if ((qsel < 0 || q == qsel) && n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
-            dim3 grid((unsigned)rs.start[4], vbg);
+            const int mt = pl.mthreads;
             rec->begin(K_MERGE_UP, n, by);
-            if (pl.mgroups == 2) k_merge_up<P, C, 2><<<grid, bs / 2, 0, st>>>(pl, rs, n);
-            else k_merge_up<P, C, 1><<<dim3((unsigned)rs.start[4], vb), bs / 2, 0, st>>>(pl, rs, n);
+            if (pl.mgroups == 2) k_merge_up<P, C, 2><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
+            else k_merge_up<P, C, 1><<<row_grid(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
             rec->end();
             ++*launches;
         }
@@ -121,15 +152,17 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                 const QuadGeom &g = pl.q[q];
                 if ((qsel >= 0 && q != qsel) || n >= g.N) continue;
                 // odd columns of T_n, even directions of T_{n+1}, R_{n+1} once, R_n written
-                by += bytes_T(pl, q, n) * (double(g.Un[n] / 2) / g.Un[n]);
+                by += bytes_T_odd(pl, q, n);
                 by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
                 by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
             }
-            dim3 grid((unsigned)rs.start[4], vbg);
+            const int mt = pl.mthreads;
             rec->begin(K_MERGE_DOWN, n, by);
-            dim3 g1((unsigned)rs.start[4], vb);
-            if (n >= 1) k_merge_down<P, C, true><<<g1, bs / 2, 0, st>>>(pl, rs, n);
-            else k_merge_down<P, C, false><<<g1, bs, 0, st>>>(pl, rs, n);
+            if (n >= 1) k_merge_down<P, C, true><<<row_grid(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
+            else {
+                const int ts = 2 * mt > 512 ? 512 : 2 * mt;   // single v per thread at level 0
+                k_merge_down<P, C, false><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
+            }
             rec->end();
             ++*launches;
         }

@@ -4,7 +4,8 @@
 
 namespace hrc {
 
-// T_n of frame q -> dst[x][k][v][C+1] (C radiances, then linear T).
+// T_n of frame q -> dst[x][k][v][C+1] (C radiances, then linear T).  Column
+// x = 0 is never computed (no fluence depends on it) and is exported as NaN.
 template <int P, int C>
 __global__ void k_export_T(Plan pl, int q, int n, float *__restrict__ dst) {
     const QuadGeom &g = pl.q[q];
@@ -16,15 +17,20 @@ __global__ void k_export_T(Plan pl, int q, int n, float *__restrict__ dst) {
         const int v = (int)(i % g.V);
         const long long r = i / g.V;
         const int k = (int)(r % K), x = (int)(r / K);
-        Iv<P, C> iv = T.load(x, k, v);
         float *o = dst + i * (C + 1);
+        if (x == 0) {
+#pragma unroll
+            for (int c = 0; c <= C; ++c) o[c] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        Iv<P, C> iv = T.load(x, k, v);
 #pragma unroll
         for (int c = 0; c < C; ++c) o[c] = (float)iv.L[c];
         o[C] = (float)iv.trans();
     }
 }
 
-// R_n of frame q -> dst[x][i][v][C].
+// R_n of frame q -> dst[x][i][v][C]; column 0 exported as NaN.
 template <int P, int C>
 __global__ void k_export_R(Plan pl, int q, int n, float *__restrict__ dst) {
     const QuadGeom &g = pl.q[q];
@@ -37,7 +43,7 @@ __global__ void k_export_R(Plan pl, int q, int n, float *__restrict__ dst) {
         const long long r = i / g.V;
         const int ip = (int)(r % I), x = (int)(r / I);
 #pragma unroll
-        for (int c = 0; c < C; ++c) dst[i * C + c] = (float)R.load(x, ip, c, v);
+        for (int c = 0; c < C; ++c) dst[i * C + c] = x == 0 ? __int_as_float(0x7fc00000) : (float)R.load(x, ip, c, v);
     }
 }
 

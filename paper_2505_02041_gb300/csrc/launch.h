@@ -133,6 +133,7 @@ cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *ds
 // phase, each written once): T entries of C radiances + 1 transmittance,
 // R entries of C values.
 double bytes_T(const Plan &pl, int q, int n);
+double bytes_T_odd(const Plan &pl, int q, int n);
 double bytes_R(const Plan &pl, int q, int n);
 
 }  // namespace hrc

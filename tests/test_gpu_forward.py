@@ -56,7 +56,11 @@ def test_forward_vacuum_is_zero():
 
 @pytest.mark.parametrize("q", range(4))
 def test_levels_match_oracle(q):
-    """Every T_n and R_n level of every quadrant frame, element by element."""
+    """Every T_n and R_n level of every quadrant frame, element by element.
+
+    Column x = 0 of every level is dead (the fluence sum reads R_0 at u + 1,
+    and column 0 feeds only column 0 of the neighbouring levels): the library
+    never computes it and exports it as NaN; every other column is compared."""
     require_gpu()
     e, s = scenes.random_scene(48, 40, 2, 12)
     h, _ = _gpu_F(e, s)
@@ -66,11 +70,14 @@ def test_levels_match_oracle(q):
         Tg = h.level(q, "T", n).cpu().numpy()
         Tr = oracle.frame_level(e, s, q, "T", n)
         assert Tg.shape == Tr.shape
-        assert np.max(np.abs(Tg - Tr)) <= 2e-5 * max(1.0, np.max(np.abs(Tr))), (q, n)
+        assert np.all(np.isnan(Tg[0]))
+        if Tg.shape[0] > 1:
+            assert np.max(np.abs(Tg[1:] - Tr[1:])) <= 2e-5 * max(1.0, np.max(np.abs(Tr))), (q, n)
     for n in range(N):
         Rg = h.level(q, "R", n).cpu().numpy()
         Rr = oracle.frame_level(e, s, q, "R", n)
-        assert np.max(np.abs(Rg - Rr)) <= 2e-5 * max(1.0, np.max(np.abs(Rr))), (q, n)
+        assert np.all(np.isnan(Rg[0]))
+        assert np.max(np.abs(Rg[1:] - Rr[1:])) <= 2e-5 * max(1.0, np.max(np.abs(Rr))), (q, n)
 
 
 @pytest.mark.parametrize("name", ["fog512", "volumetric1024"])

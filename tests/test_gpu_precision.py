@@ -45,9 +45,9 @@ def test_reduced_precision_levels_log_transmittance(prec):
     require_gpu()
     e, s = scenes.random_scene(48, 40, 2, 3)
     h, _ = _F(e, s, prec)
-    for n in (0, 2, 4, 6):
-        Tg = h.level(1, "T", n).cpu().numpy()
-        Tr = oracle.frame_level(e, s, 1, "T", n)
+    for n in (0, 2, 4, 5):
+        Tg = h.level(1, "T", n).cpu().numpy()[1:]   # column 0 is dead (not computed)
+        Tr = oracle.frame_level(e, s, 1, "T", n)[1:]
         assert np.max(np.abs(Tg[..., -1] - Tr[..., -1])) <= 1e-5
         assert err_max(Tg[..., :-1], Tr[..., :-1]) <= BOUNDS[prec][0]
 
