@@ -106,8 +106,11 @@ hrc_status hrc_fluence_host(hrc_ctx *ctx, const float *emission, const float *si
 
 /* Adjoint of the last hrc_fluence on this context: given dLoss/dF (grad_F,
  * [C][H][W]), writes dLoss/d emission ([C][H][W]) and dLoss/d sigma_t
- * ([H][W]).  Outputs are overwritten, not accumulated.  The intervals are
- * recomputed from the borrowed inputs (no forward-time storage is assumed).
+ * ([H][W]).  Outputs are overwritten, not accumulated.  It reads the
+ * intervals T_n / R_n that the last forward left in the context's buffers
+ * and re-traces the borrowed inputs, which must be unchanged since that
+ * forward; it may be called several times (another grad_F) without a new
+ * forward.  Enqueue it on the forward's stream, or order the two streams.
  * HRC_ESTATE if no forward ran on this context. */
 hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_emission,
                                 float *grad_sigma_t);

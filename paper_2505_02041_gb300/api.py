@@ -44,14 +44,16 @@ class HRC:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.ctx = _lib.hrc_create(W, H, channels, cascades)
         self.precision = "fp32"
-        self._borrowed = (None, None)
+        self._borrowed = (None, None, 0, 0)
+        self._host_levels = False
         self.set_precision(precision)
 
     # -- configuration -----------------------------------------------------
     def set_precision(self, precision: str) -> None:
         _lib.hrc_set_precision(self.ctx, _PREC[precision])
         self.precision = precision
-        self._borrowed = (None, None)
+        self._borrowed = (None, None, 0, 0)
+        self._host_levels = False
 
     @property
     def dtype(self):
@@ -72,10 +74,22 @@ class HRC:
             _lib.hrc_fluence_f64(self.ctx, emission, sigma_t, out)
         else:
             _lib.hrc_fluence(self.ctx, emission, sigma_t, out)
-        self._borrowed = (emission, sigma_t)
+        self._borrowed = (emission, sigma_t, emission._version, sigma_t._version)
+        self._host_levels = False
         return out
 
     __call__ = forward
+
+    def _levels_current(self, emission, sigma_t) -> bool:
+        """True when the context's levels are those of these inputs (same
+        storage, not modified in place since the forward)."""
+        b = self._borrowed
+        if b[0] is None:
+            return False
+        if emission is None:
+            emission, sigma_t = b[0], b[1]
+        return (b[0].data_ptr() == emission.data_ptr() and b[1].data_ptr() == sigma_t.data_ptr() and
+                b[0]._version == b[2] and b[1]._version == b[3])
 
     def forward_host(self, emission, sigma_t, out=None):
         """Host (CPU) float32 tensors in and out, copies included."""
@@ -88,17 +102,21 @@ class HRC:
             out = torch.empty((C, H, W), dtype=torch.float32, pin_memory=emission.is_pinned())
         self._stream()
         _lib.hrc_fluence_host(self.ctx, emission, sigma_t, out)
-        self._borrowed = (None, None)
+        self._borrowed = (None, None, 0, 0)
+        self._host_levels = True     # levels of the context's own device copies
         return out
 
     def backward(self, grad_F, emission=None, sigma_t=None):
-        """dLoss/d(emission, sigma_t) of the last forward (or of the given
-        inputs, which are re-borrowed first when they differ)."""
+        """dLoss/d(emission, sigma_t) at the inputs of the last forward (or at
+        the given inputs).  The backward reads the levels that forward left in
+        the context, so the forward runs again first when the inputs differ
+        or were modified in place since."""
         C, H, W = self.C, self.H, self.W
-        if emission is not None and (self._borrowed[0] is None or
-                                     self._borrowed[0].data_ptr() != emission.data_ptr() or
-                                     self._borrowed[1].data_ptr() != sigma_t.data_ptr()):
+        if emission is None and not self._host_levels and self._borrowed[0] is not None:
+            emission, sigma_t = self._borrowed[0], self._borrowed[1]
+        if emission is not None and not self._levels_current(emission, sigma_t):
             self.forward(emission, sigma_t)
+        # (no forward at all: the library answers HRC_ESTATE)
         grad_F = _dev_tensor(grad_F, self.dtype, (C, H, W), "grad_F")
         ge = torch.empty((C, H, W), dtype=self.dtype, device=grad_F.device)
         gs = torch.empty((H, W), dtype=self.dtype, device=grad_F.device)
@@ -128,7 +146,8 @@ class HRC:
         hrc_autotune); returns its forward ms per frame."""
         self._stream()
         ms = _lib.hrc_autotune(self.ctx)
-        self._borrowed = (None, None)
+        self._borrowed = (None, None, 0, 0)
+        self._host_levels = False
         return ms
 
     def launch_count(self) -> int:

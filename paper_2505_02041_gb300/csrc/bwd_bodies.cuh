@@ -1,8 +1,8 @@
 // bwd_bodies.cuh -- device bodies of the adjoint (reverse-mode) HRC kernels.
 //
-// The backward pass recomputes T_0..T_N and R_0..R_{N-1} from the inputs
-// (forward bodies), then runs the exact reverse of every forward step in
-// gather form: each adjoint entry is written by exactly one thread that
+// The backward pass reads T_0..T_N and R_0..R_{N-1} as the forward pass left
+// them in the context's buffers and runs the exact reverse of every forward
+// step in gather form: each adjoint entry is written by exactly one thread that
 // collects every term feeding it, so there are no atomics and the result is
 // deterministic.
 //

@@ -69,7 +69,7 @@ __device__ __forceinline__ void batched_adjoint_item(const BatchArgs &a, const S
     }
 }
 
-// MODE 0: forward stages only; MODE 1: backward (forward levels + adjoint).
+// MODE 0: the forward stages; MODE 1: the adjoint stages of the backward.
 template <int P, int C, int MODE>
 __global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
     using IN = typename std::conditional<P == P_FP64, double, float>::type;
@@ -119,26 +119,27 @@ __global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
         const int vb = (int)(j % sb.nvb);
         const long long r0 = (j / sb.nvb) * sb.rpi;
         const long long r1 = r0 + sb.rpi < sb.rows ? r0 + sb.rpi : sb.rows;
-        switch (sb.kind) {
-        case BK_TRACE:
-            body_trace012<P, C>(pl, (const float *)e, (const float *)s, (const double *)e, (const double *)s, 15,
-                                vb, (int)(j / sb.nvb), smem);
-            break;
-        case BK_MERGE_UP:
-            for (long long r = r0; r < r1; ++r) body_merge_up<P, C>(pl, sb.rs, sb.level, r, vb);
-            break;
-        case BK_MERGE_DOWN2:
-            for (long long r = r0; r < r1; ++r) body_merge_down<P, C, true>(pl, sb.rs, sb.level, r, vb);
-            break;
-        case BK_MERGE_DOWN1:
-            for (long long r = r0; r < r1; ++r) body_merge_down<P, C, false>(pl, sb.rs, sb.level, r, vb);
-            break;
-        case BK_SUM:
-            for (long long r = r0; r < r1; ++r) body_fluence_sum<P, C, IN>(pl, (IN *)a.F + eo, vb, (int)r);
-            break;
-        default:   // adjoint kinds exist only in backward launches
-            if constexpr (MODE == 1) batched_adjoint_item<P, C, IN>(a, sb, pl, j, vb, r0, r1, eo, so, e, s, smem);
-            break;
+        if constexpr (MODE == 0) {
+            switch (sb.kind) {
+            case BK_TRACE:
+                body_trace012<P, C>(pl, (const float *)e, (const float *)s, (const double *)e, (const double *)s, 15,
+                                    vb, (int)(j / sb.nvb), smem);
+                break;
+            case BK_MERGE_UP:
+                for (long long r = r0; r < r1; ++r) body_merge_up<P, C>(pl, sb.rs, sb.level, r, vb);
+                break;
+            case BK_MERGE_DOWN2:
+                for (long long r = r0; r < r1; ++r) body_merge_down<P, C, true>(pl, sb.rs, sb.level, r, vb);
+                break;
+            case BK_MERGE_DOWN1:
+                for (long long r = r0; r < r1; ++r) body_merge_down<P, C, false>(pl, sb.rs, sb.level, r, vb);
+                break;
+            default:   // BK_SUM
+                for (long long r = r0; r < r1; ++r) body_fluence_sum<P, C, IN>(pl, (IN *)a.F + eo, vb, (int)r);
+                break;
+            }
+        } else {
+            batched_adjoint_item<P, C, IN>(a, sb, pl, j, vb, r0, r1, eo, so, e, s, smem);
         }
         __syncthreads();
         if (threadIdx.x == 0 && sb.own != a.withhold) {
@@ -218,42 +219,41 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
         d.bytes = bytes;
         out.push_back(d);
     };
-    double by = img * (pl.C + 1) * esz;
-    for (int q = 0; q < 4; ++q)
-        for (int n = 0; n <= 2; ++n) by += bytes_T(pl, q, n);
-    tilestage(BK_TRACE, tx, ty, by);
-    for (int n = 3; n <= Nmax; ++n) {
-        by = 0;
+    double by = 0;
+    if (mode == 0) {   // the backward reads the levels the forward left in the buffers
+        by = img * (pl.C + 1) * esz;
         for (int q = 0; q < 4; ++q)
-            if (n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
-        rowstage(BK_MERGE_UP, n, vb2, by);
-    }
-    for (int n = Nmax - 1; n >= 0; --n) {
-        by = 0;
-        for (int q = 0; q < 4; ++q) {
-            const QuadGeom &g = pl.q[q];
-            if (n >= g.N) continue;
-            by += bytes_T_odd(pl, q, n);
-            by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
-            by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
+            for (int n = 0; n <= 2; ++n) by += bytes_T(pl, q, n);
+        tilestage(BK_TRACE, tx, ty, by);
+        for (int n = 3; n <= Nmax; ++n) {
+            by = 0;
+            for (int q = 0; q < 4; ++q)
+                if (n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
+            rowstage(BK_MERGE_UP, n, vb2, by);
         }
-        rowstage(n >= 1 ? BK_MERGE_DOWN2 : BK_MERGE_DOWN1, n, n >= 1 ? vb2 : vb1, by);
-    }
-    if (mode == 0) {
+        for (int n = Nmax - 1; n >= 0; --n) {
+            by = 0;
+            for (int q = 0; q < 4; ++q) {
+                const QuadGeom &g = pl.q[q];
+                if (n >= g.N) continue;
+                by += bytes_T_odd(pl, q, n);
+                by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
+                by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
+            }
+            rowstage(n >= 1 ? BK_MERGE_DOWN2 : BK_MERGE_DOWN1, n, n >= 1 ? vb2 : vb1, by);
+        }
         by = img * pl.C * esz;
         for (int q = 0; q < 4; ++q) by += bytes_R(pl, q, 0);
-        {   // fluence sum: rows = image rows, 16 per item
-            StageDesc d;
-            d.kind = BK_SUM;
-            d.level = 0;
-            std::memset(&d.rs, 0, sizeof(d.rs));
-            d.nvb = (pl.W + 255) / 256;
-            d.rows = pl.H;
-            d.rpi = 16;
-            d.count = (int)((d.rows + d.rpi - 1) / d.rpi * d.nvb);
-            d.bytes = by;
-            out.push_back(d);
-        }
+        StageDesc d;   // fluence sum: rows = image rows, 16 per item
+        d.kind = BK_SUM;
+        d.level = 0;
+        std::memset(&d.rs, 0, sizeof(d.rs));
+        d.nvb = (pl.W + 255) / 256;
+        d.rows = pl.H;
+        d.rpi = 16;
+        d.count = (int)((d.rows + d.rpi - 1) / d.rpi * d.nvb);
+        d.bytes = by;
+        out.push_back(d);
         return;
     }
     const double ab = 4.0;   // adjoint buffers are fp32 in the batched precisions
@@ -296,13 +296,11 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
 }
 
 // Dynamic shared memory of a launch: the forward needs the trace tile, the
-// backward also the adjoint-trace tile and the transposed dL/dF tile.
+// backward the adjoint-trace tile and the transposed dL/dF tile.
 template <int P, int C> size_t batched_smem(int mode) {
     using A = typename Prec<P>::A;
-    size_t m = TraceTile<A, C>::bytes();
-    if (mode == 0) return m;
-    m = m > adj_trace_smem<A, C>() ? m : adj_trace_smem<A, C>();
-    const size_t sum_tile = sizeof(A) * C * 32 * 33;
+    if (mode == 0) return TraceTile<A, C>::bytes();
+    const size_t m = adj_trace_smem<A, C>(), sum_tile = sizeof(A) * C * 32 * 33;
     return m > sum_tile ? m : sum_tile;
 }
 

@@ -107,9 +107,8 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         const QuadGeom &g = pl.q[q];
         return (n < 0 || n >= g.N) ? 0.0 : double(g.Un[n] - 1) * (1 << n) * g.V * pl.C * ab;
     };
-    // forward recompute of every T and R level (no fluence sum)
-    cudaError_t err = launch_forward_levels(pl, rt, e, s, st, launches, rec);
-    if (err != cudaSuccess) return err;
+    // T_0..T_N and R_0..R_{N-1} are the ones the last forward left in the
+    // plan's buffers (the inputs are unchanged since, by contract).
     {
         double by = img * pl.C * ab;
         for (int q = 0; q < 4; ++q) by += gRbytes(q, 0);

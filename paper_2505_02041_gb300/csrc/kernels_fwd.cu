@@ -212,11 +212,6 @@ cudaError_t prepare_forward_kernels() {
     return e;
 }
 
-cudaError_t launch_forward_levels(const Plan &pl, const RayTable &rt, const void *e, const void *s,
-                                  cudaStream_t st, int *launches, Recorder *rec) {
-    return launch_forward(pl, rt, e, s, nullptr, st, launches, rec);
-}
-
 cudaError_t launch_forward(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
                            cudaStream_t st, int *launches, Recorder *rec) {
     switch (pl.prec) {

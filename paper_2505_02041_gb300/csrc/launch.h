@@ -92,7 +92,7 @@ struct BatchArgs {
 };
 
 // Stage list of one scene: mode 0 = forward (with the fluence sum),
-// mode 1 = backward (forward levels recomputed, then every adjoint step).
+// mode 1 = backward (every adjoint step over the levels of the last forward).
 struct StageDesc {
     int kind, level, count, nvb, rpi;
     long long rows;
@@ -111,12 +111,9 @@ int plan_nmax(const Plan &pl);
 // Message returned by hrc_last_error(NULL) on this thread.
 void set_global_error(const char *msg);
 
-// Forward without the fluence sum: every T and R level (for the backward).
-cudaError_t launch_forward_levels(const Plan &pl, const RayTable &rt, const void *e, const void *s,
-                                  cudaStream_t st, int *launches, Recorder *rec);
-
-// Backward pass: recompute every level from (e, s), then the adjoint of
-// every step; writes dL/de (ge) and dL/dsigma (gs) from dL/dF (gF).
+// Backward pass: the adjoint of every step over the levels the last forward
+// left in the plan's buffers; writes dL/de (ge) and dL/dsigma (gs) from
+// dL/dF (gF), re-tracing (e, s).
 cudaError_t launch_backward(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,
                             void *ge, void *gs, cudaStream_t st, int *launches, Recorder *rec);
 

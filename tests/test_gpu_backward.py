@@ -124,3 +124,29 @@ def test_backward_before_forward_is_a_state_error():
     with pytest.raises(_lib.HRCError) as ex:
         h.backward(g)
     assert ex.value.status == _lib.HRC_ESTATE
+
+
+def test_backward_reuses_levels_and_tracks_in_place_changes():
+    """The backward reads the levels the forward left in the context: two
+    backward calls in a row (another dL/dF, no forward between) each match
+    the oracle, and an input modified in place since the forward makes the
+    Python binding run the forward again, so the gradient is the one at the
+    new inputs."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC
+    e, s = scenes.random_scene(45, 38, 2, 21)
+    g1 = scenes.rng(31).normal(size=e.shape).astype(np.float32)
+    g2 = scenes.rng(32).normal(size=e.shape).astype(np.float32)
+    h = HRC(45, 38, 2)
+    ed, sd = to_dev(e), to_dev(s)
+    h.forward(ed, sd)
+    for g in (g1, g2):
+        ge, gs = h.backward(to_dev(g))
+        ge_r, gs_r = oracle.fluence_adjoint(e, s, g)
+        assert err_max(ge.cpu().numpy(), ge_r) <= 1e-4
+        assert err_max(gs.cpu().numpy(), gs_r) <= 1e-4
+    sd.mul_(1.7)                       # in place: same storage, new version
+    ge, gs = h.backward(to_dev(g1), ed, sd)
+    ge_r, gs_r = oracle.fluence_adjoint(e, s * np.float32(1.7), g1)
+    assert err_max(ge.cpu().numpy(), ge_r) <= 1e-4
+    assert err_max(gs.cpu().numpy(), gs_r) <= 1e-4
