@@ -310,128 +310,272 @@ __device__ __forceinline__ void body_adj_merge_up(const Plan &pl, const RowSplit
 //   dL/de_j     = gL P_j w_j
 //   dL/dsigma_j = sum_c gL_c (P_j e_jc dw_j/dsigma - l_j S_jc) - gT l_j T,
 //   S_j = sum_{m>j} P_m e_m w_m,   dw/dsigma = l^2 phi'(sigma l).
-// Each tile pixel gathers, for every quadrant, ray shape R and piece index
-// J, the one ray that crosses it as its piece J (probe = pixel - offset_J),
-// and re-traces that ray from the staged tile (shapes unrolled at compile
-// time, per-pixel piece factors from the tile, as in the forward trace).
+// Writing G_j = sum_{m<=j} P_m w_m (gL . e_m) (so that sum_c gL_c S_jc =
+// G_tot - G_j), the sigma term is
+//   dL/dsigma_j = [P_j dw_j (gL . e_j) + l_j G_j] - l_j (G_tot + gT T),
+// where the bracket is known at piece j and the last factor once per ray.
+//
+// Ray-centric and deterministic, one pair tile per block, per quadrant and
+// ray shape R (shapes unrolled at compile time):
+//   phase A: one thread per probe whose ray reaches the tile traces the ray
+//            once from the staged tile and writes each piece's
+//            (dL/de_j, dL/dsigma_j) to a shared-memory slot [j][probe];
+//   phase B: each tile pixel adds, piece index by piece index, the slot of
+//            the one probe whose ray crosses it as piece j
+//            (probe = pixel - offset_j), so the summation order is fixed.
 // ---------------------------------------------------------------------------
 
-// dw/dsigma of a half piece of length l with t = exp(-sigma l):
-// l^2 phi'(sigma l), phi'(x) = (e^-x (1 + x) - 1) / x^2, by its Taylor
-// series near 0.
-__device__ __forceinline__ float dw_dsigma(float sg, float len, float t) {
-    const float tau = sg * len;
-    const float series = len * len * (-0.5f + tau * (1.f / 3.f + tau * (-1.f / 8.f + tau * (1.f / 30.f))));
-    return fabsf(tau) < 0.05f ? series : (t * (1.f + tau) - 1.f) / (sg * sg);
+// Probe box of ray shape R for a tile of PT_U x PT_V frame pixels: the probes
+// (spacing S = 2^n along u) whose ray reaches the tile lie in
+// u in [u0 - S, u0 + PT_U) (PT_U / S + 1 aligned columns) and
+// v in [v0 - dvhi, v0 + PT_V - dvlo), dv of the shape in [dvlo, dvhi] (one
+// sign: a ray is monotone in v).
+constexpr int shape_dv_min(int R) {
+    int m = 0;
+    for (int j = kShapes.start[R]; j < kShapes.start[R + 1]; ++j) m = kShapes.p[j].dv < m ? kShapes.p[j].dv : m;
+    return m;
 }
-__device__ __forceinline__ double dw_dsigma(double sg, double len, double t) {
-    const double tau = sg * len;
-    if (fabs(tau) < 1e-2)
-        return len * len * (-0.5 + tau * (1.0 / 3.0 + tau * (-1.0 / 8.0 + tau * (1.0 / 30.0 + tau * (-1.0 / 144.0 + tau * (1.0 / 840.0))))));
-    return (t * (1.0 + tau) - 1.0) / (sg * sg);
+constexpr int shape_dv_max(int R) {
+    int m = 0;
+    for (int j = kShapes.start[R]; j < kShapes.start[R + 1]; ++j) m = kShapes.p[j].dv > m ? kShapes.p[j].dv : m;
+    return m;
 }
+constexpr int shape_slots(int R) {
+    const int n = R < 2 ? 0 : (R < 5 ? 1 : 2);
+    return (kShapes.start[R + 1] - kShapes.start[R]) * (PT_U / (1 << n) + 1) *
+           (PT_V + shape_dv_max(R) - shape_dv_min(R));
+}
+constexpr int adj_max_slots() {
+    int m = 0;
+    for (int R = 0; R < HRC_MAXRAY; ++R) m = shape_slots(R) > m ? shape_slots(R) : m;
+    return m;
+}
+constexpr int ADJ_SLOTS = adj_max_slots();
 
-// Re-trace pieces M .. END-1 of a ray; piece J is the one at the gathering
-// pixel.  Accumulates the attenuated radiance of all pieces (Ltot) and of
-// pieces <= J (Lle), and records P_J, the half-piece factors of J, its
-// extinction and emission.
-template <class A, int C, int M, int END, int J>
-__device__ __forceinline__ void adj_retrace(const PairTile<A, C> &tt, int base, int su, A &Pp, A (&Ltot)[C],
-                                            A (&Lle)[C], A &Pj, A &tj, A &wj, A &sj, A (&ej)[C]) {
-    if constexpr (M < END) {
-        using pc = PieceAt<M>;
-        const int o = base + pc::du * su + pc::dv;
-        A t, w, em[C], sg;
-        tt.piece(pc::cls, o, t, w);
-        tt.emis(o, em, sg);
-        if constexpr (M == J) {
-            tj = t;
-            wj = w;
-            sj = sg;
-            Pj = Pp;
+constexpr int ADJ_THREADS = 256;   // block size of the adjoint trace
+constexpr int ADJ_ROUNDS = 3;      // probes per thread and shape, at most
+
+template <int R> struct RayBox {
+    static constexpr int n = RayAt<R>::n, k = RayAt<R>::k, S = 1 << n;
+    static constexpr int NP = RayAt<R>::end - RayAt<R>::begin;
+    static constexpr int dvlo = shape_dv_min(R), dvhi = shape_dv_max(R);
+    static constexpr int NVB = PT_V + dvhi - dvlo;
+    static constexpr int NPROBE = (PT_U / S + 1) * NVB;
+    static constexpr int ROUNDS = (NPROBE + ADJ_THREADS - 1) / ADJ_THREADS;
+    static_assert(dvlo == 0 || dvhi == 0, "a ray is monotone in v");
+    static_assert(S <= PT_HALO && dvhi - dvlo <= PT_HALO, "the halo covers every probe of the box");
+    static_assert(ROUNDS <= ADJ_ROUNDS, "prefetch registers");
+};
+
+// dL/dT of the rays of one shape for the thread's probes (round r = probe
+// threadIdx.x + r * ADJ_THREADS), loaded ahead of their use.
+template <class A, int C> struct AdjPre {
+    A gL[ADJ_ROUNDS][C], gT[ADJ_ROUNDS];
+};
+
+// Per-(piece, probe) slots: fp32 with C <= 3 as float4 {dE_0..dE_{C-1}, dS};
+// otherwise C + 1 planes.
+template <class A, int C> struct AdjSlots {
+    static constexpr bool packed = PackES<A, C>::packed;
+    A *p;
+    static constexpr size_t bytes() { return packed ? sizeof(float4) * ADJ_SLOTS : sizeof(A) * (C + 1) * ADJ_SLOTS; }
+    __device__ __forceinline__ void put(int i, const A (&dE)[C], A dS) const {
+        if constexpr (packed) {
+            float4 v = make_float4(dE[0], 0.f, 0.f, dS);
+            if constexpr (C > 1) v.y = dE[1];
+            if constexpr (C > 2) v.z = dE[2];
+            reinterpret_cast<float4 *>(p)[i] = v;
+        } else {
 #pragma unroll
-            for (int c = 0; c < C; ++c) ej[c] = em[c];
+            for (int c = 0; c < C; ++c) p[c * ADJ_SLOTS + i] = dE[c];
+            p[C * ADJ_SLOTS + i] = dS;
         }
-        if constexpr (pc::full != 0) {
-            w = w * (A(1) + t);
+    }
+    __device__ __forceinline__ void add_to(int i, A (&dE)[C], A &dS) const {
+        if constexpr (packed) {
+            const float4 v = reinterpret_cast<const float4 *>(p)[i];
+            dE[0] += v.x;
+            if constexpr (C > 1) dE[1] += v.y;
+            if constexpr (C > 2) dE[2] += v.z;
+            dS += v.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) dE[c] += p[c * ADJ_SLOTS + i];
+            dS += p[C * ADJ_SLOTS + i];
+        }
+    }
+};
+
+// Phase A, pieces J .. end-1 of shape R for the ray at region offset `base`.
+// Pp: transmittance before piece J; G: sum over earlier pieces of
+// P_m w_m (gL . e_m).  Writes dE[j] and the known part of dS[j].
+template <class A, int C, int R, int J>
+__device__ __forceinline__ void adj_pieces(const PairTile<A, C> &tt, int base, int su, const A (&gL)[C], A &Pp, A &G,
+                                           A (&dE)[RayBox<R>::NP][C], A (&dS)[RayBox<R>::NP]) {
+    if constexpr (J < RayAt<R>::end) {
+        using pc = PieceAt<J>;
+        constexpr int L = J - RayAt<R>::begin;
+        const int o = base + pc::du * su + pc::dv;
+        A t, w, d, em[C], sg;
+        tt.piece(pc::cls, o, t, w, d);
+        tt.emis(o, em, sg);
+        const A lh = class_len<A>(pc::cls);
+        A wq = w;
+        if constexpr (pc::full != 0) {                // w2 = w (1 + t), dw2 = d (1 + t) - l t w, t2 = t^2
+            d = fma(d, A(1) + t, -lh * t * w);
+            wq = w * (A(1) + t);
             t = t * t;
         }
-        const A pw = Pp * w;
+        const A len = pc::full != 0 ? A(2) * lh : lh;
+        A ge = A(0);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            Ltot[c] = fma(pw, em[c], Ltot[c]);
-            if constexpr (M <= J) Lle[c] = fma(pw, em[c], Lle[c]);
-        }
+        for (int c = 0; c < C; ++c) ge = fma(gL[c], em[c], ge);
+        const A pw = Pp * wq;
+#pragma unroll
+        for (int c = 0; c < C; ++c) dE[L][c] = gL[c] * pw;
+        G = fma(pw, ge, G);
+        dS[L] = fma(Pp * d, ge, len * G);
         Pp *= t;
-        adj_retrace<A, C, M + 1, END, J>(tt, base, su, Pp, Ltot, Lle, Pj, tj, wj, sj, ej);
+        adj_pieces<A, C, R, J + 1>(tt, base, su, gL, Pp, G, dE, dS);
     }
 }
 
-template <int P, int C, int R, int J>
-__device__ __forceinline__ void adj_gather(const Plan &pl, const PairTile<typename Prec<P>::A, C> &tt, int q, int nmax,
-                                           int V, int us, int vs, int base, int su,
-                                           typename Prec<P>::A (&dE)[C], typename Prec<P>::A &dS) {
-    using A = typename Prec<P>::A;
-    using ray = RayAt<R>;
-    if constexpr (J < ray::end) {
+template <class A, int R, int J>
+__device__ __forceinline__ void adj_finish(A K, A (&dS)[RayBox<R>::NP]) {
+    if constexpr (J < RayAt<R>::end) {
         using pc = PieceAt<J>;
-        const int up = us - pc::du, vp = vs - pc::dv;
-        if (up >= 1 && !(up & ((1 << ray::n) - 1)) && vp >= 0 && vp < V) {   // probes at u = 0 are dead
-            A gL[C], gT;
-            GTLevel<P, C>(pl, q, ray::n).load(up >> ray::n, ray::k, vp, gL, gT);
-            const int pbase = base - pc::du * su - pc::dv;
-            A Pp = A(1), Pj = A(0), tj = A(1), wj = A(0), sj = A(0);
-            A Ltot[C], Lle[C], ej[C];
+        const A len = pc::full != 0 ? A(2) * class_len<A>(pc::cls) : class_len<A>(pc::cls);
+        dS[J - RayAt<R>::begin] = fma(-len, K, dS[J - RayAt<R>::begin]);
+        adj_finish<A, R, J + 1>(K, dS);
+    }
+}
+
+// Geometry of one quadrant frame of the tile: u0 / v0 = the tile's first
+// frame column / row (u0 may be negative at the image edge for the reversed
+// frames), tu = the tile's image origin along u, fwd = frame u runs with the
+// image axis.
+struct AdjFrame {
+    int q, U, V, u0, v0, tu;
+    bool fwd;
+};
+
+// Probe of round r of shape R: frame position and whether it is a live
+// probe inside the frame.
+template <int R>
+__device__ __forceinline__ bool adj_probe(const AdjFrame &f, int ua, int i, int &up, int &vp) {
+    using B = RayBox<R>;
+    const int col = i / B::NVB, vb = i - col * B::NVB;
+    up = ua + col * B::S;
+    vp = f.v0 - B::dvhi + vb;
+    return i < B::NPROBE && up >= 1 && up < f.U && vp >= 0 && vp < f.V;   // probes at u = 0 are dead
+}
+
+template <int P, int C, int R>
+__device__ __forceinline__ void adj_prefetch(const Plan &pl, const AdjFrame &f, AdjPre<typename Prec<P>::A, C> &pre) {
+    using B = RayBox<R>;
+    const int ua = (f.u0 - 1) & ~(B::S - 1);      // first aligned column >= u0 - S
+    const GTLevel<P, C> gTl(pl, f.q, B::n);
 #pragma unroll
-            for (int c = 0; c < C; ++c) { Ltot[c] = A(0); Lle[c] = A(0); ej[c] = A(0); }
-            adj_retrace<A, C, ray::begin, ray::end, J>(tt, pbase, su, Pp, Ltot, Lle, Pj, tj, wj, sj, ej);
-            const A lh = class_len<A>(pc::cls);
-            A d = dw_dsigma(sj, lh, tj);
-            A wq = wj, len = lh;
-            if constexpr (pc::full != 0) {            // w2 = w (1 + t), dw2 = d (1 + t) - l t w
-                d = fma(d, A(1) + tj, -lh * tj * wj);
-                wq = wj * (A(1) + tj);
-                len = A(2) * lh;
-            }
-            A g = -gT * len * Pp;                     // Pp is now the ray's total T
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                dE[c] = fma(gL[c], Pj * wq, dE[c]);
-                g = fma(gL[c], Pj * ej[c] * d - len * (Ltot[c] - Lle[c]), g);
-            }
-            dS += g;
-        }
-        adj_gather<P, C, R, J + 1>(pl, tt, q, nmax, V, us, vs, base, su, dE, dS);
+    for (int r = 0; r < B::ROUNDS; ++r) {
+        int up, vp;
+        if (adj_probe<R>(f, ua, threadIdx.x + r * ADJ_THREADS, up, vp)) gTl.load(up >> B::n, B::k, vp, pre.gL[r], pre.gT[r]);
     }
 }
 
 template <int P, int C, int R>
-__device__ __forceinline__ void adj_ray(const Plan &pl, const PairTile<typename Prec<P>::A, C> &tt, int q, int nmax,
-                                        int V, int us, int vs, int base, int su,
-                                        typename Prec<P>::A (&dE)[C], typename Prec<P>::A &dS) {
-    if constexpr (R < HRC_MAXRAY) {
-        if (RayAt<R>::n <= nmax) adj_gather<P, C, R, RayAt<R>::begin>(pl, tt, q, nmax, V, us, vs, base, su, dE, dS);
-        adj_ray<P, C, R + 1>(pl, tt, q, nmax, V, us, vs, base, su, dE, dS);
+__device__ __forceinline__ void adj_phase_a(const PairTile<typename Prec<P>::A, C> &tt,
+                                            const AdjSlots<typename Prec<P>::A, C> &sl, const AdjFrame &f,
+                                            const AdjPre<typename Prec<P>::A, C> &pre) {
+    using A = typename Prec<P>::A;
+    using B = RayBox<R>;
+    const int ua = (f.u0 - 1) & ~(B::S - 1);
+    const int su = f.fwd ? PT_PITCH : -PT_PITCH;
+#pragma unroll
+    for (int r = 0; r < B::ROUNDS; ++r) {
+        const int i = threadIdx.x + r * ADJ_THREADS;
+        if (i >= B::NPROBE) break;
+        int up, vp;
+        A dE[B::NP][C], dS[B::NP];
+        if (adj_probe<R>(f, ua, i, up, vp)) {
+            const int ap = (f.fwd ? up - f.tu : f.U - 1 - up - f.tu) + PT_HALO;
+            const int base = ap * PT_PITCH + (vp - f.v0 + PT_HALO);
+            A Pp = A(1), G = A(0);
+            adj_pieces<A, C, R, RayAt<R>::begin>(tt, base, su, pre.gL[r], Pp, G, dE, dS);
+            adj_finish<A, R, RayAt<R>::begin>(fma(pre.gT[r], Pp, G), dS);   // Pp is now the ray's T
+        } else {
+#pragma unroll
+            for (int l = 0; l < B::NP; ++l) {
+                dS[l] = A(0);
+#pragma unroll
+                for (int c = 0; c < C; ++c) dE[l][c] = A(0);
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < B::NP; ++l) sl.put(l * B::NPROBE + i, dE[l], dS[l]);
     }
 }
 
-// Shared memory of the adjoint trace: the pair tile, then (pair 0 only) a
-// transposed accumulator so that dL/de and dL/dsigma leave coalesced.
+template <class A, int C, int R, int J>
+__device__ __forceinline__ void adj_phase_b(const AdjSlots<A, C> &sl, int u, int v, int ua, int v0, A (&dE)[C], A &dS) {
+    if constexpr (J < RayAt<R>::end) {
+        using B = RayBox<R>;
+        using pc = PieceAt<J>;
+        const int up = u - pc::du;
+        if ((up & (B::S - 1)) == 0)
+            sl.add_to((J - RayAt<R>::begin) * B::NPROBE + ((up - ua) >> B::n) * B::NVB + (v - pc::dv - v0 + B::dvhi),
+                      dE, dS);
+        adj_phase_b<A, C, R, J + 1>(sl, u, v, ua, v0, dE, dS);
+    }
+}
+
+// Every shape R <= HRC_MAXRAY - 1 with level <= nmax (shapes are ordered by
+// level): phase A from the prefetched dL/dT, prefetch of the next shape's,
+// barrier, phase B for the thread's two pixels (frame columns uc[i],
+// valid[i]), barrier.  nmax is uniform over the block, so are the barriers.
+template <int P, int C, int R>
+__device__ __forceinline__ void adj_shapes(const Plan &pl, const PairTile<typename Prec<P>::A, C> &tt,
+                                           const AdjSlots<typename Prec<P>::A, C> &sl, const AdjFrame &f, int nmax,
+                                           const int (&uc)[2], const bool (&valid)[2], int v,
+                                           AdjPre<typename Prec<P>::A, C> &pre,
+                                           typename Prec<P>::A (&dE)[2][C], typename Prec<P>::A (&dS)[2]) {
+    using A = typename Prec<P>::A;
+    if constexpr (R < HRC_MAXRAY) {
+        if (RayAt<R>::n <= nmax) {
+            adj_phase_a<P, C, R>(tt, sl, f, pre);
+            if constexpr (R + 1 < HRC_MAXRAY)
+                if (RayAt<R + 1>::n <= nmax) adj_prefetch<P, C, R + 1>(pl, f, pre);
+            __syncthreads();
+            const int ua = (f.u0 - 1) & ~(RayBox<R>::S - 1);
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+                if (valid[i]) adj_phase_b<A, C, R, RayAt<R>::begin>(sl, uc[i], v, ua, f.v0, dE[i], dS[i]);
+            __syncthreads();
+        }
+        adj_shapes<P, C, R + 1>(pl, tt, sl, f, nmax, uc, valid, v, pre, dE, dS);
+    }
+}
+
+// Shared memory of the adjoint trace: the pair tile, then the slots (reused
+// at the end, pair 0, as a transposed accumulator so that dL/de and
+// dL/dsigma leave coalesced).
 template <class A, int C> constexpr size_t adj_trace_smem() {
-    return PairTile<A, C>::bytes() + sizeof(A) * (C + 1) * PT_V * (PT_U + 1);
+    const size_t acc = sizeof(A) * (C + 1) * PT_V * (PT_U + 1);
+    const size_t sl = AdjSlots<A, C>::bytes();
+    return PairTile<A, C>::bytes() + (sl > acc ? sl : acc);
 }
 
 // dL/de and dL/dsigma of quadrant pair `pair` for one tile.  Each thread
-// owns the two pixels of its tile columns for both frames of the pair and
-// accumulates in registers.  Pair 0 writes the image gradients, pair 1
-// (launched after it) adds to them.
+// owns two pixels of the tile (columns c[i] along u, its lane along v) and
+// accumulates them in registers over both frames of the pair.  Pair 0
+// writes the image gradients, pair 1 (launched after it) adds to them.
 template <int P, int C, class IN>
 __device__ __forceinline__ void body_adj_trace(const Plan &pl, const IN *__restrict__ e, const IN *__restrict__ s,
                                                IN *__restrict__ ge, IN *__restrict__ gs, int pair, int bx, int by,
                                                unsigned char *smem) {
     using A = typename Prec<P>::A;
     PairTile<A, C> tt(smem);
-    A *acc = reinterpret_cast<A *>(smem + PairTile<A, C>::bytes());   // [C+1][PT_V][PT_U+1]
+    const AdjSlots<A, C> sl{reinterpret_cast<A *>(smem + PairTile<A, C>::bytes())};
+    A *acc = sl.p;                                     // [C+1][PT_V][PT_U+1], after the last phase
     const int W = pl.W, H = pl.H;
     const long long HW = (long long)W * H;
     const int x0 = pair == 0 ? bx * PT_U : bx * PT_V;
@@ -439,34 +583,56 @@ __device__ __forceinline__ void body_adj_trace(const Plan &pl, const IN *__restr
     tt.stage(pair, W, H, x0, y0, e, s);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll 1
-    for (int i = 0; i < 2; ++i) {
-        const int c = 8 * i + ((warp + i) & 7);
-        A dE[C], dS = A(0);
+    int cc[2];
 #pragma unroll
-        for (int cc = 0; cc < C; ++cc) dE[cc] = A(0);
+    for (int i = 0; i < 2; ++i) cc[i] = 8 * i + ((warp + i) & 7);
+    A dE[2][C], dS[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        dS[i] = A(0);
+#pragma unroll
+        for (int c = 0; c < C; ++c) dE[i][c] = A(0);
+    }
 #pragma unroll 1
-        for (int qq = 0; qq < 2; ++qq) {
-            const int q = 2 * pair + qq;
-            const QuadGeom &g = pl.q[q];
-            if (g.N < 1) continue;
-            const int nmax = g.N < 2 ? g.N : 2;
-            const PairGeom pg = pair_geom(pl, q, x0, y0, c, lane);
-            if (!pg.valid) continue;
-            adj_ray<P, C, 0>(pl, tt, q, nmax, g.V, pg.u, pg.v, pg.base, pg.su, dE, dS);
+    for (int qq = 0; qq < 2; ++qq) {
+        const int q = 2 * pair + qq;
+        const QuadGeom &g = pl.q[q];
+        if (g.N < 1) continue;
+        AdjFrame f;
+        f.q = q;
+        f.U = g.U;
+        f.V = g.V;
+        f.fwd = (q == 0 || q == 2);
+        f.tu = pair == 0 ? x0 : y0;
+        f.v0 = pair == 0 ? y0 : x0;
+        f.u0 = f.fwd ? f.tu : f.U - PT_U - f.tu;
+        int uc[2];
+        bool valid[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int iu = f.tu + cc[i];               // image coordinate along u
+            valid[i] = iu < f.U && f.v0 + lane < f.V;
+            uc[i] = f.fwd ? iu : f.U - 1 - iu;
         }
+        AdjPre<A, C> pre;
+        adj_prefetch<P, C, 0>(pl, f, pre);
+        adj_shapes<P, C, 0>(pl, tt, sl, f, g.N < 2 ? g.N : 2, uc, valid, f.v0 + lane, pre, dE, dS);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int c = cc[i];
         // image pixel: pair 0 (c along x, lane along y); pair 1 (c along y, lane along x)
         const int x = pair == 0 ? x0 + c : x0 + lane, y = pair == 0 ? y0 + lane : y0 + c;
         if (x >= W || y >= H) continue;
         const long long pix = (long long)y * W + x;
         if (pair == 0) {
 #pragma unroll
-            for (int cc = 0; cc < C; ++cc) acc[(cc * PT_V + lane) * (PT_U + 1) + c] = dE[cc];
-            acc[(C * PT_V + lane) * (PT_U + 1) + c] = dS;
+            for (int k = 0; k < C; ++k) acc[(k * PT_V + lane) * (PT_U + 1) + c] = dE[i][k];
+            acc[(C * PT_V + lane) * (PT_U + 1) + c] = dS[i];
         } else {
 #pragma unroll
-            for (int cc = 0; cc < C; ++cc) ge[cc * HW + pix] = IN(A(ge[cc * HW + pix]) + dE[cc]);
-            gs[pix] = IN(A(gs[pix]) + dS);
+            for (int k = 0; k < C; ++k) ge[k * HW + pix] = IN(A(ge[k * HW + pix]) + dE[i][k]);
+            gs[pix] = IN(A(gs[pix]) + dS[i]);
         }
     }
     if (pair == 0) {
@@ -477,7 +643,7 @@ __device__ __forceinline__ void body_adj_trace(const Plan &pl, const IN *__restr
             if (x >= W || y >= H) continue;
             const long long pix = (long long)y * W + x;
 #pragma unroll
-            for (int cc = 0; cc < C; ++cc) ge[cc * HW + pix] = IN(acc[(cc * PT_V + ly) * (PT_U + 1) + lx]);
+            for (int c = 0; c < C; ++c) ge[c * HW + pix] = IN(acc[(c * PT_V + ly) * (PT_U + 1) + lx]);
             gs[pix] = IN(acc[(C * PT_V + ly) * (PT_U + 1) + lx]);
         }
     }

@@ -25,7 +25,6 @@
 #include <type_traits>
 
 #include "hrc_internal.cuh"
-#include "pair_tile.cuh"
 #include "trace_shapes.cuh"
 
 namespace hrc {

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(512) k_adj_merge_up(Plan pl, RowSplitB rs, int
 }
 
 template <int P, int C, class IN>
-__global__ void __launch_bounds__(256) k_adj_trace(Plan pl, const IN *__restrict__ e, const IN *__restrict__ s,
+__global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_trace(Plan pl, const IN *__restrict__ e, const IN *__restrict__ s,
                                                    IN *__restrict__ ge, IN *__restrict__ gs, int pair) {
     extern __shared__ __align__(16) unsigned char tb_smem[];
     body_adj_trace<P, C, IN>(pl, e, s, ge, gs, pair, blockIdx.x, blockIdx.y, tb_smem);
@@ -164,7 +164,7 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                 for (int n = 0; n <= 2; ++n) by += gTbytes(q, n);
             dim3 grid(pair_tiles_x(pair, pl.W), pair_tiles_y(pair, pl.H));
             rec->begin(K_ADJ_TRACE, pair, by);
-            k_adj_trace<P, C, IN><<<grid, 256, smem, st>>>(pl, (const IN *)e, (const IN *)s, (IN *)ge, (IN *)gs, pair);
+            k_adj_trace<P, C, IN><<<grid, ADJ_THREADS, smem, st>>>(pl, (const IN *)e, (const IN *)s, (IN *)ge, (IN *)gs, pair);
             rec->end();
             ++*launches;
         }

@@ -1,8 +1,8 @@
-// pair_tile.cuh -- the staged image tile of the two trace kernels.
+// pair_tile.cuh -- the staged image tile of the adjoint trace.
 //
-// The directly traced levels (Sec. 4.2) are computed, and their adjoint
-// gathered, one quadrant pair at a time: pair 0 = frames q0, q1 (u along
-// image x), pair 1 = frames q2, q3 (u along image y).  A block covers a tile
+// The adjoint of the directly traced levels (Sec. 4.2) is gathered one
+// quadrant pair at a time: pair 0 = frames q0, q1 (u along image x), pair 1 =
+// frames q2, q3 (u along image y).  A block covers a tile
 // of PT_U pixels along u by PT_V pixels along v; the region staged in shared
 // memory adds a PT_HALO-pixel halo on every side (the longest directly
 // traced ray, v_2(k), reaches 4 pixels along and across).  The region is
@@ -11,9 +11,9 @@
 //
 // Per region pixel it holds, for the three ray classes c of trace_shapes.cuh
 // (half length l_c), the half-piece factors {t, w} = {exp(-sigma l_c),
-// l_c phi(sigma l_c)} (Eq. 4 over a uniform piece), and the emission with the
-// extinction.  Outside the image every field is vacuum (sigma = e = 0,
-// t = 1, w = l_c), which is exact.
+// l_c phi(sigma l_c)} (Eq. 4 over a uniform piece) and dw/dsigma, and the
+// emission with the extinction.  Outside the image every field is vacuum
+// (sigma = e = 0, t = 1, w = l_c, dw/dsigma = -l_c^2 / 2), which is exact.
 #pragma once
 
 #include <type_traits>
@@ -37,26 +37,45 @@ template <class A, int C> struct PackES {
     static constexpr bool packed = std::is_same<A, float>::value && C <= 3;
 };
 
+// dw/dsigma of a half piece of length l with t = exp(-sigma l):
+// l^2 phi'(sigma l), phi'(x) = (e^-x (1 + x) - 1) / x^2, by its Taylor
+// series near 0.
+__device__ __forceinline__ float dw_dsigma(float sg, float len, float t) {
+    const float tau = sg * len;
+    const float series = len * len * (-0.5f + tau * (1.f / 3.f + tau * (-1.f / 8.f + tau * (1.f / 30.f))));
+    return fabsf(tau) < 0.05f ? series : (t * (1.f + tau) - 1.f) / (sg * sg);
+}
+__device__ __forceinline__ double dw_dsigma(double sg, double len, double t) {
+    const double tau = sg * len;
+    if (fabs(tau) < 1e-2)
+        return len * len * (-0.5 + tau * (1.0 / 3.0 + tau * (-1.0 / 8.0 + tau * (1.0 / 30.0 + tau * (-1.0 / 144.0 + tau * (1.0 / 840.0))))));
+    return (t * (1.0 + tau) - 1.0) / (sg * sg);
+}
+
 template <class A, int C> struct PairTile {
     using V2 = typename Vec2<A>::T;
     V2 *tw;        // [3][PLANE]
+    A *dw;         // [3][PLANE]
     float4 *es4;   // [PLANE] when packed
     A *e;          // [C][PLANE] otherwise
     A *s;          // [PLANE] otherwise
     __device__ __forceinline__ explicit PairTile(unsigned char *smem) {
         tw = reinterpret_cast<V2 *>(smem);
-        es4 = reinterpret_cast<float4 *>(tw + 3 * PT_PLANE);
-        e = reinterpret_cast<A *>(tw + 3 * PT_PLANE);
+        dw = reinterpret_cast<A *>(tw + 3 * PT_PLANE);
+        es4 = reinterpret_cast<float4 *>(dw + 3 * PT_PLANE);
+        e = dw + 3 * PT_PLANE;
         s = e + C * PT_PLANE;
     }
+    static_assert((sizeof(A) * 3 * PT_PLANE) % 16 == 0, "16-byte aligned planes");
     static constexpr size_t bytes() {
-        return sizeof(V2) * 3 * PT_PLANE + (PackES<A, C>::packed ? sizeof(float4) * PT_PLANE
-                                                                : sizeof(A) * (C + 1) * PT_PLANE);
+        return (sizeof(V2) + sizeof(A)) * 3 * PT_PLANE +
+               (PackES<A, C>::packed ? sizeof(float4) * PT_PLANE : sizeof(A) * (C + 1) * PT_PLANE);
     }
-    __device__ __forceinline__ void piece(int cls, int o, A &t, A &w) const {
+    __device__ __forceinline__ void piece(int cls, int o, A &t, A &w, A &d) const {
         const V2 p = tw[cls * PT_PLANE + o];
         t = p.x;
         w = p.y;
+        d = dw[cls * PT_PLANE + o];
     }
     __device__ __forceinline__ void emis(int o, A (&em)[C], A &sg) const {
         if constexpr (PackES<A, C>::packed) {
@@ -99,6 +118,7 @@ template <class A, int C> struct PairTile {
                 p.x = A(1) + m;
                 p.y = sg != A(0) ? -m / sg : len;
                 tw[c * PT_PLANE + o] = p;
+                dw[c * PT_PLANE + o] = dw_dsigma(sg, len, p.x);
             }
             if constexpr (PackES<A, C>::packed) {
                 float4 v = make_float4(0.f, 0.f, 0.f, (float)sg);
