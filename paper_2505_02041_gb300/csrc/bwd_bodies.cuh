@@ -12,8 +12,9 @@
 //   body_adj_T        : the merge-down part of dL/dT_n: odd columns from the
 //                       level-n cones (Eq. 14), even directions from the level
 //                       n-1 cones at even columns (Eqs. 15-17 with Sec. 4.1)
-//   body_adj_merge_up : dL/dT_{n-1} += reverse of Eq. 18 / Eqs. 19-20 (<= 3
-//                       terms per entry: near operand or far operand)
+//   body_adj_merge_up : dL/dT_{n-1} = its merge-down part (as body_adj_T,
+//                       fused) + reverse of Eq. 18 / Eqs. 19-20 (<= 3 terms
+//                       per entry: near operand or far operand)
 //   body_adj_trace    : dL/de, dL/dsigma from dL/dT_0..T_2 (reverse of Trace,
 //                       Eq. 9): each pixel gathers every directly traced ray
 //                       crossing it, re-tracing the ray from shared memory.
@@ -160,19 +161,12 @@ __device__ __forceinline__ void body_adj_R(const Plan &pl, const RowSplitB &rs, 
 //     with weight 1/2; far fluence R_n(x+1, j, v+d), d = 2k - 2^n.
 // ---------------------------------------------------------------------------
 template <int P, int C, int E>
-__device__ __forceinline__ void body_adj_T(const Plan &pl, const RowSplitB &rs, int n, long long bx, int by) {
+__device__ __forceinline__ void adj_T_part(const Plan &pl, int q, int n, int x, int k, int v,
+                                           typename Prec<P>::A (&gL)[E][C], typename Prec<P>::A (&gT)[E]) {
     using A = typename Prec<P>::A;
-    int local;
-    const int q = quadrant_of(rs, bx, local);   // row = (q, x, k) at level n, x >= 1
     const QuadGeom &g = pl.q[q];
-    const int v = E * (by * blockDim.x + threadIdx.x);
-    if (v >= g.V) return;
-    const int K = (1 << n) + 1;
-    local += K;
-    const int x = local / K, k = local - x * K;
     const int s = 1 << n;
     const int d = 2 * k - s;
-    A gL[E][C], gT[E];
 #pragma unroll
     for (int l = 0; l < E; ++l) {
         gT[l] = A(0);
@@ -212,6 +206,25 @@ __device__ __forceinline__ void body_adj_T(const Plan &pl, const RowSplitB &rs, 
         if (k >= 2) cone(gRm, 2 * x, (k >> 1) - 1, A(0.5) * arc<P>(pl, n, k - 1), A(0.5), rq, Rn, x + 1, k - 1);
         if (k < s) cone(gRm, 2 * x, k >> 1, A(0.5) * arc<P>(pl, n, k), A(0.5), rq, Rn, x + 1, k);
     }
+}
+
+// Levels whose merge-down part is computed inside the merge-up reverse of
+// the level above (n = 2 .. N-1); adj_T covers the others.
+__host__ __device__ inline bool adj_T_fused(int n, int N) { return n >= 2 && n <= N - 1; }
+
+template <int P, int C, int E>
+__device__ __forceinline__ void body_adj_T(const Plan &pl, const RowSplitB &rs, int n, long long bx, int by) {
+    using A = typename Prec<P>::A;
+    int local;
+    const int q = quadrant_of(rs, bx, local);   // row = (q, x, k) at level n, x >= 1
+    const QuadGeom &g = pl.q[q];
+    const int v = E * (by * blockDim.x + threadIdx.x);
+    if (v >= g.V) return;
+    const int K = (1 << n) + 1;
+    local += K;
+    const int x = local / K, k = local - x * K;
+    A gL[E][C], gT[E];
+    adj_T_part<P, C, E>(pl, q, n, x, k, v, gL, gT);
     GTLevel<P, C> gTn(pl, q, n);
 #pragma unroll
     for (int l = 0; l < E; ++l)
@@ -219,7 +232,8 @@ __device__ __forceinline__ void body_adj_T(const Plan &pl, const RowSplitB &rs, 
 }
 
 // ---------------------------------------------------------------------------
-// dL/dT_{n-1}(x', kap, w) += reverse of the level-n merge up.  h = 2^{n-1}.
+// dL/dT_{n-1}(x', kap, w) = its merge-down part (adj_T_part, fused here) +
+// the reverse of the level-n merge up.  h = 2^{n-1}.
 //  even x' (near operand of column x = x'/2, far column x'+1, far offset
 //  w + 2 kap - h, shared by the three outputs):
 //    k = 2 kap (weight 1, far dir kap), k = 2 kap + 1 (F_-, weight 1/2, far
@@ -246,8 +260,7 @@ __device__ __forceinline__ void body_adj_merge_up(const Plan &pl, const RowSplit
     TLevel<P, C> Tm(pl, q, m);
     GTLevel<P, C> gTm(pl, q, m), gTn(pl, q, n);
     A aL[E][C], aT[E];
-#pragma unroll
-    for (int l = 0; l < E; ++l) gTm.load(x1, kap, w + l, aL[l], aT[l]);
+    adj_T_part<P, C, E>(pl, q, m, x1, kap, w, aL, aT);   // the merge-down part of dL/dT_{n-1}
     if (!(x1 & 1)) {
         const int x = x1 >> 1, xf = x1 + 1;
         const int vf = w + 2 * kap - h;

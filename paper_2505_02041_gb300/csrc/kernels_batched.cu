@@ -170,7 +170,7 @@ RowSplit rows_for(const Plan &pl, int kind, int n) {
         case BK_ADJ_R2:
         case BK_ADJ_R1: rows = (n + 1 < g.N) ? (long long)(g.Un[n + 1] - 1) * (2 << n) : 0; break;
         case BK_ADJ_T2:
-        case BK_ADJ_T1: rows = (g.N >= 1 && n <= g.N) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0; break;
+        case BK_ADJ_T1: rows = (g.N >= 1 && n <= g.N && !adj_T_fused(n, g.N)) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0; break;
         case BK_ADJ_MU: rows = (n >= 3 && n <= g.N) ? (long long)(g.Un[n - 1] - 1) * ((1 << (n - 1)) + 1) : 0; break;
         default: break;
         }
@@ -277,14 +277,16 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
     for (int n = 0; n <= Nmax; ++n) {
         by = 0;
         for (int q = 0; q < 4; ++q)
-            if (pl.q[q].N >= 1 && n <= pl.q[q].N)
+            if (pl.q[q].N >= 1 && n <= pl.q[q].N && !adj_T_fused(n, pl.q[q].N))
                 by += gT(q, n) + gR(q, n) + gR(q, n - 1) + bytes_R(pl, q, n) + bytes_R(pl, q, n + 1);
         rowstage(n >= 1 ? BK_ADJ_T2 : BK_ADJ_T1, n, n >= 1 ? vb2 : vb1, by);
     }
     for (int n = Nmax; n >= 3; --n) {
         by = 0;
         for (int q = 0; q < 4; ++q)
-            if (n <= pl.q[q].N) by += 2 * gT(q, n - 1) + gT(q, n) + bytes_T(pl, q, n - 1);
+            if (n <= pl.q[q].N)
+                by += gT(q, n - 1) + gT(q, n) + bytes_T(pl, q, n - 1) + gR(q, n - 1) + gR(q, n - 2) +
+                      bytes_R(pl, q, n - 1) + bytes_R(pl, q, n);
         rowstage(BK_ADJ_MU, n, vb2, by);
     }
     for (int pair = 0; pair < 2; ++pair) {

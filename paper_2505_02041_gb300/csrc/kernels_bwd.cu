@@ -66,7 +66,7 @@ RowSplitB split_rows(const Plan &pl, int kind, int n) {
         long long rows = 0;
         if (kind == 0) rows = g.N >= 1 ? g.Un[0] : 0;
         else if (kind == 1) rows = (n + 1 < g.N) ? (long long)(g.Un[n + 1] - 1) * (2 << n) : 0;
-        else if (kind == 2) rows = (g.N >= 1 && n <= g.N) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0;
+        else if (kind == 2) rows = (g.N >= 1 && n <= g.N && !adj_T_fused(n, g.N)) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0;
         else rows = (n >= 3 && n <= g.N) ? (long long)(g.Un[n - 1] - 1) * ((1 << (n - 1)) + 1) : 0;
         acc += rows;
     }
@@ -136,7 +136,7 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         if (rs.start[4] == 0) continue;
         double by = 0;
         for (int q = 0; q < 4; ++q)
-            if (pl.q[q].N >= 1 && n <= pl.q[q].N)
+            if (pl.q[q].N >= 1 && n <= pl.q[q].N && !adj_T_fused(n, pl.q[q].N))
                 by += gTbytes(q, n) + gRbytes(q, n) + gRbytes(q, n - 1) + bytes_R(pl, q, n) + bytes_R(pl, q, n + 1);
         rec->begin(K_ADJ_MERGE_DOWN, n, by);
         if (n >= 1) k_adj_T<P, C, 2><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
@@ -149,7 +149,9 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         if (rs.start[4] == 0) continue;
         double by = 0;
         for (int q = 0; q < 4; ++q)
-            if (n <= pl.q[q].N) by += 2 * gTbytes(q, n - 1) + gTbytes(q, n) + bytes_T(pl, q, n - 1);
+            if (n <= pl.q[q].N)   // merge-up reverse + the fused merge-down part of level n-1
+                by += gTbytes(q, n - 1) + gTbytes(q, n) + bytes_T(pl, q, n - 1) + gRbytes(q, n - 1) +
+                      gRbytes(q, n - 2) + bytes_R(pl, q, n - 1) + bytes_R(pl, q, n);
         rec->begin(K_ADJ_MERGE_UP, n, by);
         k_adj_merge_up<P, C><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
         rec->end();
