@@ -196,7 +196,9 @@ hrc_status hrc_batched_debug(hrc_ctx *ctx, int withhold_counter, long long spin_
  * the log-T precisions); which = 1: R_n as [U_n][2^n][V][C].  Column x = 0
  * of every level is NaN: no fluence depends on it (the sum of Algorithm 1
  * reads R_0 at u + 1, and column 0 feeds only column 0 of the levels next to
- * it), so the library never computes it.  *count receives the element count;
+ * it), so the library never computes it.  The forward does not store R_0
+ * either (the fluence sum computes it in place); this call recomputes it from
+ * T_0, T_1 and R_1 of the last forward.  *count receives the element count;
  * dst may be NULL to query it.  HRC_EINVAL if the level does not exist. */
 hrc_status hrc_copy_level(hrc_ctx *ctx, int q, int which, int n, float *dst, long long *count);
 

@@ -62,8 +62,8 @@ __device__ __forceinline__ void body_adj_sum(const Plan &pl, const GIN *__restri
     const int W = pl.W, H = pl.H;
     const int x0 = bx * 32, y0 = by * 32;
     const long long HW = (long long)W * H;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = warp; r < 32; r += 8) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < 32; r += nw) {
         const int x = x0 + lane, y = y0 + r;
 #pragma unroll
         for (int c = 0; c < C; ++c) tile[c][r][lane] = (x < W && y < H) ? A(gF[c * HW + (long long)y * W + x]) : A(0);
@@ -77,7 +77,7 @@ __device__ __forceinline__ void body_adj_sum(const Plan &pl, const GIN *__restri
         const int tu = xu ? x0 : y0, tv = xu ? y0 : x0, ext_u = xu ? W : H;
         const int v = tv + lane;
         if (v >= g.V) continue;
-        for (int cidx = warp; cidx < 32; cidx += 8) {
+        for (int cidx = warp; cidx < 32; cidx += nw) {
             if (tu + cidx >= ext_u) continue;
             const int u = (q == 0 || q == 2) ? tu + cidx : ext_u - 1 - (tu + cidx);
             const int iy = xu ? lane : cidx, ix = xu ? cidx : lane;

@@ -3,7 +3,8 @@
 //   body_trace012    : T_0..T_min(2,N) by direct tracing (Sec. 4.2, Eq. 9)
 //   body_merge_up    : T_n from T_{n-1} (Eq. 18 even k, Eqs. 19-20 odd k)
 //   body_merge_down  : R_n from R_{n+1}, T_n, T_{n+1} (Eq. 14 odd x, Eqs. 15-17 even x)
-//   body_fluence_sum : F = sum over quadrants of R_0([u+1, v], 1/2) (Algorithm 1, Lighting)
+//   body_fluence     : F = sum over quadrants of R_0([u+1, v], 1/2) (Algorithm 1,
+//                      Lighting), with the level-0 merge down computed in place
 //
 // Each body processes one block of work given by an explicit block index
 // (bx, by), so the same code runs as a standalone kernel (one launch per
@@ -238,29 +239,22 @@ __device__ __forceinline__ void body_merge_up(const Plan &pl, const RowSplit &rs
     }
 }
 
-// R_n(p, i) = F_+ + F_-, p = (x 2^n, v), i = ip + 1/2, j_+ = 2ip+1, j_- = 2ip.
-// PAIR: two consecutive v per thread (all neighbour offsets even: n >= 1).
-template <int P, int C, bool PAIR>
-__device__ __forceinline__ void body_merge_down(const Plan &pl, const RowSplit &rs, int n, long long bx, int by) {
+// R_n(p, i) = F_+ + F_-, p = (x 2^n, v), i = ip + 1/2, j_+ = 2ip+1, j_- = 2ip,
+// for v .. v+E-1 of column x >= 1 of frame q (E = 2: all neighbour offsets
+// even, n >= 1).
+template <int P, int C, int E>
+__device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, int x, int ip, int v,
+                                                 typename Prec<P>::A (&acc)[E][C]) {
     using A = typename Prec<P>::A;
-    constexpr int E = PAIR ? 2 : 1;
-    int local;
-    const int q = find_quadrant(rs, bx, local);   // row = (q, x, ip), x >= 1 (column 0 is dead)
+    constexpr bool PAIR = E == 2;
     const QuadGeom &g = pl.q[q];
-    const int v = E * (by * blockDim.x + threadIdx.x);
-    if (v >= g.V) return;
-    const int I = 1 << n;
-    local += I;
-    const int x = local >> n, ip = local & (I - 1);
     const bool top = (n + 1 >= g.N);               // R_N = 0
     const int s = 1 << n;
-    A acc[E][C];
 #pragma unroll
     for (int l = 0; l < E; ++l)
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[l][c] = A(0);
     const A Ap = arc<P>(pl, n + 1, 2 * ip + 1), Am = arc<P>(pl, n + 1, 2 * ip);
-    RLevel<P, C> Rn(pl, q, n);
     // R_{n+1}(xr, j, vq .. vq+E-1), zero outside [0, V)
     auto loadR = [&](const RLevel<P, C> &R1, int xr, int j, int c, int vq, A (&r)[E]) {
         if (PAIR) {
@@ -335,6 +329,24 @@ __device__ __forceinline__ void body_merge_down(const Plan &pl, const RowSplit &
             }
         }
     }
+}
+
+// One row segment of R_n: row = (q, x, ip), x >= 1 (column 0 is dead).
+template <int P, int C, bool PAIR>
+__device__ __forceinline__ void body_merge_down(const Plan &pl, const RowSplit &rs, int n, long long bx, int by) {
+    using A = typename Prec<P>::A;
+    constexpr int E = PAIR ? 2 : 1;
+    int local;
+    const int q = find_quadrant(rs, bx, local);
+    const QuadGeom &g = pl.q[q];
+    const int v = E * (by * blockDim.x + threadIdx.x);
+    if (v >= g.V) return;
+    const int I = 1 << n;
+    local += I;
+    const int x = local >> n, ip = local & (I - 1);
+    A acc[E][C];
+    merge_down_entry<P, C, E>(pl, q, n, x, ip, v, acc);
+    RLevel<P, C> Rn(pl, q, n);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         if (PAIR) Rn.store2(x, ip, c, v, acc[0][c], acc[E - 1][c]);
@@ -342,30 +354,59 @@ __device__ __forceinline__ void body_merge_down(const Plan &pl, const RowSplit &
     }
 }
 
-// F[c][y][x] = sum_q R_0^q(u_q + 1, v_q)   (Algorithm 1, Lighting, +1 offset).
+// F[c][y][x] = sum_q R_0^q(u_q + 1, v_q)   (Algorithm 1, Lighting, +1 offset),
+// with R_0 computed in place (merge_down_entry at n = 0): R_0 feeds only this
+// sum, so it is never stored.  One block per 32 x 32 image tile (any
+// multiple of 32 threads).  Frames q0, q1 run v along image y and q2, q3 along image x, so the
+// first pair is computed with lanes along y, parked in shared memory, and the
+// second pair with lanes along x adds to it and writes F coalesced; the sum
+// runs in frame order q0 + q1 + q2 + q3.
+template <int P, int C>
+constexpr size_t fluence_smem() { return sizeof(typename Prec<P>::A) * C * 32 * 33; }
+
 template <int P, int C, class OUT>
-__device__ __forceinline__ void body_fluence_sum(const Plan &pl, OUT *__restrict__ F, int bx, int by) {
+__device__ __forceinline__ void body_fluence(const Plan &pl, OUT *__restrict__ F, int bx, int by, unsigned char *smem) {
     using A = typename Prec<P>::A;
-    const int x = bx * blockDim.x + threadIdx.x;
-    const int y = by;
-    if (x >= pl.W) return;
-    A acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = A(0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    A (*tile)[32][33] = reinterpret_cast<A (*)[32][33]>(smem);   // [C][y][x] of the tile
+    const int W = pl.W, H = pl.H;
+    const int x0 = bx * 32, y0 = by * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // R_0^q(u + 1, v) of the pixel (x, y), added to a[]
+    auto add_r0 = [&](int q, int x, int y, A (&a)[C]) {
         const QuadGeom &g = pl.q[q];
         int u, v;
-        image_to_frame(q, pl.W, pl.H, x, y, u, v);
-        if (g.N >= 1 && u + 1 < g.U) {
-            RLevel<P, C> R0(pl, q, 0);
+        image_to_frame(q, W, H, x, y, u, v);
+        if (g.N < 1 || u + 1 >= g.U) return;
+        A r[1][C];
+        merge_down_entry<P, C, 1>(pl, q, 0, u + 1, 0, v, r);
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] += R0.load(u + 1, 0, c, v);
+        for (int c = 0; c < C; ++c) a[c] += r[0][c];
+    };
+    for (int cidx = warp; cidx < 32; cidx += nw) {         // q0, q1: lanes along y
+        const int x = x0 + cidx, y = y0 + lane;
+        A a[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) a[c] = A(0);
+        if (x < W && y < H) {
+            add_r0(0, x, y, a);
+            add_r0(1, x, y, a);
         }
-    }
-    const long long HW = (long long)pl.W * pl.H;
 #pragma unroll
-    for (int c = 0; c < C; ++c) F[c * HW + (long long)y * pl.W + x] = (OUT)acc[c];
+        for (int c = 0; c < C; ++c) tile[c][lane][cidx] = a[c];
+    }
+    __syncthreads();
+    const long long HW = (long long)W * H;
+    for (int cidx = warp; cidx < 32; cidx += nw) {         // q2, q3: lanes along x
+        const int x = x0 + lane, y = y0 + cidx;
+        if (x >= W || y >= H) continue;
+        A a[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) a[c] = tile[c][cidx][lane];
+        add_r0(2, x, y, a);
+        add_r0(3, x, y, a);
+#pragma unroll
+        for (int c = 0; c < C; ++c) F[c * HW + (long long)y * W + x] = (OUT)a[c];
+    }
 }
 
 }  // namespace hrc

@@ -932,7 +932,9 @@ hrc_status hrc_copy_level(hrc_ctx *ctx, int q, int which, int n, float *dst, lon
                                      : (long long)g.Un[n] * (1 << n) * g.V * ctx->C;
     if (count) *count = cnt;
     if (!dst) return HRC_OK;
-    cudaError_t e = launch_copy_level(pl, q, which, n, dst, ctx->stream);
+    cudaError_t e = cudaSuccess;
+    if (which == 1 && n == 0) e = launch_r0(pl, ctx->stream);   // the forward does not store R_0
+    if (e == cudaSuccess) e = launch_copy_level(pl, q, which, n, dst, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_copy_level");
     return HRC_OK;
 }

@@ -131,11 +131,8 @@ __global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
             case BK_MERGE_DOWN2:
                 for (long long r = r0; r < r1; ++r) body_merge_down<P, C, true>(pl, sb.rs, sb.level, r, vb);
                 break;
-            case BK_MERGE_DOWN1:
-                for (long long r = r0; r < r1; ++r) body_merge_down<P, C, false>(pl, sb.rs, sb.level, r, vb);
-                break;
-            default:   // BK_SUM
-                for (long long r = r0; r < r1; ++r) body_fluence_sum<P, C, IN>(pl, (IN *)a.F + eo, vb, (int)r);
+            default:   // BK_SUM (with the level-0 merge down)
+                body_fluence<P, C, IN>(pl, (IN *)a.F + eo, vb, (int)(j / sb.nvb), smem);
                 break;
             }
         } else {
@@ -165,8 +162,7 @@ RowSplit rows_for(const Plan &pl, int kind, int n) {
         long long rows = 0;
         switch (kind) {
         case BK_MERGE_UP: rows = (n >= 3 && n <= g.N) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0; break;
-        case BK_MERGE_DOWN2:
-        case BK_MERGE_DOWN1: rows = n < g.N ? (long long)(g.Un[n] - 1) * (1 << n) : 0; break;
+        case BK_MERGE_DOWN2: rows = n < g.N ? (long long)(g.Un[n] - 1) * (1 << n) : 0; break;
         case BK_ADJ_R2:
         case BK_ADJ_R1: rows = (n + 1 < g.N) ? (long long)(g.Un[n + 1] - 1) * (2 << n) : 0; break;
         case BK_ADJ_T2:
@@ -201,7 +197,7 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
         d.rs = rows_for(pl, kind, n);
         d.nvb = nvb;
         d.rows = d.rs.start[4];
-        const int per_row = (kind == BK_MERGE_DOWN1 || kind == BK_ADJ_R1 || kind == BK_ADJ_T1) ? 256 : 512;
+        const int per_row = (kind == BK_ADJ_R1 || kind == BK_ADJ_T1) ? 256 : 512;
         d.rpi = 4096 / per_row;
         d.count = (int)((d.rows + d.rpi - 1) / d.rpi * nvb);
         d.bytes = bytes;
@@ -231,7 +227,7 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
                 if (n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
             rowstage(BK_MERGE_UP, n, vb2, by);
         }
-        for (int n = Nmax - 1; n >= 0; --n) {
+        for (int n = Nmax - 1; n >= 1; --n) {   // level 0 inside the fluence stage
             by = 0;
             for (int q = 0; q < 4; ++q) {
                 const QuadGeom &g = pl.q[q];
@@ -240,20 +236,14 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
                 by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
                 by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
             }
-            rowstage(n >= 1 ? BK_MERGE_DOWN2 : BK_MERGE_DOWN1, n, n >= 1 ? vb2 : vb1, by);
+            rowstage(BK_MERGE_DOWN2, n, vb2, by);
         }
         by = img * pl.C * esz;
-        for (int q = 0; q < 4; ++q) by += bytes_R(pl, q, 0);
-        StageDesc d;   // fluence sum: rows = image rows, 16 per item
-        d.kind = BK_SUM;
-        d.level = 0;
-        std::memset(&d.rs, 0, sizeof(d.rs));
-        d.nvb = (pl.W + 255) / 256;
-        d.rows = pl.H;
-        d.rpi = 16;
-        d.count = (int)((d.rows + d.rpi - 1) / d.rpi * d.nvb);
-        d.bytes = by;
-        out.push_back(d);
+        for (int q = 0; q < 4; ++q) {
+            if (pl.q[q].N < 1) continue;
+            by += bytes_T_odd(pl, q, 0) + bytes_T(pl, q, 1) * (2.0 / 3.0) + bytes_R(pl, q, 1);
+        }
+        tilestage(BK_SUM, tx, ty, by);   // 32 x 32 tiles, as the standalone kernel
         return;
     }
     const double ab = 4.0;   // adjoint buffers are fp32 in the batched precisions
@@ -301,7 +291,7 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
 // backward the adjoint-trace tile and the transposed dL/dF tile.
 template <int P, int C> size_t batched_smem(int mode) {
     using A = typename Prec<P>::A;
-    if (mode == 0) return TraceTile<A, C>::bytes();
+    if (mode == 0) return TraceTile<A, C>::bytes() > fluence_smem<P, C>() ? TraceTile<A, C>::bytes() : fluence_smem<P, C>();
     const size_t m = adj_trace_smem<A, C>(), sum_tile = sizeof(A) * C * 32 * 33;
     return m > sum_tile ? m : sum_tile;
 }

@@ -37,8 +37,9 @@ __global__ void __launch_bounds__(512) k_merge_down(Plan pl, RowSplit rs, int n)
 }
 
 template <int P, int C, class OUT>
-__global__ void __launch_bounds__(256) k_fluence_sum(Plan pl, OUT *__restrict__ F) {
-    body_fluence_sum<P, C, OUT>(pl, F, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(128) k_fluence(Plan pl, OUT *__restrict__ F) {
+    __shared__ __align__(16) unsigned char smem[fluence_smem<P, C>()];
+    body_fluence<P, C, OUT>(pl, F, blockIdx.x, blockIdx.y, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -144,7 +145,8 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             rec->end();
             ++*launches;
         }
-        for (int n = Nmax - 1; n >= 0; --n) {
+        // with the fluence sum, level 0 is computed inside it (R_0 feeds nothing else)
+        for (int n = Nmax - 1; n >= (with_sum ? 1 : 0); --n) {
             RowSplit rs = make_split(pl, n, 2, qsel);
             if (rs.start[4] == 0) continue;
             double by = 0;
@@ -168,16 +170,52 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         }
     }
     if (with_sum) {
+        // level-0 merge-down reads (odd columns of T_0, even directions of
+        // T_1, R_1) and the fluence written
         double by = img * pl.C * esz;
-        for (int q = 0; q < 4; ++q) by += bytes_R(pl, q, 0);
-        dim3 grid((pl.W + bs - 1) / bs, pl.H);
+        for (int q = 0; q < 4; ++q) {
+            if (pl.q[q].N < 1) continue;
+            by += bytes_T_odd(pl, q, 0) + bytes_T(pl, q, 1) * (2.0 / 3.0) + bytes_R(pl, q, 1);
+        }
+        dim3 grid((pl.W + 31) / 32, (pl.H + 31) / 32);
         rec->begin(K_FLUENCE_SUM, 0, by);
-        if (P == P_FP64) k_fluence_sum<P, C, double><<<grid, bs, 0, st>>>(pl, (double *)F);
-        else k_fluence_sum<P, C, float><<<grid, bs, 0, st>>>(pl, (float *)F);
+        // 128 threads: every tile of a 1024^2 image is resident at once
+        if (P == P_FP64) k_fluence<P, C, double><<<grid, 128, 0, st>>>(pl, (double *)F);
+        else k_fluence<P, C, float><<<grid, 128, 0, st>>>(pl, (float *)F);
         rec->end();
         ++*launches;
     }
     return cudaGetLastError();
+}
+
+// R_0 of every frame into its buffer (the forward with the fluence sum never
+// stores it); for introspection.
+template <int P, int C>
+static cudaError_t r0_impl(const Plan &pl, cudaStream_t st) {
+    RowSplit rs = make_split(pl, 0, 2, -1);
+    if (rs.start[4] == 0) return cudaSuccess;
+    const int ts = 2 * pl.mthreads > 512 ? 512 : 2 * pl.mthreads;
+    k_merge_down<P, C, false><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, 0);
+    return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t r0_prec(const Plan &pl, cudaStream_t st) {
+    switch (pl.C) {
+    case 1: return r0_impl<P, 1>(pl, st);
+    case 2: return r0_impl<P, 2>(pl, st);
+    case 3: return r0_impl<P, 3>(pl, st);
+    default: return r0_impl<P, 4>(pl, st);
+    }
+}
+
+cudaError_t launch_r0(const Plan &pl, cudaStream_t st) {
+    switch (pl.prec) {
+    case P_FP32: return r0_prec<P_FP32>(pl, st);
+    case P_FP16: return r0_prec<P_FP16>(pl, st);
+    case P_BF16: return r0_prec<P_BF16>(pl, st);
+    default: return r0_prec<P_FP64>(pl, st);
+    }
 }
 
 template <int P>

@@ -57,7 +57,7 @@ cudaError_t launch_forward(const Plan &pl, const RayTable &rt, const void *e, co
 // Batched persistent launch (kernels_batched.cu)
 // ---------------------------------------------------------------------------
 enum BatchKind {
-    BK_TRACE = 0, BK_MERGE_UP, BK_MERGE_DOWN2, BK_MERGE_DOWN1, BK_SUM, BK_ADJ_SUM, BK_ADJ_R2, BK_ADJ_R1,
+    BK_TRACE = 0, BK_MERGE_UP, BK_MERGE_DOWN2, BK_SUM, BK_ADJ_SUM, BK_ADJ_R2, BK_ADJ_R1,
     BK_ADJ_T2, BK_ADJ_T1, BK_ADJ_MU, BK_ADJ_TRACE
 };
 
@@ -129,6 +129,9 @@ cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *ds
 // Algorithmic bytes of one launch (each array read once per consuming
 // phase, each written once): T entries of C radiances + 1 transmittance,
 // R entries of C values.
+// R_0 of every frame into the plan's buffer (the forward does not store it).
+cudaError_t launch_r0(const Plan &pl, cudaStream_t st);
+
 double bytes_T(const Plan &pl, int q, int n);
 double bytes_T_odd(const Plan &pl, int q, int n);
 double bytes_R(const Plan &pl, int q, int n);
