@@ -193,10 +193,12 @@ hrc_status hrc_batched_debug(hrc_ctx *ctx, int withhold_counter, long long spin_
 /* Introspection for tests: copies level n of quadrant frame q (0..3) from
  * the last forward into `dst` (device fp32).  which = 0: T_n as
  * [U_n][2^n+1][V][C+1] (C radiances then the transmittance T, linear even in
- * the log-T precisions); which = 1: R_n as [U_n][2^n][V][C].  Column x = 0
- * of every level is NaN: no fluence depends on it (the sum of Algorithm 1
- * reads R_0 at u + 1, and column 0 feeds only column 0 of the levels next to
- * it), so the library never computes it.  The forward does not store R_0
+ * the log-T precisions); which = 1: R_n as [U_n][2^n][V][C].  Entries no
+ * fluence depends on are NaN, as the library never computes them: column
+ * x = 0 of every level (the sum of Algorithm 1 reads R_0 at u + 1, and
+ * column 0 feeds only column 0 of the levels next to it), the even columns
+ * of T_0 (level 0 reads T_0 only at odd columns, Eq. 14) and the odd
+ * directions of T_1 at even columns (Eqs. 15-17 read even directions).  The forward does not store R_0
  * either (the fluence sum computes it in place); this call recomputes it from
  * T_0, T_1 and R_1 of the last forward.  *count receives the element count;
  * dst may be NULL to query it.  HRC_EINVAL if the level does not exist. */

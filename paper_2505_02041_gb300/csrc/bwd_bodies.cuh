@@ -216,13 +216,20 @@ template <int P, int C, int E>
 __device__ __forceinline__ void body_adj_T(const Plan &pl, const RowSplitB &rs, int n, long long bx, int by) {
     using A = typename Prec<P>::A;
     int local;
-    const int q = quadrant_of(rs, bx, local);   // row = (q, x, k) at level n, x >= 1
+    const int q = quadrant_of(rs, bx, local);   // row = (q, x, k) at level n, live x only
     const QuadGeom &g = pl.q[q];
     const int v = E * (by * blockDim.x + threadIdx.x);
     if (v >= g.V) return;
-    const int K = (1 << n) + 1;
-    local += K;
-    const int x = local / K, k = local - x * K;
+    int x, k;
+    if (n == 0) {                                 // odd columns only (t_live)
+        x = 2 * (local >> 1) + 1;
+        k = local & 1;
+    } else {
+        const int K = (1 << n) + 1;
+        local += K;
+        x = local / K;
+        k = local - x * K;
+    }
     A gL[E][C], gT[E];
     adj_T_part<P, C, E>(pl, q, n, x, k, v, gL, gT);
     GTLevel<P, C> gTn(pl, q, n);
@@ -480,7 +487,7 @@ __device__ __forceinline__ bool adj_probe(const AdjFrame &f, int ua, int i, int 
     const int col = i / B::NVB, vb = i - col * B::NVB;
     up = ua + col * B::S;
     vp = f.v0 - B::dvhi + vb;
-    return i < B::NPROBE && up >= 1 && up < f.U && vp >= 0 && vp < f.V;   // probes at u = 0 are dead
+    return i < B::NPROBE && up >= 1 && up < f.U && vp >= 0 && vp < f.V && t_live(B::n, up >> B::n, B::k);
 }
 
 template <int P, int C, int R>

@@ -20,7 +20,8 @@
 // Column x = 0 of every level is dead: the fluence sum reads R_0 at u + 1,
 // R_n(0) feeds only R_{n-1}(0), and T_n(0) only T_{n+1}(0) and R_n(0).  No
 // body computes or reads it (T_N, a single column when U <= 2^N, is then
-// skipped entirely).
+// skipped entirely).  The even columns of T_0 and the odd directions of T_1
+// at even columns are dead too (t_live) and are not traced.
 #pragma once
 
 #include <type_traits>
@@ -126,7 +127,7 @@ __device__ __forceinline__ void trace_store(const Plan &pl, const TraceTile<type
                                             int nmax, int u, int v, int base, int su, int sv) {
     using A = typename Prec<P>::A;
     using ray = RayAt<R>;
-    if (u == 0 || ray::n > nmax || (u & ((1 << ray::n) - 1))) return;   // probes at u = 0 are dead
+    if (ray::n > nmax || (u & ((1 << ray::n) - 1)) || !t_live(ray::n, u >> ray::n, ray::k)) return;
     Iv<P, C> iv;
 #pragma unroll
     for (int c = 0; c < C; ++c) iv.L[c] = A(0);

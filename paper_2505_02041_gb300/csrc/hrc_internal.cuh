@@ -72,6 +72,27 @@ struct RowSplit {
 
 __host__ __device__ inline int ray_id(int n, int k) { return n == 0 ? k : (n == 1 ? 2 + k : 5 + k); }
 
+// Entries T_n(x, k) that some fluence depends on.  Column 0 of every level
+// is dead (the fluence sum reads R_0 at u + 1).  T_0 is read only at odd
+// columns (Eq. 14 at level 0; the even columns of level 0 take T_1), and T_1
+// at even columns only in its even directions (Eqs. 15-17 at level 0), as
+// the merge up starts from T_2.  Dead entries are neither traced, merged,
+// nor differentiated.
+__host__ __device__ inline bool t_live(int n, int x, int k) {
+    if (x <= 0) return false;
+    if (n == 0) return (x & 1) != 0;
+    if (n == 1) return (x & 1) != 0 || (k & 1) == 0;
+    return true;
+}
+
+// Number of live (x, k) rows of T_n over the columns 0 .. Un-1.
+__host__ __device__ inline long long t_live_rows(int n, int Un) {
+    const long long odd = Un / 2, even = Un - 1 - odd;     // live columns 1 .. Un-1
+    if (n == 0) return odd * 2;
+    if (n == 1) return odd * 3 + even * 2;
+    return (long long)(Un - 1) * ((1 << n) + 1);
+}
+
 // frame (u, v) of quadrant q -> image pixel (x, y)
 __host__ __device__ inline void frame_to_image(int q, int W, int H, int u, int v, int &x, int &y) {
     x = q == 0 ? u : (q == 1 ? W - 1 - u : v);

@@ -166,7 +166,10 @@ RowSplit rows_for(const Plan &pl, int kind, int n) {
         case BK_ADJ_R2:
         case BK_ADJ_R1: rows = (n + 1 < g.N) ? (long long)(g.Un[n + 1] - 1) * (2 << n) : 0; break;
         case BK_ADJ_T2:
-        case BK_ADJ_T1: rows = (g.N >= 1 && n <= g.N && !adj_T_fused(n, g.N)) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0; break;
+        case BK_ADJ_T1:   // level 0: odd columns only
+            rows = (g.N >= 1 && n <= g.N && !adj_T_fused(n, g.N))
+                       ? (n == 0 ? (long long)(g.Un[0] / 2) * 2 : (long long)(g.Un[n] - 1) * ((1 << n) + 1)) : 0;
+            break;
         case BK_ADJ_MU: rows = (n >= 3 && n <= g.N) ? (long long)(g.Un[n - 1] - 1) * ((1 << (n - 1)) + 1) : 0; break;
         default: break;
         }
@@ -233,7 +236,7 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
                 const QuadGeom &g = pl.q[q];
                 if (n >= g.N) continue;
                 by += bytes_T_odd(pl, q, n);
-                by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
+                by += bytes_T_even_dirs(pl, q, n + 1);
                 by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
             }
             rowstage(BK_MERGE_DOWN2, n, vb2, by);
@@ -241,7 +244,7 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
         by = img * pl.C * esz;
         for (int q = 0; q < 4; ++q) {
             if (pl.q[q].N < 1) continue;
-            by += bytes_T_odd(pl, q, 0) + bytes_T(pl, q, 1) * (2.0 / 3.0) + bytes_R(pl, q, 1);
+            by += bytes_T_odd(pl, q, 0) + bytes_R(pl, q, 1) + bytes_T_even_dirs(pl, q, 1);
         }
         tilestage(BK_SUM, tx, ty, by);   // 32 x 32 tiles, as the standalone kernel
         return;
@@ -249,7 +252,7 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
     const double ab = 4.0;   // adjoint buffers are fp32 in the batched precisions
     auto gT = [&](int q, int n) {
         const QuadGeom &g = pl.q[q];
-        return (n < 0 || n > g.N) ? 0.0 : double(g.Un[n] - 1) * ((1 << n) + 1) * g.V * (pl.C + 1) * ab;
+        return (n < 0 || n > g.N) ? 0.0 : double(t_live_rows(n, g.Un[n])) * g.V * (pl.C + 1) * ab;
     };
     auto gR = [&](int q, int n) {
         const QuadGeom &g = pl.q[q];

@@ -66,7 +66,9 @@ RowSplitB split_rows(const Plan &pl, int kind, int n) {
         long long rows = 0;
         if (kind == 0) rows = g.N >= 1 ? g.Un[0] : 0;
         else if (kind == 1) rows = (n + 1 < g.N) ? (long long)(g.Un[n + 1] - 1) * (2 << n) : 0;
-        else if (kind == 2) rows = (g.N >= 1 && n <= g.N && !adj_T_fused(n, g.N)) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0;
+        else if (kind == 2)   // level 0: odd columns only
+            rows = (g.N >= 1 && n <= g.N && !adj_T_fused(n, g.N))
+                       ? (n == 0 ? (long long)(g.Un[0] / 2) * 2 : (long long)(g.Un[n] - 1) * ((1 << n) + 1)) : 0;
         else rows = (n >= 3 && n <= g.N) ? (long long)(g.Un[n - 1] - 1) * ((1 << (n - 1)) + 1) : 0;
         acc += rows;
     }
@@ -101,7 +103,7 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
     // live columns x >= 1 only (column 0 is dead)
     auto gTbytes = [&](int q, int n) {
         const QuadGeom &g = pl.q[q];
-        return (n < 0 || n > g.N) ? 0.0 : double(g.Un[n] - 1) * ((1 << n) + 1) * g.V * (pl.C + 1) * ab;
+        return (n < 0 || n > g.N) ? 0.0 : double(t_live_rows(n, g.Un[n])) * g.V * (pl.C + 1) * ab;
     };
     auto gRbytes = [&](int q, int n) {
         const QuadGeom &g = pl.q[q];

@@ -78,8 +78,8 @@ static int vblocks(const Plan &pl, int bs) {
     return (Vmax + bs - 1) / bs;
 }
 
-// Algorithmic bytes of T_n / R_n of frame q: the live columns x >= 1 only
-// (column 0 is dead and never touched).
+// Algorithmic bytes of T_n / R_n of frame q: the live entries only (column 0
+// of every level and the dead entries of T_0 / T_1 are never touched).
 static double t_entry_bytes(const Plan &pl) {
     return pl.C * (pl.prec == P_FP32 ? 4.0 : (pl.prec == P_FP64 ? 8.0 : 2.0)) + (pl.prec == P_FP64 ? 8.0 : 4.0);
 }
@@ -87,7 +87,7 @@ static double t_entry_bytes(const Plan &pl) {
 double bytes_T(const Plan &pl, int q, int n) {
     const QuadGeom &g = pl.q[q];
     if (n < 0 || n > g.N) return 0.0;
-    return double(g.Un[n] - 1) * ((1 << n) + 1) * g.V * t_entry_bytes(pl);
+    return double(t_live_rows(n, g.Un[n])) * g.V * t_entry_bytes(pl);
 }
 
 // The odd live columns of T_n (read by the level-n merge down, Eq. 14).
@@ -95,6 +95,14 @@ double bytes_T_odd(const Plan &pl, int q, int n) {
     const QuadGeom &g = pl.q[q];
     if (n < 0 || n > g.N) return 0.0;
     return double(g.Un[n] / 2) * ((1 << n) + 1) * g.V * t_entry_bytes(pl);
+}
+
+// The even directions of the live columns of T_n (read by the level n-1
+// merge down at even columns, Eqs. 15-17).
+double bytes_T_even_dirs(const Plan &pl, int q, int n) {
+    const QuadGeom &g = pl.q[q];
+    if (n < 1 || n > g.N) return 0.0;
+    return double(g.Un[n] - 1) * ((1 << (n - 1)) + 1) * g.V * t_entry_bytes(pl);
 }
 
 double bytes_R(const Plan &pl, int q, int n) {
@@ -155,7 +163,7 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                 if ((qsel >= 0 && q != qsel) || n >= g.N) continue;
                 // odd columns of T_n, even directions of T_{n+1}, R_{n+1} once, R_n written
                 by += bytes_T_odd(pl, q, n);
-                by += bytes_T(pl, q, n + 1) * (double((1 << n) + 1) / ((1 << (n + 1)) + 1));
+                by += bytes_T_even_dirs(pl, q, n + 1);
                 by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
             }
             const int mt = pl.mthreads;
@@ -175,7 +183,7 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         double by = img * pl.C * esz;
         for (int q = 0; q < 4; ++q) {
             if (pl.q[q].N < 1) continue;
-            by += bytes_T_odd(pl, q, 0) + bytes_T(pl, q, 1) * (2.0 / 3.0) + bytes_R(pl, q, 1);
+            by += bytes_T_odd(pl, q, 0) + bytes_R(pl, q, 1) + bytes_T_even_dirs(pl, q, 1);
         }
         dim3 grid((pl.W + 31) / 32, (pl.H + 31) / 32);
         rec->begin(K_FLUENCE_SUM, 0, by);

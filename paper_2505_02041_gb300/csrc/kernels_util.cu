@@ -4,8 +4,9 @@
 
 namespace hrc {
 
-// T_n of frame q -> dst[x][k][v][C+1] (C radiances, then linear T).  Column
-// x = 0 is never computed (no fluence depends on it) and is exported as NaN.
+// T_n of frame q -> dst[x][k][v][C+1] (C radiances, then linear T).  Entries
+// that no fluence depends on (t_live) are never computed and are exported as
+// NaN.
 template <int P, int C>
 __global__ void k_export_T(Plan pl, int q, int n, float *__restrict__ dst) {
     const QuadGeom &g = pl.q[q];
@@ -18,7 +19,7 @@ __global__ void k_export_T(Plan pl, int q, int n, float *__restrict__ dst) {
         const long long r = i / g.V;
         const int k = (int)(r % K), x = (int)(r / K);
         float *o = dst + i * (C + 1);
-        if (x == 0) {
+        if (!t_live(n, x, k)) {
 #pragma unroll
             for (int c = 0; c <= C; ++c) o[c] = __int_as_float(0x7fc00000);
             continue;

@@ -134,6 +134,7 @@ cudaError_t launch_r0(const Plan &pl, cudaStream_t st);
 
 double bytes_T(const Plan &pl, int q, int n);
 double bytes_T_odd(const Plan &pl, int q, int n);
+double bytes_T_even_dirs(const Plan &pl, int q, int n);
 double bytes_R(const Plan &pl, int q, int n);
 
 }  // namespace hrc

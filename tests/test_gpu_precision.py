@@ -48,6 +48,8 @@ def test_reduced_precision_levels_log_transmittance(prec):
     for n in (0, 2, 4, 5):
         Tg = h.level(1, "T", n).cpu().numpy()[1:]   # column 0 is dead (not computed)
         Tr = oracle.frame_level(e, s, 1, "T", n)[1:]
+        if n == 0:                                   # so are the even columns of T_0
+            Tg, Tr = Tg[::2], Tr[::2]
         assert np.max(np.abs(Tg[..., -1] - Tr[..., -1])) <= 1e-5
         assert err_max(Tg[..., :-1], Tr[..., :-1]) <= BOUNDS[prec][0]
 
