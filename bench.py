@@ -87,7 +87,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -218,6 +218,23 @@ def run_ours(args):
     tuned_ms = h.autotune()
     if args.schedule >= 0:
         _lib.hrc_set_schedule(h.ctx, args.schedule)
+    if args.profile_once:
+        # For profilers: after the same tuning as a bench run, one forward and
+        # one backward with direct (not graph-replayed) launches inside the
+        # NVTX range "hrc_profile" (ncu --nvtx --nvtx-include "hrc_profile/").
+        gF1 = torch.ones((C, H, W), dtype=torch.float32, device=dev)
+        h.forward(e, s, F)
+        h.backward(gF1)
+        torch.cuda.synchronize(dev)
+        _lib.hrc_set_timing(h.ctx, True)
+        torch.cuda.nvtx.range_push("hrc_profile")
+        h.forward(e, s, F)
+        h.backward(gF1)
+        torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
+        _lib.hrc_set_timing(h.ctx, False)
+        print(json.dumps({"profile_once": args.workload, "launches_fwd_bwd": h.launch_count()}))
+        return
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     gF = torch.ones((C, H, W), dtype=torch.float32, device=dev)
@@ -451,6 +468,9 @@ def main():
     ap.add_argument("--schedule", type=int, default=-1, help="launch schedule (default: the library's)")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64-scene batched persistent-launch measurement")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="tune, then run one forward + backward inside the NVTX range hrc_profile "
+                         "with direct launches (a target for ncu), print no bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
