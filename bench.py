@@ -351,6 +351,7 @@ def run_ours(args):
                    "l2": "flushed (256 MB write) before every timed step, outside the timed events",
                    "launch": "one CUDA graph per pass (captured at warm-up); configuration chosen by hrc_autotune",
                    "autotune_best_ms": tuned_ms,
+                   "launch_config": h.launch_config,
                    "baseline_context": "paper Table 1 on an RTX 3080 Laptop with fp16 storage"},
         "roofline": {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,

@@ -81,13 +81,33 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec);
  *     larger launches). */
 hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule);
 
-/* Autotuner: times every launch configuration (schedule 0/1 x one or two
- * element groups per thread in the merge kernels) with forward passes over
- * the context's own staging buffers (the timing does not depend on the
- * data), keeps the fastest, and writes its ms per frame to *best_ms (may be
- * NULL).  Synchronous.  Results do not depend on the configuration.
- * Single-scene contexts in fp32 / fp16 / bf16; the borrowed forward inputs
- * are forgotten (run hrc_fluence again before hrc_fluence_backward). */
+/* Launch configuration of a single-scene context (tuning knobs; results are
+ * identical for every setting):
+ *   schedule: as hrc_set_schedule (0 or 1);
+ *   groups:   v-pairs per thread in the merge-up kernel (1 or 2);
+ *   threads:  threads per block of the merge and adjoint-merge kernels
+ *             (64, 128, 256 or 512);
+ *   vmajor:   grid order of those kernels: 0 = rows in gridDim.x, v-blocks
+ *             in gridDim.y; 1 = the reverse (allowed while 4 (W + H) <= 65535,
+ *             the gridDim.y limit for the adjoint's level-0 rows).
+ * Defaults {0, 1, 128, 0}; hrc_autotune picks one. */
+typedef struct hrc_launch_config {
+    int schedule, groups, threads, vmajor;
+} hrc_launch_config;
+
+/* Read / set the launch configuration.  Setting it forgets the borrowed
+ * forward inputs (run hrc_fluence again before hrc_fluence_backward).
+ * HRC_EINVAL for a value outside the ranges above. */
+hrc_status hrc_get_launch_config(const hrc_ctx *ctx, hrc_launch_config *cfg);
+hrc_status hrc_set_launch_config(hrc_ctx *ctx, const hrc_launch_config *cfg);
+
+/* Autotuner: times every launch configuration (schedule x groups x threads x
+ * grid order, as hrc_launch_config) with forward passes over the context's
+ * own staging buffers (the timing does not depend on the data), keeps the
+ * fastest, and writes its ms per frame to *best_ms (may be NULL).
+ * Synchronous.  Results do not depend on the configuration.  Single-scene
+ * contexts in fp32 / fp16 / bf16; the borrowed forward inputs are forgotten
+ * (run hrc_fluence again before hrc_fluence_backward). */
 hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms);
 
 /* Forward pass, Algorithm 1 (Lighting) without the Eq. 21 blur:

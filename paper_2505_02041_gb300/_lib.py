@@ -28,6 +28,8 @@ SIGNATURES = [
     ("hrc_set_precision", _i, [_vp, _i]),
     ("hrc_set_schedule", _i, [_vp, _i]),
     ("hrc_autotune", _i, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    ("hrc_get_launch_config", _i, [_vp, _vp]),
+    ("hrc_set_launch_config", _i, [_vp, _vp]),
     ("hrc_fluence", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_fluence_host", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_fluence_backward", _i, [_vp, _vp, _vp, _vp]),
@@ -113,6 +115,22 @@ def hrc_set_precision(ctx, prec: int):
 
 def hrc_set_schedule(ctx, schedule: int):
     check(load().hrc_set_schedule(ctx, schedule), ctx)
+
+
+class hrc_launch_config(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int), ("groups", ctypes.c_int), ("threads", ctypes.c_int),
+                ("vmajor", ctypes.c_int)]
+
+
+def hrc_get_launch_config(ctx) -> dict:
+    c = hrc_launch_config()
+    check(load().hrc_get_launch_config(ctx, ctypes.byref(c)), ctx)
+    return {f: getattr(c, f) for f, _ in hrc_launch_config._fields_}
+
+
+def hrc_set_launch_config(ctx, schedule: int, groups: int, threads: int, vmajor: int):
+    c = hrc_launch_config(schedule, groups, threads, vmajor)
+    check(load().hrc_set_launch_config(ctx, ctypes.byref(c)), ctx)
 
 
 def hrc_autotune(ctx) -> float:

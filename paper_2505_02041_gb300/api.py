@@ -150,6 +150,16 @@ class HRC:
         self._host_levels = False
         return ms
 
+    @property
+    def launch_config(self) -> dict:
+        """{schedule, groups, threads, vmajor} (see hrc_launch_config)."""
+        return _lib.hrc_get_launch_config(self.ctx)
+
+    def set_launch_config(self, schedule=0, groups=1, threads=128, vmajor=0) -> None:
+        _lib.hrc_set_launch_config(self.ctx, schedule, groups, threads, vmajor)
+        self._borrowed = (None, None, 0, 0)
+        self._host_levels = False
+
     def launch_count(self) -> int:
         return _lib.hrc_last_launch_count(self.ctx)
 

@@ -436,6 +436,44 @@ hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule) {
     return HRC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+bool config_valid(const hrc_ctx *ctx, const hrc_launch_config &c) {
+    return (c.schedule == 0 || c.schedule == 1) && (c.groups == 1 || c.groups == 2) &&
+           (c.threads == 64 || c.threads == 128 || c.threads == 256 || c.threads == 512) &&
+           (c.vmajor == 0 || c.vmajor == 1) &&
+           !(c.vmajor && 4LL * (ctx->W + ctx->H) > 65535);
+}
+
+void apply_config(hrc_ctx *ctx, const hrc_launch_config &c) {
+    hrc_set_schedule(ctx, c.schedule);
+    ctx->mgroups = ctx->plan.mgroups = ctx->plan64.mgroups = c.groups;
+    ctx->mthreads = ctx->plan.mthreads = ctx->plan64.mthreads = c.threads;
+    ctx->vmajor = ctx->plan.vmajor = ctx->plan64.vmajor = c.vmajor;
+}
+}  // namespace
+
+extern "C" {
+
+hrc_status hrc_get_launch_config(const hrc_ctx *ctx, hrc_launch_config *cfg) {
+    if (!ctx || !cfg) return HRC_EINVAL;
+    cfg->schedule = ctx->sched;
+    cfg->groups = ctx->mgroups;
+    cfg->threads = ctx->mthreads;
+    cfg->vmajor = ctx->vmajor;
+    return HRC_OK;
+}
+
+hrc_status hrc_set_launch_config(hrc_ctx *ctx, const hrc_launch_config *cfg) {
+    if (!ctx || !cfg) return HRC_EINVAL;
+    if (ctx->batched) return fail(ctx, HRC_EINVAL, "hrc_set_launch_config: single-scene contexts only");
+    if (!config_valid(ctx, *cfg)) return fail(ctx, HRC_EINVAL, "hrc_set_launch_config: value out of range");
+    apply_config(ctx, *cfg);
+    ctx->have_fwd = false;
+    return HRC_OK;
+}
+
 hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
     hrc_status st = check_ctx(ctx);
     if (st != HRC_OK) return st;
@@ -449,45 +487,29 @@ hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     float best = 1e30f;
-    int best_s = ctx->sched, best_g = ctx->mgroups, best_t = ctx->mthreads, best_v = ctx->vmajor;
+    hrc_launch_config best_c;
+    hrc_get_launch_config(ctx, &best_c);
     const bool timing = ctx->rec.on;
     ctx->rec.on = false;
-    static const int kThreads[3] = {128, 256, 512};
-    for (int cand = 0; cand < 2 * 2 * 3 * 2 && st == HRC_OK; ++cand) {
-            const int sc = cand & 1, mg = 1 + ((cand >> 1) & 1), mt = kThreads[(cand >> 2) % 3], vm = (cand / 12) & 1;
-            // v-block-major grids put rows in gridDim.y (at most 65535; the
-            // adjoint's level 0 has 4 (W + H) rows)
-            if (vm && 4LL * (ctx->W + ctx->H) > 65535) continue;
-            hrc_set_schedule(ctx, sc);
-            ctx->mgroups = mg;
-            ctx->plan.mgroups = mg;
-            ctx->mthreads = mt;
-            ctx->plan.mthreads = mt;
-            ctx->vmajor = vm;
-            ctx->plan.vmajor = vm;
-            for (int r = 0; r < 2 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
-            cudaEventRecord(a, ctx->stream);
-            for (int r = 0; r < 5 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
-            cudaEventRecord(b, ctx->stream);
-            cudaEventSynchronize(b);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, a, b);
-            ms /= 5.f;
-            if (ms < best) { best = ms; best_s = sc; best_g = mg; best_t = mt; best_v = vm; }
+    static const int kThreads[4] = {64, 128, 256, 512};
+    for (int cand = 0; cand < 2 * 2 * 4 * 2 && st == HRC_OK; ++cand) {
+        const hrc_launch_config c{cand & 1, 1 + ((cand >> 1) & 1), kThreads[(cand >> 2) & 3], (cand >> 4) & 1};
+        if (!config_valid(ctx, c)) continue;
+        apply_config(ctx, c);
+        for (int r = 0; r < 2 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
+        cudaEventRecord(a, ctx->stream);
+        for (int r = 0; r < 5 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
+        cudaEventRecord(b, ctx->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        ms /= 5.f;
+        if (ms < best) { best = ms; best_c = c; }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     ctx->rec.on = timing;
-    hrc_set_schedule(ctx, best_s);
-    ctx->mgroups = best_g;
-    ctx->plan.mgroups = best_g;
-    ctx->plan64.mgroups = best_g;
-    ctx->mthreads = best_t;
-    ctx->plan.mthreads = best_t;
-    ctx->plan64.mthreads = best_t;
-    ctx->vmajor = best_v;
-    ctx->plan.vmajor = best_v;
-    ctx->plan64.vmajor = best_v;
+    apply_config(ctx, best_c);
     ctx->have_fwd = false;
     if (st != HRC_OK) return st;
     if (best_ms) *best_ms = best;

@@ -130,3 +130,30 @@ def test_autotune_keeps_results():
     F = h.forward(to_dev(e), to_dev(s))
     assert torch.equal(F, ref)
     assert err_max(F.cpu().numpy(), oracle.fluence(e, s)) <= TOL
+
+
+def test_launch_configurations_give_the_same_results():
+    """Every launch configuration (schedule, merge-up groups, block width, grid
+    order) computes the same forward and backward: the arithmetic of each
+    entry does not depend on how the work is cut into blocks."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC
+    e, s = scenes.random_scene(70, 53, 3, 31)
+    gF = scenes.rng(32).normal(size=e.shape).astype(np.float32)
+    h = HRC(70, 53, 3)
+    ed, sd, gd = to_dev(e), to_dev(s), to_dev(gF)
+    ref = None
+    for sched in (0, 1):
+        for groups in (1, 2):
+            for threads in (64, 128, 256, 512):
+                for vmajor in (0, 1):
+                    h.set_launch_config(sched, groups, threads, vmajor)
+                    assert h.launch_config == dict(schedule=sched, groups=groups, threads=threads, vmajor=vmajor)
+                    F = h.forward(ed, sd).cpu().numpy()
+                    ge, gs = h.backward(gd)
+                    out = (F, ge.cpu().numpy(), gs.cpu().numpy())
+                    if ref is None:
+                        ref = out
+                        continue
+                    for a, b in zip(out, ref):
+                        assert np.max(np.abs(a - b)) <= 1e-6 * max(1.0, np.max(np.abs(b))), (sched, groups, threads, vmajor)
