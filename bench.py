@@ -291,6 +291,16 @@ def run_ours(args):
     # timed region 2: forward + backward
     fb_ms = timed(fwd_bwd, args.steps)
     barrier()
+    # timed region 2b: forward + backward that recomputes every level
+    _lib.hrc_set_backward_recompute(h.ctx, 1)
+    fwd_bwd()
+    fwd_bwd()
+    rc_launches = h.launch_count()
+    barrier()
+    fbr_ms = timed(fwd_bwd, args.steps)
+    barrier()
+    _lib.hrc_set_backward_recompute(h.ctx, 0)
+    fwd_bwd()
     # timed region 3: the same frames with per-launch CUDA events (kernel
     # durations for the roofline; launches are not graph-replayed here)
     _lib.hrc_set_timing(h.ctx, True)
@@ -309,9 +319,10 @@ def run_ours(args):
     _lib.hrc_set_timing(h.ctx, False)
     barrier()
     clk = clocks.stop()
-    total_ms, fb_total = aggregate_max([sum(step_ms), sum(fb_ms)], world, dev)
+    total_ms, fb_total, fbr_total = aggregate_max([sum(step_ms), sum(fb_ms), sum(fbr_ms)], world, dev)
     ms_per_frame = per_frame(total_ms, args.steps, world)
     fb_mean = per_frame(fb_total, args.steps, world)
+    fbr_mean = per_frame(fbr_total, args.steps, world)
 
     # end to end: host buffers through the C ABI, copies included
     e_h = torch.from_numpy(e_np).pin_memory()
@@ -339,6 +350,8 @@ def run_ours(args):
     frame_bytes = sum(v[1] for v in per_kind.values()) / args.steps
     bwd_bytes = sum(v[1] for v in bwd_kind.values()) / args.steps
     fb_bytes = frame_bytes + bwd_bytes
+    sum_bytes = per_kind.get("fluence_sum", [0.0, 0.0, 0])[1] / args.steps
+    fbr_bytes = fb_bytes + frame_bytes - sum_bytes   # the recompute repeats the forward but the sum
     line = {
         "metric": METRIC, "value": ms_per_frame, "unit": "ms/frame", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
@@ -366,10 +379,18 @@ def run_ours(args):
                     "frac_of_peak": fb_bytes / (fb_mean * 1e-3) / 1e9 / hbm_peak,
                     "backward_phases": {k: {"ms_per_frame": v[0] / args.steps, "launches_per_frame": v[2] / args.steps,
                                             "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None}
-                                        for k, v in sorted(bwd_kind.items())}},
+                                        for k, v in sorted(bwd_kind.items())},
+                    "backward": "reads the levels the forward left in the context"},
+        "fwd_bwd_recompute": {"ms": fbr_mean, "algorithmic_bytes": fbr_bytes,
+                              "GBps": fbr_bytes / (fbr_mean * 1e-3) / 1e9,
+                              "frac_of_peak": fbr_bytes / (fbr_mean * 1e-3) / 1e9 / hbm_peak,
+                              "backward": "recomputes every level from the inputs first (hrc_set_backward_recompute)"},
         "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": (C + 1) * H * W * 4,
                 "d2h_bytes_per_step": C * H * W * 4},
-        "gpu_launches": (fwd_launches + bwd_launches) * args.steps,
+        "gpu_launches": fwd_launches * args.steps,
+        "launches_per_step": {"forward": fwd_launches, "backward": bwd_launches,
+                              "backward_recompute": rc_launches,
+                              "note": "gpu_launches counts the forward frames timed for value"},
         "clocks": clk,
     }
     if args.precisions and world == 1:

@@ -126,14 +126,25 @@ hrc_status hrc_fluence_host(hrc_ctx *ctx, const float *emission, const float *si
 
 /* Adjoint of the last hrc_fluence on this context: given dLoss/dF (grad_F,
  * [C][H][W]), writes dLoss/d emission ([C][H][W]) and dLoss/d sigma_t
- * ([H][W]).  Outputs are overwritten, not accumulated.  It reads the
- * intervals T_n / R_n that the last forward left in the context's buffers
- * and re-traces the borrowed inputs, which must be unchanged since that
- * forward; it may be called several times (another grad_F) without a new
- * forward.  Enqueue it on the forward's stream, or order the two streams.
- * HRC_ESTATE if no forward ran on this context. */
+ * ([H][W]).  Outputs are overwritten, not accumulated.  By default it reads
+ * the intervals T_n / R_n that the last forward left in the context's
+ * buffers; with hrc_set_backward_recompute(ctx, 1) it first recomputes them
+ * from the borrowed inputs.  Either way it re-traces the borrowed inputs,
+ * which must be unchanged since that forward; it may be called several
+ * times (another grad_F) without a new forward.  Enqueue it on the forward's
+ * stream, or order the two streams.  HRC_ESTATE if no forward ran on this
+ * context. */
 hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_emission,
                                 float *grad_sigma_t);
+
+/* Backward strategy of a context (single-scene or batched): 0 (default) =
+ * read the levels the forward left in the buffers; 1 = recompute every
+ * level T_0..T_N, R_1..R_{N-1} from the borrowed inputs at the start of
+ * each backward, so that the backward depends on no forward-time storage:
+ * it differentiates at the inputs' contents at the time of the backward.
+ * For unchanged inputs the gradients are the same either way; recomputing
+ * costs about one forward pass. */
+hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on);
 
 /* FP64 instance of hrc_fluence / hrc_fluence_backward (device fp64 buffers,
  * same layouts); requires hrc_set_precision(ctx, HRC_FP64_TEST). */

@@ -28,6 +28,7 @@ SIGNATURES = [
     ("hrc_set_precision", _i, [_vp, _i]),
     ("hrc_set_schedule", _i, [_vp, _i]),
     ("hrc_autotune", _i, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    ("hrc_set_backward_recompute", _i, [_vp, _i]),
     ("hrc_get_launch_config", _i, [_vp, _vp]),
     ("hrc_set_launch_config", _i, [_vp, _vp]),
     ("hrc_fluence", _i, [_vp, _vp, _vp, _vp]),
@@ -115,6 +116,10 @@ def hrc_set_precision(ctx, prec: int):
 
 def hrc_set_schedule(ctx, schedule: int):
     check(load().hrc_set_schedule(ctx, schedule), ctx)
+
+
+def hrc_set_backward_recompute(ctx, on: bool):
+    check(load().hrc_set_backward_recompute(ctx, int(bool(on))), ctx)
 
 
 class hrc_launch_config(ctypes.Structure):

@@ -150,6 +150,12 @@ class HRC:
         self._host_levels = False
         return ms
 
+    def set_backward_recompute(self, on: bool) -> None:
+        """Recompute every level at the start of each backward (True) instead
+        of reading the ones the forward left in the context (False, default);
+        see hrc_set_backward_recompute."""
+        _lib.hrc_set_backward_recompute(self.ctx, on)
+
     @property
     def launch_config(self) -> dict:
         """{schedule, groups, threads, vmajor} (see hrc_launch_config)."""
@@ -235,6 +241,9 @@ class BatchedHRC:
     def sync(self):
         """Wait and raise HRCError(HRC_ETIMEOUT) if a dependency wait gave up."""
         _lib.hrc_batched_sync(self.ctx)
+
+    def set_backward_recompute(self, on: bool) -> None:
+        _lib.hrc_set_backward_recompute(self.ctx, on)
 
     def tune(self, blocks_per_sm: int = 0, order: int = 0):
         _lib.hrc_batched_tune(self.ctx, blocks_per_sm, order)

@@ -188,6 +188,7 @@ struct hrc_ctx {
     float *dev_e = nullptr, *dev_s = nullptr, *dev_F = nullptr;   // hrc_fluence_host staging
     const void *last_e = nullptr, *last_s = nullptr;
     bool have_fwd = false;
+    bool bwd_recompute = false;  // backward recomputes the levels instead of reading the forward's
     int launches = 0;
     Recorder rec;
     std::string err;
@@ -212,12 +213,12 @@ struct hrc_ctx {
     std::vector<long long> eoff, soff;
     Plan *d_plans = nullptr;
     long long *d_eoff = nullptr, *d_soff = nullptr;
-    StageBlock *d_blocks[2] = {nullptr, nullptr};
-    int nblocks[2] = {0, 0};
-    long long total[2] = {0, 0};
-    double bbytes[2] = {0, 0};
+    StageBlock *d_blocks[3] = {nullptr, nullptr, nullptr};
+    int nblocks[3] = {0, 0, 0};
+    long long total[3] = {0, 0, 0};
+    double bbytes[3] = {0, 0, 0};
     int *d_counters = nullptr;
-    int ncounters[2] = {0, 0};
+    int ncounters[3] = {0, 0, 0};
     unsigned long long *d_ticket = nullptr;
     int *d_status = nullptr;
     int withhold = -1;
@@ -419,6 +420,7 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->d_soff);
     cudaFree(ctx->d_blocks[0]);
     cudaFree(ctx->d_blocks[1]);
+    cudaFree(ctx->d_blocks[2]);
     cudaFree(ctx->d_counters);
     cudaFree(ctx->d_ticket);
     cudaFree(ctx->d_status);
@@ -455,6 +457,13 @@ void apply_config(hrc_ctx *ctx, const hrc_launch_config &c) {
 }  // namespace
 
 extern "C" {
+
+hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on) {
+    if (!ctx) return HRC_EINVAL;
+    if (on != 0 && on != 1) return fail(ctx, HRC_EINVAL, "hrc_set_backward_recompute: 0 or 1");
+    ctx->bwd_recompute = on != 0;
+    return HRC_OK;
+}
 
 hrc_status hrc_get_launch_config(const hrc_ctx *ctx, hrc_launch_config *cfg) {
     if (!ctx || !cfg) return HRC_EINVAL;
@@ -653,9 +662,10 @@ hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_e
     const Plan pl = ctx->plan;
     const RayTable *rt = &ctx->rt;
     const void *le = ctx->last_e, *ls = ctx->last_s;
-    return run_pass(ctx, 1, le, ls, grad_F, grad_emission, grad_sigma_t,
+    const bool rc = ctx->bwd_recompute;
+    return run_pass(ctx, rc ? 4 : 1, le, ls, grad_F, grad_emission, grad_sigma_t,
                     [&](cudaStream_t s, int *n, Recorder *r) {
-                        return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, s, n, r);
+                        return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, s, n, r);
                     },
                     "hrc_fluence_backward");
 }
@@ -671,9 +681,10 @@ hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *
     const Plan pl = ctx->plan64;
     const RayTable *rt = &ctx->rt;
     const void *le = ctx->last_e, *ls = ctx->last_s;
-    return run_pass(ctx, 3, le, ls, grad_F, grad_emission, grad_sigma_t,
+    const bool rc = ctx->bwd_recompute;
+    return run_pass(ctx, rc ? 5 : 3, le, ls, grad_F, grad_emission, grad_sigma_t,
                     [&](cudaStream_t s, int *n, Recorder *r) {
-                        return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, s, n, r);
+                        return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, s, n, r);
                     },
                     "hrc_fluence_backward_f64");
 }
@@ -686,7 +697,8 @@ hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *
 
 namespace {
 
-// Build and upload the ticket tables of both modes (forward, backward).
+// Build and upload the ticket tables of the three modes (forward, backward,
+// backward with recomputed levels).
 hrc_status build_batched_tables(hrc_ctx *ctx) {
     std::vector<int> order(ctx->nscenes);
     for (int i = 0; i < ctx->nscenes; ++i) order[i] = i;
@@ -694,7 +706,7 @@ hrc_status build_batched_tables(hrc_ctx *ctx) {
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
             return (long long)ctx->Ws[a] * ctx->Hs[a] > (long long)ctx->Ws[b] * ctx->Hs[b];
         });
-    for (int mode = 0; mode < 2; ++mode) {
+    for (int mode = 0; mode < 3; ++mode) {
         std::vector<std::vector<StageDesc>> st(ctx->nscenes);
         size_t maxs = 0;
         for (int i = 0; i < ctx->nscenes; ++i) {
@@ -793,7 +805,7 @@ hrc_status run_batched(hrc_ctx *ctx, int mode, const void *e, const void *s, voi
         if (err == cudaSuccess) err = cudaMemsetAsync(a.status, 0, sizeof(int), st);
         if (err != cudaSuccess) return err;
         r->begin(K_BATCHED, mode, bytes);
-        err = launch_batched(a, prec, C, bpsm, mode, st);
+        err = launch_batched(a, prec, C, bpsm, mode == 0 ? 0 : 1, st);
         r->end();
         ++*n;
         return err;
@@ -871,7 +883,7 @@ hrc_status hrc_create_batched_prec(int n, const int *W, const int *H, int channe
         hrc_destroy(ctx);
         return fail(nullptr, st, msg);
     }
-    for (int mode = 0; mode < 2; ++mode)
+    for (int mode = 0; mode < 3; ++mode)
         if (ctx->ncounters[mode] > maxstages) {
             hrc_destroy(ctx);
             return fail(nullptr, HRC_EINVAL, "hrc_create_batched: stage count exceeds the counter buffer");
@@ -912,7 +924,7 @@ hrc_status hrc_fluence_backward_batched(hrc_ctx *ctx, const float *grad_F, float
     if (!grad_F || !grad_emission || !grad_sigma_t) return fail(ctx, HRC_EINVAL, "hrc_fluence_backward_batched: NULL pointer");
     if (!aligned16(grad_F) || !aligned16(grad_emission) || !aligned16(grad_sigma_t))
         return fail(ctx, HRC_EINVAL, "hrc_fluence_backward_batched: pointers must be 16-byte aligned");
-    return run_batched(ctx, 1, ctx->last_e, ctx->last_s, nullptr, grad_F, grad_emission, grad_sigma_t,
+    return run_batched(ctx, ctx->bwd_recompute ? 2 : 1, ctx->last_e, ctx->last_s, nullptr, grad_F, grad_emission, grad_sigma_t,
                        "hrc_fluence_backward_batched");
 }
 

@@ -69,7 +69,8 @@ __device__ __forceinline__ void batched_adjoint_item(const BatchArgs &a, const S
     }
 }
 
-// MODE 0: the forward stages; MODE 1: the adjoint stages of the backward.
+// MODE 0: the forward stages; MODE 1: the stages of the backward (the
+// adjoint, preceded by the forward's level stages when they are recomputed).
 template <int P, int C, int MODE>
 __global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
     using IN = typename std::conditional<P == P_FP64, double, float>::type;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
         const int vb = (int)(j % sb.nvb);
         const long long r0 = (j / sb.nvb) * sb.rpi;
         const long long r1 = r0 + sb.rpi < sb.rows ? r0 + sb.rpi : sb.rows;
-        if constexpr (MODE == 0) {
+        if (MODE == 0 || sb.kind <= BK_MERGE_DOWN2) {   // forward stages (mode 2 recomputes them)
             switch (sb.kind) {
             case BK_TRACE:
                 body_trace012<P, C>(pl, (const float *)e, (const float *)s, (const double *)e, (const double *)s, 15,
@@ -131,11 +132,11 @@ __global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
             case BK_MERGE_DOWN2:
                 for (long long r = r0; r < r1; ++r) body_merge_down<P, C, true>(pl, sb.rs, sb.level, r, vb);
                 break;
-            default:   // BK_SUM (with the level-0 merge down)
-                body_fluence<P, C, IN>(pl, (IN *)a.F + eo, vb, (int)(j / sb.nvb), smem);
+            default:   // BK_SUM (with the level-0 merge down); forward launches only
+                if constexpr (MODE == 0) body_fluence<P, C, IN>(pl, (IN *)a.F + eo, vb, (int)(j / sb.nvb), smem);
                 break;
             }
-        } else {
+        } else if constexpr (MODE == 1) {
             batched_adjoint_item<P, C, IN>(a, sb, pl, j, vb, r0, r1, eo, so, e, s, smem);
         }
         __syncthreads();
@@ -219,7 +220,7 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
         out.push_back(d);
     };
     double by = 0;
-    if (mode == 0) {   // the backward reads the levels the forward left in the buffers
+    if (mode != 1) {   // mode 1 reads the levels the forward left in the buffers
         by = img * (pl.C + 1) * esz;
         for (int q = 0; q < 4; ++q)
             for (int n = 0; n <= 2; ++n) by += bytes_T(pl, q, n);
@@ -241,13 +242,15 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
             }
             rowstage(BK_MERGE_DOWN2, n, vb2, by);
         }
-        by = img * pl.C * esz;
-        for (int q = 0; q < 4; ++q) {
-            if (pl.q[q].N < 1) continue;
-            by += bytes_T_odd(pl, q, 0) + bytes_R(pl, q, 1) + bytes_T_even_dirs(pl, q, 1);
+        if (mode == 0) {
+            by = img * pl.C * esz;
+            for (int q = 0; q < 4; ++q) {
+                if (pl.q[q].N < 1) continue;
+                by += bytes_T_odd(pl, q, 0) + bytes_R(pl, q, 1) + bytes_T_even_dirs(pl, q, 1);
+            }
+            tilestage(BK_SUM, tx, ty, by);   // 32 x 32 tiles, as the standalone kernel
+            return;
         }
-        tilestage(BK_SUM, tx, ty, by);   // 32 x 32 tiles, as the standalone kernel
-        return;
     }
     const double ab = 4.0;   // adjoint buffers are fp32 in the batched precisions
     auto gT = [&](int q, int n) {
@@ -294,9 +297,12 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
 // backward the adjoint-trace tile and the transposed dL/dF tile.
 template <int P, int C> size_t batched_smem(int mode) {
     using A = typename Prec<P>::A;
-    if (mode == 0) return TraceTile<A, C>::bytes() > fluence_smem<P, C>() ? TraceTile<A, C>::bytes() : fluence_smem<P, C>();
-    const size_t m = adj_trace_smem<A, C>(), sum_tile = sizeof(A) * C * 32 * 33;
-    return m > sum_tile ? m : sum_tile;
+    const size_t tr = TraceTile<A, C>::bytes();
+    if (mode == 0) return tr > fluence_smem<P, C>() ? tr : fluence_smem<P, C>();
+    size_t m = adj_trace_smem<A, C>();
+    const size_t sum_tile = sizeof(A) * C * 32 * 33;
+    m = m > sum_tile ? m : sum_tile;
+    return m > tr ? m : tr;   // the recomputing backward runs the trace stage too
 }
 
 template <int P, int C, int MODE>

@@ -93,7 +93,7 @@ int vblocks_b(const Plan &pl, int bs) {
 
 template <int P, int C>
 static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,
-                            void *ge, void *gs, cudaStream_t st, int *launches, Recorder *rec) {
+                            void *ge, void *gs, bool recompute, cudaStream_t st, int *launches, Recorder *rec) {
     using IN = typename std::conditional<P == P_FP64, double, float>::type;
     const int mt = pl.mthreads, ts = 2 * mt > 512 ? 512 : 2 * mt;   // paired-v / single-v block sizes
     int Nmax = 0;
@@ -109,8 +109,13 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         const QuadGeom &g = pl.q[q];
         return (n < 0 || n >= g.N) ? 0.0 : double(g.Un[n] - 1) * (1 << n) * g.V * pl.C * ab;
     };
-    // T_0..T_N and R_0..R_{N-1} are the ones the last forward left in the
-    // plan's buffers (the inputs are unchanged since, by contract).
+    // T_0..T_N and R_1..R_{N-1}: recomputed from (e, s), or the ones the last
+    // forward left in the plan's buffers (the inputs unchanged since, by
+    // contract).
+    if (recompute) {
+        cudaError_t err = launch_forward(pl, rt, e, s, nullptr, st, launches, rec);
+        if (err != cudaSuccess) return err;
+    }
     {
         double by = img * pl.C * ab;
         for (int q = 0; q < 4; ++q) by += gRbytes(q, 0);
@@ -178,12 +183,12 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
 
 template <int P>
 static cudaError_t bwd_prec(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,
-                            void *ge, void *gs, cudaStream_t st, int *launches, Recorder *rec) {
+                            void *ge, void *gs, bool rc, cudaStream_t st, int *launches, Recorder *rec) {
     switch (pl.C) {
-    case 1: return bwd_impl<P, 1>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
-    case 2: return bwd_impl<P, 2>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
-    case 3: return bwd_impl<P, 3>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
-    default: return bwd_impl<P, 4>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
+    case 1: return bwd_impl<P, 1>(pl, rt, e, s, gF, ge, gs, rc, st, launches, rec);
+    case 2: return bwd_impl<P, 2>(pl, rt, e, s, gF, ge, gs, rc, st, launches, rec);
+    case 3: return bwd_impl<P, 3>(pl, rt, e, s, gF, ge, gs, rc, st, launches, rec);
+    default: return bwd_impl<P, 4>(pl, rt, e, s, gF, ge, gs, rc, st, launches, rec);
     }
 }
 
@@ -211,12 +216,12 @@ cudaError_t prepare_backward_kernels() {
 }
 
 cudaError_t launch_backward(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,
-                            void *ge, void *gs, cudaStream_t st, int *launches, Recorder *rec) {
+                            void *ge, void *gs, bool recompute, cudaStream_t st, int *launches, Recorder *rec) {
     switch (pl.prec) {
-    case P_FP32: return bwd_prec<P_FP32>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
-    case P_FP16: return bwd_prec<P_FP16>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
-    case P_BF16: return bwd_prec<P_BF16>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
-    default: return bwd_prec<P_FP64>(pl, rt, e, s, gF, ge, gs, st, launches, rec);
+    case P_FP32: return bwd_prec<P_FP32>(pl, rt, e, s, gF, ge, gs, recompute, st, launches, rec);
+    case P_FP16: return bwd_prec<P_FP16>(pl, rt, e, s, gF, ge, gs, recompute, st, launches, rec);
+    case P_BF16: return bwd_prec<P_BF16>(pl, rt, e, s, gF, ge, gs, recompute, st, launches, rec);
+    default: return bwd_prec<P_FP64>(pl, rt, e, s, gF, ge, gs, recompute, st, launches, rec);
     }
 }
 

@@ -153,8 +153,8 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             rec->end();
             ++*launches;
         }
-        // with the fluence sum, level 0 is computed inside it (R_0 feeds nothing else)
-        for (int n = Nmax - 1; n >= (with_sum ? 1 : 0); --n) {
+        // R_0 feeds only the fluence sum, which computes it in place
+        for (int n = Nmax - 1; n >= 1; --n) {
             RowSplit rs = make_split(pl, n, 2, qsel);
             if (rs.start[4] == 0) continue;
             double by = 0;

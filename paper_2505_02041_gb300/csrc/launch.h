@@ -92,7 +92,9 @@ struct BatchArgs {
 };
 
 // Stage list of one scene: mode 0 = forward (with the fluence sum),
-// mode 1 = backward (every adjoint step over the levels of the last forward).
+// mode 1 = backward (every adjoint step over the levels of the last forward);
+// mode 2 = backward recomputing the levels first (forward stages without the
+// fluence sum, then the adjoint stages; run by the mode-1 kernel).
 struct StageDesc {
     int kind, level, count, nvb, rpi;
     long long rows;
@@ -111,11 +113,12 @@ int plan_nmax(const Plan &pl);
 // Message returned by hrc_last_error(NULL) on this thread.
 void set_global_error(const char *msg);
 
-// Backward pass: the adjoint of every step over the levels the last forward
-// left in the plan's buffers; writes dL/de (ge) and dL/dsigma (gs) from
-// dL/dF (gF), re-tracing (e, s).
+// Backward pass: the adjoint of every step over the levels T_n / R_n,
+// either recomputed from (e, s) first (recompute) or as the last forward left
+// them in the plan's buffers; writes dL/de (ge) and dL/dsigma (gs) from dL/dF
+// (gF), re-tracing (e, s).
 cudaError_t launch_backward(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,
-                            void *ge, void *gs, cudaStream_t st, int *launches, Recorder *rec);
+                            void *ge, void *gs, bool recompute, cudaStream_t st, int *launches, Recorder *rec);
 
 // One-time per-device kernel set-up (dynamic shared-memory limits); must run
 // with the device current before the kernels are launched or captured.

@@ -71,6 +71,13 @@ def test_batched_backward_matches_single():
     ge_r, gs_r = oracle.fluence_adjoint(es[0].numpy(), ss[0].numpy(), gFs[0].cpu().numpy())
     assert err_max(ges[0].cpu().numpy(), ge_r) <= 1e-4
     assert err_max(gss[0].cpu().numpy(), gs_r) <= 1e-4
+    # the recomputing backward (forward level stages, then the adjoint, in
+    # one persistent launch) gives the same gradients
+    b.set_backward_recompute(True)
+    ge2, gs2 = b.backward(gF)
+    b.sync()
+    assert err_max(ge2.cpu().numpy(), ge.cpu().numpy()) <= 1e-6
+    assert err_max(gs2.cpu().numpy(), gs.cpu().numpy()) <= 1e-6
 
 
 def test_batched_tuning_does_not_change_results():
