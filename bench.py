@@ -425,7 +425,9 @@ def bench_batched(args, dev):
     """64 scenes of sizes drawn from {128, 256, 512, 1024, 2048}^2 (seed 4),
     C = 3, fog / disks / rectangles as the 512^2 workload (seeds 400+i),
     bf16 interval storage: forward and forward+backward of the whole batch,
-    each pass one persistent launch (graph-replayed)."""
+    each pass one graph-replayed launch sequence: the tile steps of all
+    scenes as ordinary launches around one persistent launch of the merge
+    cascade."""
     import torch
     from paper_2505_02041_gb300 import BatchedHRC, scenes
     sizes = scenes.batched_sizes(64, 4)
@@ -463,14 +465,20 @@ def bench_batched(args, dev):
             ts.append(a.elapsed_time(z))
         return statistics.mean(ts)
 
+    from paper_2505_02041_gb300 import _lib
     fwd_ms = run(lambda: b.forward(e, s, F))
+    n_fwd = _lib.hrc_last_launch_count(b.ctx)
     fb_ms = run(lambda: (b.forward(e, s, F), b.backward(gF, ge, gs)))
+    n_bwd = _lib.hrc_last_launch_count(b.ctx)
     b.sync()
     from collections import Counter
     out = {"scenes": len(sizes), "sizes": dict(Counter(sizes)), "channels": 3, "precision": "bf16",
            "forward_ms": fwd_ms, "forward_scenes_per_s": len(sizes) / (fwd_ms * 1e-3),
            "fwd_bwd_ms": fb_ms, "fwd_bwd_scenes_per_s": len(sizes) / (fb_ms * 1e-3),
-           "launches_per_pass": 1, "autotune_ms": {f"bpsm{k[0]}_order{k[1]}": v for k, v in tune.items()},
+           "launches_per_pass": {"forward": n_fwd, "backward": n_bwd,
+                                 "note": "trace / adjoint trace of all scenes as tile launches, the merge "
+                                         "cascade of all scenes in one persistent launch"},
+           "autotune_ms": {f"bpsm{k[0]}_order{k[1]}": v for k, v in tune.items()},
            "timed_batches": n}
     b.close()
     return out

@@ -214,6 +214,15 @@ struct hrc_ctx {
     Plan *d_plans = nullptr;
     long long *d_eoff = nullptr, *d_soff = nullptr;
     StageBlock *d_blocks[3] = {nullptr, nullptr, nullptr};
+    int *d_chunk[3] = {nullptr, nullptr, nullptr};   // ticket -> block index per mode
+    // tile steps of every scene as ordinary launches around the persistent one
+    struct TileLaunch {
+        int kind = 0, pair = 0, total = 0;
+        bool before = true;              // before the persistent launch (trace) or after (adjoint trace)
+        int *d_off = nullptr, *d_nx = nullptr;
+        double bytes = 0;
+    };
+    std::vector<TileLaunch> tiles[3];
     int nblocks[3] = {0, 0, 0};
     long long total[3] = {0, 0, 0};
     double bbytes[3] = {0, 0, 0};
@@ -418,9 +427,14 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->d_plans);
     cudaFree(ctx->d_eoff);
     cudaFree(ctx->d_soff);
-    cudaFree(ctx->d_blocks[0]);
-    cudaFree(ctx->d_blocks[1]);
-    cudaFree(ctx->d_blocks[2]);
+    for (int m = 0; m < 3; ++m) {
+        cudaFree(ctx->d_blocks[m]);
+        cudaFree(ctx->d_chunk[m]);
+        for (auto &t : ctx->tiles[m]) {
+            cudaFree(t.d_off);
+            cudaFree(t.d_nx);
+        }
+    }
     cudaFree(ctx->d_counters);
     cudaFree(ctx->d_ticket);
     cudaFree(ctx->d_status);
@@ -709,9 +723,50 @@ hrc_status build_batched_tables(hrc_ctx *ctx) {
     for (int mode = 0; mode < 3; ++mode) {
         std::vector<std::vector<StageDesc>> st(ctx->nscenes);
         size_t maxs = 0;
+        // the tile steps (trace, adjoint trace) leave the persistent stage
+        // lists and become one multi-scene launch each, in list order
+        for (auto &t : ctx->tiles[mode]) {
+            cudaFree(t.d_off);
+            cudaFree(t.d_nx);
+        }
+        ctx->tiles[mode].clear();
+        std::vector<std::vector<int>> toff, tnx;
         for (int i = 0; i < ctx->nscenes; ++i) {
-            batched_stages(ctx->bplans[i], mode, st[i]);
+            std::vector<StageDesc> all;
+            batched_stages(ctx->bplans[i], mode, all);
+            int ti = 0;
+            for (const StageDesc &d : all) {
+                if (d.kind != BK_TRACE && d.kind != BK_ADJ_TRACE) {
+                    st[i].push_back(d);
+                    continue;
+                }
+                if (i == 0) {
+                    hrc_ctx::TileLaunch t;
+                    t.kind = d.kind;
+                    t.pair = d.level;
+                    t.before = d.kind == BK_TRACE;
+                    ctx->tiles[mode].push_back(t);
+                    toff.push_back(std::vector<int>(1, 0));
+                    tnx.push_back(std::vector<int>());
+                }
+                auto &t = ctx->tiles[mode][ti];
+                toff[ti].push_back(toff[ti].back() + d.count);
+                tnx[ti].push_back(d.nvb);
+                t.total += d.count;
+                t.bytes += d.bytes;
+                ++ti;
+            }
             maxs = std::max(maxs, st[i].size());
+        }
+        for (size_t k = 0; k < ctx->tiles[mode].size(); ++k) {
+            auto &t = ctx->tiles[mode][k];
+            cudaError_t e = cudaMalloc(&t.d_off, sizeof(int) * toff[k].size());
+            if (e == cudaSuccess) e = cudaMalloc(&t.d_nx, sizeof(int) * tnx[k].size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(t.d_off, toff[k].data(), sizeof(int) * toff[k].size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(t.d_nx, tnx[k].data(), sizeof(int) * tnx[k].size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "batched tile tables");
         }
         std::vector<int> cbase(ctx->nscenes);
         int nc = 0;
@@ -740,11 +795,28 @@ hrc_status build_batched_tables(hrc_ctx *ctx) {
                 tick += d.count;
                 bytes += d.bytes;
             }
+        // chunk[c] = the block holding ticket c << shift (c = 0 .. last chunk
+        // + 1, the extra entry bounding the search of the last chunk)
+        const long long nchunk = ((tick + (1LL << kTicketChunkShift) - 1) >> kTicketChunkShift) + 1;
+        std::vector<int> chunk((size_t)nchunk);
+        {
+            size_t b = 0;
+            for (long long c = 0; c < nchunk; ++c) {
+                const long long t = std::min(c << kTicketChunkShift, tick > 0 ? tick - 1 : 0);
+                while (b + 1 < blocks.size() && blocks[b + 1].first <= t) ++b;
+                chunk[(size_t)c] = (int)b;
+            }
+        }
         if (ctx->d_blocks[mode]) cudaFree(ctx->d_blocks[mode]);
+        if (ctx->d_chunk[mode]) cudaFree(ctx->d_chunk[mode]);
         ctx->d_blocks[mode] = nullptr;
+        ctx->d_chunk[mode] = nullptr;
         cudaError_t e = cudaMalloc(&ctx->d_blocks[mode], sizeof(StageBlock) * blocks.size());
         if (e == cudaSuccess)
             e = cudaMemcpy(ctx->d_blocks[mode], blocks.data(), sizeof(StageBlock) * blocks.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_chunk[mode], sizeof(int) * chunk.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ctx->d_chunk[mode], chunk.data(), sizeof(int) * chunk.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batched tables");
         ctx->nblocks[mode] = (int)blocks.size();
         ctx->total[mode] = tick;
@@ -784,6 +856,7 @@ hrc_status run_batched(hrc_ctx *ctx, int mode, const void *e, const void *s, voi
     a.eoff = ctx->d_eoff;
     a.soff = ctx->d_soff;
     a.blocks = ctx->d_blocks[mode];
+    a.chunk = ctx->d_chunk[mode];
     a.nblocks = ctx->nblocks[mode];
     a.total = ctx->total[mode];
     a.ticket = ctx->d_ticket;
@@ -799,15 +872,29 @@ hrc_status run_batched(hrc_ctx *ctx, int mode, const void *e, const void *s, voi
     a.gs = gs;
     const int prec = ctx->prec, C = ctx->C, bpsm = ctx->blocks_per_sm, nc = ctx->ncounters[mode];
     const double bytes = ctx->bbytes[mode];
+    const int nsc = ctx->nscenes;
+    const std::vector<hrc_ctx::TileLaunch> &tl = ctx->tiles[mode];
     auto enqueue = [&](cudaStream_t st, int *n, Recorder *r) {
         cudaError_t err = cudaMemsetAsync(a.counters, 0, sizeof(int) * nc, st);
         if (err == cudaSuccess) err = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned long long), st);
         if (err == cudaSuccess) err = cudaMemsetAsync(a.status, 0, sizeof(int), st);
+        auto tiles = [&](bool before) {
+            for (const auto &t : tl) {
+                if (t.before != before || err != cudaSuccess) continue;
+                r->begin(t.kind == BK_TRACE ? K_TRACE012 : K_ADJ_TRACE, t.pair, t.bytes);
+                err = launch_batched_tiles(a, prec, C, t.kind, t.d_off, t.d_nx, nsc, t.pair, t.total, st);
+                r->end();
+                ++*n;
+            }
+        };
+        tiles(true);
         if (err != cudaSuccess) return err;
         r->begin(K_BATCHED, mode, bytes);
         err = launch_batched(a, prec, C, bpsm, mode == 0 ? 0 : 1, st);
         r->end();
         ++*n;
+        if (err != cudaSuccess) return err;
+        tiles(false);
         return err;
     };
     // the graph key includes the tuning state (blocks per SM, order, test hooks)

@@ -39,40 +39,75 @@ __device__ __forceinline__ int load_acquire(const int *p) {
     return v;
 }
 
-// One item of an adjoint stage (backward launches only).
-template <int P, int C, class IN>
-__device__ __forceinline__ void batched_adjoint_item(const BatchArgs &a, const StageBlock &sb, const Plan &pl,
-                                                     long long j, int vb, long long r0, long long r1, long long eo,
-                                                     long long so, const IN *e, const IN *s, unsigned char *smem) {
-    switch (sb.kind) {
-    case BK_ADJ_SUM:
-        body_adj_sum<P, C, IN>(pl, (const IN *)a.gF + eo, vb, (int)(j / sb.nvb), smem);
-        break;
-    case BK_ADJ_R2:
-        for (long long r = r0; r < r1; ++r) body_adj_R<P, C, 2>(pl, sb.rs, sb.level, r, vb);
-        break;
-    case BK_ADJ_R1:
-        for (long long r = r0; r < r1; ++r) body_adj_R<P, C, 1>(pl, sb.rs, sb.level, r, vb);
-        break;
-    case BK_ADJ_T2:
-        for (long long r = r0; r < r1; ++r) body_adj_T<P, C, 2>(pl, sb.rs, sb.level, r, vb);
-        break;
-    case BK_ADJ_T1:
-        for (long long r = r0; r < r1; ++r) body_adj_T<P, C, 1>(pl, sb.rs, sb.level, r, vb);
-        break;
-    case BK_ADJ_MU:
-        for (long long r = r0; r < r1; ++r) body_adj_merge_up<P, C>(pl, sb.rs, sb.level, r, vb);
-        break;
-    default:   // BK_ADJ_TRACE
-        body_adj_trace<P, C, IN>(pl, e, s, (IN *)a.ge + eo, (IN *)a.gs + so, sb.level, vb, (int)(j / sb.nvb), smem);
-        break;
+// One work item of a row stage: rows r0 .. r1-1 of v-block vb.  Not inlined,
+// so that each stage kind gets its own register allocation and the
+// persistent kernel needs only the largest of them.
+template <int P, int C, int KIND>
+__device__ __noinline__ void item_rows(const Plan *pl, const StageBlock *sb, long long j) {
+    const int vb = (int)(j % sb->nvb);
+    const long long r0 = (j / sb->nvb) * sb->rpi;
+    const long long r1 = r0 + sb->rpi < sb->rows ? r0 + sb->rpi : sb->rows;
+    const int n = sb->level;
+#pragma unroll 1
+    for (long long r = r0; r < r1; ++r) {
+        if constexpr (KIND == BK_MERGE_UP) body_merge_up<P, C>(*pl, sb->rs, n, r, vb);
+        else if constexpr (KIND == BK_MERGE_DOWN2) body_merge_down<P, C, true>(*pl, sb->rs, n, r, vb);
+        else if constexpr (KIND == BK_ADJ_R2) body_adj_R<P, C, 2>(*pl, sb->rs, n, r, vb);
+        else if constexpr (KIND == BK_ADJ_R1) body_adj_R<P, C, 1>(*pl, sb->rs, n, r, vb);
+        else if constexpr (KIND == BK_ADJ_T2) body_adj_T<P, C, 2>(*pl, sb->rs, n, r, vb);
+        else if constexpr (KIND == BK_ADJ_T1) body_adj_T<P, C, 1>(*pl, sb->rs, n, r, vb);
+        else body_adj_merge_up<P, C>(*pl, sb->rs, n, r, vb);
     }
 }
 
-// MODE 0: the forward stages; MODE 1: the stages of the backward (the
-// adjoint, preceded by the forward's level stages when they are recomputed).
+// One tile item: the fluence (forward) or the reverse of the sum (backward).
+template <int P, int C, int KIND, class IN>
+__device__ __noinline__ void item_tile(const Plan *pl, const StageBlock *sb, long long j, IN *io, unsigned char *smem) {
+    const int bx = (int)(j % sb->nvb), by = (int)(j / sb->nvb);
+    if constexpr (KIND == BK_SUM) body_fluence<P, C, IN>(*pl, io, bx, by, smem);
+    else body_adj_sum<P, C, IN>(*pl, (const IN *)io, bx, by, smem);
+}
+
+// The tile steps (direct trace of T_0..T_2, its adjoint) of every scene in
+// one ordinary launch: block b is tile b - off[i] of scene i (off = prefix
+// sums of the scenes' tile counts, nx = tiles along x).  KIND 0: trace;
+// KIND 1: adjoint trace of quadrant pair `pair`.
+template <int P, int C, int KIND>
+__global__ void __launch_bounds__(256, KIND == 1 ? 3 : 2) k_batched_tiles(BatchArgs a, const int *__restrict__ off,
+                                                       const int *__restrict__ nx, int nscenes, int pair) {
+    using IN = typename std::conditional<P == P_FP64, double, float>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int scene_sh;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nscenes - 1;                 // last scene with off <= block
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        scene_sh = lo;
+    }
+    __syncthreads();
+    const int i = scene_sh;
+    const int local = (int)blockIdx.x - off[i];
+    const int bx = local % nx[i], by = local / nx[i];
+    const Plan &pl = a.plans[i];
+    const long long eo = a.eoff[i], so = a.soff[i];
+    const IN *e = (const IN *)a.e + eo;
+    const IN *s = (const IN *)a.s + so;
+    if constexpr (KIND == 0)
+        body_trace012<P, C>(pl, (const float *)e, (const float *)s, (const double *)e, (const double *)s, 15, bx, by,
+                            smem);
+    else
+        body_adj_trace<P, C, IN>(pl, e, s, (IN *)a.ge + eo, (IN *)a.gs + so, pair, bx, by, smem);
+}
+
+// The merge cascade of every scene.  MODE 0: the forward's merge and
+// fluence stages; MODE 1: the backward's (the adjoint merges, preceded by the
+// forward's merge stages when the levels are recomputed).  The tile steps run
+// in k_batched_tiles launches before / after it.
 template <int P, int C, int MODE>
-__global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
+__global__ void __launch_bounds__(256, 5) k_batched(BatchArgs a) {
     using IN = typename std::conditional<P == P_FP64, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long t_sh;
@@ -83,7 +118,10 @@ __global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
             t_sh = stop_sh ? a.total : (long long)atomicAdd(a.ticket, 1ULL);
             int b = -1;
             if (t_sh < a.total) {
-                int lo = 0, hi = a.nblocks - 1;          // last block with first <= t
+                // last block with first <= t, between the index entries
+                // around t (usually one or two blocks apart)
+                const long long c = t_sh >> kTicketChunkShift;
+                int lo = a.chunk[c], hi = a.chunk[c + 1];
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (a.blocks[mid].first <= t_sh) lo = mid;
@@ -112,32 +150,25 @@ __global__ void __launch_bounds__(256, 3) k_batched(BatchArgs a) {
         if (t >= a.total || stop_sh) break;
         const StageBlock &sb = a.blocks[b_sh];
         const long long j = t - sb.first;
-        const Plan &pl = a.plans[sb.scene];
-        const long long eo = a.eoff[sb.scene], so = a.soff[sb.scene];
-        const IN *e = (const IN *)a.e + eo;
-        const IN *s = (const IN *)a.s + so;
-        // row kinds: rows r0 .. r1-1 of v-block vb; tile kinds: one tile
-        const int vb = (int)(j % sb.nvb);
-        const long long r0 = (j / sb.nvb) * sb.rpi;
-        const long long r1 = r0 + sb.rpi < sb.rows ? r0 + sb.rpi : sb.rows;
-        if (MODE == 0 || sb.kind <= BK_MERGE_DOWN2) {   // forward stages (mode 2 recomputes them)
-            switch (sb.kind) {
-            case BK_TRACE:
-                body_trace012<P, C>(pl, (const float *)e, (const float *)s, (const double *)e, (const double *)s, 15,
-                                    vb, (int)(j / sb.nvb), smem);
-                break;
-            case BK_MERGE_UP:
-                for (long long r = r0; r < r1; ++r) body_merge_up<P, C>(pl, sb.rs, sb.level, r, vb);
-                break;
-            case BK_MERGE_DOWN2:
-                for (long long r = r0; r < r1; ++r) body_merge_down<P, C, true>(pl, sb.rs, sb.level, r, vb);
-                break;
-            default:   // BK_SUM (with the level-0 merge down); forward launches only
-                if constexpr (MODE == 0) body_fluence<P, C, IN>(pl, (IN *)a.F + eo, vb, (int)(j / sb.nvb), smem);
-                break;
+        const Plan *pl = a.plans + sb.scene;
+        const long long eo = a.eoff[sb.scene];
+        switch (sb.kind) {
+        case BK_MERGE_UP: item_rows<P, C, BK_MERGE_UP>(pl, &sb, j); break;
+        case BK_MERGE_DOWN2: item_rows<P, C, BK_MERGE_DOWN2>(pl, &sb, j); break;
+        default:
+            if constexpr (MODE == 0) {       // BK_SUM (with the level-0 merge down)
+                item_tile<P, C, BK_SUM, IN>(pl, &sb, j, (IN *)a.F + eo, smem);
+            } else {
+                switch (sb.kind) {
+                case BK_ADJ_SUM: item_tile<P, C, BK_ADJ_SUM, IN>(pl, &sb, j, (IN *)a.gF + eo, smem); break;
+                case BK_ADJ_R2: item_rows<P, C, BK_ADJ_R2>(pl, &sb, j); break;
+                case BK_ADJ_R1: item_rows<P, C, BK_ADJ_R1>(pl, &sb, j); break;
+                case BK_ADJ_T2: item_rows<P, C, BK_ADJ_T2>(pl, &sb, j); break;
+                case BK_ADJ_T1: item_rows<P, C, BK_ADJ_T1>(pl, &sb, j); break;
+                default: item_rows<P, C, BK_ADJ_MU>(pl, &sb, j); break;
+                }
             }
-        } else if constexpr (MODE == 1) {
-            batched_adjoint_item<P, C, IN>(a, sb, pl, j, vb, r0, r1, eo, so, e, s, smem);
+            break;
         }
         __syncthreads();
         if (threadIdx.x == 0 && sb.own != a.withhold) {
@@ -293,17 +324,9 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
     }
 }
 
-// Dynamic shared memory of a launch: the forward needs the trace tile, the
-// backward the adjoint-trace tile and the transposed dL/dF tile.
-template <int P, int C> size_t batched_smem(int mode) {
-    using A = typename Prec<P>::A;
-    const size_t tr = TraceTile<A, C>::bytes();
-    if (mode == 0) return tr > fluence_smem<P, C>() ? tr : fluence_smem<P, C>();
-    size_t m = adj_trace_smem<A, C>();
-    const size_t sum_tile = sizeof(A) * C * 32 * 33;
-    m = m > sum_tile ? m : sum_tile;
-    return m > tr ? m : tr;   // the recomputing backward runs the trace stage too
-}
+// Dynamic shared memory of the persistent launch: the fluence tile (forward)
+// or the transposed dL/dF tile (backward), both C x 32 x 33 words.
+template <int P, int C> size_t batched_smem(int) { return fluence_smem<P, C>(); }
 
 template <int P, int C, int MODE>
 static cudaError_t batched_launch(const BatchArgs &a, int blocks_per_sm, cudaStream_t st) {
@@ -344,6 +367,47 @@ cudaError_t launch_batched(const BatchArgs &a, int prec, int C, int blocks_per_s
     case P_FP32: return batched_prec<P_FP32>(a, C, blocks_per_sm, mode, st);
     case P_FP16: return batched_prec<P_FP16>(a, C, blocks_per_sm, mode, st);
     case P_BF16: return batched_prec<P_BF16>(a, C, blocks_per_sm, mode, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int P, int C, int KIND>
+static cudaError_t tiles_launch(const BatchArgs &a, const int *off, const int *nx, int nscenes, int pair, int total,
+                                cudaStream_t st) {
+    using A = typename Prec<P>::A;
+    const size_t smem = KIND == 0 ? TraceTile<A, C>::bytes() : adj_trace_smem<A, C>();
+    cudaError_t e = cudaFuncSetAttribute(k_batched_tiles<P, C, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_batched_tiles<P, C, KIND><<<(unsigned)total, 256, smem, st>>>(a, off, nx, nscenes, pair);
+    return cudaGetLastError();
+}
+
+template <int P, int C>
+static cudaError_t tiles_impl(const BatchArgs &a, int kind, const int *off, const int *nx, int nscenes, int pair,
+                              int total, cudaStream_t st) {
+    return kind == BK_TRACE ? tiles_launch<P, C, 0>(a, off, nx, nscenes, pair, total, st)
+                            : tiles_launch<P, C, 1>(a, off, nx, nscenes, pair, total, st);
+}
+
+template <int P>
+static cudaError_t tiles_prec(const BatchArgs &a, int C, int kind, const int *off, const int *nx, int nscenes,
+                              int pair, int total, cudaStream_t st) {
+    switch (C) {
+    case 1: return tiles_impl<P, 1>(a, kind, off, nx, nscenes, pair, total, st);
+    case 2: return tiles_impl<P, 2>(a, kind, off, nx, nscenes, pair, total, st);
+    case 3: return tiles_impl<P, 3>(a, kind, off, nx, nscenes, pair, total, st);
+    default: return tiles_impl<P, 4>(a, kind, off, nx, nscenes, pair, total, st);
+    }
+}
+
+cudaError_t launch_batched_tiles(const BatchArgs &a, int prec, int C, int kind, const int *off, const int *nx,
+                                 int nscenes, int pair, int total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    switch (prec) {
+    case P_FP32: return tiles_prec<P_FP32>(a, C, kind, off, nx, nscenes, pair, total, st);
+    case P_FP16: return tiles_prec<P_FP16>(a, C, kind, off, nx, nscenes, pair, total, st);
+    case P_BF16: return tiles_prec<P_BF16>(a, C, kind, off, nx, nscenes, pair, total, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -74,12 +74,16 @@ struct StageBlock {
     RowSplit rs;
 };
 
+constexpr int kTicketChunkShift = 6;   // tickets per entry of the ticket -> block index: 64
+
 struct BatchArgs {
     const Plan *plans;
     const long long *eoff, *soff;     // per-scene element offsets of [C][H][W] / [H][W] blocks
     const StageBlock *blocks;
     int nblocks;
     long long total;                  // tickets
+    const int *chunk;                 // chunk[c]: the block holding ticket c << kTicketChunkShift
+    int pad_;
     unsigned long long *ticket;
     int *counters;
     int *status;
@@ -103,6 +107,11 @@ struct StageDesc {
 };
 void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out);
 cudaError_t launch_batched(const BatchArgs &a, int prec, int C, int blocks_per_sm, int mode, cudaStream_t st);
+// The tile steps of every scene (kind BK_TRACE, or BK_ADJ_TRACE of quadrant
+// pair `pair`) in one launch of `total` blocks (off / nx: per-scene prefix
+// sums of tile counts and tiles along x, device arrays).
+cudaError_t launch_batched_tiles(const BatchArgs &a, int prec, int C, int kind, const int *off, const int *nx,
+                                 int nscenes, int pair, int total, cudaStream_t st);
 
 // Host-side plan and table builders (hrc_runtime.cu).
 size_t align_up(size_t x, size_t a);
