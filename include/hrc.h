@@ -215,6 +215,16 @@ hrc_status hrc_batched_sync(hrc_ctx *ctx);
  * scene first).  Results are identical for every setting. */
 hrc_status hrc_batched_tune(hrc_ctx *ctx, int blocks_per_sm, int order);
 
+/* Schedule of a batched pass, both captured and replayed as one CUDA graph:
+ * 0 (default) = the tile steps of all scenes as multi-scene launches around
+ * one persistent launch that runs every scene's merge cascade from a
+ * ticket queue with bounded dependency waits; 1 = every scene's own
+ * per-level launch sequence (as a single-scene pass), the scenes spread
+ * largest first over 8 streams forked from and joined to the caller's
+ * stream, so that kernels of different scenes overlap.  Results are
+ * identical for both. */
+hrc_status hrc_batched_schedule(hrc_ctx *ctx, int schedule);
+
 /* Test hook for the bounded waits: `withhold_counter` >= 0 makes that stage
  * counter never publish, so the stages after it time out after
  * `spin_limit` polls (about 128 ns each; <= 0 restores the default, about

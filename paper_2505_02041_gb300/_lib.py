@@ -43,6 +43,7 @@ SIGNATURES = [
     ("hrc_fluence_backward_batched", _i, [_vp, _vp, _vp, _vp]),
     ("hrc_batched_sync", _i, [_vp]),
     ("hrc_batched_tune", _i, [_vp, _i, _i]),
+    ("hrc_batched_schedule", _i, [_vp, _i]),
     ("hrc_batched_debug", _i, [_vp, _i, _ll]),
     ("hrc_fluence_noalloc", _i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
     ("hrc_copy_level", _i, [_vp, _i, _i, _i, _vp, ctypes.POINTER(_ll)]),
@@ -199,6 +200,10 @@ def hrc_fluence_backward_batched(ctx, grad_F, grad_emission, grad_sigma_t):
 
 def hrc_batched_sync(ctx):
     check(load().hrc_batched_sync(ctx), ctx)
+
+
+def hrc_batched_schedule(ctx, schedule: int):
+    check(load().hrc_batched_schedule(ctx, schedule), ctx)
 
 
 def hrc_batched_tune(ctx, blocks_per_sm: int, order: int):

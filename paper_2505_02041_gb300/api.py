@@ -245,29 +245,32 @@ class BatchedHRC:
     def set_backward_recompute(self, on: bool) -> None:
         _lib.hrc_set_backward_recompute(self.ctx, on)
 
-    def tune(self, blocks_per_sm: int = 0, order: int = 0):
+    def tune(self, blocks_per_sm: int = 0, order: int = 0, schedule: int = 0):
+        """schedule 0: persistent launch (blocks per SM, ticket order apply);
+        schedule 1: per-scene launch chains on parallel graph branches."""
         _lib.hrc_batched_tune(self.ctx, blocks_per_sm, order)
+        _lib.hrc_batched_schedule(self.ctx, schedule)
 
     def autotune(self, e_packed, s_packed, reps: int = 3):
-        """Time each (blocks per SM, ticket order) candidate on these inputs
-        and keep the fastest; returns {candidate: ms}."""
+        """Time each (schedule, blocks per SM, ticket order) candidate on these
+        inputs and keep the fastest; returns {candidate: ms}."""
         res = {}
         out = torch.empty_like(e_packed)
-        for bpsm in (0, 1, 2):
-            for order in (0, 1):
-                self.tune(bpsm, order)
+        for cand in [(0, bpsm, order) for bpsm in (0, 1, 2) for order in (0, 1)] + [(1, 0, 0)]:
+            sched, bpsm, order = cand
+            self.tune(bpsm, order, sched)
+            self.forward(e_packed, s_packed, out)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
                 self.forward(e_packed, s_packed, out)
-                torch.cuda.synchronize()
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record()
-                for _ in range(reps):
-                    self.forward(e_packed, s_packed, out)
-                b.record()
-                b.synchronize()
-                res[(bpsm, order)] = a.elapsed_time(b) / reps
-        best = min(res, key=res.get)
-        self.tune(*best)
+            b.record()
+            b.synchronize()
+            res[cand] = a.elapsed_time(b) / reps
+        sched, bpsm, order = min(res, key=res.get)
+        self.tune(bpsm, order, sched)
         return res
 
     def close(self):

@@ -234,6 +234,13 @@ struct hrc_ctx {
     long long spin_limit = 1LL << 24;   // ~2 s of 128 ns polls
     int blocks_per_sm = 0;              // 0: as many as fit
     int order = 0;                      // 0: scenes in input order per stage, 1: largest first
+    // schedule 1: one graph whose branches are the scenes' per-level launch
+    // chains, spread over kAux streams (forked from and joined to the pass)
+    int bsched = 0;
+    static constexpr int kAux = 8;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kAux] = {};
+    std::vector<int> by_size;           // scene indices, largest first
 };
 
 namespace {
@@ -427,6 +434,11 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->d_plans);
     cudaFree(ctx->d_eoff);
     cudaFree(ctx->d_soff);
+    for (int k = 0; k < hrc_ctx::kAux; ++k) {
+        if (ctx->aux[k]) cudaStreamDestroy(ctx->aux[k]);
+        if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     for (int m = 0; m < 3; ++m) {
         cudaFree(ctx->d_blocks[m]);
         cudaFree(ctx->d_chunk[m]);
@@ -849,8 +861,42 @@ hrc_status build_batched_plans(hrc_ctx *ctx, int prec) {
     return build_batched_tables(ctx);
 }
 
+// Schedule 1: every scene's own launch sequence (as a single-scene pass),
+// scenes largest first, round-robin over the auxiliary streams forked from
+// and joined back to the pass's stream; captured, the graph has one
+// independent branch per stream, so kernels of different scenes overlap.
+hrc_status run_batched_chains(hrc_ctx *ctx, int mode, const void *e, const void *s, void *F, const void *gF,
+                              void *ge, void *gs, const char *where) {
+    auto enqueue = [&](cudaStream_t st, int *n, Recorder *) {
+        Recorder off;   // per-launch timing is not recorded across streams
+        cudaError_t err = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
+        if (err == cudaSuccess) err = cudaEventRecord(ctx->ev_fork, st);
+        for (int k = 0; k < hrc_ctx::kAux && err == cudaSuccess; ++k) err = cudaStreamWaitEvent(ctx->aux[k], ctx->ev_fork, 0);
+        for (int idx = 0; idx < ctx->nscenes && err == cudaSuccess; ++idx) {
+            const int i = ctx->by_size[idx];
+            cudaStream_t as = ctx->aux[idx % hrc_ctx::kAux];
+            const Plan &pl = ctx->bplans[i];
+            const float *ei = (const float *)e + ctx->eoff[i], *si = (const float *)s + ctx->soff[i];
+            if (mode == 0)
+                err = launch_forward(pl, ctx->rt, ei, si, (float *)F + ctx->eoff[i], as, n, &off);
+            else
+                err = launch_backward(pl, ctx->rt, ei, si, (const float *)gF + ctx->eoff[i], (float *)ge + ctx->eoff[i],
+                                      (float *)gs + ctx->soff[i], mode == 2, as, n, &off);
+        }
+        for (int k = 0; k < hrc_ctx::kAux && err == cudaSuccess; ++k) {
+            err = cudaEventRecord(ctx->ev_join[k], ctx->aux[k]);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(st, ctx->ev_join[k], 0);
+        }
+        return err;
+    };
+    const void *k3 = (const void *)(intptr_t)(1 << 20);
+    return run_pass(ctx, 8 + mode, mode == 0 ? e : gF, mode == 0 ? s : ge, mode == 0 ? F : gs, k3, nullptr, enqueue,
+                    where);
+}
+
 hrc_status run_batched(hrc_ctx *ctx, int mode, const void *e, const void *s, void *F, const void *gF, void *ge,
                        void *gs, const char *where) {
+    if (ctx->bsched == 1) return run_batched_chains(ctx, mode, e, s, F, gF, ge, gs, where);
     BatchArgs a;
     a.plans = ctx->d_plans;
     a.eoff = ctx->d_eoff;
@@ -931,9 +977,18 @@ hrc_status hrc_create_batched_prec(int n, const int *W, const int *H, int channe
     ctx->C = channels;
     ctx->cascades = cascades;
     ctx->rt = make_ray_table();
+    ctx->by_size.resize(n);
+    for (int i = 0; i < n; ++i) ctx->by_size[i] = i;
+    std::stable_sort(ctx->by_size.begin(), ctx->by_size.end(),
+                     [&](int a, int b) { return (long long)W[a] * H[a] > (long long)W[b] * H[b]; });
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = prepare_device_once();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < hrc_ctx::kAux && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&ctx->aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e != cudaSuccess) { delete ctx; return fail(nullptr, HRC_ECUDA, std::string("hrc_create_batched: ") + cudaGetErrorString(e)); }
     size_t bytes = 0;
     ctx->eoff.assign(n + 1, 0);
@@ -1029,6 +1084,13 @@ hrc_status hrc_batched_debug(hrc_ctx *ctx, int withhold_counter, long long spin_
     if (!ctx || !ctx->batched) return HRC_EINVAL;
     ctx->withhold = withhold_counter;
     ctx->spin_limit = spin_limit > 0 ? spin_limit : (1LL << 24);
+    return HRC_OK;
+}
+
+hrc_status hrc_batched_schedule(hrc_ctx *ctx, int schedule) {
+    if (!ctx || !ctx->batched) return HRC_EINVAL;
+    if (schedule != 0 && schedule != 1) return fail(ctx, HRC_EINVAL, "hrc_batched_schedule: 0 or 1");
+    ctx->bsched = schedule;
     return HRC_OK;
 }
 

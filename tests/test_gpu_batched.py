@@ -115,3 +115,27 @@ def test_batched_withheld_dependency_times_out_and_recovers():
     F = b.forward(e, s)
     b.sync()
     assert torch.equal(F, ref)
+
+
+def test_batched_chain_schedule_matches_persistent():
+    """Schedule 1 (per-scene launch chains on parallel graph branches) gives
+    the persistent schedule's fluence and gradients, in both backward modes."""
+    require_gpu()
+    from paper_2505_02041_gb300 import BatchedHRC
+    C = 2
+    es, ss = _scenes(C, 30)
+    b = BatchedHRC(SIZES, C)
+    e, s = b.pack(es, ss)
+    gF = torch.randn(e.numel(), device="cuda")
+    F0 = b.forward(e, s).clone()
+    ge0, gs0 = (t.clone() for t in b.backward(gF))
+    b.sync()
+    b.tune(0, 0, 1)
+    for rc in (False, True):
+        b.set_backward_recompute(rc)
+        F1 = b.forward(e, s)
+        ge1, gs1 = b.backward(gF)
+        b.sync()
+        assert err_max(F1.cpu().numpy(), F0.cpu().numpy()) <= 1e-5
+        assert err_max(ge1.cpu().numpy(), ge0.cpu().numpy()) <= 1e-5
+        assert err_max(gs1.cpu().numpy(), gs0.cpu().numpy()) <= 1e-5
