@@ -256,6 +256,75 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[l][c] = A(0);
     const A Ap = arc<P>(pl, n + 1, 2 * ip + 1), Am = arc<P>(pl, n + 1, 2 * ip);
+    if constexpr (E == 4) {
+        // four consecutive v (v a multiple of 4, n >= 1): one 4-wide access
+        // per plane and row; a far run whose even offset is not a multiple
+        // of 4, or that crosses the grid edge, is read as two pairs
+        auto loadR4 = [&](const RLevel<P, C> &R1, int xr, int j, int c, int vq, A (&r)[4]) {
+            if ((vq & 3) == 0 && vq >= 0 && vq + 3 < g.V) {
+                R1.load4(xr, j, c, vq, r);
+                return;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int vp = vq + 2 * h;
+                if (vp >= 0 && vp < g.V) {
+                    R1.load2(xr, j, c, vp, r[2 * h], r[2 * h + 1]);
+                    if (vp + 1 >= g.V) r[2 * h + 1] = A(0);
+                } else {
+                    r[2 * h] = r[2 * h + 1] = A(0);
+                }
+            }
+        };
+        if (x & 1) {   // Eq. 14
+            TLevel<P, C> Tn(pl, q, n);
+            const int xq = (x + 1) >> 1;
+            const bool rq_ok = !top && xq < g.Un[n + 1];
+            RLevel<P, C> R1(pl, q, rq_ok ? n + 1 : n);
+#pragma unroll
+            for (int sg = 0; sg < 2; ++sg) {
+                const int kk = sg == 0 ? ip + 1 : ip;
+                const int j = sg == 0 ? 2 * ip + 1 : 2 * ip;
+                const A Aj = sg == 0 ? Ap : Am;
+                Iv<P, C> t[4];
+                Tn.load4(x, kk, v, t);
+                const int vq = v + 2 * kk - s;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    A r[4] = {A(0), A(0), A(0), A(0)};
+                    if (rq_ok) loadR4(R1, xq, j, c, vq, r);
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) acc[l][c] += fma(Aj, t[l].L[c], t[l].trans() * r[l]);
+                }
+            }
+        } else {       // Eqs. 15-17
+            TLevel<P, C> T1(pl, q, n + 1);
+            const int x2 = x >> 1;
+            const bool r1_ok = !top && x2 + 1 < g.Un[n + 1];
+            RLevel<P, C> R1(pl, q, top ? n : n + 1);
+#pragma unroll
+            for (int sg = 0; sg < 2; ++sg) {
+                const int kk = sg == 0 ? 2 * ip + 2 : 2 * ip;
+                const int j = sg == 0 ? 2 * ip + 1 : 2 * ip;
+                const A Aj = sg == 0 ? Ap : Am;
+                Iv<P, C> t[4];
+                T1.load4(x2, kk, v, t);
+                const int vq = v + 2 * kk - 2 * s;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    A r0[4] = {A(0), A(0), A(0), A(0)}, r1[4] = {A(0), A(0), A(0), A(0)};
+                    if (!top) {
+                        R1.load4(x2, j, c, v, r0);
+                        if (r1_ok) loadR4(R1, x2 + 1, j, c, vq, r1);
+                    }
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+                        acc[l][c] += A(0.5) * (r0[l] + fma(Aj, t[l].L[c], t[l].trans() * r1[l]));
+                }
+            }
+        }
+        return;
+    }
     // R_{n+1}(xr, j, vq .. vq+E-1), zero outside [0, V)
     auto loadR = [&](const RLevel<P, C> &R1, int xr, int j, int c, int vq, A (&r)[E]) {
         if (PAIR) {
@@ -329,6 +398,28 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
                     acc[l][c] += A(0.5) * (r0[l] + fma(Aj, t[l].L[c], t[l].trans() * r1[l]));
             }
         }
+    }
+}
+
+// One row segment of R_n with four consecutive v per thread (n >= 1).
+template <int P, int C>
+__device__ __forceinline__ void body_merge_down4(const Plan &pl, const RowSplit &rs, int n, long long bx, int by) {
+    using A = typename Prec<P>::A;
+    int local;
+    const int q = find_quadrant(rs, bx, local);
+    const QuadGeom &g = pl.q[q];
+    const int v = 4 * (by * blockDim.x + threadIdx.x);
+    if (v >= g.V) return;
+    const int I = 1 << n;
+    local += I;
+    const int x = local >> n, ip = local & (I - 1);
+    A acc[4][C];
+    merge_down_entry<P, C, 4>(pl, q, n, x, ip, v, acc);
+    RLevel<P, C> Rn(pl, q, n);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        A o[4] = {acc[0][c], acc[1][c], acc[2][c], acc[3][c]};
+        Rn.store4(x, ip, c, v, o);
     }
 }
 

@@ -203,6 +203,48 @@ __device__ __forceinline__ void st2(__nv_bfloat16 *p, float x, float y) {
     *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(x, y);
 }
 
+// 4-wide loads / stores of four consecutive v (the first a multiple of 4,
+// so every quadruple is 4-element aligned).
+__device__ __forceinline__ void ld4(const float *p, float (&r)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p); r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&r)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const __half *p, float (&r)[4]) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const __half2 a = *reinterpret_cast<const __half2 *>(&u.x), b = *reinterpret_cast<const __half2 *>(&u.y);
+    r[0] = __low2float(a); r[1] = __high2float(a); r[2] = __low2float(b); r[3] = __high2float(b);
+}
+__device__ __forceinline__ void ld4(const __nv_bfloat16 *p, float (&r)[4]) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&u.x),
+                         b = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
+    r[0] = __low2float(a); r[1] = __high2float(a); r[2] = __low2float(b); r[3] = __high2float(b);
+}
+__device__ __forceinline__ void st4(float *p, const float (&r)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&r)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(r[2], r[3]);
+}
+__device__ __forceinline__ void st4(__half *p, const float (&r)[4]) {
+    const __half2 a = __floats2half2_rn(r[0], r[1]), b = __floats2half2_rn(r[2], r[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned *>(&a);
+    u.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+__device__ __forceinline__ void st4(__nv_bfloat16 *p, const float (&r)[4]) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(r[0], r[1]), b = __floats2bfloat162_rn(r[2], r[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned *>(&a);
+    u.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+
 // ---------------------------------------------------------------------------
 // Level addressing
 // ---------------------------------------------------------------------------
@@ -255,6 +297,21 @@ template <int P, int C> struct TLevel {
 #pragma unroll
         for (int c = 0; c < C; ++c) st2(reinterpret_cast<SL *>(g) + (long long)c * Vs + v, a.L[c], b.L[c]);
         st2(reinterpret_cast<ST *>(g + (long long)C * Vs * sizeof(SL)) + v, a.t, b.t);
+    }    // entries v .. v+3 (v a multiple of 4; v + 3 < Vs)
+    __device__ __forceinline__ void load4(int x, int k, int v, Iv<P, C> (&r)[4]) const {
+        using A = typename Prec<P>::A;
+        const char *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            A t[4];
+            ld4(reinterpret_cast<const SL *>(g) + (long long)c * Vs + v, t);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) r[l].L[c] = t[l];
+        }
+        A t[4];
+        ld4(reinterpret_cast<const ST *>(g + (long long)C * Vs * sizeof(SL)) + v, t);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) r[l].t = t[l];
     }
 };
 
@@ -275,6 +332,10 @@ template <int P, int C> struct RLevel {
     __device__ __forceinline__ void store(int x, int i, int c, int v, A val) const { base[idx(x, i, c, v)] = from_acc<SL>(val); }
     __device__ __forceinline__ void load2(int x, int i, int c, int v, A &a, A &b) const { ld2(base + idx(x, i, c, v), a, b); }
     __device__ __forceinline__ void store2(int x, int i, int c, int v, A a, A b) const { st2(base + idx(x, i, c, v), a, b); }
+    __device__ __forceinline__ void load4(int x, int i, int c, int v, A (&r)[4]) const { ld4(base + idx(x, i, c, v), r); }
+    __device__ __forceinline__ void store4(int x, int i, int c, int v, const A (&r)[4]) const {
+        st4(base + idx(x, i, c, v), r);
+    }
 };
 
 // Adjoint levels: dLoss/dT_n entries (C radiance components, then the

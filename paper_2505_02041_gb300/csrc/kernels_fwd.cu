@@ -36,6 +36,14 @@ __global__ void __launch_bounds__(512) k_merge_down(Plan pl, RowSplit rs, int n)
     body_merge_down<P, C, PAIR>(pl, rs, n, row, vb);
 }
 
+template <int P, int C>
+__global__ void __launch_bounds__(512) k_merge_down4(Plan pl, RowSplit rs, int n) {
+    long long row;
+    int vb;
+    row_block(pl, row, vb);
+    body_merge_down4<P, C>(pl, rs, n, row, vb);
+}
+
 template <int P, int C, class OUT>
 __global__ void __launch_bounds__(128) k_fluence(Plan pl, OUT *__restrict__ F) {
     __shared__ __align__(16) unsigned char smem[fluence_smem<P, C>()];
@@ -168,7 +176,7 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             }
             const int mt = pl.mthreads;
             rec->begin(K_MERGE_DOWN, n, by);
-            if (n >= 1) k_merge_down<P, C, true><<<row_grid(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
+            if (n >= 1) k_merge_down4<P, C><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
             else {
                 const int ts = 2 * mt > 512 ? 512 : 2 * mt;   // single v per thread at level 0
                 k_merge_down<P, C, false><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
