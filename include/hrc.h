@@ -84,7 +84,8 @@ hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule);
 /* Launch configuration of a single-scene context (tuning knobs; results are
  * identical for every setting):
  *   schedule: as hrc_set_schedule (0 or 1);
- *   groups:   v-pairs per thread in the merge-up kernel (1 or 2);
+ *   groups:   v per thread in the merge-up kernel: 1 = a pair, 2 = two pairs
+ *             blockDim apart, 4 = four consecutive v;
  *   threads:  threads per block of the merge and adjoint-merge kernels
  *             (64, 128, 256 or 512);
  *   vmajor:   grid order of those kernels: 0 = rows in gridDim.x, v-blocks

@@ -240,6 +240,52 @@ __device__ __forceinline__ void body_merge_up(const Plan &pl, const RowSplit &rs
     }
 }
 
+// As body_merge_up with four consecutive v per thread (v a multiple of 4):
+// one 4-wide access per plane; a far run whose offset is not a multiple of
+// 4, or that crosses the grid edge, is read as two pairs.
+template <int P, int C>
+__device__ __forceinline__ void body_merge_up4(const Plan &pl, const RowSplit &rs, int n, long long bx, int by) {
+    int local;
+    const int q = find_quadrant(rs, bx, local);
+    const QuadGeom &g = pl.q[q];
+    const int v = 4 * (by * blockDim.x + threadIdx.x);
+    if (v >= g.V) return;
+    const int K = (1 << n) + 1;
+    local += K;
+    const int x = local / K, k = local - x * K;
+    const int m = n - 1, sm = 1 << m;
+    TLevel<P, C> Tm(pl, q, m), Tn(pl, q, n);
+    const int xn = 2 * x, xf = 2 * x + 1;
+    const bool far_ok = xf < g.Un[m];
+    Iv<P, C> out[4];
+    if ((k & 1) == 0) {                             // Eq. 18
+        const int kk = k >> 1;
+        Iv<P, C> nr[4], fr[4];
+        Tm.load4(xn, kk, v, nr);
+        if (far_ok) Tm.load4_masked(xf, kk, v + 2 * kk - sm, g.V, fr);
+        else
+#pragma unroll
+            for (int l = 0; l < 4; ++l) fr[l] = Iv<P, C>::vacuum();
+#pragma unroll
+        for (int l = 0; l < 4; ++l) out[l] = merge<P, C>(nr[l], fr[l]);
+    } else {                                        // Eqs. 19-20
+        const int kp = (k + 1) >> 1, km = (k - 1) >> 1;
+        Iv<P, C> np[4], nm[4], fp[4], fm[4];
+        Tm.load4(xn, kp, v, np);
+        Tm.load4(xn, km, v, nm);
+        if (far_ok) {
+            Tm.load4_masked(xf, km, v + 2 * kp - sm, g.V, fp);
+            Tm.load4_masked(xf, kp, v + 2 * km - sm, g.V, fm);
+        } else {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) fp[l] = fm[l] = Iv<P, C>::vacuum();
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) out[l] = blend<P, C>(merge<P, C>(nm[l], fm[l]), merge<P, C>(np[l], fp[l]));
+    }
+    Tn.store4(x, k, v, out);
+}
+
 // R_n(p, i) = F_+ + F_-, p = (x 2^n, v), i = ip + 1/2, j_+ = 2ip+1, j_- = 2ip,
 // for v .. v+E-1 of column x >= 1 of frame q (E = 2: all neighbour offsets
 // even, n >= 1).

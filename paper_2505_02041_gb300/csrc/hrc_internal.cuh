@@ -297,7 +297,28 @@ template <int P, int C> struct TLevel {
 #pragma unroll
         for (int c = 0; c < C; ++c) st2(reinterpret_cast<SL *>(g) + (long long)c * Vs + v, a.L[c], b.L[c]);
         st2(reinterpret_cast<ST *>(g + (long long)C * Vs * sizeof(SL)) + v, a.t, b.t);
-    }    // entries v .. v+3 (v a multiple of 4; v + 3 < Vs)
+    }    __device__ __forceinline__ void store4(int x, int k, int v, const Iv<P, C> (&r)[4]) const {
+        using A = typename Prec<P>::A;
+        char *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const A t[4] = {r[0].L[c], r[1].L[c], r[2].L[c], r[3].L[c]};
+            st4(reinterpret_cast<SL *>(g) + (long long)c * Vs + v, t);
+        }
+        const A t[4] = {r[0].t, r[1].t, r[2].t, r[3].t};
+        st4(reinterpret_cast<ST *>(g + (long long)C * Vs * sizeof(SL)) + v, t);
+    }
+    // entries v .. v+3 with vacuum outside [0, V) (v even): one 4-wide load
+    // when v is a multiple of 4 and the run is inside, else two pairs
+    __device__ __forceinline__ void load4_masked(int x, int k, int v, int V, Iv<P, C> (&r)[4]) const {
+        if ((v & 3) == 0 && v >= 0 && v + 3 < V) {
+            load4(x, k, v, r);
+            return;
+        }
+        load2_masked(x, k, v, V, r[0], r[1]);
+        load2_masked(x, k, v + 2, V, r[2], r[3]);
+    }
+    // entries v .. v+3 (v a multiple of 4; v + 3 < Vs)
     __device__ __forceinline__ void load4(int x, int k, int v, Iv<P, C> (&r)[4]) const {
         using A = typename Prec<P>::A;
         const char *g = row(x, k);

@@ -468,7 +468,7 @@ hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule) {
 
 namespace {
 bool config_valid(const hrc_ctx *ctx, const hrc_launch_config &c) {
-    return (c.schedule == 0 || c.schedule == 1) && (c.groups == 1 || c.groups == 2) &&
+    return (c.schedule == 0 || c.schedule == 1) && (c.groups == 1 || c.groups == 2 || c.groups == 4) &&
            (c.threads == 64 || c.threads == 128 || c.threads == 256 || c.threads == 512) &&
            (c.vmajor == 0 || c.vmajor == 1) &&
            !(c.vmajor && 4LL * (ctx->W + ctx->H) > 65535);
@@ -527,8 +527,9 @@ hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
     const bool timing = ctx->rec.on;
     ctx->rec.on = false;
     static const int kThreads[4] = {64, 128, 256, 512};
-    for (int cand = 0; cand < 2 * 2 * 4 * 2 && st == HRC_OK; ++cand) {
-        const hrc_launch_config c{cand & 1, 1 + ((cand >> 1) & 1), kThreads[(cand >> 2) & 3], (cand >> 4) & 1};
+    static const int kGroups[3] = {1, 2, 4};
+    for (int cand = 0; cand < 2 * 3 * 4 * 2 && st == HRC_OK; ++cand) {
+        const hrc_launch_config c{cand & 1, kGroups[(cand >> 1) % 3], kThreads[(cand / 6) & 3], (cand / 24) & 1};
         if (!config_valid(ctx, c)) continue;
         apply_config(ctx, c);
         for (int r = 0; r < 2 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);

@@ -37,6 +37,14 @@ __global__ void __launch_bounds__(512) k_merge_down(Plan pl, RowSplit rs, int n)
 }
 
 template <int P, int C>
+__global__ void __launch_bounds__(512) k_merge_up4(Plan pl, RowSplit rs, int n) {
+    long long row;
+    int vb;
+    row_block(pl, row, vb);
+    body_merge_up4<P, C>(pl, rs, n, row, vb);
+}
+
+template <int P, int C>
 __global__ void __launch_bounds__(512) k_merge_down4(Plan pl, RowSplit rs, int n) {
     long long row;
     int vb;
@@ -156,7 +164,10 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                 if ((qsel < 0 || q == qsel) && n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
             const int mt = pl.mthreads;
             rec->begin(K_MERGE_UP, n, by);
-            if (pl.mgroups == 2) k_merge_up<P, C, 2><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
+            // groups: 1 = a pair of v per thread, 2 = two pairs blockDim apart,
+            // 4 = four consecutive v
+            if (pl.mgroups == 4) k_merge_up4<P, C><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
+            else if (pl.mgroups == 2) k_merge_up<P, C, 2><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
             else k_merge_up<P, C, 1><<<row_grid(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
             rec->end();
             ++*launches;

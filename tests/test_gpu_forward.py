@@ -144,7 +144,7 @@ def test_launch_configurations_give_the_same_results():
     ed, sd, gd = to_dev(e), to_dev(s), to_dev(gF)
     ref = None
     for sched in (0, 1):
-        for groups in (1, 2):
+        for groups in (1, 2, 4):
             for threads in (64, 128, 256, 512):
                 for vmajor in (0, 1):
                     h.set_launch_config(sched, groups, threads, vmajor)
