@@ -125,6 +125,22 @@ __device__ __forceinline__ void body_adj_R(const Plan &pl, const RowSplitB &rs, 
     // terms at v = w - sh (sh even when E = 2): weight * T * gR_n(xp, ip, v)
     auto term = [&](int xp, int sh, A wgt, const TLevel<P, C> *T, int xt, int kt) {
         const int v = w - sh;
+        if (E == 2 && v >= 0 && v + 1 < g.V) {   // both inside: 2-wide loads
+            A t0 = wgt, t1 = wgt;
+            if (T) {
+                T->load_t2(xt, kt, v, t0, t1);
+                t0 *= wgt;
+                t1 *= wgt;
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                A g0, g1;
+                gRn.load2(xp, ip, c, v, g0, g1);
+                acc[0][c] = fma(t0, g0, acc[0][c]);
+                acc[E - 1][c] = fma(t1, g1, acc[E - 1][c]);
+            }
+            return;
+        }
 #pragma unroll
         for (int l = 0; l < E; ++l) {
             if (v + l < 0 || v + l >= g.V) continue;
@@ -176,6 +192,26 @@ __device__ __forceinline__ void adj_T_part(const Plan &pl, int q, int n, int x, 
     // one cone's contribution: arc weight Aw on gR(xg, ip), dot weight dw
     // with R(xr, j, v + d) when rq
     auto cone = [&](const GRLevel<P, C> &gR, int xg, int ip, A Aw, A dw, bool rq, const RLevel<P, C> &R, int xr, int j) {
+        if (E == 2 && v + 1 < g.V) {             // 2-wide loads (v, d even)
+            const bool r0 = rq && v + d >= 0 && v + d < g.V, r1 = rq && v + d + 1 >= 0 && v + d + 1 < g.V;
+            A dot0 = A(0), dot1 = A(0);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                A g0, g1, q0 = A(0), q1 = A(0);
+                gR.load2(xg, ip, c, v, g0, g1);
+                if (r0) {
+                    R.load2(xr, j, c, v + d, q0, q1);
+                    if (!r1) q1 = A(0);
+                }
+                gL[0][c] = fma(Aw, g0, gL[0][c]);
+                gL[E - 1][c] = fma(Aw, g1, gL[E - 1][c]);
+                dot0 = fma(g0, q0, dot0);
+                dot1 = fma(g1, q1, dot1);
+            }
+            gT[0] = fma(dw, dot0, gT[0]);
+            gT[E - 1] = fma(dw, dot1, gT[E - 1]);
+            return;
+        }
 #pragma unroll
         for (int l = 0; l < E; ++l) {
             const int vv = v + l;

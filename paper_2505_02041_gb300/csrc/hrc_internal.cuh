@@ -297,7 +297,16 @@ template <int P, int C> struct TLevel {
 #pragma unroll
         for (int c = 0; c < C; ++c) st2(reinterpret_cast<SL *>(g) + (long long)c * Vs + v, a.L[c], b.L[c]);
         st2(reinterpret_cast<ST *>(g + (long long)C * Vs * sizeof(SL)) + v, a.t, b.t);
-    }    __device__ __forceinline__ void store4(int x, int k, int v, const Iv<P, C> (&r)[4]) const {
+    }    // linear transmittance of entries v and v+1 (v even)
+    __device__ __forceinline__ void load_t2(int x, int k, int v, typename Prec<P>::A &a,
+                                            typename Prec<P>::A &b) const {
+        ld2(reinterpret_cast<const ST *>(row(x, k) + (long long)C * Vs * sizeof(SL)) + v, a, b);
+        if (Prec<P>::LOG) {
+            a = fexp(-a);
+            b = fexp(-b);
+        }
+    }
+    __device__ __forceinline__ void store4(int x, int k, int v, const Iv<P, C> (&r)[4]) const {
         using A = typename Prec<P>::A;
         char *g = row(x, k);
 #pragma unroll
@@ -401,6 +410,7 @@ template <int P, int C> struct GRLevel {
         return (((long long)x * I + i) * C + c) * Vs + v;
     }
     __device__ __forceinline__ A load(int x, int i, int c, int v) const { return base[idx(x, i, c, v)]; }
+    __device__ __forceinline__ void load2(int x, int i, int c, int v, A &a, A &b) const { ld2(base + idx(x, i, c, v), a, b); }
     __device__ __forceinline__ void store(int x, int i, int c, int v, A val) const { base[idx(x, i, c, v)] = val; }
     __device__ __forceinline__ void store2(int x, int i, int c, int v, A a, A b) const { st2(base + idx(x, i, c, v), a, b); }
 };
