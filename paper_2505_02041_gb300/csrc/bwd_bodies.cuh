@@ -317,15 +317,15 @@ __device__ __forceinline__ void body_adj_merge_up(const Plan &pl, const RowSplit
             Iv<P, C> fr[E];
             if (xok) Tm.load2_masked(xf, fdir, vf, g.V, fr[0], fr[1]);
             else fr[0] = fr[1] = Iv<P, C>::vacuum();
+            A gL[E][C], gT[E];
+            gTn.load2(x, kout, w, gL, gT);      // w even, w + 1 < Vs
 #pragma unroll
             for (int l = 0; l < E; ++l) {
-                A gL[C], gT;
-                gTn.load(x, kout, w + l, gL, gT);
-                A dT = gT * fr[l].trans();
+                A dT = gT[l] * fr[l].trans();
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    aL[l][c] = fma(wgt, gL[c], aL[l][c]);
-                    dT = fma(gL[c], fr[l].L[c], dT);
+                    aL[l][c] = fma(wgt, gL[l][c], aL[l][c]);
+                    dT = fma(gL[l][c], fr[l].L[c], dT);
                 }
                 aT[l] = fma(wgt, dT, aT[l]);
             }
@@ -342,20 +342,23 @@ __device__ __forceinline__ void body_adj_merge_up(const Plan &pl, const RowSplit
             if (v < 0 || v >= g.V) continue;          // v even: then v + 1 may still be in range
             Iv<P, C> nr[E];
             Tm.load2(xn, ndir, v, nr[0], nr[1]);
+            A gL[E][C], gT[E];
+            if (v + 1 < g.V) {
+                gTn.load2(x, kout, v, gL, gT);
+            } else {                            // v + 1 outside: its term is dropped below
+                gTn.load(x, kout, v, gL[0], gT[0]);
+            }
 #pragma unroll
             for (int l = 0; l < E; ++l) {
                 if (v + l >= g.V) continue;
-                A gL[C], gT;
-                gTn.load(x, kout, v + l, gL, gT);
                 const A tn = wgt * nr[l].trans();
 #pragma unroll
-                for (int c = 0; c < C; ++c) aL[l][c] = fma(tn, gL[c], aL[l][c]);
-                aT[l] = fma(tn, gT, aT[l]);
+                for (int c = 0; c < C; ++c) aL[l][c] = fma(tn, gL[l][c], aL[l][c]);
+                aT[l] = fma(tn, gT[l], aT[l]);
             }
         }
     }
-#pragma unroll
-    for (int l = 0; l < E; ++l) gTm.store(x1, kap, w + l, aL[l], aT[l]);
+    gTm.store2(x1, kap, w, aL, aT);           // w even, w + 1 < Vs
 }
 
 // ---------------------------------------------------------------------------

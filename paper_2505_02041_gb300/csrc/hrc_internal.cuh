@@ -395,6 +395,19 @@ template <int P, int C> struct GTLevel {
         for (int c = 0; c < C; ++c) g[(long long)c * Vs + v] = L[c];
         g[(long long)C * Vs + v] = T;
     }
+    // entries v and v+1 (v even)
+    __device__ __forceinline__ void load2(int x, int k, int v, A (&L)[2][C], A (&T)[2]) const {
+        const A *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) ld2(g + (long long)c * Vs + v, L[0][c], L[1][c]);
+        ld2(g + (long long)C * Vs + v, T[0], T[1]);
+    }
+    __device__ __forceinline__ void store2(int x, int k, int v, const A (&L)[2][C], const A (&T)[2]) const {
+        A *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) st2(g + (long long)c * Vs + v, L[0][c], L[1][c]);
+        st2(g + (long long)C * Vs + v, T[0], T[1]);
+    }
 };
 
 template <int P, int C> struct GRLevel {
