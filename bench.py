@@ -215,13 +215,16 @@ def run_ours(args):
     s = torch.from_numpy(s_np).to(dev)
     F = torch.empty((C, H, W), dtype=torch.float32, device=dev)
     h = HRC(W, H, C, 0, args.precision)
-    tuned_ms = h.autotune()
+    tuned_ms = h.autotune() if not args.profile_once else None
     if args.schedule >= 0:
         _lib.hrc_set_schedule(h.ctx, args.schedule)
     if args.profile_once:
-        # For profilers: after the same tuning as a bench run, one forward and
-        # one backward with direct (not graph-replayed) launches inside the
-        # NVTX range "hrc_profile" (ncu --nvtx --nvtx-include "hrc_profile/").
+        # For profilers: one forward and one backward with direct (not
+        # graph-replayed) launches inside the NVTX range "hrc_profile" (ncu
+        # --nvtx --nvtx-include "hrc_profile/"), in a fixed launch
+        # configuration: the autotuner's usual pick at 1024^2 (its timings are
+        # meaningless under a profiler, which serialises every launch).
+        h.set_launch_config(*args.profile_config)
         gF1 = torch.ones((C, H, W), dtype=torch.float32, device=dev)
         h.forward(e, s, F)
         h.backward(gF1)
@@ -500,9 +503,12 @@ def main():
     ap.add_argument("--schedule", type=int, default=-1, help="launch schedule (default: the library's)")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64-scene batched persistent-launch measurement")
+    ap.add_argument("--profile-config", type=int, nargs=4, default=[0, 1, 128, 1],
+                    metavar=("SCHEDULE", "GROUPS", "THREADS", "VMAJOR"),
+                    help="launch configuration of --profile-once (default: the autotuner's usual pick at 1024^2)")
     ap.add_argument("--profile-once", action="store_true",
-                    help="tune, then run one forward + backward inside the NVTX range hrc_profile "
-                         "with direct launches (a target for ncu), print no bench line")
+                    help="run one forward + backward inside the NVTX range hrc_profile with direct "
+                         "launches in --profile-config (a target for ncu), print no bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
