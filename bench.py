@@ -503,8 +503,8 @@ def main():
     ap.add_argument("--schedule", type=int, default=-1, help="launch schedule (default: the library's)")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64-scene batched persistent-launch measurement")
-    ap.add_argument("--profile-config", type=int, nargs=4, default=[0, 1, 128, 1],
-                    metavar=("SCHEDULE", "GROUPS", "THREADS", "VMAJOR"),
+    ap.add_argument("--profile-config", type=int, nargs=5, default=[0, 1, 128, 1, 0],
+                    metavar=("SCHEDULE", "GROUPS", "THREADS", "VMAJOR", "MDOWN"),
                     help="launch configuration of --profile-once (default: the autotuner's usual pick at 1024^2)")
     ap.add_argument("--profile-once", action="store_true",
                     help="run one forward + backward inside the NVTX range hrc_profile with direct "

@@ -90,10 +90,13 @@ hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule);
  *             (64, 128, 256 or 512);
  *   vmajor:   grid order of those kernels: 0 = rows in gridDim.x, v-blocks
  *             in gridDim.y; 1 = the reverse (allowed while 4 (W + H) <= 65535,
- *             the gridDim.y limit for the adjoint's level-0 rows).
- * Defaults {0, 1, 128, 0}; hrc_autotune picks one. */
+ *             the gridDim.y limit for the adjoint's level-0 rows);
+ *   mdown:    merge-down kernel (fp32 / fp16 / bf16): 0 = every thread loads
+ *             its operands; 1 = each block's rows are staged in shared
+ *             memory by bulk (TMA) copies completed on an mbarrier.
+ * Defaults {0, 1, 128, 0, 0}; hrc_autotune picks one. */
 typedef struct hrc_launch_config {
-    int schedule, groups, threads, vmajor;
+    int schedule, groups, threads, vmajor, mdown;
 } hrc_launch_config;
 
 /* Read / set the launch configuration.  Setting it forgets the borrowed
@@ -146,6 +149,12 @@ hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_e
  * For unchanged inputs the gradients are the same either way; recomputing
  * costs about one forward pass. */
 hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on);
+
+/* Waits for the context's stream and reports whether a bounded device-side
+ * wait of the bulk-copy merge-down kernel gave up since the last call
+ * (HRC_ETIMEOUT: that launch ended early and its outputs are incomplete;
+ * the status is device-wide and is cleared by this call). */
+hrc_status hrc_sync(hrc_ctx *ctx);
 
 /* FP64 instance of hrc_fluence / hrc_fluence_backward (device fp64 buffers,
  * same layouts); requires hrc_set_precision(ctx, HRC_FP64_TEST). */

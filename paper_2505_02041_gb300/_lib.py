@@ -29,6 +29,7 @@ SIGNATURES = [
     ("hrc_set_schedule", _i, [_vp, _i]),
     ("hrc_autotune", _i, [_vp, ctypes.POINTER(ctypes.c_float)]),
     ("hrc_set_backward_recompute", _i, [_vp, _i]),
+    ("hrc_sync", _i, [_vp]),
     ("hrc_get_launch_config", _i, [_vp, _vp]),
     ("hrc_set_launch_config", _i, [_vp, _vp]),
     ("hrc_fluence", _i, [_vp, _vp, _vp, _vp]),
@@ -125,7 +126,7 @@ def hrc_set_backward_recompute(ctx, on: bool):
 
 class hrc_launch_config(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("groups", ctypes.c_int), ("threads", ctypes.c_int),
-                ("vmajor", ctypes.c_int)]
+                ("vmajor", ctypes.c_int), ("mdown", ctypes.c_int)]
 
 
 def hrc_get_launch_config(ctx) -> dict:
@@ -134,8 +135,12 @@ def hrc_get_launch_config(ctx) -> dict:
     return {f: getattr(c, f) for f, _ in hrc_launch_config._fields_}
 
 
-def hrc_set_launch_config(ctx, schedule: int, groups: int, threads: int, vmajor: int):
-    c = hrc_launch_config(schedule, groups, threads, vmajor)
+def hrc_sync(ctx):
+    check(load().hrc_sync(ctx), ctx)
+
+
+def hrc_set_launch_config(ctx, schedule: int, groups: int, threads: int, vmajor: int, mdown: int = 0):
+    c = hrc_launch_config(schedule, groups, threads, vmajor, mdown)
     check(load().hrc_set_launch_config(ctx, ctypes.byref(c)), ctx)
 
 

@@ -161,10 +161,15 @@ class HRC:
         """{schedule, groups, threads, vmajor} (see hrc_launch_config)."""
         return _lib.hrc_get_launch_config(self.ctx)
 
-    def set_launch_config(self, schedule=0, groups=1, threads=128, vmajor=0) -> None:
-        _lib.hrc_set_launch_config(self.ctx, schedule, groups, threads, vmajor)
+    def set_launch_config(self, schedule=0, groups=1, threads=128, vmajor=0, mdown=0) -> None:
+        _lib.hrc_set_launch_config(self.ctx, schedule, groups, threads, vmajor, mdown)
         self._borrowed = (None, None, 0, 0)
         self._host_levels = False
+
+    def sync(self) -> None:
+        """Wait for the context's stream; raise HRCError(HRC_ETIMEOUT) if a
+        bounded bulk-copy wait gave up."""
+        _lib.hrc_sync(self.ctx)
 
     def launch_count(self) -> int:
         return _lib.hrc_last_launch_count(self.ctx)

@@ -1,0 +1,67 @@
+// bulk_copy.cuh -- shared-memory staging by the Tensor Memory Accelerator's
+// bulk (non-tensor) copies, completed on an mbarrier.
+//
+// One thread arms the barrier with the byte count it expects and issues the
+// copies (global -> shared, 16-byte aligned addresses, sizes multiples of 16
+// bytes); every thread waits on the barrier's phase.  Waits are bounded:
+// after kBulkSpinLimit polls a wait gives up and reports it, so a kernel
+// never spins forever.
+#pragma once
+
+#include <cstdint>
+
+namespace hrc {
+
+constexpr long long kBulkSpinLimit = 1LL << 24;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes the initialised barrier visible to the asynchronous (copy) proxy.
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arrive (count 1) and expect `bytes` more bytes of completed transactions.
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, unsigned bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the barrier's phase; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
+    for (long long i = 0; i < kBulkSpinLimit; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+// `bytes` (a multiple of 16) from global `src` to shared `dst`, both 16-byte
+// aligned, completing on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+}  // namespace hrc

@@ -48,6 +48,7 @@ struct Plan {
     int mgroups;                     // merge kernels: element groups per thread (1 or 2)
     int mthreads;                    // merge kernels: threads per block for paired-v bodies
     int vmajor;                      // merge kernels: 1 = v-blocks of a row are adjacent in launch order
+    int mdown;                       // merge down: 0 = per-thread loads, 1 = rows staged by bulk copies
     long long arcs_off;              // byte offset: float A[2^n + j] for level n (n >= 1)
     long long arcs_off_d;            // same table in double
     char *arena;

@@ -107,6 +107,7 @@ size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan 
     pl.mgroups = 1;
     pl.mthreads = 128;
     pl.vmajor = 0;
+    pl.mdown = 0;
     const size_t SLb = sl_bytes(prec), STb = st_bytes(prec);
     int Nmax = 0;
     for (int q = 0; q < 4; ++q) {
@@ -176,6 +177,7 @@ struct hrc_ctx {
     int mgroups = 1;
     int mthreads = 128;
     int vmajor = 0;
+    int mdown = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     RayTable rt;
@@ -283,7 +285,7 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
     const void *key[5] = {p0, p1, p2, p3, p4};
     for (auto &g : ctx->graphs) {
         if (g.exec && g.kind == kind && g.prec == ctx->prec && g.sched == ctx->sched && g.mgroups == ctx->mgroups &&
-            g.tune == ctx->mthreads * 2 + ctx->vmajor &&
+            g.tune == ctx->mthreads * 4 + ctx->vmajor * 2 + ctx->mdown &&
             std::memcmp(g.p, key, sizeof(key)) == 0) {
             cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(ctx, e, where);
@@ -314,7 +316,7 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
     slot.prec = ctx->prec;
     slot.sched = ctx->sched;
     slot.mgroups = ctx->mgroups;
-    slot.tune = ctx->mthreads * 2 + ctx->vmajor;
+    slot.tune = ctx->mthreads * 4 + ctx->vmajor * 2 + ctx->mdown;
     std::memcpy(slot.p, key, sizeof(key));
     slot.launches = n;
     e = cudaGraphLaunch(exec, ctx->stream);
@@ -414,6 +416,7 @@ hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out) {
     ctx->plan.mgroups = ctx->mgroups;
     ctx->plan.mthreads = ctx->mthreads;
     ctx->plan.vmajor = ctx->vmajor;
+    ctx->plan.mdown = ctx->mdown;
     e = upload_arcs(ctx->plan, ctx->arena);
     if (e != cudaSuccess) { hrc_destroy(ctx); return fail(nullptr, HRC_ECUDA, "hrc_create: arc upload failed"); }
     *out = ctx;
@@ -470,7 +473,7 @@ namespace {
 bool config_valid(const hrc_ctx *ctx, const hrc_launch_config &c) {
     return (c.schedule == 0 || c.schedule == 1) && (c.groups == 1 || c.groups == 2 || c.groups == 4) &&
            (c.threads == 64 || c.threads == 128 || c.threads == 256 || c.threads == 512) &&
-           (c.vmajor == 0 || c.vmajor == 1) &&
+           (c.vmajor == 0 || c.vmajor == 1) && (c.mdown == 0 || c.mdown == 1) &&
            !(c.vmajor && 4LL * (ctx->W + ctx->H) > 65535);
 }
 
@@ -479,10 +482,21 @@ void apply_config(hrc_ctx *ctx, const hrc_launch_config &c) {
     ctx->mgroups = ctx->plan.mgroups = ctx->plan64.mgroups = c.groups;
     ctx->mthreads = ctx->plan.mthreads = ctx->plan64.mthreads = c.threads;
     ctx->vmajor = ctx->plan.vmajor = ctx->plan64.vmajor = c.vmajor;
+    ctx->mdown = ctx->plan.mdown = ctx->plan64.mdown = c.mdown;
 }
 }  // namespace
 
 extern "C" {
+
+hrc_status hrc_sync(hrc_ctx *ctx) {
+    if (!ctx) return HRC_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    int status = 0;
+    if (e == cudaSuccess) e = read_bulk_status(&status);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_sync");
+    if (status != 0) return fail(ctx, HRC_ETIMEOUT, "a bulk-copy wait gave up (its launch ended early)");
+    return HRC_OK;
+}
 
 hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on) {
     if (!ctx) return HRC_EINVAL;
@@ -497,6 +511,7 @@ hrc_status hrc_get_launch_config(const hrc_ctx *ctx, hrc_launch_config *cfg) {
     cfg->groups = ctx->mgroups;
     cfg->threads = ctx->mthreads;
     cfg->vmajor = ctx->vmajor;
+    cfg->mdown = ctx->mdown;
     return HRC_OK;
 }
 
@@ -528,8 +543,9 @@ hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
     ctx->rec.on = false;
     static const int kThreads[4] = {64, 128, 256, 512};
     static const int kGroups[3] = {1, 2, 4};
-    for (int cand = 0; cand < 2 * 3 * 4 * 2 && st == HRC_OK; ++cand) {
-        const hrc_launch_config c{cand & 1, kGroups[(cand >> 1) % 3], kThreads[(cand / 6) & 3], (cand / 24) & 1};
+    for (int cand = 0; cand < 2 * 3 * 4 * 2 * 2 && st == HRC_OK; ++cand) {
+        const hrc_launch_config c{cand & 1, kGroups[(cand >> 1) % 3], kThreads[(cand / 6) & 3], (cand / 24) & 1,
+                                  (cand / 48) & 1};
         if (!config_valid(ctx, c)) continue;
         apply_config(ctx, c);
         for (int r = 0; r < 2 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
@@ -602,6 +618,7 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
             p64.mgroups = ctx->mgroups;
             p64.mthreads = ctx->mthreads;
             p64.vmajor = ctx->vmajor;
+            p64.mdown = ctx->mdown;
             ctx->plan64 = p64;
             e = upload_arcs(ctx->plan64, ctx->arena64);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
@@ -614,6 +631,7 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
         p.mgroups = ctx->mgroups;
         p.mthreads = ctx->mthreads;
         p.vmajor = ctx->vmajor;
+        p.mdown = ctx->mdown;
         ctx->plan = p;
         cudaError_t e = upload_arcs(ctx->plan, ctx->arena);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");

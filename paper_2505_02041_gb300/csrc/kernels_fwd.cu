@@ -1,9 +1,14 @@
 // kernels_fwd.cu -- forward HRC kernels for sm_103a (standalone launches of
 // the bodies in fwd_bodies.cuh) and the forward launch sequence.
+#include "bulk_copy.cuh"
 #include "fwd_bodies.cuh"
 #include "launch.h"
 
 namespace hrc {
+
+// Status of the bulk-copy kernels: HRC_ETIMEOUT (5) once a bounded wait on a
+// copy barrier gave up (read and cleared by read_bulk_status).
+__device__ int g_bulk_status;
 
 template <int P, int C>
 __global__ void __launch_bounds__(256) k_trace012(Plan pl, const float *__restrict__ e, const float *__restrict__ s,
@@ -50,6 +55,154 @@ __global__ void __launch_bounds__(512) k_merge_down4(Plan pl, RowSplit rs, int n
     int vb;
     row_block(pl, row, vb);
     body_merge_down4<P, C>(pl, rs, n, row, vb);
+}
+
+// ---------------------------------------------------------------------------
+// Merge down (level n >= 1) with the block's rows staged in shared memory by
+// bulk copies.  One block of 128 threads = one row (q, x, ip) x kBV v (four
+// consecutive v per thread).  Thread 0 copies, for both edges of the cone
+// (Eq. 14 at odd x, Eqs. 15-17 at even x), the T planes of the edge's row,
+// the far R window (its start rounded down to 16 bytes, clipped to the
+// row) and, at even x, the near R row; every thread then reads only shared
+// memory.  Out-of-range far values are zeroed by a select, never read.
+// ---------------------------------------------------------------------------
+constexpr int kBV = 512;
+
+template <int P, int C> struct BulkMD {
+    using SL = typename Prec<P>::SL;
+    using ST = typename Prec<P>::ST;
+    static constexpr int AL = 16 / (int)sizeof(SL);   // elements per 16 bytes
+    static constexpr int FW = kBV + 16;                  // far window length
+    static constexpr size_t bytes() {
+        return sizeof(SL) * 2 * C * kBV + sizeof(ST) * 2 * kBV + sizeof(SL) * 2 * C * FW + sizeof(SL) * 2 * C * kBV;
+    }
+};
+
+template <int P, int C>
+__global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, int n) {
+    using SL = typename Prec<P>::SL;
+    using ST = typename Prec<P>::ST;
+    using A = typename Prec<P>::A;
+    using B = BulkMD<P, C>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    long long row;
+    int vb;
+    row_block(pl, row, vb);
+    int local;
+    const int q = find_quadrant(rs, row, local);
+    const QuadGeom &g = pl.q[q];
+    const int v0 = vb * kBV;
+    if (v0 >= g.V) return;                                   // uniform over the block
+    const int I = 1 << n;
+    local += I;
+    const int x = local >> n, ip = local & (I - 1);
+    const bool top = n + 1 >= g.N;                           // R_N = 0
+    const int s = 1 << n;
+    const bool odd = (x & 1) != 0;
+    const int x2 = x >> 1;
+    const int xt = odd ? x : x2;                             // T row: T_n(x, .) or T_{n+1}(x/2, .)
+    const int xq = odd ? (x + 1) >> 1 : x2 + 1;              // far column at level n+1
+    const bool far_ok = !top && xq < g.Un[n + 1];
+    const bool near_ok = !odd && !top;
+    int kk[2], j[2], off[2], fa[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        kk[e] = odd ? (e == 0 ? ip + 1 : ip) : (e == 0 ? 2 * ip + 2 : 2 * ip);
+        j[e] = e == 0 ? 2 * ip + 1 : 2 * ip;
+        off[e] = 2 * kk[e] - (odd ? s : 2 * s);
+        const int a = v0 + off[e];
+        fa[e] = a >= 0 ? a / B::AL * B::AL : -((-a + B::AL - 1) / B::AL) * B::AL;   // round down
+    }
+    SL *tl = reinterpret_cast<SL *>(smem);                   // [2][C][kBV]
+    ST *tt = reinterpret_cast<ST *>(tl + 2 * C * kBV);       // [2][kBV]
+    SL *rf = reinterpret_cast<SL *>(tt + 2 * kBV);           // [2][C][FW]
+    SL *rn = rf + 2 * C * B::FW;                             // [2][C][kBV]
+    const int vend = v0 + kBV < g.Vs ? v0 + kBV : g.Vs;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const TLevel<P, C> Tt(pl, q, odd ? n : n + 1);
+        const RLevel<P, C> R1(pl, q, top ? n : n + 1);
+        const unsigned tb = (unsigned)(vend - v0);
+        unsigned total = 2u * tb * (unsigned)(C * sizeof(SL) + sizeof(ST));
+        int fs[2], fe[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            fs[e] = fa[e] > 0 ? fa[e] : 0;
+            fe[e] = fa[e] + B::FW < g.Vs ? fa[e] + B::FW : g.Vs;
+            if (far_ok && fe[e] > fs[e]) total += (unsigned)(C * (fe[e] - fs[e]) * sizeof(SL));
+        }
+        if (near_ok) total += 2u * (unsigned)(C * tb * sizeof(SL));
+        mbar_arrive_expect(&bar, total);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const char *gr = Tt.row(xt, kk[e]);
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                bulk_load(tl + (e * C + c) * kBV, reinterpret_cast<const SL *>(gr) + (long long)c * g.Vs + v0,
+                          tb * sizeof(SL), &bar);
+            bulk_load(tt + e * kBV, reinterpret_cast<const ST *>(gr + (long long)C * g.Vs * sizeof(SL)) + v0,
+                      tb * sizeof(ST), &bar);
+            if (far_ok && fe[e] > fs[e])
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    bulk_load(rf + (e * C + c) * B::FW + (fs[e] - fa[e]), R1.base + R1.idx(xq, j[e], c, fs[e]),
+                              (unsigned)((fe[e] - fs[e]) * sizeof(SL)), &bar);
+            if (near_ok)
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    bulk_load(rn + (e * C + c) * kBV, R1.base + R1.idx(x2, j[e], c, v0), tb * sizeof(SL), &bar);
+        }
+    }
+    if (!mbar_wait(&bar, 0)) {                                // gave up: report, drain, leave
+        if (threadIdx.x == 0) atomicExch(&g_bulk_status, 5);
+        mbar_wait(&bar, 0);
+        return;
+    }
+    const int v = v0 + 4 * (int)threadIdx.x;
+    if (v >= g.V) return;
+    const int ti = v - v0;
+    const A Ap = arc<P>(pl, n + 1, 2 * ip + 1), Am = arc<P>(pl, n + 1, 2 * ip);
+    A acc[4][C];
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[l][c] = A(0);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const A Aj = e == 0 ? Ap : Am;
+        A tr[4];
+        ld4(tt + e * kBV + ti, tr);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) tr[l] = Prec<P>::LOG ? fexp(-tr[l]) : tr[l];
+        const int fi = ti + (v0 + off[e] - fa[e]);           // far window index of v (even)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            A L[4], r[4], r0[4];
+            ld4(tl + (e * C + c) * kBV + ti, L);
+            ld2(rf + (e * C + c) * B::FW + fi, r[0], r[1]);
+            ld2(rf + (e * C + c) * B::FW + fi + 2, r[2], r[3]);
+            if (near_ok) ld4(rn + (e * C + c) * kBV + ti, r0);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int vf = v + l + off[e];
+                const A rr = (far_ok && vf >= 0 && vf < g.V) ? r[l] : A(0);
+                const A f = fma(Aj, L[l], tr[l] * rr);
+                if (odd) acc[l][c] += f;                                         // Eq. 14
+                else acc[l][c] += A(0.5) * ((near_ok ? r0[l] : A(0)) + f);       // Eqs. 15-17
+            }
+        }
+    }
+    const RLevel<P, C> Rn(pl, q, n);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const A o[4] = {acc[0][c], acc[1][c], acc[2][c], acc[3][c]};
+        Rn.store4(x, ip, c, v, o);
+    }
 }
 
 template <int P, int C, class OUT>
@@ -187,7 +340,9 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             }
             const int mt = pl.mthreads;
             rec->begin(K_MERGE_DOWN, n, by);
-            if (n >= 1) k_merge_down4<P, C><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
+            if (n >= 1 && pl.mdown == 1 && P != P_FP64)
+                k_merge_down_bulk<P, C><<<row_grid(pl, rs.start[4], kBV), 128, BulkMD<P, C>::bytes(), st>>>(pl, rs, n);
+            else if (n >= 1) k_merge_down4<P, C><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
             else {
                 const int ts = 2 * mt > 512 ? 512 : 2 * mt;   // single v per thread at level 0
                 k_merge_down<P, C, false><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
@@ -266,6 +421,21 @@ static cudaError_t prepare_prec() {
     set((const void *)k_trace012<P, 2>, TraceTile<typename Prec<P>::A, 2>::bytes());
     set((const void *)k_trace012<P, 3>, TraceTile<typename Prec<P>::A, 3>::bytes());
     set((const void *)k_trace012<P, 4>, TraceTile<typename Prec<P>::A, 4>::bytes());
+    if constexpr (P != P_FP64) {
+        set((const void *)k_merge_down_bulk<P, 1>, BulkMD<P, 1>::bytes());
+        set((const void *)k_merge_down_bulk<P, 2>, BulkMD<P, 2>::bytes());
+        set((const void *)k_merge_down_bulk<P, 3>, BulkMD<P, 3>::bytes());
+        set((const void *)k_merge_down_bulk<P, 4>, BulkMD<P, 4>::bytes());
+    }
+    return e;
+}
+
+// Reads and clears the bulk-copy kernels' status (after the caller's stream
+// has been synchronised): 0, or 5 (HRC_ETIMEOUT) if a copy wait gave up.
+cudaError_t read_bulk_status(int *status) {
+    int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(status, g_bulk_status, sizeof(int));
+    if (e == cudaSuccess && *status != 0) e = cudaMemcpyToSymbol(g_bulk_status, &zero, sizeof(int));
     return e;
 }
 

@@ -144,6 +144,9 @@ cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *ds
 // R_0 of every frame into the plan's buffer (the forward does not store it).
 cudaError_t launch_r0(const Plan &pl, cudaStream_t st);
 
+// Reads and clears the bulk-copy kernels' timeout status (0 or 5).
+cudaError_t read_bulk_status(int *status);
+
 double bytes_T(const Plan &pl, int q, int n);
 double bytes_T_odd(const Plan &pl, int q, int n);
 double bytes_T_even_dirs(const Plan &pl, int q, int n);

@@ -146,14 +146,17 @@ def test_launch_configurations_give_the_same_results():
     for sched in (0, 1):
         for groups in (1, 2, 4):
             for threads in (64, 128, 256, 512):
-                for vmajor in (0, 1):
-                    h.set_launch_config(sched, groups, threads, vmajor)
-                    assert h.launch_config == dict(schedule=sched, groups=groups, threads=threads, vmajor=vmajor)
+                for vmajor, mdown in ((0, 0), (1, 0), (0, 1), (1, 1)):
+                    h.set_launch_config(sched, groups, threads, vmajor, mdown)
+                    assert h.launch_config == dict(schedule=sched, groups=groups, threads=threads, vmajor=vmajor,
+                                                   mdown=mdown)
                     F = h.forward(ed, sd).cpu().numpy()
                     ge, gs = h.backward(gd)
                     out = (F, ge.cpu().numpy(), gs.cpu().numpy())
                     if ref is None:
                         ref = out
                         continue
+                    h.sync()
                     for a, b in zip(out, ref):
-                        assert np.max(np.abs(a - b)) <= 1e-6 * max(1.0, np.max(np.abs(b))), (sched, groups, threads, vmajor)
+                        assert np.max(np.abs(a - b)) <= 1e-6 * max(1.0, np.max(np.abs(b))), (sched, groups, threads,
+                                                                                              vmajor, mdown)
