@@ -156,6 +156,13 @@ hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on);
  * the status is device-wide and is cleared by this call). */
 hrc_status hrc_sync(hrc_ctx *ctx);
 
+/* Test hook for the bulk-copy waits: the merge-down kernel with mdown = 1
+ * arms its barrier with `extra_bytes` (0..4096) more than it copies, so its
+ * waits run out after `limit_ns` (<= 0 restores the default, 2 s) and
+ * hrc_sync reports HRC_ETIMEOUT instead of the kernel hanging.  {0, 0}
+ * restores normal operation; the context stays usable. */
+hrc_status hrc_debug_bulk_wait(hrc_ctx *ctx, int extra_bytes, long long limit_ns);
+
 /* FP64 instance of hrc_fluence / hrc_fluence_backward (device fp64 buffers,
  * same layouts); requires hrc_set_precision(ctx, HRC_FP64_TEST). */
 hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *sigma_t, double *out);

@@ -30,6 +30,7 @@ SIGNATURES = [
     ("hrc_autotune", _i, [_vp, ctypes.POINTER(ctypes.c_float)]),
     ("hrc_set_backward_recompute", _i, [_vp, _i]),
     ("hrc_sync", _i, [_vp]),
+    ("hrc_debug_bulk_wait", _i, [_vp, _i, ctypes.c_longlong]),
     ("hrc_get_launch_config", _i, [_vp, _vp]),
     ("hrc_set_launch_config", _i, [_vp, _vp]),
     ("hrc_fluence", _i, [_vp, _vp, _vp, _vp]),
@@ -137,6 +138,10 @@ def hrc_get_launch_config(ctx) -> dict:
 
 def hrc_sync(ctx):
     check(load().hrc_sync(ctx), ctx)
+
+
+def hrc_debug_bulk_wait(ctx, extra_bytes: int, limit_ns: int):
+    check(load().hrc_debug_bulk_wait(ctx, extra_bytes, limit_ns), ctx)
 
 
 def hrc_set_launch_config(ctx, schedule: int, groups: int, threads: int, vmajor: int, mdown: int = 0):

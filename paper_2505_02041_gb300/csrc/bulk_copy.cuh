@@ -3,16 +3,15 @@
 //
 // One thread arms the barrier with the byte count it expects and issues the
 // copies (global -> shared, 16-byte aligned addresses, sizes multiples of 16
-// bytes); every thread waits on the barrier's phase.  Waits are bounded:
-// after kBulkSpinLimit polls a wait gives up and reports it, so a kernel
-// never spins forever.
+// bytes); every thread waits on the barrier's phase.  Waits are bounded in
+// time (the global nanosecond timer): past the limit a wait gives up and the
+// kernel reports it, so a kernel never spins forever.
 #pragma once
 
 #include <cstdint>
 
 namespace hrc {
 
-constexpr long long kBulkSpinLimit = 1LL << 24;
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -48,11 +47,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
     return ok != 0;
 }
 
-// Bounded wait for the barrier's phase; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
-    for (long long i = 0; i < kBulkSpinLimit; ++i)
-        if (mbar_try_wait(bar, phase)) return true;
-    return false;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the barrier's phase for at most limit_ns; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase, long long limit_ns) {
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, phase))
+        if ((long long)(global_ns() - t0) > limit_ns) return false;
+    return true;
 }
 
 // `bytes` (a multiple of 16) from global `src` to shared `dst`, both 16-byte

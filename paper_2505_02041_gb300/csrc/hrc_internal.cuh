@@ -49,6 +49,8 @@ struct Plan {
     int mthreads;                    // merge kernels: threads per block for paired-v bodies
     int vmajor;                      // merge kernels: 1 = v-blocks of a row are adjacent in launch order
     int mdown;                       // merge down: 0 = per-thread loads, 1 = rows staged by bulk copies
+    long long bulk_limit_ns;         // bound of a bulk-copy barrier wait
+    int bulk_extra_tx;               // test hook: bytes expected but never copied (0 in use)
     long long arcs_off;              // byte offset: float A[2^n + j] for level n (n >= 1)
     long long arcs_off_d;            // same table in double
     char *arena;

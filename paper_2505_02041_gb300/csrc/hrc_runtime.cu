@@ -108,6 +108,8 @@ size_t build_plan(int W, int H, int C, int cascades, int prec, size_t off, Plan 
     pl.mthreads = 128;
     pl.vmajor = 0;
     pl.mdown = 0;
+    pl.bulk_limit_ns = 2000000000LL;   // 2 s
+    pl.bulk_extra_tx = 0;
     const size_t SLb = sl_bytes(prec), STb = st_bytes(prec);
     int Nmax = 0;
     for (int q = 0; q < 4; ++q) {
@@ -487,6 +489,16 @@ void apply_config(hrc_ctx *ctx, const hrc_launch_config &c) {
 }  // namespace
 
 extern "C" {
+
+hrc_status hrc_debug_bulk_wait(hrc_ctx *ctx, int extra_bytes, long long limit_ns) {
+    if (!ctx || ctx->batched || extra_bytes < 0 || extra_bytes > 4096) return HRC_EINVAL;
+    const long long lim = limit_ns > 0 ? limit_ns : 2000000000LL;
+    ctx->plan.bulk_extra_tx = ctx->plan64.bulk_extra_tx = extra_bytes;
+    ctx->plan.bulk_limit_ns = ctx->plan64.bulk_limit_ns = lim;
+    clear_graphs(ctx);   // the graphs hold the plan by value
+    ctx->have_fwd = false;
+    return HRC_OK;
+}
 
 hrc_status hrc_sync(hrc_ctx *ctx) {
     if (!ctx) return HRC_EINVAL;

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, i
             if (far_ok && fe[e] > fs[e]) total += (unsigned)(C * (fe[e] - fs[e]) * sizeof(SL));
         }
         if (near_ok) total += 2u * (unsigned)(C * tb * sizeof(SL));
-        mbar_arrive_expect(&bar, total);
+        mbar_arrive_expect(&bar, total + (unsigned)pl.bulk_extra_tx);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const char *gr = Tt.row(xt, kk[e]);
@@ -158,9 +158,9 @@ __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, i
                     bulk_load(rn + (e * C + c) * kBV, R1.base + R1.idx(x2, j[e], c, v0), tb * sizeof(SL), &bar);
         }
     }
-    if (!mbar_wait(&bar, 0)) {                                // gave up: report, drain, leave
+    if (!mbar_wait(&bar, 0, pl.bulk_limit_ns)) {              // gave up: report, let the copies land, leave
         if (threadIdx.x == 0) atomicExch(&g_bulk_status, 5);
-        mbar_wait(&bar, 0);
+        mbar_wait(&bar, 0, pl.bulk_limit_ns);
         return;
     }
     const int v = v0 + 4 * (int)threadIdx.x;

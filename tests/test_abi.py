@@ -73,6 +73,7 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.hrc_batched_schedule(None, 1) == _lib.HRC_EINVAL
     assert lib.hrc_set_backward_recompute(None, 1) == _lib.HRC_EINVAL
     assert lib.hrc_sync(None) == _lib.HRC_EINVAL
+    assert lib.hrc_debug_bulk_wait(None, 0, 0) == _lib.HRC_EINVAL
     assert lib.hrc_get_launch_config(None, None) == _lib.HRC_EINVAL
     assert lib.hrc_set_launch_config(None, None) == _lib.HRC_EINVAL
     # the allocation-free entry point rejects sizes beyond its fixed scratch

@@ -160,3 +160,24 @@ def test_launch_configurations_give_the_same_results():
                     for a, b in zip(out, ref):
                         assert np.max(np.abs(a - b)) <= 1e-6 * max(1.0, np.max(np.abs(b))), (sched, groups, threads,
                                                                                               vmajor, mdown)
+
+
+def test_bulk_copy_wait_times_out_and_recovers():
+    """The bulk-copy merge down waits on a barrier with a time limit: armed
+    (test hook) with bytes that never arrive, its waits give up after 1 ms,
+    hrc_sync reports HRC_ETIMEOUT, and the context then computes correctly."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC, _lib
+    e, s = scenes.random_scene(64, 48, 2, 51)
+    h = HRC(64, 48, 2)
+    h.set_launch_config(0, 1, 128, 1, 1)
+    ed, sd = to_dev(e), to_dev(s)
+    _lib.hrc_debug_bulk_wait(h.ctx, 16, 1_000_000)
+    h.forward(ed, sd)
+    with pytest.raises(_lib.HRCError) as ex:
+        h.sync()
+    assert ex.value.status == _lib.HRC_ETIMEOUT
+    _lib.hrc_debug_bulk_wait(h.ctx, 0, 0)
+    F = h.forward(ed, sd)
+    h.sync()
+    assert err_max(F.cpu().numpy(), oracle.fluence(e, s)) <= TOL
