@@ -574,16 +574,33 @@ __device__ __forceinline__ void adj_phase_a(const PairTile<typename Prec<P>::A, 
     }
 }
 
-template <class A, int C, int R, int J>
-__device__ __forceinline__ void adj_phase_b(const AdjSlots<A, C> &sl, int u, int v, int ua, int v0, A (&dE)[C], A &dS) {
+// Phase B for the pieces J .. end-1 of shape R that can reach a pixel whose
+// frame column u has u mod S == RHO (piece J crosses it for the probe at
+// u - du_J only when that column is a probe column, i.e. du_J mod S == RHO):
+// the selection is made at compile time, so no piece is tested at run time.
+template <class A, int C, int R, int RHO, int J>
+__device__ __forceinline__ void adj_phase_b_res(const AdjSlots<A, C> &sl, int u, int v, int ua, int v0, A (&dE)[C],
+                                                A &dS) {
     if constexpr (J < RayAt<R>::end) {
         using B = RayBox<R>;
         using pc = PieceAt<J>;
-        const int up = u - pc::du;
-        if ((up & (B::S - 1)) == 0)
-            sl.add_to((J - RayAt<R>::begin) * B::NPROBE + ((up - ua) >> B::n) * B::NVB + (v - pc::dv - v0 + B::dvhi),
+        if constexpr ((pc::du & (B::S - 1)) == RHO)
+            sl.add_to((J - RayAt<R>::begin) * B::NPROBE + ((u - pc::du - ua) >> B::n) * B::NVB +
+                          (v - pc::dv - v0 + B::dvhi),
                       dE, dS);
-        adj_phase_b<A, C, R, J + 1>(sl, u, v, ua, v0, dE, dS);
+        adj_phase_b_res<A, C, R, RHO, J + 1>(sl, u, v, ua, v0, dE, dS);
+    }
+}
+
+// Dispatch on the pixel column's residue (uniform over a warp).
+template <class A, int C, int R, int RHO = 0>
+__device__ __forceinline__ void adj_phase_b(const AdjSlots<A, C> &sl, int u, int v, int ua, int v0, A (&dE)[C],
+                                            A &dS) {
+    if constexpr (RHO < RayBox<R>::S) {
+        if ((u & (RayBox<R>::S - 1)) == RHO)
+            adj_phase_b_res<A, C, R, RHO, RayAt<R>::begin>(sl, u, v, ua, v0, dE, dS);
+        else
+            adj_phase_b<A, C, R, RHO + 1>(sl, u, v, ua, v0, dE, dS);
     }
 }
 
@@ -607,7 +624,7 @@ __device__ __forceinline__ void adj_shapes(const Plan &pl, const PairTile<typena
             const int ua = (f.u0 - 1) & ~(RayBox<R>::S - 1);
 #pragma unroll
             for (int i = 0; i < 2; ++i)
-                if (valid[i]) adj_phase_b<A, C, R, RayAt<R>::begin>(sl, uc[i], v, ua, f.v0, dE[i], dS[i]);
+                if (valid[i]) adj_phase_b<A, C, R>(sl, uc[i], v, ua, f.v0, dE[i], dS[i]);
             __syncthreads();
         }
         adj_shapes<P, C, R + 1>(pl, tt, sl, f, nmax, uc, valid, v, pre, dE, dS);
