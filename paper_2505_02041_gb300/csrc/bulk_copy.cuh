@@ -8,6 +8,7 @@
 // kernel reports it, so a kernel never spins forever.
 #pragma once
 
+#include <cuda.h>
 #include <cstdint>
 
 namespace hrc {
@@ -68,6 +69,25 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                      smem_addr(dst)),
                  "l"(src), "r"(bytes), "r"(smem_addr(bar))
                  : "memory");
+}
+
+// Tensor (tiled) copies through a tensor map: the box at coordinates (x, y)
+// or (x, y, z) of `map` (a __grid_constant__ kernel parameter) into shared
+// `dst` (128-byte aligned), completing on `bar`.  Elements outside the
+// tensor read as zero.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
 }
 
 }  // namespace hrc

@@ -26,6 +26,7 @@
 
 #include <type_traits>
 
+#include "bulk_copy.cuh"
 #include "hrc_internal.cuh"
 #include "trace_shapes.cuh"
 
@@ -94,6 +95,62 @@ template <class A, int C> struct TraceTile {
             for (int c = 0; c < C; ++c) e[c * TR_PLANE + o] = in ? A(ein[c * HW + pix]) : A(0);
         }
     }
+    // The same staging with the region of e and sigma fetched by TMA tensor
+    // copies (fp32 inputs; the out-of-grid part of the box reads as zero,
+    // which is vacuum).  The boxes land in a staging area that overlaps the
+    // w and e planes: every thread first takes its pixels into registers,
+    // then the planes are written.  False when the copy wait gave up.
+    __device__ __forceinline__ bool stage_tma(int x0, int y0, const CUtensorMap *tme, const CUtensorMap *tms,
+                                              uint64_t *bar, long long limit_ns) {
+        static_assert(sizeof(A) == 4, "fp32 staging");
+        constexpr int BOX = TR_REG * TR_REG;                        // 40 x 40
+        constexpr int PER = (BOX + 255) / 256;                      // pixels per thread (256 threads)
+        float *stg = reinterpret_cast<float *>(w);                  // [C + 1][BOX]
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect(bar, (unsigned)((C + 1) * BOX * sizeof(float)));
+#pragma unroll
+            for (int c = 0; c < C; ++c) tma_load_3d(stg + c * BOX, tme, x0 - TR_HALO, y0 - TR_HALO, c, bar);
+            tma_load_2d(stg + C * BOX, tms, x0 - TR_HALO, y0 - TR_HALO, bar);
+        }
+        if (!mbar_wait(bar, 0, limit_ns)) {
+            mbar_wait(bar, 0, limit_ns);                            // let the copies land
+            return false;
+        }
+        float sv[PER], ev[PER][C];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + 256 * k;
+            if (i >= BOX) break;
+            sv[k] = stg[C * BOX + i];
+#pragma unroll
+            for (int c = 0; c < C; ++c) ev[k][c] = stg[c * BOX + i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + 256 * k;
+            if (i >= BOX) break;
+            const int ry = i / TR_REG, rx = i - ry * TR_REG;
+            const int o = ry * TR_PITCH + rx;
+            const A sg = sv[k];
+            s[o] = sg;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                A tc, wc;
+                piece_factors<A>(sg, class_len<A>(c), tc, wc);
+                t[c * TR_PLANE + o] = tc;
+                w[c * TR_PLANE + o] = wc;
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) e[c * TR_PLANE + o] = ev[k][c];
+        }
+        return true;
+    }
 };
 
 // Trace of ray shape R from the probe whose tile offset is `base`; su / sv
@@ -142,16 +199,32 @@ __device__ __forceinline__ void trace_store(const Plan &pl, const TraceTile<type
 // frame's u axis (one column of every residue mod 4, so the warps get equal
 // shares of the level-1 and level-2 probes); its lanes run along v, so every
 // T store is a 128-byte coalesced row segment in every frame.
+// With tme / tms (fp32 inputs), the region is fetched by TMA tensor copies;
+// a copy wait that gives up sets *status to 5 (HRC_ETIMEOUT) and leaves the
+// tile's T entries unwritten.
 template <int P, int C>
 __device__ __forceinline__ void body_trace012(const Plan &pl, const float *__restrict__ e, const float *__restrict__ s,
                                               const double *__restrict__ ed, const double *__restrict__ sd, int qmask,
-                                              int bx, int by, unsigned char *tr_smem) {
+                                              int bx, int by, unsigned char *tr_smem,
+                                              const CUtensorMap *tme = nullptr, const CUtensorMap *tms = nullptr,
+                                              int *status = nullptr) {
     using A = typename Prec<P>::A;
     TraceTile<A, C> tt(tr_smem);
     const int W = pl.W, H = pl.H;
     const int x0 = bx * TR_TILE, y0 = by * TR_TILE;
-    if (P == P_FP64) tt.stage(W, H, x0, y0, ed, sd);
-    else tt.stage(W, H, x0, y0, e, s);
+    if constexpr (P == P_FP64) {
+        tt.stage(W, H, x0, y0, ed, sd);
+    } else {
+        if (tme) {
+            __shared__ __align__(8) uint64_t bar;
+            if (!tt.stage_tma(x0, y0, tme, tms, &bar, pl.bulk_limit_ns)) {
+                if (threadIdx.x == 0 && status) atomicExch(status, 5);
+                return;
+            }
+        } else {
+            tt.stage(W, H, x0, y0, e, s);
+        }
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = 0; q < 4; ++q) {

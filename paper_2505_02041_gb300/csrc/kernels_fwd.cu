@@ -1,5 +1,8 @@
 // kernels_fwd.cu -- forward HRC kernels for sm_103a (standalone launches of
 // the bodies in fwd_bodies.cuh) and the forward launch sequence.
+#include <cudaTypedefs.h>
+#include <cstring>
+
 #include "bulk_copy.cuh"
 #include "fwd_bodies.cuh"
 #include "launch.h"
@@ -13,9 +16,11 @@ __device__ int g_bulk_status;
 template <int P, int C>
 __global__ void __launch_bounds__(256) k_trace012(Plan pl, const float *__restrict__ e, const float *__restrict__ s,
                                                   const double *__restrict__ ed, const double *__restrict__ sd,
-                                                  int qmask) {
-    extern __shared__ __align__(16) unsigned char tr_smem[];
-    body_trace012<P, C>(pl, e, s, ed, sd, qmask, blockIdx.x, blockIdx.y, tr_smem);
+                                                  int qmask, const __grid_constant__ CUtensorMap tme,
+                                                  const __grid_constant__ CUtensorMap tms, int use_tma) {
+    extern __shared__ __align__(128) unsigned char tr_smem[];
+    body_trace012<P, C>(pl, e, s, ed, sd, qmask, blockIdx.x, blockIdx.y, tr_smem, use_tma ? &tme : nullptr,
+                        use_tma ? &tms : nullptr, &g_bulk_status);
 }
 
 // Row and v-block of this block: the launch grid is (rows, v-blocks), or
@@ -281,6 +286,36 @@ double bytes_R(const Plan &pl, int q, int n) {
     return double(g.Un[n] - 1) * (1 << n) * g.V * vr;
 }
 
+// Tensor maps of the fp32 inputs for the trace's TMA staging: emission
+// [C][H][W] (3D) and extinction [H][W] (2D), 40 x 40 boxes, zero fill
+// outside.  Needs 16-byte row strides (W a multiple of 4) and 16-byte
+// aligned bases; false otherwise (the trace then stages with plain loads).
+static bool encode_trace_maps(const Plan &pl, const void *e, const void *s, CUtensorMap &me, CUtensorMap &ms) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode || pl.W % 4 != 0 || (reinterpret_cast<uintptr_t>(e) & 15) || (reinterpret_cast<uintptr_t>(s) & 15))
+        return false;
+    const cuuint32_t box[3] = {TR_REG, TR_REG, 1}, estr[3] = {1, 1, 1};
+    const cuuint64_t de[3] = {(cuuint64_t)pl.W, (cuuint64_t)pl.H, (cuuint64_t)pl.C};
+    const cuuint64_t se[2] = {(cuuint64_t)pl.W * 4, (cuuint64_t)pl.W * pl.H * 4};
+    if (encode(&me, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(e), de, se, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (encode(&ms, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(s), de, se, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    return true;
+}
+
 template <int P, int C>
 static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
                             cudaStream_t st, int *launches, Recorder *rec, bool with_sum) {
@@ -305,7 +340,11 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                     for (int n = 0; n <= 2; ++n) by += bytes_T(pl, q, n);
             dim3 grid((pl.W + TR_TILE - 1) / TR_TILE, (pl.H + TR_TILE - 1) / TR_TILE);
             rec->begin(K_TRACE012, 0, by);
-            k_trace012<P, C><<<grid, 256, smem, st>>>(pl, ef, sf, ed, sd, qsel < 0 ? 15 : (1 << qsel));
+            CUtensorMap me, ms;
+            std::memset(&me, 0, sizeof(me));
+            std::memset(&ms, 0, sizeof(ms));
+            const int use_tma = (P != P_FP64 && encode_trace_maps(pl, e, s, me, ms)) ? 1 : 0;
+            k_trace012<P, C><<<grid, 256, smem, st>>>(pl, ef, sf, ed, sd, qsel < 0 ? 15 : (1 << qsel), me, ms, use_tma);
             rec->end();
             ++*launches;
         }
