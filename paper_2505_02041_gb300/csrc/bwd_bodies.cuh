@@ -644,10 +644,14 @@ template <class A, int C> constexpr size_t adj_trace_smem() {
 // owns two pixels of the tile (columns c[i] along u, its lane along v) and
 // accumulates them in registers over both frames of the pair.  Pair 0
 // writes the image gradients, pair 1 (launched after it) adds to them.
+// With tme / tms (fp32 inputs) the tile region is fetched by TMA tensor
+// copies; a copy wait that gives up sets *status to 5 (HRC_ETIMEOUT) and
+// leaves the tile's gradients unwritten.
 template <int P, int C, class IN>
 __device__ __forceinline__ void body_adj_trace(const Plan &pl, const IN *__restrict__ e, const IN *__restrict__ s,
                                                IN *__restrict__ ge, IN *__restrict__ gs, int pair, int bx, int by,
-                                               unsigned char *smem) {
+                                               unsigned char *smem, const CUtensorMap *tme = nullptr,
+                                               const CUtensorMap *tms = nullptr, int *status = nullptr) {
     using A = typename Prec<P>::A;
     PairTile<A, C> tt(smem);
     const AdjSlots<A, C> sl{reinterpret_cast<A *>(smem + PairTile<A, C>::bytes())};
@@ -656,7 +660,19 @@ __device__ __forceinline__ void body_adj_trace(const Plan &pl, const IN *__restr
     const long long HW = (long long)W * H;
     const int x0 = pair == 0 ? bx * PT_U : bx * PT_V;
     const int y0 = pair == 0 ? by * PT_V : by * PT_U;
-    tt.stage(pair, W, H, x0, y0, e, s);
+    if constexpr (sizeof(A) == 4) {
+        if (tme) {
+            __shared__ __align__(8) uint64_t bar;
+            if (!tt.stage_tma(pair, x0, y0, tme, tms, &bar, pl.bulk_limit_ns)) {
+                if (threadIdx.x == 0 && status) atomicExch(status, 5);
+                return;
+            }
+        } else {
+            tt.stage(pair, W, H, x0, y0, e, s);
+        }
+    } else {
+        tt.stage(pair, W, H, x0, y0, e, s);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int cc[2];

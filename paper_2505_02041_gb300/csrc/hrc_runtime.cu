@@ -503,8 +503,10 @@ hrc_status hrc_debug_bulk_wait(hrc_ctx *ctx, int extra_bytes, long long limit_ns
 hrc_status hrc_sync(hrc_ctx *ctx) {
     if (!ctx) return HRC_EINVAL;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    int status = 0;
+    int status = 0, status_b = 0;
     if (e == cudaSuccess) e = read_bulk_status(&status);
+    if (e == cudaSuccess) e = read_adj_bulk_status(&status_b);
+    status |= status_b;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_sync");
     if (status != 0) return fail(ctx, HRC_ETIMEOUT, "a bulk-copy wait gave up (its launch ended early)");
     return HRC_OK;

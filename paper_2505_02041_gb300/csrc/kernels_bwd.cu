@@ -2,6 +2,8 @@
 // the bodies in bwd_bodies.cuh) and the backward launch sequence.
 #include <type_traits>
 
+#include <cstring>
+
 #include "bwd_bodies.cuh"
 #include "launch.h"
 
@@ -43,11 +45,17 @@ __global__ void __launch_bounds__(512) k_adj_merge_up(Plan pl, RowSplitB rs, int
     body_adj_merge_up<P, C>(pl, rs, n, row, vb);
 }
 
+// HRC_ETIMEOUT (5) once a TMA copy wait of the adjoint trace gave up.
+__device__ int g_adj_bulk_status;
+
 template <int P, int C, class IN>
 __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_trace(Plan pl, const IN *__restrict__ e, const IN *__restrict__ s,
-                                                   IN *__restrict__ ge, IN *__restrict__ gs, int pair) {
-    extern __shared__ __align__(16) unsigned char tb_smem[];
-    body_adj_trace<P, C, IN>(pl, e, s, ge, gs, pair, blockIdx.x, blockIdx.y, tb_smem);
+                                                   IN *__restrict__ ge, IN *__restrict__ gs, int pair,
+                                                   const __grid_constant__ CUtensorMap tme,
+                                                   const __grid_constant__ CUtensorMap tms, int use_tma) {
+    extern __shared__ __align__(128) unsigned char tb_smem[];
+    body_adj_trace<P, C, IN>(pl, e, s, ge, gs, pair, blockIdx.x, blockIdx.y, tb_smem, use_tma ? &tme : nullptr,
+                             use_tma ? &tms : nullptr, &g_adj_bulk_status);
 }
 
 // ---------------------------------------------------------------------------
@@ -173,7 +181,14 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                 for (int n = 0; n <= 2; ++n) by += gTbytes(q, n);
             dim3 grid(pair_tiles_x(pair, pl.W), pair_tiles_y(pair, pl.H));
             rec->begin(K_ADJ_TRACE, pair, by);
-            k_adj_trace<P, C, IN><<<grid, ADJ_THREADS, smem, st>>>(pl, (const IN *)e, (const IN *)s, (IN *)ge, (IN *)gs, pair);
+            CUtensorMap me, ms;
+            std::memset(&me, 0, sizeof(me));
+            std::memset(&ms, 0, sizeof(ms));
+            const int use_tma = (P != P_FP64 && encode_image_maps(pl, e, s, pair == 0 ? PT_RU : PT_RV,
+                                                                  pair == 0 ? PT_RV : PT_RU, me, ms))
+                                    ? 1 : 0;
+            k_adj_trace<P, C, IN><<<grid, ADJ_THREADS, smem, st>>>(pl, (const IN *)e, (const IN *)s, (IN *)ge, (IN *)gs,
+                                                                   pair, me, ms, use_tma);
             rec->end();
             ++*launches;
         }
@@ -223,6 +238,13 @@ cudaError_t launch_backward(const Plan &pl, const RayTable &rt, const void *e, c
     case P_BF16: return bwd_prec<P_BF16>(pl, rt, e, s, gF, ge, gs, recompute, st, launches, rec);
     default: return bwd_prec<P_FP64>(pl, rt, e, s, gF, ge, gs, recompute, st, launches, rec);
     }
+}
+
+cudaError_t read_adj_bulk_status(int *status) {
+    int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(status, g_adj_bulk_status, sizeof(int));
+    if (e == cudaSuccess && *status != 0) e = cudaMemcpyToSymbol(g_adj_bulk_status, &zero, sizeof(int));
+    return e;
 }
 
 }  // namespace hrc

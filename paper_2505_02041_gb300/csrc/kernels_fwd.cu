@@ -286,11 +286,13 @@ double bytes_R(const Plan &pl, int q, int n) {
     return double(g.Un[n] - 1) * (1 << n) * g.V * vr;
 }
 
-// Tensor maps of the fp32 inputs for the trace's TMA staging: emission
-// [C][H][W] (3D) and extinction [H][W] (2D), 40 x 40 boxes, zero fill
-// outside.  Needs 16-byte row strides (W a multiple of 4) and 16-byte
-// aligned bases; false otherwise (the trace then stages with plain loads).
-static bool encode_trace_maps(const Plan &pl, const void *e, const void *s, CUtensorMap &me, CUtensorMap &ms) {
+// Tensor maps of the fp32 inputs for the TMA staging of the trace kernels:
+// emission [C][H][W] (3D) and extinction [H][W] (2D), box_x x box_y boxes,
+// zero fill outside.  Needs 16-byte row strides (W a multiple of 4) and
+// 16-byte aligned bases; false otherwise (the kernels then stage with plain
+// loads).
+bool encode_image_maps(const Plan &pl, const void *e, const void *s, int box_x, int box_y, CUtensorMap &me,
+                       CUtensorMap &ms) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -302,7 +304,7 @@ static bool encode_trace_maps(const Plan &pl, const void *e, const void *s, CUte
     }();
     if (!encode || pl.W % 4 != 0 || (reinterpret_cast<uintptr_t>(e) & 15) || (reinterpret_cast<uintptr_t>(s) & 15))
         return false;
-    const cuuint32_t box[3] = {TR_REG, TR_REG, 1}, estr[3] = {1, 1, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1}, estr[3] = {1, 1, 1};
     const cuuint64_t de[3] = {(cuuint64_t)pl.W, (cuuint64_t)pl.H, (cuuint64_t)pl.C};
     const cuuint64_t se[2] = {(cuuint64_t)pl.W * 4, (cuuint64_t)pl.W * pl.H * 4};
     if (encode(&me, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(e), de, se, box, estr,
@@ -343,7 +345,7 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             CUtensorMap me, ms;
             std::memset(&me, 0, sizeof(me));
             std::memset(&ms, 0, sizeof(ms));
-            const int use_tma = (P != P_FP64 && encode_trace_maps(pl, e, s, me, ms)) ? 1 : 0;
+            const int use_tma = (P != P_FP64 && encode_image_maps(pl, e, s, TR_REG, TR_REG, me, ms)) ? 1 : 0;
             k_trace012<P, C><<<grid, 256, smem, st>>>(pl, ef, sf, ed, sd, qsel < 0 ? 15 : (1 << qsel), me, ms, use_tma);
             rec->end();
             ++*launches;

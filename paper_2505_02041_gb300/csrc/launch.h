@@ -1,5 +1,7 @@
 // launch.h -- host-side entry points of the kernel translation units.
 #pragma once
+
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -146,6 +148,12 @@ cudaError_t launch_r0(const Plan &pl, cudaStream_t st);
 
 // Reads and clears the bulk-copy kernels' timeout status (0 or 5).
 cudaError_t read_bulk_status(int *status);
+cudaError_t read_adj_bulk_status(int *status);
+
+// Tensor maps of fp32 emission / extinction for TMA tile staging (false when
+// the layout does not allow them).
+bool encode_image_maps(const Plan &pl, const void *e, const void *s, int box_x, int box_y, CUtensorMap &me,
+                       CUtensorMap &ms);
 
 double bytes_T(const Plan &pl, int q, int n);
 double bytes_T_odd(const Plan &pl, int q, int n);

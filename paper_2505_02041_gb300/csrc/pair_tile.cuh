@@ -18,6 +18,7 @@
 
 #include <type_traits>
 
+#include "bulk_copy.cuh"
 #include "hrc_internal.cuh"
 #include "trace_shapes.cuh"
 
@@ -134,6 +135,76 @@ template <class A, int C> struct PairTile {
                 s[o] = sg;
             }
         }
+    }
+    // The same staging with the region of e and sigma fetched by TMA tensor
+    // copies (fp32; box PT_RU x PT_RV along image x, y for pair 0, PT_RV x
+    // PT_RU for pair 1; zero outside the grid = vacuum).  The boxes land in a
+    // staging area overlapping the tw planes: every thread takes its pixels
+    // into registers first, then the planes are written.  False when the
+    // copy wait gave up.
+    __device__ __forceinline__ bool stage_tma(int pair, int x0, int y0, const CUtensorMap *tme, const CUtensorMap *tms,
+                                              uint64_t *bar, long long limit_ns) {
+        static_assert(sizeof(A) == 4, "fp32 staging");
+        constexpr int BOX = PT_RU * PT_RV;
+        constexpr int PER = (BOX + 255) / 256;
+        static_assert((C + 1) * BOX * 4 <= 3 * PT_PLANE * 8, "staging fits the tw planes");
+        float *stg = reinterpret_cast<float *>(tw);   // [C + 1][BOX]
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect(bar, (unsigned)((C + 1) * BOX * sizeof(float)));
+#pragma unroll
+            for (int c = 0; c < C; ++c) tma_load_3d(stg + c * BOX, tme, x0 - PT_HALO, y0 - PT_HALO, c, bar);
+            tma_load_2d(stg + C * BOX, tms, x0 - PT_HALO, y0 - PT_HALO, bar);
+        }
+        if (!mbar_wait(bar, 0, limit_ns)) {
+            mbar_wait(bar, 0, limit_ns);
+            return false;
+        }
+        float sv[PER], ev[PER][C];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + 256 * k;
+            if (i >= BOX) break;
+            sv[k] = stg[C * BOX + i];
+#pragma unroll
+            for (int c = 0; c < C; ++c) ev[k][c] = stg[c * BOX + i];
+        }
+        __syncthreads();
+        const int nx = pair == 0 ? PT_RU : PT_RV;     // box extent along image x
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = threadIdx.x + 256 * k;
+            if (i >= BOX) break;
+            const int ix = i % nx, iy = i / nx;
+            const int a = pair == 0 ? ix : iy, b = pair == 0 ? iy : ix;
+            const int o = a * PT_PITCH + b;
+            const A sg = sv[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const A len = class_len<A>(c);
+                const A m = fexpm1(-sg * len);
+                V2 p;
+                p.x = A(1) + m;
+                p.y = sg != A(0) ? -m / sg : len;
+                tw[c * PT_PLANE + o] = p;
+                dw[c * PT_PLANE + o] = dw_dsigma(sg, len, p.x);
+            }
+            if constexpr (PackES<A, C>::packed) {
+                float4 v = make_float4(ev[k][0], 0.f, 0.f, sg);
+                if constexpr (C > 1) v.y = ev[k][1];
+                if constexpr (C > 2) v.z = ev[k][2];
+                es4[o] = v;
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) e[c * PT_PLANE + o] = ev[k][c];
+                s[o] = sg;
+            }
+        }
+        return true;
     }
 };
 
