@@ -65,15 +65,17 @@ def test_backward_fp64_vs_oracle(W, H, C, seed):
 
 
 def test_backward_fp64_central_differences_256():
-    """Differentiable HRC on 256x256, C=1 (four scenes of the batch-16
-    workload, seeds 100+b, fog/disks/rectangles with C=1): loss
-    ||F(e, s) - F_target||^2 with F_target from a hidden scene (seed 1000+b);
-    adjoint vs FP64 central differences (h = 1e-3) at 64 seeded pixels."""
+    """Differentiable HRC on 256x256, C=1, the whole batch of 16 scenes
+    (seeds 100+b, fog/disks/rectangles with C=1): loss ||F(e, s) - F_target||^2
+    with F_target from a hidden scene (seed 1000+b); the backward recomputes
+    every cascade level from the inputs (hrc_set_backward_recompute); adjoint
+    vs FP64 central differences (h = 1e-3) at 64 seeded pixels per scene."""
     require_gpu()
     from paper_2505_02041_gb300 import HRC
     h = HRC(256, 256, 1, 0, "fp64")
+    h.set_backward_recompute(True)
     pix = scenes.rng(7).integers(0, 256, size=(64, 2))
-    for b in range(4):
+    for b in range(16):
         e, s = scenes.scene_disks_rects_fog(256, 256, 1, 100 + b)
         et, _ = scenes.scene_disks_rects_fog(256, 256, 1, 1000 + b)
         ed, sd = to_dev(e, torch.float64), to_dev(s, torch.float64)
@@ -83,22 +85,29 @@ def test_backward_fp64_central_differences_256():
         ge, gs = h.backward(gF.contiguous(), ed, sd)
         ge, gs = ge.cpu().numpy(), gs.cpu().numpy()
 
-        def loss(ee, ss):
-            return float(torch.sum((h.forward(ee, ss) - Ft) ** 2))
-
         hstep = 1e-3
-        # rounding floor of a central difference of the loss in fp64
-        floor = 16 * np.finfo(np.float64).eps * loss(ed, sd) / hstep
+        eps = np.finfo(np.float64).eps
+
+        def central(ep, sp, em, sm):
+            """(loss(+) - loss(-)) / 2h formed pixel by pixel as
+            sum (F+ - F-)(F+ + F- - 2 F_t) / 2h, which avoids cancelling two
+            large sums; with the rounding floor of that form."""
+            Fp = h.forward(ep, sp).clone()
+            Fm = h.forward(em, sm)
+            fd = float(torch.sum((Fp - Fm) * (Fp + Fm - 2 * Ft))) / (2 * hstep)
+            floor = 64 * eps * float(torch.sum((Fp.abs() + Fm.abs()) * (Fp + Fm - 2 * Ft).abs())) / (2 * hstep)
+            return fd, floor
+
         for (y, x) in pix:
             ep, em = ed.clone(), ed.clone()
             ep[0, y, x] += hstep
             em[0, y, x] -= hstep
-            fd = (loss(ep, sd) - loss(em, sd)) / (2 * hstep)
+            fd, floor = central(ep, sd, em, sd)
             assert abs(fd - ge[0, y, x]) <= 1e-7 * abs(fd) + floor, (b, y, x, fd, ge[0, y, x], floor)
             sp, sm = sd.clone(), sd.clone()
             sp[y, x] += hstep
             sm[y, x] -= hstep
-            fd = (loss(ed, sp) - loss(ed, sm)) / (2 * hstep)
+            fd, floor = central(ed, sp, ed, sm)
             assert abs(fd - gs[y, x]) <= 1e-5 * abs(fd) + floor, (b, y, x, fd, gs[y, x], floor)
 
 
