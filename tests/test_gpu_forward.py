@@ -109,14 +109,27 @@ def test_forward_full_size_workloads(name):
     assert err_max(F, oracle.fluence(e, s)) <= TOL
 
 
-def test_forward_host_entry_matches_device_entry():
+@pytest.mark.parametrize("W,H", [(70, 50), (64, 48)])
+def test_forward_host_entry_matches_device_entry(W, H):
+    """Host buffers, pinned or pageable, staged through device copies: the
+    fluence equals the device entry point's exactly, and a backward after it
+    equals the oracle's."""
     require_gpu()
     from paper_2505_02041_gb300 import HRC
-    e, s = scenes.random_scene(70, 50, 3, 13)
-    h = HRC(70, 50, 3)
+    e, s = scenes.random_scene(W, H, 3, 13)
+    h = HRC(W, H, 3)
     Fd = h.forward(to_dev(e), to_dev(s)).cpu()
-    Fh = h.forward_host(torch.from_numpy(e).pin_memory(), torch.from_numpy(s).pin_memory())
-    assert torch.equal(Fd, Fh)
+    gF = scenes.rng(14).normal(size=e.shape).astype(np.float32)
+    ge_r, gs_r = oracle.fluence_adjoint(e, s, gF)
+    for pinned in (True, False):
+        et, st = torch.from_numpy(e.copy()), torch.from_numpy(s.copy())
+        if pinned:
+            et, st = et.pin_memory(), st.pin_memory()
+        out = torch.empty((3, H, W), dtype=torch.float32, pin_memory=pinned)
+        Fh = h.forward_host(et, st, out)
+        assert torch.equal(Fd, Fh), pinned
+        ge, gs = h.backward(to_dev(gF))
+        assert err_max(ge.cpu().numpy(), ge_r) <= 1e-4 and err_max(gs.cpu().numpy(), gs_r) <= 1e-4
 
 
 def test_autotune_keeps_results():
