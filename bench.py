@@ -58,6 +58,15 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def traffic_key(kind, cfg):
+    """The kernel variant whose DRAM bytes stand for `kind`: the merge down
+    has a per-thread-load kernel (mdown 0) and a bulk-copy-staged one
+    (mdown 1), each with its own line."""
+    if kind == "merge_down" and cfg.get("mdown", 0) == 1:
+        return "merge_down_bulk"
+    return kind
+
+
 def ncu_traffic(kind, workload):
     """Per-launch DRAM bytes of `kind` from the committed ncu summary, if it
     was taken on the current kernel sources."""
@@ -390,7 +399,7 @@ def run_ours(args):
                    "baseline_context": "paper Table 1 on an RTX 3080 Laptop with fp16 storage"},
         "roofline": {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                     "traffic": ncu_traffic(kind, args.workload),
+                     "traffic": ncu_traffic(traffic_key(kind, h.launch_config), args.workload),
                      "timing": "per-launch CUDA events on the launching stream (timed region 3)"},
         "frame": {"algorithmic_bytes": frame_bytes, "GBps": frame_bytes / (ms_per_frame * 1e-3) / 1e9,
                   "frac_of_peak": frame_bytes / (ms_per_frame * 1e-3) / 1e9 / hbm_peak,
