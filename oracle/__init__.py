@@ -5,7 +5,7 @@ benchmark's CPU-baseline leg use it to check and time the CUDA path.  The
 product package never imports it, and it shares no code with the product.
 
 ``hrc_oracle.c`` follows Algorithm 1 and Eqs. 7-20 step by step in double
-precision; ``recursive.py`` is a second, independent formulation of
+precision, and the cross blur of Eq. 21 (Sec. 4.2) with its adjoint; ``recursive.py`` is a second, independent formulation of
 Eqs. 14-20 (memoised recursion, pure Python, tiny grids only).
 
 Images are numpy arrays: emission ``e[C][H][W]`` and extinction ``s[H][W]``.
@@ -54,6 +54,10 @@ def _declare(L):
     L.orc_fluence_adjoint.restype = None
     L.orc_bruteforce.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
     L.orc_bruteforce.restype = None
+    L.orc_cross_blur.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
+    L.orc_cross_blur.restype = None
+    L.orc_cross_blur_adjoint.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
+    L.orc_cross_blur_adjoint.restype = None
     L.orc_num_threads.argtypes = []
     L.orc_num_threads.restype = ctypes.c_int
     L.orc_set_num_threads.argtypes = [ctypes.c_int]
@@ -166,6 +170,36 @@ def fluence_adjoint(e, s, gF, cascades: int = 0):
     gs = np.zeros((H, W))
     lib().orc_fluence_adjoint(_p(e), _p(s), _p(gF), C, W, H, cascades, _p(ge), _p(gs))
     return ge, gs
+
+
+def cross_blur(F, s, threshold: float = 0.5) -> np.ndarray:
+    """The cross blur of Eq. 21 with opacity rejection (Sec. 4.2): each pixel
+    averages itself (weight 4) with the edge neighbours (weight 1) inside the
+    grid whose opacity 1 - exp(-sigma) is within `threshold` of its own, the
+    kept weights renormalised.  F[C][H][W] -> float64 [C][H][W]."""
+    F, s, C, H, W = _img(F, s)
+    out = np.zeros((C, H, W))
+    lib().orc_cross_blur(_p(F), _p(s), C, W, H, float(threshold), _p(out))
+    return out
+
+
+def cross_blur_adjoint(g, s, threshold: float = 0.5) -> np.ndarray:
+    """Transpose of cross_blur for fixed sigma: dL/dF from dL/d(blurred F)."""
+    g, s, C, H, W = _img(g, s)
+    gF = np.zeros((C, H, W))
+    lib().orc_cross_blur_adjoint(_p(g), _p(s), C, W, H, float(threshold), _p(gF))
+    return gF
+
+
+def fluence_blurred(e, s, threshold: float = 0.5, cascades: int = 0) -> np.ndarray:
+    """Algorithm 1 (Lighting) followed by the cross blur of Eq. 21."""
+    return cross_blur(fluence(e, s, cascades), s, threshold)
+
+
+def fluence_blurred_adjoint(e, s, gF, threshold: float = 0.5, cascades: int = 0):
+    """Gradient of sum(gF * fluence_blurred(e, s)) w.r.t. (e, s); the blur's
+    kept set is held fixed (its dependence on s is piecewise constant)."""
+    return fluence_adjoint(e, s, cross_blur_adjoint(gF, s, threshold), cascades)
 
 
 def bruteforce(e, s, M: int = 4096) -> np.ndarray:

@@ -673,6 +673,77 @@ void orc_bruteforce(const double *e, const double *s, int C, int W, int H, int M
     frame_free(&f);
 }
 
+/* ---------------------------------------------------------------------------
+ * Cross blur (Sec. 4.2, Eq. 21).  After the four quadrants are summed, each
+ * pixel becomes the weighted mean of itself (weight 4) and its four edge
+ * neighbours (weight 1 each), the 1/8 of Eq. 21, leaving out the neighbours
+ * whose opacity differs significantly from the pixel's.  The paper gives no
+ * measure or threshold; the reading used here: opacity is the absorptance of
+ * one pixel length, alpha = 1 - exp(-sigma); a neighbour is kept iff it lies
+ * inside the grid and |alpha_m - alpha_c| <= thr; the kept weights are
+ * renormalised to sum to 1 (so the interior with every neighbour kept is
+ * exactly Eq. 21).
+ * ------------------------------------------------------------------------ */
+static const int blur_dx[4] = {1, -1, 0, 0}, blur_dy[4] = {0, 0, 1, -1};
+
+static int blur_keep(const double *s, int W, int H, long x, long y, long xm, long ym, double thr)
+{
+    if (xm < 0 || xm >= W || ym < 0 || ym >= H) return 0;
+    double ac = 1.0 - exp(-s[y * W + x]);
+    double am = 1.0 - exp(-s[ym * W + xm]);
+#if ORC_MUTANT == 17
+    ac = s[y * W + x];
+    am = s[ym * W + xm];
+#endif
+    return fabs(am - ac) <= thr;
+}
+
+/* out = B F: the blurred image (F, out: [C][H][W]; s: [H][W]). */
+void orc_cross_blur(const double *F, const double *s, int C, int W, int H, double thr, double *out)
+{
+    const double wc = ORC_MUTANT == 15 ? 2.0 : 4.0;
+    for (long y = 0; y < H; ++y)
+        for (long x = 0; x < W; ++x) {
+            double wsum = wc;
+            double acc[8];
+            for (int c = 0; c < C; ++c) acc[c] = wc * F[((size_t)c * H + y) * W + x];
+            for (int d = 0; d < 4; ++d) {
+                long xm = x + blur_dx[d], ym = y + blur_dy[d];
+                if (!blur_keep(s, W, H, x, y, xm, ym, thr)) continue;
+                wsum += 1.0;
+                for (int c = 0; c < C; ++c) acc[c] += F[((size_t)c * H + ym) * W + xm];
+            }
+            if (ORC_MUTANT == 16) wsum = 8.0;
+            for (int c = 0; c < C; ++c) out[((size_t)c * H + y) * W + x] = acc[c] / wsum;
+        }
+}
+
+/* gF = B^T g, the adjoint of the blur for fixed s, by scattering each
+ * output pixel's weights back onto the pixels it read.  The kept set depends
+ * on s only through the threshold test, which is piecewise constant, so the
+ * blur contributes nothing to dL/dsigma (away from the measure-zero set where
+ * a pair sits exactly at the threshold). */
+void orc_cross_blur_adjoint(const double *g, const double *s, int C, int W, int H, double thr, double *gF)
+{
+    memset(gF, 0, sizeof(double) * (size_t)C * W * H);
+    for (long y = 0; y < H; ++y)
+        for (long x = 0; x < W; ++x) {
+            double wsum = 4.0;
+            for (int d = 0; d < 4; ++d)
+                wsum += blur_keep(s, W, H, x, y, x + blur_dx[d], y + blur_dy[d], thr) ? 1.0 : 0.0;
+            for (int c = 0; c < C; ++c) {
+                const double gc = g[((size_t)c * H + y) * W + x] / wsum;
+                gF[((size_t)c * H + y) * W + x] += 4.0 * gc;
+                for (int d = 0; d < 4; ++d) {
+                    long xm = x + blur_dx[d], ym = y + blur_dy[d];
+                    if (!blur_keep(s, W, H, x, y, xm, ym, thr)) continue;
+                    if (ORC_MUTANT == 18) gF[((size_t)c * H + y) * W + x] += gc;
+                    else gF[((size_t)c * H + ym) * W + xm] += gc;
+                }
+            }
+        }
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -35,6 +35,10 @@ MUTANTS = {
     12: "adjoint weight of R_{n+1}(p, j)",
     13: "adjoint sign of the suffix-radiance term",
     14: "Eq. 14 arcs of level n",
+    15: "Eq. 21 centre weight",
+    16: "cross blur without renormalisation of the kept weights",
+    17: "cross blur threshold on extinction instead of opacity",
+    18: "cross blur adjoint scattered onto the wrong pixel",
 }
 
 
@@ -81,6 +85,30 @@ def failed_pins(O):
         if abs(fd - gs[y, x]) > 1e-6 * max(1.0, abs(fd)):
             bad.append("fd")
             break
+    bad += failed_blur_pins(O)
+    return bad
+
+
+def failed_blur_pins(O):
+    """The cross-blur pins (Eq. 21): action on a quadratic, constants under
+    rejections, the threshold side of a hand-built row, the adjoint's
+    dot-product identity."""
+    bad = []
+    y, x = np.mgrid[0:7, 0:9].astype(np.float64)
+    B = O.cross_blur((x * x + 3 * y * y)[None], np.full((7, 9), 0.3))[0]
+    if np.max(np.abs(B[1:-1, 1:-1] - (x * x + 3 * y * y + 1.0)[1:-1, 1:-1])) > 1e-12:
+        bad.append("blur-quadratic")
+    g = np.random.default_rng(3)
+    s = g.choice([0.0, 0.7, 3.0, 50.0], size=(8, 6))
+    if np.max(np.abs(O.cross_blur(np.full((1, 8, 6), 2.0), s) - 2.0)) > 1e-14:
+        bad.append("blur-constant")
+    row = np.array([[-math.log(0.6), 0.0, -math.log(0.4)]])
+    if abs(O.cross_blur(np.array([[[0.0, 1.0, 0.0]]]), row)[0, 0, 1] - 0.8) > 1e-15:
+        bad.append("blur-threshold")
+    F = g.normal(size=(2, 8, 6))
+    G = g.normal(size=(2, 8, 6))
+    if abs(np.sum(O.cross_blur(F, s) * G) - np.sum(F * O.cross_blur_adjoint(G, s))) > 1e-12:
+        bad.append("blur-adjoint")
     return bad
 
 
