@@ -58,6 +58,32 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def bench_cross_blur(h, fwd, fwd_bwd, timed, gF, gE, gS, hbm_peak, thr=0.5, steps=10):
+    """The frame with the Eq. 21 cross blur on (graph-launched forward and
+    forward+backward), and the blur kernels' own per-launch times against
+    their algorithmic bytes ((2C + 1) fp32 planes per pixel each)."""
+    from paper_2505_02041_gb300 import _lib
+    h.set_cross_blur(True, thr)
+    for _ in range(3):
+        fwd_bwd()
+    f_ms = timed(fwd, steps)
+    fb_ms = timed(fwd_bwd, steps)
+    _lib.hrc_set_timing(h.ctx, True)
+    kf, kb = {}, {}
+    timed(fwd, steps, kf)
+    timed(lambda: _lib.hrc_fluence_backward(h.ctx, gF, gE, gS), steps, kb)
+    _lib.hrc_set_timing(h.ctx, False)
+    h.set_cross_blur(False)
+    out = {"threshold": thr, "forward_ms": statistics.mean(f_ms), "fwd_bwd_ms": statistics.mean(fb_ms)}
+    for name, d in (("cross_blur", kf.get("cross_blur")), ("adj_cross_blur", kb.get("adj_cross_blur"))):
+        if d:
+            us = d[0] / d[2] * 1e3
+            by = d[1] / d[2]
+            out[name] = {"us": us, "bytes": by, "GBps": by / (us * 1e-6) / 1e9,
+                         "frac_of_peak": by / (us * 1e-6) / 1e9 / hbm_peak}
+    return out
+
+
 def traffic_key(kind, cfg):
     """The kernel variant whose DRAM bytes stand for `kind`: the merge down
     has a per-thread-load kernel (mdown 0) and a bulk-copy-staged one
@@ -430,6 +456,7 @@ def run_ours(args):
                               "note": "gpu_launches counts the forward frames timed for value"},
         "clocks": clk,
     }
+    line["cross_blur"] = bench_cross_blur(h, fwd, fwd_bwd, timed, gF, gE, gS, hbm_peak)
     if args.precisions and world == 1:
         import oracle
         Fr = oracle.fluence(e_np, s_np)

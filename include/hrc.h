@@ -150,6 +150,26 @@ hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_e
  * costs about one forward pass. */
 hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on);
 
+/* Cross blur (Sec. 4.2, Eq. 21), applied after the fluence sum by every
+ * later hrc_fluence / hrc_fluence_host / hrc_fluence_f64 on a single-scene
+ * context, and differentiated by the matching backward.  Each pixel becomes
+ * the mean of itself (weight 4) and its four edge neighbours (weight 1
+ * each), leaving out neighbours outside the grid and those whose opacity
+ * 1 - exp(-sigma_t) differs from the pixel's by more than `threshold`; the
+ * kept weights are renormalised, so the interior with every neighbour kept
+ * is exactly 1/8 [0 1 0; 1 4 1; 0 1 0].  The paper does not state the
+ * opacity measure or threshold; 0.5 is this library's default reading.
+ * The kept set is piecewise constant in sigma_t, so the blur adds nothing
+ * to dLoss/d sigma_t; its adjoint is the transpose for fixed sigma_t.
+ *   enable:    0 = off (the default), 1 = on;
+ *   threshold: opacity difference in [0, 1] (1 keeps every neighbour).
+ * The first enable allocates one context-owned buffer of W * H * C doubles
+ * (the unblurred fluence, and dLoss/d(unblurred fluence) in the backward).
+ * HRC_EINVAL for other values or on a batched context; HRC_ENOMEM if the
+ * buffer does not fit.  hrc_fluence_noalloc never blurs. */
+hrc_status hrc_set_cross_blur(hrc_ctx *ctx, int enable, float threshold);
+hrc_status hrc_get_cross_blur(const hrc_ctx *ctx, int *enable, float *threshold);
+
 /* Waits for the context's stream and reports whether a bounded device-side
  * wait of the bulk-copy merge-down kernel gave up since the last call
  * (HRC_ETIMEOUT: that launch ended early and its outputs are incomplete;
@@ -271,7 +291,7 @@ int hrc_last_launch_count(const hrc_ctx *ctx);
  * the last compute call; it returns the number of records (or -1 on error).
  * `kind`: 0 trace T_0..T_2, 1 merge up, 2 merge down, 3 fluence sum,
  * 4 adjoint sum, 5 adjoint merge down, 6 adjoint merge up, 7 adjoint trace,
- * 8 batched persistent kernel, 9 other.  `bytes` is the launch's
+ * 8 batched persistent kernel, 9 other, 10 cross blur, 11 adjoint cross blur.  `bytes` is the launch's
  * algorithmic traffic (each array it consumes read once, each array it
  * produces written once). */
 typedef struct { int kind; int level; float ms; double bytes; } hrc_kernel_time;

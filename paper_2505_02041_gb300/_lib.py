@@ -30,6 +30,8 @@ SIGNATURES = [
     ("hrc_autotune", _i, [_vp, ctypes.POINTER(ctypes.c_float)]),
     ("hrc_set_backward_recompute", _i, [_vp, _i]),
     ("hrc_sync", _i, [_vp]),
+    ("hrc_set_cross_blur", _i, [_vp, _i, ctypes.c_float]),
+    ("hrc_get_cross_blur", _i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
     ("hrc_debug_bulk_wait", _i, [_vp, _i, ctypes.c_longlong]),
     ("hrc_get_launch_config", _i, [_vp, _vp]),
     ("hrc_set_launch_config", _i, [_vp, _vp]),
@@ -123,6 +125,18 @@ def hrc_set_schedule(ctx, schedule: int):
 
 def hrc_set_backward_recompute(ctx, on: bool):
     check(load().hrc_set_backward_recompute(ctx, int(bool(on))), ctx)
+
+
+def hrc_set_cross_blur(ctx, enable: bool, threshold: float = 0.5):
+    check(load().hrc_set_cross_blur(ctx, int(bool(enable)), float(threshold)), ctx)
+
+
+def hrc_get_cross_blur(ctx):
+    """(enabled, threshold) of the context's cross blur."""
+    en = _i()
+    th = ctypes.c_float()
+    check(load().hrc_get_cross_blur(ctx, ctypes.byref(en), ctypes.byref(th)), ctx)
+    return bool(en.value), th.value
 
 
 class hrc_launch_config(ctypes.Structure):
@@ -244,7 +258,7 @@ class hrc_kernel_time(ctypes.Structure):
 
 
 KERNEL_KINDS = ["trace012", "merge_up", "merge_down", "fluence_sum", "adj_sum", "adj_merge_down",
-                "adj_merge_up", "adj_trace", "batched", "other"]
+                "adj_merge_up", "adj_trace", "batched", "other", "cross_blur", "adj_cross_blur"]
 
 
 def hrc_set_timing(ctx, enable: bool):

@@ -156,9 +156,20 @@ class HRC:
         see hrc_set_backward_recompute."""
         _lib.hrc_set_backward_recompute(self.ctx, on)
 
+    def set_cross_blur(self, enable: bool = True, threshold: float = 0.5) -> None:
+        """Cross blur of Eq. 21 after the fluence sum, leaving out neighbours
+        whose opacity 1 - exp(-sigma) differs by more than `threshold`
+        (see hrc_set_cross_blur); the backward differentiates it."""
+        _lib.hrc_set_cross_blur(self.ctx, enable, threshold)
+
+    @property
+    def cross_blur(self):
+        """(enabled, threshold)."""
+        return _lib.hrc_get_cross_blur(self.ctx)
+
     @property
     def launch_config(self) -> dict:
-        """{schedule, groups, threads, vmajor} (see hrc_launch_config)."""
+        """{schedule, groups, threads, vmajor, mdown} (see hrc_launch_config)."""
         return _lib.hrc_get_launch_config(self.ctx)
 
     def set_launch_config(self, schedule=0, groups=1, threads=128, vmajor=0, mdown=0) -> None:

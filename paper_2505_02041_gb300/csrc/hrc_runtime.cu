@@ -193,6 +193,9 @@ struct hrc_ctx {
     const void *last_e = nullptr, *last_s = nullptr;
     bool have_fwd = false;
     bool bwd_recompute = false;  // backward recomputes the levels instead of reading the forward's
+    bool blur = false;           // cross blur (Eq. 21) after the fluence sum
+    float blur_thr = 0.5f;       // its opacity threshold
+    void *blur_buf = nullptr;    // W * H * C doubles: unblurred F, or dL/d(unblurred F)
     int launches = 0;
     Recorder rec;
     std::string err;
@@ -434,6 +437,7 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->dev_e);
     cudaFree(ctx->dev_s);
     cudaFree(ctx->dev_F);
+    cudaFree(ctx->blur_buf);
     for (auto &g : ctx->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     cudaFree(ctx->d_plans);
@@ -516,6 +520,33 @@ hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on) {
     if (!ctx) return HRC_EINVAL;
     if (on != 0 && on != 1) return fail(ctx, HRC_EINVAL, "hrc_set_backward_recompute: 0 or 1");
     ctx->bwd_recompute = on != 0;
+    return HRC_OK;
+}
+
+hrc_status hrc_set_cross_blur(hrc_ctx *ctx, int enable, float threshold) {
+    if (!ctx) return HRC_EINVAL;
+    if (ctx->batched) return fail(ctx, HRC_EINVAL, "hrc_set_cross_blur: single-scene contexts only");
+    if ((enable != 0 && enable != 1) || !(threshold >= 0.f && threshold <= 1.f))
+        return fail(ctx, HRC_EINVAL, "hrc_set_cross_blur: enable 0 or 1, threshold in [0, 1]");
+    if (enable && !ctx->blur_buf) {
+        const size_t bytes = (size_t)ctx->W * ctx->H * ctx->C * sizeof(double);
+        cudaError_t e = cudaMalloc(&ctx->blur_buf, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->blur_buf = nullptr;
+            return fail(ctx, HRC_ENOMEM, "hrc_set_cross_blur: buffer of " + std::to_string(bytes) + " bytes does not fit");
+        }
+    }
+    ctx->blur = enable != 0;
+    ctx->blur_thr = threshold;
+    clear_graphs(ctx);   // the graphs hold the pass as it was captured
+    return HRC_OK;
+}
+
+hrc_status hrc_get_cross_blur(const hrc_ctx *ctx, int *enable, float *threshold) {
+    if (!ctx || !enable || !threshold) return HRC_EINVAL;
+    *enable = ctx->blur ? 1 : 0;
+    *threshold = ctx->blur_thr;
     return HRC_OK;
 }
 
@@ -665,8 +696,15 @@ hrc_status hrc_fluence(hrc_ctx *ctx, const float *emission, const float *sigma_t
         return fail(ctx, HRC_EINVAL, "hrc_fluence: pointers must be 16-byte aligned");
     const Plan pl = ctx->plan;
     const RayTable *rt = &ctx->rt;
+    void *Fr = ctx->blur ? ctx->blur_buf : nullptr;
+    const double thr = ctx->blur_thr;
     st = run_pass(ctx, 0, emission, sigma_t, out, nullptr, nullptr,
-                  [&](cudaStream_t s, int *n, Recorder *r) { return launch_forward(pl, *rt, emission, sigma_t, out, s, n, r); },
+                  [&](cudaStream_t s, int *n, Recorder *r) {
+                      if (!Fr) return launch_forward(pl, *rt, emission, sigma_t, out, s, n, r);
+                      cudaError_t e = launch_forward(pl, *rt, emission, sigma_t, Fr, s, n, r);
+                      if (e != cudaSuccess) return e;
+                      return launch_cross_blur(pl, Fr, sigma_t, out, thr, s, n, r);
+                  },
                   "hrc_fluence");
     if (st != HRC_OK) return st;
     ctx->last_e = emission;
@@ -700,8 +738,15 @@ hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *s
         return fail(ctx, HRC_EINVAL, "hrc_fluence_f64: pointers must be 16-byte aligned");
     const Plan pl = ctx->plan64;
     const RayTable *rt = &ctx->rt;
+    void *Fr = ctx->blur ? ctx->blur_buf : nullptr;
+    const double thr = ctx->blur_thr;
     st = run_pass(ctx, 2, emission, sigma_t, out, nullptr, nullptr,
-                  [&](cudaStream_t s, int *n, Recorder *r) { return launch_forward(pl, *rt, emission, sigma_t, out, s, n, r); },
+                  [&](cudaStream_t s, int *n, Recorder *r) {
+                      if (!Fr) return launch_forward(pl, *rt, emission, sigma_t, out, s, n, r);
+                      cudaError_t e = launch_forward(pl, *rt, emission, sigma_t, Fr, s, n, r);
+                      if (e != cudaSuccess) return e;
+                      return launch_cross_blur(pl, Fr, sigma_t, out, thr, s, n, r);
+                  },
                   "hrc_fluence_f64");
     if (st != HRC_OK) return st;
     ctx->last_e = emission;
@@ -722,9 +767,15 @@ hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_e
     const RayTable *rt = &ctx->rt;
     const void *le = ctx->last_e, *ls = ctx->last_s;
     const bool rc = ctx->bwd_recompute;
+    void *gFr = ctx->blur ? ctx->blur_buf : nullptr;
+    const double thr = ctx->blur_thr;
     return run_pass(ctx, rc ? 4 : 1, le, ls, grad_F, grad_emission, grad_sigma_t,
                     [&](cudaStream_t s, int *n, Recorder *r) {
-                        return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, s, n, r);
+                        if (!gFr)
+                            return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, s, n, r);
+                        cudaError_t e = launch_cross_blur_adj(pl, grad_F, ls, gFr, thr, s, n, r);
+                        if (e != cudaSuccess) return e;
+                        return launch_backward(pl, *rt, le, ls, gFr, grad_emission, grad_sigma_t, rc, s, n, r);
                     },
                     "hrc_fluence_backward");
 }
@@ -741,9 +792,15 @@ hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *
     const RayTable *rt = &ctx->rt;
     const void *le = ctx->last_e, *ls = ctx->last_s;
     const bool rc = ctx->bwd_recompute;
+    void *gFr = ctx->blur ? ctx->blur_buf : nullptr;
+    const double thr = ctx->blur_thr;
     return run_pass(ctx, rc ? 5 : 3, le, ls, grad_F, grad_emission, grad_sigma_t,
                     [&](cudaStream_t s, int *n, Recorder *r) {
-                        return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, s, n, r);
+                        if (!gFr)
+                            return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, s, n, r);
+                        cudaError_t e = launch_cross_blur_adj(pl, grad_F, ls, gFr, thr, s, n, r);
+                        if (e != cudaSuccess) return e;
+                        return launch_backward(pl, *rt, le, ls, gFr, grad_emission, grad_sigma_t, rc, s, n, r);
                     },
                     "hrc_fluence_backward_f64");
 }

@@ -14,7 +14,7 @@ namespace hrc {
 enum KernelKind {
     K_TRACE012 = 0, K_MERGE_UP = 1, K_MERGE_DOWN = 2, K_FLUENCE_SUM = 3,
     K_ADJ_SUM = 4, K_ADJ_MERGE_DOWN = 5, K_ADJ_MERGE_UP = 6, K_ADJ_TRACE = 7,
-    K_BATCHED = 8, K_OTHER = 9
+    K_BATCHED = 8, K_OTHER = 9, K_CROSS_BLUR = 10, K_ADJ_CROSS_BLUR = 11
 };
 
 // Optional per-launch CUDA-event timing (off by default).  Events come from
@@ -136,6 +136,15 @@ cudaError_t launch_backward(const Plan &pl, const RayTable &rt, const void *e, c
 cudaError_t prepare_forward_kernels();
 cudaError_t prepare_backward_kernels();
 cudaError_t prepare_device_once();
+
+// Cross blur of Eq. 21 with opacity rejection (kernels_blur.cu): F = B Fr,
+// and its transpose gFr = B^T g for fixed sigma; arrays [C][H][W] (fp64 for
+// P_FP64, else fp32), s = sigma_t [H][W].
+cudaError_t launch_cross_blur(const Plan &pl, const void *Fr, const void *s, void *F, double thr, cudaStream_t st,
+                              int *launches, Recorder *rec);
+cudaError_t launch_cross_blur_adj(const Plan &pl, const void *g, const void *s, void *gFr, double thr,
+                                  cudaStream_t st, int *launches, Recorder *rec);
+double bytes_cross_blur(const Plan &pl);
 
 // Dense fp32 copy of level n of frame q (which = 0: T_n, 1: R_n).
 cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *dst, cudaStream_t st);

@@ -72,6 +72,8 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.hrc_batched_sync(None) == _lib.HRC_EINVAL
     assert lib.hrc_batched_schedule(None, 1) == _lib.HRC_EINVAL
     assert lib.hrc_set_backward_recompute(None, 1) == _lib.HRC_EINVAL
+    assert lib.hrc_set_cross_blur(None, 1, 0.5) == _lib.HRC_EINVAL
+    assert lib.hrc_get_cross_blur(None, None, None) == _lib.HRC_EINVAL
     assert lib.hrc_sync(None) == _lib.HRC_EINVAL
     assert lib.hrc_debug_bulk_wait(None, 0, 0) == _lib.HRC_EINVAL
     assert lib.hrc_get_launch_config(None, None) == _lib.HRC_EINVAL
