@@ -5,8 +5,11 @@ benchmark's CPU-baseline leg use it to check and time the CUDA path.  The
 product package never imports it, and it shares no code with the product.
 
 ``hrc_oracle.c`` follows Algorithm 1 and Eqs. 7-20 step by step in double
-precision, and the cross blur of Eq. 21 (Sec. 4.2) with its adjoint; ``recursive.py`` is a second, independent formulation of
-Eqs. 14-20 (memoised recursion, pure Python, tiny grids only).
+precision, and the cross blur of Eq. 21 (Sec. 4.2) with its adjoint.  The
+multi-bounce iteration of Sec. 4.2 (fluence fed back as a scattering
+source) is composed from them here, in numpy.  ``recursive.py`` is a
+second, independent formulation of Eqs. 14-20 (memoised recursion, pure
+Python, tiny grids only).
 
 Images are numpy arrays: emission ``e[C][H][W]`` and extinction ``s[H][W]``.
 """
@@ -200,6 +203,68 @@ def fluence_blurred_adjoint(e, s, gF, threshold: float = 0.5, cascades: int = 0)
     """Gradient of sum(gF * fluence_blurred(e, s)) w.r.t. (e, s); the blur's
     kept set is held fixed (its dependence on s is piecewise constant)."""
     return fluence_adjoint(e, s, cross_blur_adjoint(gF, s, threshold), cascades)
+
+
+def _lighting(e, s, cascades, blur):
+    return fluence(e, s, cascades) if blur is None else fluence_blurred(e, s, blur, cascades)
+
+
+def _lighting_adjoint(e, s, g, cascades, blur):
+    if blur is None:
+        return fluence_adjoint(e, s, g, cascades)
+    return fluence_blurred_adjoint(e, s, g, blur, cascades)
+
+
+def bounce_source(e, s, albedo, F, _mutant=0):
+    """Emission of the next bounce (Sec. 4.2: the output fluence fed into
+    another iteration), read as isotropic single scattering in 2D: a pixel
+    with extinction sigma and albedo rho scatters sigma * rho of the fluence F
+    (radiance integrated over the full turn) evenly over 2 pi, so its source
+    per unit length becomes e + rho * sigma * F / (2 pi)."""
+    k = (1.0 if _mutant == 1 else s[None]) * albedo * F
+    return e + (k if _mutant == 2 else k / (2.0 * np.pi))
+
+
+def fluence_bounces(e, s, albedo, bounces: int, cascades: int = 0, blur=None, _mutant=0):
+    """Multi-bounce lighting: F_0 = Lighting(e), e_k = e + albedo * s * F_{k-1}
+    / (2 pi), F_k = Lighting(e_k); returns F_bounces (float64 [C][H][W]).
+    `blur` = None, or the cross-blur threshold applied by every Lighting."""
+    e, s, C, H, W = _img(e, s)
+    albedo = np.ascontiguousarray(albedo, dtype=np.float64).reshape(C, H, W)
+    F = _lighting(e, s, cascades, blur)
+    for _ in range(bounces - (1 if _mutant == 3 else 0)):
+        F = _lighting(bounce_source(e, s, albedo, F, _mutant), s, cascades, blur)
+    return F
+
+
+def fluence_bounces_adjoint(e, s, albedo, gF, bounces: int, cascades: int = 0, blur=None, _mutant=0):
+    """Gradient of sum(gF * fluence_bounces(...)) w.r.t. (e, s, albedo), by
+    the reverse of the iteration: the adjoint of Lighting at each e_k, and of
+    the source update through F_{k-1}, s and albedo."""
+    e, s, C, H, W = _img(e, s)
+    albedo = np.ascontiguousarray(albedo, dtype=np.float64).reshape(C, H, W)
+    g = np.ascontiguousarray(gF, dtype=np.float64).reshape(C, H, W)
+    Fs, es = [], [e]
+    F = _lighting(e, s, cascades, blur)
+    for _ in range(bounces):
+        Fs.append(F)
+        es.append(bounce_source(e, s, albedo, F))
+        F = _lighting(es[-1], s, cascades, blur)
+    ge = np.zeros((C, H, W))
+    gs = np.zeros((H, W))
+    ga = np.zeros((C, H, W))
+    for k in range(bounces, -1, -1):
+        gek, gsk = _lighting_adjoint(es[k], s, g, cascades, blur)
+        ge += gek
+        gs += gsk
+        if k == 0:
+            break
+        Fp = Fs[k - 1]
+        if _mutant != 4:
+            gs += np.sum(gek * albedo * Fp, axis=0) / (2.0 * np.pi)
+        ga += gek * s[None] * Fp / (2.0 * np.pi)
+        g = gek * albedo * s[None] / (2.0 * np.pi)
+    return ge, gs, ga
 
 
 def bruteforce(e, s, M: int = 4096) -> np.ndarray:
