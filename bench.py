@@ -84,6 +84,42 @@ def bench_cross_blur(h, fwd, fwd_bwd, timed, gF, gE, gS, hbm_peak, thr=0.5, step
     return out
 
 
+def bench_bounces(h, e, s, timed, hbm_peak, K=6, rho=0.5, steps=5):
+    """Multi-bounce lighting with K bounces (the count of the paper's Fig. 14)
+    and a uniform albedo: graph-launched forward and forward+backward, and
+    the source-update kernel's per-launch time against its algorithmic bytes
+    ((4C + 1) fp32 planes per pixel)."""
+    import torch
+    from paper_2505_02041_gb300 import _lib
+    C, H, W = e.shape
+    h.reserve_bounces(K)
+    a = torch.full_like(e, rho)
+    F = torch.empty_like(e)
+    gF = torch.ones_like(e)
+    ge, gsg, ga = torch.empty_like(e), torch.empty_like(s), torch.empty_like(e)
+    fwd = lambda: _lib.hrc_fluence_bounces(h.ctx, e, s, a, K, F)
+    fwd_bwd = lambda: (fwd(), _lib.hrc_fluence_bounces_backward(h.ctx, gF, ge, gsg, ga))
+    for _ in range(3):
+        fwd_bwd()
+    f_ms = timed(fwd, steps)
+    fb_ms = timed(fwd_bwd, steps)
+    fwd()
+    launches = h.launch_count()
+    _lib.hrc_set_timing(h.ctx, True)
+    kf = {}
+    timed(fwd, steps, kf)
+    _lib.hrc_set_timing(h.ctx, False)
+    out = {"bounces": K, "albedo": rho, "forward_ms": statistics.mean(f_ms), "fwd_bwd_ms": statistics.mean(fb_ms),
+           "forward_ms_per_bounce": statistics.mean(f_ms) / (K + 1), "launches_forward": launches}
+    d = kf.get("bounce_source")
+    if d:
+        us = d[0] / d[2] * 1e3
+        by = d[1] / d[2]
+        out["bounce_source"] = {"us": us, "bytes": by, "GBps": by / (us * 1e-6) / 1e9,
+                                "frac_of_peak": by / (us * 1e-6) / 1e9 / hbm_peak}
+    return out
+
+
 def traffic_key(kind, cfg):
     """The kernel variant whose DRAM bytes stand for `kind`: the merge down
     has a per-thread-load kernel (mdown 0) and a bulk-copy-staged one
@@ -457,6 +493,7 @@ def run_ours(args):
         "clocks": clk,
     }
     line["cross_blur"] = bench_cross_blur(h, fwd, fwd_bwd, timed, gF, gE, gS, hbm_peak)
+    line["multi_bounce"] = bench_bounces(h, e, s, timed, hbm_peak)
     if args.precisions and world == 1:
         import oracle
         Fr = oracle.fluence(e_np, s_np)

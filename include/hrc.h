@@ -170,6 +170,54 @@ hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on);
 hrc_status hrc_set_cross_blur(hrc_ctx *ctx, int enable, float threshold);
 hrc_status hrc_get_cross_blur(const hrc_ctx *ctx, int *enable, float *threshold);
 
+/* Multiple diffuse bounces (Sec. 4.2: the output fluence fed into another
+ * iteration of the method; Fig. 14).  Bounce 0 is hrc_fluence on
+ * `emission`; bounce k + 1 runs it on
+ *     e_{k+1} = emission + albedo * sigma_t * F_k / (2 pi),
+ * the source of isotropic single scattering in 2D with a per-pixel,
+ * per-channel albedo (the scattering fraction of sigma_t; values in [0, 1)
+ * converge as bounces grow).  The paper gives no formula for the feedback;
+ * this is this library's reading.  Each bounce includes the cross blur
+ * when it is enabled.  `out` receives F_bounces ([C][H][W]).
+ *
+ * hrc_reserve_bounces allocates the context-owned buffers for up to
+ * `max_bounces` (0 .. 64; 2 max_bounces + 2 planes of W * H * C doubles):
+ * the e_k and F_k of the last bounce forward, which its backward reads, and
+ * the backward's scratch.  It must be called before the first bounce call;
+ * a larger count reallocates (synchronising the stream).  HRC_EINVAL on a
+ * batched context or a count out of range; HRC_ENOMEM if they do not fit.
+ *
+ * hrc_fluence_bounces: device pointers, 16-byte aligned; albedo is
+ * [C][H][W].  The pointers are borrowed until the next forward (as for
+ * hrc_fluence).  HRC_EINVAL for bounces outside [0, reserved],
+ * HRC_ESTATE without a reservation or in HRC_FP64_TEST (use the _f64
+ * variant there).
+ *
+ * hrc_fluence_bounces_backward: adjoint of the last hrc_fluence_bounces on
+ * this context: dLoss/d emission, d sigma_t ([H][W]) and d albedo
+ * ([C][H][W]) from dLoss/dF_bounces, overwritten, by the reverse of every
+ * bounce (the last one reads the levels its forward left, unless
+ * hrc_set_backward_recompute is on or a backward since has reused the
+ * buffers; every earlier bounce recomputes its levels from the stored
+ * e_k).  HRC_ESTATE if the last forward on the context was not a bounce
+ * forward.  A plain hrc_fluence_backward after a bounce forward is
+ * HRC_ESTATE too.
+ *
+ * hrc_bounce_source writes out = emission + albedo * sigma_t * fluence /
+ * (2 pi) on the context's stream (one bounce per frame, "temporally":
+ * feed the previous frame's fluence into this frame's emission). */
+hrc_status hrc_reserve_bounces(hrc_ctx *ctx, int max_bounces);
+hrc_status hrc_fluence_bounces(hrc_ctx *ctx, const float *emission, const float *sigma_t, const float *albedo,
+                               int bounces, float *out);
+hrc_status hrc_fluence_bounces_backward(hrc_ctx *ctx, const float *grad_F, float *grad_emission,
+                                        float *grad_sigma_t, float *grad_albedo);
+hrc_status hrc_fluence_bounces_f64(hrc_ctx *ctx, const double *emission, const double *sigma_t,
+                                   const double *albedo, int bounces, double *out);
+hrc_status hrc_fluence_bounces_backward_f64(hrc_ctx *ctx, const double *grad_F, double *grad_emission,
+                                            double *grad_sigma_t, double *grad_albedo);
+hrc_status hrc_bounce_source(hrc_ctx *ctx, const float *emission, const float *sigma_t, const float *albedo,
+                             const float *fluence, float *out);
+
 /* Waits for the context's stream and reports whether a bounded device-side
  * wait of the bulk-copy merge-down kernel gave up since the last call
  * (HRC_ETIMEOUT: that launch ended early and its outputs are incomplete;
@@ -291,7 +339,8 @@ int hrc_last_launch_count(const hrc_ctx *ctx);
  * the last compute call; it returns the number of records (or -1 on error).
  * `kind`: 0 trace T_0..T_2, 1 merge up, 2 merge down, 3 fluence sum,
  * 4 adjoint sum, 5 adjoint merge down, 6 adjoint merge up, 7 adjoint trace,
- * 8 batched persistent kernel, 9 other, 10 cross blur, 11 adjoint cross blur.  `bytes` is the launch's
+ * 8 batched persistent kernel, 9 other, 10 cross blur, 11 adjoint cross blur,
+ * 12 bounce source update, 13 its adjoint.  `bytes` is the launch's
  * algorithmic traffic (each array it consumes read once, each array it
  * produces written once). */
 typedef struct { int kind; int level; float ms; double bytes; } hrc_kernel_time;

@@ -12,11 +12,11 @@ Importing the package is cheap; the CUDA library loads on first use.
 """
 import importlib
 
-__all__ = ["HRC", "BatchedHRC", "fluence", "build"]
+__all__ = ["HRC", "BatchedHRC", "fluence", "fluence_bounces", "build"]
 
 
 def __getattr__(name):
-    if name in ("HRC", "BatchedHRC", "fluence"):
+    if name in ("HRC", "BatchedHRC", "fluence", "fluence_bounces"):
         return getattr(importlib.import_module(__name__ + ".api"), name)
     if name == "build":
         return importlib.import_module(__name__ + ".build").build

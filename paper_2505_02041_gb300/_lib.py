@@ -32,6 +32,12 @@ SIGNATURES = [
     ("hrc_sync", _i, [_vp]),
     ("hrc_set_cross_blur", _i, [_vp, _i, ctypes.c_float]),
     ("hrc_get_cross_blur", _i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
+    ("hrc_reserve_bounces", _i, [_vp, _i]),
+    ("hrc_fluence_bounces", _i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    ("hrc_fluence_bounces_backward", _i, [_vp, _vp, _vp, _vp, _vp]),
+    ("hrc_fluence_bounces_f64", _i, [_vp, _vp, _vp, _vp, _i, _vp]),
+    ("hrc_fluence_bounces_backward_f64", _i, [_vp, _vp, _vp, _vp, _vp]),
+    ("hrc_bounce_source", _i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("hrc_debug_bulk_wait", _i, [_vp, _i, ctypes.c_longlong]),
     ("hrc_get_launch_config", _i, [_vp, _vp]),
     ("hrc_set_launch_config", _i, [_vp, _vp]),
@@ -137,6 +143,32 @@ def hrc_get_cross_blur(ctx):
     th = ctypes.c_float()
     check(load().hrc_get_cross_blur(ctx, ctypes.byref(en), ctypes.byref(th)), ctx)
     return bool(en.value), th.value
+
+
+def hrc_reserve_bounces(ctx, max_bounces: int):
+    check(load().hrc_reserve_bounces(ctx, max_bounces), ctx)
+
+
+def hrc_fluence_bounces(ctx, emission, sigma_t, albedo, bounces: int, out):
+    check(load().hrc_fluence_bounces(ctx, ptr(emission), ptr(sigma_t), ptr(albedo), bounces, ptr(out)), ctx)
+
+
+def hrc_fluence_bounces_backward(ctx, grad_F, grad_emission, grad_sigma_t, grad_albedo):
+    check(load().hrc_fluence_bounces_backward(ctx, ptr(grad_F), ptr(grad_emission), ptr(grad_sigma_t),
+                                              ptr(grad_albedo)), ctx)
+
+
+def hrc_fluence_bounces_f64(ctx, emission, sigma_t, albedo, bounces: int, out):
+    check(load().hrc_fluence_bounces_f64(ctx, ptr(emission), ptr(sigma_t), ptr(albedo), bounces, ptr(out)), ctx)
+
+
+def hrc_fluence_bounces_backward_f64(ctx, grad_F, grad_emission, grad_sigma_t, grad_albedo):
+    check(load().hrc_fluence_bounces_backward_f64(ctx, ptr(grad_F), ptr(grad_emission), ptr(grad_sigma_t),
+                                                  ptr(grad_albedo)), ctx)
+
+
+def hrc_bounce_source(ctx, emission, sigma_t, albedo, fluence, out):
+    check(load().hrc_bounce_source(ctx, ptr(emission), ptr(sigma_t), ptr(albedo), ptr(fluence), ptr(out)), ctx)
 
 
 class hrc_launch_config(ctypes.Structure):
@@ -258,7 +290,8 @@ class hrc_kernel_time(ctypes.Structure):
 
 
 KERNEL_KINDS = ["trace012", "merge_up", "merge_down", "fluence_sum", "adj_sum", "adj_merge_down",
-                "adj_merge_up", "adj_trace", "batched", "other", "cross_blur", "adj_cross_blur"]
+                "adj_merge_up", "adj_trace", "batched", "other", "cross_blur", "adj_cross_blur",
+                "bounce_source", "adj_bounce"]
 
 
 def hrc_set_timing(ctx, enable: bool):

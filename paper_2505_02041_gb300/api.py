@@ -46,6 +46,7 @@ class HRC:
         self.precision = "fp32"
         self._borrowed = (None, None, 0, 0)
         self._host_levels = False
+        self._bounced = None
         self.set_precision(precision)
 
     # -- configuration -----------------------------------------------------
@@ -76,6 +77,7 @@ class HRC:
             _lib.hrc_fluence(self.ctx, emission, sigma_t, out)
         self._borrowed = (emission, sigma_t, emission._version, sigma_t._version)
         self._host_levels = False
+        self._bounced = None
         return out
 
     __call__ = forward
@@ -126,6 +128,67 @@ class HRC:
         else:
             _lib.hrc_fluence_backward(self.ctx, grad_F, ge, gs)
         return ge, gs
+
+    # -- multiple bounces (hrc_fluence_bounces) ----------------------------
+    def reserve_bounces(self, max_bounces: int) -> None:
+        """Context buffers for up to `max_bounces` bounces (hrc_reserve_bounces)."""
+        _lib.hrc_reserve_bounces(self.ctx, max_bounces)
+
+    def forward_bounces(self, emission, sigma_t, albedo, bounces: int, out=None):
+        """F after `bounces` extra bounces: each feeds albedo * sigma * F / (2 pi)
+        back into the emission (see hrc_fluence_bounces)."""
+        C, H, W = self.C, self.H, self.W
+        emission = _dev_tensor(emission, self.dtype, (C, H, W), "emission")
+        sigma_t = _dev_tensor(sigma_t, self.dtype, (H, W), "sigma_t")
+        albedo = _dev_tensor(albedo, self.dtype, (C, H, W), "albedo")
+        if out is None:
+            out = torch.empty((C, H, W), dtype=self.dtype, device=emission.device)
+        self._stream()
+        if self.precision == "fp64":
+            _lib.hrc_fluence_bounces_f64(self.ctx, emission, sigma_t, albedo, bounces, out)
+        else:
+            _lib.hrc_fluence_bounces(self.ctx, emission, sigma_t, albedo, bounces, out)
+        self._borrowed = (None, None, 0, 0)
+        self._host_levels = False
+        self._bounced = (emission, sigma_t, albedo, bounces, emission._version, sigma_t._version, albedo._version)
+        return out
+
+    def backward_bounces(self, grad_F, emission=None, sigma_t=None, albedo=None, bounces=None):
+        """dLoss/d(emission, sigma_t, albedo) of the last forward_bounces (or of
+        the given inputs: the bounce forward runs again first when they differ
+        from the last one's or were modified in place since)."""
+        C, H, W = self.C, self.H, self.W
+        b = self._bounced
+        if emission is not None:
+            current = (b is not None and b[3] == bounces and
+                       all(x.data_ptr() == y.data_ptr() and x._version == v
+                           for x, y, v in zip(b[:3], (emission, sigma_t, albedo), b[4:])))
+            if not current:
+                self.forward_bounces(emission, sigma_t, albedo, bounces)
+        grad_F = _dev_tensor(grad_F, self.dtype, (C, H, W), "grad_F")
+        ge = torch.empty((C, H, W), dtype=self.dtype, device=grad_F.device)
+        gs = torch.empty((H, W), dtype=self.dtype, device=grad_F.device)
+        ga = torch.empty((C, H, W), dtype=self.dtype, device=grad_F.device)
+        self._stream()
+        if self.precision == "fp64":
+            _lib.hrc_fluence_bounces_backward_f64(self.ctx, grad_F, ge, gs, ga)
+        else:
+            _lib.hrc_fluence_bounces_backward(self.ctx, grad_F, ge, gs, ga)
+        return ge, gs, ga
+
+    def bounce_source(self, emission, sigma_t, albedo, fluence, out=None):
+        """emission + albedo * sigma_t * fluence / (2 pi) (hrc_bounce_source), for
+        one bounce per frame."""
+        C, H, W = self.C, self.H, self.W
+        emission = _dev_tensor(emission, torch.float32, (C, H, W), "emission")
+        sigma_t = _dev_tensor(sigma_t, torch.float32, (H, W), "sigma_t")
+        albedo = _dev_tensor(albedo, torch.float32, (C, H, W), "albedo")
+        fluence = _dev_tensor(fluence, torch.float32, (C, H, W), "fluence")
+        if out is None:
+            out = torch.empty_like(emission)
+        self._stream()
+        _lib.hrc_bounce_source(self.ctx, emission, sigma_t, albedo, fluence, out)
+        return out
 
     def level(self, q: int, which: str, n: int) -> torch.Tensor:
         """T_n (which='T': [U_n][2^n+1][V][C+1]) or R_n (which='R':
@@ -314,6 +377,29 @@ class _FluenceFn(torch.autograd.Function):
         emission, sigma_t = ctx.saved_tensors
         ge, gs = ctx.hrc.backward(grad_F.contiguous(), emission.detach(), sigma_t.detach())
         return None, ge, gs
+
+
+class _BouncesFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, hrc: HRC, emission, sigma_t, albedo, bounces):
+        out = hrc.forward_bounces(emission.detach(), sigma_t.detach(), albedo.detach(), bounces)
+        ctx.hrc = hrc
+        ctx.bounces = bounces
+        ctx.save_for_backward(emission, sigma_t, albedo)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_F):
+        emission, sigma_t, albedo = ctx.saved_tensors
+        ge, gs, ga = ctx.hrc.backward_bounces(grad_F.contiguous(), emission.detach(), sigma_t.detach(),
+                                              albedo.detach(), ctx.bounces)
+        return None, ge, gs, ga, None
+
+
+def fluence_bounces(hrc: HRC, emission, sigma_t, albedo, bounces: int):
+    """Differentiable multi-bounce fluence (forward -> hrc_fluence_bounces,
+    backward -> hrc_fluence_bounces_backward); reserve the bounces first."""
+    return _BouncesFn.apply(hrc, emission, sigma_t, albedo, bounces)
 
 
 def fluence(hrc: HRC, emission, sigma_t):

@@ -196,6 +196,15 @@ struct hrc_ctx {
     bool blur = false;           // cross blur (Eq. 21) after the fluence sum
     float blur_thr = 0.5f;       // its opacity threshold
     void *blur_buf = nullptr;    // W * H * C doubles: unblurred F, or dL/d(unblurred F)
+    // multiple bounces: e_1..e_cap and F_0..F_{cap-1} of the last bounce
+    // forward, then the backward's dL/de_k, dL/dF_{k-1} and dL/dsigma_k
+    int bounce_cap = 0;
+    char *bounce_buf = nullptr;
+    size_t bounce_plane = 0;        // bytes of one [C][H][W] set of doubles
+    bool have_bounce = false;       // a bounce forward ran (its inputs below)
+    const void *last_a = nullptr;
+    int last_K = 0;
+    bool bounce_levels_ok = false;  // the level buffers hold those of bounce last_K
     int launches = 0;
     Recorder rec;
     std::string err;
@@ -204,7 +213,7 @@ struct hrc_ctx {
     // replayed on the caller's stream.
     struct GraphEntry {
         int kind = -1, prec = -1, sched = -1, mgroups = -1, tune = -1;
-        const void *p[5] = {};
+        const void *p[8] = {};
         cudaGraphExec_t exec = nullptr;
         int launches = 0;
     };
@@ -277,9 +286,17 @@ cudaError_t upload_arcs(const Plan &pl, char *arena) {
 // Enqueue one pass (forward or backward) on the context's stream: replay its
 // CUDA graph when one exists for these pointers, capture one otherwise.
 // With per-launch timing on, the kernels are launched directly.
+struct PassKey {
+    const void *p[8];
+};
+
 template <class ENQ>
 hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, const void *p2, const void *p3,
-                    const void *p4, ENQ &&enqueue, const char *where) {
+                    const void *p4, ENQ &&enqueue, const char *where);
+
+// Same, keyed by up to eight pointers (or counts cast to pointers).
+template <class ENQ>
+hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue, const char *where) {
     ctx->launches = 0;
     if (ctx->rec.on || !ctx->use_graphs) {
         ctx->rec.reset(ctx->stream);
@@ -287,11 +304,11 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
         if (e != cudaSuccess) return cuda_fail(ctx, e, where);
         return HRC_OK;
     }
-    const void *key[5] = {p0, p1, p2, p3, p4};
+    const void *const *key = pk.p;
     for (auto &g : ctx->graphs) {
         if (g.exec && g.kind == kind && g.prec == ctx->prec && g.sched == ctx->sched && g.mgroups == ctx->mgroups &&
             g.tune == ctx->mthreads * 4 + ctx->vmajor * 2 + ctx->mdown &&
-            std::memcmp(g.p, key, sizeof(key)) == 0) {
+            std::memcmp(g.p, key, sizeof(pk.p)) == 0) {
             cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(ctx, e, where);
             ctx->launches = g.launches;
@@ -322,7 +339,7 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
     slot.sched = ctx->sched;
     slot.mgroups = ctx->mgroups;
     slot.tune = ctx->mthreads * 4 + ctx->vmajor * 2 + ctx->mdown;
-    std::memcpy(slot.p, key, sizeof(key));
+    std::memcpy(slot.p, key, sizeof(pk.p));
     slot.launches = n;
     e = cudaGraphLaunch(exec, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, where);
@@ -330,11 +347,37 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
     return HRC_OK;
 }
 
+template <class ENQ>
+hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, const void *p2, const void *p3,
+                    const void *p4, ENQ &&enqueue, const char *where) {
+    const PassKey pk{{p0, p1, p2, p3, p4, nullptr, nullptr, nullptr}};
+    return run_pass_key(ctx, kind, pk, enqueue, where);
+}
+
 void clear_graphs(hrc_ctx *ctx) {
     for (auto &g : ctx->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g = hrc_ctx::GraphEntry();
     }
+}
+
+// One Lighting pass (Algorithm 1, then the Eq. 21 blur when enabled) and
+// its adjoint, as enqueued by every single-scene entry point.
+cudaError_t enqueue_lighting(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
+                             void *blur_buf, double thr, cudaStream_t st, int *n, Recorder *r) {
+    if (!blur_buf) return launch_forward(pl, rt, e, s, F, st, n, r);
+    cudaError_t err = launch_forward(pl, rt, e, s, blur_buf, st, n, r);
+    if (err != cudaSuccess) return err;
+    return launch_cross_blur(pl, blur_buf, s, F, thr, st, n, r);
+}
+
+cudaError_t enqueue_lighting_adj(const Plan &pl, const RayTable &rt, const void *e, const void *s, const void *gF,
+                                 void *ge, void *gs, bool recompute, void *blur_buf, double thr, cudaStream_t st,
+                                 int *n, Recorder *r) {
+    if (!blur_buf) return launch_backward(pl, rt, e, s, gF, ge, gs, recompute, st, n, r);
+    cudaError_t err = launch_cross_blur_adj(pl, gF, s, blur_buf, thr, st, n, r);
+    if (err != cudaSuccess) return err;
+    return launch_backward(pl, rt, e, s, blur_buf, ge, gs, recompute, st, n, r);
 }
 
 hrc_status check_ctx(hrc_ctx *ctx) {
@@ -438,6 +481,7 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->dev_s);
     cudaFree(ctx->dev_F);
     cudaFree(ctx->blur_buf);
+    cudaFree(ctx->bounce_buf);
     for (auto &g : ctx->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     cudaFree(ctx->d_plans);
@@ -700,16 +744,14 @@ hrc_status hrc_fluence(hrc_ctx *ctx, const float *emission, const float *sigma_t
     const double thr = ctx->blur_thr;
     st = run_pass(ctx, 0, emission, sigma_t, out, nullptr, nullptr,
                   [&](cudaStream_t s, int *n, Recorder *r) {
-                      if (!Fr) return launch_forward(pl, *rt, emission, sigma_t, out, s, n, r);
-                      cudaError_t e = launch_forward(pl, *rt, emission, sigma_t, Fr, s, n, r);
-                      if (e != cudaSuccess) return e;
-                      return launch_cross_blur(pl, Fr, sigma_t, out, thr, s, n, r);
+                      return enqueue_lighting(pl, *rt, emission, sigma_t, out, Fr, thr, s, n, r);
                   },
                   "hrc_fluence");
     if (st != HRC_OK) return st;
     ctx->last_e = emission;
     ctx->last_s = sigma_t;
     ctx->have_fwd = true;
+    ctx->have_bounce = false;
     return HRC_OK;
 }
 
@@ -742,16 +784,14 @@ hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *s
     const double thr = ctx->blur_thr;
     st = run_pass(ctx, 2, emission, sigma_t, out, nullptr, nullptr,
                   [&](cudaStream_t s, int *n, Recorder *r) {
-                      if (!Fr) return launch_forward(pl, *rt, emission, sigma_t, out, s, n, r);
-                      cudaError_t e = launch_forward(pl, *rt, emission, sigma_t, Fr, s, n, r);
-                      if (e != cudaSuccess) return e;
-                      return launch_cross_blur(pl, Fr, sigma_t, out, thr, s, n, r);
+                      return enqueue_lighting(pl, *rt, emission, sigma_t, out, Fr, thr, s, n, r);
                   },
                   "hrc_fluence_f64");
     if (st != HRC_OK) return st;
     ctx->last_e = emission;
     ctx->last_s = sigma_t;
     ctx->have_fwd = true;
+    ctx->have_bounce = false;
     return HRC_OK;
 }
 
@@ -771,11 +811,8 @@ hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_e
     const double thr = ctx->blur_thr;
     return run_pass(ctx, rc ? 4 : 1, le, ls, grad_F, grad_emission, grad_sigma_t,
                     [&](cudaStream_t s, int *n, Recorder *r) {
-                        if (!gFr)
-                            return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, s, n, r);
-                        cudaError_t e = launch_cross_blur_adj(pl, grad_F, ls, gFr, thr, s, n, r);
-                        if (e != cudaSuccess) return e;
-                        return launch_backward(pl, *rt, le, ls, gFr, grad_emission, grad_sigma_t, rc, s, n, r);
+                        return enqueue_lighting_adj(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, gFr,
+                                                    thr, s, n, r);
                     },
                     "hrc_fluence_backward");
 }
@@ -796,13 +833,178 @@ hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *
     const double thr = ctx->blur_thr;
     return run_pass(ctx, rc ? 5 : 3, le, ls, grad_F, grad_emission, grad_sigma_t,
                     [&](cudaStream_t s, int *n, Recorder *r) {
-                        if (!gFr)
-                            return launch_backward(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, s, n, r);
-                        cudaError_t e = launch_cross_blur_adj(pl, grad_F, ls, gFr, thr, s, n, r);
-                        if (e != cudaSuccess) return e;
-                        return launch_backward(pl, *rt, le, ls, gFr, grad_emission, grad_sigma_t, rc, s, n, r);
+                        return enqueue_lighting_adj(pl, *rt, le, ls, grad_F, grad_emission, grad_sigma_t, rc, gFr,
+                                                    thr, s, n, r);
                     },
                     "hrc_fluence_backward_f64");
+}
+
+
+// ---------------------------------------------------------------------------
+// Multiple bounces
+// ---------------------------------------------------------------------------
+hrc_status hrc_reserve_bounces(hrc_ctx *ctx, int max_bounces) {
+    if (!ctx) return HRC_EINVAL;
+    if (ctx->batched) return fail(ctx, HRC_EINVAL, "hrc_reserve_bounces: single-scene contexts only");
+    if (max_bounces < 0 || max_bounces > 64) return fail(ctx, HRC_EINVAL, "hrc_reserve_bounces: 0 .. 64 bounces");
+    if (ctx->bounce_buf && max_bounces <= ctx->bounce_cap) return HRC_OK;
+    const size_t img = (size_t)ctx->W * ctx->H;
+    const size_t plane = align_up(img * ctx->C * sizeof(double), 256);
+    const size_t bytes = (2 * (size_t)max_bounces + 2) * plane + img * sizeof(double);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    clear_graphs(ctx);   // graphs may hold the old buffers
+    cudaFree(ctx->bounce_buf);
+    ctx->bounce_buf = nullptr;
+    ctx->bounce_cap = 0;
+    ctx->have_bounce = false;
+    cudaError_t e = cudaMalloc(&ctx->bounce_buf, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->bounce_buf = nullptr;
+        return fail(ctx, HRC_ENOMEM, "hrc_reserve_bounces: " + std::to_string(bytes) + " bytes do not fit");
+    }
+    ctx->bounce_cap = max_bounces;
+    ctx->bounce_plane = plane;
+    return HRC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Buffers of the bounce arena: e_k (k = 1 .. cap), F_k (k = 0 .. cap - 1),
+// then the backward's dL/de_k, dL/dF_{k-1} (both [C][H][W]) and dL/dsigma_k.
+char *bounce_e(hrc_ctx *ctx, int k) { return ctx->bounce_buf + (size_t)(k - 1) * ctx->bounce_plane; }
+char *bounce_F(hrc_ctx *ctx, int k) { return ctx->bounce_buf + (size_t)(ctx->bounce_cap + k) * ctx->bounce_plane; }
+char *bounce_scratch(hrc_ctx *ctx, int j) {
+    return ctx->bounce_buf + (size_t)(2 * ctx->bounce_cap + j) * ctx->bounce_plane;
+}
+
+hrc_status bounces_forward(hrc_ctx *ctx, const void *e, const void *s, const void *a, int K, void *out, bool f64,
+                           const char *where) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (ctx->batched) return fail(ctx, HRC_ESTATE, std::string(where) + ": batched context");
+    if (f64 != (ctx->prec == P_FP64))
+        return fail(ctx, HRC_ESTATE, std::string(where) + (f64 ? ": set HRC_FP64_TEST first" : ": context is in HRC_FP64_TEST"));
+    if (!e || !s || !a || !out) return fail(ctx, HRC_EINVAL, std::string(where) + ": NULL pointer");
+    if (!aligned16(e) || !aligned16(s) || !aligned16(a) || !aligned16(out))
+        return fail(ctx, HRC_EINVAL, std::string(where) + ": pointers must be 16-byte aligned");
+    if (!ctx->bounce_buf) return fail(ctx, HRC_ESTATE, std::string(where) + ": call hrc_reserve_bounces first");
+    if (K < 0 || K > ctx->bounce_cap)
+        return fail(ctx, HRC_EINVAL, std::string(where) + ": bounces must be in [0, the count reserved by hrc_reserve_bounces]");
+    const Plan pl = f64 ? ctx->plan64 : ctx->plan;
+    const RayTable *rt = &ctx->rt;
+    void *blur = ctx->blur ? ctx->blur_buf : nullptr;
+    const double thr = ctx->blur_thr;
+    const PassKey key{{e, s, a, out, (const void *)(intptr_t)K, nullptr, nullptr, nullptr}};
+    st = run_pass_key(ctx, f64 ? 13 : 12, key,
+                      [&](cudaStream_t sm, int *n, Recorder *r) {
+                          for (int k = 0; k <= K; ++k) {
+                              const void *ek = k == 0 ? e : (const void *)bounce_e(ctx, k);
+                              void *Fk = k == K ? out : (void *)bounce_F(ctx, k);
+                              cudaError_t err = enqueue_lighting(pl, *rt, ek, s, Fk, blur, thr, sm, n, r);
+                              if (err == cudaSuccess && k < K)
+                                  err = launch_bounce_source(pl, e, s, a, Fk, bounce_e(ctx, k + 1), sm, n, r);
+                              if (err != cudaSuccess) return err;
+                          }
+                          return cudaSuccess;
+                      },
+                      where);
+    if (st != HRC_OK) return st;
+    ctx->have_fwd = false;   // the levels are those of bounce K, not of (e, s)
+    ctx->have_bounce = true;
+    ctx->last_e = e;
+    ctx->last_s = s;
+    ctx->last_a = a;
+    ctx->last_K = K;
+    ctx->bounce_levels_ok = true;
+    return HRC_OK;
+}
+
+hrc_status bounces_backward(hrc_ctx *ctx, const void *gF, void *ge, void *gs, void *ga, bool f64, const char *where) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (f64 != (ctx->prec == P_FP64))
+        return fail(ctx, HRC_ESTATE, std::string(where) + (f64 ? ": set HRC_FP64_TEST first" : ": context is in HRC_FP64_TEST"));
+    if (!ctx->have_bounce) return fail(ctx, HRC_ESTATE, std::string(where) + ": no bounce forward on this context");
+    if (!gF || !ge || !gs || !ga) return fail(ctx, HRC_EINVAL, std::string(where) + ": NULL pointer");
+    if (!aligned16(gF) || !aligned16(ge) || !aligned16(gs) || !aligned16(ga))
+        return fail(ctx, HRC_EINVAL, std::string(where) + ": pointers must be 16-byte aligned");
+    const Plan pl = f64 ? ctx->plan64 : ctx->plan;
+    const RayTable *rt = &ctx->rt;
+    void *blur = ctx->blur ? ctx->blur_buf : nullptr;
+    const double thr = ctx->blur_thr;
+    const void *le = ctx->last_e, *ls = ctx->last_s, *la = ctx->last_a;
+    const int K = ctx->last_K;
+    // the last bounce may read the levels its forward left, unless a
+    // backward since recomputed earlier bounces over them
+    const bool rcK = ctx->bwd_recompute || !ctx->bounce_levels_ok;
+    void *gek = bounce_scratch(ctx, 0), *gFp = bounce_scratch(ctx, 1), *gsk = bounce_scratch(ctx, 2);
+    const PassKey key{{le, ls, la, gF, ge, gs, ga, (const void *)(intptr_t)(2 * K + (rcK ? 1 : 0))}};
+    st = run_pass_key(ctx, f64 ? 15 : 14, key,
+                      [&](cudaStream_t sm, int *n, Recorder *r) {
+                          const void *gin = gF;
+                          for (int k = K; k >= 0; --k) {
+                              const void *ek = k == 0 ? le : (const void *)bounce_e(ctx, k);
+                              cudaError_t err = enqueue_lighting_adj(pl, *rt, ek, ls, gin, gek, gsk, k == K ? rcK : true,
+                                                                     blur, thr, sm, n, r);
+                              if (err == cudaSuccess)
+                                  err = launch_bounce_adj(pl, k == K, k > 0, gek, gsk, k > 0 ? bounce_F(ctx, k - 1) : nullptr,
+                                                          la, ls, ge, gs, ga, gFp, sm, n, r);
+                              if (err != cudaSuccess) return err;
+                              gin = gFp;
+                          }
+                          return cudaSuccess;
+                      },
+                      where);
+    if (st != HRC_OK) return st;
+    if (K > 0) ctx->bounce_levels_ok = false;   // bounce 0's levels are in the buffers now
+    return HRC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hrc_status hrc_fluence_bounces(hrc_ctx *ctx, const float *emission, const float *sigma_t, const float *albedo,
+                               int bounces, float *out) {
+    return bounces_forward(ctx, emission, sigma_t, albedo, bounces, out, false, "hrc_fluence_bounces");
+}
+
+hrc_status hrc_fluence_bounces_f64(hrc_ctx *ctx, const double *emission, const double *sigma_t,
+                                   const double *albedo, int bounces, double *out) {
+    return bounces_forward(ctx, emission, sigma_t, albedo, bounces, out, true, "hrc_fluence_bounces_f64");
+}
+
+hrc_status hrc_fluence_bounces_backward(hrc_ctx *ctx, const float *grad_F, float *grad_emission,
+                                        float *grad_sigma_t, float *grad_albedo) {
+    return bounces_backward(ctx, grad_F, grad_emission, grad_sigma_t, grad_albedo, false,
+                            "hrc_fluence_bounces_backward");
+}
+
+hrc_status hrc_fluence_bounces_backward_f64(hrc_ctx *ctx, const double *grad_F, double *grad_emission,
+                                            double *grad_sigma_t, double *grad_albedo) {
+    return bounces_backward(ctx, grad_F, grad_emission, grad_sigma_t, grad_albedo, true,
+                            "hrc_fluence_bounces_backward_f64");
+}
+
+hrc_status hrc_bounce_source(hrc_ctx *ctx, const float *emission, const float *sigma_t, const float *albedo,
+                             const float *fluence, float *out) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (ctx->batched || ctx->prec == P_FP64)
+        return fail(ctx, HRC_ESTATE, "hrc_bounce_source: single-scene fp32 / fp16 / bf16 contexts");
+    if (!emission || !sigma_t || !albedo || !fluence || !out) return fail(ctx, HRC_EINVAL, "hrc_bounce_source: NULL pointer");
+    if (!aligned16(emission) || !aligned16(sigma_t) || !aligned16(albedo) || !aligned16(fluence) || !aligned16(out))
+        return fail(ctx, HRC_EINVAL, "hrc_bounce_source: pointers must be 16-byte aligned");
+    Recorder off;
+    int n = 0;
+    cudaError_t e = launch_bounce_source(ctx->plan, emission, sigma_t, albedo, fluence, out, ctx->stream, &n, &off);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_bounce_source");
+    ctx->launches = n;
+    return HRC_OK;
 }
 
 

@@ -14,7 +14,7 @@ namespace hrc {
 enum KernelKind {
     K_TRACE012 = 0, K_MERGE_UP = 1, K_MERGE_DOWN = 2, K_FLUENCE_SUM = 3,
     K_ADJ_SUM = 4, K_ADJ_MERGE_DOWN = 5, K_ADJ_MERGE_UP = 6, K_ADJ_TRACE = 7,
-    K_BATCHED = 8, K_OTHER = 9, K_CROSS_BLUR = 10, K_ADJ_CROSS_BLUR = 11
+    K_BATCHED = 8, K_OTHER = 9, K_CROSS_BLUR = 10, K_ADJ_CROSS_BLUR = 11, K_BOUNCE = 12, K_ADJ_BOUNCE = 13
 };
 
 // Optional per-launch CUDA-event timing (off by default).  Events come from
@@ -145,6 +145,16 @@ cudaError_t launch_cross_blur(const Plan &pl, const void *Fr, const void *s, voi
 cudaError_t launch_cross_blur_adj(const Plan &pl, const void *g, const void *s, void *gFr, double thr,
                                   cudaStream_t st, int *launches, Recorder *rec);
 double bytes_cross_blur(const Plan &pl);
+
+// Multi-bounce source update (kernels_bounce.cu): eo = e + a * s * F / (2 pi)
+// over [C][H][W] planes (s: [H][W]); and its reverse for bounce k (first: k
+// is the last bounce, the accumulators ge / gs / ga are overwritten; has_prev:
+// k >= 1, so F_{k-1} = Fp exists and dL/dF_{k-1} is written to gFp).
+cudaError_t launch_bounce_source(const Plan &pl, const void *e, const void *s, const void *a, const void *F,
+                                 void *eo, cudaStream_t st, int *launches, Recorder *rec);
+cudaError_t launch_bounce_adj(const Plan &pl, bool first, bool has_prev, const void *gek, const void *gsk,
+                              const void *Fp, const void *a, const void *s, void *ge, void *gs, void *ga, void *gFp,
+                              cudaStream_t st, int *launches, Recorder *rec);
 
 // Dense fp32 copy of level n of frame q (which = 0: T_n, 1: R_n).
 cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *dst, cudaStream_t st);
