@@ -5,7 +5,8 @@ benchmark's CPU-baseline leg use it to check and time the CUDA path.  The
 product package never imports it, and it shares no code with the product.
 
 ``hrc_oracle.c`` follows Algorithm 1 and Eqs. 7-20 step by step in double
-precision, and the cross blur of Eq. 21 (Sec. 4.2) with its adjoint.  The
+precision (optionally with an environment map, footnote 1 of Sec. 4.2), and
+the cross blur of Eq. 21 (Sec. 4.2) with its adjoint.  The
 multi-bounce iteration of Sec. 4.2 (fluence fed back as a scattering
 source) is composed from them here, in numpy.  ``recursive.py`` is a
 second, independent formulation of Eqs. 14-20 (memoised recursion, pure
@@ -49,6 +50,12 @@ def _declare(L):
     L.orc_levels.restype = ctypes.c_int
     L.orc_fluence.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
     L.orc_fluence.restype = None
+    L.orc_fluence_env.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D,
+                                  ctypes.c_int, _D]
+    L.orc_fluence_env.restype = None
+    L.orc_fluence_adjoint_env.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          _D, ctypes.c_int, _D, _D]
+    L.orc_fluence_adjoint_env.restype = None
     L.orc_frame_level.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
     L.orc_frame_level.restype = ctypes.c_long
@@ -136,11 +143,26 @@ def levels(U: int, cascades: int = 0) -> int:
     return lib().orc_levels(U, cascades)
 
 
-def fluence(e, s, cascades: int = 0) -> np.ndarray:
-    """Algorithm 1 (Lighting): F[C][H][W] in float64."""
+def _env(env, C):
+    env = np.ascontiguousarray(env, dtype=np.float64)
+    if env.ndim == 1:
+        env = np.repeat(env[None], C, axis=0)
+    assert env.ndim == 2 and env.shape[0] == C and env.shape[1] >= 1
+    return env
+
+
+def fluence(e, s, cascades: int = 0, env=None) -> np.ndarray:
+    """Algorithm 1 (Lighting): F[C][H][W] in float64.  `env` ([C][M] or [M]):
+    an environment map (footnote 1 of Sec. 4.2), radiance seen along the
+    image-space look angle theta_m = 2 pi (m + 1/2) / M (theta from +x
+    towards +y = down the rows), linearly interpolated."""
     e, s, C, H, W = _img(e, s)
     F = np.zeros((C, H, W))
-    lib().orc_fluence(_p(e), _p(s), C, W, H, cascades, _p(F))
+    if env is None:
+        lib().orc_fluence(_p(e), _p(s), C, W, H, cascades, _p(F))
+    else:
+        env = _env(env, C)
+        lib().orc_fluence_env(_p(e), _p(s), C, W, H, cascades, _p(env), env.shape[1], _p(F))
     return F
 
 
@@ -165,13 +187,19 @@ def frame_level(e, s, q: int, which: str, n: int, cascades: int = 0) -> np.ndarr
     return out.reshape(Un, 1 << n, V, C)
 
 
-def fluence_adjoint(e, s, gF, cascades: int = 0):
-    """Gradient of sum(gF * F) w.r.t. (e, s), float64."""
+def fluence_adjoint(e, s, gF, cascades: int = 0, env=None):
+    """Gradient of sum(gF * F) w.r.t. (e, s), float64 (with the environment
+    map `env` as in fluence, held fixed)."""
     e, s, C, H, W = _img(e, s)
     gF = np.ascontiguousarray(gF, dtype=np.float64).reshape(C, H, W)
     ge = np.zeros((C, H, W))
     gs = np.zeros((H, W))
-    lib().orc_fluence_adjoint(_p(e), _p(s), _p(gF), C, W, H, cascades, _p(ge), _p(gs))
+    if env is None:
+        lib().orc_fluence_adjoint(_p(e), _p(s), _p(gF), C, W, H, cascades, _p(ge), _p(gs))
+    else:
+        env = _env(env, C)
+        lib().orc_fluence_adjoint_env(_p(e), _p(s), _p(gF), C, W, H, cascades, _p(env), env.shape[1],
+                                      _p(ge), _p(gs))
     return ge, gs
 
 

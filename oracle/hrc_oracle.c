@@ -268,6 +268,7 @@ typedef struct {
     long Un[ORC_MAXL + 1];
     double *T[ORC_MAXL + 1];   /* [x][k][v][C+1]: C radiances then T */
     double *R[ORC_MAXL + 1];   /* [x][i][v][C]; R[N] unused (== 0)   */
+    double *Renv[ORC_MAXL + 1];/* [i][C] environment values, or NULL */
 } Cascades;
 
 static size_t T_index(const Cascades *cs, int n, long x, long k, long v)
@@ -301,6 +302,74 @@ static const double *R_get(const Cascades *cs, int n, long pu, long pv, long ip)
     return cs->R[n] + R_index(cs, n, x, ip, pv);
 }
 
+/* The value of R_n(p, i) wherever it is looked up: the stored entry, else
+ * (outside the stored ranges, or n = N) the environment's value of cone i
+ * at level n, or NULL (= 0) without an environment (footnote 1 of
+ * Sec. 4.2: R_N from an environment map looked up along v_N(i)). */
+static const double *R_val(const Cascades *cs, int n, long pu, long pv, long ip)
+{
+    const double *r = R_get(cs, n, pu, pv, ip);
+    if (r) return r;
+    return cs->Renv[n] ? cs->Renv[n] + (size_t)ip * cs->C : NULL;
+}
+
+/* Environment radiance seen along the image direction (dx, dy), y down the
+ * rows: env[c][m] samples the look angle theta_m = 2 pi (m + 1/2) / M with
+ * theta = atan2(dy, dx) in [0, 2 pi); linear interpolation, periodic. */
+static double env_lookup(const double *env, int M, int c, double dx, double dy)
+{
+    double th = atan2(dy, dx);
+    if (th < 0) th += 2.0 * M_PI;
+    double t = th * M / (2.0 * M_PI) - 0.5;
+    double m0 = floor(t), fr = t - m0;
+    long i0 = ((long)m0 % M + M) % M, i1 = (i0 + 1) % M;
+    return (1.0 - fr) * env[(size_t)c * M + i0] + fr * env[(size_t)c * M + i1];
+}
+
+/* frame direction (du, dv) -> image direction (dx, dy), inverse of the
+ * quadrant maps of frame_to_image */
+static void frame_dir_to_image(int q, double du, double dv, double *dx, double *dy)
+{
+    switch (q) {
+    case 0: *dx = du;  *dy = dv;  break;
+    case 1: *dx = -du; *dy = dv;  break;
+    case 2: *dx = dv;  *dy = du;  break;
+    default: *dx = dv; *dy = -du; break;
+    }
+#if ORC_MUTANT == 19
+    if (q == 1) *dx = du;
+#endif
+}
+
+/* Environment values of frame q: at level N, cone j' = j + 1/2 sees
+ * A_N(j') E(direction of v_N(j')); an out-of-range lookup at level n < N
+ * sees, through vacuum (nothing outside the grid absorbs or emits), the sum
+ * of its two cones at level n + 1 (Eq. 14 / Eq. 15 with T = <0, 1>), i.e.
+ * of its level-N descendants. */
+static void env_tables(Cascades *cs, int q, const double *env, int M)
+{
+    int C = cs->C, N = cs->N;
+    for (int n = 0; n <= N; ++n) cs->Renv[n] = NULL;
+    if (!env) return;
+    for (int n = N; n >= 0; --n) {
+        long I = 1L << n;
+        cs->Renv[n] = (double *)calloc((size_t)I * C, sizeof(double));
+        for (long j = 0; j < I; ++j)
+            for (int c = 0; c < C; ++c) {
+                double v;
+                if (n == N || ORC_MUTANT == 20) {
+                    double dx, dy, s2 = (double)(1L << n);
+                    frame_dir_to_image(q, s2, 2.0 * j + 1.0 - s2, &dx, &dy);
+                    v = (ORC_MUTANT == 21 ? 1.0 : orc_arc(n, (int)j)) * env_lookup(env, M, c, dx, dy);
+                    if (ORC_MUTANT == 20 && n < N) v = 0.0;
+                } else {
+                    v = cs->Renv[n + 1][(size_t)(2 * j) * C + c] + cs->Renv[n + 1][(size_t)(2 * j + 1) * C + c];
+                }
+                cs->Renv[n][(size_t)j * C + c] = v;
+            }
+    }
+}
+
 /* Merge (Eq. 7) of near a and far b, each C radiances + T; NULL = vacuum. */
 static void merge(int C, const double *a, const double *b, double *out)
 {
@@ -313,12 +382,13 @@ static void merge(int C, const double *a, const double *b, double *out)
 }
 
 /* Algorithm 1, procedure HRC, for one frame.  Keeps every T and R level. */
-static void hrc_frame(const Frame *f, int cascades, Cascades *cs)
+static void hrc_frame(const Frame *f, int cascades, int q, const double *env, int M, Cascades *cs)
 {
     int C = f->C;
     cs->C = C; cs->U = f->U; cs->V = f->V;
     cs->N = orc_levels(f->U, cascades);
     int N = cs->N;
+    env_tables(cs, q, env, M);
     for (int n = 0; n <= N; ++n) {
         cs->Un[n] = level_cols(f->U, n);
         long K = (1L << n) + 1;
@@ -395,7 +465,7 @@ static void hrc_frame(const Frame *f, int cascades, Cascades *cs)
                             long j = sgn == 0 ? jp : jm;
                             double A = sgn == 0 ? Ap : Am;
                             const double *t = T_get(cs, n, pu, pv, kk);
-                            const double *r = R_get(cs, n + 1, pu + s, pv + 2 * kk - s, j);
+                            const double *r = R_val(cs, n + 1, pu + s, pv + 2 * kk - s, j);
                             double Tt = t ? t[C] : 1.0;
                             for (int c = 0; c < C; ++c)
                                 o[c] += A * (t ? t[c] : 0.0) + Tt * (r ? r[c] : 0.0);
@@ -408,9 +478,9 @@ static void hrc_frame(const Frame *f, int cascades, Cascades *cs)
                             long kk = sgn == 0 ? 2 * ip + 2 : 2 * ip;
                             long j = sgn == 0 ? jp : jm;
                             double A = sgn == 0 ? Ap : Am;
-                            const double *r0 = R_get(cs, n + 1, pu, pv, j);
+                            const double *r0 = R_val(cs, n + 1, pu, pv, j);
                             const double *t = T_get(cs, n + 1, pu, pv, kk);
-                            const double *r1 = R_get(cs, n + 1, pu + s1, ORC_MUTANT == 9 ? pv + kk - s : pv + 2 * kk - s1, j);
+                            const double *r1 = R_val(cs, n + 1, pu + s1, ORC_MUTANT == 9 ? pv + kk - s : pv + 2 * kk - s1, j);
                             double Tt = t ? t[C] : 1.0;
                             for (int c = 0; c < C; ++c)
                                 o[c] += 0.5 * ((ORC_MUTANT == 5 ? 2.0 : 1.0) * (r0 ? r0[c] : 0.0) + A * (t ? t[c] : 0.0) +
@@ -423,7 +493,7 @@ static void hrc_frame(const Frame *f, int cascades, Cascades *cs)
 
 static void cascades_free(Cascades *cs)
 {
-    for (int n = 0; n <= cs->N; ++n) { free(cs->T[n]); free(cs->R[n]); }
+    for (int n = 0; n <= cs->N; ++n) { free(cs->T[n]); free(cs->R[n]); free(cs->Renv[n]); }
 }
 
 /* ---------------------------------------------------------------------------
@@ -439,27 +509,32 @@ void orc_trace(const double *e, const double *s, int C, int W, int H,
     frame_free(&f);
 }
 
-/* Algorithm 1, Lighting: F(x, y) = sum over quadrants of R_0([x+1, y], 0). */
-void orc_fluence(const double *e, const double *s, int C, int W, int H, int cascades, double *F)
+/* Algorithm 1, Lighting: F(x, y) = sum over quadrants of R_0([x+1, y], 0);
+ * with an environment map env[C][M] (NULL: none), footnote 1 of Sec. 4.2. */
+void orc_fluence_env(const double *e, const double *s, int C, int W, int H, int cascades, const double *env, int M,
+                     double *F)
 {
     memset(F, 0, sizeof(double) * (size_t)C * W * H);
     for (int q = 0; q < 4; ++q) {
         Frame f = frame_build(q, e, s, C, W, H);
         Cascades cs;
-        hrc_frame(&f, cascades, &cs);
-        if (cs.N >= 1) {
-            for (long u = 0; u < f.U; ++u)
-                for (long v = 0; v < f.V; ++v) {
-                    long x, y;
-                    frame_to_image(q, W, H, u, v, &x, &y);
-                    const double *r = R_get(&cs, 0, ORC_MUTANT == 6 ? u : u + 1, v, 0);
-                    if (!r) continue;
-                    for (int c = 0; c < C; ++c) F[((size_t)c * H + y) * W + x] += r[c];
-                }
-        }
+        hrc_frame(&f, cascades, q, env, M, &cs);
+        for (long u = 0; u < f.U; ++u)
+            for (long v = 0; v < f.V; ++v) {
+                long x, y;
+                frame_to_image(q, W, H, u, v, &x, &y);
+                const double *r = R_val(&cs, 0, ORC_MUTANT == 6 ? u : u + 1, v, 0);
+                if (!r) continue;
+                for (int c = 0; c < C; ++c) F[((size_t)c * H + y) * W + x] += r[c];
+            }
         cascades_free(&cs);
         frame_free(&f);
     }
+}
+
+void orc_fluence(const double *e, const double *s, int C, int W, int H, int cascades, double *F)
+{
+    orc_fluence_env(e, s, C, W, H, cascades, NULL, 0, F);
 }
 
 /* One level of one frame, for level-by-level tests.  which = 0: T_n
@@ -470,7 +545,7 @@ long orc_frame_level(const double *e, const double *s, int C, int W, int H, int 
 {
     Frame f = frame_build(q, e, s, C, W, H);
     Cascades cs;
-    hrc_frame(&f, cascades, &cs);
+    hrc_frame(&f, cascades, q, NULL, 0, &cs);
     long cnt = -1;
     if (which == 0 && n >= 0 && n <= cs.N) {
         cnt = cs.Un[n] * ((1L << n) + 1) * f.V * (C + 1);
@@ -487,15 +562,15 @@ long orc_frame_level(const double *e, const double *s, int C, int W, int H, int 
 /* Gradient of sum(gF * F) with respect to e and s (the FP64 reverse of
  * orc_fluence: reverse fluence sum, reverse merge down, reverse merge up,
  * reverse trace).  ge, gs are overwritten. */
-void orc_fluence_adjoint(const double *e, const double *s, const double *gF, int C, int W, int H,
-                         int cascades, double *ge, double *gs)
+void orc_fluence_adjoint_env(const double *e, const double *s, const double *gF, int C, int W, int H,
+                             int cascades, const double *env, int M, double *ge, double *gs)
 {
     memset(ge, 0, sizeof(double) * (size_t)C * W * H);
     memset(gs, 0, sizeof(double) * (size_t)W * H);
     for (int q = 0; q < 4; ++q) {
         Frame f = frame_build(q, e, s, C, W, H);
         Cascades cs;
-        hrc_frame(&f, cascades, &cs);
+        hrc_frame(&f, cascades, q, env, M, &cs);
         int N = cs.N;
         if (N < 1) { cascades_free(&cs); frame_free(&f); continue; }
         double *gT[ORC_MAXL + 1], *gR[ORC_MAXL + 1];
@@ -531,12 +606,13 @@ void orc_fluence_adjoint(const double *e, const double *s, const double *gF, int
                                 long qu = pu + sn, qv = pv + 2 * kk - sn;
                                 const double *t = T_get(&cs, n, pu, pv, kk);
                                 const double *r = R_get(&cs, n + 1, qu, qv, j);
+                                const double *rv = R_val(&cs, n + 1, qu, qv, j);
                                 double Tt = t ? t[C] : 1.0;
                                 if (t) {
                                     double *gt = gT[n] + T_index(&cs, n, x, kk, y);
                                     for (int c = 0; c < C; ++c) {
                                         gt[c] += A * g[c];
-                                        gt[C] += g[c] * (r ? r[c] : 0.0);
+                                        gt[C] += g[c] * (rv ? rv[c] : 0.0);
                                     }
                                 }
                                 if (r) {
@@ -550,6 +626,7 @@ void orc_fluence_adjoint(const double *e, const double *s, const double *gF, int
                                 const double *r0 = R_get(&cs, n + 1, pu, pv, j);
                                 const double *t = T_get(&cs, n + 1, pu, pv, kk);
                                 const double *r1 = R_get(&cs, n + 1, qu, qv, j);
+                                const double *r1v = R_val(&cs, n + 1, qu, qv, j);
                                 double Tt = t ? t[C] : 1.0;
                                 if (r0) {
                                     double *gr = gR[n + 1] + R_index(&cs, n + 1, pu >> (n + 1), j, pv);
@@ -559,7 +636,7 @@ void orc_fluence_adjoint(const double *e, const double *s, const double *gF, int
                                     double *gt = gT[n + 1] + T_index(&cs, n + 1, pu >> (n + 1), kk, pv);
                                     for (int c = 0; c < C; ++c) {
                                         gt[c] += 0.5 * A * g[c];
-                                        gt[C] += 0.5 * g[c] * (r1 ? r1[c] : 0.0);
+                                        gt[C] += 0.5 * g[c] * (r1v ? r1v[c] : 0.0);
                                     }
                                 }
                                 if (r1) {
@@ -640,6 +717,12 @@ void orc_fluence_adjoint(const double *e, const double *s, const double *gF, int
         cascades_free(&cs);
         frame_free(&f);
     }
+}
+
+void orc_fluence_adjoint(const double *e, const double *s, const double *gF, int C, int W, int H,
+                         int cascades, double *ge, double *gs)
+{
+    orc_fluence_adjoint_env(e, s, gF, C, W, H, cascades, NULL, 0, ge, gs);
 }
 
 /* Eq. 1 by brute force: F(p) = sum_m (2 pi / M) L_r(p <- p + D w(theta_m)),

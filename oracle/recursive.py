@@ -49,9 +49,21 @@ def _image_of(q, W, H, u, v):
     return v, H - 1 - u
 
 
+def _env_radiance(env, dx, dy):
+    """Environment map env[C][M] along image direction (dx, dy): samples at
+    look angles 2 pi (m + 1/2) / M from +x towards +y, linear in between."""
+    M = env.shape[1]
+    th = math.atan2(dy, dx) % (2 * math.pi)
+    t = th / (2 * math.pi) * M - 0.5
+    m0 = math.floor(t)
+    f = t - m0
+    return (1 - f) * env[:, m0 % M] + f * env[:, (m0 + 1) % M]
+
+
 class _Frame:
-    def __init__(self, fe, fs, cascades):
+    def __init__(self, fe, fs, cascades, look=None):
         self.e, self.s = fe, fs            # e[C][U][V], s[U][V]
+        self.look = look                   # (du, dv) -> radiance seen that way, or None
         self.C, self.U, self.V = fe.shape
         N = 0
         while (1 << N) < self.U:
@@ -126,9 +138,13 @@ class _Frame:
         return math.atan2(2 * (jp + 1) - s, s) - math.atan2(2 * jp - s, s)   # Eq. 13
 
     def _R(self, n, pu, pv, ip):
-        """R_n(p, i), i = ip + 1/2 (Eqs. 14-17), R_N = 0."""
+        """R_n(p, i), i = ip + 1/2 (Eqs. 14-17); R_N = 0, or with an
+        environment map A_N(i) times the map along v_N(i) (footnote 1)."""
         if n >= self.N:
-            return (0.0,) * self.C
+            if self.look is None:
+                return (0.0,) * self.C
+            s = 1 << n
+            return tuple(self.A(n, ip) * self.look(s, 2 * ip + 1 - s))
         s = 1 << n
         x = pu >> n
         out = np.zeros(self.C)
@@ -147,8 +163,10 @@ class _Frame:
         return tuple(out)
 
 
-def fluence(e, s, cascades: int = 0) -> np.ndarray:
-    """F[C][H][W] from the recursive formulation (float64)."""
+def fluence(e, s, cascades: int = 0, env=None) -> np.ndarray:
+    """F[C][H][W] from the recursive formulation (float64); `env` an
+    environment map [C][M] (R_N only; outside the grid the recursion runs on
+    through vacuum)."""
     e = np.asarray(e, np.float64)
     s = np.asarray(s, np.float64)
     if e.ndim == 2:
@@ -157,8 +175,18 @@ def fluence(e, s, cascades: int = 0) -> np.ndarray:
     F = np.zeros((C, H, W))
     for q in range(4):
         fe, fs = _frame(q, e, s)
-        fr = _Frame(fe, fs, cascades)
-        if fr.N < 1:
+        look = None
+        if env is not None:
+            envq = np.asarray(env, np.float64).reshape(C, -1)
+
+            def look(du, dv, q=q, envq=envq):
+                # image direction of the frame direction (du, dv): the image
+                # points of two frame points one step apart
+                x0, y0 = _image_of(q, W, H, 0, 0)
+                x1, y1 = _image_of(q, W, H, du, dv)
+                return _env_radiance(envq, x1 - x0, y1 - y0)
+        fr = _Frame(fe, fs, cascades, look)
+        if fr.N < 1 and look is None:
             continue
         for u in range(fr.U):
             for v in range(fr.V):

@@ -39,6 +39,9 @@ MUTANTS = {
     16: "cross blur without renormalisation of the kept weights",
     17: "cross blur threshold on extinction instead of opacity",
     18: "cross blur adjoint scattered onto the wrong pixel",
+    19: "environment look direction of frame q1 mirrored",
+    20: "environment only at level N (out-of-grid lookups below it zero)",
+    21: "environment values without the arc weight",
 }
 
 
@@ -86,6 +89,30 @@ def failed_pins(O):
             bad.append("fd")
             break
     bad += failed_blur_pins(O)
+    bad += failed_env_pins(O)
+    return bad
+
+
+def failed_env_pins(O):
+    """The environment-map pins (footnote 1 of Sec. 4.2): uniform map in
+    vacuum, array form = recursive form, light from -x behind an opaque
+    right half."""
+    bad = []
+    F = O.fluence(np.zeros((1, 9, 11)), np.zeros((9, 11)), env=np.full((1, 8), 1.7))
+    if np.max(np.abs(F - 2 * math.pi * 1.7)) > 1e-13:
+        bad.append("env-uniform")
+    e, s = scenes.random_scene(12, 10, 1, 77)
+    env = np.random.default_rng(4).uniform(0, 2, size=(1, 24))
+    if np.max(np.abs(O.fluence(e, s, env=env) - recursive.fluence(e, s, env=env))) > 1e-11:
+        bad.append("env-recursive")
+    X = 32
+    sw = np.zeros((X, X))
+    sw[:, X // 2:] = 1e3
+    th = 2 * math.pi * (np.arange(256) + 0.5) / 256
+    lobe = np.where(np.cos(th - math.pi) > 0, np.cos(th - math.pi), 0.0) ** 8
+    Fw = O.fluence(np.zeros((1, X, X)), sw, env=lobe[None])[0]
+    if np.max(np.abs(Fw[:, :X // 2 - 8] - 35 * math.pi / 128)) > 0.02 * 35 * math.pi / 128:
+        bad.append("env-direction")
     return bad
 
 
