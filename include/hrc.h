@@ -170,6 +170,23 @@ hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on);
 hrc_status hrc_set_cross_blur(hrc_ctx *ctx, int enable, float threshold);
 hrc_status hrc_get_cross_blur(const hrc_ctx *ctx, int *enable, float *threshold);
 
+/* Environment map (footnote 1 of Sec. 4.2): light arriving from outside
+ * the grid, with nothing outside that absorbs or emits.  env is a device
+ * array [C][M] (fp32, 16-byte aligned): the radiance seen along the image
+ * look angle theta_m = 2 pi (m + 1/2) / M, theta measured from +x (along a
+ * row) towards +y (down the rows), linearly interpolated between samples
+ * and periodic.  Every later forward and backward on this single-scene
+ * context takes R_N(p, i) = A_N(i) env(direction of v_N(i)) and, for an R
+ * lookup outside the grid, the sum of its level-N descendants (what the
+ * recursion gives when continued outside through vacuum).  The map is
+ * converted into a per-frame, per-level table when this call runs (the
+ * stream is synchronised; env may be freed afterwards) and is held fixed
+ * by the backward (no gradient with respect to it).  env = NULL removes
+ * the map (R_N = 0 again).  The first map allocates the table
+ * (12 * 4 * 2^(N+1) * C bytes).  HRC_EINVAL on a batched context or for M
+ * outside [1, 2^20]; a forward must run again before a backward. */
+hrc_status hrc_set_environment(hrc_ctx *ctx, const float *env, int M);
+
 /* Multiple diffuse bounces (Sec. 4.2: the output fluence fed into another
  * iteration of the method; Fig. 14).  Bounce 0 is hrc_fluence on
  * `emission`; bounce k + 1 runs it on

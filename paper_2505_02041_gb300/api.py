@@ -129,6 +129,23 @@ class HRC:
             _lib.hrc_fluence_backward(self.ctx, grad_F, ge, gs)
         return ge, gs
 
+    def set_environment(self, env=None) -> None:
+        """Environment map (footnote 1 of Sec. 4.2): a CUDA float32 tensor
+        [C][M] (or [M], the same for every channel) of radiance along the look
+        angles 2 pi (m + 1/2) / M from +x towards +y; None removes it."""
+        if env is None:
+            _lib.hrc_set_environment(self.ctx, None, 0)
+            self._env = None
+        else:
+            if env.dim() == 1:
+                env = env.expand(self.C, env.shape[0])
+            env = _dev_tensor(env, torch.float32, (self.C, env.shape[-1]), "env")
+            self._stream()
+            _lib.hrc_set_environment(self.ctx, env, env.shape[-1])
+            self._env = env
+        self._borrowed = (None, None, 0, 0)
+        self._bounced = None
+
     # -- multiple bounces (hrc_fluence_bounces) ----------------------------
     def reserve_bounces(self, max_bounces: int) -> None:
         """Context buffers for up to `max_bounces` bounces (hrc_reserve_bounces)."""

@@ -176,7 +176,7 @@ __device__ __forceinline__ void body_adj_R(const Plan &pl, const RowSplitB &rs, 
 //     T_n(x, k) as F_+ (arc A_n(k-1)), cone k/2 as F_- (arc A_n(k)), each
 //     with weight 1/2; far fluence R_n(x+1, j, v+d), d = 2k - 2^n.
 // ---------------------------------------------------------------------------
-template <int P, int C, int E>
+template <int P, int C, int E, bool ENV = false>
 __device__ __forceinline__ void adj_T_part(const Plan &pl, int q, int n, int x, int k, int v,
                                            typename Prec<P>::A (&gL)[E][C], typename Prec<P>::A (&gT)[E]) {
     using A = typename Prec<P>::A;
@@ -191,17 +191,21 @@ __device__ __forceinline__ void adj_T_part(const Plan &pl, int q, int n, int x, 
     }
     // one cone's contribution: arc weight Aw on gR(xg, ip), dot weight dw
     // with R(xr, j, v + d) when rq
-    auto cone = [&](const GRLevel<P, C> &gR, int xg, int ip, A Aw, A dw, bool rq, const RLevel<P, C> &R, int xr, int j) {
+    // (R of level rl; out of range, the environment's value, 0 without a map)
+    auto cone = [&](const GRLevel<P, C> &gR, int xg, int ip, A Aw, A dw, bool rq, const RLevel<P, C> &R, int xr, int j,
+                    int rl) {
         if (E == 2 && v + 1 < g.V) {             // 2-wide loads (v, d even)
             const bool r0 = rq && v + d >= 0 && v + d < g.V, r1 = rq && v + d + 1 >= 0 && v + d + 1 < g.V;
             A dot0 = A(0), dot1 = A(0);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                A g0, g1, q0 = A(0), q1 = A(0);
+                A g0, g1, q0, q1;
                 gR.load2(xg, ip, c, v, g0, g1);
+                const A ev = renv<P, C, ENV>(pl, q, rl, j, c);
+                q0 = q1 = ev;
                 if (r0) {
                     R.load2(xr, j, c, v + d, q0, q1);
-                    if (!r1) q1 = A(0);
+                    if (!r1) q1 = ev;
                 }
                 gL[0][c] = fma(Aw, g0, gL[0][c]);
                 gL[E - 1][c] = fma(Aw, g1, gL[E - 1][c]);
@@ -221,7 +225,7 @@ __device__ __forceinline__ void adj_T_part(const Plan &pl, int q, int n, int x, 
             for (int c = 0; c < C; ++c) {
                 const A gr = gR.load(xg, ip, c, vv);
                 gL[l][c] = fma(Aw, gr, gL[l][c]);
-                if (rok) dot = fma(gr, R.load(xr, j, c, vv + d), dot);
+                dot = fma(gr, rok ? R.load(xr, j, c, vv + d) : renv<P, C, ENV>(pl, q, rl, j, c), dot);
             }
             gT[l] = fma(dw, dot, gT[l]);
         }
@@ -231,16 +235,16 @@ __device__ __forceinline__ void adj_T_part(const Plan &pl, int q, int n, int x, 
         const int xq = (x + 1) >> 1;
         const bool rq = (n + 1 < g.N) && xq < g.Un[n + 1];
         RLevel<P, C> R1(pl, q, rq ? n + 1 : n);
-        if (k >= 1) cone(gRn, x, k - 1, arc<P>(pl, n + 1, 2 * k - 1), A(1), rq, R1, xq, 2 * k - 1);
-        if (k < s) cone(gRn, x, k, arc<P>(pl, n + 1, 2 * k), A(1), rq, R1, xq, 2 * k);
+        if (k >= 1) cone(gRn, x, k - 1, arc<P>(pl, n + 1, 2 * k - 1), A(1), rq, R1, xq, 2 * k - 1, n + 1);
+        if (k < s) cone(gRn, x, k, arc<P>(pl, n + 1, 2 * k), A(1), rq, R1, xq, 2 * k, n + 1);
     }
     if (!(k & 1) && n >= 1) {
         const int m = n - 1;
         GRLevel<P, C> gRm(pl, q, m);
         const bool rq = (n < g.N) && x + 1 < g.Un[n];
         RLevel<P, C> Rn(pl, q, rq ? n : 0);
-        if (k >= 2) cone(gRm, 2 * x, (k >> 1) - 1, A(0.5) * arc<P>(pl, n, k - 1), A(0.5), rq, Rn, x + 1, k - 1);
-        if (k < s) cone(gRm, 2 * x, k >> 1, A(0.5) * arc<P>(pl, n, k), A(0.5), rq, Rn, x + 1, k);
+        if (k >= 2) cone(gRm, 2 * x, (k >> 1) - 1, A(0.5) * arc<P>(pl, n, k - 1), A(0.5), rq, Rn, x + 1, k - 1, n);
+        if (k < s) cone(gRm, 2 * x, k >> 1, A(0.5) * arc<P>(pl, n, k), A(0.5), rq, Rn, x + 1, k, n);
     }
 }
 
@@ -248,7 +252,7 @@ __device__ __forceinline__ void adj_T_part(const Plan &pl, int q, int n, int x, 
 // the level above (n = 2 .. N-1); adj_T covers the others.
 __host__ __device__ inline bool adj_T_fused(int n, int N) { return n >= 2 && n <= N - 1; }
 
-template <int P, int C, int E>
+template <int P, int C, int E, bool ENV = false>
 __device__ __forceinline__ void body_adj_T(const Plan &pl, const RowSplitB &rs, int n, long long bx, int by) {
     using A = typename Prec<P>::A;
     int local;
@@ -267,7 +271,7 @@ __device__ __forceinline__ void body_adj_T(const Plan &pl, const RowSplitB &rs, 
         k = local - x * K;
     }
     A gL[E][C], gT[E];
-    adj_T_part<P, C, E>(pl, q, n, x, k, v, gL, gT);
+    adj_T_part<P, C, E, ENV>(pl, q, n, x, k, v, gL, gT);
     GTLevel<P, C> gTn(pl, q, n);
 #pragma unroll
     for (int l = 0; l < E; ++l)
@@ -287,7 +291,7 @@ __device__ __forceinline__ void body_adj_T(const Plan &pl, const RowSplitB &rs, 
 //    k = 2 kap - 1 at v = w - (2 kap - 2 - h) (F_-, near dir kap - 1, 1/2)
 // Two consecutive w per thread (all offsets are even for n >= 3).
 // ---------------------------------------------------------------------------
-template <int P, int C>
+template <int P, int C, bool ENV = false>
 __device__ __forceinline__ void body_adj_merge_up(const Plan &pl, const RowSplitB &rs, int n, long long bx, int by) {
     using A = typename Prec<P>::A;
     constexpr int E = 2;
@@ -303,7 +307,7 @@ __device__ __forceinline__ void body_adj_merge_up(const Plan &pl, const RowSplit
     TLevel<P, C> Tm(pl, q, m);
     GTLevel<P, C> gTm(pl, q, m), gTn(pl, q, n);
     A aL[E][C], aT[E];
-    adj_T_part<P, C, E>(pl, q, m, x1, kap, w, aL, aT);   // the merge-down part of dL/dT_{n-1}
+    adj_T_part<P, C, E, ENV>(pl, q, m, x1, kap, w, aL, aT);   // the merge-down part of dL/dT_{n-1}
     if (!(x1 & 1)) {
         const int x = x1 >> 1, xf = x1 + 1;
         const int vf = w + 2 * kap - h;

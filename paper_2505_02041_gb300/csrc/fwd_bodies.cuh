@@ -362,7 +362,7 @@ __device__ __forceinline__ void body_merge_up4(const Plan &pl, const RowSplit &r
 // R_n(p, i) = F_+ + F_-, p = (x 2^n, v), i = ip + 1/2, j_+ = 2ip+1, j_- = 2ip,
 // for v .. v+E-1 of column x >= 1 of frame q (E = 2: all neighbour offsets
 // even, n >= 1).
-template <int P, int C, int E>
+template <int P, int C, int E, bool ENV = false>
 __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, int x, int ip, int v,
                                                  typename Prec<P>::A (&acc)[E][C]) {
     using A = typename Prec<P>::A;
@@ -384,14 +384,15 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
                 R1.load4(xr, j, c, vq, r);
                 return;
             }
+            const A ev = renv<P, C, ENV>(pl, q, n + 1, j, c);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int vp = vq + 2 * h;
                 if (vp >= 0 && vp < g.V) {
                     R1.load2(xr, j, c, vp, r[2 * h], r[2 * h + 1]);
-                    if (vp + 1 >= g.V) r[2 * h + 1] = A(0);
+                    if (vp + 1 >= g.V) r[2 * h + 1] = ev;
                 } else {
-                    r[2 * h] = r[2 * h + 1] = A(0);
+                    r[2 * h] = r[2 * h + 1] = ev;
                 }
             }
         };
@@ -410,8 +411,9 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
                 const int vq = v + 2 * kk - s;
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    A r[4] = {A(0), A(0), A(0), A(0)};
+                    A r[4];
                     if (rq_ok) loadR4(R1, xq, j, c, vq, r);
+                    else r[0] = r[1] = r[2] = r[3] = renv<P, C, ENV>(pl, q, n + 1, j, c);
 #pragma unroll
                     for (int l = 0; l < 4; ++l) acc[l][c] += fma(Aj, t[l].L[c], t[l].trans() * r[l]);
                 }
@@ -431,11 +433,12 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
                 const int vq = v + 2 * kk - 2 * s;
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    A r0[4] = {A(0), A(0), A(0), A(0)}, r1[4] = {A(0), A(0), A(0), A(0)};
-                    if (!top) {
-                        R1.load4(x2, j, c, v, r0);
-                        if (r1_ok) loadR4(R1, x2 + 1, j, c, vq, r1);
-                    }
+                    A r0[4], r1[4];
+                    const A ev = renv<P, C, ENV>(pl, q, n + 1, j, c);
+                    if (!top) R1.load4(x2, j, c, v, r0);
+                    else r0[0] = r0[1] = r0[2] = r0[3] = ev;
+                    if (r1_ok) loadR4(R1, x2 + 1, j, c, vq, r1);
+                    else r1[0] = r1[1] = r1[2] = r1[3] = ev;
 #pragma unroll
                     for (int l = 0; l < 4; ++l)
                         acc[l][c] += A(0.5) * (r0[l] + fma(Aj, t[l].L[c], t[l].trans() * r1[l]));
@@ -444,17 +447,17 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
         }
         return;
     }
-    // R_{n+1}(xr, j, vq .. vq+E-1), zero outside [0, V)
+    // R_{n+1}(xr, j, vq .. vq+E-1); outside [0, V) the environment's value
     auto loadR = [&](const RLevel<P, C> &R1, int xr, int j, int c, int vq, A (&r)[E]) {
         if (PAIR) {
             if (vq >= 0 && vq < g.V) {
                 R1.load2(xr, j, c, vq, r[0], r[E - 1]);
-                if (vq + 1 >= g.V) r[E - 1] = A(0);
+                if (vq + 1 >= g.V) r[E - 1] = renv<P, C, ENV>(pl, q, n + 1, j, c);
             } else {
-                r[0] = r[E - 1] = A(0);
+                r[0] = r[E - 1] = renv<P, C, ENV>(pl, q, n + 1, j, c);
             }
         } else {
-            r[0] = (vq >= 0 && vq < g.V) ? R1.load(xr, j, c, vq) : A(0);
+            r[0] = (vq >= 0 && vq < g.V) ? R1.load(xr, j, c, vq) : renv<P, C, ENV>(pl, q, n + 1, j, c);
         }
     };
     auto loadT = [&](const TLevel<P, C> &T, int xx, int kk, Iv<P, C> (&t)[E]) {
@@ -481,7 +484,7 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
                 if (rq_ok) loadR(R1, xq, j, c, vq, r);
                 else
 #pragma unroll
-                    for (int l = 0; l < E; ++l) r[l] = A(0);
+                    for (int l = 0; l < E; ++l) r[l] = renv<P, C, ENV>(pl, q, n + 1, j, c);
 #pragma unroll
                 for (int l = 0; l < E; ++l) acc[l][c] += fma(Aj, t[l].L[c], t[l].trans() * r[l]);
             }
@@ -505,13 +508,14 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 A r0[E], r1[E];
+                const A ev = renv<P, C, ENV>(pl, q, n + 1, j, c);
 #pragma unroll
-                for (int l = 0; l < E; ++l) { r0[l] = A(0); r1[l] = A(0); }
+                for (int l = 0; l < E; ++l) { r0[l] = ev; r1[l] = ev; }
                 if (!top) {
                     if (PAIR) R1.load2(x2, j, c, v, r0[0], r0[E - 1]);
                     else r0[0] = R1.load(x2, j, c, v);
-                    if (r1_ok) loadR(R1, x2 + 1, j, c, vq, r1);
                 }
+                if (r1_ok) loadR(R1, x2 + 1, j, c, vq, r1);
 #pragma unroll
                 for (int l = 0; l < E; ++l)
                     acc[l][c] += A(0.5) * (r0[l] + fma(Aj, t[l].L[c], t[l].trans() * r1[l]));
@@ -521,7 +525,7 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
 }
 
 // One row segment of R_n with four consecutive v per thread (n >= 1).
-template <int P, int C>
+template <int P, int C, bool ENV = false>
 __device__ __forceinline__ void body_merge_down4(const Plan &pl, const RowSplit &rs, int n, long long bx, int by) {
     using A = typename Prec<P>::A;
     int local;
@@ -533,7 +537,7 @@ __device__ __forceinline__ void body_merge_down4(const Plan &pl, const RowSplit 
     local += I;
     const int x = local >> n, ip = local & (I - 1);
     A acc[4][C];
-    merge_down_entry<P, C, 4>(pl, q, n, x, ip, v, acc);
+    merge_down_entry<P, C, 4, ENV>(pl, q, n, x, ip, v, acc);
     RLevel<P, C> Rn(pl, q, n);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -543,7 +547,7 @@ __device__ __forceinline__ void body_merge_down4(const Plan &pl, const RowSplit 
 }
 
 // One row segment of R_n: row = (q, x, ip), x >= 1 (column 0 is dead).
-template <int P, int C, bool PAIR>
+template <int P, int C, bool PAIR, bool ENV = false>
 __device__ __forceinline__ void body_merge_down(const Plan &pl, const RowSplit &rs, int n, long long bx, int by) {
     using A = typename Prec<P>::A;
     constexpr int E = PAIR ? 2 : 1;
@@ -556,7 +560,7 @@ __device__ __forceinline__ void body_merge_down(const Plan &pl, const RowSplit &
     local += I;
     const int x = local >> n, ip = local & (I - 1);
     A acc[E][C];
-    merge_down_entry<P, C, E>(pl, q, n, x, ip, v, acc);
+    merge_down_entry<P, C, E, ENV>(pl, q, n, x, ip, v, acc);
     RLevel<P, C> Rn(pl, q, n);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -575,7 +579,7 @@ __device__ __forceinline__ void body_merge_down(const Plan &pl, const RowSplit &
 template <int P, int C>
 constexpr size_t fluence_smem() { return sizeof(typename Prec<P>::A) * C * 32 * 33; }
 
-template <int P, int C, class OUT>
+template <int P, int C, class OUT, bool ENV = false>
 __device__ __forceinline__ void body_fluence(const Plan &pl, OUT *__restrict__ F, int bx, int by, unsigned char *smem) {
     using A = typename Prec<P>::A;
     A (*tile)[32][33] = reinterpret_cast<A (*)[32][33]>(smem);   // [C][y][x] of the tile
@@ -587,9 +591,13 @@ __device__ __forceinline__ void body_fluence(const Plan &pl, OUT *__restrict__ F
         const QuadGeom &g = pl.q[q];
         int u, v;
         image_to_frame(q, W, H, x, y, u, v);
-        if (g.N < 1 || u + 1 >= g.U) return;
+        if (g.N < 1 || u + 1 >= g.U) {             // the probe at u + 1 is outside: the environment
+#pragma unroll
+            for (int c = 0; c < C; ++c) a[c] += renv<P, C, ENV>(pl, q, 0, 0, c);
+            return;
+        }
         A r[1][C];
-        merge_down_entry<P, C, 1>(pl, q, 0, u + 1, 0, v, r);
+        merge_down_entry<P, C, 1, ENV>(pl, q, 0, u + 1, 0, v, r);
 #pragma unroll
         for (int c = 0; c < C; ++c) a[c] += r[0][c];
     };

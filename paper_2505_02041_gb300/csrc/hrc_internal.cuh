@@ -54,6 +54,12 @@ struct Plan {
     long long arcs_off;              // byte offset: float A[2^n + j] for level n (n >= 1)
     long long arcs_off_d;            // same table in double
     char *arena;
+    // environment map (footnote 1 of Sec. 4.2): value of cone j at level n of
+    // frame q at [q * env_stride + (2^n + j) * C + c] (fp32 / fp64 copies);
+    // null without a map (out-of-grid R lookups are then 0)
+    const float *envf;
+    const double *envd;
+    long long env_stride;
     QuadGeom q[4];
 };
 
@@ -347,6 +353,26 @@ template <int P, int C> struct TLevel {
         for (int l = 0; l < 4; ++l) r[l].t = t[l];
     }
 };
+
+// Value of an R_n lookup outside the stored ranges (and of any R_N lookup):
+// the environment's value of cone j (the sum of its level-N descendants,
+// i.e. the recursion continued outside the grid through vacuum) in kernels
+// compiled for a map (ENV), else 0 -- a compile-time choice, so that the
+// map-free kernels carry none of its code or registers.
+template <int P, int C, bool ENV>
+__device__ __forceinline__ typename Prec<P>::A renv(const Plan &pl, int q, int n, int j, int c) {
+    using A = typename Prec<P>::A;
+    if constexpr (!ENV) {
+        return A(0);
+    } else {
+        const long long i = q * pl.env_stride + ((long long)(1 << n) + j) * C + c;
+        if constexpr (P == P_FP64) return pl.envd[i];
+        else return pl.envf[i];
+    }
+}
+
+// Whether a plan carries an environment map (kernels dispatch on it).
+inline bool plan_has_env(const Plan &pl) { return pl.envf != nullptr || pl.envd != nullptr; }
 
 template <int P, int C> struct RLevel {
     using SL = typename Prec<P>::SL;

@@ -205,6 +205,9 @@ struct hrc_ctx {
     const void *last_a = nullptr;
     int last_K = 0;
     bool bounce_levels_ok = false;  // the level buffers hold those of bounce last_K
+    // environment map: per-frame, per-level cone values (kernels_env.cu)
+    char *env_tab = nullptr;
+    bool env_on = false;
     int launches = 0;
     Recorder rec;
     std::string err;
@@ -361,6 +364,22 @@ void clear_graphs(hrc_ctx *ctx) {
     }
 }
 
+// Point the plans at the environment table (or at none).
+void apply_env(hrc_ctx *ctx) {
+    for (Plan *p : {&ctx->plan, &ctx->plan64}) {
+        if (ctx->env_on) {
+            const long long stride = env_table_stride(ctx->plan);
+            p->envd = reinterpret_cast<const double *>(ctx->env_tab);
+            p->envf = reinterpret_cast<const float *>(p->envd + 4 * stride);
+            p->env_stride = stride;
+        } else {
+            p->envd = nullptr;
+            p->envf = nullptr;
+            p->env_stride = 0;
+        }
+    }
+}
+
 // One Lighting pass (Algorithm 1, then the Eq. 21 blur when enabled) and
 // its adjoint, as enqueued by every single-scene entry point.
 cudaError_t enqueue_lighting(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
@@ -482,6 +501,7 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->dev_F);
     cudaFree(ctx->blur_buf);
     cudaFree(ctx->bounce_buf);
+    cudaFree(ctx->env_tab);
     for (auto &g : ctx->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     cudaFree(ctx->d_plans);
@@ -727,6 +747,37 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
     }
     ctx->prec = (int)prec;
     ctx->have_fwd = false;
+    ctx->have_bounce = false;
+    apply_env(ctx);
+    return HRC_OK;
+}
+
+hrc_status hrc_set_environment(hrc_ctx *ctx, const float *env, int M) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (ctx->batched) return fail(ctx, HRC_EINVAL, "hrc_set_environment: single-scene contexts only");
+    if (env && (M < 1 || M > (1 << 20)))
+        return fail(ctx, HRC_EINVAL, "hrc_set_environment: M must be in [1, 2^20]");
+    if (env && !aligned16(env)) return fail(ctx, HRC_EINVAL, "hrc_set_environment: env must be 16-byte aligned");
+    if (env && !ctx->env_tab) {
+        const size_t bytes = env_table_bytes(ctx->plan);
+        cudaError_t e = cudaMalloc(&ctx->env_tab, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->env_tab = nullptr;
+            return fail(ctx, HRC_ENOMEM, "hrc_set_environment: table does not fit");
+        }
+    }
+    if (env) {
+        cudaError_t e = launch_env_table(ctx->plan, env, M, ctx->env_tab, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_environment");
+    }
+    ctx->env_on = env != nullptr;
+    apply_env(ctx);
+    clear_graphs(ctx);     // the graphs hold the plans by value
+    ctx->have_fwd = false; // levels and fluence of an earlier forward saw the old map
+    ctx->have_bounce = false;
     return HRC_OK;
 }
 
@@ -855,6 +906,7 @@ hrc_status hrc_reserve_bounces(hrc_ctx *ctx, int max_bounces) {
     else cudaDeviceSynchronize();
     clear_graphs(ctx);   // graphs may hold the old buffers
     cudaFree(ctx->bounce_buf);
+    cudaFree(ctx->env_tab);
     ctx->bounce_buf = nullptr;
     ctx->bounce_cap = 0;
     ctx->have_bounce = false;

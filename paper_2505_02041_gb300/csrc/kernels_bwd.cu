@@ -29,20 +29,20 @@ __global__ void __launch_bounds__(512) k_adj_R(Plan pl, RowSplitB rs, int n) {
     body_adj_R<P, C, E>(pl, rs, n, row, vb);
 }
 
-template <int P, int C, int E>
+template <int P, int C, int E, bool ENV>
 __global__ void __launch_bounds__(512) k_adj_T(Plan pl, RowSplitB rs, int n) {
     long long row;
     int vb;
     row_block_b(pl, row, vb);
-    body_adj_T<P, C, E>(pl, rs, n, row, vb);
+    body_adj_T<P, C, E, ENV>(pl, rs, n, row, vb);
 }
 
-template <int P, int C>
+template <int P, int C, bool ENV>
 __global__ void __launch_bounds__(512) k_adj_merge_up(Plan pl, RowSplitB rs, int n) {
     long long row;
     int vb;
     row_block_b(pl, row, vb);
-    body_adj_merge_up<P, C>(pl, rs, n, row, vb);
+    body_adj_merge_up<P, C, ENV>(pl, rs, n, row, vb);
 }
 
 // HRC_ETIMEOUT (5) once a TMA copy wait of the adjoint trace gave up.
@@ -104,6 +104,7 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                             void *ge, void *gs, bool recompute, cudaStream_t st, int *launches, Recorder *rec) {
     using IN = typename std::conditional<P == P_FP64, double, float>::type;
     const int mt = pl.mthreads, ts = 2 * mt > 512 ? 512 : 2 * mt;   // paired-v / single-v block sizes
+    const bool env = plan_has_env(pl);   // kernels compiled for an environment map
     int Nmax = 0;
     for (int q = 0; q < 4; ++q) Nmax = pl.q[q].N > Nmax ? pl.q[q].N : Nmax;
     const double ab = P == P_FP64 ? 8.0 : 4.0;
@@ -154,8 +155,13 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             if (pl.q[q].N >= 1 && n <= pl.q[q].N && !adj_T_fused(n, pl.q[q].N))
                 by += gTbytes(q, n) + gRbytes(q, n) + gRbytes(q, n - 1) + bytes_R(pl, q, n) + bytes_R(pl, q, n + 1);
         rec->begin(K_ADJ_MERGE_DOWN, n, by);
-        if (n >= 1) k_adj_T<P, C, 2><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
-        else k_adj_T<P, C, 1><<<row_grid_b(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
+        if (n >= 1) {
+            if (env) k_adj_T<P, C, 2, true><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
+            else k_adj_T<P, C, 2, false><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
+        } else {
+            if (env) k_adj_T<P, C, 1, true><<<row_grid_b(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
+            else k_adj_T<P, C, 1, false><<<row_grid_b(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
+        }
         rec->end();
         ++*launches;
     }
@@ -168,7 +174,8 @@ static cudaError_t bwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
                 by += gTbytes(q, n - 1) + gTbytes(q, n) + bytes_T(pl, q, n - 1) + gRbytes(q, n - 1) +
                       gRbytes(q, n - 2) + bytes_R(pl, q, n - 1) + bytes_R(pl, q, n);
         rec->begin(K_ADJ_MERGE_UP, n, by);
-        k_adj_merge_up<P, C><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
+        if (env) k_adj_merge_up<P, C, true><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
+        else k_adj_merge_up<P, C, false><<<row_grid_b(pl, rs.start[4], 2 * mt), mt, 0, st>>>(pl, rs, n);
         rec->end();
         ++*launches;
     }

@@ -38,12 +38,12 @@ __global__ void __launch_bounds__(512) k_merge_up(Plan pl, RowSplit rs, int n) {
     body_merge_up<P, C, G>(pl, rs, n, row, vb);
 }
 
-template <int P, int C, bool PAIR>
+template <int P, int C, bool PAIR, bool ENV>
 __global__ void __launch_bounds__(512) k_merge_down(Plan pl, RowSplit rs, int n) {
     long long row;
     int vb;
     row_block(pl, row, vb);
-    body_merge_down<P, C, PAIR>(pl, rs, n, row, vb);
+    body_merge_down<P, C, PAIR, ENV>(pl, rs, n, row, vb);
 }
 
 template <int P, int C>
@@ -54,12 +54,12 @@ __global__ void __launch_bounds__(512) k_merge_up4(Plan pl, RowSplit rs, int n) 
     body_merge_up4<P, C>(pl, rs, n, row, vb);
 }
 
-template <int P, int C>
+template <int P, int C, bool ENV>
 __global__ void __launch_bounds__(512) k_merge_down4(Plan pl, RowSplit rs, int n) {
     long long row;
     int vb;
     row_block(pl, row, vb);
-    body_merge_down4<P, C>(pl, rs, n, row, vb);
+    body_merge_down4<P, C, ENV>(pl, rs, n, row, vb);
 }
 
 // ---------------------------------------------------------------------------
@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(512) k_merge_down4(Plan pl, RowSplit rs, int n
 // (Eq. 14 at odd x, Eqs. 15-17 at even x), the T planes of the edge's row,
 // the far R window (its start rounded down to 16 bytes, clipped to the
 // row) and, at even x, the near R row; every thread then reads only shared
-// memory.  Out-of-range far values are zeroed by a select, never read.
+// memory.  Out-of-range far values (and R_N) are the environment's values
+// (0 without a map), chosen by a select; they are never read from the rows.
 // ---------------------------------------------------------------------------
 constexpr int kBV = 512;
 
@@ -83,7 +84,7 @@ template <int P, int C> struct BulkMD {
     }
 };
 
-template <int P, int C>
+template <int P, int C, bool ENV>
 __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, int n) {
     using SL = typename Prec<P>::SL;
     using ST = typename Prec<P>::ST;
@@ -188,6 +189,7 @@ __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, i
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             A L[4], r[4], r0[4];
+            const A ev = renv<P, C, ENV>(pl, q, n + 1, j[e], c);   // out of range: the environment
             ld4(tl + (e * C + c) * kBV + ti, L);
             ld2(rf + (e * C + c) * B::FW + fi, r[0], r[1]);
             ld2(rf + (e * C + c) * B::FW + fi + 2, r[2], r[3]);
@@ -195,10 +197,10 @@ __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, i
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
                 const int vf = v + l + off[e];
-                const A rr = (far_ok && vf >= 0 && vf < g.V) ? r[l] : A(0);
+                const A rr = (far_ok && vf >= 0 && vf < g.V) ? r[l] : ev;
                 const A f = fma(Aj, L[l], tr[l] * rr);
                 if (odd) acc[l][c] += f;                                         // Eq. 14
-                else acc[l][c] += A(0.5) * ((near_ok ? r0[l] : A(0)) + f);       // Eqs. 15-17
+                else acc[l][c] += A(0.5) * ((near_ok ? r0[l] : ev) + f);         // Eqs. 15-17
             }
         }
     }
@@ -210,10 +212,10 @@ __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, i
     }
 }
 
-template <int P, int C, class OUT>
+template <int P, int C, class OUT, bool ENV>
 __global__ void __launch_bounds__(128) k_fluence(Plan pl, OUT *__restrict__ F) {
     __shared__ __align__(16) unsigned char smem[fluence_smem<P, C>()];
-    body_fluence<P, C, OUT>(pl, F, blockIdx.x, blockIdx.y, smem);
+    body_fluence<P, C, OUT, ENV>(pl, F, blockIdx.x, blockIdx.y, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -322,6 +324,7 @@ template <int P, int C>
 static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
                             cudaStream_t st, int *launches, Recorder *rec, bool with_sum) {
     const int bs = 256;
+    const bool env = plan_has_env(pl);   // kernels compiled for an environment map
     int Nmax = 0;
     for (int q = 0; q < 4; ++q) Nmax = pl.q[q].N > Nmax ? pl.q[q].N : Nmax;
     const float *ef = (const float *)e, *sf = (const float *)s;
@@ -381,12 +384,18 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             }
             const int mt = pl.mthreads;
             rec->begin(K_MERGE_DOWN, n, by);
-            if (n >= 1 && pl.mdown == 1 && P != P_FP64)
-                k_merge_down_bulk<P, C><<<row_grid(pl, rs.start[4], kBV), 128, BulkMD<P, C>::bytes(), st>>>(pl, rs, n);
-            else if (n >= 1) k_merge_down4<P, C><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
-            else {
+            if (n >= 1 && pl.mdown == 1 && P != P_FP64) {
+                if (env)
+                    k_merge_down_bulk<P, C, true><<<row_grid(pl, rs.start[4], kBV), 128, BulkMD<P, C>::bytes(), st>>>(pl, rs, n);
+                else
+                    k_merge_down_bulk<P, C, false><<<row_grid(pl, rs.start[4], kBV), 128, BulkMD<P, C>::bytes(), st>>>(pl, rs, n);
+            } else if (n >= 1) {
+                if (env) k_merge_down4<P, C, true><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
+                else k_merge_down4<P, C, false><<<row_grid(pl, rs.start[4], 4 * mt), mt, 0, st>>>(pl, rs, n);
+            } else {
                 const int ts = 2 * mt > 512 ? 512 : 2 * mt;   // single v per thread at level 0
-                k_merge_down<P, C, false><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
+                if (env) k_merge_down<P, C, false, true><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
+                else k_merge_down<P, C, false, false><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, n);
             }
             rec->end();
             ++*launches;
@@ -403,8 +412,13 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         dim3 grid((pl.W + 31) / 32, (pl.H + 31) / 32);
         rec->begin(K_FLUENCE_SUM, 0, by);
         // 128 threads: every tile of a 1024^2 image is resident at once
-        if (P == P_FP64) k_fluence<P, C, double><<<grid, 128, 0, st>>>(pl, (double *)F);
-        else k_fluence<P, C, float><<<grid, 128, 0, st>>>(pl, (float *)F);
+        if (P == P_FP64) {
+            if (env) k_fluence<P, C, double, true><<<grid, 128, 0, st>>>(pl, (double *)F);
+            else k_fluence<P, C, double, false><<<grid, 128, 0, st>>>(pl, (double *)F);
+        } else {
+            if (env) k_fluence<P, C, float, true><<<grid, 128, 0, st>>>(pl, (float *)F);
+            else k_fluence<P, C, float, false><<<grid, 128, 0, st>>>(pl, (float *)F);
+        }
         rec->end();
         ++*launches;
     }
@@ -418,7 +432,8 @@ static cudaError_t r0_impl(const Plan &pl, cudaStream_t st) {
     RowSplit rs = make_split(pl, 0, 2, -1);
     if (rs.start[4] == 0) return cudaSuccess;
     const int ts = 2 * pl.mthreads > 512 ? 512 : 2 * pl.mthreads;
-    k_merge_down<P, C, false><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, 0);
+    if (plan_has_env(pl)) k_merge_down<P, C, false, true><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, 0);
+    else k_merge_down<P, C, false, false><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, 0);
     return cudaGetLastError();
 }
 
@@ -463,10 +478,14 @@ static cudaError_t prepare_prec() {
     set((const void *)k_trace012<P, 3>, TraceTile<typename Prec<P>::A, 3>::bytes());
     set((const void *)k_trace012<P, 4>, TraceTile<typename Prec<P>::A, 4>::bytes());
     if constexpr (P != P_FP64) {
-        set((const void *)k_merge_down_bulk<P, 1>, BulkMD<P, 1>::bytes());
-        set((const void *)k_merge_down_bulk<P, 2>, BulkMD<P, 2>::bytes());
-        set((const void *)k_merge_down_bulk<P, 3>, BulkMD<P, 3>::bytes());
-        set((const void *)k_merge_down_bulk<P, 4>, BulkMD<P, 4>::bytes());
+        set((const void *)k_merge_down_bulk<P, 1, false>, BulkMD<P, 1>::bytes());
+        set((const void *)k_merge_down_bulk<P, 1, true>, BulkMD<P, 1>::bytes());
+        set((const void *)k_merge_down_bulk<P, 2, false>, BulkMD<P, 2>::bytes());
+        set((const void *)k_merge_down_bulk<P, 2, true>, BulkMD<P, 2>::bytes());
+        set((const void *)k_merge_down_bulk<P, 3, false>, BulkMD<P, 3>::bytes());
+        set((const void *)k_merge_down_bulk<P, 3, true>, BulkMD<P, 3>::bytes());
+        set((const void *)k_merge_down_bulk<P, 4, false>, BulkMD<P, 4>::bytes());
+        set((const void *)k_merge_down_bulk<P, 4, true>, BulkMD<P, 4>::bytes());
     }
     return e;
 }

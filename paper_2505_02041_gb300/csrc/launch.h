@@ -156,6 +156,13 @@ cudaError_t launch_bounce_adj(const Plan &pl, bool first, bool has_prev, const v
                               const void *Fp, const void *a, const void *s, void *ge, void *gs, void *ga, void *gFp,
                               cudaStream_t st, int *launches, Recorder *rec);
 
+// Environment table of a map env[C][M] (kernels_env.cu): 4 * stride doubles
+// then the same values as floats, stride = 2^(Nmax + 1) * C elements per
+// frame, entry (2^n + j) * C + c; see Plan::envf / envd.
+long long env_table_stride(const Plan &pl);
+size_t env_table_bytes(const Plan &pl);
+cudaError_t launch_env_table(const Plan &pl, const float *env, int M, void *table, cudaStream_t st);
+
 // Dense fp32 copy of level n of frame q (which = 0: T_n, 1: R_n).
 cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *dst, cudaStream_t st);
 
