@@ -120,6 +120,24 @@ def bench_bounces(h, e, s, timed, hbm_peak, K=6, rho=0.5, steps=5):
     return out
 
 
+def bench_environment(h, fwd, fwd_bwd, timed, steps=10):
+    """The frame under an environment map (footnote 1 of Sec. 4.2; a smooth
+    sky-like map of 256 directions): graph-launched forward and
+    forward+backward."""
+    import math
+    import torch
+    C = h.C
+    th = torch.tensor([2 * math.pi * (m + 0.5) / 256 for m in range(256)], device="cuda")
+    env = torch.stack([1.0 + 0.8 * torch.sin(th + 0.3 * k) for k in range(C)]).float().contiguous()
+    h.set_environment(env)
+    for _ in range(3):
+        fwd_bwd()
+    out = {"map_directions": 256, "forward_ms": statistics.mean(timed(fwd, steps)),
+           "fwd_bwd_ms": statistics.mean(timed(fwd_bwd, steps))}
+    h.set_environment(None)
+    return out
+
+
 def traffic_key(kind, cfg):
     """The kernel variant whose DRAM bytes stand for `kind`: the merge down
     has a per-thread-load kernel (mdown 0) and a bulk-copy-staged one
@@ -313,15 +331,30 @@ def run_ours(args):
         # --nvtx --nvtx-include "hrc_profile/"), in a fixed launch
         # configuration: the autotuner's usual pick at 1024^2 (its timings are
         # meaningless under a profiler, which serialises every launch).
+        # --profile-blur adds the Eq. 21 cross blur to both passes,
+        # --profile-bounces K runs a K-bounce forward + backward instead.
         h.set_launch_config(*args.profile_config)
         gF1 = torch.ones((C, H, W), dtype=torch.float32, device=dev)
-        h.forward(e, s, F)
-        h.backward(gF1)
+        if args.profile_blur:
+            h.set_cross_blur(True)
+        K = args.profile_bounces
+        if K > 0:
+            h.reserve_bounces(K)
+            alb = torch.full_like(e, 0.5)
+
+        def passes():
+            if K > 0:
+                h.forward_bounces(e, s, alb, K, F)
+                h.backward_bounces(gF1)
+            else:
+                h.forward(e, s, F)
+                h.backward(gF1)
+
+        passes()
         torch.cuda.synchronize(dev)
         _lib.hrc_set_timing(h.ctx, True)
         torch.cuda.nvtx.range_push("hrc_profile")
-        h.forward(e, s, F)
-        h.backward(gF1)
+        passes()
         torch.cuda.synchronize(dev)
         torch.cuda.nvtx.range_pop()
         _lib.hrc_set_timing(h.ctx, False)
@@ -494,6 +527,7 @@ def run_ours(args):
     }
     line["cross_blur"] = bench_cross_blur(h, fwd, fwd_bwd, timed, gF, gE, gS, hbm_peak)
     line["multi_bounce"] = bench_bounces(h, e, s, timed, hbm_peak)
+    line["environment"] = bench_environment(h, fwd, fwd_bwd, timed)
     if args.precisions and world == 1:
         import oracle
         Fr = oracle.fluence(e_np, s_np)
@@ -604,6 +638,9 @@ def main():
     ap.add_argument("--profile-config", type=int, nargs=5, default=[0, 1, 128, 1, 0],
                     metavar=("SCHEDULE", "GROUPS", "THREADS", "VMAJOR", "MDOWN"),
                     help="launch configuration of --profile-once (default: the autotuner's usual pick at 1024^2)")
+    ap.add_argument("--profile-blur", action="store_true", help="--profile-once with the cross blur on")
+    ap.add_argument("--profile-bounces", type=int, default=0,
+                    help="--profile-once: a forward + backward of this many bounces (albedo 0.5)")
     ap.add_argument("--profile-once", action="store_true",
                     help="run one forward + backward inside the NVTX range hrc_profile with direct "
                          "launches in --profile-config (a target for ncu), print no bench line")
