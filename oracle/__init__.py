@@ -151,11 +151,31 @@ def _env(env, C):
     return env
 
 
+def _per_channel(fn, e, s, *rest):
+    """Per-channel extinction s[C][H][W] (the paper stores T as C-vectors,
+    Sec. 5): Merge (Eq. 7), the Eq. 20 blend, the merge down (Eqs. 14-17),
+    the fluence sum, the cross blur and the bounce source all act channel
+    by channel, and Trace gives channel c's radiance and transmittance from
+    (e_c, sigma_c) alone, so the method is exactly C independent
+    single-channel problems; fn(c, e_c, s_c, *rest_c) solves channel c.
+    Returns the channel results stacked (tuples stacked element-wise)."""
+    e = np.asarray(e)
+    s = np.asarray(s)
+    assert s.ndim == 3 and s.shape[0] == e.shape[0]
+    outs = [fn(c, e[c:c + 1], s[c], *[np.asarray(r)[c:c + 1] for r in rest]) for c in range(s.shape[0])]
+    if isinstance(outs[0], tuple):
+        return tuple(np.concatenate([o[i] if o[i].ndim == 3 else o[i][None] for o in outs]) for i in range(len(outs[0])))
+    return np.concatenate(outs)
+
+
 def fluence(e, s, cascades: int = 0, env=None) -> np.ndarray:
     """Algorithm 1 (Lighting): F[C][H][W] in float64.  `env` ([C][M] or [M]):
     an environment map (footnote 1 of Sec. 4.2), radiance seen along the
     image-space look angle theta_m = 2 pi (m + 1/2) / M (theta from +x
     towards +y = down the rows), linearly interpolated."""
+    if np.ndim(s) == 3:
+        return _per_channel(lambda c, ec, sc: fluence(ec, sc, cascades, None if env is None else _env(env, len(e))[c:c + 1]),
+                            e, s)
     e, s, C, H, W = _img(e, s)
     F = np.zeros((C, H, W))
     if env is None:
@@ -190,6 +210,10 @@ def frame_level(e, s, q: int, which: str, n: int, cascades: int = 0) -> np.ndarr
 def fluence_adjoint(e, s, gF, cascades: int = 0, env=None):
     """Gradient of sum(gF * F) w.r.t. (e, s), float64 (with the environment
     map `env` as in fluence, held fixed)."""
+    if np.ndim(s) == 3:
+        return _per_channel(lambda c, ec, sc, gc: fluence_adjoint(ec, sc, gc, cascades,
+                                                                  None if env is None else _env(env, len(e))[c:c + 1]),
+                            e, s, np.asarray(gF).reshape(np.shape(e)))
     e, s, C, H, W = _img(e, s)
     gF = np.ascontiguousarray(gF, dtype=np.float64).reshape(C, H, W)
     ge = np.zeros((C, H, W))
@@ -207,7 +231,10 @@ def cross_blur(F, s, threshold: float = 0.5) -> np.ndarray:
     """The cross blur of Eq. 21 with opacity rejection (Sec. 4.2): each pixel
     averages itself (weight 4) with the edge neighbours (weight 1) inside the
     grid whose opacity 1 - exp(-sigma) is within `threshold` of its own, the
-    kept weights renormalised.  F[C][H][W] -> float64 [C][H][W]."""
+    kept weights renormalised.  F[C][H][W] -> float64 [C][H][W]; with
+    per-channel extinction s[C][H][W], channel c tests sigma_c."""
+    if np.ndim(s) == 3:
+        return _per_channel(lambda c, Fc, sc: cross_blur(Fc, sc, threshold), F, s)
     F, s, C, H, W = _img(F, s)
     out = np.zeros((C, H, W))
     lib().orc_cross_blur(_p(F), _p(s), C, W, H, float(threshold), _p(out))
@@ -216,6 +243,8 @@ def cross_blur(F, s, threshold: float = 0.5) -> np.ndarray:
 
 def cross_blur_adjoint(g, s, threshold: float = 0.5) -> np.ndarray:
     """Transpose of cross_blur for fixed sigma: dL/dF from dL/d(blurred F)."""
+    if np.ndim(s) == 3:
+        return _per_channel(lambda c, gc, sc: cross_blur_adjoint(gc, sc, threshold), g, s)
     g, s, C, H, W = _img(g, s)
     gF = np.zeros((C, H, W))
     lib().orc_cross_blur_adjoint(_p(g), _p(s), C, W, H, float(threshold), _p(gF))
@@ -249,7 +278,8 @@ def bounce_source(e, s, albedo, F, _mutant=0):
     with extinction sigma and albedo rho scatters sigma * rho of the fluence F
     (radiance integrated over the full turn) evenly over 2 pi, so its source
     per unit length becomes e + rho * sigma * F / (2 pi)."""
-    k = (1.0 if _mutant == 1 else s[None]) * albedo * F
+    sb = s if np.ndim(s) == 3 else s[None]   # per-channel extinction: sigma_c for channel c
+    k = (1.0 if _mutant == 1 else sb) * albedo * F
     return e + (k if _mutant == 2 else k / (2.0 * np.pi))
 
 
@@ -257,6 +287,9 @@ def fluence_bounces(e, s, albedo, bounces: int, cascades: int = 0, blur=None, _m
     """Multi-bounce lighting: F_0 = Lighting(e), e_k = e + albedo * s * F_{k-1}
     / (2 pi), F_k = Lighting(e_k); returns F_bounces (float64 [C][H][W]).
     `blur` = None, or the cross-blur threshold applied by every Lighting."""
+    if np.ndim(s) == 3:
+        return _per_channel(lambda c, ec, sc, ac: fluence_bounces(ec, sc, ac, bounces, cascades, blur, _mutant),
+                            e, s, albedo)
     e, s, C, H, W = _img(e, s)
     albedo = np.ascontiguousarray(albedo, dtype=np.float64).reshape(C, H, W)
     F = _lighting(e, s, cascades, blur)
@@ -269,6 +302,10 @@ def fluence_bounces_adjoint(e, s, albedo, gF, bounces: int, cascades: int = 0, b
     """Gradient of sum(gF * fluence_bounces(...)) w.r.t. (e, s, albedo), by
     the reverse of the iteration: the adjoint of Lighting at each e_k, and of
     the source update through F_{k-1}, s and albedo."""
+    if np.ndim(s) == 3:
+        return _per_channel(lambda c, ec, sc, ac, gc: fluence_bounces_adjoint(ec, sc, ac, gc, bounces, cascades, blur,
+                                                                             _mutant),
+                            e, s, albedo, np.asarray(gF).reshape(np.shape(e)))
     e, s, C, H, W = _img(e, s)
     albedo = np.ascontiguousarray(albedo, dtype=np.float64).reshape(C, H, W)
     g = np.ascontiguousarray(gF, dtype=np.float64).reshape(C, H, W)
