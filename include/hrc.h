@@ -170,6 +170,25 @@ hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on);
 hrc_status hrc_set_cross_blur(hrc_ctx *ctx, int enable, float threshold);
 hrc_status hrc_get_cross_blur(const hrc_ctx *ctx, int *enable, float *threshold);
 
+/* Per-channel extinction (the paper keeps T as C-vectors, Sec. 5).  With
+ * per_channel = 1, every later call on this single-scene context takes
+ * sigma_t as [C][H][W] (channel c has its own extinction) and returns
+ * dLoss/d sigma_t as [C][H][W]; with 0 (the default) sigma_t is one [H][W]
+ * plane shared by the channels.  Once the transmittance is per channel,
+ * every step of the method (Merge, the Eq. 20 blend, the merge down, the
+ * fluence sum, the cross blur, the bounce source) acts channel by channel,
+ * so the context runs C single-channel contexts (created by the first
+ * enable, each with its own level buffers: C radiances and C
+ * transmittances per entry in all) on its stream; its settings (stream,
+ * precision, launch configuration, backward strategy, cross blur, bounce
+ * reservation, timing, environment map row c for channel c) are mirrored
+ * into them.  Channel planes whose address is not 16-byte aligned (W * H
+ * not a multiple of 4) pass through context-owned staging buffers.
+ * hrc_copy_level answers HRC_ESTATE in this mode.  HRC_EINVAL on a batched
+ * context or for other values; HRC_ENOMEM if the channel contexts do not
+ * fit. */
+hrc_status hrc_set_channel_extinction(hrc_ctx *ctx, int per_channel);
+
 /* Environment map (footnote 1 of Sec. 4.2): light arriving from outside
  * the grid, with nothing outside that absorbs or emits.  env is a device
  * array [C][M] (fp32, 16-byte aligned): the radiance seen along the image

@@ -33,6 +33,7 @@ SIGNATURES = [
     ("hrc_set_cross_blur", _i, [_vp, _i, ctypes.c_float]),
     ("hrc_get_cross_blur", _i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
     ("hrc_set_environment", _i, [_vp, _vp, _i]),
+    ("hrc_set_channel_extinction", _i, [_vp, _i]),
     ("hrc_reserve_bounces", _i, [_vp, _i]),
     ("hrc_fluence_bounces", _i, [_vp, _vp, _vp, _vp, _i, _vp]),
     ("hrc_fluence_bounces_backward", _i, [_vp, _vp, _vp, _vp, _vp]),
@@ -148,6 +149,10 @@ def hrc_get_cross_blur(ctx):
 
 def hrc_set_environment(ctx, env, M: int):
     check(load().hrc_set_environment(ctx, ptr(env), M), ctx)
+
+
+def hrc_set_channel_extinction(ctx, per_channel: bool):
+    check(load().hrc_set_channel_extinction(ctx, int(bool(per_channel))), ctx)
 
 
 def hrc_reserve_bounces(ctx, max_bounces: int):

@@ -47,6 +47,7 @@ class HRC:
         self._borrowed = (None, None, 0, 0)
         self._host_levels = False
         self._bounced = None
+        self.per_channel = False
         self.set_precision(precision)
 
     # -- configuration -----------------------------------------------------
@@ -67,7 +68,7 @@ class HRC:
     def forward(self, emission, sigma_t, out=None):
         C, H, W = self.C, self.H, self.W
         emission = _dev_tensor(emission, self.dtype, (C, H, W), "emission")
-        sigma_t = _dev_tensor(sigma_t, self.dtype, (H, W), "sigma_t")
+        sigma_t = _dev_tensor(sigma_t, self.dtype, self.sigma_shape, "sigma_t")
         if out is None:
             out = torch.empty((C, H, W), dtype=self.dtype, device=emission.device)
         self._stream()
@@ -99,7 +100,7 @@ class HRC:
         emission = emission.contiguous()
         sigma_t = sigma_t.contiguous()
         assert emission.dtype == torch.float32 and tuple(emission.shape) == (C, H, W)
-        assert sigma_t.dtype == torch.float32 and tuple(sigma_t.shape) == (H, W)
+        assert sigma_t.dtype == torch.float32 and tuple(sigma_t.shape) == self.sigma_shape
         if out is None:
             out = torch.empty((C, H, W), dtype=torch.float32, pin_memory=emission.is_pinned())
         self._stream()
@@ -121,13 +122,25 @@ class HRC:
         # (no forward at all: the library answers HRC_ESTATE)
         grad_F = _dev_tensor(grad_F, self.dtype, (C, H, W), "grad_F")
         ge = torch.empty((C, H, W), dtype=self.dtype, device=grad_F.device)
-        gs = torch.empty((H, W), dtype=self.dtype, device=grad_F.device)
+        gs = torch.empty(self.sigma_shape, dtype=self.dtype, device=grad_F.device)
         self._stream()
         if self.precision == "fp64":
             _lib.hrc_fluence_backward_f64(self.ctx, grad_F, ge, gs)
         else:
             _lib.hrc_fluence_backward(self.ctx, grad_F, ge, gs)
         return ge, gs
+
+    def set_channel_extinction(self, per_channel: bool = True) -> None:
+        """sigma_t per channel ([C][H][W]) instead of one shared [H][W] plane
+        (hrc_set_channel_extinction); dL/dsigma_t then has the same shape."""
+        _lib.hrc_set_channel_extinction(self.ctx, per_channel)
+        self.per_channel = bool(per_channel)
+        self._borrowed = (None, None, 0, 0)
+        self._bounced = None
+
+    @property
+    def sigma_shape(self):
+        return (self.C, self.H, self.W) if self.per_channel else (self.H, self.W)
 
     def set_environment(self, env=None) -> None:
         """Environment map (footnote 1 of Sec. 4.2): a CUDA float32 tensor
@@ -156,7 +169,7 @@ class HRC:
         back into the emission (see hrc_fluence_bounces)."""
         C, H, W = self.C, self.H, self.W
         emission = _dev_tensor(emission, self.dtype, (C, H, W), "emission")
-        sigma_t = _dev_tensor(sigma_t, self.dtype, (H, W), "sigma_t")
+        sigma_t = _dev_tensor(sigma_t, self.dtype, self.sigma_shape, "sigma_t")
         albedo = _dev_tensor(albedo, self.dtype, (C, H, W), "albedo")
         if out is None:
             out = torch.empty((C, H, W), dtype=self.dtype, device=emission.device)
@@ -184,7 +197,7 @@ class HRC:
                 self.forward_bounces(emission, sigma_t, albedo, bounces)
         grad_F = _dev_tensor(grad_F, self.dtype, (C, H, W), "grad_F")
         ge = torch.empty((C, H, W), dtype=self.dtype, device=grad_F.device)
-        gs = torch.empty((H, W), dtype=self.dtype, device=grad_F.device)
+        gs = torch.empty(self.sigma_shape, dtype=self.dtype, device=grad_F.device)
         ga = torch.empty((C, H, W), dtype=self.dtype, device=grad_F.device)
         self._stream()
         if self.precision == "fp64":
@@ -198,7 +211,7 @@ class HRC:
         one bounce per frame."""
         C, H, W = self.C, self.H, self.W
         emission = _dev_tensor(emission, torch.float32, (C, H, W), "emission")
-        sigma_t = _dev_tensor(sigma_t, torch.float32, (H, W), "sigma_t")
+        sigma_t = _dev_tensor(sigma_t, torch.float32, self.sigma_shape, "sigma_t")
         albedo = _dev_tensor(albedo, torch.float32, (C, H, W), "albedo")
         fluence = _dev_tensor(fluence, torch.float32, (C, H, W), "fluence")
         if out is None:

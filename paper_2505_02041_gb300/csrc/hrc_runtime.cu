@@ -205,9 +205,21 @@ struct hrc_ctx {
     const void *last_a = nullptr;
     int last_K = 0;
     bool bounce_levels_ok = false;  // the level buffers hold those of bounce last_K
-    // environment map: per-frame, per-level cone values (kernels_env.cu)
+    // environment map: per-frame, per-level cone values (kernels_env.cu), and
+    // a copy of the map with 16-byte-aligned rows (for per-channel contexts)
     char *env_tab = nullptr;
     bool env_on = false;
+    float *env_map = nullptr;
+    int env_M = 0, env_pitch = 0;
+    // per-channel extinction: one single-channel context per channel (the
+    // method separates exactly by channel once the extinction does), on this
+    // context's stream; channel planes whose address is not 16-byte aligned
+    // (W * H not a multiple of 4) pass through kStagePlanes aligned buffers
+    bool per_channel = false;
+    std::vector<hrc_ctx *> chan;
+    char *chan_stage = nullptr;
+    size_t chan_plane = 0;
+    static constexpr int kStagePlanes = 7;   // e, sigma, albedo, F / dL/dF, dL/de, dL/dsigma, dL/dalbedo
     int launches = 0;
     Recorder rec;
     std::string err;
@@ -427,11 +439,21 @@ int hrc_last_launch_count(const hrc_ctx *ctx) { return ctx ? ctx->launches : 0; 
 hrc_status hrc_set_timing(hrc_ctx *ctx, int enable) {
     if (!ctx) return HRC_EINVAL;
     ctx->rec.on = enable != 0;
+    for (hrc_ctx *k : ctx->chan) hrc_set_timing(k, enable);
     return HRC_OK;
 }
 
 int hrc_get_timing(hrc_ctx *ctx, hrc_kernel_time *out, int cap) {
     if (!ctx) return -1;
+    if (ctx->per_channel) {   // the channels' records, channel after channel
+        int n = 0;
+        for (hrc_ctx *k : ctx->chan) {
+            const int m = hrc_get_timing(k, out ? out + n : nullptr, cap - n);
+            if (m < 0) return -1;
+            n += m;
+        }
+        return n;
+    }
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return -1;
     int n = 0;
     for (const auto &r : ctx->rec.recs) {
@@ -502,6 +524,9 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->blur_buf);
     cudaFree(ctx->bounce_buf);
     cudaFree(ctx->env_tab);
+    cudaFree(ctx->env_map);
+    cudaFree(ctx->chan_stage);
+    for (hrc_ctx *k : ctx->chan) hrc_destroy(k);
     for (auto &g : ctx->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     cudaFree(ctx->d_plans);
@@ -534,6 +559,7 @@ hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule) {
     ctx->sched = schedule;
     ctx->plan.sched = schedule;
     ctx->plan64.sched = schedule;
+    for (hrc_ctx *k : ctx->chan) hrc_set_schedule(k, schedule);
     return HRC_OK;
 }
 
@@ -584,6 +610,7 @@ hrc_status hrc_set_backward_recompute(hrc_ctx *ctx, int on) {
     if (!ctx) return HRC_EINVAL;
     if (on != 0 && on != 1) return fail(ctx, HRC_EINVAL, "hrc_set_backward_recompute: 0 or 1");
     ctx->bwd_recompute = on != 0;
+    for (hrc_ctx *k : ctx->chan) hrc_set_backward_recompute(k, on);
     return HRC_OK;
 }
 
@@ -604,6 +631,10 @@ hrc_status hrc_set_cross_blur(hrc_ctx *ctx, int enable, float threshold) {
     ctx->blur = enable != 0;
     ctx->blur_thr = threshold;
     clear_graphs(ctx);   // the graphs hold the pass as it was captured
+    for (hrc_ctx *k : ctx->chan) {
+        hrc_status st = hrc_set_cross_blur(k, enable, threshold);
+        if (st != HRC_OK) return fail(ctx, st, k->err);
+    }
     return HRC_OK;
 }
 
@@ -630,12 +661,20 @@ hrc_status hrc_set_launch_config(hrc_ctx *ctx, const hrc_launch_config *cfg) {
     if (!config_valid(ctx, *cfg)) return fail(ctx, HRC_EINVAL, "hrc_set_launch_config: value out of range");
     apply_config(ctx, *cfg);
     ctx->have_fwd = false;
+    for (hrc_ctx *k : ctx->chan) hrc_set_launch_config(k, cfg);
     return HRC_OK;
 }
 
 hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
     hrc_status st = check_ctx(ctx);
     if (st != HRC_OK) return st;
+    if (ctx->per_channel) {   // tune one channel's context, apply its pick to all
+        st = hrc_autotune(ctx->chan[0], best_ms);
+        if (st != HRC_OK) return fail(ctx, st, ctx->chan[0]->err);
+        hrc_launch_config c;
+        hrc_get_launch_config(ctx->chan[0], &c);
+        return hrc_set_launch_config(ctx, &c);
+    }
     if (ctx->batched || ctx->prec == P_FP64) return fail(ctx, HRC_EINVAL, "hrc_autotune: single-scene fp32/fp16/bf16 contexts");
     // the timing does not depend on the data: time on the context's own buffers
     const size_t img = (size_t)ctx->W * ctx->H;
@@ -680,6 +719,7 @@ hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
 hrc_status hrc_set_stream(hrc_ctx *ctx, void *stream) {
     if (!ctx) return HRC_EINVAL;
     ctx->stream = (cudaStream_t)stream;
+    for (hrc_ctx *k : ctx->chan) hrc_set_stream(k, stream);
     return HRC_OK;
 }
 
@@ -749,6 +789,185 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
     ctx->have_fwd = false;
     ctx->have_bounce = false;
     apply_env(ctx);
+    for (hrc_ctx *k : ctx->chan) {
+        hrc_status st = hrc_set_precision(k, prec);
+        if (st != HRC_OK) return fail(ctx, st, k->err);
+    }
+    return HRC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Channel c's plane of a [C][H][W] argument: p + c W H elements, read
+// directly when 16-byte aligned, else copied into aligned staging buffer
+// `slot` of that channel first (inputs) or written there and copied out
+// afterwards (outputs).
+struct ChanArgs {
+    hrc_ctx *ctx;
+    size_t esz, plane;
+    cudaError_t err = cudaSuccess;
+    char *stage(int c, int slot) const {
+        return ctx->chan_stage + ((size_t)c * hrc_ctx::kStagePlanes + slot) * ctx->chan_plane;
+    }
+    const void *in(int c, int slot, const void *p) {
+        const char *q = static_cast<const char *>(p) + (size_t)c * plane;
+        if (aligned16(q)) return q;
+        if (err == cudaSuccess) err = cudaMemcpyAsync(stage(c, slot), q, plane, cudaMemcpyDeviceToDevice, ctx->stream);
+        return stage(c, slot);
+    }
+    void *out(int c, int slot, void *p) const {
+        char *q = static_cast<char *>(p) + (size_t)c * plane;
+        return aligned16(q) ? static_cast<void *>(q) : static_cast<void *>(stage(c, slot));
+    }
+    void done(int c, int slot, void *p) {
+        char *q = static_cast<char *>(p) + (size_t)c * plane;
+        if (!aligned16(q) && err == cudaSuccess)
+            err = cudaMemcpyAsync(q, stage(c, slot), plane, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+};
+
+ChanArgs chan_args(hrc_ctx *ctx, bool f64) {
+    ChanArgs a{ctx, f64 ? sizeof(double) : sizeof(float), 0};
+    a.plane = (size_t)ctx->W * ctx->H * a.esz;
+    return a;
+}
+
+// Sum of the channels' launch counts into the parent's.
+void chan_launches(hrc_ctx *ctx) {
+    int n = 0;
+    for (hrc_ctx *k : ctx->chan) n += k->launches;
+    ctx->launches = n;
+}
+
+hrc_status chan_status(hrc_ctx *ctx, hrc_status st, hrc_ctx *k) { return st == HRC_OK ? st : fail(ctx, st, k->err); }
+
+hrc_status chan_forward(hrc_ctx *ctx, const void *e, const void *s, void *F, bool f64) {
+    if (!e || !s || !F) return fail(ctx, HRC_EINVAL, "hrc_fluence: NULL pointer");
+    ChanArgs a = chan_args(ctx, f64);
+    for (int c = 0; c < ctx->C; ++c) {
+        hrc_ctx *k = ctx->chan[c];
+        const void *ec = a.in(c, 0, e), *sc = a.in(c, 1, s);
+        void *Fc = a.out(c, 3, F);
+        if (a.err != cudaSuccess) return cuda_fail(ctx, a.err, "hrc_fluence (per-channel staging)");
+        hrc_status st = f64 ? hrc_fluence_f64(k, (const double *)ec, (const double *)sc, (double *)Fc)
+                            : hrc_fluence(k, (const float *)ec, (const float *)sc, (float *)Fc);
+        if (st != HRC_OK) return chan_status(ctx, st, k);
+        a.done(c, 3, F);
+    }
+    if (a.err != cudaSuccess) return cuda_fail(ctx, a.err, "hrc_fluence (per-channel staging)");
+    chan_launches(ctx);
+    ctx->have_fwd = true;
+    return HRC_OK;
+}
+
+hrc_status chan_backward(hrc_ctx *ctx, const void *gF, void *ge, void *gs, bool f64) {
+    if (!gF || !ge || !gs) return fail(ctx, HRC_EINVAL, "hrc_fluence_backward: NULL pointer");
+    ChanArgs a = chan_args(ctx, f64);
+    for (int c = 0; c < ctx->C; ++c) {
+        hrc_ctx *k = ctx->chan[c];
+        const void *gc = a.in(c, 3, gF);
+        void *ec = a.out(c, 4, ge), *sc = a.out(c, 5, gs);
+        if (a.err != cudaSuccess) return cuda_fail(ctx, a.err, "hrc_fluence_backward (per-channel staging)");
+        hrc_status st = f64 ? hrc_fluence_backward_f64(k, (const double *)gc, (double *)ec, (double *)sc)
+                            : hrc_fluence_backward(k, (const float *)gc, (float *)ec, (float *)sc);
+        if (st != HRC_OK) return chan_status(ctx, st, k);
+        a.done(c, 4, ge);
+        a.done(c, 5, gs);
+    }
+    if (a.err != cudaSuccess) return cuda_fail(ctx, a.err, "hrc_fluence_backward (per-channel staging)");
+    chan_launches(ctx);
+    return HRC_OK;
+}
+
+hrc_status chan_bounces(hrc_ctx *ctx, const void *e, const void *s, const void *al, int K, void *F, bool f64) {
+    if (!e || !s || !al || !F) return fail(ctx, HRC_EINVAL, "hrc_fluence_bounces: NULL pointer");
+    ChanArgs a = chan_args(ctx, f64);
+    for (int c = 0; c < ctx->C; ++c) {
+        hrc_ctx *k = ctx->chan[c];
+        const void *ec = a.in(c, 0, e), *sc = a.in(c, 1, s), *ac = a.in(c, 2, al);
+        void *Fc = a.out(c, 3, F);
+        if (a.err != cudaSuccess) return cuda_fail(ctx, a.err, "hrc_fluence_bounces (per-channel staging)");
+        hrc_status st =
+            f64 ? hrc_fluence_bounces_f64(k, (const double *)ec, (const double *)sc, (const double *)ac, K, (double *)Fc)
+                : hrc_fluence_bounces(k, (const float *)ec, (const float *)sc, (const float *)ac, K, (float *)Fc);
+        if (st != HRC_OK) return chan_status(ctx, st, k);
+        a.done(c, 3, F);
+    }
+    if (a.err != cudaSuccess) return cuda_fail(ctx, a.err, "hrc_fluence_bounces (per-channel staging)");
+    chan_launches(ctx);
+    ctx->have_bounce = true;
+    return HRC_OK;
+}
+
+hrc_status chan_bounces_backward(hrc_ctx *ctx, const void *gF, void *ge, void *gs, void *ga, bool f64) {
+    if (!gF || !ge || !gs || !ga) return fail(ctx, HRC_EINVAL, "hrc_fluence_bounces_backward: NULL pointer");
+    ChanArgs a = chan_args(ctx, f64);
+    for (int c = 0; c < ctx->C; ++c) {
+        hrc_ctx *k = ctx->chan[c];
+        const void *gc = a.in(c, 3, gF);
+        void *ec = a.out(c, 4, ge), *sc = a.out(c, 5, gs), *ac = a.out(c, 6, ga);
+        if (a.err != cudaSuccess) return cuda_fail(ctx, a.err, "hrc_fluence_bounces_backward (per-channel staging)");
+        hrc_status st = f64 ? hrc_fluence_bounces_backward_f64(k, (const double *)gc, (double *)ec, (double *)sc, (double *)ac)
+                            : hrc_fluence_bounces_backward(k, (const float *)gc, (float *)ec, (float *)sc, (float *)ac);
+        if (st != HRC_OK) return chan_status(ctx, st, k);
+        a.done(c, 4, ge);
+        a.done(c, 5, gs);
+        a.done(c, 6, ga);
+    }
+    if (a.err != cudaSuccess) return cuda_fail(ctx, a.err, "hrc_fluence_bounces_backward (per-channel staging)");
+    chan_launches(ctx);
+    return HRC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hrc_status hrc_set_channel_extinction(hrc_ctx *ctx, int per_channel) {
+    if (!ctx) return HRC_EINVAL;
+    if (ctx->batched) return fail(ctx, HRC_EINVAL, "hrc_set_channel_extinction: single-scene contexts only");
+    if (per_channel != 0 && per_channel != 1) return fail(ctx, HRC_EINVAL, "hrc_set_channel_extinction: 0 or 1");
+    if (per_channel && ctx->chan.empty()) {
+        const size_t img = (size_t)ctx->W * ctx->H;
+        if (img % 4 != 0) {   // some channel planes are not 16-byte aligned: staging buffers
+            ctx->chan_plane = align_up(img * sizeof(double), 256);
+            cudaError_t e = cudaMalloc(&ctx->chan_stage, ctx->chan_plane * hrc_ctx::kStagePlanes * ctx->C);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                ctx->chan_stage = nullptr;
+                return fail(ctx, HRC_ENOMEM, "hrc_set_channel_extinction: staging buffers do not fit");
+            }
+        }
+        hrc_launch_config cfg;
+        hrc_get_launch_config(ctx, &cfg);
+        for (int c = 0; c < ctx->C; ++c) {
+            hrc_ctx *k = nullptr;
+            hrc_status st = hrc_create(ctx->W, ctx->H, 1, ctx->cascades, &k);
+            if (st == HRC_OK) ctx->chan.push_back(k);
+            if (st == HRC_OK) st = hrc_set_stream(k, ctx->stream);
+            if (st == HRC_OK) st = hrc_set_precision(k, (hrc_precision)ctx->prec);
+            if (st == HRC_OK) st = hrc_set_launch_config(k, &cfg);
+            if (st == HRC_OK) st = hrc_set_backward_recompute(k, ctx->bwd_recompute ? 1 : 0);
+            if (st == HRC_OK && ctx->blur_buf) st = hrc_set_cross_blur(k, ctx->blur ? 1 : 0, ctx->blur_thr);
+            if (st == HRC_OK && ctx->bounce_buf) st = hrc_reserve_bounces(k, ctx->bounce_cap);
+            if (st == HRC_OK) st = hrc_set_timing(k, ctx->rec.on ? 1 : 0);
+            if (st == HRC_OK && ctx->env_on)
+                st = hrc_set_environment(k, ctx->env_map + (size_t)c * ctx->env_pitch, ctx->env_M);
+            if (st != HRC_OK) {
+                std::string msg = k ? k->err : g_create_error;
+                for (hrc_ctx *x : ctx->chan) hrc_destroy(x);
+                ctx->chan.clear();
+                cudaFree(ctx->chan_stage);
+                ctx->chan_stage = nullptr;
+                return fail(ctx, st, "hrc_set_channel_extinction: " + msg);
+            }
+        }
+    }
+    ctx->per_channel = per_channel != 0;
+    ctx->have_fwd = false;
+    ctx->have_bounce = false;
     return HRC_OK;
 }
 
@@ -770,8 +989,26 @@ hrc_status hrc_set_environment(hrc_ctx *ctx, const float *env, int M) {
     }
     if (env) {
         cudaError_t e = launch_env_table(ctx->plan, env, M, ctx->env_tab, ctx->stream);
+        const int pitch = (M + 3) / 4 * 4;   // a row per channel, 16-byte aligned
+        if (e == cudaSuccess && pitch * ctx->C > ctx->env_pitch * ctx->C) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->env_map);
+            ctx->env_map = nullptr;
+            ctx->env_pitch = 0;
+            e = cudaMalloc(&ctx->env_map, sizeof(float) * pitch * ctx->C);
+        }
+        if (e == cudaSuccess) {
+            ctx->env_pitch = ctx->env_pitch > pitch ? ctx->env_pitch : pitch;
+            ctx->env_M = M;
+            e = cudaMemcpy2DAsync(ctx->env_map, sizeof(float) * ctx->env_pitch, env, sizeof(float) * M,
+                                  sizeof(float) * M, ctx->C, cudaMemcpyDeviceToDevice, ctx->stream);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_environment");
+    }
+    for (int c = 0; c < (int)ctx->chan.size(); ++c) {   // channel c sees row c
+        hrc_status st2 = hrc_set_environment(ctx->chan[c], env ? ctx->env_map + (size_t)c * ctx->env_pitch : nullptr, M);
+        if (st2 != HRC_OK) return fail(ctx, st2, ctx->chan[c]->err);
     }
     ctx->env_on = env != nullptr;
     apply_env(ctx);
@@ -784,6 +1021,7 @@ hrc_status hrc_set_environment(hrc_ctx *ctx, const float *env, int M) {
 hrc_status hrc_fluence(hrc_ctx *ctx, const float *emission, const float *sigma_t, float *out) {
     hrc_status st = check_ctx(ctx);
     if (st != HRC_OK) return st;
+    if (ctx->per_channel && ctx->prec != P_FP64) return chan_forward(ctx, emission, sigma_t, out, false);
     if (ctx->prec == P_FP64) return fail(ctx, HRC_ESTATE, "hrc_fluence: context is in HRC_FP64_TEST; use hrc_fluence_f64");
     if (ctx->batched) return fail(ctx, HRC_ESTATE, "hrc_fluence: batched context; use hrc_fluence_batched");
     if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence: NULL pointer");
@@ -809,6 +1047,17 @@ hrc_status hrc_fluence(hrc_ctx *ctx, const float *emission, const float *sigma_t
 hrc_status hrc_fluence_host(hrc_ctx *ctx, const float *emission, const float *sigma_t, float *out) {
     hrc_status st = check_ctx(ctx);
     if (st != HRC_OK) return st;
+    if (ctx->per_channel) {   // channel c: its planes of the host arrays through its own staging
+        if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence_host: NULL pointer");
+        const size_t img = (size_t)ctx->W * ctx->H;
+        for (int c = 0; c < ctx->C; ++c) {
+            st = hrc_fluence_host(ctx->chan[c], emission + c * img, sigma_t + c * img, out + c * img);
+            if (st != HRC_OK) return chan_status(ctx, st, ctx->chan[c]);
+        }
+        chan_launches(ctx);
+        ctx->have_fwd = true;
+        return HRC_OK;
+    }
     if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence_host: NULL pointer");
     const size_t img = (size_t)ctx->W * ctx->H;
     cudaError_t e = cudaMemcpyAsync(ctx->dev_e, emission, img * ctx->C * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
@@ -825,6 +1074,7 @@ hrc_status hrc_fluence_host(hrc_ctx *ctx, const float *emission, const float *si
 hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *sigma_t, double *out) {
     hrc_status st = check_ctx(ctx);
     if (st != HRC_OK) return st;
+    if (ctx->per_channel && ctx->prec == P_FP64) return chan_forward(ctx, emission, sigma_t, out, true);
     if (ctx->prec != P_FP64) return fail(ctx, HRC_ESTATE, "hrc_fluence_f64: set HRC_FP64_TEST first");
     if (!emission || !sigma_t || !out) return fail(ctx, HRC_EINVAL, "hrc_fluence_f64: NULL pointer");
     if (!aligned16(emission) || !aligned16(sigma_t) || !aligned16(out))
@@ -849,6 +1099,7 @@ hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *s
 hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_emission, float *grad_sigma_t) {
     hrc_status st = check_ctx(ctx);
     if (st != HRC_OK) return st;
+    if (ctx->per_channel && ctx->prec != P_FP64) return chan_backward(ctx, grad_F, grad_emission, grad_sigma_t, false);
     if (ctx->prec == P_FP64) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward: context is in HRC_FP64_TEST");
     if (!ctx->have_fwd) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward: no forward pass on this context");
     if (!grad_F || !grad_emission || !grad_sigma_t) return fail(ctx, HRC_EINVAL, "hrc_fluence_backward: NULL pointer");
@@ -871,6 +1122,7 @@ hrc_status hrc_fluence_backward(hrc_ctx *ctx, const float *grad_F, float *grad_e
 hrc_status hrc_fluence_backward_f64(hrc_ctx *ctx, const double *grad_F, double *grad_emission, double *grad_sigma_t) {
     hrc_status st = check_ctx(ctx);
     if (st != HRC_OK) return st;
+    if (ctx->per_channel && ctx->prec == P_FP64) return chan_backward(ctx, grad_F, grad_emission, grad_sigma_t, true);
     if (ctx->prec != P_FP64) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward_f64: set HRC_FP64_TEST first");
     if (!ctx->have_fwd) return fail(ctx, HRC_ESTATE, "hrc_fluence_backward_f64: no forward pass on this context");
     if (!grad_F || !grad_emission || !grad_sigma_t) return fail(ctx, HRC_EINVAL, "hrc_fluence_backward_f64: NULL pointer");
@@ -918,6 +1170,10 @@ hrc_status hrc_reserve_bounces(hrc_ctx *ctx, int max_bounces) {
     }
     ctx->bounce_cap = max_bounces;
     ctx->bounce_plane = plane;
+    for (hrc_ctx *k : ctx->chan) {
+        hrc_status st = hrc_reserve_bounces(k, max_bounces);
+        if (st != HRC_OK) return fail(ctx, st, k->err);
+    }
     return HRC_OK;
 }
 
@@ -1022,22 +1278,30 @@ extern "C" {
 
 hrc_status hrc_fluence_bounces(hrc_ctx *ctx, const float *emission, const float *sigma_t, const float *albedo,
                                int bounces, float *out) {
+    if (ctx && ctx->per_channel && ctx->prec != P_FP64 && check_ctx(ctx) == HRC_OK)
+        return chan_bounces(ctx, emission, sigma_t, albedo, bounces, out, false);
     return bounces_forward(ctx, emission, sigma_t, albedo, bounces, out, false, "hrc_fluence_bounces");
 }
 
 hrc_status hrc_fluence_bounces_f64(hrc_ctx *ctx, const double *emission, const double *sigma_t,
                                    const double *albedo, int bounces, double *out) {
+    if (ctx && ctx->per_channel && ctx->prec == P_FP64 && check_ctx(ctx) == HRC_OK)
+        return chan_bounces(ctx, emission, sigma_t, albedo, bounces, out, true);
     return bounces_forward(ctx, emission, sigma_t, albedo, bounces, out, true, "hrc_fluence_bounces_f64");
 }
 
 hrc_status hrc_fluence_bounces_backward(hrc_ctx *ctx, const float *grad_F, float *grad_emission,
                                         float *grad_sigma_t, float *grad_albedo) {
+    if (ctx && ctx->per_channel && ctx->prec != P_FP64 && check_ctx(ctx) == HRC_OK)
+        return chan_bounces_backward(ctx, grad_F, grad_emission, grad_sigma_t, grad_albedo, false);
     return bounces_backward(ctx, grad_F, grad_emission, grad_sigma_t, grad_albedo, false,
                             "hrc_fluence_bounces_backward");
 }
 
 hrc_status hrc_fluence_bounces_backward_f64(hrc_ctx *ctx, const double *grad_F, double *grad_emission,
                                             double *grad_sigma_t, double *grad_albedo) {
+    if (ctx && ctx->per_channel && ctx->prec == P_FP64 && check_ctx(ctx) == HRC_OK)
+        return chan_bounces_backward(ctx, grad_F, grad_emission, grad_sigma_t, grad_albedo, true);
     return bounces_backward(ctx, grad_F, grad_emission, grad_sigma_t, grad_albedo, true,
                             "hrc_fluence_bounces_backward_f64");
 }
@@ -1053,7 +1317,8 @@ hrc_status hrc_bounce_source(hrc_ctx *ctx, const float *emission, const float *s
         return fail(ctx, HRC_EINVAL, "hrc_bounce_source: pointers must be 16-byte aligned");
     Recorder off;
     int n = 0;
-    cudaError_t e = launch_bounce_source(ctx->plan, emission, sigma_t, albedo, fluence, out, ctx->stream, &n, &off);
+    cudaError_t e = launch_bounce_source(ctx->plan, emission, sigma_t, albedo, fluence, out, ctx->stream, &n, &off,
+                                         ctx->per_channel);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_bounce_source");
     ctx->launches = n;
     return HRC_OK;
@@ -1450,6 +1715,7 @@ hrc_status hrc_batched_tune(hrc_ctx *ctx, int blocks_per_sm, int order) {
 
 hrc_status hrc_copy_level(hrc_ctx *ctx, int q, int which, int n, float *dst, long long *count) {
     if (!ctx) return HRC_EINVAL;
+    if (ctx->per_channel) return fail(ctx, HRC_ESTATE, "hrc_copy_level: per-channel extinction (levels live per channel)");
     const Plan &pl = ctx->prec == P_FP64 ? ctx->plan64 : ctx->plan;
     if (q < 0 || q > 3 || (which != 0 && which != 1)) return fail(ctx, HRC_EINVAL, "hrc_copy_level: bad q / which");
     const QuadGeom &g = pl.q[q];

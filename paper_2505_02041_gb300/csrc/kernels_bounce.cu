@@ -28,33 +28,34 @@ namespace {
 
 template <class T> __device__ __forceinline__ T inv_two_pi() { return T(0.15915494309189533576888376337251436); }
 
+// ss: stride between the channels' extinction planes (0: one plane shared
+// by all channels; n: per-channel extinction)
 template <class T, int C>
-__global__ void __launch_bounds__(256) k_bounce_source(long long n, const T *__restrict__ e,
+__global__ void __launch_bounds__(256) k_bounce_source(long long n, long long ss, const T *__restrict__ e,
                                                        const T *__restrict__ s, const T *__restrict__ a,
                                                        const T *__restrict__ F, T *__restrict__ eo) {
     const T k = inv_two_pi<T>();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const T sg = __ldg(s + i) * k;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const long long j = c * n + i;
-            eo[j] = __ldg(e + j) + __ldg(a + j) * sg * __ldg(F + j);
+            eo[j] = __ldg(e + j) + __ldg(a + j) * (__ldg(s + c * ss + i) * k) * __ldg(F + j);
         }
     }
 }
 
 // fp32, n % 4 == 0: 4-wide accesses (every plane starts 16-byte aligned)
 template <int C>
-__global__ void __launch_bounds__(256) k_bounce_source4(long long n4, const float4 *__restrict__ e,
+__global__ void __launch_bounds__(256) k_bounce_source4(long long n4, long long ss4, const float4 *__restrict__ e,
                                                         const float4 *__restrict__ s, const float4 *__restrict__ a,
                                                         const float4 *__restrict__ F, float4 *__restrict__ eo) {
     const float k = inv_two_pi<float>();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
          i += (long long)gridDim.x * blockDim.x) {
-        float4 sg = __ldg(s + i);
-        sg.x *= k; sg.y *= k; sg.z *= k; sg.w *= k;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
+            float4 sg = __ldg(s + c * ss4 + i);
+            sg.x *= k; sg.y *= k; sg.z *= k; sg.w *= k;
             const long long j = c * n4 + i;
             const float4 ev = __ldg(e + j), av = __ldg(a + j), fv = __ldg(F + j);
             eo[j] = make_float4(ev.x + av.x * sg.x * fv.x, ev.y + av.y * sg.y * fv.y, ev.z + av.z * sg.z * fv.z,
@@ -118,8 +119,8 @@ double bytes_bounce_adj(const Plan &pl, bool first, bool has_prev) {
 }
 
 cudaError_t launch_bounce_source(const Plan &pl, const void *e, const void *s, const void *a, const void *F,
-                                 void *eo, cudaStream_t st, int *launches, Recorder *rec) {
-    const long long n = (long long)pl.W * pl.H;
+                                 void *eo, cudaStream_t st, int *launches, Recorder *rec, bool per_channel_sigma) {
+    const long long n = (long long)pl.W * pl.H, ss = per_channel_sigma ? n : 0;
     rec->begin(K_BOUNCE, 0, bytes_bounce_source(pl));
     const bool v4 = pl.prec != P_FP64 && n % 4 == 0;
     const int grid = stride_grid(v4 ? n / 4 : n, 256);
@@ -127,13 +128,13 @@ cudaError_t launch_bounce_source(const Plan &pl, const void *e, const void *s, c
 #define HRC_BOUNCE_CASE(CC)                                                                                       \
     case CC:                                                                                                      \
         if (pl.prec == P_FP64)                                                                                    \
-            k_bounce_source<double, CC><<<grid, 256, 0, st>>>(n, (const double *)e, (const double *)s,            \
+            k_bounce_source<double, CC><<<grid, 256, 0, st>>>(n, ss, (const double *)e, (const double *)s,        \
                                                               (const double *)a, (const double *)F, (double *)eo); \
         else if (v4)                                                                                              \
-            k_bounce_source4<CC><<<grid, 256, 0, st>>>(n / 4, (const float4 *)e, (const float4 *)s,               \
+            k_bounce_source4<CC><<<grid, 256, 0, st>>>(n / 4, ss / 4, (const float4 *)e, (const float4 *)s,      \
                                                        (const float4 *)a, (const float4 *)F, (float4 *)eo);       \
         else                                                                                                      \
-            k_bounce_source<float, CC><<<grid, 256, 0, st>>>(n, (const float *)e, (const float *)s,               \
+            k_bounce_source<float, CC><<<grid, 256, 0, st>>>(n, ss, (const float *)e, (const float *)s,           \
                                                              (const float *)a, (const float *)F, (float *)eo);    \
         break;
         HRC_BOUNCE_CASE(1) HRC_BOUNCE_CASE(2) HRC_BOUNCE_CASE(3) HRC_BOUNCE_CASE(4)

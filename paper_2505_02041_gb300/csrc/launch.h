@@ -151,7 +151,8 @@ double bytes_cross_blur(const Plan &pl);
 // is the last bounce, the accumulators ge / gs / ga are overwritten; has_prev:
 // k >= 1, so F_{k-1} = Fp exists and dL/dF_{k-1} is written to gFp).
 cudaError_t launch_bounce_source(const Plan &pl, const void *e, const void *s, const void *a, const void *F,
-                                 void *eo, cudaStream_t st, int *launches, Recorder *rec);
+                                 void *eo, cudaStream_t st, int *launches, Recorder *rec,
+                                 bool per_channel_sigma = false);
 cudaError_t launch_bounce_adj(const Plan &pl, bool first, bool has_prev, const void *gek, const void *gsk,
                               const void *Fp, const void *a, const void *s, void *ge, void *gs, void *ga, void *gFp,
                               cudaStream_t st, int *launches, Recorder *rec);

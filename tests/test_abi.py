@@ -76,6 +76,7 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.hrc_get_cross_blur(None, None, None) == _lib.HRC_EINVAL
     assert lib.hrc_reserve_bounces(None, 2) == _lib.HRC_EINVAL
     assert lib.hrc_set_environment(None, None, 4) == _lib.HRC_EINVAL
+    assert lib.hrc_set_channel_extinction(None, 1) == _lib.HRC_EINVAL
     assert lib.hrc_fluence_bounces(None, None, None, None, 1, None) == _lib.HRC_EINVAL
     assert lib.hrc_fluence_bounces_backward(None, None, None, None, None) == _lib.HRC_EINVAL
     assert lib.hrc_bounce_source(None, None, None, None, None, None) == _lib.HRC_EINVAL
