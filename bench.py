@@ -138,6 +138,28 @@ def bench_environment(h, fwd, fwd_bwd, timed, steps=10):
     return out
 
 
+def bench_channels(h, e, s, timed, steps=10):
+    """Per-channel extinction (sigma_t[C][H][W]: the workload's extinction
+    scaled by 1, 0.5 and 2 per channel): graph-launched forward and
+    forward+backward through the per-channel contexts."""
+    import torch
+    from paper_2505_02041_gb300 import _lib
+    C = h.C
+    S = torch.stack([s * f for f in (1.0, 0.5, 2.0, 1.5)[:C]]).contiguous()
+    F = torch.empty_like(e)
+    gF = torch.ones_like(e)
+    ge, gs = torch.empty_like(e), torch.empty_like(S)
+    h.set_channel_extinction(True)
+    fwd = lambda: _lib.hrc_fluence(h.ctx, e, S, F)
+    fwd_bwd = lambda: (fwd(), _lib.hrc_fluence_backward(h.ctx, gF, ge, gs))
+    for _ in range(3):
+        fwd_bwd()
+    out = {"forward_ms": statistics.mean(timed(fwd, steps)), "fwd_bwd_ms": statistics.mean(timed(fwd_bwd, steps)),
+           "launches_forward": (fwd(), h.launch_count())[1]}
+    h.set_channel_extinction(False)
+    return out
+
+
 def traffic_key(kind, cfg):
     """The kernel variant whose DRAM bytes stand for `kind`: the merge down
     has a per-thread-load kernel (mdown 0) and a bulk-copy-staged one
@@ -528,6 +550,7 @@ def run_ours(args):
     line["cross_blur"] = bench_cross_blur(h, fwd, fwd_bwd, timed, gF, gE, gS, hbm_peak)
     line["multi_bounce"] = bench_bounces(h, e, s, timed, hbm_peak)
     line["environment"] = bench_environment(h, fwd, fwd_bwd, timed)
+    line["per_channel_extinction"] = bench_channels(h, e, s, timed)
     if args.precisions and world == 1:
         import oracle
         Fr = oracle.fluence(e_np, s_np)
