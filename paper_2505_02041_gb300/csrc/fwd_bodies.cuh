@@ -368,7 +368,7 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
     using A = typename Prec<P>::A;
     constexpr bool PAIR = E == 2;
     const QuadGeom &g = pl.q[q];
-    const bool top = (n + 1 >= g.N);               // R_N = 0
+    const bool top = (n + 1 >= g.N);               // R_N: 0, or the environment map
     const int s = 1 << n;
 #pragma unroll
     for (int l = 0; l < E; ++l)

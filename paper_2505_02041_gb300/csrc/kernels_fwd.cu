@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, i
     const int I = 1 << n;
     local += I;
     const int x = local >> n, ip = local & (I - 1);
-    const bool top = n + 1 >= g.N;                           // R_N = 0
+    const bool top = n + 1 >= g.N;                           // R_N: 0, or the environment map
     const int s = 1 << n;
     const bool odd = (x & 1) != 0;
     const int x2 = x >> 1;
