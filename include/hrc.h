@@ -74,16 +74,22 @@ hrc_status hrc_set_stream(hrc_ctx *ctx, void *cuda_stream);
  * Switching to HRC_FP64_TEST allocates its fp64 buffers once. */
 hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec);
 
-/* Launch schedule (a tuning knob; results are identical either way):
+/* Launch schedule (a tuning knob; results are identical for every value):
  * 0 = every kernel launch covers the four quadrant frames (level-major);
  * 1 = the frames run one after another, so that each level's producer and
- *     consumer meet in L2.  Default 0 (faster on GB300: four times fewer,
- *     larger launches). */
+ *     consumer meet in L2;
+ * 2 = the four frames' chains (trace, merge up, merge down) run as four
+ *     parallel branches of the pass (context-owned streams, forked from and
+ *     joined to the caller's stream; parallel paths of the captured graph),
+ *     so that one frame's launch fills the SMs while another's drains; the
+ *     fluence sum follows the join.  With per-launch timing on, and in the
+ *     level recomputation of the backward, 2 runs as 0.
+ * Default 0. */
 hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule);
 
 /* Launch configuration of a single-scene context (tuning knobs; results are
  * identical for every setting):
- *   schedule: as hrc_set_schedule (0 or 1);
+ *   schedule: as hrc_set_schedule (0, 1 or 2);
  *   groups:   v per thread in the merge-up kernel: 1 = a pair, 2 = two pairs
  *             blockDim apart, 4 = four consecutive v;
  *   threads:  threads per block of the merge and adjoint-merge kernels

@@ -193,6 +193,8 @@ struct hrc_ctx {
     const void *last_e = nullptr, *last_s = nullptr;
     bool have_fwd = false;
     bool bwd_recompute = false;  // backward recomputes the levels instead of reading the forward's
+    Branches br{};               // the forward's four frame branches (launch schedule 2)
+    bool br_ok = false;
     bool blur = false;           // cross blur (Eq. 21) after the fluence sum
     float blur_thr = 0.5f;       // its opacity threshold
     void *blur_buf = nullptr;    // W * H * C doubles: unblurred F, or dL/d(unblurred F)
@@ -395,9 +397,9 @@ void apply_env(hrc_ctx *ctx) {
 // One Lighting pass (Algorithm 1, then the Eq. 21 blur when enabled) and
 // its adjoint, as enqueued by every single-scene entry point.
 cudaError_t enqueue_lighting(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
-                             void *blur_buf, double thr, cudaStream_t st, int *n, Recorder *r) {
-    if (!blur_buf) return launch_forward(pl, rt, e, s, F, st, n, r);
-    cudaError_t err = launch_forward(pl, rt, e, s, blur_buf, st, n, r);
+                             void *blur_buf, double thr, cudaStream_t st, int *n, Recorder *r, const Branches *br) {
+    if (!blur_buf) return launch_forward(pl, rt, e, s, F, st, n, r, br);
+    cudaError_t err = launch_forward(pl, rt, e, s, blur_buf, st, n, r, br);
     if (err != cudaSuccess) return err;
     return launch_cross_blur(pl, blur_buf, s, F, thr, st, n, r);
 }
@@ -479,7 +481,20 @@ hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out) {
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = prepare_device_once();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { delete ctx; return fail(nullptr, HRC_ECUDA, std::string("hrc_create: ") + cudaGetErrorString(e)); }
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&ctx->br.s[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->br.fork, cudaEventDisableTiming);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ctx->br.join[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) ctx->br_ok = true;
+    if (e != cudaSuccess) {
+        for (int i = 0; i < 4; ++i) {
+            if (ctx->br.s[i]) cudaStreamDestroy(ctx->br.s[i]);
+            if (ctx->br.join[i]) cudaEventDestroy(ctx->br.join[i]);
+        }
+        if (ctx->br.fork) cudaEventDestroy(ctx->br.fork);
+        if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+        delete ctx;
+        return fail(nullptr, HRC_ECUDA, std::string("hrc_create: ") + cudaGetErrorString(e));
+    }
     // The fp32 layout is the largest of the fp32 / fp16 / bf16 layouts.
     Plan p32;
     size_t bytes = build_plan(W, H, channels, cascades, P_FP32, 0, p32, true);
@@ -549,13 +564,18 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->d_ticket);
     cudaFree(ctx->d_status);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (int i = 0; i < 4; ++i) {
+        if (ctx->br.s[i]) cudaStreamDestroy(ctx->br.s[i]);
+        if (ctx->br.join[i]) cudaEventDestroy(ctx->br.join[i]);
+    }
+    if (ctx->br.fork) cudaEventDestroy(ctx->br.fork);
     delete ctx;
     return HRC_OK;
 }
 
 hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule) {
     if (!ctx) return HRC_EINVAL;
-    if (schedule != 0 && schedule != 1) return fail(ctx, HRC_EINVAL, "hrc_set_schedule: 0 or 1");
+    if (schedule < 0 || schedule > 2) return fail(ctx, HRC_EINVAL, "hrc_set_schedule: 0, 1 or 2");
     ctx->sched = schedule;
     ctx->plan.sched = schedule;
     ctx->plan64.sched = schedule;
@@ -567,7 +587,7 @@ hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule) {
 
 namespace {
 bool config_valid(const hrc_ctx *ctx, const hrc_launch_config &c) {
-    return (c.schedule == 0 || c.schedule == 1) && (c.groups == 1 || c.groups == 2 || c.groups == 4) &&
+    return (c.schedule >= 0 && c.schedule <= 2) && (c.groups == 1 || c.groups == 2 || c.groups == 4) &&
            (c.threads == 64 || c.threads == 128 || c.threads == 256 || c.threads == 512) &&
            (c.vmajor == 0 || c.vmajor == 1) && (c.mdown == 0 || c.mdown == 1) &&
            !(c.vmajor && 4LL * (ctx->W + ctx->H) > 65535);
@@ -691,9 +711,9 @@ hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
     ctx->rec.on = false;
     static const int kThreads[4] = {64, 128, 256, 512};
     static const int kGroups[3] = {1, 2, 4};
-    for (int cand = 0; cand < 2 * 3 * 4 * 2 * 2 && st == HRC_OK; ++cand) {
-        const hrc_launch_config c{cand & 1, kGroups[(cand >> 1) % 3], kThreads[(cand / 6) & 3], (cand / 24) & 1,
-                                  (cand / 48) & 1};
+    for (int cand = 0; cand < 3 * 3 * 4 * 2 * 2 && st == HRC_OK; ++cand) {
+        const hrc_launch_config c{cand % 3, kGroups[(cand / 3) % 3], kThreads[(cand / 9) & 3], (cand / 36) & 1,
+                                  (cand / 72) & 1};
         if (!config_valid(ctx, c)) continue;
         apply_config(ctx, c);
         for (int r = 0; r < 2 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
@@ -1031,9 +1051,10 @@ hrc_status hrc_fluence(hrc_ctx *ctx, const float *emission, const float *sigma_t
     const RayTable *rt = &ctx->rt;
     void *Fr = ctx->blur ? ctx->blur_buf : nullptr;
     const double thr = ctx->blur_thr;
+    const Branches *br = ctx->br_ok ? &ctx->br : nullptr;
     st = run_pass(ctx, 0, emission, sigma_t, out, nullptr, nullptr,
                   [&](cudaStream_t s, int *n, Recorder *r) {
-                      return enqueue_lighting(pl, *rt, emission, sigma_t, out, Fr, thr, s, n, r);
+                      return enqueue_lighting(pl, *rt, emission, sigma_t, out, Fr, thr, s, n, r, br);
                   },
                   "hrc_fluence");
     if (st != HRC_OK) return st;
@@ -1083,9 +1104,10 @@ hrc_status hrc_fluence_f64(hrc_ctx *ctx, const double *emission, const double *s
     const RayTable *rt = &ctx->rt;
     void *Fr = ctx->blur ? ctx->blur_buf : nullptr;
     const double thr = ctx->blur_thr;
+    const Branches *br = ctx->br_ok ? &ctx->br : nullptr;
     st = run_pass(ctx, 2, emission, sigma_t, out, nullptr, nullptr,
                   [&](cudaStream_t s, int *n, Recorder *r) {
-                      return enqueue_lighting(pl, *rt, emission, sigma_t, out, Fr, thr, s, n, r);
+                      return enqueue_lighting(pl, *rt, emission, sigma_t, out, Fr, thr, s, n, r, br);
                   },
                   "hrc_fluence_f64");
     if (st != HRC_OK) return st;
@@ -1206,13 +1228,14 @@ hrc_status bounces_forward(hrc_ctx *ctx, const void *e, const void *s, const voi
     const RayTable *rt = &ctx->rt;
     void *blur = ctx->blur ? ctx->blur_buf : nullptr;
     const double thr = ctx->blur_thr;
+    const Branches *br = ctx->br_ok ? &ctx->br : nullptr;
     const PassKey key{{e, s, a, out, (const void *)(intptr_t)K, nullptr, nullptr, nullptr}};
     st = run_pass_key(ctx, f64 ? 13 : 12, key,
                       [&](cudaStream_t sm, int *n, Recorder *r) {
                           for (int k = 0; k <= K; ++k) {
                               const void *ek = k == 0 ? e : (const void *)bounce_e(ctx, k);
                               void *Fk = k == K ? out : (void *)bounce_F(ctx, k);
-                              cudaError_t err = enqueue_lighting(pl, *rt, ek, s, Fk, blur, thr, sm, n, r);
+                              cudaError_t err = enqueue_lighting(pl, *rt, ek, s, Fk, blur, thr, sm, n, r, br);
                               if (err == cudaSuccess && k < K)
                                   err = launch_bounce_source(pl, e, s, a, Fk, bounce_e(ctx, k + 1), sm, n, r);
                               if (err != cudaSuccess) return err;

@@ -221,16 +221,16 @@ __global__ void __launch_bounds__(128) k_fluence(Plan pl, OUT *__restrict__ F) {
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
-static RowSplit make_split(const Plan &pl, int n, int kind, int qsel) {
+static RowSplit make_split(const Plan &pl, int n, int kind, int qm) {
     // kind 0: trace rows (q, u); 1: merge-up rows (q, x, k) at level n;
-    // 2: merge-down rows (q, x, ip) at level n.  qsel >= 0 keeps one frame.
+    // 2: merge-down rows (q, x, ip) at level n.  qm: mask of the frames kept.
     RowSplit rs;
     long long acc = 0;
     for (int q = 0; q < 4; ++q) {
         rs.start[q] = acc;
         const QuadGeom &g = pl.q[q];
         long long rows = 0;
-        if (qsel >= 0 && q != qsel) continue;
+        if (!((qm >> q) & 1)) continue;
         if (kind == 0) rows = g.U;
         else if (kind == 1) rows = (n <= g.N && n >= 3) ? (long long)(g.Un[n] - 1) * ((1 << n) + 1) : 0;
         else rows = (n < g.N) ? (long long)(g.Un[n] - 1) * (1 << n) : 0;
@@ -322,7 +322,7 @@ bool encode_image_maps(const Plan &pl, const void *e, const void *s, int box_x, 
 
 template <int P, int C>
 static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
-                            cudaStream_t st, int *launches, Recorder *rec, bool with_sum) {
+                            cudaStream_t st0, int *launches, Recorder *rec, bool with_sum, const Branches *br) {
     const int bs = 256;
     const bool env = plan_has_env(pl);   // kernels compiled for an environment map
     int Nmax = 0;
@@ -334,14 +334,27 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
     const size_t smem = TraceTile<typename Prec<P>::A, C>::bytes();
     // sched 0: every launch covers the four frames (level-major);
     // sched 1: frame by frame, so that each level's producer and consumer
-    //          (tens of MB per frame) meet in L2.
-    const int passes = pl.sched == 1 ? 4 : 1;
+    //          (tens of MB per frame) meet in L2;
+    // sched 2: frames {0, 1} and {2, 3} (equal extents) on two parallel
+    //          branches, so that one branch's launch fills the SMs while the
+    //          other's drains.
+    const bool par = pl.sched == 2 && br != nullptr && !rec->on;
+    const int sched = (pl.sched == 2 && !par) ? 0 : pl.sched;
+    const int passes = sched == 1 ? 4 : (sched == 2 ? 2 : 1);
+    const int nbr = passes;
+    if (par) {
+        cudaError_t err = cudaEventRecord(br->fork, st0);
+        for (int i = 0; i < nbr && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(br->s[i], br->fork, 0);
+        if (err != cudaSuccess) return err;
+    }
     for (int pass = 0; pass < passes; ++pass) {
-        const int qsel = pl.sched == 1 ? pass : -1;
+        const int qm = sched == 1 ? 1 << pass : (sched == 2 ? 3 << (2 * pass) : 15);
+        const int nq = __builtin_popcount(qm);
+        const cudaStream_t st = par ? br->s[pass] : st0;
         {
-            double by = img * (pl.C + 1) * esz / (pl.sched == 1 ? 4 : 1);
+            double by = img * (pl.C + 1) * esz * nq / 4;
             for (int q = 0; q < 4; ++q)
-                if (qsel < 0 || q == qsel)
+                if ((qm >> q) & 1)
                     for (int n = 0; n <= 2; ++n) by += bytes_T(pl, q, n);
             dim3 grid((pl.W + TR_TILE - 1) / TR_TILE, (pl.H + TR_TILE - 1) / TR_TILE);
             rec->begin(K_TRACE012, 0, by);
@@ -349,16 +362,16 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             std::memset(&me, 0, sizeof(me));
             std::memset(&ms, 0, sizeof(ms));
             const int use_tma = (P != P_FP64 && encode_image_maps(pl, e, s, TR_REG, TR_REG, me, ms)) ? 1 : 0;
-            k_trace012<P, C><<<grid, 256, smem, st>>>(pl, ef, sf, ed, sd, qsel < 0 ? 15 : (1 << qsel), me, ms, use_tma);
+            k_trace012<P, C><<<grid, 256, smem, st>>>(pl, ef, sf, ed, sd, qm, me, ms, use_tma);
             rec->end();
             ++*launches;
         }
         for (int n = 3; n <= Nmax; ++n) {
-            RowSplit rs = make_split(pl, n, 1, qsel);
+            RowSplit rs = make_split(pl, n, 1, qm);
             if (rs.start[4] == 0) continue;
             double by = 0;
             for (int q = 0; q < 4; ++q)
-                if ((qsel < 0 || q == qsel) && n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
+                if (((qm >> q) & 1) && n <= pl.q[q].N) by += bytes_T(pl, q, n - 1) + bytes_T(pl, q, n);
             const int mt = pl.mthreads;
             rec->begin(K_MERGE_UP, n, by);
             // groups: 1 = a pair of v per thread, 2 = two pairs blockDim apart,
@@ -371,12 +384,12 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         }
         // R_0 feeds only the fluence sum, which computes it in place
         for (int n = Nmax - 1; n >= 1; --n) {
-            RowSplit rs = make_split(pl, n, 2, qsel);
+            RowSplit rs = make_split(pl, n, 2, qm);
             if (rs.start[4] == 0) continue;
             double by = 0;
             for (int q = 0; q < 4; ++q) {
                 const QuadGeom &g = pl.q[q];
-                if ((qsel >= 0 && q != qsel) || n >= g.N) continue;
+                if (!((qm >> q) & 1) || n >= g.N) continue;
                 // odd columns of T_n, even directions of T_{n+1}, R_{n+1} once, R_n written
                 by += bytes_T_odd(pl, q, n);
                 by += bytes_T_even_dirs(pl, q, n + 1);
@@ -401,6 +414,15 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             ++*launches;
         }
     }
+    if (par) {
+        cudaError_t err = cudaSuccess;
+        for (int i = 0; i < nbr && err == cudaSuccess; ++i) {
+            err = cudaEventRecord(br->join[i], br->s[i]);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(st0, br->join[i], 0);
+        }
+        if (err != cudaSuccess) return err;
+    }
+    const cudaStream_t st = st0;
     if (with_sum) {
         // level-0 merge-down reads (odd columns of T_0, even directions of
         // T_1, R_1) and the fluence written
@@ -429,7 +451,7 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
 // stores it); for introspection.
 template <int P, int C>
 static cudaError_t r0_impl(const Plan &pl, cudaStream_t st) {
-    RowSplit rs = make_split(pl, 0, 2, -1);
+    RowSplit rs = make_split(pl, 0, 2, 15);
     if (rs.start[4] == 0) return cudaSuccess;
     const int ts = 2 * pl.mthreads > 512 ? 512 : 2 * pl.mthreads;
     if (plan_has_env(pl)) k_merge_down<P, C, false, true><<<row_grid(pl, rs.start[4], ts), ts, 0, st>>>(pl, rs, 0);
@@ -458,12 +480,12 @@ cudaError_t launch_r0(const Plan &pl, cudaStream_t st) {
 
 template <int P>
 static cudaError_t fwd_prec(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
-                            cudaStream_t st, int *launches, Recorder *rec) {
+                            cudaStream_t st, int *launches, Recorder *rec, const Branches *br) {
     switch (pl.C) {
-    case 1: return fwd_impl<P, 1>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
-    case 2: return fwd_impl<P, 2>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
-    case 3: return fwd_impl<P, 3>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
-    default: return fwd_impl<P, 4>(pl, rt, e, s, F, st, launches, rec, F != nullptr);
+    case 1: return fwd_impl<P, 1>(pl, rt, e, s, F, st, launches, rec, F != nullptr, br);
+    case 2: return fwd_impl<P, 2>(pl, rt, e, s, F, st, launches, rec, F != nullptr, br);
+    case 3: return fwd_impl<P, 3>(pl, rt, e, s, F, st, launches, rec, F != nullptr, br);
+    default: return fwd_impl<P, 4>(pl, rt, e, s, F, st, launches, rec, F != nullptr, br);
     }
 }
 
@@ -508,12 +530,12 @@ cudaError_t prepare_forward_kernels() {
 }
 
 cudaError_t launch_forward(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
-                           cudaStream_t st, int *launches, Recorder *rec) {
+                           cudaStream_t st, int *launches, Recorder *rec, const Branches *br) {
     switch (pl.prec) {
-    case P_FP32: return fwd_prec<P_FP32>(pl, rt, e, s, F, st, launches, rec);
-    case P_FP16: return fwd_prec<P_FP16>(pl, rt, e, s, F, st, launches, rec);
-    case P_BF16: return fwd_prec<P_BF16>(pl, rt, e, s, F, st, launches, rec);
-    default: return fwd_prec<P_FP64>(pl, rt, e, s, F, st, launches, rec);
+    case P_FP32: return fwd_prec<P_FP32>(pl, rt, e, s, F, st, launches, rec, br);
+    case P_FP16: return fwd_prec<P_FP16>(pl, rt, e, s, F, st, launches, rec, br);
+    case P_BF16: return fwd_prec<P_BF16>(pl, rt, e, s, F, st, launches, rec, br);
+    default: return fwd_prec<P_FP64>(pl, rt, e, s, F, st, launches, rec, br);
     }
 }
 

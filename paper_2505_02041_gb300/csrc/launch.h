@@ -50,10 +50,21 @@ struct Recorder {
     }
 };
 
+// Parallel branches of a pass (launch schedule 2): the pass forks from its
+// stream onto s[0..3] through `fork` and joins back through join[0..3];
+// inside graph capture the branches become parallel paths of the graph.
+struct Branches {
+    cudaStream_t s[4];
+    cudaEvent_t fork, join[4];
+};
+
 // Forward pass of Algorithm 1 (all four quadrant frames), enqueued on `st`.
-// e, s, F are fp32 device pointers (fp64 for P_FP64).
+// e, s, F are fp32 device pointers (fp64 for P_FP64).  With schedule 2 and
+// `br`, each frame's chain (trace, merge up, merge down) runs on its own
+// branch and the fluence sum after the join; without `br` (or with per-launch
+// timing on) schedule 2 runs level-major like schedule 0.
 cudaError_t launch_forward(const Plan &pl, const RayTable &rt, const void *e, const void *s, void *F,
-                           cudaStream_t st, int *launches, Recorder *rec);
+                           cudaStream_t st, int *launches, Recorder *rec, const Branches *br = nullptr);
 
 // ---------------------------------------------------------------------------
 // Batched persistent launch (kernels_batched.cu)

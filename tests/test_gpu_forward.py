@@ -140,9 +140,13 @@ def test_autotune_keeps_results():
     e, s = scenes.random_scene(300, 260, 3, 14)
     h = HRC(300, 260, 3)
     ref = h.forward(to_dev(e), to_dev(s)).clone()
-    for sched in (0, 1):
+    for sched in (0, 1, 2):
         _lib.hrc_set_schedule(h.ctx, sched)
         F = h.forward(to_dev(e), to_dev(s))
+        assert torch.equal(F, ref)
+        _lib.hrc_set_timing(h.ctx, True)          # direct launches (schedule 2 runs level-major)
+        F = h.forward(to_dev(e), to_dev(s))
+        _lib.hrc_set_timing(h.ctx, False)
         assert torch.equal(F, ref)
     ms = h.autotune()
     assert ms > 0
@@ -162,7 +166,7 @@ def test_launch_configurations_give_the_same_results():
     h = HRC(70, 53, 3)
     ed, sd, gd = to_dev(e), to_dev(s), to_dev(gF)
     ref = None
-    for sched in (0, 1):
+    for sched in (0, 1, 2):
         for groups in (1, 2, 4):
             for threads in (64, 128, 256, 512):
                 for vmajor, mdown in ((0, 0), (1, 0), (0, 1), (1, 1)):
