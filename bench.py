@@ -149,14 +149,18 @@ def bench_channels(h, e, s, timed, steps=10):
     F = torch.empty_like(e)
     gF = torch.ones_like(e)
     ge, gs = torch.empty_like(e), torch.empty_like(S)
+    cfg = h.launch_config
     h.set_channel_extinction(True)
+    tuned = h.autotune()          # tunes the single-channel contexts (their best configuration differs)
     fwd = lambda: _lib.hrc_fluence(h.ctx, e, S, F)
     fwd_bwd = lambda: (fwd(), _lib.hrc_fluence_backward(h.ctx, gF, ge, gs))
     for _ in range(3):
         fwd_bwd()
     out = {"forward_ms": statistics.mean(timed(fwd, steps)), "fwd_bwd_ms": statistics.mean(timed(fwd_bwd, steps)),
-           "launches_forward": (fwd(), h.launch_count())[1]}
+           "launches_forward": (fwd(), h.launch_count())[1], "autotune_best_ms": tuned,
+           "launch_config": h.launch_config}
     h.set_channel_extinction(False)
+    h.set_launch_config(**cfg)
     return out
 
 
