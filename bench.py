@@ -130,10 +130,14 @@ def bench_environment(h, fwd, fwd_bwd, timed, steps=10):
     th = torch.tensor([2 * math.pi * (m + 0.5) / 256 for m in range(256)], device="cuda")
     env = torch.stack([1.0 + 0.8 * torch.sin(th + 0.3 * k) for k in range(C)]).float().contiguous()
     h.set_environment(env)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.set_environment(env)                 # the table build (synchronous), timed on the host
+    table_ms = (time.perf_counter() - t0) * 1e3
     for _ in range(3):
         fwd_bwd()
     out = {"map_directions": 256, "forward_ms": statistics.mean(timed(fwd, steps)),
-           "fwd_bwd_ms": statistics.mean(timed(fwd_bwd, steps))}
+           "fwd_bwd_ms": statistics.mean(timed(fwd_bwd, steps)), "table_build_ms": table_ms}
     h.set_environment(None)
     return out
 

@@ -13,9 +13,10 @@
 // the value of R_N(., m) = A_N(m) env(...) summed the way Eqs. 14 / 15 sum
 // two cones when every interval is vacuum <0, 1>: an R_n lookup outside the
 // grid sees exactly this (nothing outside absorbs or emits, and a path that
-// has left the grid never re-enters).  One thread per (q, 2^n + j, c),
-// computed once per map, in double, with a float copy for the fp32 / fp16 /
-// bf16 kernels.
+// has left the grid never re-enters).  Computed once per map, in double,
+// with a float copy for the fp32 / fp16 / bf16 kernels: one thread per
+// level-N cone evaluates the map, then one thread per (q, 2^n + j, c) sums
+// its descendants in increasing order.
 #include <cuda_runtime.h>
 
 #include "hrc_internal.cuh"
@@ -37,29 +38,43 @@ __device__ double env_at(const float *__restrict__ env, int M, int c, double dx,
     return (1.0 - f) * (double)env[(long long)c * M + i0] + f * (double)env[(long long)c * M + i1];
 }
 
-__global__ void __launch_bounds__(128) k_env_table(Plan pl, const float *__restrict__ env, int M, int C, int S,
-                                                   double *__restrict__ td, float *__restrict__ tf) {
+// Level-N entries: A_N(m) env(direction of v_N(m)), one thread each.
+__global__ void __launch_bounds__(128) k_env_leaves(Plan pl, const float *__restrict__ env, int M, int C, int S,
+                                                    double *__restrict__ td) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int q = (int)(idx / ((long long)S * C));
+    if (q >= 4) return;
+    const int rem = (int)(idx - (long long)q * S * C);
+    const int m = rem / C, c = rem - m * C;
+    const int N = pl.q[q].N;
+    if (m >= (1 << N)) return;
+    const double sN = (double)(1 << N);
+    const double du = sN, dv = 2.0 * m + 1.0 - sN;        // v_N(m + 1/2)
+    const double dx = q == 0 ? du : (q == 1 ? -du : dv);
+    const double dy = q == 0 ? dv : (q == 1 ? dv : (q == 2 ? du : -du));
+    const double a = atan((2.0 * (m + 1) - sN) / sN) - atan((2.0 * m - sN) / sN);   // Eq. 13
+    td[(long long)q * S * C + ((long long)(1 << N) + m) * C + c] = a * env_at(env, M, c, dx, dy);
+}
+
+// Every entry: the sum of its level-N descendants (in increasing order),
+// read from the leaves; the float copy beside it.
+__global__ void __launch_bounds__(128) k_env_table(Plan pl, int C, int S, double *__restrict__ td,
+                                                   float *__restrict__ tf) {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long total = 4LL * S * C;
     if (idx >= total) return;
     const int q = (int)(idx / ((long long)S * C));
     const int rem = (int)(idx - (long long)q * S * C);
     const int lv = rem / C, c = rem - lv * C;
-    double acc = 0.0;
     const int N = pl.q[q].N;
     const int n = lv > 0 ? 31 - __clz(lv) : -1;
+    double acc = 0.0;
     if (n >= 0 && n <= N) {
         const int j = lv - (1 << n);
-        const double sN = (double)(1 << N);
-        for (int m = j << (N - n); m < (j + 1) << (N - n); ++m) {
-            const double du = sN, dv = 2.0 * m + 1.0 - sN;        // v_N(m + 1/2)
-            const double dx = q == 0 ? du : (q == 1 ? -du : dv);
-            const double dy = q == 0 ? dv : (q == 1 ? dv : (q == 2 ? du : -du));
-            const double a = atan((2.0 * (m + 1) - sN) / sN) - atan((2.0 * m - sN) / sN);   // Eq. 13
-            acc += a * env_at(env, M, c, dx, dy);
-        }
+        const double *leaf = td + (long long)q * S * C + (long long)(1 << N) * C + c;
+        for (int m = j << (N - n); m < (j + 1) << (N - n); ++m) acc += leaf[(long long)m * C];
     }
-    td[idx] = acc;
+    if (n != N) td[idx] = acc;   // (level N keeps its leaves; unused entries become 0)
     tf[idx] = (float)acc;
 }
 
@@ -77,7 +92,9 @@ cudaError_t launch_env_table(const Plan &pl, const float *env, int M, void *tabl
     double *td = reinterpret_cast<double *>(table);
     float *tf = reinterpret_cast<float *>(td + total);
     const int S = (int)(stride / pl.C);
-    k_env_table<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(pl, env, M, pl.C, S, td, tf);
+    const unsigned grid = (unsigned)((total + 127) / 128);
+    k_env_leaves<<<grid, 128, 0, st>>>(pl, env, M, pl.C, S, td);
+    k_env_table<<<grid, 128, 0, st>>>(pl, pl.C, S, td, tf);
     return cudaGetLastError();
 }
 
