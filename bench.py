@@ -573,9 +573,12 @@ def run_ours(args):
                 hp.forward(e, s, Fp)
             ms = timed(lambda: hp.forward(e, s, Fp), args.steps)
             Fn = Fp.cpu().numpy().astype(np.float64)
+            lit = np.abs(Fr) >= 1e-3 * np.max(np.abs(Fr))   # pixels with non-negligible fluence
             rows[prec] = {"ms_per_frame": statistics.mean(ms),
                           "err_max": float(np.max(np.abs(Fn - Fr)) / np.max(np.abs(Fr))),
-                          "rel_l2": float(np.linalg.norm(Fn - Fr) / np.linalg.norm(Fr))}
+                          "rel_l2": float(np.linalg.norm(Fn - Fr) / np.linalg.norm(Fr)),
+                          "pixel_rel_max": float(np.max(np.abs(Fn - Fr)[lit] / np.abs(Fr)[lit])),
+                          "pixel_rel_mean": float(np.mean(np.abs(Fn - Fr)[lit] / np.abs(Fr)[lit]))}
             hp.close()
         line["precisions"] = rows
     if args.batched and world == 1:

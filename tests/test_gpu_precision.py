@@ -34,7 +34,9 @@ def test_reduced_precision_forward(prec, name):
     Fr = oracle.fluence(e, s)
     em = err_max(F, Fr)
     l2 = np.linalg.norm(F - Fr) / np.linalg.norm(Fr)
-    print(f"{name} {prec}: err_max={em:.3e} relL2={l2:.3e}")
+    lit = np.abs(Fr) >= 1e-3 * np.max(np.abs(Fr))
+    pr = np.max(np.abs(F - Fr)[lit] / np.abs(Fr)[lit])
+    print(f"{name} {prec}: err_max={em:.3e} relL2={l2:.3e} pixel-relative max (F >= 1e-3 max)={pr:.3e}")
     assert em <= BOUNDS[prec][0] and l2 <= BOUNDS[prec][1]
 
 
