@@ -314,10 +314,31 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "precision": "fp64 CPU oracle"},
         "cpu_baseline": {"value": ms, "unit": "ms/frame", "cores": oracle.num_threads(), "kind": "oracle",
+                         "cpu_model": cpu_model(), "cpu_count": os.cpu_count(),
                          "sample": f"{args.steps} full {W}x{H} C={C} frames (OpenMP over rows)"},
         "e2e": {"value": ms, "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_model():
+    """The host CPU's model name (x86 'model name', or the Arm implementer /
+    part numbers), for the CPU-baseline record."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return os.uname().machine
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = (x.strip() for x in line.split(":", 1))
+            fields.setdefault(k, v)
+    if "model name" in fields:
+        return fields["model name"]
+    parts = {"0xd4f": "Neoverse V2", "0xd40": "Neoverse V1", "0xd0c": "Neoverse N1"}
+    part = fields.get("CPU part", "")
+    return f"{os.uname().machine} {parts.get(part, 'CPU part ' + part)}".strip()
 
 
 def cpu_baseline(workload, budget_s=20.0):
@@ -334,6 +355,7 @@ def cpu_baseline(workload, budget_s=20.0):
         if time.perf_counter() - t_start > budget_s * 0.5 or len(times) >= 5:
             break
     return {"value": statistics.mean(times), "unit": "ms/frame", "cores": oracle.num_threads(), "kind": "oracle",
+            "cpu_model": cpu_model(), "cpu_count": os.cpu_count(),
             "sample": f"{len(times)} full {W}x{H} C={C} frames of the same workload (FP64, OpenMP over rows)"}
 
 
