@@ -6,20 +6,32 @@
  * the acceleration structure T_3..T_N built by interval extension (Sec. 4.1,
  * Eqs. 18-20), the merge down the cascades R_{N-1}..R_0 (Eqs. 13-17) and the
  * sum over four quadrants (Algorithm 1, procedure Lighting), plus the exact
- * adjoint of all of it.  No cross blur (Eq. 21) is applied.
+ * adjoint of all of it.  Options of a context add the Eq. 21 cross blur
+ * (hrc_set_cross_blur), multiple bounces (hrc_fluence_bounces), an
+ * environment map for R_N (hrc_set_environment) and per-channel extinction
+ * (hrc_set_channel_extinction); all are off by default.
  *
  * Data conventions (shared by every entry point):
  *   - Images are row-major: emission e[C][H][W] (the per-unit-length source
  *     term integrated in Eq. 4), extinction sigma_t[H][W] (Eq. 2, per pixel
- *     length, one channel shared by all C colours), fluence F[C][H][W].
+ *     length, one channel shared by all C colours unless per-channel
+ *     extinction is enabled: then [C][H][W]), fluence F[C][H][W].
  *     Pixel (x, y) is the unit square [x, x+1] x [y, y+1]; its probe sits at
  *     the centre.  Cells outside the grid are vacuum with no emission.
  *   - Unless stated otherwise, tensor pointers are DEVICE pointers to
  *     contiguous fp32 data, 16-byte aligned.  The library never frees or
  *     keeps ownership of caller memory.
  *   - A context owns every scratch buffer (all T and R levels, gradients).
- *     It allocates them in hrc_create / hrc_create_batched (and, for the FP64
- *     test precision, in hrc_set_precision); compute calls allocate nothing.
+ *     It allocates them in hrc_create / hrc_create_batched and in the set-up
+ *     calls that enable an option (hrc_set_precision for FP64,
+ *     hrc_set_cross_blur, hrc_reserve_bounces, hrc_set_environment,
+ *     hrc_set_channel_extinction).  Compute calls allocate no buffer; the
+ *     first call with a new set of pointers (or a new configuration)
+ *     captures and instantiates a CUDA graph of the pass, which the driver
+ *     allocates, and later calls with the same pointers replay it.  A
+ *     context keeps eight such graphs (the oldest is replaced), so a caller
+ *     whose tensors move every step pays a capture every step: keep the
+ *     buffers at fixed addresses, or use hrc_set_graphs(ctx, 0).
  *   - Compute calls are asynchronous on the context's stream: HRC_OK means
  *     "enqueued".  Argument errors are reported synchronously; an
  *     asynchronous CUDA error surfaces as HRC_ECUDA on a later call.
@@ -43,7 +55,9 @@ typedef enum {
     HRC_ENOMEM = 2,    /* device allocation failed                              */
     HRC_ECUDA = 3,     /* CUDA launch or runtime error                          */
     HRC_ESTATE = 4,    /* call out of order (e.g. backward before forward)      */
-    HRC_ETIMEOUT = 5,  /* a bounded device-side wait gave up (batched path)     */
+    HRC_ETIMEOUT = 5,  /* a bounded device-side wait gave up (its launch ended
+                          early; reported by hrc_sync / hrc_batched_sync /
+                          hrc_noalloc_sync)                                      */
     HRC_EBOUNDS = 6    /* a device-side bounds check fired (debug builds)       */
 } hrc_status;
 
@@ -63,6 +77,15 @@ typedef enum {
  * Allocates every buffer of the forward and backward passes on the current
  * device.  Returns HRC_EINVAL / HRC_ENOMEM / HRC_ECUDA on failure (*out = 0). */
 hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out);
+
+/* CUDA graphs of whole passes (default 1): with 1, each pass is captured
+ * once per set of pointers and configuration and replayed afterwards (eight
+ * graphs per context); with 0, every call launches its kernels directly
+ * (no capture, no graph memory; about 0.1 ms more launch time per 1024^2
+ * frame).  hrc_graph_captures returns how many graphs the context (and its
+ * per-channel contexts) has captured so far, -1 for NULL. */
+hrc_status hrc_set_graphs(hrc_ctx *ctx, int enable);
+long long hrc_graph_captures(const hrc_ctx *ctx);
 
 /* Release the context and its device buffers (synchronises its stream). */
 hrc_status hrc_destroy(hrc_ctx *ctx);
@@ -99,7 +122,12 @@ hrc_status hrc_set_schedule(hrc_ctx *ctx, int schedule);
  *             the gridDim.y limit for the adjoint's level-0 rows);
  *   mdown:    merge-down kernel (fp32 / fp16 / bf16): 0 = every thread loads
  *             its operands; 1 = each block's rows are staged in shared
- *             memory by bulk (TMA) copies completed on an mbarrier.
+ *             memory by bulk (TMA) copies completed on an mbarrier; 2 = one
+ *             persistent launch for every level (as many 128-thread blocks
+ *             as fit on every SM take row segments from a ticket counter;
+ *             level-to-level dependencies are tracked by per-column
+ *             completion counters with bounded waits; not with schedule 2).
+ *             FP64 always uses 0.
  * Defaults {0, 1, 128, 0, 0}; hrc_autotune picks one. */
 typedef struct hrc_launch_config {
     int schedule, groups, threads, vmajor, mdown;
@@ -266,11 +294,13 @@ hrc_status hrc_bounce_source(hrc_ctx *ctx, const float *emission, const float *s
  * the status is device-wide and is cleared by this call). */
 hrc_status hrc_sync(hrc_ctx *ctx);
 
-/* Test hook for the bulk-copy waits: the merge-down kernel with mdown = 1
- * arms its barrier with `extra_bytes` (0..4096) more than it copies, so its
- * waits run out after `limit_ns` (<= 0 restores the default, 2 s) and
- * hrc_sync reports HRC_ETIMEOUT instead of the kernel hanging.  {0, 0}
- * restores normal operation; the context stays usable. */
+/* Test hook for the bounded device-side waits: with extra_bytes > 0
+ * (0..4096) the trace and the mdown = 1 merge down arm their copy barriers
+ * with that many bytes more than they copy, and the mdown = 2 persistent
+ * merge down publishes no finished item, so their waits run out after
+ * `limit_ns` (<= 0 restores the default, 2 s) and hrc_sync reports
+ * HRC_ETIMEOUT instead of a kernel hanging.  {0, 0} restores normal
+ * operation; the context stays usable. */
 hrc_status hrc_debug_bulk_wait(hrc_ctx *ctx, int extra_bytes, long long limit_ns);
 
 /* FP64 instance of hrc_fluence / hrc_fluence_backward (device fp64 buffers,
@@ -328,9 +358,27 @@ hrc_status hrc_fluence_backward_batched(hrc_ctx *ctx, const float *grad_F, float
  * or different host threads -- race on it and must be serialised by the
  * caller. */
 #define HRC_NOALLOC_MAX_SIDE 128
-#define HRC_NOALLOC_SCRATCH_BYTES 20443136ULL
+#define HRC_NOALLOC_SCRATCH_BYTES 20443392ULL
 hrc_status hrc_fluence_noalloc(int W, int H, int channels, const float *emission, const float *sigma_t,
                                float *out, void *cuda_stream);
+
+/* Completion status of hrc_fluence_noalloc on the current device: waits for
+ * `cuda_stream`, then reads and clears the no-alloc path's own status word
+ * (a word inside the fixed array, shared by every no-alloc call on the
+ * device and by no context).  HRC_ETIMEOUT when a bounded copy wait of a
+ * call since the last check gave up (that call's fluence is incomplete;
+ * its message says whether copies could still have been in flight), else
+ * HRC_OK.  Allocates nothing.  The one-time set-up of hrc_fluence_noalloc
+ * is redone automatically if the array's device address changes (e.g.
+ * after cudaDeviceReset); a caller that resets the device must make the
+ * next no-alloc call before any stream capture, as for the first. */
+hrc_status hrc_noalloc_sync(void *cuda_stream);
+
+/* Test hook for hrc_noalloc_sync: later hrc_fluence_noalloc calls arm the
+ * trace's copy barrier with `extra_bytes` (0..4096) that never arrive and
+ * bound its wait by `limit_ns` (<= 0 restores the default, 2 s), so the
+ * wait gives up; (0, 0) restores normal operation. */
+hrc_status hrc_noalloc_debug_wait(int extra_bytes, long long limit_ns);
 
 /* Waits for the batched context's stream and reports the status of its
  * last persistent launch: HRC_ETIMEOUT if a bounded dependency wait gave
@@ -376,7 +424,12 @@ hrc_status hrc_copy_level(hrc_ctx *ctx, int q, int which, int n, float *dst, lon
 int hrc_last_launch_count(const hrc_ctx *ctx);
 
 /* Per-launch timing.  With timing enabled, every kernel a compute call
- * enqueues is bracketed by CUDA events on the context's stream.
+ * enqueues is bracketed by CUDA events on the context's stream: enable = 1
+ * launches the kernels directly (no graph; each record then also holds
+ * that launch's host-side launch latency), enable = 2 captures the pass
+ * into a CUDA graph whose event-record nodes bracket each kernel, and
+ * replays it (the kernels timed as the graphs of normal operation run
+ * them), 0 switches timing off.
  * hrc_get_timing synchronises the stream and fills up to `cap` records of
  * the last compute call; it returns the number of records (or -1 on error).
  * `kind`: 0 trace T_0..T_2, 1 merge up, 2 merge down, 3 fluence sum,

@@ -58,6 +58,10 @@ SIGNATURES = [
     ("hrc_batched_schedule", _i, [_vp, _i]),
     ("hrc_batched_debug", _i, [_vp, _i, _ll]),
     ("hrc_fluence_noalloc", _i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
+    ("hrc_noalloc_sync", _i, [_vp]),
+    ("hrc_noalloc_debug_wait", _i, [_i, _ll]),
+    ("hrc_set_graphs", _i, [_vp, _i]),
+    ("hrc_graph_captures", _ll, [_vp]),
     ("hrc_copy_level", _i, [_vp, _i, _i, _i, _vp, ctypes.POINTER(_ll)]),
     ("hrc_last_launch_count", _i, [_vp]),
     ("hrc_set_timing", _i, [_vp, _i]),
@@ -285,6 +289,22 @@ def hrc_fluence_noalloc(W: int, H: int, channels: int, emission, sigma_t, out, s
     check(load().hrc_fluence_noalloc(W, H, channels, ptr(emission), ptr(sigma_t), ptr(out), stream_handle))
 
 
+def hrc_noalloc_sync(stream_handle=None):
+    check(load().hrc_noalloc_sync(stream_handle))
+
+
+def hrc_noalloc_debug_wait(extra_bytes: int, limit_ns: int):
+    check(load().hrc_noalloc_debug_wait(extra_bytes, limit_ns))
+
+
+def hrc_set_graphs(ctx, enable: bool):
+    check(load().hrc_set_graphs(ctx, 1 if enable else 0), ctx)
+
+
+def hrc_graph_captures(ctx) -> int:
+    return int(load().hrc_graph_captures(ctx))
+
+
 def hrc_copy_level(ctx, q: int, which: int, n: int, dst=None) -> int:
     cnt = _ll()
     check(load().hrc_copy_level(ctx, q, which, n, ptr(dst), ctypes.byref(cnt)), ctx)
@@ -304,8 +324,10 @@ KERNEL_KINDS = ["trace012", "merge_up", "merge_down", "fluence_sum", "adj_sum", 
                 "bounce_source", "adj_bounce"]
 
 
-def hrc_set_timing(ctx, enable: bool):
-    check(load().hrc_set_timing(ctx, 1 if enable else 0), ctx)
+def hrc_set_timing(ctx, enable):
+    """0 / False: off; 1 / True: direct launches bracketed by events;
+    2: event-record nodes inside the replayed graphs."""
+    check(load().hrc_set_timing(ctx, int(enable)), ctx)
 
 
 def hrc_get_timing(ctx, cap: int = 512):

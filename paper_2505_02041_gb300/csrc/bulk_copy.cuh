@@ -36,6 +36,12 @@ __device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, unsigned bytes
         : "memory");
 }
 
+// Arrive (count 1) with no transaction bytes.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
     unsigned ok;
     asm volatile(
@@ -69,6 +75,16 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                      smem_addr(dst)),
                  "l"(src), "r"(bytes), "r"(smem_addr(bar))
                  : "memory");
+}
+
+// The same with an L2 cache policy (createpolicy) for the source lines.
+__device__ __forceinline__ void bulk_load_hint(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                               uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
 }
 
 // Tensor (tiled) copies through a tensor map: the box at coordinates (x, y)

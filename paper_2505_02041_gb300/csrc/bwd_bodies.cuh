@@ -649,13 +649,13 @@ template <class A, int C> constexpr size_t adj_trace_smem() {
 // accumulates them in registers over both frames of the pair.  Pair 0
 // writes the image gradients, pair 1 (launched after it) adds to them.
 // With tme / tms (fp32 inputs) the tile region is fetched by TMA tensor
-// copies; a copy wait that gives up sets *status to 5 (HRC_ETIMEOUT) and
-// leaves the tile's gradients unwritten.
+// copies; a copy wait that gives up records its code in the plan's status
+// word and leaves the tile's gradients unwritten.
 template <int P, int C, class IN>
 __device__ __forceinline__ void body_adj_trace(const Plan &pl, const IN *__restrict__ e, const IN *__restrict__ s,
                                                IN *__restrict__ ge, IN *__restrict__ gs, int pair, int bx, int by,
                                                unsigned char *smem, const CUtensorMap *tme = nullptr,
-                                               const CUtensorMap *tms = nullptr, int *status = nullptr) {
+                                               const CUtensorMap *tms = nullptr) {
     using A = typename Prec<P>::A;
     PairTile<A, C> tt(smem);
     const AdjSlots<A, C> sl{reinterpret_cast<A *>(smem + PairTile<A, C>::bytes())};
@@ -667,8 +667,9 @@ __device__ __forceinline__ void body_adj_trace(const Plan &pl, const IN *__restr
     if constexpr (sizeof(A) == 4) {
         if (tme) {
             __shared__ __align__(8) uint64_t bar;
-            if (!tt.stage_tma(pair, x0, y0, tme, tms, &bar, pl.bulk_limit_ns)) {
-                if (threadIdx.x == 0 && status) atomicExch(status, 5);
+            const int code = tt.stage_tma(pair, x0, y0, tme, tms, &bar, pl.bulk_limit_ns);
+            if (code != 0) {
+                if (threadIdx.x == 0) atomicMax(pl.status, code);
                 return;
             }
         } else {

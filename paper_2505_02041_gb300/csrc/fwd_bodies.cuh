@@ -99,9 +99,10 @@ template <class A, int C> struct TraceTile {
     // copies (fp32 inputs; the out-of-grid part of the box reads as zero,
     // which is vacuum).  The boxes land in a staging area that overlaps the
     // w and e planes: every thread first takes its pixels into registers,
-    // then the planes are written.  False when the copy wait gave up.
-    __device__ __forceinline__ bool stage_tma(int x0, int y0, const CUtensorMap *tme, const CUtensorMap *tms,
-                                              uint64_t *bar, long long limit_ns) {
+    // then the planes are written.  Returns 0, or kWaitTimeout / kWaitLost
+    // when the copy wait gave up.
+    __device__ __forceinline__ int stage_tma(int x0, int y0, const CUtensorMap *tme, const CUtensorMap *tms,
+                                             uint64_t *bar, long long limit_ns, unsigned extra_tx) {
         static_assert(sizeof(A) == 4, "fp32 staging");
         constexpr int BOX = TR_REG * TR_REG;                        // 40 x 40
         constexpr int PER = (BOX + 255) / 256;                      // pixels per thread (256 threads)
@@ -112,15 +113,13 @@ template <class A, int C> struct TraceTile {
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            mbar_arrive_expect(bar, (unsigned)((C + 1) * BOX * sizeof(float)));
+            mbar_arrive_expect(bar, (unsigned)((C + 1) * BOX * sizeof(float)) + extra_tx);
 #pragma unroll
             for (int c = 0; c < C; ++c) tma_load_3d(stg + c * BOX, tme, x0 - TR_HALO, y0 - TR_HALO, c, bar);
             tma_load_2d(stg + C * BOX, tms, x0 - TR_HALO, y0 - TR_HALO, bar);
         }
-        if (!mbar_wait(bar, 0, limit_ns)) {
-            mbar_wait(bar, 0, limit_ns);                            // let the copies land
-            return false;
-        }
+        if (!mbar_wait(bar, 0, limit_ns))                           // gave up: let the copies land
+            return mbar_wait(bar, 0, drain_limit_ns(limit_ns)) ? kWaitTimeout : kWaitLost;
         float sv[PER], ev[PER][C];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
@@ -149,7 +148,7 @@ template <class A, int C> struct TraceTile {
 #pragma unroll
             for (int c = 0; c < C; ++c) e[c * TR_PLANE + o] = ev[k][c];
         }
-        return true;
+        return 0;
     }
 };
 
@@ -200,14 +199,13 @@ __device__ __forceinline__ void trace_store(const Plan &pl, const TraceTile<type
 // shares of the level-1 and level-2 probes); its lanes run along v, so every
 // T store is a 128-byte coalesced row segment in every frame.
 // With tme / tms (fp32 inputs), the region is fetched by TMA tensor copies;
-// a copy wait that gives up sets *status to 5 (HRC_ETIMEOUT) and leaves the
-// tile's T entries unwritten.
+// a copy wait that gives up records its code in the plan's status word and
+// leaves the tile's T entries unwritten.
 template <int P, int C>
 __device__ __forceinline__ void body_trace012(const Plan &pl, const float *__restrict__ e, const float *__restrict__ s,
                                               const double *__restrict__ ed, const double *__restrict__ sd, int qmask,
                                               int bx, int by, unsigned char *tr_smem,
-                                              const CUtensorMap *tme = nullptr, const CUtensorMap *tms = nullptr,
-                                              int *status = nullptr) {
+                                              const CUtensorMap *tme = nullptr, const CUtensorMap *tms = nullptr) {
     using A = typename Prec<P>::A;
     TraceTile<A, C> tt(tr_smem);
     const int W = pl.W, H = pl.H;
@@ -217,8 +215,9 @@ __device__ __forceinline__ void body_trace012(const Plan &pl, const float *__res
     } else {
         if (tme) {
             __shared__ __align__(8) uint64_t bar;
-            if (!tt.stage_tma(x0, y0, tme, tms, &bar, pl.bulk_limit_ns)) {
-                if (threadIdx.x == 0 && status) atomicExch(status, 5);
+            const int code = tt.stage_tma(x0, y0, tme, tms, &bar, pl.bulk_limit_ns, (unsigned)pl.bulk_extra_tx);
+            if (code != 0) {
+                if (threadIdx.x == 0) atomicMax(pl.status, code);
                 return;
             }
         } else {
@@ -462,7 +461,7 @@ __device__ __forceinline__ void merge_down_entry(const Plan &pl, int q, int n, i
     };
     auto loadT = [&](const TLevel<P, C> &T, int xx, int kk, Iv<P, C> (&t)[E]) {
         if (PAIR) T.load2(xx, kk, v, t[0], t[E - 1]);
-        else t[0] = T.load(xx, kk, v);
+        else t[0] = T.load_ef(xx, kk, v, l2_evict_first());   // level 0: T rows read once from HBM
     };
     if (x & 1) {
         // Eq. 14: F_+- = A_{n+1}(j) T_n(p, i +- 1/2).L + T_n(p, i +- 1/2).T R_{n+1}(p + v_n(i +- 1/2), j)

@@ -60,8 +60,27 @@ struct Plan {
     const float *envf;
     const double *envd;
     long long env_stride;
+    // control block of the persistent merge-down launch (kernels_persist.cu):
+    // ticket counter, status word and per-column completion counters; null
+    // where the context has none (the persistent launch is then not used)
+    char *pctl;
+    long long pctl_bytes;
+    // status word of this plan's kernels: 0, or a code set by a bounded wait
+    // that gave up (kWaitTimeout; kWaitLost when a copy may still have been
+    // in flight as the block left); read and cleared by the host after a
+    // synchronisation.  Never null for a plan that is launched.
+    int *status;
     QuadGeom q[4];
 };
+
+// Codes of the status word (Plan::status).  A wait on a copy barrier that
+// gives up after its bound is kWaitTimeout; the block then waits once more,
+// with the longer drain bound, for the copies already issued to land, and
+// records kWaitLost if even that runs out (shared memory of a later block on
+// the same SM could then still be written by them).
+constexpr int kWaitTimeout = 5;
+constexpr int kWaitLost = 7;
+__host__ __device__ inline long long drain_limit_ns(long long limit_ns) { return 4 * limit_ns + 100000000LL; }
 
 // Pieces of the directly traced rays (levels 0..2) from a pixel centre:
 // pixel offset (du, dv) and length.  Ray r of level n, direction k:
@@ -255,6 +274,35 @@ __device__ __forceinline__ void st4(__nv_bfloat16 *p, const float (&r)[4]) {
 }
 
 // ---------------------------------------------------------------------------
+// L2 residency.  The merge down reads each T row from HBM (the merge up
+// wrote it long before), while R_{n+1} -- written by the previous launch --
+// is read three times (near at even x, far from both neighbours).  Loading
+// the T rows with the evict-first policy lets them stream through the L2
+// without displacing the R levels.  Used where it measured faster: the
+// bulk-staged merge down and the level-0 merge down inside the fluence sum
+// (the per-thread merge down at 2048^2 was slower with it: a T row is read
+// by two neighbouring blocks, and the second read then misses).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ float ld1_ef(const float *p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld1_ef(const double *p, uint64_t) { return *p; }
+template <class H> __device__ __forceinline__ float ld1_ef_16(const H *p, uint64_t pol) {
+    unsigned short u;
+    asm volatile("ld.global.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(u) : "l"(p), "l"(pol));
+    return to_acc(*reinterpret_cast<const H *>(&u));
+}
+__device__ __forceinline__ float ld1_ef(const __half *p, uint64_t pol) { return ld1_ef_16(p, pol); }
+__device__ __forceinline__ float ld1_ef(const __nv_bfloat16 *p, uint64_t pol) { return ld1_ef_16(p, pol); }
+
+// ---------------------------------------------------------------------------
 // Level addressing
 // ---------------------------------------------------------------------------
 template <int P, int C> struct TLevel {
@@ -335,6 +383,15 @@ template <int P, int C> struct TLevel {
         }
         load2_masked(x, k, v, V, r[0], r[1]);
         load2_masked(x, k, v + 2, V, r[2], r[3]);
+    }
+    // entry v, loaded with an L2 policy
+    __device__ __forceinline__ Iv<P, C> load_ef(int x, int k, int v, uint64_t pol) const {
+        const char *g = row(x, k);
+        Iv<P, C> r;
+#pragma unroll
+        for (int c = 0; c < C; ++c) r.L[c] = ld1_ef(reinterpret_cast<const SL *>(g) + (long long)c * Vs + v, pol);
+        r.t = ld1_ef(reinterpret_cast<const ST *>(g + (long long)C * Vs * sizeof(SL)) + v, pol);
+        return r;
     }
     // entries v .. v+3 (v a multiple of 4; v + 3 < Vs)
     __device__ __forceinline__ void load4(int x, int k, int v, Iv<P, C> (&r)[4]) const {

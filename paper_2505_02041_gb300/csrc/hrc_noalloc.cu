@@ -33,7 +33,8 @@ constexpr int kMaxChannels = 4;
 constexpr int kMaxLevels = 7;                     // ceil(log2(128))
 constexpr size_t kArcFloatOff = 0;                // float A_n table, (1 << n) + j
 constexpr size_t kArcDoubleOff = 1024;            // double copy (unused by fp32 kernels)
-constexpr size_t kLevelsOff = 3072;               // first T level
+constexpr size_t kStatusOff = 3072;               // status word of the bounded copy waits
+constexpr size_t kLevelsOff = 3328;               // first T level
 
 constexpr size_t cx_align(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -63,7 +64,8 @@ constexpr size_t layout_bytes(int side, int C) {
 constexpr size_t kScratchBytes = layout_bytes(kMaxSide, kMaxChannels);
 static_assert(kScratchBytes == HRC_NOALLOC_SCRATCH_BYTES, "hrc.h states the scratch size");
 static_assert((size_t(2) << kMaxLevels) * 4 <= kArcDoubleOff - kArcFloatOff, "arc table fits");
-static_assert((size_t(2) << kMaxLevels) * 8 <= kLevelsOff - kArcDoubleOff, "arc table fits");
+static_assert((size_t(2) << kMaxLevels) * 8 <= kStatusOff - kArcDoubleOff, "arc table fits");
+static_assert(kStatusOff + sizeof(int) <= kLevelsOff, "status word fits");
 
 // The scratch itself.  Host code must never use this name as an address: on
 // the host it is only a stand-in; the device address comes from
@@ -74,6 +76,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 char *g_dev_ptr[kMaxDevices] = {};
 bool g_ready[kMaxDevices] = {};
+// test hook (hrc_noalloc_debug_wait): bytes the trace's copy barrier
+// expects but never receives, and the bound of that wait
+int g_extra_tx = 0;
+long long g_limit_ns = 2000000000LL;
 RayTable g_rays;
 bool g_rays_ready = false;
 thread_local std::string g_err;
@@ -85,20 +91,25 @@ hrc_status fail(hrc_status st, const std::string &msg) {
 }
 
 // Once per device, with that device current: resolve the device address of
-// the scratch array and write the constant arc table (Eq. 13) into it.
+// the scratch array, write the constant arc table (Eq. 13) into it and clear
+// the status word.  The address is resolved again on every call (no
+// allocation, no synchronisation); if it ever differs from the cached one
+// (the device was reset and the library's module loaded anew), the set-up
+// runs again.
 hrc_status setup_device(int dev, char **base) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_rays_ready) {
         g_rays = make_ray_table();
         g_rays_ready = true;
     }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || p == nullptr)
+        return fail(HRC_ECUDA, std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+    if (g_ready[dev] && g_dev_ptr[dev] != static_cast<char *>(p)) g_ready[dev] = false;
     if (!g_ready[dev]) {
         cudaError_t ep = prepare_device_once();
         if (ep != cudaSuccess) return fail(HRC_ECUDA, std::string("kernel set-up failed: ") + cudaGetErrorString(ep));
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || p == nullptr)
-            return fail(HRC_ECUDA, std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
         float af[size_t(2) << kMaxLevels] = {};
         double ad[size_t(2) << kMaxLevels] = {};
         for (int n = 0; n <= kMaxLevels; ++n) {
@@ -112,6 +123,7 @@ hrc_status setup_device(int dev, char **base) {
         char *d = static_cast<char *>(p);
         e = cudaMemcpy(d + kArcFloatOff, af, sizeof(af), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d + kArcDoubleOff, ad, sizeof(ad), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(d + kStatusOff, 0, sizeof(int));
         if (e != cudaSuccess) return fail(HRC_ECUDA, std::string("arc table upload failed: ") + cudaGetErrorString(e));
         g_dev_ptr[dev] = d;
         g_ready[dev] = true;
@@ -144,9 +156,42 @@ extern "C" hrc_status hrc_fluence_noalloc(int W, int H, int channels, const floa
     pl.arena = base;
     pl.arcs_off = (long long)kArcFloatOff;
     pl.arcs_off_d = (long long)kArcDoubleOff;
+    pl.status = reinterpret_cast<int *>(base + kStatusOff);
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        pl.bulk_extra_tx = g_extra_tx;
+        pl.bulk_limit_ns = g_limit_ns;
+    }
     Recorder rec;   // timing off
     int launches = 0;
     e = launch_forward(pl, g_rays, emission, sigma_t, out, static_cast<cudaStream_t>(cuda_stream), &launches, &rec);
     if (e != cudaSuccess) return fail(HRC_ECUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+    return HRC_OK;
+}
+
+extern "C" hrc_status hrc_noalloc_sync(void *cuda_stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail(HRC_ECUDA, "no usable current device");
+    char *base = nullptr;
+    hrc_status st = setup_device(dev, &base);
+    if (st != HRC_OK) return st;
+    e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, base + kStatusOff, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && status != 0) e = cudaMemset(base + kStatusOff, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(HRC_ECUDA, std::string("status read failed: ") + cudaGetErrorString(e));
+    if (status == kWaitLost)
+        return fail(HRC_ETIMEOUT, "a copy wait gave up and its copies did not land within the drain bound: "
+                                  "results of later launches on this device are suspect");
+    if (status != 0) return fail(HRC_ETIMEOUT, "a copy wait gave up: the last call's fluence is incomplete");
+    return HRC_OK;
+}
+
+extern "C" hrc_status hrc_noalloc_debug_wait(int extra_bytes, long long limit_ns) {
+    if (extra_bytes < 0 || extra_bytes > 4096) return fail(HRC_EINVAL, "extra_bytes must be in [0, 4096]");
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_extra_tx = extra_bytes;
+    g_limit_ns = limit_ns > 0 ? limit_ns : 2000000000LL;
     return HRC_OK;
 }

@@ -189,6 +189,8 @@ struct hrc_ctx {
     size_t arena_bytes = 0;
     char *arena64 = nullptr;
     size_t arena64_bytes = 0;
+    char *pctl = nullptr;        // control block of the persistent merge down (ticket, status, counters)
+    size_t pctl_bytes = 0;
     float *dev_e = nullptr, *dev_s = nullptr, *dev_F = nullptr;   // hrc_fluence_host staging
     const void *last_e = nullptr, *last_s = nullptr;
     bool have_fwd = false;
@@ -224,12 +226,15 @@ struct hrc_ctx {
     static constexpr int kStagePlanes = 7;   // e, sigma, albedo, F / dL/dF, dL/de, dL/dsigma, dL/dalbedo
     int launches = 0;
     Recorder rec;
+    int timing_mode = 0;         // 0 off, 1 direct launches with events, 2 events inside the graphs
     std::string err;
     // CUDA graphs of whole passes, keyed by pass kind, precision, schedule
     // and the caller's pointers; captured on a context-owned stream and
     // replayed on the caller's stream.
     struct GraphEntry {
         int kind = -1, prec = -1, sched = -1, mgroups = -1, tune = -1;
+        bool timed = false;                  // captured with event-record nodes (timing mode 2)
+        std::vector<Recorder::Rec> recs;     // those nodes' events
         const void *p[8] = {};
         cudaGraphExec_t exec = nullptr;
         int launches = 0;
@@ -237,6 +242,7 @@ struct hrc_ctx {
     GraphEntry graphs[8];
     int graph_next = 0;
     bool use_graphs = true;
+    long long graph_captures = 0;   // graphs captured and instantiated so far
     cudaStream_t cap_stream = nullptr;
     // batched contexts
     bool batched = false;
@@ -290,6 +296,22 @@ hrc_status cuda_fail(hrc_ctx *ctx, cudaError_t e, const char *where) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+}  // namespace
+
+namespace hrc {
+
+cudaError_t read_plan_status(const Plan &pl, int *status) {
+    *status = 0;
+    if (!pl.status) return cudaSuccess;
+    cudaError_t e = cudaMemcpy(status, pl.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && *status != 0) e = cudaMemset(pl.status, 0, sizeof(int));
+    return e;
+}
+
+}  // namespace hrc
+
+namespace {
+
 // Upload the arc tables of a plan into its arena.
 cudaError_t upload_arcs(const Plan &pl, char *arena) {
     std::vector<float> af;
@@ -315,30 +337,41 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
 template <class ENQ>
 hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue, const char *where) {
     ctx->launches = 0;
-    if (ctx->rec.on || !ctx->use_graphs) {
+    if ((ctx->rec.on && ctx->timing_mode != 2) || !ctx->use_graphs) {
+        ctx->rec.ext = false;
         ctx->rec.reset(ctx->stream);
         cudaError_t e = enqueue(ctx->stream, &ctx->launches, &ctx->rec);
         if (e != cudaSuccess) return cuda_fail(ctx, e, where);
         return HRC_OK;
     }
+    const bool timed = ctx->rec.on;
     const void *const *key = pk.p;
     for (auto &g : ctx->graphs) {
         if (g.exec && g.kind == kind && g.prec == ctx->prec && g.sched == ctx->sched && g.mgroups == ctx->mgroups &&
-            g.tune == ctx->mthreads * 4 + ctx->vmajor * 2 + ctx->mdown &&
+            g.tune == ctx->mthreads * 8 + ctx->vmajor * 4 + ctx->mdown && g.timed == timed &&
             std::memcmp(g.p, key, sizeof(pk.p)) == 0) {
             cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(ctx, e, where);
             ctx->launches = g.launches;
+            if (timed) ctx->rec.recs = g.recs;
             return HRC_OK;
         }
     }
     Recorder off;
+    Recorder *rr = &off;
+    if (timed) {   // fresh events from the pool for this graph's record nodes
+        ctx->rec.ext = true;
+        ctx->rec.st = ctx->cap_stream;
+        ctx->rec.recs.clear();
+        rr = &ctx->rec;
+    }
     int n = 0;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, where);
-    cudaError_t e1 = enqueue(ctx->cap_stream, &n, &off);
+    cudaError_t e1 = enqueue(ctx->cap_stream, &n, rr);
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    ctx->rec.ext = false;
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         return cuda_fail(ctx, e1 != cudaSuccess ? e1 : e2, where);
@@ -347,6 +380,7 @@ hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+    ++ctx->graph_captures;
     auto &slot = ctx->graphs[ctx->graph_next];
     ctx->graph_next = (ctx->graph_next + 1) % 8;
     if (slot.exec) cudaGraphExecDestroy(slot.exec);
@@ -355,7 +389,9 @@ hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue
     slot.prec = ctx->prec;
     slot.sched = ctx->sched;
     slot.mgroups = ctx->mgroups;
-    slot.tune = ctx->mthreads * 4 + ctx->vmajor * 2 + ctx->mdown;
+    slot.tune = ctx->mthreads * 8 + ctx->vmajor * 4 + ctx->mdown;
+    slot.timed = timed;
+    slot.recs = timed ? ctx->rec.recs : std::vector<Recorder::Rec>();
     std::memcpy(slot.p, key, sizeof(pk.p));
     slot.launches = n;
     e = cudaGraphLaunch(exec, ctx->stream);
@@ -438,9 +474,26 @@ const char *hrc_last_error(const hrc_ctx *ctx) {
 
 int hrc_last_launch_count(const hrc_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+hrc_status hrc_set_graphs(hrc_ctx *ctx, int enable) {
+    if (!ctx) return HRC_EINVAL;
+    if (enable != 0 && enable != 1) return fail(ctx, HRC_EINVAL, "hrc_set_graphs: 0 or 1");
+    ctx->use_graphs = enable != 0;
+    for (hrc_ctx *k : ctx->chan) hrc_set_graphs(k, enable);
+    return HRC_OK;
+}
+
+long long hrc_graph_captures(const hrc_ctx *ctx) {
+    if (!ctx) return -1;
+    long long n = ctx->graph_captures;
+    for (const hrc_ctx *k : ctx->chan) n += k->graph_captures;
+    return n;
+}
+
 hrc_status hrc_set_timing(hrc_ctx *ctx, int enable) {
     if (!ctx) return HRC_EINVAL;
+    if (enable < 0 || enable > 2) return fail(ctx, HRC_EINVAL, "hrc_set_timing: 0, 1 or 2");
     ctx->rec.on = enable != 0;
+    ctx->timing_mode = enable;
     for (hrc_ctx *k : ctx->chan) hrc_set_timing(k, enable);
     return HRC_OK;
 }
@@ -514,6 +567,18 @@ hrc_status hrc_create(int W, int H, int channels, int cascades, hrc_ctx **out) {
         hrc_destroy(ctx);
         return fail(nullptr, HRC_ENOMEM, "hrc_create: staging allocation failed");
     }
+    ctx->pctl_bytes = persist_ctl_bytes(p32);
+    e = cudaMalloc(&ctx->pctl, ctx->pctl_bytes);
+    if (e == cudaSuccess) e = cudaMemset(ctx->pctl, 0, ctx->pctl_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->pctl = nullptr;
+        hrc_destroy(ctx);
+        return fail(nullptr, HRC_ENOMEM, "hrc_create: control block allocation failed");
+    }
+    p32.pctl = ctx->pctl;
+    p32.pctl_bytes = (long long)ctx->pctl_bytes;
+    p32.status = reinterpret_cast<int *>(ctx->pctl + 8);
     ctx->plan = p32;
     ctx->plan.arena = ctx->arena;
     ctx->plan.sched = ctx->sched;
@@ -533,6 +598,7 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     else cudaDeviceSynchronize();
     cudaFree(ctx->arena);
     cudaFree(ctx->arena64);
+    cudaFree(ctx->pctl);
     cudaFree(ctx->dev_e);
     cudaFree(ctx->dev_s);
     cudaFree(ctx->dev_F);
@@ -589,7 +655,8 @@ namespace {
 bool config_valid(const hrc_ctx *ctx, const hrc_launch_config &c) {
     return (c.schedule >= 0 && c.schedule <= 2) && (c.groups == 1 || c.groups == 2 || c.groups == 4) &&
            (c.threads == 64 || c.threads == 128 || c.threads == 256 || c.threads == 512) &&
-           (c.vmajor == 0 || c.vmajor == 1) && (c.mdown == 0 || c.mdown == 1) &&
+           (c.vmajor == 0 || c.vmajor == 1) && (c.mdown >= 0 && c.mdown <= 2) &&
+           !(c.mdown == 2 && c.schedule == 2) &&
            !(c.vmajor && 4LL * (ctx->W + ctx->H) > 65535);
 }
 
@@ -617,12 +684,17 @@ hrc_status hrc_debug_bulk_wait(hrc_ctx *ctx, int extra_bytes, long long limit_ns
 hrc_status hrc_sync(hrc_ctx *ctx) {
     if (!ctx) return HRC_EINVAL;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    int status = 0, status_b = 0;
-    if (e == cudaSuccess) e = read_bulk_status(&status);
-    if (e == cudaSuccess) e = read_adj_bulk_status(&status_b);
-    status |= status_b;
+    int status = 0;
+    if (e == cudaSuccess) e = read_plan_status(ctx->plan, &status);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_sync");
-    if (status != 0) return fail(ctx, HRC_ETIMEOUT, "a bulk-copy wait gave up (its launch ended early)");
+    for (hrc_ctx *k : ctx->chan) {   // per-channel contexts keep status words of their own
+        const hrc_status st = hrc_sync(k);
+        if (st != HRC_OK) return fail(ctx, st, k->err);
+    }
+    if (status == kWaitLost)
+        return fail(ctx, HRC_ETIMEOUT, "a copy wait gave up and its copies did not land within the drain bound: "
+                                       "results of later launches on this device are suspect");
+    if (status != 0) return fail(ctx, HRC_ETIMEOUT, "a bounded copy or dependency wait gave up (its launch ended early)");
     return HRC_OK;
 }
 
@@ -711,9 +783,10 @@ hrc_status hrc_autotune(hrc_ctx *ctx, float *best_ms) {
     ctx->rec.on = false;
     static const int kThreads[4] = {64, 128, 256, 512};
     static const int kGroups[3] = {1, 2, 4};
-    for (int cand = 0; cand < 3 * 3 * 4 * 2 * 2 && st == HRC_OK; ++cand) {
+    for (int cand = 0; cand < 3 * 3 * 4 * 2 * 3 && st == HRC_OK; ++cand) {
         const hrc_launch_config c{cand % 3, kGroups[(cand / 3) % 3], kThreads[(cand / 9) & 3], (cand / 36) & 1,
-                                  (cand / 72) & 1};
+                                  (cand / 72) % 3};
+        if (c.mdown == 2 && !persist_down_usable(ctx->plan)) continue;
         if (!config_valid(ctx, c)) continue;
         apply_config(ctx, c);
         for (int r = 0; r < 2 && st == HRC_OK; ++r) st = hrc_fluence(ctx, ctx->dev_e, ctx->dev_s, ctx->dev_F);
@@ -788,6 +861,7 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
             p64.mthreads = ctx->mthreads;
             p64.vmajor = ctx->vmajor;
             p64.mdown = ctx->mdown;
+            p64.status = reinterpret_cast<int *>(ctx->pctl + 8);
             ctx->plan64 = p64;
             e = upload_arcs(ctx->plan64, ctx->arena64);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
@@ -801,6 +875,9 @@ hrc_status hrc_set_precision(hrc_ctx *ctx, hrc_precision prec) {
         p.mthreads = ctx->mthreads;
         p.vmajor = ctx->vmajor;
         p.mdown = ctx->mdown;
+        p.pctl = ctx->pctl;
+        p.pctl_bytes = (long long)ctx->pctl_bytes;
+        p.status = reinterpret_cast<int *>(ctx->pctl + 8);
         ctx->plan = p;
         cudaError_t e = upload_arcs(ctx->plan, ctx->arena);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_precision");
@@ -1482,6 +1559,7 @@ hrc_status build_batched_plans(hrc_ctx *ctx, int prec) {
         ctx->bplans[i].mgroups = 1;
         ctx->bplans[i].mthreads = 128;
         ctx->bplans[i].vmajor = 0;
+        ctx->bplans[i].status = ctx->d_status;
     }
     if (off > ctx->arena_bytes) return fail(ctx, HRC_ENOMEM, "batched layout exceeds the arena");
     for (int i = 0; i < ctx->nscenes; ++i) {

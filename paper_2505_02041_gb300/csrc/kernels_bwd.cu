@@ -45,9 +45,6 @@ __global__ void __launch_bounds__(512) k_adj_merge_up(Plan pl, RowSplitB rs, int
     body_adj_merge_up<P, C, ENV>(pl, rs, n, row, vb);
 }
 
-// HRC_ETIMEOUT (5) once a TMA copy wait of the adjoint trace gave up.
-__device__ int g_adj_bulk_status;
-
 template <int P, int C, class IN>
 __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_trace(Plan pl, const IN *__restrict__ e, const IN *__restrict__ s,
                                                    IN *__restrict__ ge, IN *__restrict__ gs, int pair,
@@ -55,7 +52,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_trace(Plan pl, const IN 
                                                    const __grid_constant__ CUtensorMap tms, int use_tma) {
     extern __shared__ __align__(128) unsigned char tb_smem[];
     body_adj_trace<P, C, IN>(pl, e, s, ge, gs, pair, blockIdx.x, blockIdx.y, tb_smem, use_tma ? &tme : nullptr,
-                             use_tma ? &tms : nullptr, &g_adj_bulk_status);
+                             use_tma ? &tms : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -245,13 +242,6 @@ cudaError_t launch_backward(const Plan &pl, const RayTable &rt, const void *e, c
     case P_BF16: return bwd_prec<P_BF16>(pl, rt, e, s, gF, ge, gs, recompute, st, launches, rec);
     default: return bwd_prec<P_FP64>(pl, rt, e, s, gF, ge, gs, recompute, st, launches, rec);
     }
-}
-
-cudaError_t read_adj_bulk_status(int *status) {
-    int zero = 0;
-    cudaError_t e = cudaMemcpyFromSymbol(status, g_adj_bulk_status, sizeof(int));
-    if (e == cudaSuccess && *status != 0) e = cudaMemcpyToSymbol(g_adj_bulk_status, &zero, sizeof(int));
-    return e;
 }
 
 }  // namespace hrc

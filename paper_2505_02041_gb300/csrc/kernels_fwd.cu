@@ -9,10 +9,6 @@
 
 namespace hrc {
 
-// Status of the bulk-copy kernels: HRC_ETIMEOUT (5) once a bounded wait on a
-// copy barrier gave up (read and cleared by read_bulk_status).
-__device__ int g_bulk_status;
-
 template <int P, int C>
 __global__ void __launch_bounds__(256) k_trace012(Plan pl, const float *__restrict__ e, const float *__restrict__ s,
                                                   const double *__restrict__ ed, const double *__restrict__ sd,
@@ -20,7 +16,7 @@ __global__ void __launch_bounds__(256) k_trace012(Plan pl, const float *__restri
                                                   const __grid_constant__ CUtensorMap tms, int use_tma) {
     extern __shared__ __align__(128) unsigned char tr_smem[];
     body_trace012<P, C>(pl, e, s, ed, sd, qmask, blockIdx.x, blockIdx.y, tr_smem, use_tma ? &tme : nullptr,
-                        use_tma ? &tms : nullptr, &g_bulk_status);
+                        use_tma ? &tms : nullptr);
 }
 
 // Row and v-block of this block: the launch grid is (rows, v-blocks), or
@@ -144,15 +140,16 @@ __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, i
         }
         if (near_ok) total += 2u * (unsigned)(C * tb * sizeof(SL));
         mbar_arrive_expect(&bar, total + (unsigned)pl.bulk_extra_tx);
+        const uint64_t pol = l2_evict_first();               // T rows: read once from HBM
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const char *gr = Tt.row(xt, kk[e]);
 #pragma unroll
             for (int c = 0; c < C; ++c)
-                bulk_load(tl + (e * C + c) * kBV, reinterpret_cast<const SL *>(gr) + (long long)c * g.Vs + v0,
-                          tb * sizeof(SL), &bar);
-            bulk_load(tt + e * kBV, reinterpret_cast<const ST *>(gr + (long long)C * g.Vs * sizeof(SL)) + v0,
-                      tb * sizeof(ST), &bar);
+                bulk_load_hint(tl + (e * C + c) * kBV, reinterpret_cast<const SL *>(gr) + (long long)c * g.Vs + v0,
+                               tb * sizeof(SL), &bar, pol);
+            bulk_load_hint(tt + e * kBV, reinterpret_cast<const ST *>(gr + (long long)C * g.Vs * sizeof(SL)) + v0,
+                           tb * sizeof(ST), &bar, pol);
             if (far_ok && fe[e] > fs[e])
 #pragma unroll
                 for (int c = 0; c < C; ++c)
@@ -164,9 +161,9 @@ __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, i
                     bulk_load(rn + (e * C + c) * kBV, R1.base + R1.idx(x2, j[e], c, v0), tb * sizeof(SL), &bar);
         }
     }
-    if (!mbar_wait(&bar, 0, pl.bulk_limit_ns)) {              // gave up: report, let the copies land, leave
-        if (threadIdx.x == 0) atomicExch(&g_bulk_status, 5);
-        mbar_wait(&bar, 0, pl.bulk_limit_ns);
+    if (!mbar_wait(&bar, 0, pl.bulk_limit_ns)) {              // gave up: let the copies land, report, leave
+        const int code = mbar_wait(&bar, 0, drain_limit_ns(pl.bulk_limit_ns)) ? kWaitTimeout : kWaitLost;
+        if (threadIdx.x == 0) atomicMax(pl.status, code);
         return;
     }
     const int v = v0 + 4 * (int)threadIdx.x;
@@ -382,7 +379,25 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
             rec->end();
             ++*launches;
         }
-        // R_0 feeds only the fluence sum, which computes it in place
+        // R_0 feeds only the fluence sum, which computes it in place.
+        // mdown 2: every level in one persistent launch (kernels_persist.cu)
+        if (pl.mdown == 2 && P != P_FP64 && persist_down_usable(pl)) {
+            auto level_bytes = [&](int n) {
+                double by = 0;
+                for (int q = 0; q < 4; ++q) {
+                    const QuadGeom &g = pl.q[q];
+                    if (!((qm >> q) & 1) || n >= g.N) continue;
+                    by += bytes_T_odd(pl, q, n) + bytes_T_even_dirs(pl, q, n + 1);
+                    by += bytes_R(pl, q, n + 1) + bytes_R(pl, q, n);
+                }
+                return by;
+            };
+            double by = 0;
+            for (int n = Nmax - 1; n >= 1; --n) by += level_bytes(n);
+            const cudaError_t err = launch_merge_down_persist(pl, qm, Nmax - 1, 1, st, launches, rec, by);
+            if (err != cudaSuccess) return err;
+            continue;
+        }
         for (int n = Nmax - 1; n >= 1; --n) {
             RowSplit rs = make_split(pl, n, 2, qm);
             if (rs.start[4] == 0) continue;
@@ -509,15 +524,6 @@ static cudaError_t prepare_prec() {
         set((const void *)k_merge_down_bulk<P, 4, false>, BulkMD<P, 4>::bytes());
         set((const void *)k_merge_down_bulk<P, 4, true>, BulkMD<P, 4>::bytes());
     }
-    return e;
-}
-
-// Reads and clears the bulk-copy kernels' status (after the caller's stream
-// has been synchronised): 0, or 5 (HRC_ETIMEOUT) if a copy wait gave up.
-cudaError_t read_bulk_status(int *status) {
-    int zero = 0;
-    cudaError_t e = cudaMemcpyFromSymbol(status, g_bulk_status, sizeof(int));
-    if (e == cudaSuccess && *status != 0) e = cudaMemcpyToSymbol(g_bulk_status, &zero, sizeof(int));
     return e;
 }
 

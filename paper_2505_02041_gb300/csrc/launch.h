@@ -18,10 +18,14 @@ enum KernelKind {
 };
 
 // Optional per-launch CUDA-event timing (off by default).  Events come from
-// a pool created when timing is enabled; recording is stream-ordered.
+// a pool created when timing is enabled; recording is stream-ordered.  With
+// `ext` the records are made while a graph is being captured: they become
+// event-record nodes of the graph (cudaEventRecordExternal), so every replay
+// times the kernels as the graph runs them.
 struct Recorder {
     struct Rec { int kind, level; double bytes; cudaEvent_t a, b; };
     bool on = false;
+    bool ext = false;
     cudaStream_t st = nullptr;
     std::vector<cudaEvent_t> pool;
     std::vector<Rec> recs;
@@ -35,15 +39,19 @@ struct Recorder {
         }
         return pool[used++];
     }
+    void record(cudaEvent_t e) {
+        if (ext) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else cudaEventRecord(e, st);
+    }
     void begin(int kind, int level, double bytes) {
         if (!on) return;
         Rec r{kind, level, bytes, next(), next()};
-        cudaEventRecord(r.a, st);
+        record(r.a);
         recs.push_back(r);
     }
     void end() {
         if (!on || recs.empty()) return;
-        cudaEventRecord(recs.back().b, st);
+        record(recs.back().b);
     }
     ~Recorder() {
         for (auto e : pool) cudaEventDestroy(e);
@@ -184,9 +192,18 @@ cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *ds
 // R_0 of every frame into the plan's buffer (the forward does not store it).
 cudaError_t launch_r0(const Plan &pl, cudaStream_t st);
 
-// Reads and clears the bulk-copy kernels' timeout status (0 or 5).
-cudaError_t read_bulk_status(int *status);
-cudaError_t read_adj_bulk_status(int *status);
+// Persistent merge down (kernels_persist.cu): R_{n_hi} .. R_{n_lo} of the
+// frames in qm in one launch, after resetting the plan's control block
+// (pl.pctl, persist_ctl_bytes(pl) bytes).  `bytes`: the algorithmic bytes
+// recorded for the launch.
+bool persist_down_usable(const Plan &pl);
+size_t persist_ctl_bytes(const Plan &pl);
+cudaError_t launch_merge_down_persist(const Plan &pl, int qm, int n_hi, int n_lo, cudaStream_t st, int *launches,
+                                      Recorder *rec, double bytes);
+
+// Reads and clears a plan's status word (after its stream has been
+// synchronised): 0, kWaitTimeout or kWaitLost.
+cudaError_t read_plan_status(const Plan &pl, int *status);
 
 // Tensor maps of fp32 emission / extinction for TMA tile staging (false when
 // the layout does not allow them).

@@ -140,10 +140,10 @@ template <class A, int C> struct PairTile {
     // copies (fp32; box PT_RU x PT_RV along image x, y for pair 0, PT_RV x
     // PT_RU for pair 1; zero outside the grid = vacuum).  The boxes land in a
     // staging area overlapping the tw planes: every thread takes its pixels
-    // into registers first, then the planes are written.  False when the
-    // copy wait gave up.
-    __device__ __forceinline__ bool stage_tma(int pair, int x0, int y0, const CUtensorMap *tme, const CUtensorMap *tms,
-                                              uint64_t *bar, long long limit_ns) {
+    // into registers first, then the planes are written.  Returns 0, or
+    // kWaitTimeout / kWaitLost when the copy wait gave up.
+    __device__ __forceinline__ int stage_tma(int pair, int x0, int y0, const CUtensorMap *tme, const CUtensorMap *tms,
+                                             uint64_t *bar, long long limit_ns) {
         static_assert(sizeof(A) == 4, "fp32 staging");
         constexpr int BOX = PT_RU * PT_RV;
         constexpr int PER = (BOX + 255) / 256;
@@ -160,10 +160,8 @@ template <class A, int C> struct PairTile {
             for (int c = 0; c < C; ++c) tma_load_3d(stg + c * BOX, tme, x0 - PT_HALO, y0 - PT_HALO, c, bar);
             tma_load_2d(stg + C * BOX, tms, x0 - PT_HALO, y0 - PT_HALO, bar);
         }
-        if (!mbar_wait(bar, 0, limit_ns)) {
-            mbar_wait(bar, 0, limit_ns);
-            return false;
-        }
+        if (!mbar_wait(bar, 0, limit_ns))                           // gave up: let the copies land
+            return mbar_wait(bar, 0, drain_limit_ns(limit_ns)) ? kWaitTimeout : kWaitLost;
         float sv[PER], ev[PER][C];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
@@ -204,7 +202,7 @@ template <class A, int C> struct PairTile {
                 s[o] = sg;
             }
         }
-        return true;
+        return 0;
     }
 };
 

@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "hrc.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:hrc_status|int|const char \*)\s*(hrc_\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:hrc_status|int|long long|const char \*)\s*(hrc_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 

@@ -169,7 +169,9 @@ def test_launch_configurations_give_the_same_results():
     for sched in (0, 1, 2):
         for groups in (1, 2, 4):
             for threads in (64, 128, 256, 512):
-                for vmajor, mdown in ((0, 0), (1, 0), (0, 1), (1, 1)):
+                for vmajor, mdown in ((0, 0), (1, 0), (0, 1), (1, 1), (0, 2), (1, 2)):
+                    if mdown == 2 and sched == 2:
+                        continue                  # the persistent merge down runs on one branch only
                     h.set_launch_config(sched, groups, threads, vmajor, mdown)
                     assert h.launch_config == dict(schedule=sched, groups=groups, threads=threads, vmajor=vmajor,
                                                    mdown=mdown)
@@ -194,6 +196,65 @@ def test_bulk_copy_wait_times_out_and_recovers():
     e, s = scenes.random_scene(64, 48, 2, 51)
     h = HRC(64, 48, 2)
     h.set_launch_config(0, 1, 128, 1, 1)
+    ed, sd = to_dev(e), to_dev(s)
+    other = HRC(64, 48, 2)                       # a second context on the same GPU
+    _lib.hrc_debug_bulk_wait(h.ctx, 16, 1_000_000)
+    h.forward(ed, sd)
+    Fo = other.forward(ed, sd)
+    other.sync()                                 # its status word is its own: no timeout reported here
+    with pytest.raises(_lib.HRCError) as ex:
+        h.sync()
+    assert ex.value.status == _lib.HRC_ETIMEOUT
+    _lib.hrc_debug_bulk_wait(h.ctx, 0, 0)
+    F = h.forward(ed, sd)
+    h.sync()
+    assert err_max(F.cpu().numpy(), oracle.fluence(e, s)) <= TOL
+    assert err_max(Fo.cpu().numpy(), oracle.fluence(e, s)) <= TOL
+
+
+@pytest.mark.parametrize("W,H,C,casc,seed", [
+    (48, 40, 2, 0, 12), (300, 260, 3, 0, 33), (257, 130, 1, 0, 34), (1, 6, 1, 0, 35), (5, 7, 4, 0, 36),
+    (64, 64, 1, 3, 37), (1030, 20, 3, 0, 38),
+])
+def test_persistent_merge_down_matches_bulk_and_oracle(W, H, C, casc, seed):
+    """The merge down of every level in one persistent launch (mdown 2) does
+    each entry's arithmetic in the same order as the one-launch-per-level
+    bulk-staged kernel (mdown 1): the fluence is identical bit for bit, and
+    every R level matches the oracle."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC
+    e, s = scenes.random_scene(W, H, C, seed)
+    h = HRC(W, H, C, casc)
+    ed, sd = to_dev(e), to_dev(s)
+    h.set_launch_config(0, 1, 128, 0, 1)
+    Fb = h.forward(ed, sd).clone()
+    for sched in (0, 1):
+        h.set_launch_config(sched, 1, 128, 0, 2)
+        F = h.forward(ed, sd)
+        h.sync()
+        assert torch.equal(F, Fb), sched
+    assert err_max(F.cpu().numpy(), oracle.fluence(e, s, casc)) <= TOL
+    for q in range(4):
+        U = W if q < 2 else H
+        N = int(np.ceil(np.log2(U))) if U > 1 else 0
+        if casc > 0:
+            N = min(N, casc)
+        for n in range(1, N):
+            Rg = h.level(q, "R", n).cpu().numpy()
+            Rr = oracle.frame_level(e, s, q, "R", n, casc)
+            assert np.max(np.abs(Rg[1:] - Rr[1:])) <= 2e-5 * max(1.0, np.max(np.abs(Rr))), (q, n)
+
+
+def test_persistent_merge_down_wait_times_out_and_recovers():
+    """The persistent merge down bounds every dependency wait: with the test
+    hook on, no item is published, so every wait on the level above gives up
+    after 1 ms; hrc_sync reports HRC_ETIMEOUT and the context then computes
+    correctly."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC, _lib
+    e, s = scenes.random_scene(64, 48, 2, 52)
+    h = HRC(64, 48, 2)
+    h.set_launch_config(0, 1, 128, 0, 2)
     ed, sd = to_dev(e), to_dev(s)
     _lib.hrc_debug_bulk_wait(h.ctx, 16, 1_000_000)
     h.forward(ed, sd)
