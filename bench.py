@@ -70,8 +70,8 @@ def bench_cross_blur(h, fwd, fwd_bwd, timed, gF, gE, gS, hbm_peak, thr=0.5, step
     fb_ms = timed(fwd_bwd, steps)
     _lib.hrc_set_timing(h.ctx, True)
     kf, kb = {}, {}
-    timed(fwd, steps, kf)
-    timed(lambda: _lib.hrc_fluence_backward(h.ctx, gF, gE, gS), steps, kb)
+    timed(fwd, steps, h, kf)
+    timed(lambda: _lib.hrc_fluence_backward(h.ctx, gF, gE, gS), steps, h, kb)
     _lib.hrc_set_timing(h.ctx, False)
     h.set_cross_blur(False)
     out = {"threshold": thr, "forward_ms": statistics.mean(f_ms), "fwd_bwd_ms": statistics.mean(fb_ms)}
@@ -107,7 +107,7 @@ def bench_bounces(h, e, s, timed, hbm_peak, K=6, rho=0.5, steps=5):
     launches = h.launch_count()
     _lib.hrc_set_timing(h.ctx, True)
     kf = {}
-    timed(fwd, steps, kf)
+    timed(fwd, steps, h, kf)
     _lib.hrc_set_timing(h.ctx, False)
     out = {"bounces": K, "albedo": rho, "forward_ms": statistics.mean(f_ms), "fwd_bwd_ms": statistics.mean(fb_ms),
            "forward_ms_per_bounce": statistics.mean(f_ms) / (K + 1), "launches_forward": launches}
@@ -265,6 +265,42 @@ def paper_schedule_bytes(W, H, C, precision):
     return total + W * H * (1 + C) * 4.0 + W * H * C * 4.0
 
 
+def survey_backward_bytes(W, H, C, precision, recompute):
+    """Bytes of one backward pass over the same stored-level schedule
+    (Sec. 4.3.2 with the adjoint of every step; the SURVEY byte model), per
+    quadrant frame with |T_n| = U V (1 + 2^-n), V_T = C b_L + 4, V_R = C b_L,
+    gradients fp32 (V_gT = 4 (C + 1), V_gR = 4 C):
+      forward recompute (recompute=True only): T_0..T_N written, T_2..T_{N-1}
+        read by the merge up, R_1..R_{N-1} written;
+      adjoint of the sum: dL/dF read once (per image);
+      adjoint merge down, n = N-1 .. 0: dL/dR_n and R_{n+1} read, |T_n| T
+        entries read, dL/dR_{n+1} and |T_n| dL/dT entries written (each
+        counted once: the lower end of 'a write plus at most one
+        read-modify-write');
+      adjoint merge up, n = N .. 3: dL/dT_n and T_{n-1} read, dL/dT_{n-1}
+        read-modified-written;
+      trace adjoint: dL/dT_0..dL/dT_2 and the inputs read, dL/de and dL/dsigma
+        written (per image)."""
+    bl = 4.0 if precision == "fp32" else 2.0
+    vt, vr = C * bl + 4.0, C * bl
+    vgt, vgr = 4.0 * (C + 1), 4.0 * C
+    total = 0.0
+    for U, V in ((W, H), (W, H), (H, W), (H, W)):
+        N = max(0, (U - 1).bit_length())
+        X2 = U * V
+        t = lambda n: X2 * (1.0 + 2.0 ** -n)
+        if recompute:
+            total += vt * sum(t(n) for n in range(N + 1)) + vt * sum(t(n) for n in range(2, N)) + (N - 1) * X2 * vr
+        for n in range(N - 1, -1, -1):
+            total += X2 * vgr + (X2 * vr if n + 1 < N else 0.0) + t(n) * vt
+            total += (X2 * vgr if n + 1 < N else 0.0) + t(n) * vgt
+        for n in range(N, 2, -1):
+            total += t(n) * vgt + t(n - 1) * vt + 2 * t(n - 1) * vgt
+        total += sum(t(n) for n in range(min(N, 2) + 1)) * vgt
+    img = W * H
+    return total + img * C * 4.0 + img * (1 + C) * 4.0 + img * (1 + C) * 4.0
+
+
 def aggregate_max(values, world, device=None):
     """Element-wise max over ranks of per-rank totals (identity on one rank):
     the job's time is its slowest rank's."""
@@ -359,6 +395,179 @@ def cpu_baseline(workload, budget_s=20.0):
             "sample": f"{len(times)} full {W}x{H} C={C} frames of the same workload (FP64, OpenMP over rows)"}
 
 
+class Timer:
+    """Steps timed with CUDA events on the launching stream, the L2 flushed
+    (a 256 MB write) before each step, outside the events."""
+
+    def __init__(self, dev):
+        import torch
+        self.torch = torch
+        self.dev = dev
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def __call__(self, step, n, h=None, per=None):
+        torch = self.torch
+        stream = torch.cuda.current_stream(self.dev)
+        out = []
+        for _ in range(n):
+            self.flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+            if per is not None:
+                accumulate(per, h)
+        return out
+
+
+def accumulate(per, h):
+    """Add the timing records of h's last call to per[kind] = [ms, bytes,
+    records, launches]."""
+    from paper_2505_02041_gb300 import _lib
+    for kind, level, ms, by, nl in _lib.hrc_get_timing(h.ctx):
+        d = per.setdefault(kind, [0.0, 0.0, 0, 0])
+        d[0] += ms
+        d[1] += by
+        d[2] += 1
+        d[3] += nl
+
+
+def phase_table(per, steps, hbm_peak):
+    return {k: {"ms_per_frame": v[0] / steps, "launches_per_frame": v[3] / steps, "bytes_per_frame": v[1] / steps,
+                "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None,
+                "frac_of_peak": v[1] / (v[0] * 1e-3) / 1e9 / hbm_peak if v[0] > 0 else None}
+            for k, v in sorted(per.items())}
+
+
+def measure_context(h, e, s, timed, steps, hbm_peak):
+    """One context on one workload: graph-replayed forward and forward +
+    backward (both backward strategies), then the same frames with the
+    kernels timed by phase inside the replayed graphs (timing mode 3: one
+    event before the first and one after the last launch of each phase, no
+    event between launches) and launch by launch with direct launches
+    (timing mode 1, each record including that launch's host-side launch
+    latency)."""
+    import torch
+    from paper_2505_02041_gb300 import _lib
+    F = torch.empty_like(e)
+    gF = torch.ones_like(e)
+    gE = torch.empty_like(e)
+    gS = torch.empty_like(s)
+    fwd = lambda: h.forward(e, s, F)
+
+    def fwd_bwd():
+        h.forward(e, s, F)
+        _lib.hrc_fluence_backward(h.ctx, gF, gE, gS)
+
+    for _ in range(3):
+        fwd_bwd()
+    fwd()
+    n_fwd = h.launch_count()
+    fwd_bwd()
+    n_bwd = h.launch_count()
+    out = {"forward_ms": timed(fwd, steps), "fwd_bwd_ms": timed(fwd_bwd, steps),
+           "launches": {"forward": n_fwd, "backward": n_bwd}}
+    _lib.hrc_set_backward_recompute(h.ctx, 1)
+    fwd_bwd()
+    fwd_bwd()
+    out["launches"]["backward_recompute"] = h.launch_count()
+    out["fwd_bwd_recompute_ms"] = timed(fwd_bwd, steps)
+    _lib.hrc_set_backward_recompute(h.ctx, 0)
+    for mode, name in ((3, "graph"), (1, "direct")):
+        _lib.hrc_set_timing(h.ctx, mode)
+        fw, bw = {}, {}
+        fwd()
+        timed(fwd, steps, h, fw)
+        h.forward(e, s, F)
+        timed(lambda: _lib.hrc_fluence_backward(h.ctx, gF, gE, gS), steps, h, bw)
+        _lib.hrc_set_timing(h.ctx, 0)
+        out["phases_" + name] = (fw, bw)
+    h.sync()
+    out["gbufs"] = (F, gF, gE, gS)
+    return out
+
+
+def roofline_of(phases_graph, phases_direct, steps, hbm_peak, workload, launch_config):
+    """The dominant phase (largest share of the forward, timed inside the
+    graph) against the measured copy peak, beside its launch-by-launch
+    direct timing."""
+    kind, (kms, kbytes, krec, klaunch) = max(phases_graph.items(), key=lambda kv: kv[1][0])
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    d = phases_direct.get(kind)
+    direct = None
+    if d and d[0] > 0:
+        ad = (d[1] / d[2]) / ((d[0] / d[2]) * 1e-3) / 1e9
+        direct = {"achieved": ad, "frac": ad / hbm_peak, "us_per_launch": d[0] / d[2] * 1e3,
+                  "timing": "each launch launched directly, bracketed by CUDA events (host launch latency included)"}
+    return {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "launches_per_frame": klaunch / steps,
+            "bytes_per_launch": kbytes / max(klaunch, 1), "us_per_launch": kms / max(klaunch, 1) * 1e3,
+            "traffic": ncu_traffic(traffic_key(kind, launch_config), workload),
+            "timing": "the phase's launches as the replayed graph runs them, one CUDA event before the first and "
+                      "one after the last (timing mode 3, on the launching stream, timed region 3); per launch = "
+                      "phase time / launches, inter-launch gaps included",
+            "per_launch_direct": direct}
+
+
+def summarize(m, W, H, C, precision, steps, hbm_peak, world=1):
+    """Per-frame figures of measure_context's record."""
+    fw3, bw3 = m["phases_graph"]
+    fwd_ms = per_frame(sum(m["forward_ms"]), steps, world)
+    fb_ms = per_frame(sum(m["fwd_bwd_ms"]), steps, world)
+    fbr_ms = per_frame(sum(m["fwd_bwd_recompute_ms"]), steps, world)
+    frame_bytes = sum(v[1] for v in fw3.values()) / steps
+    bwd_bytes = sum(v[1] for v in bw3.values()) / steps
+    sum_bytes = fw3.get("fluence_sum", [0.0, 0.0, 0, 0])[1] / steps
+    fb_bytes = frame_bytes + bwd_bytes
+    fbr_bytes = fb_bytes + frame_bytes - sum_bytes
+    paper = paper_schedule_bytes(W, H, C, precision)
+    sb = survey_backward_bytes(W, H, C, precision, False)
+    sbr = survey_backward_bytes(W, H, C, precision, True)
+    gbps = lambda b, ms: b / (ms * 1e-3) / 1e9
+    return {
+        "forward_ms": fwd_ms, "fwd_bwd_ms": fb_ms, "fwd_bwd_recompute_ms": fbr_ms,
+        "frame": {"algorithmic_bytes": frame_bytes, "GBps": gbps(frame_bytes, fwd_ms),
+                  "frac_of_peak": gbps(frame_bytes, fwd_ms) / hbm_peak,
+                  "paper_schedule_bytes": paper, "paper_schedule_frac": gbps(paper, fwd_ms) / hbm_peak},
+        "fwd_bwd": {"ms": fb_ms, "algorithmic_bytes": fb_bytes, "GBps": gbps(fb_bytes, fb_ms),
+                    "frac_of_peak": gbps(fb_bytes, fb_ms) / hbm_peak,
+                    "survey_schedule_bytes": paper + sb, "survey_schedule_frac": gbps(paper + sb, fb_ms) / hbm_peak,
+                    "backward": "reads the levels the forward left in the context"},
+        "fwd_bwd_recompute": {"ms": fbr_ms, "algorithmic_bytes": fbr_bytes, "GBps": gbps(fbr_bytes, fbr_ms),
+                              "frac_of_peak": gbps(fbr_bytes, fbr_ms) / hbm_peak,
+                              "survey_schedule_bytes": paper + sbr,
+                              "survey_schedule_frac": gbps(paper + sbr, fbr_ms) / hbm_peak,
+                              "backward": "recomputes every level from the inputs first"},
+    }
+
+
+def bench_size(name, precision, timed, steps, hbm_peak):
+    """Another workload size (512^2 or 2048^2) in its own autotuned context."""
+    import torch
+    from paper_2505_02041_gb300 import HRC, scenes
+    e_np, s_np = scenes.scene_by_name(name)
+    C, H, W = e_np.shape
+    dev = torch.device("cuda", torch.cuda.current_device())
+    e = torch.from_numpy(e_np).to(dev)
+    s = torch.from_numpy(s_np).to(dev)
+    h = HRC(W, H, C, 0, precision)
+    tuned = h.autotune()
+    m = measure_context(h, e, s, timed, steps, hbm_peak)
+    out = {"workload": f"{name}: {WORKLOADS[name]}", "launch_config": h.launch_config, "autotune_best_ms": tuned,
+           "launches": m["launches"]}
+    out.update(summarize(m, W, H, C, precision, steps, hbm_peak))
+    out["roofline"] = roofline_of(m["phases_graph"][0], m["phases_direct"][0], steps, hbm_peak, name, h.launch_config)
+    out["phases"] = phase_table(m["phases_graph"][0], steps, hbm_peak)
+    out["backward_phases"] = phase_table(m["phases_graph"][1], steps, hbm_peak)
+    if name in PAPER_MS:
+        out["paper_table1_ms"] = PAPER_MS[name]
+    h.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -414,11 +623,8 @@ def run_ours(args):
         _lib.hrc_set_timing(h.ctx, False)
         print(json.dumps({"profile_once": args.workload, "launches_fwd_bwd": h.launch_count()}))
         return
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    gF = torch.ones((C, H, W), dtype=torch.float32, device=dev)
-    gE = torch.empty_like(e)
-    gS = torch.empty_like(s)
+    timed = Timer(dev)
+    hbm_peak, peak_kind = peaks()
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -426,82 +632,21 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    def fwd():
-        h.forward(e, s, F)
-
-    def fwd_bwd():
-        h.forward(e, s, F)
-        _lib.hrc_fluence_backward(h.ctx, gF, gE, gS)
-
-    def timed(step, n, per_kind=None):
-        """n steps, L2 flushed before each, CUDA events on the launching
-        stream around each step; returns per-step ms."""
-        out = []
-        for _ in range(n):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            step()
-            b.record(stream)
-            b.synchronize()
-            out.append(a.elapsed_time(b))
-            if per_kind is not None:
-                for kind, level, ms, by in _lib.hrc_get_timing(h.ctx):
-                    d = per_kind.setdefault(kind, [0.0, 0.0, 0])
-                    d[0] += ms
-                    d[1] += by
-                    d[2] += 1
-        return out
-
     for _ in range(max(args.warmup, 3)):
-        fwd_bwd()
-    fwd()
-    fwd_launches = h.launch_count()
-    fwd_bwd()
-    bwd_launches = h.launch_count()
-
-    # timed region 1: forward frames, graph-launched (the headline value)
+        h.forward(e, s, F)
+    # timed regions 1 (forward frames, graph-replayed: the headline value),
+    # 2 (forward + backward, both strategies) and 3 (the same frames with
+    # phase and launch timing), nvidia-smi sampling the clocks throughout
     clocks = Clocks(local)
     barrier()
     clocks.start()
-    step_ms = timed(fwd, args.steps)
-    barrier()
-    # timed region 2: forward + backward
-    fb_ms = timed(fwd_bwd, args.steps)
-    barrier()
-    # timed region 2b: forward + backward that recomputes every level
-    _lib.hrc_set_backward_recompute(h.ctx, 1)
-    fwd_bwd()
-    fwd_bwd()
-    rc_launches = h.launch_count()
-    barrier()
-    fbr_ms = timed(fwd_bwd, args.steps)
-    barrier()
-    _lib.hrc_set_backward_recompute(h.ctx, 0)
-    fwd_bwd()
-    # timed region 3: the same frames with per-launch CUDA events (kernel
-    # durations for the roofline; launches are not graph-replayed here)
-    _lib.hrc_set_timing(h.ctx, True)
-    per_kind = {}
-    prof_ms = timed(fwd, args.steps, per_kind)
-    bwd_kind = {}
-    h.forward(e, s, F)
-    for _ in range(args.steps):
-        flush.zero_()
-        _lib.hrc_fluence_backward(h.ctx, gF, gE, gS)
-        for kind, level, ms, by in _lib.hrc_get_timing(h.ctx):
-            d = bwd_kind.setdefault(kind, [0.0, 0.0, 0])
-            d[0] += ms
-            d[1] += by
-            d[2] += 1
-    _lib.hrc_set_timing(h.ctx, False)
+    m = measure_context(h, e, s, timed, args.steps, hbm_peak)
     barrier()
     clk = clocks.stop()
-    total_ms, fb_total, fbr_total = aggregate_max([sum(step_ms), sum(fb_ms), sum(fbr_ms)], world, dev)
+    F, gF, gE, gS = m["gbufs"]
+    total_ms, fb_total, fbr_total = aggregate_max([sum(m["forward_ms"]), sum(m["fwd_bwd_ms"]),
+                                                   sum(m["fwd_bwd_recompute_ms"])], world, dev)
     ms_per_frame = per_frame(total_ms, args.steps, world)
-    fb_mean = per_frame(fb_total, args.steps, world)
-    fbr_mean = per_frame(fbr_total, args.steps, world)
 
     # end to end: host buffers through the C ABI, copies included
     e_h = torch.from_numpy(e_np).pin_memory()
@@ -520,18 +665,11 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
-    hbm_peak, peak_kind = peaks()
-    kind, (kms, kbytes, kcount) = max(per_kind.items(), key=lambda kv: kv[1][0])
-    achieved = (kbytes / kcount) / ((kms / kcount) * 1e-3) / 1e9
-    phases = {k: {"ms_per_frame": v[0] / args.steps, "launches_per_frame": v[2] / args.steps,
-                  "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None}
-              for k, v in sorted(per_kind.items())}
-    frame_bytes = sum(v[1] for v in per_kind.values()) / args.steps
-    bwd_bytes = sum(v[1] for v in bwd_kind.values()) / args.steps
-    fb_bytes = frame_bytes + bwd_bytes
-    paper_bytes = paper_schedule_bytes(W, H, C, args.precision)
-    sum_bytes = per_kind.get("fluence_sum", [0.0, 0.0, 0])[1] / args.steps
-    fbr_bytes = fb_bytes + frame_bytes - sum_bytes   # the recompute repeats the forward but the sum
+    fw3, bw3 = m["phases_graph"]
+    fw1, bw1 = m["phases_direct"]
+    summ = summarize(m, W, H, C, args.precision, args.steps, hbm_peak, world)
+    summ["fwd_bwd"]["ms"] = per_frame(fb_total, args.steps, world)
+    summ["fwd_bwd_recompute"]["ms"] = per_frame(fbr_total, args.steps, world)
     line = {
         "metric": METRIC, "value": ms_per_frame, "unit": "ms/frame", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
@@ -546,39 +684,30 @@ def run_ours(args):
                    "autotune_best_ms": tuned_ms,
                    "launch_config": h.launch_config,
                    "baseline_context": "paper Table 1 on an RTX 3080 Laptop with fp16 storage"},
-        "roofline": {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                     "traffic": ncu_traffic(traffic_key(kind, h.launch_config), args.workload),
-                     "timing": "per-launch CUDA events on the launching stream (timed region 3)"},
-        "frame": {"algorithmic_bytes": frame_bytes, "GBps": frame_bytes / (ms_per_frame * 1e-3) / 1e9,
-                  "frac_of_peak": frame_bytes / (ms_per_frame * 1e-3) / 1e9 / hbm_peak,
-                  "ms_with_per_launch_events": statistics.mean(prof_ms),
-                  "paper_schedule_bytes": paper_bytes,
-                  "paper_schedule_frac": paper_bytes / (ms_per_frame * 1e-3) / 1e9 / hbm_peak,
-                  "note": "algorithmic_bytes: this implementation's schedule (live entries only, R_0 and the "
-                          "fluence sum fused); paper_schedule_bytes: every level materialised and re-read "
-                          "once per consuming phase (Sec. 4.3.2), whose time at the measured peak is the "
-                          "roofline the frame is also compared with"},
-        "phases": phases,
-        "fwd_bwd": {"ms": fb_mean, "algorithmic_bytes": fb_bytes,
-                    "GBps": fb_bytes / (fb_mean * 1e-3) / 1e9,
-                    "frac_of_peak": fb_bytes / (fb_mean * 1e-3) / 1e9 / hbm_peak,
-                    "backward_phases": {k: {"ms_per_frame": v[0] / args.steps, "launches_per_frame": v[2] / args.steps,
-                                            "GBps": v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else None}
-                                        for k, v in sorted(bwd_kind.items())},
-                    "backward": "reads the levels the forward left in the context"},
-        "fwd_bwd_recompute": {"ms": fbr_mean, "algorithmic_bytes": fbr_bytes,
-                              "GBps": fbr_bytes / (fbr_mean * 1e-3) / 1e9,
-                              "frac_of_peak": fbr_bytes / (fbr_mean * 1e-3) / 1e9 / hbm_peak,
-                              "backward": "recomputes every level from the inputs first (hrc_set_backward_recompute)"},
+        "roofline": roofline_of(fw3, fw1, args.steps, hbm_peak, args.workload, h.launch_config),
+        "frame": dict(summ["frame"],
+                      note="algorithmic_bytes: this implementation's schedule (live entries only, R_0 and the "
+                           "fluence sum fused); paper_schedule_bytes: every level materialised and re-read once per "
+                           "consuming phase (Sec. 4.3.2), whose time at the measured peak is the roofline the frame "
+                           "is also compared with"),
+        "phases": phase_table(fw3, args.steps, hbm_peak),
+        "phases_direct": phase_table(fw1, args.steps, hbm_peak),
+        "fwd_bwd": dict(summ["fwd_bwd"], backward_phases=phase_table(bw3, args.steps, hbm_peak)),
+        "fwd_bwd_recompute": summ["fwd_bwd_recompute"],
         "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": (C + 1) * H * W * 4,
                 "d2h_bytes_per_step": C * H * W * 4},
-        "gpu_launches": fwd_launches * args.steps,
-        "launches_per_step": {"forward": fwd_launches, "backward": bwd_launches,
-                              "backward_recompute": rc_launches,
-                              "note": "gpu_launches counts the forward frames timed for value"},
+        "gpu_launches": m["launches"]["forward"] * args.steps,
+        "launches_per_step": dict(m["launches"], note="gpu_launches counts the forward frames timed for value"),
         "clocks": clk,
     }
+    if world == 1 and args.sizes:
+        line["sizes"] = {nm: bench_size(nm, args.precision, timed, 10, hbm_peak) for nm in ("fog512", "fog2048")}
+    fwd = lambda: h.forward(e, s, F)
+
+    def fwd_bwd():
+        h.forward(e, s, F)
+        _lib.hrc_fluence_backward(h.ctx, gF, gE, gS)
+
     line["cross_blur"] = bench_cross_blur(h, fwd, fwd_bwd, timed, gF, gE, gS, hbm_peak)
     line["multi_bounce"] = bench_bounces(h, e, s, timed, hbm_peak)
     line["environment"] = bench_environment(h, fwd, fwd_bwd, timed)
@@ -593,18 +722,30 @@ def run_ours(args):
             Fp = torch.empty((C, H, W), dtype=torch.float32, device=dev)
             for _ in range(3):
                 hp.forward(e, s, Fp)
-            ms = timed(lambda: hp.forward(e, s, Fp), args.steps)
+            ms = statistics.mean(timed(lambda: hp.forward(e, s, Fp), args.steps))
+            _lib.hrc_set_timing(hp.ctx, 3)
+            per = {}
+            hp.forward(e, s, Fp)
+            timed(lambda: hp.forward(e, s, Fp), 5, hp, per)
+            _lib.hrc_set_timing(hp.ctx, 0)
+            by = sum(v[1] for v in per.values()) / 5
             Fn = Fp.cpu().numpy().astype(np.float64)
             lit = np.abs(Fr) >= 1e-3 * np.max(np.abs(Fr))   # pixels with non-negligible fluence
-            rows[prec] = {"ms_per_frame": statistics.mean(ms),
+            rows[prec] = {"ms_per_frame": ms, "algorithmic_bytes": by, "GBps": by / (ms * 1e-3) / 1e9,
+                          "frac_of_peak": by / (ms * 1e-3) / 1e9 / hbm_peak,
+                          "paper_schedule_bytes": paper_schedule_bytes(W, H, C, prec),
+                          "launch_config": hp.launch_config,
+                          "phases": phase_table(per, 5, hbm_peak),
                           "err_max": float(np.max(np.abs(Fn - Fr)) / np.max(np.abs(Fr))),
                           "rel_l2": float(np.linalg.norm(Fn - Fr) / np.linalg.norm(Fr)),
                           "pixel_rel_max": float(np.max(np.abs(Fn - Fr)[lit] / np.abs(Fr)[lit])),
                           "pixel_rel_mean": float(np.mean(np.abs(Fn - Fr)[lit] / np.abs(Fr)[lit]))}
             hp.close()
+        rows["speedup_vs_fp32"] = {p: rows["fp32"]["ms_per_frame"] / rows[p]["ms_per_frame"] for p in ("fp16", "bf16")}
         line["precisions"] = rows
     if args.batched and world == 1:
-        del h, e, s, F, gF, gE, gS, flush
+        h.close()
+        del h, e, s, F, gF, gE, gS, m
         torch.cuda.empty_cache()
         line["batched"] = bench_batched(args, dev)
     if world == 1 and not args.no_cpu_baseline:
@@ -618,32 +759,20 @@ def bench_batched(args, dev):
     """64 scenes of sizes drawn from {128, 256, 512, 1024, 2048}^2 (seed 4),
     C = 3, fog / disks / rectangles as the 512^2 workload (seeds 400+i),
     bf16 interval storage: forward and forward+backward of the whole batch,
-    each pass one graph-replayed launch sequence: the tile steps of all
-    scenes as ordinary launches around one persistent launch of the merge
-    cascade."""
+    each pass one graph-replayed launch sequence.  Beside it, the same 64
+    scenes as a loop of single-scene hrc_fluence (+ hrc_fluence_backward)
+    calls in the same precision: one autotuned context per size, each
+    scene's inputs copied into that context's fixed buffers (so that its
+    graph is replayed) and its outputs copied out, every copy inside the
+    timed region."""
     import torch
-    from paper_2505_02041_gb300 import BatchedHRC, scenes
+    from paper_2505_02041_gb300 import BatchedHRC, HRC, _lib, scenes
     sizes = scenes.batched_sizes(64, 4)
     es, ss = [], []
     for i, X in enumerate(sizes):
         e, s = scenes.scene_disks_rects_fog(X, X, 3, 400 + i)
         es.append(torch.from_numpy(e))
         ss.append(torch.from_numpy(s))
-    try:
-        b = BatchedHRC([(X, X) for X in sizes], 3, 0, "bf16")
-    except Exception as ex:   # the batch needs about 200 GB of device memory
-        return {"unavailable": f"batched context: {ex}"}
-    e, s = b.pack(es, ss)
-    del es, ss
-    F = torch.empty_like(e)
-    gF = torch.ones_like(e)
-    ge = torch.empty_like(e)
-    gs = torch.empty_like(s)
-    tune = b.autotune(e, s, reps=2)
-    best = min(tune, key=tune.get)
-    b.forward(e, s, F)
-    b.backward(gF, ge, gs)
-    b.sync()
     n = max(3, min(args.steps, 5))
     stream = torch.cuda.current_stream(dev)
 
@@ -659,7 +788,58 @@ def bench_batched(args, dev):
             ts.append(a.elapsed_time(z))
         return statistics.mean(ts)
 
-    from paper_2505_02041_gb300 import _lib
+    # the loop of single-scene calls
+    ed = [t.to(dev) for t in es]
+    sd = [t.to(dev) for t in ss]
+    Fd = [torch.empty_like(t) for t in ed]
+    ged = [torch.empty_like(t) for t in ed]
+    gsd = [torch.empty_like(t) for t in sd]
+    ctxs, bufs = {}, {}
+    for X in sorted(set(sizes)):
+        hx = HRC(X, X, 3, 0, "bf16")
+        hx.autotune()
+        ctxs[X] = hx
+        bufs[X] = [torch.empty((3, X, X), device=dev), torch.empty((X, X), device=dev),
+                   torch.empty((3, X, X), device=dev), torch.ones((3, X, X), device=dev),
+                   torch.empty((3, X, X), device=dev), torch.empty((X, X), device=dev)]
+
+    def loop(backward):
+        for i, X in enumerate(sizes):
+            eb, sb, Fb, gFb, geb, gsb = bufs[X]
+            eb.copy_(ed[i])
+            sb.copy_(sd[i])
+            ctxs[X].forward(eb, sb, Fb)
+            Fd[i].copy_(Fb)
+            if backward:
+                _lib.hrc_fluence_backward(ctxs[X].ctx, gFb, geb, gsb)
+                ged[i].copy_(geb)
+                gsd[i].copy_(gsb)
+
+    loop(True)
+    loop(True)
+    torch.cuda.synchronize(dev)
+    loop_fwd_ms = run(lambda: loop(False))
+    loop_fb_ms = run(lambda: loop(True))
+    for hx in ctxs.values():
+        hx.close()
+    del ctxs, bufs, ed, sd, Fd, ged, gsd
+    torch.cuda.empty_cache()
+
+    try:
+        b = BatchedHRC([(X, X) for X in sizes], 3, 0, "bf16")
+    except Exception as ex:   # the batch needs about 200 GB of device memory
+        return {"unavailable": f"batched context: {ex}", "loop_forward_ms": loop_fwd_ms, "loop_fwd_bwd_ms": loop_fb_ms}
+    e, s = b.pack(es, ss)
+    del es, ss
+    F = torch.empty_like(e)
+    gF = torch.ones_like(e)
+    ge = torch.empty_like(e)
+    gs = torch.empty_like(s)
+    tune = b.autotune(e, s, reps=2)
+    best = min(tune, key=tune.get)
+    b.forward(e, s, F)
+    b.backward(gF, ge, gs)
+    b.sync()
     fwd_ms = run(lambda: b.forward(e, s, F))
     n_fwd = _lib.hrc_last_launch_count(b.ctx)
     fb_ms = run(lambda: (b.forward(e, s, F), b.backward(gF, ge, gs)))
@@ -669,6 +849,8 @@ def bench_batched(args, dev):
     out = {"scenes": len(sizes), "sizes": dict(Counter(sizes)), "channels": 3, "precision": "bf16",
            "forward_ms": fwd_ms, "forward_scenes_per_s": len(sizes) / (fwd_ms * 1e-3),
            "fwd_bwd_ms": fb_ms, "fwd_bwd_scenes_per_s": len(sizes) / (fb_ms * 1e-3),
+           "loop_forward_ms": loop_fwd_ms, "loop_fwd_bwd_ms": loop_fb_ms,
+           "speedup_vs_loop": {"forward": loop_fwd_ms / fwd_ms, "fwd_bwd": loop_fb_ms / fb_ms},
            "launches_per_pass": {"forward": n_fwd, "backward": n_bwd},
            "schedule": ("persistent: trace / adjoint trace of all scenes as tile launches, the merge cascade "
                         "of all scenes in one persistent launch" if best[0] == 0 else
@@ -693,6 +875,8 @@ def main():
     ap.add_argument("--schedule", type=int, default=-1, help="launch schedule (default: the library's)")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64-scene batched persistent-launch measurement")
+    ap.add_argument("--no-sizes", dest="sizes", action="store_false",
+                    help="skip the 512^2 and 2048^2 workloads")
     ap.add_argument("--profile-config", type=int, nargs=5, default=[0, 1, 128, 1, 0],
                     metavar=("SCHEDULE", "GROUPS", "THREADS", "VMAJOR", "MDOWN"),
                     help="launch configuration of --profile-once (default: the autotuner's usual pick at 1024^2)")

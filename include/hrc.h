@@ -428,8 +428,11 @@ int hrc_last_launch_count(const hrc_ctx *ctx);
  * launches the kernels directly (no graph; each record then also holds
  * that launch's host-side launch latency), enable = 2 captures the pass
  * into a CUDA graph whose event-record nodes bracket each kernel, and
- * replays it (the kernels timed as the graphs of normal operation run
- * them), 0 switches timing off.
+ * replays it, enable = 3 does the same with one record per phase (the
+ * consecutive launches of one kind, with no event node between them: the
+ * phase timed as the graphs of normal operation run it; `level` is then
+ * the phase's first level and `launches` its launch count), 0 switches
+ * timing off.
  * hrc_get_timing synchronises the stream and fills up to `cap` records of
  * the last compute call; it returns the number of records (or -1 on error).
  * `kind`: 0 trace T_0..T_2, 1 merge up, 2 merge down, 3 fluence sum,
@@ -438,7 +441,7 @@ int hrc_last_launch_count(const hrc_ctx *ctx);
  * 12 bounce source update, 13 its adjoint.  `bytes` is the launch's
  * algorithmic traffic (each array it consumes read once, each array it
  * produces written once). */
-typedef struct { int kind; int level; float ms; double bytes; } hrc_kernel_time;
+typedef struct { int kind; int level; float ms; double bytes; int launches; } hrc_kernel_time;
 hrc_status hrc_set_timing(hrc_ctx *ctx, int enable);
 int hrc_get_timing(hrc_ctx *ctx, hrc_kernel_time *out, int cap);
 

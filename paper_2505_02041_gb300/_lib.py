@@ -316,7 +316,7 @@ def hrc_last_launch_count(ctx) -> int:
 
 
 class hrc_kernel_time(ctypes.Structure):
-    _fields_ = [("kind", _i), ("level", _i), ("ms", ctypes.c_float), ("bytes", ctypes.c_double)]
+    _fields_ = [("kind", _i), ("level", _i), ("ms", ctypes.c_float), ("bytes", ctypes.c_double), ("launches", _i)]
 
 
 KERNEL_KINDS = ["trace012", "merge_up", "merge_down", "fluence_sum", "adj_sum", "adj_merge_down",
@@ -331,12 +331,13 @@ def hrc_set_timing(ctx, enable):
 
 
 def hrc_get_timing(ctx, cap: int = 512):
-    """List of (kind name, level, ms, algorithmic bytes) of the last call."""
+    """List of (kind name, level, ms, algorithmic bytes, launches) of the last
+    call (launches > 1 only for the phase records of timing mode 3)."""
     arr = (hrc_kernel_time * cap)()
     n = load().hrc_get_timing(ctx, ctypes.cast(arr, _vp), cap)
     if n < 0:
         raise HRCError(HRC_ECUDA, "hrc_get_timing failed")
-    return [(KERNEL_KINDS[arr[i].kind], arr[i].level, arr[i].ms, arr[i].bytes) for i in range(n)]
+    return [(KERNEL_KINDS[arr[i].kind], arr[i].level, arr[i].ms, arr[i].bytes, arr[i].launches) for i in range(n)]
 
 
 def hrc_last_error(ctx=None) -> str:

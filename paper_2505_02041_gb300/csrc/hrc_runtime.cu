@@ -226,14 +226,14 @@ struct hrc_ctx {
     static constexpr int kStagePlanes = 7;   // e, sigma, albedo, F / dL/dF, dL/de, dL/dsigma, dL/dalbedo
     int launches = 0;
     Recorder rec;
-    int timing_mode = 0;         // 0 off, 1 direct launches with events, 2 events inside the graphs
+    int timing_mode = 0;         // 0 off, 1 direct launches with events, 2 / 3 events inside the graphs
     std::string err;
     // CUDA graphs of whole passes, keyed by pass kind, precision, schedule
     // and the caller's pointers; captured on a context-owned stream and
     // replayed on the caller's stream.
     struct GraphEntry {
         int kind = -1, prec = -1, sched = -1, mgroups = -1, tune = -1;
-        bool timed = false;                  // captured with event-record nodes (timing mode 2)
+        int timed = 0;                       // captured with event-record nodes: the timing mode (2 or 3)
         std::vector<Recorder::Rec> recs;     // those nodes' events
         const void *p[8] = {};
         cudaGraphExec_t exec = nullptr;
@@ -337,10 +337,12 @@ hrc_status run_pass(hrc_ctx *ctx, int kind, const void *p0, const void *p1, cons
 template <class ENQ>
 hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue, const char *where) {
     ctx->launches = 0;
-    if ((ctx->rec.on && ctx->timing_mode != 2) || !ctx->use_graphs) {
+    if ((ctx->rec.on && ctx->timing_mode == 1) || !ctx->use_graphs) {
         ctx->rec.ext = false;
+        ctx->rec.coarse = false;
         ctx->rec.reset(ctx->stream);
         cudaError_t e = enqueue(ctx->stream, &ctx->launches, &ctx->rec);
+        ctx->rec.finish();
         if (e != cudaSuccess) return cuda_fail(ctx, e, where);
         return HRC_OK;
     }
@@ -348,7 +350,7 @@ hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue
     const void *const *key = pk.p;
     for (auto &g : ctx->graphs) {
         if (g.exec && g.kind == kind && g.prec == ctx->prec && g.sched == ctx->sched && g.mgroups == ctx->mgroups &&
-            g.tune == ctx->mthreads * 8 + ctx->vmajor * 4 + ctx->mdown && g.timed == timed &&
+            g.tune == ctx->mthreads * 8 + ctx->vmajor * 4 + ctx->mdown && g.timed == (timed ? ctx->timing_mode : 0) &&
             std::memcmp(g.p, key, sizeof(pk.p)) == 0) {
             cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(ctx, e, where);
@@ -361,6 +363,8 @@ hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue
     Recorder *rr = &off;
     if (timed) {   // fresh events from the pool for this graph's record nodes
         ctx->rec.ext = true;
+        ctx->rec.coarse = ctx->timing_mode == 3;
+        ctx->rec.open = false;
         ctx->rec.st = ctx->cap_stream;
         ctx->rec.recs.clear();
         rr = &ctx->rec;
@@ -370,6 +374,7 @@ hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue
     cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, where);
     cudaError_t e1 = enqueue(ctx->cap_stream, &n, rr);
+    rr->finish();
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
     ctx->rec.ext = false;
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
@@ -390,7 +395,7 @@ hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue
     slot.sched = ctx->sched;
     slot.mgroups = ctx->mgroups;
     slot.tune = ctx->mthreads * 8 + ctx->vmajor * 4 + ctx->mdown;
-    slot.timed = timed;
+    slot.timed = timed ? ctx->timing_mode : 0;
     slot.recs = timed ? ctx->rec.recs : std::vector<Recorder::Rec>();
     std::memcpy(slot.p, key, sizeof(pk.p));
     slot.launches = n;
@@ -491,7 +496,7 @@ long long hrc_graph_captures(const hrc_ctx *ctx) {
 
 hrc_status hrc_set_timing(hrc_ctx *ctx, int enable) {
     if (!ctx) return HRC_EINVAL;
-    if (enable < 0 || enable > 2) return fail(ctx, HRC_EINVAL, "hrc_set_timing: 0, 1 or 2");
+    if (enable < 0 || enable > 3) return fail(ctx, HRC_EINVAL, "hrc_set_timing: 0, 1, 2 or 3");
     ctx->rec.on = enable != 0;
     ctx->timing_mode = enable;
     for (hrc_ctx *k : ctx->chan) hrc_set_timing(k, enable);
@@ -515,7 +520,7 @@ int hrc_get_timing(hrc_ctx *ctx, hrc_kernel_time *out, int cap) {
         if (n >= cap) break;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return -1;
-        if (out) out[n] = hrc_kernel_time{r.kind, r.level, ms, r.bytes};
+        if (out) out[n] = hrc_kernel_time{r.kind, r.level, ms, r.bytes, r.launches};
         ++n;
     }
     return n;

@@ -22,15 +22,20 @@ enum KernelKind {
 // `ext` the records are made while a graph is being captured: they become
 // event-record nodes of the graph (cudaEventRecordExternal), so every replay
 // times the kernels as the graph runs them.
+// With `coarse`, consecutive launches of one kind form one record (a phase:
+// one event before its first launch, one after its last), so that no event
+// sits between the launches of a phase.
 struct Recorder {
-    struct Rec { int kind, level; double bytes; cudaEvent_t a, b; };
+    struct Rec { int kind, level; double bytes; cudaEvent_t a, b; int launches; };
     bool on = false;
     bool ext = false;
+    bool coarse = false;
+    bool open = false;
     cudaStream_t st = nullptr;
     std::vector<cudaEvent_t> pool;
     std::vector<Rec> recs;
     size_t used = 0;
-    void reset(cudaStream_t s) { st = s; recs.clear(); used = 0; }
+    void reset(cudaStream_t s) { st = s; recs.clear(); used = 0; open = false; }
     cudaEvent_t next() {
         if (used == pool.size()) {
             cudaEvent_t e;
@@ -45,13 +50,28 @@ struct Recorder {
     }
     void begin(int kind, int level, double bytes) {
         if (!on) return;
-        Rec r{kind, level, bytes, next(), next()};
+        if (coarse && open) {
+            if (recs.back().kind == kind) {   // the phase continues
+                recs.back().bytes += bytes;
+                ++recs.back().launches;
+                return;
+            }
+            finish();
+        }
+        Rec r{kind, level, bytes, next(), next(), 1};
         record(r.a);
         recs.push_back(r);
+        open = coarse;
     }
     void end() {
-        if (!on || recs.empty()) return;
+        if (!on || recs.empty() || coarse) return;
         record(recs.back().b);
+    }
+    // closes the open phase (coarse records); called at the end of a pass
+    void finish() {
+        if (!on || !open || recs.empty()) return;
+        record(recs.back().b);
+        open = false;
     }
     ~Recorder() {
         for (auto e : pool) cudaEventDestroy(e);
