@@ -396,8 +396,11 @@ hrc_status hrc_batched_tune(hrc_ctx *ctx, int blocks_per_sm, int order);
  * ticket queue with bounded dependency waits; 1 = every scene's own
  * per-level launch sequence (as a single-scene pass), the scenes spread
  * largest first over 8 streams forked from and joined to the caller's
- * stream, so that kernels of different scenes overlap.  Results are
- * identical for both. */
+ * stream, so that kernels of different scenes overlap; 2 = level-major
+ * multi-scene launches: one launch per stage (each merge-up level, each
+ * merge-down level, the fluence sum; each adjoint level) covering every
+ * scene that has it, the tile steps as multi-scene tile launches.  Results
+ * are identical for all three. */
 hrc_status hrc_batched_schedule(hrc_ctx *ctx, int schedule);
 
 /* Test hook for the bounded waits: `withhold_counter` >= 0 makes that stage

@@ -356,7 +356,8 @@ class BatchedHRC:
 
     def tune(self, blocks_per_sm: int = 0, order: int = 0, schedule: int = 0):
         """schedule 0: persistent launch (blocks per SM, ticket order apply);
-        schedule 1: per-scene launch chains on parallel graph branches."""
+        schedule 1: per-scene launch chains on parallel graph branches;
+        schedule 2: level-major multi-scene launches."""
         _lib.hrc_batched_tune(self.ctx, blocks_per_sm, order)
         _lib.hrc_batched_schedule(self.ctx, schedule)
 
@@ -365,7 +366,7 @@ class BatchedHRC:
         inputs and keep the fastest; returns {candidate: ms}."""
         res = {}
         out = torch.empty_like(e_packed)
-        for cand in [(0, bpsm, order) for bpsm in (0, 1, 2) for order in (0, 1)] + [(1, 0, 0)]:
+        for cand in [(0, bpsm, order) for bpsm in (0, 1, 2) for order in (0, 1)] + [(1, 0, 0), (2, 0, 0)]:
             sched, bpsm, order = cand
             self.tune(bpsm, order, sched)
             self.forward(e_packed, s_packed, out)

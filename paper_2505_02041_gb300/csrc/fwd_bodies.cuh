@@ -341,19 +341,30 @@ __device__ __forceinline__ void body_merge_up4(const Plan &pl, const RowSplit &r
 #pragma unroll
         for (int l = 0; l < 4; ++l) out[l] = merge<P, C>(nr[l], fr[l]);
     } else {                                        // Eqs. 19-20
+        // the two merges one after the other: half the operands live at a
+        // time (the four-operand form needed ~95 registers, 5 blocks per SM)
         const int kp = (k + 1) >> 1, km = (k - 1) >> 1;
-        Iv<P, C> np[4], nm[4], fp[4], fm[4];
-        Tm.load4(xn, kp, v, np);
-        Tm.load4(xn, km, v, nm);
-        if (far_ok) {
-            Tm.load4_masked(xf, km, v + 2 * kp - sm, g.V, fp);
-            Tm.load4_masked(xf, kp, v + 2 * km - sm, g.V, fm);
-        } else {
+        Iv<P, C> mm[4];
+        {
+            Iv<P, C> nm[4], fm[4];
+            Tm.load4(xn, km, v, nm);
+            if (far_ok) Tm.load4_masked(xf, kp, v + 2 * km - sm, g.V, fm);
+            else
 #pragma unroll
-            for (int l = 0; l < 4; ++l) fp[l] = fm[l] = Iv<P, C>::vacuum();
+                for (int l = 0; l < 4; ++l) fm[l] = Iv<P, C>::vacuum();
+#pragma unroll
+            for (int l = 0; l < 4; ++l) mm[l] = merge<P, C>(nm[l], fm[l]);
         }
+        {
+            Iv<P, C> np[4], fp[4];
+            Tm.load4(xn, kp, v, np);
+            if (far_ok) Tm.load4_masked(xf, km, v + 2 * kp - sm, g.V, fp);
+            else
 #pragma unroll
-        for (int l = 0; l < 4; ++l) out[l] = blend<P, C>(merge<P, C>(nm[l], fm[l]), merge<P, C>(np[l], fp[l]));
+                for (int l = 0; l < 4; ++l) fp[l] = Iv<P, C>::vacuum();
+#pragma unroll
+            for (int l = 0; l < 4; ++l) out[l] = blend<P, C>(mm[l], merge<P, C>(np[l], fp[l]));
+        }
     }
     Tn.store4(x, k, v, out);
 }
@@ -568,6 +579,154 @@ __device__ __forceinline__ void body_merge_down(const Plan &pl, const RowSplit &
     }
 }
 
+// ---------------------------------------------------------------------------
+// Merge down (level n >= 1) with the block's rows staged in shared memory by
+// bulk copies.  One block of 128 threads = one row (q, x, ip) x kBV v (four
+// consecutive v per thread).  Thread 0 copies, for both edges of the cone
+// (Eq. 14 at odd x, Eqs. 15-17 at even x), the T planes of the edge's row,
+// the far R window (its start rounded down to 16 bytes, clipped to the
+// row) and, at even x, the near R row; every thread then reads only shared
+// memory.  Out-of-range far values (and R_N) are the environment's values
+// (0 without a map), chosen by a select; they are never read from the rows.
+// ---------------------------------------------------------------------------
+constexpr int kBV = 512;
+
+template <int P, int C> struct BulkMD {
+    using SL = typename Prec<P>::SL;
+    using ST = typename Prec<P>::ST;
+    static constexpr int AL = 16 / (int)sizeof(SL);   // elements per 16 bytes
+    static constexpr int FW = kBV + 16;                  // far window length
+    static constexpr size_t bytes() {
+        return sizeof(SL) * 2 * C * kBV + sizeof(ST) * 2 * kBV + sizeof(SL) * 2 * C * FW + sizeof(SL) * 2 * C * kBV;
+    }
+};
+
+template <int P, int C, bool ENV>
+__device__ __forceinline__ void body_merge_down_bulk(const Plan &pl, const RowSplit &rs, int n, long long row, int vb,
+                                                     unsigned char *smem, uint64_t &bar) {
+    using SL = typename Prec<P>::SL;
+    using ST = typename Prec<P>::ST;
+    using A = typename Prec<P>::A;
+    using B = BulkMD<P, C>;
+    int local;
+    const int q = find_quadrant(rs, row, local);
+    const QuadGeom &g = pl.q[q];
+    const int v0 = vb * kBV;
+    if (v0 >= g.V) return;                                   // uniform over the block
+    const int I = 1 << n;
+    local += I;
+    const int x = local >> n, ip = local & (I - 1);
+    const bool top = n + 1 >= g.N;                           // R_N: 0, or the environment map
+    const int s = 1 << n;
+    const bool odd = (x & 1) != 0;
+    const int x2 = x >> 1;
+    const int xt = odd ? x : x2;                             // T row: T_n(x, .) or T_{n+1}(x/2, .)
+    const int xq = odd ? (x + 1) >> 1 : x2 + 1;              // far column at level n+1
+    const bool far_ok = !top && xq < g.Un[n + 1];
+    const bool near_ok = !odd && !top;
+    int kk[2], j[2], off[2], fa[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        kk[e] = odd ? (e == 0 ? ip + 1 : ip) : (e == 0 ? 2 * ip + 2 : 2 * ip);
+        j[e] = e == 0 ? 2 * ip + 1 : 2 * ip;
+        off[e] = 2 * kk[e] - (odd ? s : 2 * s);
+        const int a = v0 + off[e];
+        fa[e] = a >= 0 ? a / B::AL * B::AL : -((-a + B::AL - 1) / B::AL) * B::AL;   // round down
+    }
+    SL *tl = reinterpret_cast<SL *>(smem);                   // [2][C][kBV]
+    ST *tt = reinterpret_cast<ST *>(tl + 2 * C * kBV);       // [2][kBV]
+    SL *rf = reinterpret_cast<SL *>(tt + 2 * kBV);           // [2][C][FW]
+    SL *rn = rf + 2 * C * B::FW;                             // [2][C][kBV]
+    const int vend = v0 + kBV < g.Vs ? v0 + kBV : g.Vs;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const TLevel<P, C> Tt(pl, q, odd ? n : n + 1);
+        const RLevel<P, C> R1(pl, q, top ? n : n + 1);
+        const unsigned tb = (unsigned)(vend - v0);
+        unsigned total = 2u * tb * (unsigned)(C * sizeof(SL) + sizeof(ST));
+        int fs[2], fe[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            fs[e] = fa[e] > 0 ? fa[e] : 0;
+            fe[e] = fa[e] + B::FW < g.Vs ? fa[e] + B::FW : g.Vs;
+            if (far_ok && fe[e] > fs[e]) total += (unsigned)(C * (fe[e] - fs[e]) * sizeof(SL));
+        }
+        if (near_ok) total += 2u * (unsigned)(C * tb * sizeof(SL));
+        mbar_arrive_expect(&bar, total + (unsigned)pl.bulk_extra_tx);
+        const uint64_t pol = l2_evict_first();               // T rows: read once from HBM
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const char *gr = Tt.row(xt, kk[e]);
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                bulk_load_hint(tl + (e * C + c) * kBV, reinterpret_cast<const SL *>(gr) + (long long)c * g.Vs + v0,
+                               tb * sizeof(SL), &bar, pol);
+            bulk_load_hint(tt + e * kBV, reinterpret_cast<const ST *>(gr + (long long)C * g.Vs * sizeof(SL)) + v0,
+                           tb * sizeof(ST), &bar, pol);
+            if (far_ok && fe[e] > fs[e])
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    bulk_load(rf + (e * C + c) * B::FW + (fs[e] - fa[e]), R1.base + R1.idx(xq, j[e], c, fs[e]),
+                              (unsigned)((fe[e] - fs[e]) * sizeof(SL)), &bar);
+            if (near_ok)
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    bulk_load(rn + (e * C + c) * kBV, R1.base + R1.idx(x2, j[e], c, v0), tb * sizeof(SL), &bar);
+        }
+    }
+    if (!mbar_wait(&bar, 0, pl.bulk_limit_ns)) {              // gave up: let the copies land, report, leave
+        const int code = mbar_wait(&bar, 0, drain_limit_ns(pl.bulk_limit_ns)) ? kWaitTimeout : kWaitLost;
+        if (threadIdx.x == 0) atomicMax(pl.status, code);
+        return;
+    }
+    const int v = v0 + 4 * (int)threadIdx.x;
+    if (v >= g.V) return;
+    const int ti = v - v0;
+    const A Ap = arc<P>(pl, n + 1, 2 * ip + 1), Am = arc<P>(pl, n + 1, 2 * ip);
+    A acc[4][C];
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[l][c] = A(0);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const A Aj = e == 0 ? Ap : Am;
+        A tr[4];
+        ld4(tt + e * kBV + ti, tr);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) tr[l] = Prec<P>::LOG ? fexp(-tr[l]) : tr[l];
+        const int fi = ti + (v0 + off[e] - fa[e]);           // far window index of v (even)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            A L[4], r[4], r0[4];
+            const A ev = renv<P, C, ENV>(pl, q, n + 1, j[e], c);   // out of range: the environment
+            ld4(tl + (e * C + c) * kBV + ti, L);
+            ld2(rf + (e * C + c) * B::FW + fi, r[0], r[1]);
+            ld2(rf + (e * C + c) * B::FW + fi + 2, r[2], r[3]);
+            if (near_ok) ld4(rn + (e * C + c) * kBV + ti, r0);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int vf = v + l + off[e];
+                const A rr = (far_ok && vf >= 0 && vf < g.V) ? r[l] : ev;
+                const A f = fma(Aj, L[l], tr[l] * rr);
+                if (odd) acc[l][c] += f;                                         // Eq. 14
+                else acc[l][c] += A(0.5) * ((near_ok ? r0[l] : ev) + f);         // Eqs. 15-17
+            }
+        }
+    }
+    const RLevel<P, C> Rn(pl, q, n);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const A o[4] = {acc[0][c], acc[1][c], acc[2][c], acc[3][c]};
+        Rn.store4(x, ip, c, v, o);
+    }
+}
+
+
 // F[c][y][x] = sum_q R_0^q(u_q + 1, v_q)   (Algorithm 1, Lighting, +1 offset),
 // with R_0 computed in place (merge_down_entry at n = 0): R_0 feeds only this
 // sum, so it is never stored.  One block per 32 x 32 image tile (any
@@ -600,30 +759,54 @@ __device__ __forceinline__ void body_fluence(const Plan &pl, OUT *__restrict__ F
 #pragma unroll
         for (int c = 0; c < C; ++c) a[c] += r[0][c];
     };
-    for (int cidx = warp; cidx < 32; cidx += nw) {         // q0, q1: lanes along y
-        const int x = x0 + cidx, y = y0 + lane;
-        A a[C];
+    // two columns per iteration (cidx and cidx + nw, of equal parity): their
+    // loads are independent, so a thread has twice as many in flight
+    for (int cidx = warp; cidx < 32; cidx += 2 * nw) {     // q0, q1: lanes along y
+        const int cb = cidx + nw, y = y0 + lane;
+        A a[C], b[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) a[c] = A(0);
-        if (x < W && y < H) {
-            add_r0(0, x, y, a);
-            add_r0(1, x, y, a);
+        for (int c = 0; c < C; ++c) a[c] = b[c] = A(0);
+        if (y < H) {
+            if (x0 + cidx < W) {
+                add_r0(0, x0 + cidx, y, a);
+                add_r0(1, x0 + cidx, y, a);
+            }
+            if (cb < 32 && x0 + cb < W) {
+                add_r0(0, x0 + cb, y, b);
+                add_r0(1, x0 + cb, y, b);
+            }
         }
 #pragma unroll
-        for (int c = 0; c < C; ++c) tile[c][lane][cidx] = a[c];
+        for (int c = 0; c < C; ++c) {
+            tile[c][lane][cidx] = a[c];
+            if (cb < 32) tile[c][lane][cb] = b[c];
+        }
     }
     __syncthreads();
     const long long HW = (long long)W * H;
-    for (int cidx = warp; cidx < 32; cidx += nw) {         // q2, q3: lanes along x
-        const int x = x0 + lane, y = y0 + cidx;
-        if (x >= W || y >= H) continue;
-        A a[C];
+    for (int cidx = warp; cidx < 32; cidx += 2 * nw) {     // q2, q3: lanes along x
+        const int cb = cidx + nw, x = x0 + lane;
+        if (x >= W) continue;
+        const bool ua = y0 + cidx < H, ub = cb < 32 && y0 + cb < H;
+        A a[C], b[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) a[c] = tile[c][cidx][lane];
-        add_r0(2, x, y, a);
-        add_r0(3, x, y, a);
+        for (int c = 0; c < C; ++c) {
+            a[c] = ua ? tile[c][cidx][lane] : A(0);
+            b[c] = ub ? tile[c][cb][lane] : A(0);
+        }
+        if (ua) {
+            add_r0(2, x, y0 + cidx, a);
+            add_r0(3, x, y0 + cidx, a);
+        }
+        if (ub) {
+            add_r0(2, x, y0 + cb, b);
+            add_r0(3, x, y0 + cb, b);
+        }
 #pragma unroll
-        for (int c = 0; c < C; ++c) F[c * HW + (long long)y * W + x] = (OUT)a[c];
+        for (int c = 0; c < C; ++c) {
+            if (ua) F[c * HW + (long long)(y0 + cidx) * W + x] = (OUT)a[c];
+            if (ub) F[c * HW + (long long)(y0 + cb) * W + x] = (OUT)b[c];
+        }
     }
 }
 

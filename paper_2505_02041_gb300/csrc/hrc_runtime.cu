@@ -262,6 +262,13 @@ struct hrc_ctx {
         double bytes = 0;
     };
     std::vector<TileLaunch> tiles[3];
+    // schedule 2: level-major multi-scene launches of each mode
+    struct MultiLaunch {
+        int kind = 0, level = 0, blocks = 0, nent = 0;
+        MultiEnt *d_ents = nullptr;
+        double bytes = 0;
+    };
+    std::vector<MultiLaunch> multi[3];
     int nblocks[3] = {0, 0, 0};
     long long total[3] = {0, 0, 0};
     double bbytes[3] = {0, 0, 0};
@@ -624,6 +631,7 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     for (int m = 0; m < 3; ++m) {
+        for (auto &ml : ctx->multi[m]) cudaFree(ml.d_ents);
         cudaFree(ctx->d_blocks[m]);
         cudaFree(ctx->d_chunk[m]);
         for (auto &t : ctx->tiles[m]) {
@@ -1548,6 +1556,27 @@ hrc_status build_batched_tables(hrc_ctx *ctx) {
         ctx->total[mode] = tick;
         ctx->ncounters[mode] = nc;
         ctx->bbytes[mode] = bytes;
+        // schedule 2: the same stages as level-major multi-scene launches
+        for (auto &ml : ctx->multi[mode]) cudaFree(ml.d_ents);
+        ctx->multi[mode].clear();
+        std::vector<MultiDesc> md;
+        multi_stages(ctx->bplans, mode, md);
+        for (const MultiDesc &d : md) {
+            hrc_ctx::MultiLaunch ml;
+            ml.kind = d.kind;
+            ml.level = d.level;
+            ml.blocks = d.blocks;
+            ml.nent = (int)d.ents.size();
+            ml.bytes = d.bytes;
+            e = cudaMalloc(&ml.d_ents, sizeof(MultiEnt) * d.ents.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(ml.d_ents, d.ents.data(), sizeof(MultiEnt) * d.ents.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(ml.d_ents);
+                return cuda_fail(ctx, e, "batched multi-scene tables");
+            }
+            ctx->multi[mode].push_back(ml);
+        }
     }
     return HRC_OK;
 }
@@ -1564,6 +1593,12 @@ hrc_status build_batched_plans(hrc_ctx *ctx, int prec) {
         ctx->bplans[i].mgroups = 1;
         ctx->bplans[i].mthreads = 128;
         ctx->bplans[i].vmajor = 0;
+        // per-scene chains (schedule 1): the launch configuration the
+        // single-scene autotuner picks at most sizes: four v per thread in the
+        // merge up, and bulk-copy staging of the merge down in the 16-bit
+        // precisions
+        ctx->bplans[i].mgroups = 4;
+        ctx->bplans[i].mdown = (prec == P_FP16 || prec == P_BF16) ? 1 : 0;
         ctx->bplans[i].status = ctx->d_status;
     }
     if (off > ctx->arena_bytes) return fail(ctx, HRC_ENOMEM, "batched layout exceeds the arena");
@@ -1609,9 +1644,63 @@ hrc_status run_batched_chains(hrc_ctx *ctx, int mode, const void *e, const void 
                     where);
 }
 
+// Schedule 2: the tile steps of every scene as multi-scene tile launches and
+// every other stage as one level-major multi-scene launch, in dependency
+// order (kernels_batched.cu, multi_stages).
+hrc_status run_batched_levels(hrc_ctx *ctx, int mode, const void *e, const void *s, void *F, const void *gF,
+                              void *ge, void *gs, const char *where) {
+    BatchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.plans = ctx->d_plans;
+    a.eoff = ctx->d_eoff;
+    a.soff = ctx->d_soff;
+    a.status = ctx->d_status;
+    a.e = e;
+    a.s = s;
+    a.F = F;
+    a.gF = gF;
+    a.ge = ge;
+    a.gs = gs;
+    const int prec = ctx->prec, C = ctx->C, nsc = ctx->nscenes;
+    const std::vector<hrc_ctx::TileLaunch> &tl = ctx->tiles[mode];
+    const std::vector<hrc_ctx::MultiLaunch> &ml = ctx->multi[mode];
+    auto enqueue = [&](cudaStream_t st, int *n, Recorder *r) {
+        cudaError_t err = cudaMemsetAsync(a.status, 0, sizeof(int), st);
+        auto tiles = [&](bool before) {
+            for (const auto &t : tl) {
+                if (t.before != before || err != cudaSuccess) continue;
+                r->begin(t.kind == BK_TRACE ? K_TRACE012 : K_ADJ_TRACE, t.pair, t.bytes);
+                err = launch_batched_tiles(a, prec, C, t.kind, t.d_off, t.d_nx, nsc, t.pair, t.total, st);
+                r->end();
+                ++*n;
+            }
+        };
+        tiles(true);
+        for (const auto &m : ml) {
+            if (err != cudaSuccess) break;
+            const int kk = m.kind == MK_MERGE_UP4 ? K_MERGE_UP
+                           : (m.kind == MK_MERGE_DOWN4 || m.kind == MK_MERGE_DOWN_BULK) ? K_MERGE_DOWN
+                           : m.kind == MK_SUM ? K_FLUENCE_SUM
+                           : m.kind == MK_ADJ_SUM ? K_ADJ_SUM
+                           : m.kind == MK_ADJ_MU ? K_ADJ_MERGE_UP : K_ADJ_MERGE_DOWN;
+            void *io = m.kind == MK_SUM ? F : (m.kind == MK_ADJ_SUM ? const_cast<void *>(gF) : nullptr);
+            r->begin(kk, m.level, m.bytes);
+            err = launch_multi(prec, C, m.kind, ctx->d_plans, m.d_ents, m.nent, m.level, m.blocks, ctx->d_eoff, io, st);
+            r->end();
+            ++*n;
+        }
+        if (err == cudaSuccess) tiles(false);
+        return err;
+    };
+    const void *k3 = (const void *)(intptr_t)(2 << 20);
+    return run_pass(ctx, 8 + mode, mode == 0 ? e : gF, mode == 0 ? s : ge, mode == 0 ? F : gs, k3, nullptr, enqueue,
+                    where);
+}
+
 hrc_status run_batched(hrc_ctx *ctx, int mode, const void *e, const void *s, void *F, const void *gF, void *ge,
                        void *gs, const char *where) {
     if (ctx->bsched == 1) return run_batched_chains(ctx, mode, e, s, F, gF, ge, gs, where);
+    if (ctx->bsched == 2) return run_batched_levels(ctx, mode, e, s, F, gF, ge, gs, where);
     BatchArgs a;
     a.plans = ctx->d_plans;
     a.eoff = ctx->d_eoff;
@@ -1804,7 +1893,7 @@ hrc_status hrc_batched_debug(hrc_ctx *ctx, int withhold_counter, long long spin_
 
 hrc_status hrc_batched_schedule(hrc_ctx *ctx, int schedule) {
     if (!ctx || !ctx->batched) return HRC_EINVAL;
-    if (schedule != 0 && schedule != 1) return fail(ctx, HRC_EINVAL, "hrc_batched_schedule: 0 or 1");
+    if (schedule < 0 || schedule > 2) return fail(ctx, HRC_EINVAL, "hrc_batched_schedule: 0, 1 or 2");
     ctx->bsched = schedule;
     return HRC_OK;
 }

@@ -23,6 +23,7 @@
 // an acquire load, fences, and the CTA synchronises before reading.  No SM
 // reads a buffer region before its producing stage completed (every stage
 // reads only levels of earlier stages), so no stale L1 line can be hit.
+#include <algorithm>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -179,6 +180,145 @@ __global__ void __launch_bounds__(256, 5) k_batched(BatchArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Level-major multi-scene launches: one stage of every scene per launch, so a
+// batch of many small scenes becomes a few large launches instead of a long
+// chain of small ones per scene.  Every block runs the standalone kernel's
+// body on its scene's plan (read from global memory).
+// ---------------------------------------------------------------------------
+int multi_threads(int kind) {
+    switch (kind) {
+    case MK_SUM: return 128;
+    case MK_ADJ_SUM: return 256;
+    case MK_ADJ_R1:
+    case MK_ADJ_T1: return 256;
+    default: return 128;
+    }
+}
+
+int multi_vblock(int kind) {
+    switch (kind) {
+    case MK_MERGE_UP4:
+    case MK_MERGE_DOWN4:
+    case MK_MERGE_DOWN_BULK: return 4 * 128;   // four v per thread
+    case MK_ADJ_R1:
+    case MK_ADJ_T1: return 256;            // one v per thread
+    default: return 2 * 128;               // a pair of v per thread
+    }
+}
+
+// The block's entry (binary search) and its scene's plan, copied into
+// shared memory: the bodies read the plan's fields in every address
+// computation, which then cost a shared-memory load instead of a global one.
+__device__ __forceinline__ const MultiEnt &multi_entry(const Plan *__restrict__ plans,
+                                                       const MultiEnt *__restrict__ ents, int nent, Plan &spl) {
+    __shared__ int ent_sh;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nent - 1;                    // last entry with first <= block
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ents[mid].first <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        ent_sh = lo;
+    }
+    __syncthreads();
+    const MultiEnt &m = ents[ent_sh];
+    static_assert(sizeof(Plan) % 4 == 0, "plan copied as 32-bit words");
+    const unsigned *src = reinterpret_cast<const unsigned *>(plans + m.scene);
+    unsigned *dst = reinterpret_cast<unsigned *>(&spl);
+    for (int i = threadIdx.x; i < (int)(sizeof(Plan) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    return m;
+}
+
+template <int P, int C, int KIND>
+__global__ void __launch_bounds__(256) k_multi(const Plan *__restrict__ plans, const MultiEnt *__restrict__ ents,
+                                               int nent, int n, const long long *__restrict__ eoff, void *io) {
+    using IN = typename std::conditional<P == P_FP64, double, float>::type;
+    __shared__ __align__(16) unsigned char smem[sizeof(typename Prec<P>::A) * C * 32 * 33];
+    __shared__ __align__(16) Plan spl;
+    const MultiEnt &m = multi_entry(plans, ents, nent, spl);
+    const Plan &pl = spl;
+    const int local = (int)blockIdx.x - m.first;
+    const int row = local / m.nvb, vb = local - row * m.nvb;
+    if constexpr (KIND == MK_MERGE_UP4) body_merge_up4<P, C>(pl, m.rs, n, row, vb);
+    else if constexpr (KIND == MK_MERGE_DOWN4) body_merge_down4<P, C, false>(pl, m.rs, n, row, vb);
+    else if constexpr (KIND == MK_SUM) body_fluence<P, C, IN, false>(pl, (IN *)io + eoff[m.scene], vb, row, smem);
+    else if constexpr (KIND == MK_ADJ_SUM) body_adj_sum<P, C, IN>(pl, (const IN *)io + eoff[m.scene], vb, row, smem);
+    else if constexpr (KIND == MK_ADJ_R2) body_adj_R<P, C, 2>(pl, m.rs, n, row, vb);
+    else if constexpr (KIND == MK_ADJ_R1) body_adj_R<P, C, 1>(pl, m.rs, n, row, vb);
+    else if constexpr (KIND == MK_ADJ_T2) body_adj_T<P, C, 2, false>(pl, m.rs, n, row, vb);
+    else if constexpr (KIND == MK_ADJ_T1) body_adj_T<P, C, 1, false>(pl, m.rs, n, row, vb);
+    else body_adj_merge_up<P, C, false>(pl, m.rs, n, row, vb);
+}
+
+// The merge down with the block's rows staged by bulk copies (the 16-bit
+// precisions' faster form).
+template <int P, int C>
+__global__ void __launch_bounds__(128) k_multi_bulk(const Plan *__restrict__ plans, const MultiEnt *__restrict__ ents,
+                                                    int nent, int n) {
+    extern __shared__ __align__(128) unsigned char dsmem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(16) Plan spl;
+    const MultiEnt &m = multi_entry(plans, ents, nent, spl);
+    const int local = (int)blockIdx.x - m.first;
+    const int row = local / m.nvb, vb = local - row * m.nvb;
+    body_merge_down_bulk<P, C, false>(spl, m.rs, n, row, vb, dsmem, bar);
+}
+
+template <int P, int C>
+static cudaError_t multi_impl(int kind, const Plan *plans, const MultiEnt *ents, int nent, int n, int blocks,
+                              const long long *eoff, void *io, cudaStream_t st) {
+    const int t = multi_threads(kind);
+    if (kind == MK_MERGE_DOWN_BULK) {
+        if constexpr (P == P_FP64) {
+            return cudaErrorInvalidValue;
+        } else {
+            const size_t smem = BulkMD<P, C>::bytes();
+            cudaError_t e = cudaFuncSetAttribute(k_multi_bulk<P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            k_multi_bulk<P, C><<<blocks, 128, smem, st>>>(plans, ents, nent, n);
+            return cudaGetLastError();
+        }
+    }
+    switch (kind) {
+    case MK_MERGE_UP4: k_multi<P, C, MK_MERGE_UP4><<<blocks, t, 0, st>>>(plans, ents, nent, n, eoff, io); break;
+    case MK_MERGE_DOWN4: k_multi<P, C, MK_MERGE_DOWN4><<<blocks, t, 0, st>>>(plans, ents, nent, n, eoff, io); break;
+    case MK_SUM: k_multi<P, C, MK_SUM><<<blocks, t, 0, st>>>(plans, ents, nent, n, eoff, io); break;
+    case MK_ADJ_SUM: k_multi<P, C, MK_ADJ_SUM><<<blocks, t, 0, st>>>(plans, ents, nent, n, eoff, io); break;
+    case MK_ADJ_R2: k_multi<P, C, MK_ADJ_R2><<<blocks, t, 0, st>>>(plans, ents, nent, n, eoff, io); break;
+    case MK_ADJ_R1: k_multi<P, C, MK_ADJ_R1><<<blocks, t, 0, st>>>(plans, ents, nent, n, eoff, io); break;
+    case MK_ADJ_T2: k_multi<P, C, MK_ADJ_T2><<<blocks, t, 0, st>>>(plans, ents, nent, n, eoff, io); break;
+    case MK_ADJ_T1: k_multi<P, C, MK_ADJ_T1><<<blocks, t, 0, st>>>(plans, ents, nent, n, eoff, io); break;
+    default: k_multi<P, C, MK_ADJ_MU><<<blocks, t, 0, st>>>(plans, ents, nent, n, eoff, io); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t multi_prec(int C, int kind, const Plan *plans, const MultiEnt *ents, int nent, int n, int blocks,
+                              const long long *eoff, void *io, cudaStream_t st) {
+    switch (C) {
+    case 1: return multi_impl<P, 1>(kind, plans, ents, nent, n, blocks, eoff, io, st);
+    case 2: return multi_impl<P, 2>(kind, plans, ents, nent, n, blocks, eoff, io, st);
+    case 3: return multi_impl<P, 3>(kind, plans, ents, nent, n, blocks, eoff, io, st);
+    default: return multi_impl<P, 4>(kind, plans, ents, nent, n, blocks, eoff, io, st);
+    }
+}
+
+cudaError_t launch_multi(int prec, int C, int kind, const Plan *plans, const MultiEnt *ents, int nent, int n,
+                         int blocks, const long long *eoff, void *io, cudaStream_t st) {
+    if (blocks <= 0 || nent <= 0) return cudaSuccess;
+    switch (prec) {
+    case P_FP32: return multi_prec<P_FP32>(C, kind, plans, ents, nent, n, blocks, eoff, io, st);
+    case P_FP16: return multi_prec<P_FP16>(C, kind, plans, ents, nent, n, blocks, eoff, io, st);
+    case P_BF16: return multi_prec<P_BF16>(C, kind, plans, ents, nent, n, blocks, eoff, io, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host: the stage list of one scene (same work decomposition as the
 // standalone launch sequences, with 256-thread blocks: paired-v bodies cover
 // 512 v per block, single-v bodies 256).
@@ -321,6 +461,79 @@ void batched_stages(const Plan &pl, int mode, std::vector<StageDesc> &out) {
         for (int q = 2 * pair; q < 2 * pair + 2; ++q)
             for (int n = 0; n <= 2; ++n) bt += gT(q, n);
         tilestage(BK_ADJ_TRACE, pair_tiles_x(pair, pl.W), pair_tiles_y(pair, pl.H), bt, pair);
+    }
+}
+
+void multi_stages(const std::vector<Plan> &plans, int mode, std::vector<MultiDesc> &out) {
+    out.clear();
+    const int ns = (int)plans.size();
+    const bool bulk = ns > 0 && (plans[0].prec == P_FP16 || plans[0].prec == P_BF16);
+    std::vector<std::vector<StageDesc>> st(ns);
+    int Nmax = 0;
+    for (int i = 0; i < ns; ++i) {
+        batched_stages(plans[i], mode, st[i]);
+        Nmax = std::max(Nmax, plan_nmax(plans[i]));
+    }
+    auto mk = [](int bk) {
+        switch (bk) {
+        case BK_MERGE_UP: return (int)MK_MERGE_UP4;
+        case BK_MERGE_DOWN2: return (int)MK_MERGE_DOWN4;   // bulk form chosen below
+        case BK_SUM: return (int)MK_SUM;
+        case BK_ADJ_SUM: return (int)MK_ADJ_SUM;
+        case BK_ADJ_R2: return (int)MK_ADJ_R2;
+        case BK_ADJ_R1: return (int)MK_ADJ_R1;
+        case BK_ADJ_T2: return (int)MK_ADJ_T2;
+        case BK_ADJ_T1: return (int)MK_ADJ_T1;
+        case BK_ADJ_MU: return (int)MK_ADJ_MU;
+        default: return -1;
+        }
+    };
+    // the launches in dependency order: (multi kind, level)
+    std::vector<std::pair<int, int>> keys;
+    if (mode != 1) {
+        for (int n = 3; n <= Nmax; ++n) keys.push_back({MK_MERGE_UP4, n});
+        for (int n = Nmax - 1; n >= 1; --n) keys.push_back({MK_MERGE_DOWN4, n});   // (bulk in 16-bit)
+        if (mode == 0) keys.push_back({MK_SUM, 0});
+    }
+    if (mode != 0) {
+        keys.push_back({MK_ADJ_SUM, 0});
+        keys.push_back({MK_ADJ_R1, 0});
+        for (int n = 1; n + 1 < Nmax; ++n) keys.push_back({MK_ADJ_R2, n});
+        keys.push_back({MK_ADJ_T1, 0});
+        for (int n = 1; n <= Nmax; ++n) keys.push_back({MK_ADJ_T2, n});
+        for (int n = Nmax; n >= 3; --n) keys.push_back({MK_ADJ_MU, n});
+    }
+    for (const auto &key : keys) {
+        MultiDesc d;
+        d.kind = key.first;
+        d.level = key.second;
+        d.blocks = 0;
+        d.bytes = 0;
+        for (int i = 0; i < ns; ++i)
+            for (const StageDesc &sd : st[i]) {
+                if (mk(sd.kind) != d.kind || sd.level != d.level) continue;
+                MultiEnt m;
+                std::memset(&m, 0, sizeof(m));
+                m.first = d.blocks;
+                m.scene = i;
+                m.rs = sd.rs;
+                long long rows;
+                if (d.kind == MK_SUM || d.kind == MK_ADJ_SUM) {
+                    m.nvb = sd.nvb;           // tiles along x
+                    rows = sd.rows;           // tiles along y
+                } else {
+                    int Vmax = 0;
+                    for (int q = 0; q < 4; ++q) Vmax = std::max(Vmax, plans[i].q[q].V);
+                    m.nvb = (Vmax + multi_vblock(d.kind) - 1) / multi_vblock(d.kind);
+                    rows = sd.rs.start[4];
+                }
+                if (rows <= 0) continue;
+                d.ents.push_back(m);
+                d.blocks += (int)(rows * m.nvb);
+                d.bytes += sd.bytes;
+            }
+        if (d.kind == MK_MERGE_DOWN4 && bulk) d.kind = MK_MERGE_DOWN_BULK;
+        if (d.blocks > 0) out.push_back(d);
     }
 }
 

@@ -58,159 +58,18 @@ __global__ void __launch_bounds__(512) k_merge_down4(Plan pl, RowSplit rs, int n
     body_merge_down4<P, C, ENV>(pl, rs, n, row, vb);
 }
 
-// ---------------------------------------------------------------------------
-// Merge down (level n >= 1) with the block's rows staged in shared memory by
-// bulk copies.  One block of 128 threads = one row (q, x, ip) x kBV v (four
-// consecutive v per thread).  Thread 0 copies, for both edges of the cone
-// (Eq. 14 at odd x, Eqs. 15-17 at even x), the T planes of the edge's row,
-// the far R window (its start rounded down to 16 bytes, clipped to the
-// row) and, at even x, the near R row; every thread then reads only shared
-// memory.  Out-of-range far values (and R_N) are the environment's values
-// (0 without a map), chosen by a select; they are never read from the rows.
-// ---------------------------------------------------------------------------
-constexpr int kBV = 512;
-
-template <int P, int C> struct BulkMD {
-    using SL = typename Prec<P>::SL;
-    using ST = typename Prec<P>::ST;
-    static constexpr int AL = 16 / (int)sizeof(SL);   // elements per 16 bytes
-    static constexpr int FW = kBV + 16;                  // far window length
-    static constexpr size_t bytes() {
-        return sizeof(SL) * 2 * C * kBV + sizeof(ST) * 2 * kBV + sizeof(SL) * 2 * C * FW + sizeof(SL) * 2 * C * kBV;
-    }
-};
-
 template <int P, int C, bool ENV>
 __global__ void __launch_bounds__(128) k_merge_down_bulk(Plan pl, RowSplit rs, int n) {
-    using SL = typename Prec<P>::SL;
-    using ST = typename Prec<P>::ST;
-    using A = typename Prec<P>::A;
-    using B = BulkMD<P, C>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
     long long row;
     int vb;
     row_block(pl, row, vb);
-    int local;
-    const int q = find_quadrant(rs, row, local);
-    const QuadGeom &g = pl.q[q];
-    const int v0 = vb * kBV;
-    if (v0 >= g.V) return;                                   // uniform over the block
-    const int I = 1 << n;
-    local += I;
-    const int x = local >> n, ip = local & (I - 1);
-    const bool top = n + 1 >= g.N;                           // R_N: 0, or the environment map
-    const int s = 1 << n;
-    const bool odd = (x & 1) != 0;
-    const int x2 = x >> 1;
-    const int xt = odd ? x : x2;                             // T row: T_n(x, .) or T_{n+1}(x/2, .)
-    const int xq = odd ? (x + 1) >> 1 : x2 + 1;              // far column at level n+1
-    const bool far_ok = !top && xq < g.Un[n + 1];
-    const bool near_ok = !odd && !top;
-    int kk[2], j[2], off[2], fa[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        kk[e] = odd ? (e == 0 ? ip + 1 : ip) : (e == 0 ? 2 * ip + 2 : 2 * ip);
-        j[e] = e == 0 ? 2 * ip + 1 : 2 * ip;
-        off[e] = 2 * kk[e] - (odd ? s : 2 * s);
-        const int a = v0 + off[e];
-        fa[e] = a >= 0 ? a / B::AL * B::AL : -((-a + B::AL - 1) / B::AL) * B::AL;   // round down
-    }
-    SL *tl = reinterpret_cast<SL *>(smem);                   // [2][C][kBV]
-    ST *tt = reinterpret_cast<ST *>(tl + 2 * C * kBV);       // [2][kBV]
-    SL *rf = reinterpret_cast<SL *>(tt + 2 * kBV);           // [2][C][FW]
-    SL *rn = rf + 2 * C * B::FW;                             // [2][C][kBV]
-    const int vend = v0 + kBV < g.Vs ? v0 + kBV : g.Vs;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const TLevel<P, C> Tt(pl, q, odd ? n : n + 1);
-        const RLevel<P, C> R1(pl, q, top ? n : n + 1);
-        const unsigned tb = (unsigned)(vend - v0);
-        unsigned total = 2u * tb * (unsigned)(C * sizeof(SL) + sizeof(ST));
-        int fs[2], fe[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            fs[e] = fa[e] > 0 ? fa[e] : 0;
-            fe[e] = fa[e] + B::FW < g.Vs ? fa[e] + B::FW : g.Vs;
-            if (far_ok && fe[e] > fs[e]) total += (unsigned)(C * (fe[e] - fs[e]) * sizeof(SL));
-        }
-        if (near_ok) total += 2u * (unsigned)(C * tb * sizeof(SL));
-        mbar_arrive_expect(&bar, total + (unsigned)pl.bulk_extra_tx);
-        const uint64_t pol = l2_evict_first();               // T rows: read once from HBM
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const char *gr = Tt.row(xt, kk[e]);
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-                bulk_load_hint(tl + (e * C + c) * kBV, reinterpret_cast<const SL *>(gr) + (long long)c * g.Vs + v0,
-                               tb * sizeof(SL), &bar, pol);
-            bulk_load_hint(tt + e * kBV, reinterpret_cast<const ST *>(gr + (long long)C * g.Vs * sizeof(SL)) + v0,
-                           tb * sizeof(ST), &bar, pol);
-            if (far_ok && fe[e] > fs[e])
-#pragma unroll
-                for (int c = 0; c < C; ++c)
-                    bulk_load(rf + (e * C + c) * B::FW + (fs[e] - fa[e]), R1.base + R1.idx(xq, j[e], c, fs[e]),
-                              (unsigned)((fe[e] - fs[e]) * sizeof(SL)), &bar);
-            if (near_ok)
-#pragma unroll
-                for (int c = 0; c < C; ++c)
-                    bulk_load(rn + (e * C + c) * kBV, R1.base + R1.idx(x2, j[e], c, v0), tb * sizeof(SL), &bar);
-        }
-    }
-    if (!mbar_wait(&bar, 0, pl.bulk_limit_ns)) {              // gave up: let the copies land, report, leave
-        const int code = mbar_wait(&bar, 0, drain_limit_ns(pl.bulk_limit_ns)) ? kWaitTimeout : kWaitLost;
-        if (threadIdx.x == 0) atomicMax(pl.status, code);
-        return;
-    }
-    const int v = v0 + 4 * (int)threadIdx.x;
-    if (v >= g.V) return;
-    const int ti = v - v0;
-    const A Ap = arc<P>(pl, n + 1, 2 * ip + 1), Am = arc<P>(pl, n + 1, 2 * ip);
-    A acc[4][C];
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[l][c] = A(0);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const A Aj = e == 0 ? Ap : Am;
-        A tr[4];
-        ld4(tt + e * kBV + ti, tr);
-#pragma unroll
-        for (int l = 0; l < 4; ++l) tr[l] = Prec<P>::LOG ? fexp(-tr[l]) : tr[l];
-        const int fi = ti + (v0 + off[e] - fa[e]);           // far window index of v (even)
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            A L[4], r[4], r0[4];
-            const A ev = renv<P, C, ENV>(pl, q, n + 1, j[e], c);   // out of range: the environment
-            ld4(tl + (e * C + c) * kBV + ti, L);
-            ld2(rf + (e * C + c) * B::FW + fi, r[0], r[1]);
-            ld2(rf + (e * C + c) * B::FW + fi + 2, r[2], r[3]);
-            if (near_ok) ld4(rn + (e * C + c) * kBV + ti, r0);
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const int vf = v + l + off[e];
-                const A rr = (far_ok && vf >= 0 && vf < g.V) ? r[l] : ev;
-                const A f = fma(Aj, L[l], tr[l] * rr);
-                if (odd) acc[l][c] += f;                                         // Eq. 14
-                else acc[l][c] += A(0.5) * ((near_ok ? r0[l] : ev) + f);         // Eqs. 15-17
-            }
-        }
-    }
-    const RLevel<P, C> Rn(pl, q, n);
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        const A o[4] = {acc[0][c], acc[1][c], acc[2][c], acc[3][c]};
-        Rn.store4(x, ip, c, v, o);
-    }
+    body_merge_down_bulk<P, C, ENV>(pl, rs, n, row, vb, smem, bar);
 }
 
 template <int P, int C, class OUT, bool ENV>
-__global__ void __launch_bounds__(128) k_fluence(Plan pl, OUT *__restrict__ F) {
+__global__ void __launch_bounds__(512) k_fluence(Plan pl, OUT *__restrict__ F) {
     __shared__ __align__(16) unsigned char smem[fluence_smem<P, C>()];
     body_fluence<P, C, OUT, ENV>(pl, F, blockIdx.x, blockIdx.y, smem);
 }
@@ -448,13 +307,16 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         }
         dim3 grid((pl.W + 31) / 32, (pl.H + 31) / 32);
         rec->begin(K_FLUENCE_SUM, 0, by);
-        // 128 threads: every tile of a 1024^2 image is resident at once
+        // 128 threads: every tile of a 1024^2 image is resident at once;
+        // grids of fewer than 600 tiles (about 4 per SM; 512^2 and below) take 512
+        // threads per tile, so that the GPU still holds enough loads in flight
+        const int ft = (long long)grid.x * grid.y < 600 ? 512 : 128;
         if (P == P_FP64) {
-            if (env) k_fluence<P, C, double, true><<<grid, 128, 0, st>>>(pl, (double *)F);
-            else k_fluence<P, C, double, false><<<grid, 128, 0, st>>>(pl, (double *)F);
+            if (env) k_fluence<P, C, double, true><<<grid, ft, 0, st>>>(pl, (double *)F);
+            else k_fluence<P, C, double, false><<<grid, ft, 0, st>>>(pl, (double *)F);
         } else {
-            if (env) k_fluence<P, C, float, true><<<grid, 128, 0, st>>>(pl, (float *)F);
-            else k_fluence<P, C, float, false><<<grid, 128, 0, st>>>(pl, (float *)F);
+            if (env) k_fluence<P, C, float, true><<<grid, ft, 0, st>>>(pl, (float *)F);
+            else k_fluence<P, C, float, false><<<grid, ft, 0, st>>>(pl, (float *)F);
         }
         rec->end();
         ++*launches;

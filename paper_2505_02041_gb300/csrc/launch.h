@@ -154,6 +154,35 @@ cudaError_t launch_batched(const BatchArgs &a, int prec, int C, int blocks_per_s
 cudaError_t launch_batched_tiles(const BatchArgs &a, int prec, int C, int kind, const int *off, const int *nx,
                                  int nscenes, int pair, int total, cudaStream_t st);
 
+// Level-major multi-scene launches (batched schedule 2): one launch runs one
+// stage (a merge-up level, a merge-down level, an adjoint level, the fluence
+// sum or its reverse) of every scene that has it.  Block b of the launch is
+// block b - first of the entry (scene) with the largest first <= b.
+enum MultiKind { MK_MERGE_UP4 = 0, MK_MERGE_DOWN4, MK_SUM, MK_ADJ_SUM, MK_ADJ_R2, MK_ADJ_R1, MK_ADJ_T2, MK_ADJ_T1,
+                 MK_ADJ_MU, MK_MERGE_DOWN_BULK };
+struct MultiEnt {
+    int first;       // first block of this scene
+    int scene;
+    int nvb;         // v-blocks per row (row kinds), tiles along x (tile kinds)
+    int pad;
+    RowSplit rs;     // the stage's rows (row kinds)
+};
+// Threads per block of a kind, and the v covered by one block of a row kind.
+int multi_threads(int kind);
+int multi_vblock(int kind);
+cudaError_t launch_multi(int prec, int C, int kind, const Plan *plans, const MultiEnt *ents, int nent, int n,
+                         int blocks, const long long *eoff, void *io, cudaStream_t st);
+// The multi-scene launches of a pass (mode as batched_stages), level-major:
+// forward merge up n ascending, merge down n descending, the sum; backward
+// reverse of the sum, dL/dR n ascending, dL/dT n ascending, merge-up reverse
+// n descending.  The tile steps (trace, adjoint trace) are not included.
+struct MultiDesc {
+    int kind, level, blocks;
+    double bytes;
+    std::vector<MultiEnt> ents;
+};
+void multi_stages(const std::vector<Plan> &plans, int mode, std::vector<MultiDesc> &out);
+
 // Host-side plan and table builders (hrc_runtime.cu).
 size_t align_up(size_t x, size_t a);
 int levels_for(int U, int cascades);

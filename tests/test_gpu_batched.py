@@ -117,28 +117,36 @@ def test_batched_withheld_dependency_times_out_and_recovers():
     assert torch.equal(F, ref)
 
 
-def test_batched_chain_schedule_matches_persistent():
-    """Schedule 1 (per-scene launch chains on parallel graph branches) gives
-    the persistent schedule's fluence and gradients, in both backward modes."""
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_batched_schedules_match_persistent(precision):
+    """Schedule 1 (per-scene launch chains on parallel graph branches) and
+    schedule 2 (level-major multi-scene launches) give the persistent
+    schedule's fluence and gradients, in both backward modes; every entry is
+    computed by the same arithmetic, so they agree to rounding (fp32), or to
+    the rounding of the 16-bit levels where separately compiled kernels fuse
+    a multiply-add differently (bf16: 5e-3 of the largest value)."""
     require_gpu()
     from paper_2505_02041_gb300 import BatchedHRC
     C = 2
     es, ss = _scenes(C, 30)
-    b = BatchedHRC(SIZES, C)
+    b = BatchedHRC(SIZES, C, 0, precision)
     e, s = b.pack(es, ss)
     gF = torch.randn(e.numel(), device="cuda")
     F0 = b.forward(e, s).clone()
     ge0, gs0 = (t.clone() for t in b.backward(gF))
     b.sync()
-    b.tune(0, 0, 1)
-    for rc in (False, True):
-        b.set_backward_recompute(rc)
-        F1 = b.forward(e, s)
-        ge1, gs1 = b.backward(gF)
-        b.sync()
-        assert err_max(F1.cpu().numpy(), F0.cpu().numpy()) <= 1e-5
-        assert err_max(ge1.cpu().numpy(), ge0.cpu().numpy()) <= 1e-5
-        assert err_max(gs1.cpu().numpy(), gs0.cpu().numpy()) <= 1e-5
+    tol = 1e-5 if precision == "fp32" else 5e-3
+    for sched in (1, 2):
+        b.tune(0, 0, sched)
+        for rc in (False, True):
+            b.set_backward_recompute(rc)
+            F1 = b.forward(e, s)
+            ge1, gs1 = b.backward(gF)
+            b.sync()
+            assert err_max(F1.cpu().numpy(), F0.cpu().numpy()) <= tol, (sched, rc)
+            assert err_max(ge1.cpu().numpy(), ge0.cpu().numpy()) <= tol, (sched, rc)
+            assert err_max(gs1.cpu().numpy(), gs0.cpu().numpy()) <= tol, (sched, rc)
+        b.set_backward_recompute(False)
 
 
 @pytest.mark.slow
@@ -146,8 +154,9 @@ def test_full_size_64_scene_batch_against_oracle():
     """The benchmark's batch at full size: 64 scenes of 128^2 .. 2048^2
     (C = 3, bf16 intervals, about 200 GB of device memory), tuned as the
     benchmark tunes it.  One scene of each of four sizes is compared in full
-    with the FP64 oracle, within the bf16 bounds stated for the single-scene
-    path (max error 4e-2, relative L2 1.5e-2 of the largest value)."""
+    with the FP64 oracle, within about three times the bf16 errors measured
+    on the single-scene workloads (max error 6e-3 of the largest value,
+    relative L2 2e-3)."""
     require_gpu()
     from paper_2505_02041_gb300 import BatchedHRC
     torch.cuda.empty_cache()
@@ -174,7 +183,7 @@ def test_full_size_64_scene_batch_against_oracle():
         Fr = oracle.fluence(es[i].numpy(), ss[i].numpy())
         Fg = Fs[i].cpu().numpy()
         scale = np.max(np.abs(Fr))
-        assert np.max(np.abs(Fg - Fr)) <= 4e-2 * scale, X
-        assert np.linalg.norm(Fg - Fr) <= 1.5e-2 * np.linalg.norm(Fr), X
+        assert np.max(np.abs(Fg - Fr)) <= 6e-3 * scale, X
+        assert np.linalg.norm(Fg - Fr) <= 2e-3 * np.linalg.norm(Fr), X
     assert checked == {128, 512, 1024, 2048}
     b.close()
