@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 from paper_2505_02041_gb300 import scenes
-from gpu_util import require_gpu, err_max, to_dev, torch
+from gpu_util import require_gpu, err_max, assert_fp32, to_dev, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,7 @@ def test_env_forward_fp32_vs_oracle(W, H, C, casc, M, seed):
     h = HRC(W, H, C, casc)
     h.set_environment(to_dev(env))
     F = h.forward(to_dev(e), to_dev(s)).cpu().numpy()
-    assert err_max(F, oracle.fluence(e, s, casc, env=env)) <= 1e-4
+    assert_fp32(F, oracle.fluence(e, s, casc, env=env))
 
 
 def test_env_every_launch_configuration():
@@ -53,7 +53,7 @@ def test_env_every_launch_configuration():
     for cfg in [(0, 1, 128, 0, 0), (1, 2, 64, 1, 0), (0, 4, 256, 1, 1), (1, 4, 512, 0, 1), (0, 2, 64, 0, 1)]:
         h.set_launch_config(*cfg)
         F = h.forward(ed, sd).cpu().numpy()
-        assert err_max(F, Fr) <= 1e-4, cfg
+        assert_fp32(F, Fr, msg=cfg)
 
 
 @pytest.mark.parametrize("W,H,C,seed", [(16, 16, 1, 0), (37, 23, 2, 1)])
@@ -68,7 +68,7 @@ def test_env_forward_fp64_vs_oracle(W, H, C, seed):
     assert err_max(F, oracle.fluence(e, s, env=env)) <= 1e-10
 
 
-@pytest.mark.parametrize("prec,tol", [("fp16", 5e-3), ("bf16", 4e-2)])
+@pytest.mark.parametrize("prec,tol", [("fp16", 1e-3), ("bf16", 6e-3)])
 def test_env_reduced_precision(prec, tol):
     """The map in the reduced-precision storage modes (the same bounds as
     their fluence without a map)."""
@@ -153,7 +153,7 @@ def test_env_removed_and_host_entry():
     F0 = h.forward(ed, sd).clone()
     h.set_environment(to_dev(env))
     Fh = h.forward_host(torch.from_numpy(e.copy()), torch.from_numpy(s.copy())).numpy()
-    assert err_max(Fh, oracle.fluence(e, s, env=env)) <= 1e-4
+    assert_fp32(Fh, oracle.fluence(e, s, env=env))
     h.set_environment(None)
     assert torch.equal(h.forward(ed, sd), F0)
 
@@ -171,4 +171,4 @@ def test_env_full_size_workload():
     h.autotune()
     h.set_environment(to_dev(env))
     F = h.forward(to_dev(e), to_dev(s)).cpu().numpy()
-    assert err_max(F, oracle.fluence(e, s, env=env)) <= 1e-4
+    assert_fp32(F, oracle.fluence(e, s, env=env))

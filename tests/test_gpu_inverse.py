@@ -46,7 +46,7 @@ def test_inverse_rendering_recovers_emission():
     assert err_max(F, target.cpu().numpy()) <= 5e-2
 
 
-@pytest.mark.parametrize("prec,tol", [("fp16", 5e-3), ("bf16", 4e-2)])
+@pytest.mark.parametrize("prec,tol", [("fp16", 1e-3), ("bf16", 6e-3)])
 def test_optional_steps_in_reduced_precision(prec, tol):
     """Cross blur, two bounces and per-channel extinction with fp16 / bf16
     interval storage, forward against the FP64 oracle within the modes'

@@ -2,9 +2,15 @@
 transmittance, fp32 arithmetic) against the FP64 oracle.
 
 These modes change the stored values, so they are compared with the oracle
-at a stated error rather than the fp32 bound: err_max (max |diff| / max |F|)
-and the relative L2 error are checked against bounds a few times above the
-values measured on these scenes.
+at a stated error rather than the fp32 bound: err_max (max |diff| / max |F|),
+the relative L2 error and the largest pixel-relative error over the pixels
+with F >= 1e-3 max F are checked against bounds about three times the values
+measured on the 1024^2 volumetric workload (fp16: 2.1e-4, 7.1e-5, 6.8e-4;
+bf16: 1.7e-3, 6.2e-4, 4.6e-3).  The other two scenes measure fp16 2.0e-4 /
+1.8e-4 / 9.9e-4 (disks64) and 3.1e-4 / 1.5e-4 / 1.5e-3 (fog512), bf16
+1.7e-3 / 1.4e-3 / 6.9e-3 and 2.1e-3 / 1.1e-3 / 1.3e-2.  A level entry is one
+16-bit rounding away from the exact value (bf16: 2^-8 relative), so the
+level comparison has its own bounds (bf16 measured 8.5e-3).
 """
 import numpy as np
 import pytest
@@ -15,7 +21,8 @@ from gpu_util import require_gpu, err_max, to_dev, torch
 
 pytestmark = pytest.mark.gpu
 
-BOUNDS = {"fp16": (5e-3, 2e-3), "bf16": (4e-2, 1.5e-2)}   # (err_max, rel L2)
+BOUNDS = {"fp16": (1e-3, 6e-4, 3e-3), "bf16": (6e-3, 4e-3, 2e-2)}   # (err_max, rel L2, pixel-relative)
+LEVEL_BOUNDS = {"fp16": 2e-3, "bf16": 1.5e-2}
 
 
 def _F(e, s, prec):
@@ -26,7 +33,7 @@ def _F(e, s, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-@pytest.mark.parametrize("name", ["disks64", "fog512"])
+@pytest.mark.parametrize("name", ["disks64", "fog512", "volumetric1024"])
 def test_reduced_precision_forward(prec, name):
     require_gpu()
     e, s = scenes.scene_by_name(name)
@@ -37,7 +44,7 @@ def test_reduced_precision_forward(prec, name):
     lit = np.abs(Fr) >= 1e-3 * np.max(np.abs(Fr))
     pr = np.max(np.abs(F - Fr)[lit] / np.abs(Fr)[lit])
     print(f"{name} {prec}: err_max={em:.3e} relL2={l2:.3e} pixel-relative max (F >= 1e-3 max)={pr:.3e}")
-    assert em <= BOUNDS[prec][0] and l2 <= BOUNDS[prec][1]
+    assert em <= BOUNDS[prec][0] and l2 <= BOUNDS[prec][1] and pr <= BOUNDS[prec][2]
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
@@ -53,7 +60,7 @@ def test_reduced_precision_levels_log_transmittance(prec):
         if n == 0:                                   # so are the even columns of T_0
             Tg, Tr = Tg[::2], Tr[::2]
         assert np.max(np.abs(Tg[..., -1] - Tr[..., -1])) <= 1e-5
-        assert err_max(Tg[..., :-1], Tr[..., :-1]) <= BOUNDS[prec][0]
+        assert err_max(Tg[..., :-1], Tr[..., :-1]) <= LEVEL_BOUNDS[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
