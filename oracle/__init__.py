@@ -30,12 +30,11 @@ _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
 
 
-def build(force: bool = False, out: str = _LIB, defines=()) -> str:
-    """Compile the C oracle with gcc (OpenMP on)."""
-    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+def build(force: bool = False, out: str = _LIB, src: str = _SRC) -> str:
+    """Compile the C oracle (or another source file `src`) with gcc (OpenMP on)."""
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", *[f"-D{d}" for d in defines],
-                               "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", tmp, src, "-lm"])
         os.replace(tmp, out)
     return out
 
@@ -103,11 +102,11 @@ class _Bound:
         return call
 
 
-def load_variant(path: str, defines=()):
-    """Build (if needed) and load a variant of the oracle compiled with the
-    given preprocessor definitions; returns an object with this module's
-    functions (trace, fluence, fluence_adjoint, ...)."""
-    build(out=path, defines=defines)
+def load_variant(path: str, src: str):
+    """Build and load a variant of the oracle compiled from the C source file
+    `src` (the mutation test's edited copies); returns an object with this
+    module's functions (trace, fluence, fluence_adjoint, ...)."""
+    build(force=True, out=path, src=src)
     return _Bound(_declare(ctypes.CDLL(path)))
 
 
@@ -272,39 +271,37 @@ def _lighting_adjoint(e, s, g, cascades, blur):
     return fluence_blurred_adjoint(e, s, g, blur, cascades)
 
 
-def bounce_source(e, s, albedo, F, _mutant=0):
+def bounce_source(e, s, albedo, F):
     """Emission of the next bounce (Sec. 4.2: the output fluence fed into
     another iteration), read as isotropic single scattering in 2D: a pixel
     with extinction sigma and albedo rho scatters sigma * rho of the fluence F
     (radiance integrated over the full turn) evenly over 2 pi, so its source
     per unit length becomes e + rho * sigma * F / (2 pi)."""
     sb = s if np.ndim(s) == 3 else s[None]   # per-channel extinction: sigma_c for channel c
-    k = (1.0 if _mutant == 1 else sb) * albedo * F
-    return e + (k if _mutant == 2 else k / (2.0 * np.pi))
+    return e + sb * albedo * F / (2.0 * np.pi)
 
 
-def fluence_bounces(e, s, albedo, bounces: int, cascades: int = 0, blur=None, _mutant=0):
+def fluence_bounces(e, s, albedo, bounces: int, cascades: int = 0, blur=None):
     """Multi-bounce lighting: F_0 = Lighting(e), e_k = e + albedo * s * F_{k-1}
     / (2 pi), F_k = Lighting(e_k); returns F_bounces (float64 [C][H][W]).
     `blur` = None, or the cross-blur threshold applied by every Lighting."""
     if np.ndim(s) == 3:
-        return _per_channel(lambda c, ec, sc, ac: fluence_bounces(ec, sc, ac, bounces, cascades, blur, _mutant),
+        return _per_channel(lambda c, ec, sc, ac: fluence_bounces(ec, sc, ac, bounces, cascades, blur),
                             e, s, albedo)
     e, s, C, H, W = _img(e, s)
     albedo = np.ascontiguousarray(albedo, dtype=np.float64).reshape(C, H, W)
     F = _lighting(e, s, cascades, blur)
-    for _ in range(bounces - (1 if _mutant == 3 else 0)):
-        F = _lighting(bounce_source(e, s, albedo, F, _mutant), s, cascades, blur)
+    for _ in range(bounces):
+        F = _lighting(bounce_source(e, s, albedo, F), s, cascades, blur)
     return F
 
 
-def fluence_bounces_adjoint(e, s, albedo, gF, bounces: int, cascades: int = 0, blur=None, _mutant=0):
+def fluence_bounces_adjoint(e, s, albedo, gF, bounces: int, cascades: int = 0, blur=None):
     """Gradient of sum(gF * fluence_bounces(...)) w.r.t. (e, s, albedo), by
     the reverse of the iteration: the adjoint of Lighting at each e_k, and of
     the source update through F_{k-1}, s and albedo."""
     if np.ndim(s) == 3:
-        return _per_channel(lambda c, ec, sc, ac, gc: fluence_bounces_adjoint(ec, sc, ac, gc, bounces, cascades, blur,
-                                                                             _mutant),
+        return _per_channel(lambda c, ec, sc, ac, gc: fluence_bounces_adjoint(ec, sc, ac, gc, bounces, cascades, blur),
                             e, s, albedo, np.asarray(gF).reshape(np.shape(e)))
     e, s, C, H, W = _img(e, s)
     albedo = np.ascontiguousarray(albedo, dtype=np.float64).reshape(C, H, W)
@@ -325,8 +322,7 @@ def fluence_bounces_adjoint(e, s, albedo, gF, bounces: int, cascades: int = 0, b
         if k == 0:
             break
         Fp = Fs[k - 1]
-        if _mutant != 4:
-            gs += np.sum(gek * albedo * Fp, axis=0) / (2.0 * np.pi)
+        gs += np.sum(gek * albedo * Fp, axis=0) / (2.0 * np.pi)
         ga += gek * s[None] * Fp / (2.0 * np.pi)
         g = gek * albedo * s[None] / (2.0 * np.pi)
     return ge, gs, ga

@@ -36,13 +36,6 @@
 
 #define ORC_MAXL 16
 
-/* ORC_MUTANT selects a deliberately planted mistake (0 = none).  Only the
- * mutation test builds the non-zero variants, to show that the pins catch
- * a wrong sign, index, weight or operand anywhere in the method. */
-#ifndef ORC_MUTANT
-#define ORC_MUTANT 0
-#endif
-
 /* ---------------------------------------------------------------------------
  * Frame fields (Algorithm 1, Lighting: one orientation per quadrant).
  * ------------------------------------------------------------------------ */
@@ -59,7 +52,7 @@ static void frame_to_image(int q, int W, int H, long u, long v, long *x, long *y
     case 0: *x = u;         *y = v;         break;
     case 1: *x = W - 1 - u; *y = v;         break;
     case 2: *x = v;         *y = u;         break;
-    default: *x = v;        *y = ORC_MUTANT == 10 ? u : H - 1 - u; break;
+    default: *x = v;        *y = H - 1 - u; break;
     }
 }
 
@@ -183,7 +176,7 @@ static void trace(const Frame *f, double pu, double pv, double qu, double qv, do
         double sg = frame_sigma(f, pc[m].u, pc[m].v);
         double l = pc[m].len;
         double tau = sg * l;
-        double w = ORC_MUTANT == 7 ? l : l * phi(tau);
+        double w = l * phi(tau);
         for (int c = 0; c < f->C; ++c) L[c] += Tacc * frame_emis(f, c, pc[m].u, pc[m].v) * w;
         Tacc *= exp(-tau);
     }
@@ -229,7 +222,7 @@ static void trace_adjoint(const Frame *f, double pu, double pv, double qu, doubl
         for (int c = 0; c < C; ++c) {
             double em = f->e[((size_t)c * f->U + u) * f->V + v];
             ge[((size_t)c * f->U + u) * f->V + v] += gL[c] * P[m] * l * phi(sg * l);
-            g += gL[c] * (P[m] * em * l * l * dphi(sg * l) - (ORC_MUTANT == 13 ? -l : l) * S[m * C + c]);
+            g += gL[c] * (P[m] * em * l * l * dphi(sg * l) - l * S[m * C + c]);
         }
         g -= gT * l * Ttot;
         gs[u * f->V + v] += g;
@@ -336,9 +329,6 @@ static void frame_dir_to_image(int q, double du, double dv, double *dx, double *
     case 2: *dx = dv;  *dy = du;  break;
     default: *dx = dv; *dy = -du; break;
     }
-#if ORC_MUTANT == 19
-    if (q == 1) *dx = du;
-#endif
 }
 
 /* Environment values of frame q: at level N, cone j' = j + 1/2 sees
@@ -357,11 +347,10 @@ static void env_tables(Cascades *cs, int q, const double *env, int M)
         for (long j = 0; j < I; ++j)
             for (int c = 0; c < C; ++c) {
                 double v;
-                if (n == N || ORC_MUTANT == 20) {
+                if (n == N) {
                     double dx, dy, s2 = (double)(1L << n);
                     frame_dir_to_image(q, s2, 2.0 * j + 1.0 - s2, &dx, &dy);
-                    v = (ORC_MUTANT == 21 ? 1.0 : orc_arc(n, (int)j)) * env_lookup(env, M, c, dx, dy);
-                    if (ORC_MUTANT == 20 && n < N) v = 0.0;
+                    v = orc_arc(n, (int)j) * env_lookup(env, M, c, dx, dy);
                 } else {
                     v = cs->Renv[n + 1][(size_t)(2 * j) * C + c] + cs->Renv[n + 1][(size_t)(2 * j + 1) * C + c];
                 }
@@ -376,7 +365,7 @@ static void merge(int C, const double *a, const double *b, double *out)
     double Ta = a ? a[C] : 1.0, Tb = b ? b[C] : 1.0;
     for (int c = 0; c < C; ++c) {
         double La = a ? a[c] : 0.0, Lb = b ? b[c] : 0.0;
-        out[c] = La + (ORC_MUTANT == 8 ? Tb : Ta) * Lb;
+        out[c] = La + Ta * Lb;
     }
     out[C] = Ta * Tb;
 }
@@ -427,16 +416,16 @@ static void hrc_frame(const Frame *f, int cascades, int q, const double *env, in
                     if ((k & 1) == 0) {
                         long kk = k / 2;   /* T_n(p, 2kk) = Merge(T_m(p,kk), T_m(p+v_m(kk),kk)) */
                         merge(C, T_get(cs, m, pu, pv, kk),
-                              T_get(cs, m, pu + sm, ORC_MUTANT == 1 ? pv - 2 * kk + sm : pv + 2 * kk - sm, kk), o);
+                              T_get(cs, m, pu + sm, pv + 2 * kk - sm, kk), o);
                     } else {
                         long kp = (k + 1) / 2, km = (k - 1) / 2;   /* kappa +- 1/2 */
                         /* F_+ = Merge(T_m(p, kappa+1/2), T_m(p + v_m(kappa+1/2), kappa-1/2)) */
                         merge(C, T_get(cs, m, pu, pv, kp),
-                              T_get(cs, m, pu + sm, pv + 2 * kp - sm, ORC_MUTANT == 2 ? kp : km), Fp);
+                              T_get(cs, m, pu + sm, pv + 2 * kp - sm, km), Fp);
                         /* F_- = Merge(T_m(p, kappa-1/2), T_m(p + v_m(kappa-1/2), kappa+1/2)) */
                         merge(C, T_get(cs, m, pu, pv, km),
                               T_get(cs, m, pu + sm, pv + 2 * km - sm, kp), Fm);
-                        for (int c = 0; c <= C; ++c) o[c] = ORC_MUTANT == 3 ? Fp[c] : 0.5 * (Fm[c] + Fp[c]);   /* Eq. 20 */
+                        for (int c = 0; c <= C; ++c) o[c] = 0.5 * (Fm[c] + Fp[c]);   /* Eq. 20 */
                     }
                 }
         }
@@ -453,11 +442,10 @@ static void hrc_frame(const Frame *f, int cascades, int q, const double *env, in
                     double *o = cs->R[n] + R_index(cs, n, x, ip, y);
                     /* j_+ = 2i + 1/2 -> index 2ip+1; j_- = 2i - 1/2 -> 2ip */
                     long jp = 2 * ip + 1, jm = 2 * ip;
-                    double Ap = orc_arc(ORC_MUTANT == 14 ? n : n + 1, (int)(ORC_MUTANT == 14 ? ip : jp));
-                    double Am = orc_arc(ORC_MUTANT == 14 ? n : n + 1, (int)(ORC_MUTANT == 14 ? ip : jm));
-                    if (ORC_MUTANT == 4) Ap = Am;
+                    double Ap = orc_arc(n + 1, (int)jp);
+                    double Am = orc_arc(n + 1, (int)jm);
                     for (int c = 0; c < C; ++c) o[c] = 0.0;
-                    if (ORC_MUTANT == 11 ? !(x & 1) && x > 0 : (x & 1)) {
+                    if (x & 1) {
                         /* Eq. 14: F_+- = Merge_r(A x T_n(p, i +- 1/2), R_{n+1}(q_+-, j_+-)),
                          * q_+- = p + v_n(i +- 1/2); i + 1/2 = ip + 1, i - 1/2 = ip. */
                         for (int sgn = 0; sgn < 2; ++sgn) {
@@ -480,10 +468,10 @@ static void hrc_frame(const Frame *f, int cascades, int q, const double *env, in
                             double A = sgn == 0 ? Ap : Am;
                             const double *r0 = R_val(cs, n + 1, pu, pv, j);
                             const double *t = T_get(cs, n + 1, pu, pv, kk);
-                            const double *r1 = R_val(cs, n + 1, pu + s1, ORC_MUTANT == 9 ? pv + kk - s : pv + 2 * kk - s1, j);
+                            const double *r1 = R_val(cs, n + 1, pu + s1, pv + 2 * kk - s1, j);
                             double Tt = t ? t[C] : 1.0;
                             for (int c = 0; c < C; ++c)
-                                o[c] += 0.5 * ((ORC_MUTANT == 5 ? 2.0 : 1.0) * (r0 ? r0[c] : 0.0) + A * (t ? t[c] : 0.0) +
+                                o[c] += 0.5 * ((r0 ? r0[c] : 0.0) + A * (t ? t[c] : 0.0) +
                                                Tt * (r1 ? r1[c] : 0.0));
                         }
                     }
@@ -523,7 +511,7 @@ void orc_fluence_env(const double *e, const double *s, int C, int W, int H, int 
             for (long v = 0; v < f.V; ++v) {
                 long x, y;
                 frame_to_image(q, W, H, u, v, &x, &y);
-                const double *r = R_val(&cs, 0, ORC_MUTANT == 6 ? u : u + 1, v, 0);
+                const double *r = R_val(&cs, 0, u + 1, v, 0);
                 if (!r) continue;
                 for (int c = 0; c < C; ++c) F[((size_t)c * H + y) * W + x] += r[c];
             }
@@ -630,7 +618,7 @@ void orc_fluence_adjoint_env(const double *e, const double *s, const double *gF,
                                 double Tt = t ? t[C] : 1.0;
                                 if (r0) {
                                     double *gr = gR[n + 1] + R_index(&cs, n + 1, pu >> (n + 1), j, pv);
-                                    for (int c = 0; c < C; ++c) gr[c] += (ORC_MUTANT == 12 ? 1.0 : 0.5) * g[c];
+                                    for (int c = 0; c < C; ++c) gr[c] += 0.5 * g[c];
                                 }
                                 if (t) {
                                     double *gt = gT[n + 1] + T_index(&cs, n + 1, pu >> (n + 1), kk, pv);
@@ -774,17 +762,13 @@ static int blur_keep(const double *s, int W, int H, long x, long y, long xm, lon
     if (xm < 0 || xm >= W || ym < 0 || ym >= H) return 0;
     double ac = 1.0 - exp(-s[y * W + x]);
     double am = 1.0 - exp(-s[ym * W + xm]);
-#if ORC_MUTANT == 17
-    ac = s[y * W + x];
-    am = s[ym * W + xm];
-#endif
     return fabs(am - ac) <= thr;
 }
 
 /* out = B F: the blurred image (F, out: [C][H][W]; s: [H][W]). */
 void orc_cross_blur(const double *F, const double *s, int C, int W, int H, double thr, double *out)
 {
-    const double wc = ORC_MUTANT == 15 ? 2.0 : 4.0;
+    const double wc = 4.0;
     for (long y = 0; y < H; ++y)
         for (long x = 0; x < W; ++x) {
             double wsum = wc;
@@ -796,7 +780,6 @@ void orc_cross_blur(const double *F, const double *s, int C, int W, int H, doubl
                 wsum += 1.0;
                 for (int c = 0; c < C; ++c) acc[c] += F[((size_t)c * H + ym) * W + xm];
             }
-            if (ORC_MUTANT == 16) wsum = 8.0;
             for (int c = 0; c < C; ++c) out[((size_t)c * H + y) * W + x] = acc[c] / wsum;
         }
 }
@@ -820,8 +803,7 @@ void orc_cross_blur_adjoint(const double *g, const double *s, int C, int W, int 
                 for (int d = 0; d < 4; ++d) {
                     long xm = x + blur_dx[d], ym = y + blur_dy[d];
                     if (!blur_keep(s, W, H, x, y, xm, ym, thr)) continue;
-                    if (ORC_MUTANT == 18) gF[((size_t)c * H + y) * W + x] += gc;
-                    else gF[((size_t)c * H + ym) * W + xm] += gc;
+                    gF[((size_t)c * H + ym) * W + xm] += gc;
                 }
             }
         }

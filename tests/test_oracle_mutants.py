@@ -1,12 +1,13 @@
 """Mutation check of the oracle's pins.
 
-Each variant of hrc_oracle.c compiled with -DORC_MUTANT=k carries one
-planted mistake (a flipped sign, a swapped index, a dropped weight, a wrong
-operand, a wrong quadrant map, a broken adjoint term).  The pins used
-against the real oracle -- Fig. 2, the uniform slab, the independent
-recursive formulation, the uniform emissive medium and central
-differences -- must reject every variant.  The mistakes are planted in the
-oracle, on the CPU; the real oracle passes the same checks.
+Each variant is a temporary copy of hrc_oracle.c with one planted mistake
+(a flipped sign, a swapped index, a dropped weight, a wrong operand, a wrong
+quadrant map, a broken adjoint term), made by the (search, replace) edits
+below -- each search text must occur exactly once in the oracle -- and
+compiled on its own.  The oracle itself carries no trace of them.  The pins
+used against the real oracle -- Fig. 2, the uniform slab, the independent
+recursive formulation, the uniform emissive medium and central differences
+-- must reject every variant.  The real oracle passes the same checks.
 """
 import math
 import os
@@ -20,29 +21,64 @@ from oracle import recursive
 from paper_2505_02041_gb300 import scenes
 from conftest import read_golden
 
+# name -> [(search, replace), ...] applied to a copy of oracle/hrc_oracle.c
 MUTANTS = {
-    1: "Eq. 18 far-operand offset sign",
-    2: "Eq. 19 far-operand direction",
-    3: "Eq. 20 average dropped",
-    4: "Eq. 14 arc of the wrong half-cone",
-    5: "Eq. 15 weight of R_{n+1}(p, j)",
-    6: "fluence sum without the +1 offset",
-    7: "Trace piece weight without phi",
-    8: "Merge with the far transmittance",
-    9: "Eq. 17 offset on the wrong level",
-    10: "quadrant frame map of -y",
-    11: "odd / even x swapped",
-    12: "adjoint weight of R_{n+1}(p, j)",
-    13: "adjoint sign of the suffix-radiance term",
-    14: "Eq. 14 arcs of level n",
-    15: "Eq. 21 centre weight",
-    16: "cross blur without renormalisation of the kept weights",
-    17: "cross blur threshold on extinction instead of opacity",
-    18: "cross blur adjoint scattered onto the wrong pixel",
-    19: "environment look direction of frame q1 mirrored",
-    20: "environment only at level N (out-of-grid lookups below it zero)",
-    21: "environment values without the arc weight",
+    "Eq. 18 far-operand offset sign": [
+        ("T_get(cs, m, pu + sm, pv + 2 * kk - sm, kk), o);", "T_get(cs, m, pu + sm, pv - 2 * kk + sm, kk), o);")],
+    "Eq. 19 far-operand direction": [
+        ("T_get(cs, m, pu + sm, pv + 2 * kp - sm, km), Fp);", "T_get(cs, m, pu + sm, pv + 2 * kp - sm, kp), Fp);")],
+    "Eq. 20 average dropped": [
+        ("o[c] = 0.5 * (Fm[c] + Fp[c]);   /* Eq. 20 */", "o[c] = Fp[c];")],
+    "Eq. 14 arc of the wrong half-cone": [
+        ("double Am = orc_arc(n + 1, (int)jm);", "double Am = orc_arc(n + 1, (int)jm);\n                    Ap = Am;")],
+    "Eq. 15 weight of R_{n+1}(p, j)": [
+        ("o[c] += 0.5 * ((r0 ? r0[c] : 0.0) +", "o[c] += 0.5 * (2.0 * (r0 ? r0[c] : 0.0) +")],
+    "fluence sum without the +1 offset": [
+        ("R_val(&cs, 0, u + 1, v, 0);", "R_val(&cs, 0, u, v, 0);")],
+    "Trace piece weight without phi": [
+        ("double w = l * phi(tau);", "double w = l;")],
+    "Merge with the far transmittance": [
+        ("out[c] = La + Ta * Lb;", "out[c] = La + Tb * Lb;")],
+    "Eq. 17 offset on the wrong level": [
+        ("R_val(cs, n + 1, pu + s1, pv + 2 * kk - s1, j);", "R_val(cs, n + 1, pu + s1, pv + kk - s, j);")],
+    "quadrant frame map of -y": [
+        ("*y = H - 1 - u; break;", "*y = u; break;")],
+    "odd / even x swapped": [
+        ("if (x & 1) {\n                        /* Eq. 14", "if (!(x & 1) && x > 0) {\n                        /* Eq. 14")],
+    "adjoint weight of R_{n+1}(p, j)": [
+        ("gr[c] += 0.5 * g[c];", "gr[c] += 1.0 * g[c];")],
+    "adjoint sign of the suffix-radiance term": [
+        ("dphi(sg * l) - l * S[m * C + c]);", "dphi(sg * l) + l * S[m * C + c]);")],
+    "Eq. 14 arcs of level n": [
+        ("double Ap = orc_arc(n + 1, (int)jp);\n                    double Am = orc_arc(n + 1, (int)jm);",
+         "double Ap = orc_arc(n, (int)ip);\n                    double Am = orc_arc(n, (int)ip);")],
+    "Eq. 21 centre weight": [
+        ("const double wc = 4.0;", "const double wc = 2.0;")],
+    "cross blur without renormalisation of the kept weights": [
+        ("            for (int c = 0; c < C; ++c) out[((size_t)c * H + y) * W + x] = acc[c] / wsum;",
+         "            wsum = 8.0;\n            for (int c = 0; c < C; ++c) out[((size_t)c * H + y) * W + x] = acc[c] / wsum;")],
+    "cross blur threshold on extinction instead of opacity": [
+        ("    return fabs(am - ac) <= thr;", "    ac = s[y * W + x];\n    am = s[ym * W + xm];\n    return fabs(am - ac) <= thr;")],
+    "cross blur adjoint scattered onto the wrong pixel": [
+        ("gF[((size_t)c * H + ym) * W + xm] += gc;", "gF[((size_t)c * H + y) * W + x] += gc;")],
+    "environment look direction of frame q1 mirrored": [
+        ("    default: *dx = dv; *dy = -du; break;\n    }\n}", "    default: *dx = dv; *dy = -du; break;\n    }\n    if (q == 1) *dx = du;\n}")],
+    "environment only at level N (out-of-grid lookups below it zero)": [
+        ("v = cs->Renv[n + 1][(size_t)(2 * j) * C + c] + cs->Renv[n + 1][(size_t)(2 * j + 1) * C + c];", "v = 0.0;")],
+    "environment values without the arc weight": [
+        ("v = orc_arc(n, (int)j) * env_lookup(env, M, c, dx, dy);", "v = env_lookup(env, M, c, dx, dy);")],
 }
+
+
+def mutant_source(edits):
+    """The oracle's C source with `edits` applied (each search text found
+    exactly once)."""
+    with open(os.path.join(os.path.dirname(oracle.__file__), "hrc_oracle.c")) as f:
+        src = f.read()
+    for old, new in edits:
+        assert src.count(old) == 1, f"edit target not unique in the oracle: {old!r}"
+        src = src.replace(old, new)
+    return src
 
 
 def failed_pins(O):
@@ -143,12 +179,28 @@ def test_real_oracle_passes_every_pin():
     assert failed_pins(oracle) == []
 
 
-@pytest.mark.parametrize("k", sorted(MUTANTS))
-def test_every_planted_mistake_is_caught(k):
-    path = os.path.join(tempfile.gettempdir(), f"liboracle_mutant{k}_{os.getpid()}.so")
+def test_mutant_edits_apply_and_the_oracle_is_plain():
+    """Every edit finds its target exactly once, and the oracle's source
+    holds no switch for a planted mistake."""
+    with open(os.path.join(os.path.dirname(oracle.__file__), "hrc_oracle.c")) as f:
+        src = f.read()
+    assert "MUTANT" not in src
+    for edits in MUTANTS.values():
+        assert mutant_source(edits) != src
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_every_planted_mistake_is_caught(name):
+    d = tempfile.mkdtemp(prefix="oracle_mutant_")
+    src = os.path.join(d, "hrc_oracle_mutant.c")
+    lib = os.path.join(d, "liboracle_mutant.so")
     try:
-        O = oracle.load_variant(path, defines=[f"ORC_MUTANT={k}"])
-        assert failed_pins(O), f"mutant {k} ({MUTANTS[k]}) passed every pin"
+        with open(src, "w") as f:
+            f.write(mutant_source(MUTANTS[name]))
+        O = oracle.load_variant(lib, src)
+        assert failed_pins(O), f"planted mistake '{name}' passed every pin"
     finally:
-        if os.path.exists(path):
-            os.remove(path)
+        for p in (src, lib):
+            if os.path.exists(p):
+                os.remove(p)
+        os.rmdir(d)
