@@ -55,6 +55,12 @@ def _declare(L):
     L.orc_fluence_adjoint_env.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           _D, ctypes.c_int, _D, _D]
     L.orc_fluence_adjoint_env.restype = None
+    L.orc_fluence_top.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D,
+                                  ctypes.c_int, _D]
+    L.orc_fluence_top.restype = None
+    L.orc_fluence_adjoint_top.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          _D, ctypes.c_int, _D, _D]
+    L.orc_fluence_adjoint_top.restype = None
     L.orc_frame_level.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
     L.orc_frame_level.restype = ctypes.c_long
@@ -150,6 +156,12 @@ def _env(env, C):
     return env
 
 
+def _top(top, C):
+    top = np.ascontiguousarray(top, dtype=np.float64)
+    assert top.ndim == 3 and top.shape[0] == 4 and top.shape[2] == C, "top radiance is [4][K][C]"
+    return top
+
+
 def _per_channel(fn, e, s, *rest):
     """Per-channel extinction s[C][H][W] (the paper stores T as C-vectors,
     Sec. 5): Merge (Eq. 7), the Eq. 20 blend, the merge down (Eqs. 14-17),
@@ -167,17 +179,25 @@ def _per_channel(fn, e, s, *rest):
     return np.concatenate(outs)
 
 
-def fluence(e, s, cascades: int = 0, env=None) -> np.ndarray:
+def fluence(e, s, cascades: int = 0, env=None, top=None) -> np.ndarray:
     """Algorithm 1 (Lighting): F[C][H][W] in float64.  `env` ([C][M] or [M]):
     an environment map (footnote 1 of Sec. 4.2), radiance seen along the
     image-space look angle theta_m = 2 pi (m + 1/2) / M (theta from +x
-    towards +y = down the rows), linearly interpolated."""
+    towards +y = down the rows), linearly interpolated.  `top` ([4][K][C]):
+    the top-level radiance R_N itself, supplied by the caller (the same
+    footnote: R_N computed by another method), cone j < 2^N of frame q at
+    top[q][j][c]; outside the grid, as with a map, a lower level sees the
+    sum of its level-N descendants."""
     if np.ndim(s) == 3:
-        return _per_channel(lambda c, ec, sc: fluence(ec, sc, cascades, None if env is None else _env(env, len(e))[c:c + 1]),
+        return _per_channel(lambda c, ec, sc: fluence(ec, sc, cascades, None if env is None else _env(env, len(e))[c:c + 1],
+                                                      None if top is None else _top(top, len(e))[:, :, c:c + 1]),
                             e, s)
     e, s, C, H, W = _img(e, s)
     F = np.zeros((C, H, W))
-    if env is None:
+    if top is not None:
+        top = _top(top, C)
+        lib().orc_fluence_top(_p(e), _p(s), C, W, H, cascades, _p(top), top.shape[1], _p(F))
+    elif env is None:
         lib().orc_fluence(_p(e), _p(s), C, W, H, cascades, _p(F))
     else:
         env = _env(env, C)
@@ -206,18 +226,23 @@ def frame_level(e, s, q: int, which: str, n: int, cascades: int = 0) -> np.ndarr
     return out.reshape(Un, 1 << n, V, C)
 
 
-def fluence_adjoint(e, s, gF, cascades: int = 0, env=None):
+def fluence_adjoint(e, s, gF, cascades: int = 0, env=None, top=None):
     """Gradient of sum(gF * F) w.r.t. (e, s), float64 (with the environment
-    map `env` as in fluence, held fixed)."""
+    map `env` or the top-level radiance `top` as in fluence, held fixed)."""
     if np.ndim(s) == 3:
         return _per_channel(lambda c, ec, sc, gc: fluence_adjoint(ec, sc, gc, cascades,
-                                                                  None if env is None else _env(env, len(e))[c:c + 1]),
+                                                                  None if env is None else _env(env, len(e))[c:c + 1],
+                                                                  None if top is None else _top(top, len(e))[:, :, c:c + 1]),
                             e, s, np.asarray(gF).reshape(np.shape(e)))
     e, s, C, H, W = _img(e, s)
     gF = np.ascontiguousarray(gF, dtype=np.float64).reshape(C, H, W)
     ge = np.zeros((C, H, W))
     gs = np.zeros((H, W))
-    if env is None:
+    if top is not None:
+        top = _top(top, C)
+        lib().orc_fluence_adjoint_top(_p(e), _p(s), _p(gF), C, W, H, cascades, _p(top), top.shape[1],
+                                      _p(ge), _p(gs))
+    elif env is None:
         lib().orc_fluence_adjoint(_p(e), _p(s), _p(gF), C, W, H, cascades, _p(ge), _p(gs))
     else:
         env = _env(env, C)

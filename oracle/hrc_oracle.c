@@ -332,22 +332,26 @@ static void frame_dir_to_image(int q, double du, double dv, double *dx, double *
 }
 
 /* Environment values of frame q: at level N, cone j' = j + 1/2 sees
- * A_N(j') E(direction of v_N(j')); an out-of-range lookup at level n < N
- * sees, through vacuum (nothing outside the grid absorbs or emits), the sum
- * of its two cones at level n + 1 (Eq. 14 / Eq. 15 with T = <0, 1>), i.e.
- * of its level-N descendants. */
-static void env_tables(Cascades *cs, int q, const double *env, int M)
+ * A_N(j') E(direction of v_N(j')) -- or, when the caller supplies the
+ * top-level radiance itself (footnote 1 of Sec. 4.2: R_N computed by some
+ * other method), top[q][j][c] (K entries per frame); an out-of-range lookup
+ * at level n < N sees, through vacuum (nothing outside the grid absorbs or
+ * emits), the sum of its two cones at level n + 1 (Eq. 14 / Eq. 15 with
+ * T = <0, 1>), i.e. of its level-N descendants. */
+static void env_tables(Cascades *cs, int q, const double *env, int M, const double *top, int K)
 {
     int C = cs->C, N = cs->N;
     for (int n = 0; n <= N; ++n) cs->Renv[n] = NULL;
-    if (!env) return;
+    if (!env && !top) return;
     for (int n = N; n >= 0; --n) {
         long I = 1L << n;
         cs->Renv[n] = (double *)calloc((size_t)I * C, sizeof(double));
         for (long j = 0; j < I; ++j)
             for (int c = 0; c < C; ++c) {
                 double v;
-                if (n == N) {
+                if (n == N && top) {
+                    v = top[((size_t)q * K + j) * C + c];
+                } else if (n == N) {
                     double dx, dy, s2 = (double)(1L << n);
                     frame_dir_to_image(q, s2, 2.0 * j + 1.0 - s2, &dx, &dy);
                     v = orc_arc(n, (int)j) * env_lookup(env, M, c, dx, dy);
@@ -371,13 +375,14 @@ static void merge(int C, const double *a, const double *b, double *out)
 }
 
 /* Algorithm 1, procedure HRC, for one frame.  Keeps every T and R level. */
-static void hrc_frame(const Frame *f, int cascades, int q, const double *env, int M, Cascades *cs)
+static void hrc_frame(const Frame *f, int cascades, int q, const double *env, int M, const double *top, int K,
+                      Cascades *cs)
 {
     int C = f->C;
     cs->C = C; cs->U = f->U; cs->V = f->V;
     cs->N = orc_levels(f->U, cascades);
     int N = cs->N;
-    env_tables(cs, q, env, M);
+    env_tables(cs, q, env, M, top, K);
     for (int n = 0; n <= N; ++n) {
         cs->Un[n] = level_cols(f->U, n);
         long K = (1L << n) + 1;
@@ -499,14 +504,14 @@ void orc_trace(const double *e, const double *s, int C, int W, int H,
 
 /* Algorithm 1, Lighting: F(x, y) = sum over quadrants of R_0([x+1, y], 0);
  * with an environment map env[C][M] (NULL: none), footnote 1 of Sec. 4.2. */
-void orc_fluence_env(const double *e, const double *s, int C, int W, int H, int cascades, const double *env, int M,
-                     double *F)
+static void fluence_outside(const double *e, const double *s, int C, int W, int H, int cascades, const double *env,
+                            int M, const double *top, int K, double *F)
 {
     memset(F, 0, sizeof(double) * (size_t)C * W * H);
     for (int q = 0; q < 4; ++q) {
         Frame f = frame_build(q, e, s, C, W, H);
         Cascades cs;
-        hrc_frame(&f, cascades, q, env, M, &cs);
+        hrc_frame(&f, cascades, q, env, M, top, K, &cs);
         for (long u = 0; u < f.U; ++u)
             for (long v = 0; v < f.V; ++v) {
                 long x, y;
@@ -520,9 +525,23 @@ void orc_fluence_env(const double *e, const double *s, int C, int W, int H, int 
     }
 }
 
+void orc_fluence_env(const double *e, const double *s, int C, int W, int H, int cascades, const double *env, int M,
+                     double *F)
+{
+    fluence_outside(e, s, C, W, H, cascades, env, M, NULL, 0, F);
+}
+
+/* The same with the top-level radiance top[4][K][C] given (cone j < 2^N of
+ * frame q at level N at top[(q K + j) C + c]). */
+void orc_fluence_top(const double *e, const double *s, int C, int W, int H, int cascades, const double *top, int K,
+                     double *F)
+{
+    fluence_outside(e, s, C, W, H, cascades, NULL, 0, top, K, F);
+}
+
 void orc_fluence(const double *e, const double *s, int C, int W, int H, int cascades, double *F)
 {
-    orc_fluence_env(e, s, C, W, H, cascades, NULL, 0, F);
+    fluence_outside(e, s, C, W, H, cascades, NULL, 0, NULL, 0, F);
 }
 
 /* One level of one frame, for level-by-level tests.  which = 0: T_n
@@ -533,7 +552,7 @@ long orc_frame_level(const double *e, const double *s, int C, int W, int H, int 
 {
     Frame f = frame_build(q, e, s, C, W, H);
     Cascades cs;
-    hrc_frame(&f, cascades, q, NULL, 0, &cs);
+    hrc_frame(&f, cascades, q, NULL, 0, NULL, 0, &cs);
     long cnt = -1;
     if (which == 0 && n >= 0 && n <= cs.N) {
         cnt = cs.Un[n] * ((1L << n) + 1) * f.V * (C + 1);
@@ -550,15 +569,15 @@ long orc_frame_level(const double *e, const double *s, int C, int W, int H, int 
 /* Gradient of sum(gF * F) with respect to e and s (the FP64 reverse of
  * orc_fluence: reverse fluence sum, reverse merge down, reverse merge up,
  * reverse trace).  ge, gs are overwritten. */
-void orc_fluence_adjoint_env(const double *e, const double *s, const double *gF, int C, int W, int H,
-                             int cascades, const double *env, int M, double *ge, double *gs)
+static void adjoint_outside(const double *e, const double *s, const double *gF, int C, int W, int H, int cascades,
+                            const double *env, int M, const double *top, int K, double *ge, double *gs)
 {
     memset(ge, 0, sizeof(double) * (size_t)C * W * H);
     memset(gs, 0, sizeof(double) * (size_t)W * H);
     for (int q = 0; q < 4; ++q) {
         Frame f = frame_build(q, e, s, C, W, H);
         Cascades cs;
-        hrc_frame(&f, cascades, q, env, M, &cs);
+        hrc_frame(&f, cascades, q, env, M, top, K, &cs);
         int N = cs.N;
         if (N < 1) { cascades_free(&cs); frame_free(&f); continue; }
         double *gT[ORC_MAXL + 1], *gR[ORC_MAXL + 1];
@@ -710,7 +729,19 @@ void orc_fluence_adjoint_env(const double *e, const double *s, const double *gF,
 void orc_fluence_adjoint(const double *e, const double *s, const double *gF, int C, int W, int H,
                          int cascades, double *ge, double *gs)
 {
-    orc_fluence_adjoint_env(e, s, gF, C, W, H, cascades, NULL, 0, ge, gs);
+    adjoint_outside(e, s, gF, C, W, H, cascades, NULL, 0, NULL, 0, ge, gs);
+}
+
+void orc_fluence_adjoint_env(const double *e, const double *s, const double *gF, int C, int W, int H,
+                             int cascades, const double *env, int M, double *ge, double *gs)
+{
+    adjoint_outside(e, s, gF, C, W, H, cascades, env, M, NULL, 0, ge, gs);
+}
+
+void orc_fluence_adjoint_top(const double *e, const double *s, const double *gF, int C, int W, int H,
+                             int cascades, const double *top, int K, double *ge, double *gs)
+{
+    adjoint_outside(e, s, gF, C, W, H, cascades, NULL, 0, top, K, ge, gs);
 }
 
 /* Eq. 1 by brute force: F(p) = sum_m (2 pi / M) L_r(p <- p + D w(theta_m)),

@@ -61,9 +61,10 @@ def _env_radiance(env, dx, dy):
 
 
 class _Frame:
-    def __init__(self, fe, fs, cascades, look=None):
+    def __init__(self, fe, fs, cascades, look=None, top=None):
         self.e, self.s = fe, fs            # e[C][U][V], s[U][V]
         self.look = look                   # (du, dv) -> radiance seen that way, or None
+        self.top = top                     # R_N of cone j at top[j] ([K][C]), or None
         self.C, self.U, self.V = fe.shape
         N = 0
         while (1 << N) < self.U:
@@ -141,6 +142,8 @@ class _Frame:
         """R_n(p, i), i = ip + 1/2 (Eqs. 14-17); R_N = 0, or with an
         environment map A_N(i) times the map along v_N(i) (footnote 1)."""
         if n >= self.N:
+            if self.top is not None:
+                return tuple(float(x) for x in self.top[ip])
             if self.look is None:
                 return (0.0,) * self.C
             s = 1 << n
@@ -163,10 +166,11 @@ class _Frame:
         return tuple(out)
 
 
-def fluence(e, s, cascades: int = 0, env=None) -> np.ndarray:
+def fluence(e, s, cascades: int = 0, env=None, top=None) -> np.ndarray:
     """F[C][H][W] from the recursive formulation (float64); `env` an
-    environment map [C][M] (R_N only; outside the grid the recursion runs on
-    through vacuum)."""
+    environment map [C][M], or `top` the top-level radiance [4][K][C] (cone
+    j of frame q at top[q][j]): R_N only, outside the grid the recursion runs
+    on through vacuum."""
     e = np.asarray(e, np.float64)
     s = np.asarray(s, np.float64)
     if e.ndim == 2:
@@ -185,8 +189,8 @@ def fluence(e, s, cascades: int = 0, env=None) -> np.ndarray:
                 x0, y0 = _image_of(q, W, H, 0, 0)
                 x1, y1 = _image_of(q, W, H, du, dv)
                 return _env_radiance(envq, x1 - x0, y1 - y0)
-        fr = _Frame(fe, fs, cascades, look)
-        if fr.N < 1 and look is None:
+        fr = _Frame(fe, fs, cascades, look, None if top is None else np.asarray(top, np.float64)[q])
+        if fr.N < 1 and look is None and top is None:
             continue
         for u in range(fr.U):
             for v in range(fr.V):

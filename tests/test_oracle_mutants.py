@@ -67,6 +67,10 @@ MUTANTS = {
         ("v = cs->Renv[n + 1][(size_t)(2 * j) * C + c] + cs->Renv[n + 1][(size_t)(2 * j + 1) * C + c];", "v = 0.0;")],
     "environment values without the arc weight": [
         ("v = orc_arc(n, (int)j) * env_lookup(env, M, c, dx, dy);", "v = env_lookup(env, M, c, dx, dy);")],
+    "top-level radiance of the next frame": [
+        ("v = top[((size_t)q * K + j) * C + c];", "v = top[((size_t)((q + 1) & 3) * K + j) * C + c];")],
+    "top-level radiance in reversed cone order": [
+        ("v = top[((size_t)q * K + j) * C + c];", "v = top[((size_t)q * K + ((1L << N) - 1 - j)) * C + c];")],
 }
 
 
@@ -126,6 +130,24 @@ def failed_pins(O):
             break
     bad += failed_blur_pins(O)
     bad += failed_env_pins(O)
+    bad += failed_top_pins(O)
+    return bad
+
+
+def failed_top_pins(O):
+    """The caller-supplied top-level radiance: a table built from a map
+    reproduces the map's fluence, and the uniform table in vacuum gives
+    2 pi E0."""
+    from test_oracle_top_pins import top_from_map
+    bad = []
+    e, s = scenes.random_scene(20, 6, 2, 4)
+    env = np.random.default_rng(4).uniform(0, 2, size=(2, 24))
+    a = O.fluence(e, s, env=env)
+    if np.max(np.abs(a - O.fluence(e, s, top=top_from_map(env, 20, 6)))) > 1e-12 * np.max(np.abs(a)):
+        bad.append("top-map")
+    F = O.fluence(np.zeros((1, 11, 13)), np.zeros((11, 13)), top=top_from_map(np.full((1, 8), 1.7), 13, 11))
+    if np.max(np.abs(F - 2 * math.pi * 1.7)) > 1e-12:
+        bad.append("top-uniform")
     return bad
 
 
