@@ -240,6 +240,23 @@ hrc_status hrc_set_channel_extinction(hrc_ctx *ctx, int per_channel);
  * outside [1, 2^20]; a forward must run again before a backward. */
 hrc_status hrc_set_environment(hrc_ctx *ctx, const float *env, int M);
 
+/* Top-level radiance supplied by the caller (footnote 1 of Sec. 4.2: the
+ * light from outside the grid enters only through R_N, which another method
+ * -- cone tracing an offscreen scene, a sky model -- may compute).  top is a
+ * device array [4][K][C] (fp32): top[(q K + j) C + c] is R_N of cone j of
+ * quadrant frame q at its top level N_q (j < 2^N_q; K >= 2^N for the largest
+ * N of the context), i.e. the radiance integrated over the cone between the
+ * frame directions v_N(j) and v_N(j + 1), v_N(k) = (2^N, 2k - 2^N) in frame
+ * coordinates (u along +x, -x, +y, -y image axes and v along +y, +y, +x, +x
+ * for q = 0 .. 3).  The values do not depend on the probe; an R lookup
+ * outside the grid at a lower level sees the sum of its level-N
+ * descendants, as with an environment map, which this call replaces (and
+ * hrc_set_environment replaces it; either with NULL removes both).  The
+ * values are held fixed in the adjoint.  Synchronous; allocates the table
+ * once.  With per-channel extinction, channel c takes its own values.
+ * HRC_EINVAL for a batched context or K out of range. */
+hrc_status hrc_set_top_radiance(hrc_ctx *ctx, const float *top, int K);
+
 /* Multiple diffuse bounces (Sec. 4.2: the output fluence fed into another
  * iteration of the method; Fig. 14).  Bounce 0 is hrc_fluence on
  * `emission`; bounce k + 1 runs it on

@@ -33,6 +33,7 @@ SIGNATURES = [
     ("hrc_set_cross_blur", _i, [_vp, _i, ctypes.c_float]),
     ("hrc_get_cross_blur", _i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
     ("hrc_set_environment", _i, [_vp, _vp, _i]),
+    ("hrc_set_top_radiance", _i, [_vp, _vp, _i]),
     ("hrc_set_channel_extinction", _i, [_vp, _i]),
     ("hrc_reserve_bounces", _i, [_vp, _i]),
     ("hrc_fluence_bounces", _i, [_vp, _vp, _vp, _vp, _i, _vp]),
@@ -153,6 +154,10 @@ def hrc_get_cross_blur(ctx):
 
 def hrc_set_environment(ctx, env, M: int):
     check(load().hrc_set_environment(ctx, ptr(env), M), ctx)
+
+
+def hrc_set_top_radiance(ctx, top, K: int):
+    check(load().hrc_set_top_radiance(ctx, ptr(top) if top is not None else None, K), ctx)
 
 
 def hrc_set_channel_extinction(ctx, per_channel: bool):

@@ -159,6 +159,21 @@ class HRC:
         self._borrowed = (None, None, 0, 0)
         self._bounced = None
 
+    def set_top_radiance(self, top=None) -> None:
+        """Top-level radiance R_N supplied by the caller (footnote 1 of Sec.
+        4.2): a CUDA float32 tensor [4][K][C], cone j of frame q at
+        [q][j][c] (see hrc_set_top_radiance); None removes it."""
+        if top is None:
+            _lib.hrc_set_environment(self.ctx, None, 0)
+            self._env = None
+        else:
+            top = _dev_tensor(top, torch.float32, (4, top.shape[1], self.C), "top")
+            self._stream()
+            _lib.hrc_set_top_radiance(self.ctx, top, top.shape[1])
+            self._env = top
+        self._borrowed = (None, None, 0, 0)
+        self._bounced = None
+
     # -- multiple bounces (hrc_fluence_bounces) ----------------------------
     def reserve_bounces(self, max_bounces: int) -> None:
         """Context buffers for up to `max_bounces` bounces (hrc_reserve_bounces)."""

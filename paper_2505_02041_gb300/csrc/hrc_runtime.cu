@@ -215,6 +215,12 @@ struct hrc_ctx {
     bool env_on = false;
     float *env_map = nullptr;
     int env_M = 0, env_pitch = 0;
+    // or the top-level radiance supplied by the caller: [C][4 K] per channel
+    // (channel c's [4][K] table, for per-channel contexts)
+    bool env_top = false;
+    float *top_map = nullptr;
+    int top_K = 0;
+    size_t top_cap = 0;
     // per-channel extinction: one single-channel context per channel (the
     // method separates exactly by channel once the extinction does), on this
     // context's stream; channel planes whose address is not 16-byte aligned
@@ -618,6 +624,7 @@ hrc_status hrc_destroy(hrc_ctx *ctx) {
     cudaFree(ctx->bounce_buf);
     cudaFree(ctx->env_tab);
     cudaFree(ctx->env_map);
+    cudaFree(ctx->top_map);
     cudaFree(ctx->chan_stage);
     for (hrc_ctx *k : ctx->chan) hrc_destroy(k);
     for (auto &g : ctx->graphs)
@@ -1062,8 +1069,10 @@ hrc_status hrc_set_channel_extinction(hrc_ctx *ctx, int per_channel) {
             if (st == HRC_OK) st = hrc_set_backward_recompute(k, ctx->bwd_recompute ? 1 : 0);
             if (st == HRC_OK && ctx->blur_buf) st = hrc_set_cross_blur(k, ctx->blur ? 1 : 0, ctx->blur_thr);
             if (st == HRC_OK && ctx->bounce_buf) st = hrc_reserve_bounces(k, ctx->bounce_cap);
-            if (st == HRC_OK) st = hrc_set_timing(k, ctx->rec.on ? 1 : 0);
-            if (st == HRC_OK && ctx->env_on)
+            if (st == HRC_OK) st = hrc_set_timing(k, ctx->timing_mode);
+            if (st == HRC_OK && ctx->env_on && ctx->env_top)
+                st = hrc_set_top_radiance(k, ctx->top_map + (size_t)c * 4 * ctx->top_K, ctx->top_K);
+            else if (st == HRC_OK && ctx->env_on)
                 st = hrc_set_environment(k, ctx->env_map + (size_t)c * ctx->env_pitch, ctx->env_M);
             if (st != HRC_OK) {
                 std::string msg = k ? k->err : g_create_error;
@@ -1121,9 +1130,58 @@ hrc_status hrc_set_environment(hrc_ctx *ctx, const float *env, int M) {
         if (st2 != HRC_OK) return fail(ctx, st2, ctx->chan[c]->err);
     }
     ctx->env_on = env != nullptr;
+    ctx->env_top = false;
     apply_env(ctx);
     clear_graphs(ctx);     // the graphs hold the plans by value
     ctx->have_fwd = false; // levels and fluence of an earlier forward saw the old map
+    ctx->have_bounce = false;
+    return HRC_OK;
+}
+
+hrc_status hrc_set_top_radiance(hrc_ctx *ctx, const float *top, int K) {
+    hrc_status st = check_ctx(ctx);
+    if (st != HRC_OK) return st;
+    if (ctx->batched) return fail(ctx, HRC_EINVAL, "hrc_set_top_radiance: single-scene contexts only");
+    if (!top) return hrc_set_environment(ctx, nullptr, 0);
+    const int need = 1 << plan_nmax(ctx->plan);
+    if (K < need || K > (1 << 20))
+        return fail(ctx, HRC_EINVAL, "hrc_set_top_radiance: K must be in [2^N, 2^20] with N = " +
+                                         std::to_string(plan_nmax(ctx->plan)));
+    if (!ctx->env_tab) {
+        const size_t bytes = env_table_bytes(ctx->plan);
+        cudaError_t e = cudaMalloc(&ctx->env_tab, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->env_tab = nullptr;
+            return fail(ctx, HRC_ENOMEM, "hrc_set_top_radiance: table does not fit");
+        }
+    }
+    cudaError_t e = launch_env_top(ctx->plan, top, K, ctx->env_tab, ctx->stream);
+    // keep a channel-major copy [C][4 K] for the per-channel contexts
+    const size_t cap = (size_t)ctx->C * 4 * K;
+    if (e == cudaSuccess && cap > ctx->top_cap) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->top_map);
+        ctx->top_map = nullptr;
+        ctx->top_cap = 0;
+        e = cudaMalloc(&ctx->top_map, sizeof(float) * cap);
+        if (e == cudaSuccess) ctx->top_cap = cap;
+    }
+    for (int c = 0; c < ctx->C && e == cudaSuccess; ++c)
+        e = cudaMemcpy2DAsync(ctx->top_map + (size_t)c * 4 * K, sizeof(float), top + c, sizeof(float) * ctx->C,
+                              sizeof(float), (size_t)4 * K, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hrc_set_top_radiance");
+    ctx->top_K = K;
+    for (int c = 0; c < (int)ctx->chan.size(); ++c) {   // channel c sees its own table
+        hrc_status st2 = hrc_set_top_radiance(ctx->chan[c], ctx->top_map + (size_t)c * 4 * K, K);
+        if (st2 != HRC_OK) return fail(ctx, st2, ctx->chan[c]->err);
+    }
+    ctx->env_on = true;
+    ctx->env_top = true;
+    apply_env(ctx);
+    clear_graphs(ctx);     // the graphs hold the plans by value
+    ctx->have_fwd = false;
     ctx->have_bounce = false;
     return HRC_OK;
 }

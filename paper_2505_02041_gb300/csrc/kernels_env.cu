@@ -1,5 +1,6 @@
 // kernels_env.cu -- environment map (footnote 1 of Sec. 4.2: with no
-// occluders outside the grid, R_N is the map looked up along v_N(i)).
+// occluders outside the grid, R_N is the map looked up along v_N(i)), or
+// the top-level radiance R_N itself supplied by the caller.
 //
 // The map env[c][m] holds the radiance seen along the image-space look
 // angle theta_m = 2 pi (m + 1/2) / M, theta measured from +x towards +y
@@ -56,6 +57,20 @@ __global__ void __launch_bounds__(128) k_env_leaves(Plan pl, const float *__rest
     td[(long long)q * S * C + ((long long)(1 << N) + m) * C + c] = a * env_at(env, M, c, dx, dy);
 }
 
+// Level-N entries supplied by the caller (footnote 1 of Sec. 4.2: R_N from
+// another method): top[(q K + m) C + c] for cone m < 2^N of frame q.
+__global__ void __launch_bounds__(128) k_env_top(Plan pl, const float *__restrict__ top, int K, int C, int S,
+                                                 double *__restrict__ td) {
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int q = (int)(idx / ((long long)S * C));
+    if (q >= 4) return;
+    const int rem = (int)(idx - (long long)q * S * C);
+    const int m = rem / C, c = rem - m * C;
+    const int N = pl.q[q].N;
+    if (m >= (1 << N)) return;
+    td[(long long)q * S * C + ((long long)(1 << N) + m) * C + c] = (double)top[((long long)q * K + m) * C + c];
+}
+
 // Every entry: the sum of its level-N descendants (in increasing order),
 // read from the leaves; the float copy beside it.
 __global__ void __launch_bounds__(128) k_env_table(Plan pl, int C, int S, double *__restrict__ td,
@@ -94,6 +109,18 @@ cudaError_t launch_env_table(const Plan &pl, const float *env, int M, void *tabl
     const int S = (int)(stride / pl.C);
     const unsigned grid = (unsigned)((total + 127) / 128);
     k_env_leaves<<<grid, 128, 0, st>>>(pl, env, M, pl.C, S, td);
+    k_env_table<<<grid, 128, 0, st>>>(pl, pl.C, S, td, tf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_env_top(const Plan &pl, const float *top, int K, void *table, cudaStream_t st) {
+    const long long stride = env_table_stride(pl);
+    const long long total = 4 * stride;
+    double *td = reinterpret_cast<double *>(table);
+    float *tf = reinterpret_cast<float *>(td + total);
+    const int S = (int)(stride / pl.C);
+    const unsigned grid = (unsigned)((total + 127) / 128);
+    k_env_top<<<grid, 128, 0, st>>>(pl, top, K, pl.C, S, td);
     k_env_table<<<grid, 128, 0, st>>>(pl, pl.C, S, td, tf);
     return cudaGetLastError();
 }

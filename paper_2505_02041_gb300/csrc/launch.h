@@ -231,6 +231,8 @@ cudaError_t launch_bounce_adj(const Plan &pl, bool first, bool has_prev, const v
 long long env_table_stride(const Plan &pl);
 size_t env_table_bytes(const Plan &pl);
 cudaError_t launch_env_table(const Plan &pl, const float *env, int M, void *table, cudaStream_t st);
+// The same table from caller-supplied level-N values top[4][K][C].
+cudaError_t launch_env_top(const Plan &pl, const float *top, int K, void *table, cudaStream_t st);
 
 // Dense fp32 copy of level n of frame q (which = 0: T_n, 1: R_n).
 cudaError_t launch_copy_level(const Plan &pl, int q, int which, int n, float *dst, cudaStream_t st);

@@ -172,3 +172,65 @@ def test_env_full_size_workload():
     h.set_environment(to_dev(env))
     F = h.forward(to_dev(e), to_dev(s)).cpu().numpy()
     assert_fp32(F, oracle.fluence(e, s, env=env))
+
+
+# ---------------------------------------------------------------------------
+# Top-level radiance supplied by the caller (hrc_set_top_radiance): R_N of
+# every cone of every frame given directly, e.g. from cone tracing.
+# ---------------------------------------------------------------------------
+def _top(W, H, C, seed):
+    K = 1
+    while K < max(W, H):
+        K *= 2
+    return scenes.rng(seed).uniform(0.0, 1.0, size=(4, K, C)).astype(np.float32)
+
+
+@pytest.mark.parametrize("W,H,C,seed", [(16, 16, 1, 0), (37, 23, 2, 1), (20, 6, 3, 2), (1, 6, 1, 3), (64, 48, 3, 4)])
+def test_top_radiance_forward_and_backward_vs_oracle(W, H, C, seed):
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC
+    e, s = scenes.random_scene(W, H, C, seed)
+    top = _top(W, H, C, 200 + seed)
+    h = HRC(W, H, C)
+    h.set_top_radiance(to_dev(top))
+    ed, sd = to_dev(e), to_dev(s)
+    for cfg in [(0, 1, 128, 0, 0), (1, 4, 64, 1, 1), (0, 4, 128, 0, 2)]:
+        h.set_launch_config(*cfg)
+        F = h.forward(ed, sd).cpu().numpy()
+        assert_fp32(F, oracle.fluence(e, s, top=top), msg=cfg)
+    gF = scenes.rng(300 + seed).normal(size=e.shape).astype(np.float32)
+    ge, gs = h.backward(to_dev(gF))
+    ge_r, gs_r = oracle.fluence_adjoint(e, s, gF, top=top)
+    assert err_max(ge.cpu().numpy(), ge_r) <= 1e-4 and err_max(gs.cpu().numpy(), gs_r) <= 1e-4
+
+
+def test_top_radiance_from_a_map_equals_the_map():
+    """A table built from a map (the cone's arc times the map along the
+    cone's middle direction) gives the map's fluence."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC
+    from test_oracle_top_pins import top_from_map
+    e, s = scenes.random_scene(48, 40, 2, 5)
+    env = _env(2, 32, 6)
+    h = HRC(48, 40, 2)
+    ed, sd = to_dev(e), to_dev(s)
+    h.set_environment(to_dev(env))
+    Fm = h.forward(ed, sd).cpu().numpy()
+    h.set_top_radiance(to_dev(top_from_map(env.astype(np.float64), 48, 40).astype(np.float32)))
+    Ft = h.forward(ed, sd).cpu().numpy()
+    assert_fp32(Ft, Fm)
+    h.set_top_radiance(None)
+    assert_fp32(h.forward(ed, sd).cpu().numpy(), oracle.fluence(e, s))
+
+
+def test_top_radiance_with_per_channel_extinction():
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC
+    e, s = scenes.random_scene(33, 21, 3, 7)
+    S = np.stack([s, 0.5 * s, 2.0 * s]).astype(np.float32)
+    top = _top(33, 21, 3, 8)
+    h = HRC(33, 21, 3)
+    h.set_channel_extinction(True)
+    h.set_top_radiance(to_dev(top))
+    F = h.forward(to_dev(e), to_dev(S)).cpu().numpy()
+    assert_fp32(F, oracle.fluence(e, S, top=top))
