@@ -727,13 +727,103 @@ __device__ __forceinline__ void body_merge_down_bulk(const Plan &pl, const RowSp
 }
 
 
+// R_0^q(x, 0, v) and R_0^q(x, 0, v + 1) (v even) added to a[0] / a[1]: the
+// n = 0 case of merge_down_entry for a pair of v, with the same arithmetic
+// per entry.  At odd x the far run starts at the odd offset v -+ 1 and is
+// read as the aligned pairs on either side of it; v + 1 may lie past V
+// (inside the padded row): that entry is computed and never used.
+template <int P, int C, bool ENV>
+__device__ __forceinline__ void r0_pair_add(const Plan &pl, int q, int x, int v, typename Prec<P>::A (&a)[2][C]) {
+    using A = typename Prec<P>::A;
+    const QuadGeom &g = pl.q[q];
+    if (g.N < 1 || x >= g.U) {                 // the probe at u + 1 is outside: the environment
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const A ev = renv<P, C, ENV>(pl, q, 0, 0, c);
+            a[0][c] += ev;
+            a[1][c] += ev;
+        }
+        return;
+    }
+    const bool top = g.N <= 1;                  // R_1 is R_N: 0, or the environment map
+    const A Ap = arc<P>(pl, 1, 1), Am = arc<P>(pl, 1, 0);
+    const uint64_t pol = l2_evict_first();      // T rows: read once from HBM
+    A acc[2][C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[0][c] = acc[1][c] = A(0);
+    if (x & 1) {                                // Eq. 14 at n = 0: k = j = 1, 0
+        const TLevel<P, C> T0(pl, q, 0);
+        const int xq = (x + 1) >> 1;
+        const bool rq_ok = !top && xq < g.Un[1];
+        const RLevel<P, C> R1(pl, q, rq_ok ? 1 : 0);
+#pragma unroll
+        for (int j = 1; j >= 0; --j) {
+            const A Aj = j ? Ap : Am;
+            Iv<P, C> t0, t1;
+            T0.load2_ef(x, j, v, pol, t0, t1);
+            const A tr0 = t0.trans(), tr1 = t1.trans();
+            const int vq = v + 2 * j - 1;       // odd
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const A ev = renv<P, C, ENV>(pl, q, 1, j, c);
+                A r0 = ev, r1 = ev, lo, hi;
+                if (rq_ok) {
+                    if (vq >= 0 && vq < g.V) {
+                        R1.load2(xq, j, c, vq - 1, lo, hi);
+                        r0 = hi;
+                    }
+                    if (vq + 1 < g.V) {
+                        R1.load2(xq, j, c, vq + 1, lo, hi);
+                        r1 = lo;
+                    }
+                }
+                acc[0][c] += fma(Aj, t0.L[c], tr0 * r0);
+                acc[1][c] += fma(Aj, t1.L[c], tr1 * r1);
+            }
+        }
+    } else {                                    // Eqs. 15-17 at n = 0: k = 2, 0 and j = 1, 0
+        const TLevel<P, C> T1(pl, q, 1);
+        const int x2 = x >> 1;
+        const bool r1_ok = !top && x2 + 1 < g.Un[1];
+        const RLevel<P, C> R1(pl, q, top ? 0 : 1);
+#pragma unroll
+        for (int j = 1; j >= 0; --j) {
+            const A Aj = j ? Ap : Am;
+            Iv<P, C> t0, t1;
+            T1.load2_ef(x2, 2 * j, v, pol, t0, t1);
+            const A tr0 = t0.trans(), tr1 = t1.trans();
+            const int vq = v + 4 * j - 2;       // even
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const A ev = renv<P, C, ENV>(pl, q, 1, j, c);
+                A n0 = ev, n1 = ev, f0 = ev, f1 = ev;
+                if (!top) R1.load2(x2, j, c, v, n0, n1);
+                if (r1_ok && vq >= 0 && vq < g.V) {
+                    R1.load2(x2 + 1, j, c, vq, f0, f1);
+                    if (vq + 1 >= g.V) f1 = ev;
+                }
+                acc[0][c] += A(0.5) * (n0 + fma(Aj, t0.L[c], tr0 * f0));
+                acc[1][c] += A(0.5) * (n1 + fma(Aj, t1.L[c], tr1 * f1));
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        a[0][c] += acc[0][c];
+        a[1][c] += acc[1][c];
+    }
+}
+
 // F[c][y][x] = sum_q R_0^q(u_q + 1, v_q)   (Algorithm 1, Lighting, +1 offset),
-// with R_0 computed in place (merge_down_entry at n = 0): R_0 feeds only this
-// sum, so it is never stored.  One block per 32 x 32 image tile (any
-// multiple of 32 threads).  Frames q0, q1 run v along image y and q2, q3 along image x, so the
-// first pair is computed with lanes along y, parked in shared memory, and the
-// second pair with lanes along x adds to it and writes F coalesced; the sum
-// runs in frame order q0 + q1 + q2 + q3.
+// with R_0 computed in place (r0_pair_add): R_0 feeds only this sum, so it
+// is never stored.  One block per 32 x 32 image tile (any multiple of 32
+// threads).  Frames q0, q1 run v along image y and q2, q3 along image x, so
+// the first pair is computed with v along y, parked in shared memory, and the
+// second pair with v along x adds to it and writes F; the sum runs in frame
+// order q0 + q1 + q2 + q3.  A thread takes two consecutive pixels along v
+// (one 2-wide access per plane and row), a half-warp one tile line; the two
+// half-warps take lines 2 apart, so the warp's x = u + 1 share one parity and
+// it runs one branch of the merge.
 template <int P, int C>
 constexpr size_t fluence_smem() { return sizeof(typename Prec<P>::A) * C * 32 * 33; }
 
@@ -744,69 +834,56 @@ __device__ __forceinline__ void body_fluence(const Plan &pl, OUT *__restrict__ F
     const int W = pl.W, H = pl.H;
     const int x0 = bx * 32, y0 = by * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // R_0^q(u + 1, v) of the pixel (x, y), added to a[]
-    auto add_r0 = [&](int q, int x, int y, A (&a)[C]) {
-        const QuadGeom &g = pl.q[q];
+    const int hl = lane & 15, half = lane >> 4;
+    // line pair p = 0 .. 15 -> tile lines 4 (p >> 1) + (p & 1) + {0, 2}
+    auto line = [&](int p) { return 4 * (p >> 1) + (p & 1) + 2 * half; };
+    auto add_frame = [&](int q, int x, int y, A (&a)[2][C]) {
         int u, v;
         image_to_frame(q, W, H, x, y, u, v);
-        if (g.N < 1 || u + 1 >= g.U) {             // the probe at u + 1 is outside: the environment
-#pragma unroll
-            for (int c = 0; c < C; ++c) a[c] += renv<P, C, ENV>(pl, q, 0, 0, c);
-            return;
-        }
-        A r[1][C];
-        merge_down_entry<P, C, 1, ENV>(pl, q, 0, u + 1, 0, v, r);
-#pragma unroll
-        for (int c = 0; c < C; ++c) a[c] += r[0][c];
+        r0_pair_add<P, C, ENV>(pl, q, u + 1, v, a);
     };
-    // two columns per iteration (cidx and cidx + nw, of equal parity): their
-    // loads are independent, so a thread has twice as many in flight
-    for (int cidx = warp; cidx < 32; cidx += 2 * nw) {     // q0, q1: lanes along y
-        const int cb = cidx + nw, y = y0 + lane;
-        A a[C], b[C];
+    for (int p = warp; p < 16; p += nw) {       // q0, q1: pixels (x, y), (x, y + 1)
+        const int ca = line(p), y = y0 + 2 * hl;
+        A a[2][C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) a[c] = b[c] = A(0);
-        if (y < H) {
-            if (x0 + cidx < W) {
-                add_r0(0, x0 + cidx, y, a);
-                add_r0(1, x0 + cidx, y, a);
-            }
-            if (cb < 32 && x0 + cb < W) {
-                add_r0(0, x0 + cb, y, b);
-                add_r0(1, x0 + cb, y, b);
-            }
+        for (int c = 0; c < C; ++c) a[0][c] = a[1][c] = A(0);
+        if (y < H && x0 + ca < W) {
+            add_frame(0, x0 + ca, y, a);
+            add_frame(1, x0 + ca, y, a);
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            tile[c][lane][cidx] = a[c];
-            if (cb < 32) tile[c][lane][cb] = b[c];
+            tile[c][2 * hl][ca] = a[0][c];
+            tile[c][2 * hl + 1][ca] = a[1][c];
         }
     }
     __syncthreads();
     const long long HW = (long long)W * H;
-    for (int cidx = warp; cidx < 32; cidx += 2 * nw) {     // q2, q3: lanes along x
-        const int cb = cidx + nw, x = x0 + lane;
-        if (x >= W) continue;
-        const bool ua = y0 + cidx < H, ub = cb < 32 && y0 + cb < H;
-        A a[C], b[C];
+    // F rows of even width from an aligned base take 2-wide stores
+    const bool wide = (W & 1) == 0 && (reinterpret_cast<uintptr_t>(F) & (2 * sizeof(OUT) - 1)) == 0;
+    auto put = [&](int y, int x, const A (&a)[2][C]) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            a[c] = ua ? tile[c][cidx][lane] : A(0);
-            b[c] = ub ? tile[c][cb][lane] : A(0);
+            OUT *o = F + c * HW + (long long)y * W + x;
+            if (wide) {
+                st2(o, a[0][c], a[1][c]);
+            } else {
+                o[0] = (OUT)a[0][c];
+                if (x + 1 < W) o[1] = (OUT)a[1][c];
+            }
         }
-        if (ua) {
-            add_r0(2, x, y0 + cidx, a);
-            add_r0(3, x, y0 + cidx, a);
-        }
-        if (ub) {
-            add_r0(2, x, y0 + cb, b);
-            add_r0(3, x, y0 + cb, b);
-        }
+    };
+    for (int p = warp; p < 16; p += nw) {       // q2, q3: pixels (x, y), (x + 1, y)
+        const int ra = line(p), x = x0 + 2 * hl;
+        if (x >= W || y0 + ra >= H) continue;
+        A a[2][C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            if (ua) F[c * HW + (long long)(y0 + cidx) * W + x] = (OUT)a[c];
-            if (ub) F[c * HW + (long long)(y0 + cb) * W + x] = (OUT)b[c];
-        }
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) a[e][c] = tile[c][ra][2 * hl + e];
+        add_frame(2, x, y0 + ra, a);
+        add_frame(3, x, y0 + ra, a);
+        put(y0 + ra, x, a);
     }
 }
 

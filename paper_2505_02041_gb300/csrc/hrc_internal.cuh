@@ -45,10 +45,11 @@ struct QuadGeom {
 struct Plan {
     int W, H, C, prec;
     int sched;                       // 0: each launch covers all four frames; 1: frame by frame
-    int mgroups;                     // merge kernels: element groups per thread (1 or 2)
+    int mgroups;                     // merge up: 1 = a pair of v per thread, 2 = two pairs, 4 = four consecutive v
     int mthreads;                    // merge kernels: threads per block for paired-v bodies
     int vmajor;                      // merge kernels: 1 = v-blocks of a row are adjacent in launch order
-    int mdown;                       // merge down: 0 = per-thread loads, 1 = rows staged by bulk copies
+    int mdown;                       // merge down: 0 = per-thread loads, 1 = rows staged by bulk copies,
+                                     // 2 = every level in one persistent launch
     long long bulk_limit_ns;         // bound of a bulk-copy barrier wait
     int bulk_extra_tx;               // test hook: bytes expected but never copied (0 in use)
     long long arcs_off;              // byte offset: float A[2^n + j] for level n (n >= 1)
@@ -181,6 +182,12 @@ template <int P, int C> struct Iv {
     __device__ __forceinline__ A trans() const { return Prec<P>::LOG ? fexp(-t) : t; }
 };
 
+// A product the compiler may not contract into a later addition: the blend
+// (Eq. 20) adds two merged transmittances, and an FMA formed there in one
+// kernel and not in another would round the same entry differently.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Merge (Eq. 7): <r_n + t_n r_f, t_n t_f>
 template <int P, int C>
 __device__ __forceinline__ Iv<P, C> merge(const Iv<P, C> &n, const Iv<P, C> &f) {
@@ -188,7 +195,7 @@ __device__ __forceinline__ Iv<P, C> merge(const Iv<P, C> &n, const Iv<P, C> &f) 
     typename Prec<P>::A tn = n.trans();
 #pragma unroll
     for (int c = 0; c < C; ++c) r.L[c] = fma(tn, f.L[c], n.L[c]);
-    r.t = Prec<P>::LOG ? n.t + f.t : n.t * f.t;
+    r.t = Prec<P>::LOG ? n.t + f.t : mul_rn(n.t, f.t);
     return r;
 }
 
@@ -301,6 +308,24 @@ template <class H> __device__ __forceinline__ float ld1_ef_16(const H *p, uint64
 }
 __device__ __forceinline__ float ld1_ef(const __half *p, uint64_t pol) { return ld1_ef_16(p, pol); }
 __device__ __forceinline__ float ld1_ef(const __nv_bfloat16 *p, uint64_t pol) { return ld1_ef_16(p, pol); }
+// entries p[0], p[1] (p 2-element aligned) with an L2 policy
+__device__ __forceinline__ void ld2_ef(const float *p, uint64_t pol, float &x, float &y) {
+    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(x), "=f"(y) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld2_ef(const double *p, uint64_t, double &x, double &y) { ld2(p, x, y); }
+template <class H2> __device__ __forceinline__ void ld2_ef_16(const void *p, uint64_t pol, float &x, float &y) {
+    unsigned u;
+    asm volatile("ld.global.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(u) : "l"(p), "l"(pol));
+    const H2 t = *reinterpret_cast<const H2 *>(&u);
+    x = __low2float(t);
+    y = __high2float(t);
+}
+__device__ __forceinline__ void ld2_ef(const __half *p, uint64_t pol, float &x, float &y) {
+    ld2_ef_16<__half2>(p, pol, x, y);
+}
+__device__ __forceinline__ void ld2_ef(const __nv_bfloat16 *p, uint64_t pol, float &x, float &y) {
+    ld2_ef_16<__nv_bfloat162>(p, pol, x, y);
+}
 
 // ---------------------------------------------------------------------------
 // Level addressing
@@ -392,6 +417,13 @@ template <int P, int C> struct TLevel {
         for (int c = 0; c < C; ++c) r.L[c] = ld1_ef(reinterpret_cast<const SL *>(g) + (long long)c * Vs + v, pol);
         r.t = ld1_ef(reinterpret_cast<const ST *>(g + (long long)C * Vs * sizeof(SL)) + v, pol);
         return r;
+    }
+    // entries v and v+1 (v even), loaded with an L2 policy
+    __device__ __forceinline__ void load2_ef(int x, int k, int v, uint64_t pol, Iv<P, C> &a, Iv<P, C> &b) const {
+        const char *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) ld2_ef(reinterpret_cast<const SL *>(g) + (long long)c * Vs + v, pol, a.L[c], b.L[c]);
+        ld2_ef(reinterpret_cast<const ST *>(g + (long long)C * Vs * sizeof(SL)) + v, pol, a.t, b.t);
     }
     // entries v .. v+3 (v a multiple of 4; v + 3 < Vs)
     __device__ __forceinline__ void load4(int x, int k, int v, Iv<P, C> (&r)[4]) const {

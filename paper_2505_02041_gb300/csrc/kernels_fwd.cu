@@ -307,10 +307,11 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         }
         dim3 grid((pl.W + 31) / 32, (pl.H + 31) / 32);
         rec->begin(K_FLUENCE_SUM, 0, by);
-        // 128 threads: every tile of a 1024^2 image is resident at once;
-        // grids of fewer than 600 tiles (about 4 per SM; 512^2 and below) take 512
-        // threads per tile, so that the GPU still holds enough loads in flight
-        const int ft = (long long)grid.x * grid.y < 600 ? 512 : 128;
+        // 256 threads (two pixels each, one line pair per warp) on large
+        // grids; grids of fewer than 600 tiles (about 4 per SM; 512^2 and
+        // below) take 512 threads per tile, so that the GPU still holds
+        // enough loads in flight
+        const int ft = (long long)grid.x * grid.y < 600 ? 512 : 256;
         if (P == P_FP64) {
             if (env) k_fluence<P, C, double, true><<<grid, ft, 0, st>>>(pl, (double *)F);
             else k_fluence<P, C, double, false><<<grid, ft, 0, st>>>(pl, (double *)F);
