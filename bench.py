@@ -747,7 +747,10 @@ def run_ours(args):
         h.close()
         del h, e, s, F, gF, gE, gS, m
         torch.cuda.empty_cache()
-        line["batched"] = bench_batched(args, dev)
+        # 64 scenes of sizes drawn from {128, ..., 2048}^2 (the 2048^2 ones
+        # hold ~80 % of the work), and 256 small scenes from {64, 128, 256}^2
+        line["batched"] = bench_batched(args, dev, scenes.batched_sizes(64, 4), 400)
+        line["batched_small"] = bench_batched(args, dev, scenes.batched_sizes(256, 5, (64, 128, 256)), 1000)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
@@ -755,22 +758,20 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def bench_batched(args, dev):
-    """64 scenes of sizes drawn from {128, 256, 512, 1024, 2048}^2 (seed 4),
-    C = 3, fog / disks / rectangles as the 512^2 workload (seeds 400+i),
-    bf16 interval storage: forward and forward+backward of the whole batch,
-    each pass one graph-replayed launch sequence.  Beside it, the same 64
-    scenes as a loop of single-scene hrc_fluence (+ hrc_fluence_backward)
-    calls in the same precision: one autotuned context per size, each
-    scene's inputs copied into that context's fixed buffers (so that its
-    graph is replayed) and its outputs copied out, every copy inside the
-    timed region."""
+def bench_batched(args, dev, sizes, seed0):
+    """A batch of square scenes of the given sizes, C = 3, fog / disks /
+    rectangles as the 512^2 workload (seeds seed0 + i), bf16 interval
+    storage: forward and forward+backward of the whole batch, each pass one
+    graph-replayed launch sequence.  Beside it, the same scenes as a loop of
+    single-scene hrc_fluence (+ hrc_fluence_backward) calls in the same
+    precision: one autotuned context per size, each scene's inputs copied
+    into that context's fixed buffers (so that its graph is replayed) and
+    its outputs copied out, every copy inside the timed region."""
     import torch
     from paper_2505_02041_gb300 import BatchedHRC, HRC, _lib, scenes
-    sizes = scenes.batched_sizes(64, 4)
     es, ss = [], []
     for i, X in enumerate(sizes):
-        e, s = scenes.scene_disks_rects_fog(X, X, 3, 400 + i)
+        e, s = scenes.scene_disks_rects_fog(X, X, 3, seed0 + i)
         es.append(torch.from_numpy(e))
         ss.append(torch.from_numpy(s))
     n = max(3, min(args.steps, 5))
