@@ -142,6 +142,63 @@ def bench_environment(h, fwd, fwd_bwd, timed, steps=10):
     return out
 
 
+def bench_autograd(h, e, s, steps=10, warmup=3):
+    """Gradient steps of an inverse-rendering loop through the autograd
+    function `fluence` (forward hrc_fluence, backward hrc_fluence_backward):
+    loss = mean((F(e) - F_target)^2), F_target the workload's own fluence,
+    Adam on the emission from half its value.  `steady`: the plain loop,
+    whose fresh output and gradient tensors come back from the caching
+    allocator at recurring addresses; `moving`: every step differentiates
+    through copies of its inputs that stay alive for 16 steps, so every step
+    presents new addresses.  Each with graph replay on (the default) and off:
+    ms per step (CUDA events on the stream, the optimiser step included) and
+    the graphs the context captured per timed step."""
+    import torch
+    from paper_2505_02041_gb300 import _lib, fluence
+    with torch.no_grad():
+        target = h.forward(e, s).clone()
+    stream = torch.cuda.current_stream(e.device)
+    out = {}
+    for mode in ("steady", "moving"):
+        for graphs in (True, False):
+            _lib.hrc_set_graphs(h.ctx, graphs)
+            p = torch.nn.Parameter(0.5 * e.clone())
+            opt = torch.optim.Adam([p], lr=0.01)
+            keep = []
+
+            def step():
+                ein, sin = p, s
+                if mode == "moving":
+                    ein, sin = p.clone(), s.clone()
+                    keep.append((ein, sin))
+                    if len(keep) > 16:
+                        keep.pop(0)
+                loss = torch.mean((fluence(h, ein, sin) - target) ** 2)
+                opt.zero_grad(set_to_none=True)
+                loss.backward()
+                opt.step()
+
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize(e.device)
+            c0 = _lib.hrc_graph_captures(h.ctx)
+            ts = []
+            for _ in range(steps):
+                a = torch.cuda.Event(enable_timing=True)
+                z = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                z.record(stream)
+                z.synchronize()
+                ts.append(a.elapsed_time(z))
+            out[f"{mode}_graphs_{'on' if graphs else 'off'}"] = {
+                "ms_per_step": statistics.mean(ts),
+                "graph_captures_per_step": (_lib.hrc_graph_captures(h.ctx) - c0) / steps}
+            del keep, opt, p
+    _lib.hrc_set_graphs(h.ctx, True)
+    return out
+
+
 def bench_channels(h, e, s, timed, steps=10):
     """Per-channel extinction (sigma_t[C][H][W]: the workload's extinction
     scaled by 1, 0.5 and 2 per channel): graph-launched forward and
@@ -712,6 +769,7 @@ def run_ours(args):
     line["multi_bounce"] = bench_bounces(h, e, s, timed, hbm_peak)
     line["environment"] = bench_environment(h, fwd, fwd_bwd, timed)
     line["per_channel_extinction"] = bench_channels(h, e, s, timed)
+    line["autograd"] = bench_autograd(h, e, s)
     if args.precisions and world == 1:
         import oracle
         Fr = oracle.fluence(e_np, s_np)

@@ -7,8 +7,9 @@
  * Eqs. 18-20), the merge down the cascades R_{N-1}..R_0 (Eqs. 13-17) and the
  * sum over four quadrants (Algorithm 1, procedure Lighting), plus the exact
  * adjoint of all of it.  Options of a context add the Eq. 21 cross blur
- * (hrc_set_cross_blur), multiple bounces (hrc_fluence_bounces), an
- * environment map for R_N (hrc_set_environment) and per-channel extinction
+ * (hrc_set_cross_blur), multiple bounces (hrc_fluence_bounces), offscreen
+ * light as R_N from an environment map (hrc_set_environment) or from a
+ * caller-supplied table (hrc_set_top_radiance), and per-channel extinction
  * (hrc_set_channel_extinction); all are off by default.
  *
  * Data conventions (shared by every entry point):
@@ -25,13 +26,18 @@
  *     It allocates them in hrc_create / hrc_create_batched and in the set-up
  *     calls that enable an option (hrc_set_precision for FP64,
  *     hrc_set_cross_blur, hrc_reserve_bounces, hrc_set_environment,
- *     hrc_set_channel_extinction).  Compute calls allocate no buffer; the
- *     first call with a new set of pointers (or a new configuration)
- *     captures and instantiates a CUDA graph of the pass, which the driver
- *     allocates, and later calls with the same pointers replay it.  A
- *     context keeps eight such graphs (the oldest is replaced), so a caller
- *     whose tensors move every step pays a capture every step: keep the
- *     buffers at fixed addresses, or use hrc_set_graphs(ctx, 0).
+ *     hrc_set_top_radiance, hrc_set_channel_extinction).  Compute calls
+ *     allocate no buffer; the first call with a new set of pointers (or a
+ *     new configuration) captures and instantiates a CUDA graph of the
+ *     pass, which the driver allocates, and later calls with the same
+ *     pointers replay it.  A
+ *     context keeps eight such graphs (the oldest is replaced).  When at
+ *     least six of them were never replayed (the caller's tensors move
+ *     every call), a pass with a new pointer set is launched directly
+ *     instead of captured, unless that set was seen in the last sixteen
+ *     such passes; so a caller whose tensors move every step pays about the
+ *     direct-launch cost (hrc_set_graphs(ctx, 0)), and one whose tensors
+ *     recur gets graphs.
  *   - Compute calls are asynchronous on the context's stream: HRC_OK means
  *     "enqueued".  Argument errors are reported synchronously; an
  *     asynchronous CUDA error surfaces as HRC_ECUDA on a later call.

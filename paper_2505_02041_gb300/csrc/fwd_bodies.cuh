@@ -55,23 +55,64 @@ template <class A> __device__ __forceinline__ void piece_factors(A sg, A len, A 
 
 // Shared-memory tile of a 32 x 32 image block with a 4-pixel halo (the
 // longest directly traced ray, v_2(k), reaches 4 pixels along and across):
-// extinction, the piece factors of the three classes, and the emission.
-// Outside the image every field is vacuum (sigma = e = 0, t = 1, w = l).
+// the piece factors {t, w} of the three ray classes as 2-vectors, and the
+// emission with the extinction (one float4 per pixel in fp32 with C <= 3,
+// else planes), so a ray piece costs two shared loads.  Outside the image
+// every field is vacuum (sigma = e = 0, t = 1, w = l).
 constexpr int TR_TILE = 32, TR_HALO = 4, TR_REG = TR_TILE + 2 * TR_HALO, TR_PITCH = TR_REG + 1;
 constexpr int TR_PLANE = TR_REG * TR_PITCH;
 
 template <class A, int C> struct TraceTile {
-    A *s;       // [PLANE]
-    A *t;       // [3][PLANE]
-    A *w;       // [3][PLANE]
-    A *e;       // [C][PLANE]
+    using V2 = typename Vec2<A>::T;
+    static constexpr bool packed = PackES<A, C>::packed;
+    V2 *tw;        // [3][PLANE]
+    float4 *es4;   // [PLANE] when packed
+    A *e;          // [C][PLANE] otherwise
+    A *s;          // [PLANE] otherwise
     __device__ __forceinline__ explicit TraceTile(unsigned char *smem) {
-        s = reinterpret_cast<A *>(smem);
-        t = s + TR_PLANE;
-        w = t + 3 * TR_PLANE;
-        e = w + 3 * TR_PLANE;
+        tw = reinterpret_cast<V2 *>(smem);
+        es4 = reinterpret_cast<float4 *>(tw + 3 * TR_PLANE);
+        e = reinterpret_cast<A *>(tw + 3 * TR_PLANE);
+        s = e + C * TR_PLANE;
     }
-    static constexpr size_t bytes() { return sizeof(A) * (7 + C) * TR_PLANE; }
+    static constexpr size_t bytes() {
+        return sizeof(V2) * 3 * TR_PLANE + (packed ? sizeof(float4) * TR_PLANE : sizeof(A) * (C + 1) * TR_PLANE);
+    }
+    __device__ __forceinline__ void emis(int o, A (&em)[C], A &sg) const {
+        if constexpr (packed) {
+            const float4 v = es4[o];
+            em[0] = v.x;
+            if constexpr (C > 1) em[1] = v.y;
+            if constexpr (C > 2) em[2] = v.z;
+            sg = v.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) em[c] = e[c * TR_PLANE + o];
+            sg = s[o];
+        }
+    }
+    // the fields of region pixel o from its extinction and emission
+    __device__ __forceinline__ void put(int o, A sg, const A (&ev)[C]) const {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            A tc, wc;
+            piece_factors<A>(sg, class_len<A>(c), tc, wc);
+            V2 p;
+            p.x = tc;
+            p.y = wc;
+            tw[c * TR_PLANE + o] = p;
+        }
+        if constexpr (packed) {
+            float4 v = make_float4(ev[0], 0.f, 0.f, sg);
+            if constexpr (C > 1) v.y = ev[1];
+            if constexpr (C > 2) v.z = ev[2];
+            es4[o] = v;
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) e[c * TR_PLANE + o] = ev[c];
+            s[o] = sg;
+        }
+    }
     template <class IN>
     __device__ __forceinline__ void stage(int W, int H, int x0, int y0, const IN *__restrict__ ein,
                                           const IN *__restrict__ sin) {
@@ -81,24 +122,16 @@ template <class A, int C> struct TraceTile {
             const int x = x0 - TR_HALO + rx, y = y0 - TR_HALO + ry;
             const bool in = x >= 0 && x < W && y >= 0 && y < H;
             const long long pix = (long long)y * W + x;
-            const int o = ry * TR_PITCH + rx;
-            const A sg = in ? A(sin[pix]) : A(0);
-            s[o] = sg;
+            A ev[C];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                A tc, wc;
-                piece_factors<A>(sg, class_len<A>(c), tc, wc);
-                t[c * TR_PLANE + o] = tc;
-                w[c * TR_PLANE + o] = wc;
-            }
-#pragma unroll
-            for (int c = 0; c < C; ++c) e[c * TR_PLANE + o] = in ? A(ein[c * HW + pix]) : A(0);
+            for (int c = 0; c < C; ++c) ev[c] = in ? A(ein[c * HW + pix]) : A(0);
+            put(ry * TR_PITCH + rx, in ? A(sin[pix]) : A(0), ev);
         }
     }
     // The same staging with the region of e and sigma fetched by TMA tensor
     // copies (fp32 inputs; the out-of-grid part of the box reads as zero,
     // which is vacuum).  The boxes land in a staging area that overlaps the
-    // w and e planes: every thread first takes its pixels into registers,
+    // {t, w} planes: every thread first takes its pixels into registers,
     // then the planes are written.  Returns 0, or kWaitTimeout / kWaitLost
     // when the copy wait gave up.
     __device__ __forceinline__ int stage_tma(int x0, int y0, const CUtensorMap *tme, const CUtensorMap *tms,
@@ -106,7 +139,8 @@ template <class A, int C> struct TraceTile {
         static_assert(sizeof(A) == 4, "fp32 staging");
         constexpr int BOX = TR_REG * TR_REG;                        // 40 x 40
         constexpr int PER = (BOX + 255) / 256;                      // pixels per thread (256 threads)
-        float *stg = reinterpret_cast<float *>(w);                  // [C + 1][BOX]
+        static_assert((C + 1) * BOX * sizeof(float) <= 3 * TR_PLANE * sizeof(V2), "staging fits the {t, w} planes");
+        float *stg = reinterpret_cast<float *>(tw);                 // [C + 1][BOX]
         if (threadIdx.x == 0) {
             mbar_init(bar, 1);
             mbar_init_fence();
@@ -135,18 +169,7 @@ template <class A, int C> struct TraceTile {
             const int i = threadIdx.x + 256 * k;
             if (i >= BOX) break;
             const int ry = i / TR_REG, rx = i - ry * TR_REG;
-            const int o = ry * TR_PITCH + rx;
-            const A sg = sv[k];
-            s[o] = sg;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                A tc, wc;
-                piece_factors<A>(sg, class_len<A>(c), tc, wc);
-                t[c * TR_PLANE + o] = tc;
-                w[c * TR_PLANE + o] = wc;
-            }
-#pragma unroll
-            for (int c = 0; c < C; ++c) e[c * TR_PLANE + o] = ev[k][c];
+            put(ry * TR_PITCH + rx, sv[k], ev[k]);
         }
         return 0;
     }
@@ -163,17 +186,18 @@ __device__ __forceinline__ void trace_pieces(const TraceTile<typename Prec<P>::A
     if constexpr (J < END) {
         using pc = PieceAt<J>;
         const int o = base + pc::du * su + pc::dv * sv;
-        A t = tt.t[pc::cls * TR_PLANE + o];
-        A w = tt.w[pc::cls * TR_PLANE + o];
+        const typename TraceTile<A, C>::V2 p = tt.tw[pc::cls * TR_PLANE + o];
+        A t = p.x, w = p.y, em[C], sg;
+        tt.emis(o, em, sg);
         if constexpr (pc::full != 0) {
             w = w * (A(1) + t);
             t = t * t;
         }
         const A wt = Tacc * w;
 #pragma unroll
-        for (int c = 0; c < C; ++c) L[c] = fma(wt, tt.e[c * TR_PLANE + o], L[c]);
+        for (int c = 0; c < C; ++c) L[c] = fma(wt, em[c], L[c]);
         Tacc *= t;
-        if constexpr (Prec<P>::LOG) tau = fma(tt.s[o], A(pc::full ? 2 : 1) * class_len<A>(pc::cls), tau);
+        if constexpr (Prec<P>::LOG) tau = fma(sg, A(pc::full ? 2 : 1) * class_len<A>(pc::cls), tau);
         trace_pieces<P, C, J + 1, END>(tt, base, su, sv, L, Tacc, tau);
     }
 }

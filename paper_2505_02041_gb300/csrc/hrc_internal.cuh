@@ -145,6 +145,16 @@ template <> struct Prec<P_FP16> { using SL = __half;         using ST = float;  
 template <> struct Prec<P_BF16> { using SL = __nv_bfloat16;  using ST = float;  using A = float;  static constexpr bool LOG = true;  };
 template <> struct Prec<P_FP64> { using SL = double;         using ST = double; using A = double; static constexpr bool LOG = false; };
 
+// Shared-memory tiles of the two trace kernels: a pixel's {t, w} of one ray
+// class as one 2-vector, and {e0, e1, e2, sigma} as one float4 in fp32 with
+// C <= 3 (one shared load each); otherwise e and sigma as separate planes.
+template <class A> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+template <class A, int C> struct PackES {
+    static constexpr bool packed = sizeof(A) == 4 && C <= 3;
+};
+
 __device__ __forceinline__ float to_acc(float x) { return x; }
 __device__ __forceinline__ double to_acc(double x) { return x; }
 __device__ __forceinline__ float to_acc(__half x) { return __half2float(x); }

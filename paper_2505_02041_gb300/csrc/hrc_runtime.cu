@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -244,11 +245,18 @@ struct hrc_ctx {
         const void *p[8] = {};
         cudaGraphExec_t exec = nullptr;
         int launches = 0;
+        long long replays = 0;
     };
     GraphEntry graphs[8];
     int graph_next = 0;
     bool use_graphs = true;
     long long graph_captures = 0;   // graphs captured and instantiated so far
+    // Passes whose pointer set is new while the cache thrashes (most cached
+    // graphs never replayed: the caller's tensors move every call) launch
+    // directly; the keys of those passes are remembered, and one that comes
+    // back is captured after all.
+    unsigned long long seen[16] = {};
+    int seen_next = 0;
     cudaStream_t cap_stream = nullptr;
     // batched contexts
     bool batched = false;
@@ -367,8 +375,40 @@ hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue
             std::memcmp(g.p, key, sizeof(pk.p)) == 0) {
             cudaError_t e = cudaGraphLaunch(g.exec, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+            ++g.replays;
             ctx->launches = g.launches;
             if (timed) ctx->rec.recs = g.recs;
+            return HRC_OK;
+        }
+    }
+    if (!timed) {
+        // the key of this pass (FNV-1a over the pass kind, the configuration and the pointers)
+        unsigned long long hk = 1469598103934665603ULL;
+        auto mix = [&hk](unsigned long long v) {
+            for (int b = 0; b < 8; ++b) {
+                hk ^= (v >> (8 * b)) & 0xffULL;
+                hk *= 1099511628211ULL;
+            }
+        };
+        mix((unsigned long long)kind);
+        mix((unsigned long long)ctx->prec);
+        mix((unsigned long long)ctx->sched);
+        mix((unsigned long long)ctx->mgroups);
+        mix((unsigned long long)(ctx->mthreads * 8 + ctx->vmajor * 4 + ctx->mdown));
+        for (int i = 0; i < 8; ++i) mix((unsigned long long)(uintptr_t)key[i]);
+        int unreplayed = 0;
+        for (const auto &g : ctx->graphs) unreplayed += (g.exec && g.replays == 0) ? 1 : 0;
+        bool seen = false;
+        for (unsigned long long h : ctx->seen) seen = seen || h == hk;
+        if (unreplayed >= 6 && !seen) {
+            ctx->seen[ctx->seen_next] = hk;
+            ctx->seen_next = (ctx->seen_next + 1) % 16;
+            ctx->rec.ext = false;
+            ctx->rec.coarse = false;
+            ctx->rec.reset(ctx->stream);
+            cudaError_t e = enqueue(ctx->stream, &ctx->launches, &ctx->rec);
+            ctx->rec.finish();
+            if (e != cudaSuccess) return cuda_fail(ctx, e, where);
             return HRC_OK;
         }
     }
@@ -412,6 +452,7 @@ hrc_status run_pass_key(hrc_ctx *ctx, int kind, const PassKey &pk, ENQ &&enqueue
     slot.recs = timed ? ctx->rec.recs : std::vector<Recorder::Rec>();
     std::memcpy(slot.p, key, sizeof(pk.p));
     slot.launches = n;
+    slot.replays = 0;
     e = cudaGraphLaunch(exec, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, where);
     ctx->launches = n;

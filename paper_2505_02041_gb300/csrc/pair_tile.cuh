@@ -28,16 +28,6 @@ constexpr int PT_U = 16, PT_V = 32, PT_HALO = 4;
 constexpr int PT_RU = PT_U + 2 * PT_HALO, PT_RV = PT_V + 2 * PT_HALO, PT_PITCH = PT_RV + 1;
 constexpr int PT_PLANE = PT_RU * PT_PITCH;
 
-template <class A> struct Vec2;
-template <> struct Vec2<float> { using T = float2; };
-template <> struct Vec2<double> { using T = double2; };
-
-// e and sigma of one pixel.  fp32 with C <= 3 packs {e0, e1, e2, sigma} in a
-// float4 (one shared load); otherwise separate planes.
-template <class A, int C> struct PackES {
-    static constexpr bool packed = std::is_same<A, float>::value && C <= 3;
-};
-
 // dw/dsigma of a half piece of length l with t = exp(-sigma l):
 // l^2 phi'(sigma l), phi'(x) = (e^-x (1 + x) - 1) / x^2, by its Taylor
 // series near 0.

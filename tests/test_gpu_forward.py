@@ -265,3 +265,30 @@ def test_persistent_merge_down_wait_times_out_and_recovers():
     F = h.forward(ed, sd)
     h.sync()
     assert_fp32(F.cpu().numpy(), oracle.fluence(e, s))
+
+
+def test_graph_cache_launches_directly_when_pointers_move():
+    """Outputs at a new address on every call: the first six passes are
+    captured, then (six cached graphs never replayed) new pointer sets run
+    as direct launches; a cached set is replayed, a recurring new set is
+    captured after all.  Every output is the same fluence."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC, _lib
+    e, s = scenes.random_scene(64, 48, 2, 53)
+    h = HRC(64, 48, 2)
+    ed, sd = to_dev(e), to_dev(s)
+    outs = [torch.full((2, 48, 64), float("nan"), device="cuda") for _ in range(24)]
+    for o in outs:
+        h.forward(ed, sd, o)
+    h.sync()
+    assert _lib.hrc_graph_captures(h.ctx) == 6
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    assert_fp32(outs[0].cpu().numpy(), oracle.fluence(e, s))
+    h.forward(ed, sd, outs[0])                   # cached: replayed
+    assert _lib.hrc_graph_captures(h.ctx) == 6
+    h.forward(ed, sd, outs[20])                  # launched directly before, seen again: captured
+    h.forward(ed, sd, outs[20])
+    h.sync()
+    assert _lib.hrc_graph_captures(h.ctx) == 7
+    assert torch.equal(outs[20], outs[1])
