@@ -911,4 +911,184 @@ __device__ __forceinline__ void body_fluence(const Plan &pl, OUT *__restrict__ F
     }
 }
 
+
+// R_0^q(x, 0, v .. v + 3) (v a multiple of 4) added to a[0 .. 3]: the n = 0
+// case of merge_down_entry for four consecutive v, with the same arithmetic
+// per entry.  T rows and the near R row are read as aligned quads; a far
+// run starts off the quad boundary (at v -+ 1 at odd x, v -+ 2 at even x)
+// and is read as the aligned quad at v plus the one or two entries beyond
+// it.  Entries v + l past V (inside the padded row) are computed and never
+// used.
+template <int P, int C, bool ENV>
+__device__ __forceinline__ void r0_quad_add(const Plan &pl, int q, int x, int v, typename Prec<P>::A (&a)[4][C]) {
+    using A = typename Prec<P>::A;
+    const QuadGeom &g = pl.q[q];
+    if (g.N < 1 || x >= g.U) {                 // the probe at u + 1 is outside: the environment
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const A ev = renv<P, C, ENV>(pl, q, 0, 0, c);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) a[l][c] += ev;
+        }
+        return;
+    }
+    const bool top = g.N <= 1;                  // R_1 is R_N: 0, or the environment map
+    const A Ap = arc<P>(pl, 1, 1), Am = arc<P>(pl, 1, 0);
+    const uint64_t pol = l2_evict_first();      // T rows: read once from HBM
+    const int V = g.V;
+    A acc[4][C];
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[l][c] = A(0);
+    if (x & 1) {                                // Eq. 14 at n = 0: k = j = 1, 0
+        const TLevel<P, C> T0(pl, q, 0);
+        const int xq = (x + 1) >> 1;
+        const bool rq_ok = !top && xq < g.Un[1];
+        const RLevel<P, C> R1(pl, q, rq_ok ? 1 : 0);
+#pragma unroll
+        for (int j = 1; j >= 0; --j) {
+            const A Aj = j ? Ap : Am;
+            Iv<P, C> t[4];
+            T0.load4_ef(x, j, v, pol, t);
+            A tr[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) tr[l] = t[l].trans();
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const A ev = renv<P, C, ENV>(pl, q, 1, j, c);
+                A r[4] = {ev, ev, ev, ev}, w[4];
+                if (rq_ok) {
+                    // far run v + 2j - 1 .. v + 2j + 2: the quad at v and the entry before or after it
+                    R1.load4(xq, j, c, v, w);
+                    if (j) {
+#pragma unroll
+                        for (int l = 0; l < 3; ++l)
+                            if (v + 1 + l < V) r[l] = w[l + 1];
+                        if (v + 4 < V) r[3] = R1.load(xq, j, c, v + 4);
+                    } else {
+                        if (v >= 1) r[0] = R1.load(xq, j, c, v - 1);
+#pragma unroll
+                        for (int l = 1; l < 4; ++l)
+                            if (v + l - 1 < V) r[l] = w[l - 1];
+                    }
+                }
+#pragma unroll
+                for (int l = 0; l < 4; ++l) acc[l][c] += fma(Aj, t[l].L[c], tr[l] * r[l]);
+            }
+        }
+    } else {                                    // Eqs. 15-17 at n = 0: k = 2, 0 and j = 1, 0
+        const TLevel<P, C> T1(pl, q, 1);
+        const int x2 = x >> 1;
+        const bool r1_ok = !top && x2 + 1 < g.Un[1];
+        const RLevel<P, C> R1(pl, q, top ? 0 : 1);
+#pragma unroll
+        for (int j = 1; j >= 0; --j) {
+            const A Aj = j ? Ap : Am;
+            Iv<P, C> t[4];
+            T1.load4_ef(x2, 2 * j, v, pol, t);
+            A tr[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) tr[l] = t[l].trans();
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const A ev = renv<P, C, ENV>(pl, q, 1, j, c);
+                A n0[4] = {ev, ev, ev, ev}, f[4] = {ev, ev, ev, ev}, w[4];
+                if (!top) R1.load4(x2, j, c, v, n0);
+                if (r1_ok) {
+                    // far run v + 4j - 2 .. v + 4j + 1: the quad at v and the pair after or before it
+                    R1.load4(x2 + 1, j, c, v, w);
+                    if (j) {
+                        if (v + 2 < V) f[0] = w[2];
+                        if (v + 3 < V) f[1] = w[3];
+                        if (v + 4 < V) {
+                            A p0, p1;
+                            R1.load2(x2 + 1, j, c, v + 4, p0, p1);
+                            f[2] = p0;
+                            if (v + 5 < V) f[3] = p1;
+                        }
+                    } else {
+                        if (v >= 2) R1.load2(x2 + 1, j, c, v - 2, f[0], f[1]);
+                        if (v < V) f[2] = w[0];
+                        if (v + 1 < V) f[3] = w[1];
+                    }
+                }
+#pragma unroll
+                for (int l = 0; l < 4; ++l) acc[l][c] += A(0.5) * (n0[l] + fma(Aj, t[l].L[c], tr[l] * f[l]));
+            }
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+        for (int c = 0; c < C; ++c) a[l][c] += acc[l][c];
+}
+
+// body_fluence with four consecutive pixels along v per thread (one 4-wide
+// access per plane and row; r0_quad_add), eight lanes one tile line; a
+// warp's four line groups are lines two apart, so its x = u + 1 share one
+// parity and it runs one branch of the merge.  Same sum, same order, same
+// shared tile.  Used for the 16-bit storage modes on large grids, where a
+// 2-wide access moves only 4 bytes of radiance (any multiple of 32 threads;
+// 8 warps keep every line group busy).
+template <int P, int C, class OUT, bool ENV = false>
+__device__ __forceinline__ void body_fluence4(const Plan &pl, OUT *__restrict__ F, int bx, int by, unsigned char *smem) {
+    using A = typename Prec<P>::A;
+    A (*tile)[32][33] = reinterpret_cast<A (*)[32][33]>(smem);   // [C][y][x] of the tile
+    const int W = pl.W, H = pl.H;
+    const int x0 = bx * 32, y0 = by * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ql = lane & 7, grp = lane >> 3;
+    // line group p = 0 .. 7 -> tile lines 8 (p >> 1) + (p & 1) + 2 grp
+    auto line = [&](int p) { return 8 * (p >> 1) + (p & 1) + 2 * grp; };
+    auto add_frame = [&](int q, int x, int y, A (&a)[4][C]) {
+        int u, v;
+        image_to_frame(q, W, H, x, y, u, v);
+        r0_quad_add<P, C, ENV>(pl, q, u + 1, v, a);
+    };
+    for (int p = warp; p < 8; p += nw) {        // q0, q1: pixels (x, y .. y + 3)
+        const int ca = line(p), y = y0 + 4 * ql;
+        A a[4][C];
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+#pragma unroll
+            for (int c = 0; c < C; ++c) a[l][c] = A(0);
+        if (y < H && x0 + ca < W) {
+            add_frame(0, x0 + ca, y, a);
+            add_frame(1, x0 + ca, y, a);
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) tile[c][4 * ql + l][ca] = a[l][c];
+    }
+    __syncthreads();
+    const long long HW = (long long)W * H;
+    // F rows whose width is a multiple of 4, from an aligned base, take 4-wide stores
+    const bool wide = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(F) & (4 * sizeof(OUT) - 1)) == 0;
+    for (int p = warp; p < 8; p += nw) {        // q2, q3: pixels (x .. x + 3, y)
+        const int ra = line(p), x = x0 + 4 * ql;
+        if (x >= W || y0 + ra >= H) continue;
+        A a[4][C];
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) a[l][c] = tile[c][ra][4 * ql + l];
+        add_frame(2, x, y0 + ra, a);
+        add_frame(3, x, y0 + ra, a);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            OUT *o = F + c * HW + (long long)(y0 + ra) * W + x;
+            if (wide) {
+                const OUT t[4] = {(OUT)a[0][c], (OUT)a[1][c], (OUT)a[2][c], (OUT)a[3][c]};
+                st4(o, t);
+            } else {
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+                    if (x + l < W) o[l] = (OUT)a[l][c];
+            }
+        }
+    }
+}
+
 }  // namespace hrc

@@ -336,6 +336,26 @@ __device__ __forceinline__ void ld2_ef(const __half *p, uint64_t pol, float &x, 
 __device__ __forceinline__ void ld2_ef(const __nv_bfloat16 *p, uint64_t pol, float &x, float &y) {
     ld2_ef_16<__nv_bfloat162>(p, pol, x, y);
 }
+// entries p[0 .. 3] (p 4-element aligned) with an L2 policy
+__device__ __forceinline__ void ld4_ef(const float *p, uint64_t pol, float (&r)[4]) {
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3])
+                 : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld4_ef(const double *p, uint64_t, double (&r)[4]) { ld4(p, r); }
+template <class H2> __device__ __forceinline__ void ld4_ef_16(const void *p, uint64_t pol, float (&r)[4]) {
+    unsigned u0, u1;
+    asm volatile("ld.global.L2::cache_hint.v2.b32 {%0, %1}, [%2], %3;" : "=r"(u0), "=r"(u1) : "l"(p), "l"(pol));
+    const H2 a = *reinterpret_cast<const H2 *>(&u0), b = *reinterpret_cast<const H2 *>(&u1);
+    r[0] = __low2float(a);
+    r[1] = __high2float(a);
+    r[2] = __low2float(b);
+    r[3] = __high2float(b);
+}
+__device__ __forceinline__ void ld4_ef(const __half *p, uint64_t pol, float (&r)[4]) { ld4_ef_16<__half2>(p, pol, r); }
+__device__ __forceinline__ void ld4_ef(const __nv_bfloat16 *p, uint64_t pol, float (&r)[4]) {
+    ld4_ef_16<__nv_bfloat162>(p, pol, r);
+}
 
 // ---------------------------------------------------------------------------
 // Level addressing
@@ -429,6 +449,22 @@ template <int P, int C> struct TLevel {
         return r;
     }
     // entries v and v+1 (v even), loaded with an L2 policy
+    // entries v .. v+3 (v a multiple of 4; v + 3 < Vs), loaded with an L2 policy
+    __device__ __forceinline__ void load4_ef(int x, int k, int v, uint64_t pol, Iv<P, C> (&r)[4]) const {
+        using A = typename Prec<P>::A;
+        const char *g = row(x, k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            A t[4];
+            ld4_ef(reinterpret_cast<const SL *>(g) + (long long)c * Vs + v, pol, t);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) r[l].L[c] = t[l];
+        }
+        A t[4];
+        ld4_ef(reinterpret_cast<const ST *>(g + (long long)C * Vs * sizeof(SL)) + v, pol, t);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) r[l].t = t[l];
+    }
     __device__ __forceinline__ void load2_ef(int x, int k, int v, uint64_t pol, Iv<P, C> &a, Iv<P, C> &b) const {
         const char *g = row(x, k);
 #pragma unroll

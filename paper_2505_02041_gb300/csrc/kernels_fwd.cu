@@ -74,6 +74,17 @@ __global__ void __launch_bounds__(512) k_fluence(Plan pl, OUT *__restrict__ F) {
     body_fluence<P, C, OUT, ENV>(pl, F, blockIdx.x, blockIdx.y, smem);
 }
 
+// Four pixels per thread, 128 threads, 7 blocks per SM (at most 73
+// registers): without a cap the quad body takes 80-100 registers and 5
+// blocks per SM and is slower than the pair body; with 8 blocks (64
+// registers) it spills more and gains less (bf16, 1024^2: 49 us with pairs,
+// 42 us at 8 blocks, 39 us at 7, 59 us at 6).
+template <int P, int C, class OUT, bool ENV>
+__global__ void __launch_bounds__(128, 7) k_fluence4(Plan pl, OUT *__restrict__ F) {
+    __shared__ __align__(16) unsigned char smem[fluence_smem<P, C>()];
+    body_fluence4<P, C, OUT, ENV>(pl, F, blockIdx.x, blockIdx.y, smem);
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
@@ -307,14 +318,24 @@ static cudaError_t fwd_impl(const Plan &pl, const RayTable &rt, const void *e, c
         }
         dim3 grid((pl.W + 31) / 32, (pl.H + 31) / 32);
         rec->begin(K_FLUENCE_SUM, 0, by);
-        // 256 threads (two pixels each, one line pair per warp) on large
-        // grids; grids of fewer than 600 tiles (about 4 per SM; 512^2 and
-        // below) take 512 threads per tile, so that the GPU still holds
-        // enough loads in flight
-        const int ft = (long long)grid.x * grid.y < 600 ? 512 : 256;
-        if (P == P_FP64) {
+        // Pairs of pixels per thread, 256 threads on large grids; grids of
+        // fewer than 600 tiles (about 4 per SM; 512^2 and below) take 512, so
+        // that the GPU still holds enough loads in flight.  The 16-bit modes
+        // on large grids take four pixels per thread (k_fluence4): a pair of
+        // 16-bit radiances is only a 4-byte access.
+        const long long tiles = (long long)grid.x * grid.y;
+        const int ft = tiles < 600 ? 512 : 256;
+        if constexpr (P == P_FP64) {
             if (env) k_fluence<P, C, double, true><<<grid, ft, 0, st>>>(pl, (double *)F);
             else k_fluence<P, C, double, false><<<grid, ft, 0, st>>>(pl, (double *)F);
+        } else if constexpr (P == P_FP16 || P == P_BF16) {
+            if (tiles >= 600) {
+                if (env) k_fluence4<P, C, float, true><<<grid, 128, 0, st>>>(pl, (float *)F);
+                else k_fluence4<P, C, float, false><<<grid, 128, 0, st>>>(pl, (float *)F);
+            } else {
+                if (env) k_fluence<P, C, float, true><<<grid, ft, 0, st>>>(pl, (float *)F);
+                else k_fluence<P, C, float, false><<<grid, ft, 0, st>>>(pl, (float *)F);
+            }
         } else {
             if (env) k_fluence<P, C, float, true><<<grid, ft, 0, st>>>(pl, (float *)F);
             else k_fluence<P, C, float, false><<<grid, ft, 0, st>>>(pl, (float *)F);
