@@ -107,3 +107,25 @@ def test_merge_down_variants_bit_identical(prec, W, H, C, seed, with_env):
         h.sync()
         assert torch.equal(F, F0), mdown
     assert np.all(np.isfinite(F0.cpu().numpy()))
+
+
+@pytest.mark.parametrize("prec,C,with_env", [("bf16", 1, False), ("fp16", 2, True), ("bf16", 4, True), ("fp16", 3, False)])
+def test_reduced_precision_large_grid_forms(prec, C, with_env):
+    """Grids of 600 tiles and more take the four-pixels-per-thread fluence
+    sum in the 16-bit modes (640 x 960 = 20 x 30 tiles): against the oracle
+    at the stated bounds, for every channel count, with and without a map."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC
+    e, s = scenes.random_scene(640, 960, C, 70 + C)
+    env = _env(C, 40, 80 + C) if with_env else None
+    h = HRC(640, 960, C, 0, prec)
+    if with_env:
+        h.set_environment(to_dev(env))
+    F = h.forward(to_dev(e), to_dev(s)).cpu().numpy()
+    Fr = oracle.fluence(e, s, env=env) if with_env else oracle.fluence(e, s)
+    em = err_max(F, Fr)
+    l2 = np.linalg.norm(F - Fr) / np.linalg.norm(Fr)
+    lit = np.abs(Fr) >= 1e-3 * np.max(np.abs(Fr))
+    pr = np.max(np.abs(F - Fr)[lit] / np.abs(Fr)[lit])
+    print(f"640x960 C={C} {prec} env={with_env}: err_max={em:.3e} relL2={l2:.3e} pixel-relative={pr:.3e}")
+    assert em <= BOUNDS[prec][0] and l2 <= BOUNDS[prec][1] and pr <= BOUNDS[prec][2]
