@@ -312,9 +312,15 @@ hrc_status hrc_bounce_source(hrc_ctx *ctx, const float *emission, const float *s
                              const float *fluence, float *out);
 
 /* Waits for the context's stream and reports whether a bounded device-side
- * wait of the bulk-copy merge-down kernel gave up since the last call
- * (HRC_ETIMEOUT: that launch ended early and its outputs are incomplete;
- * the status is device-wide and is cleared by this call). */
+ * wait of its kernels (the trace kernels' tensor-copy waits, the bulk-copy
+ * merge down, the persistent merge down's dependency waits; its per-channel
+ * contexts' too) gave up since the last call: HRC_ETIMEOUT, that launch
+ * ended early and its outputs are incomplete.  The status word belongs to
+ * this context alone and is cleared by this call.  A block that gave up
+ * first waits once more, with a much longer bound, for the copies it had
+ * issued; if even that runs out the message (hrc_last_error) says so, and
+ * the results of later launches on this device are then suspect (a late
+ * copy could still land in the shared memory of another block). */
 hrc_status hrc_sync(hrc_ctx *ctx);
 
 /* Test hook for the bounded device-side waits: with extra_bytes > 0
