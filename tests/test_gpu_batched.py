@@ -149,6 +149,48 @@ def test_batched_schedules_match_persistent(precision):
         b.set_backward_recompute(False)
 
 
+def test_small_scene_batch_matches_single_and_oracle():
+    """The benchmark's small-scene batch: 256 scenes of 64^2 .. 256^2 (C = 3,
+    bf16 intervals), tuned as the benchmark tunes it.  One scene of each size:
+    forward and backward equal the single-scene path's to fp32 rounding of the
+    same bf16 arithmetic, and the fluence matches the FP64 oracle at the bf16
+    bounds (max error 6e-3 of the largest value, relative L2 2e-3)."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC, BatchedHRC
+    sizes = scenes.batched_sizes(256, 5, (64, 128, 256))
+    es, ss = [], []
+    for i, X in enumerate(sizes):
+        e, s = scenes.scene_disks_rects_fog(X, X, 3, 1000 + i)
+        es.append(torch.from_numpy(e))
+        ss.append(torch.from_numpy(s))
+    b = BatchedHRC([(X, X) for X in sizes], 3, 0, "bf16")
+    e, s = b.pack(es, ss)
+    b.autotune(e, s, reps=1)
+    F = b.forward(e, s)
+    gF = torch.randn(e.numel(), device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    ge, gs = b.backward(gF)
+    b.sync()
+    Fs, ges, gss, gFs = b.unpack(F), b.unpack(ge), b.unpack(gs, "s"), b.unpack(gF)
+    checked = set()
+    for i, X in enumerate(sizes):
+        if X in checked:
+            continue
+        checked.add(X)
+        h1 = HRC(X, X, 3, 0, "bf16")
+        F1 = h1.forward(es[i].cuda(), ss[i].cuda())
+        ge1, gs1 = h1.backward(gFs[i].contiguous())
+        assert err_max(Fs[i].cpu().numpy(), F1.cpu().numpy()) <= 1e-5, X
+        assert err_max(ges[i].cpu().numpy(), ge1.cpu().numpy()) <= 1e-5, X
+        assert err_max(gss[i].cpu().numpy(), gs1.cpu().numpy()) <= 1e-5, X
+        Fr = oracle.fluence(es[i].numpy(), ss[i].numpy())
+        Fg = Fs[i].cpu().numpy()
+        assert np.max(np.abs(Fg - Fr)) <= 6e-3 * np.max(np.abs(Fr)), X
+        assert np.linalg.norm(Fg - Fr) <= 2e-3 * np.linalg.norm(Fr), X
+        h1.close()
+    assert checked == {64, 128, 256}
+    b.close()
+
+
 @pytest.mark.slow
 def test_full_size_64_scene_batch_against_oracle():
     """The benchmark's batch at full size: 64 scenes of 128^2 .. 2048^2
