@@ -292,3 +292,26 @@ def test_graph_cache_launches_directly_when_pointers_move():
     h.sync()
     assert _lib.hrc_graph_captures(h.ctx) == 7
     assert torch.equal(outs[20], outs[1])
+
+
+@pytest.mark.parametrize("W,H", [(16384, 24), (24, 16384)])
+def test_maximum_extent_forward_and_backward(W, H):
+    """The largest accepted extent along one axis (16384: 14 cascades in the
+    frames that run along it, 5 in the others): forward and backward against
+    the oracle, and 16385 rejected."""
+    require_gpu()
+    from paper_2505_02041_gb300 import HRC, _lib
+    e, s = scenes.random_scene(W, H, 1, 90)
+    gF = scenes.rng(91).normal(size=e.shape).astype(np.float32)
+    h = HRC(W, H, 1)
+    F = h.forward(to_dev(e), to_dev(s))
+    ge, gs = h.backward(to_dev(gF))
+    h.sync()
+    assert_fp32(F.cpu().numpy(), oracle.fluence(e, s))
+    ge_r, gs_r = oracle.fluence_adjoint(e, s, gF)
+    assert err_max(ge.cpu().numpy(), ge_r) <= 1e-4
+    assert err_max(gs.cpu().numpy(), gs_r) <= 1e-4
+    h.close()
+    with pytest.raises(_lib.HRCError) as ex:
+        HRC(W + 1 if W > H else W, H + 1 if H > W else H, 1)
+    assert ex.value.status == _lib.HRC_EINVAL
